@@ -1,0 +1,207 @@
+"""Pins of the CPU oracle's tracker against what the paper and the
+mathematics fix (Sec. III-E, Eq. 4-5). No GPU."""
+import numpy as np
+import pytest
+from scipy.linalg import expm
+
+import oracle
+from paper_2609_30459_gb300 import synth
+
+
+def texture(seed, h=160, w=200, sigma=2.0):
+    return synth.quantize(synth.band_limited_texture(seed, h, w, sigma), None, 0)
+
+
+PTS = np.array([[100.0, 80.0], [60.0, 50.0], [140.0, 110.0], [45.3, 90.7], [120.6, 40.2]],
+               np.float32)
+
+
+def shifted(img, d):
+    """target(x) = source(x - d) for an integer shift d (periodic texture)."""
+    return np.roll(img, shift=(d[1], d[0]), axis=(0, 1))
+
+
+# ---------------------------------------------------------------- pattern ---
+
+def test_pattern_52_odd_lattice():
+    P = oracle.pattern(0)
+    assert P.shape == (52, 2)
+    assert len({tuple(p) for p in P.tolist()}) == 52
+    assert np.all(np.abs(P) % 2 == 1) and np.all(np.abs(P) <= 7)
+    assert np.all(np.abs(P).sum(1) <= 10)
+    rot = {(-v, u) for u, v in P.tolist()}          # 90 degree rotation
+    assert rot == {tuple(p) for p in P.tolist()}
+    assert np.allclose(P.mean(0), 0)
+
+
+# ------------------------------------------------------------- exp, solve ---
+
+@pytest.mark.parametrize("d", [(0.3, -1.2, 0.0), (1.0, 2.0, 0.3), (-0.5, 0.1, -1e-12),
+                               (2.0, -1.0, 2.5)])
+def test_se2_exp_matches_matrix_exponential(d):
+    dx, dy, dth = d
+    twist = np.array([[0, -dth, dx], [dth, 0, dy], [0, 0, 0]])
+    assert np.allclose(oracle.se2_exp(dx, dy, dth), expm(twist), atol=1e-12)
+
+
+def test_template_gain_is_solve_of_hessian():
+    img = texture(1)
+    t = oracle.template(img, 100.25, 80.5)
+    assert t["status"] == 0
+    J, H, G = t["J"], t["H"], t["G"]
+    assert np.allclose(H, J.T @ J, rtol=1e-12)
+    assert np.allclose(G, np.linalg.solve(H, J.T), rtol=1e-9, atol=1e-12)
+
+
+def test_template_on_linear_ramp_closed_form():
+    # I = a x + b y + c: bilinear sampling and the +-1 px central difference
+    # are exact, so g = (a, b) everywhere and, since the pattern is centred,
+    # I-bar = I(q). J_i = [a, b, b u_i - a v_i] / I-bar (Sec. III-E).
+    a, b, c = 2.0, 3.0, 20.0
+    y, x = np.mgrid[0:40, 0:40]
+    img = (a * x + b * y + c).astype(np.uint8)
+    qx, qy = 20.25, 19.5
+    t = oracle.template(img, qx, qy)
+    P = oracle.pattern(0)
+    mean = a * qx + b * qy + c
+    assert t["mean"] == pytest.approx(mean, rel=1e-12)
+    assert np.allclose(t["s"], a * (qx + P[:, 0]) + b * (qy + P[:, 1]) + c, rtol=1e-12)
+    assert np.allclose(t["gx"], a) and np.allclose(t["gy"], b)
+    Jref = np.stack([np.full(52, a), np.full(52, b), b * P[:, 0] - a * P[:, 1]], 1) / mean
+    assert np.allclose(t["J"], Jref, rtol=1e-12)
+    # aperture problem: translation along (b, -a) is unobservable on a ramp
+    assert t["status"] == oracle.STATUS["DEGENERATE_H"]
+    assert np.allclose(t["H"] @ np.array([b, -a, 0.0]), 0, atol=1e-12)
+
+
+# ----------------------------------------------------------- tracking pins ---
+
+def test_self_tracking_is_exactly_identity():
+    img = texture(2)
+    pyr = oracle.pyramid(img, 3)
+    r = oracle.track(pyr, pyr, PTS)
+    assert (r["status"] == 0).all()
+    assert np.array_equal(r["warp"][:, :2], PTS.astype(np.float64))
+    assert (r["warp"][:, 2] == 0).all() and (r["fb_dist"] == 0).all()
+
+
+@pytest.mark.parametrize("d", [(2, -1), (-3, 0), (1, 1), (5, 4), (-4, -5)])
+def test_integer_translation_recovered_exactly(d):
+    # target(x) = source(x - d): the residual of Eq. 4 vanishes exactly at the
+    # true warp, which is a fixed point of Eq. 5. Run to convergence.
+    src = texture(3)
+    r = oracle.track(oracle.pyramid(src, 3), oracle.pyramid(shifted(src, d), 3), PTS,
+                     gn_iters=30)
+    assert (r["status"] == 0).all()
+    assert np.abs(r["warp"][:, :2] - (PTS + np.array(d))).max() < 1e-9
+    assert np.abs(r["warp"][:, 2]).max() < 1e-9
+    assert r["fb_dist"].max() < 1e-9
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_lk_rounds_to_brute_force_ssd_argmin(seed):
+    # tiny image, noisy integer shift: the tracked flow rounds to the integer
+    # shift that minimises the mean-normalised SSD of Eq. 4 (brute force).
+    rng = np.random.default_rng(seed)
+    src = texture(10 + seed, 32, 32, 1.5)
+    d = tuple(int(v) for v in rng.integers(-2, 3, 2))
+    tgt = synth.quantize(shifted(src, d).astype(float), rng, 2.0)
+    p = np.array([[15.5, 16.0]], np.float32)
+    P = oracle.pattern(0)
+    # p = (15.5, 16): samples fall half-way between columns, on rows exactly
+    s = (src[(16 + P[:, 1]).astype(int), (15 + P[:, 0]).astype(int)].astype(float)
+         + src[(16 + P[:, 1]).astype(int), (16 + P[:, 0]).astype(int)]) / 2
+    best, arg = np.inf, None
+    for ty in range(-3, 4):
+        for tx in range(-3, 4):
+            r = (tgt[(16 + ty + P[:, 1]).astype(int), (15 + tx + P[:, 0]).astype(int)]
+                 .astype(float) + tgt[(16 + ty + P[:, 1]).astype(int),
+                                      (16 + tx + P[:, 0]).astype(int)]) / 2
+            e = r / r.mean() - s / s.mean()
+            if (e * e).sum() < best:
+                best, arg = (e * e).sum(), (tx, ty)
+    res = oracle.track([src], [tgt], p, gn_iters=30, fb=False)
+    assert res["status"][0] == 0
+    flow = res["warp"][0, :2] - p[0]
+    assert tuple(np.round(flow).astype(int)) == arg == d
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2, 3])
+def test_subpixel_se2_recovery_on_smooth_texture(seed):
+    # Render the next frame from an FP64 smooth texture under a known
+    # sub-pixel SE(2) motion; the tracked warp must match the ground truth
+    # to within the bilinear-interpolation and quantisation error.
+    rng = np.random.default_rng(seed)
+    scene = synth.PlanarScene(100 + seed, 512, 512, sigma=3.0)
+    w, h = 240, 180
+    p0 = synth.Pose()
+    th = np.deg2rad(rng.uniform(0.8, 1.5) * rng.choice([-1, 1]))
+    p1 = synth.Pose(1.0, float(th), *rng.uniform(-2.5, 2.5, 2))
+    a = scene.render(p0, w, h, noise_sigma=0)
+    b = scene.render(p1, w, h, noise_sigma=0)
+    pts = np.array([[120.0, 90.0], [60.5, 60.25], [180.0, 120.0], [90.0, 130.0]], np.float32)
+    gt = synth.PlanarScene.map_points(p0, p1, pts, w, h, scene.c_tex)
+    r = oracle.track(oracle.pyramid(a, 3), oracle.pyramid(b, 3), pts, gn_iters=10)
+    assert (r["status"] == 0).all()
+    assert np.abs(r["warp"][:, :2] - gt).max() < 0.05
+    # the warp maps pattern offsets into the new frame: rotation by -theta.
+    # Over a 7 px patch the angle is weakly observed (0.2 deg ~ 0.025 px at
+    # the rim); |theta| >= 0.8 deg keeps a sign error (>= 1.6 deg) detectable.
+    assert np.abs(r["warp"][:, 2] + p1.th).max() < np.deg2rad(0.4)
+
+
+def test_gain_invariance_single_level():
+    # Eq. 4 divides each patch by its mean: a gain of 1.5 on the target
+    # changes nothing (one level, so the integer pyramid plays no part).
+    src = (texture(4).astype(int) // 3 * 2).astype(np.uint8)     # even, <= 170
+    tgt = shifted(src, (2, 1))
+    tgt_gain = (tgt.astype(int) * 3 // 2).astype(np.uint8)
+    pts = PTS + np.float32(0.3)
+    r1 = oracle.track([src], [tgt], pts, fb=False)
+    r2 = oracle.track([src], [tgt_gain], pts, fb=False)
+    assert (r1["status"] == 0).all() and (r2["status"] == 0).all()
+    assert np.abs(r1["warp"] - r2["warp"]).max() < 1e-9
+
+
+def test_forward_backward_symmetry():
+    src = texture(5)
+    d = (3, -2)
+    A, B = oracle.pyramid(src, 3), oracle.pyramid(shifted(src, d), 3)
+    f = oracle.track(A, B, PTS, gn_iters=30)
+    q = f["warp"][:, :2].astype(np.float32)
+    b = oracle.track(B, A, q, gn_iters=30)
+    assert np.abs(b["warp"][:, :2] - PTS).max() < 1e-9
+    assert np.abs(f["back"][:, :2] - PTS).max() < 1e-9
+
+
+# ------------------------------------------------------------ status rules ---
+
+def test_status_rules():
+    S = oracle.STATUS
+    flat = np.full((80, 80), 90, np.uint8)
+    r = oracle.track(oracle.pyramid(flat, 2), oracle.pyramid(flat, 2), [[40, 40]])
+    assert r["status"][0] == S["DEGENERATE_H"]
+    zero = np.zeros((80, 80), np.uint8)
+    r = oracle.track([zero], [zero], [[40, 40]])
+    assert r["status"][0] == S["ZERO_MEAN"]
+    img = texture(6)
+    pyr = oracle.pyramid(img, 3)
+    # template reach is 7 (pattern) + 1 (gradient) + 1 (bilinear) px at level 0
+    r = oracle.track(pyr, pyr, [[8.0, 50.0], [7.99, 50.0], [190.0, 50.0], [191.0, 50.0]])
+    assert r["status"].tolist() == [0, S["OOB_TEMPLATE"], 0, S["OOB_TEMPLATE"]]
+    r = oracle.track(pyr, pyr, [[100.0, 80.0]], init=[[-30.0, 80.0, 0.0]])
+    assert r["status"][0] == S["OOB_WARP"]
+    r = oracle.track(pyr, oracle.pyramid(shifted(img, (4, 0)), 3), [[100.0, 80.0]],
+                     fb_max_dist=-1.0)
+    assert r["status"][0] == S["FB_FAIL"]
+
+
+def test_skipped_coarse_level_near_border():
+    # near the border the coarse templates leave the image and are skipped;
+    # the track still runs at the finer levels.
+    src = texture(7)
+    d = (1, 1)
+    r = oracle.track(oracle.pyramid(src, 3), oracle.pyramid(shifted(src, d), 3),
+                     [[12.0, 80.0]], gn_iters=30)
+    assert r["status"][0] == 0
+    assert np.abs(r["warp"][0, :2] - (12 + 1, 81)).max() < 1e-9
