@@ -1,0 +1,263 @@
+/*
+ * vio.h -- C ABI of the GB300 stereo visual frontend (libvio.so).
+ *
+ * Method: VkVIO, "Cross-platform GPU Acceleration for Visual-Inertial
+ * Odometry with Vulkan" (arxiv 2609.30459), Sec. III: per frame, an image
+ * pyramid (Sec. III-C), grid-cell FAST-9 detection (Sec. III-D) and
+ * patch-based inverse-compositional KLT tracking, temporal and across the
+ * stereo pair, with a forward-backward check (Sec. III-E).
+ *
+ * Conventions for every call:
+ *  - Pointers named d_* are DEVICE pointers owned by the caller; the library
+ *    never frees or retains them past the call's completion on the stream.
+ *    Host structs passed by pointer are read during the call only.
+ *  - Calls are asynchronous on the given cudaStream_t (passed as void*;
+ *    NULL = the legacy default stream). They enqueue kernels and return; no
+ *    host synchronisation and no allocation happen outside *_create.
+ *  - Arguments are validated on the host before anything is enqueued. A call
+ *    that returns non-zero has enqueued nothing, except VIO_ERR_CUDA, which
+ *    reports a launch error from the CUDA runtime.
+ *  - Images are uint8, row-major, with a row pitch in bytes. Pixel centres
+ *    are at integer coordinates; level-l coordinates are level-0 coordinates
+ *    divided by 2^l. Keypoints are float32 (x, y) in level-0 pixels.
+ *  - Batches: calls work on n_images images of one size at fixed strides
+ *    (vio_pyr_batch), e.g. the two cameras of a stereo pair, or many frames.
+ */
+#ifndef VIO_H_
+#define VIO_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status -- */
+typedef int32_t vio_status;
+enum {
+  VIO_OK = 0,
+  VIO_ERR_INVALID_ARG = 1, /* a pointer, size or parameter is invalid      */
+  VIO_ERR_CUDA = 2,        /* the CUDA runtime reported an error           */
+  VIO_ERR_OOM = 3,         /* device allocation failed in *_create          */
+  VIO_ERR_TIMEOUT = 4,     /* reserved: a bounded device-side wait expired */
+  VIO_ERR_UNSUPPORTED = 5  /* valid but outside what this build handles    */
+};
+
+/* Per-keypoint track status (uint8). */
+enum {
+  VIO_TRACK_OK = 0,
+  VIO_TRACK_OOB_TEMPLATE = 1, /* level-0 template leaves the source image    */
+  VIO_TRACK_OOB_WARP = 2,     /* a warped sample leaves the target image     */
+  VIO_TRACK_DEGENERATE_H = 3, /* level-0 Hessian not positive definite       */
+  VIO_TRACK_ZERO_MEAN = 4,    /* patch mean <= 0 (Eq. 4 undefined)           */
+  VIO_TRACK_FB_FAIL = 5,      /* forward-backward distance above threshold   */
+  VIO_TRACK_NAN = 6,          /* non-finite Gauss-Newton increment           */
+  VIO_TRACK_EMPTY = 255       /* slot holds no keypoint                      */
+};
+
+#define VIO_MAX_LEVELS 8
+#define VIO_MAX_THRESHOLDS 8
+#define VIO_MAX_K 8
+
+/* ---------------------------------------------------------------- params -- */
+/* Frontend parameters. Defaults (vio_params_default) follow the paper:
+ * threshold sequence <40,20,10,5> and k = 1 (Sec. III-D), 5 Gauss-Newton
+ * iterations per level (Sec. III-E), 50 px cells (Sec. IV-D). Values the
+ * paper leaves open: 4 levels, round-to-nearest pyramid (Eq. 1), pattern 0,
+ * forward-backward threshold 0.2 px, detection border 9 px (the level-0
+ * reach of the tracking template). */
+typedef struct {
+  int32_t n_levels;                      /* pyramid levels incl. level 0, 1..8 */
+  int32_t round_mode;                    /* 0 = nearest (Eq. 1), 1 = floor (Eq. 3) */
+  int32_t gn_iters;                      /* Gauss-Newton iterations per level  */
+  int32_t pattern_id;                    /* 0 = the 52-point odd lattice       */
+  int32_t cell_w, cell_h;                /* detection cell size, level-0 px    */
+  int32_t k_per_cell;                    /* keypoints per cell, 1..VIO_MAX_K   */
+  int32_t n_thresholds;                  /* 1..VIO_MAX_THRESHOLDS              */
+  int32_t thresholds[VIO_MAX_THRESHOLDS];/* descending FAST thresholds, >= 0   */
+  int32_t detect_border;                 /* candidates need b <= x <= w-1-b    */
+  float fb_max_dist;                     /* forward-backward threshold, px     */
+} vio_params;
+
+void vio_params_default(vio_params* p);
+
+/* ------------------------------------------------------------ pyramids -- */
+/* Geometry of one image's pyramid (Sec. III-C). Level 0 is the caller's
+ * frame (pitch level0_pitch); levels 1..n-1 are packed in one caller buffer
+ * ("upper buffer") at offset[l], each with a 128-byte-aligned pitch. Level
+ * sizes: w_{l+1} = floor(w_l / 2), h_{l+1} = floor(h_l / 2). */
+typedef struct {
+  int32_t n_levels;
+  int32_t w[VIO_MAX_LEVELS], h[VIO_MAX_LEVELS], pitch[VIO_MAX_LEVELS];
+  int64_t offset[VIO_MAX_LEVELS]; /* byte offset of level l >= 1 in the upper buffer */
+  int64_t upper_bytes;            /* size of the upper buffer, multiple of 256 */
+} vio_pyr_layout;
+
+/* Fills *out for a w x h image with n_levels levels. Needs every level at
+ * least 1x1 and level0_pitch >= w. */
+vio_status vio_pyr_layout_make(int32_t w, int32_t h, int32_t n_levels, int32_t level0_pitch,
+                               vio_pyr_layout* out);
+
+/* n_images pyramids of one layout: image i has level 0 at
+ * d_level0 + i * level0_stride and its upper buffer at
+ * d_upper + i * upper_stride (strides in bytes, upper_stride >= upper_bytes
+ * and a multiple of 16). */
+typedef struct {
+  const uint8_t* d_level0;
+  int64_t level0_stride;
+  uint8_t* d_upper;
+  int64_t upper_stride;
+  int32_t n_images;
+} vio_pyr_batch;
+
+/* ------------------------------------------------------------- context -- */
+typedef struct vio_ctx vio_ctx;
+
+/* Allocates the scratch the calls below need for images up to max_w x
+ * max_h and batches up to max_images. The only allocating calls are
+ * vio_ctx_create and vio_frontend_create. */
+vio_status vio_ctx_create(vio_ctx** ctx, const vio_params* p, int32_t max_w, int32_t max_h,
+                          int32_t max_images);
+vio_status vio_ctx_destroy(vio_ctx* ctx);
+const char* vio_status_string(vio_status s);
+
+/* --------------------------------------------------------------- stages -- */
+
+/* Sec. III-C, Eq. 1-3: builds levels 1..n-1 of every pyramid of the batch
+ * from its level 0: a separable 5x5 binomial [1,4,6,4,1] filter, 2:1
+ * subsampling, integer arithmetic, rounding per p->round_mode, edges
+ * clamped. Reads level 0, writes the upper buffers. */
+vio_status vio_pyramid_build(vio_ctx* ctx, const vio_pyr_layout* layout,
+                             const vio_pyr_batch* batch, void* stream);
+
+/* Sec. III-D: the FAST-9 score of every pixel of one image: the largest
+ * integer tau >= 0 for which 9 contiguous pixels of the 16-pixel radius-3
+ * Bresenham circle are all brighter than I(p)+tau or all darker than
+ * I(p)-tau; -1 where there is none or the circle leaves the image.
+ * d_score: w*h int16, row-major, pitch w elements. */
+vio_status vio_fast_scores(const uint8_t* d_img, int32_t w, int32_t h, int32_t pitch,
+                           int16_t* d_score, void* stream);
+
+/* Sec. III-D: grid-cell detection on level 0 of every image of the batch.
+ * Cells are the full cell_w x cell_h cells of a grid anchored at (0,0)
+ * (gx = w / cell_w by gy = h / cell_h). Per cell, for the thresholds in
+ * turn: corners with score >= T, strict 3x3 local maxima (compared with all
+ * 8 image neighbours), the strongest k_eff = k - occupancy[cell] of them,
+ * stopping at the first threshold that yields k_eff; ties ordered by
+ * (score desc, y asc, x asc). Equivalent one-pass form is used.
+ *   d_occupancy: per image gx*gy uint8 counts of existing tracks (raster
+ *                order, image stride gx*gy), or NULL for none.
+ *   d_mask:      per image w*h uint8, 0 = pixel excluded, image stride
+ *                mask_stride, row pitch w; or NULL.
+ *   d_kp, d_score: per image `capacity` slots (image stride capacity): the
+ *                keypoints in cell raster order, then by rank; float2 (x,y)
+ *                and int16 score.
+ *   d_count:     per image int32, the number written (<= capacity).
+ * Uses the context's scratch: calls on one context must not overlap. */
+vio_status vio_detect_grid(vio_ctx* ctx, const vio_pyr_layout* layout,
+                           const vio_pyr_batch* batch, const uint8_t* d_occupancy,
+                           const uint8_t* d_mask, int64_t mask_stride, float* d_kp,
+                           int16_t* d_score, int32_t* d_count, int32_t capacity, void* stream);
+
+/* Flags of vio_track_patches. */
+enum { VIO_TRACK_FORWARD = 0, VIO_TRACK_WITH_FB = 1 };
+
+/* Sec. III-E, Eq. 4-5: pyramidal inverse-compositional KLT of 52-point
+ * patches with an SE(2) warp (t_x, t_y, theta), coarse to fine, gn_iters
+ * Gauss-Newton steps per level, from pyramid src[i] to dst[i]. The warp maps
+ * pattern offset x to R(theta) x + t; t is the keypoint's position in the
+ * target. One warp of 32 threads tracks one keypoint.
+ *   d_pts:    per image `capacity` float2 source positions (image stride
+ *             capacity), level-0 px.
+ *   d_init:   per keypoint float3 starting warp (t_x, t_y, theta), same
+ *             indexing, or NULL for the identity start t = p, theta = 0.
+ *   d_count:  per image int32 number of valid keypoints (<= capacity), or
+ *             NULL for `capacity` each.
+ *   d_out:    per keypoint float3 forward result (t_x, t_y, theta), level 0.
+ *   d_status: per keypoint uint8 VIO_TRACK_* status; slots >= count get
+ *             VIO_TRACK_EMPTY.
+ *   d_fb_dist: per keypoint float forward-backward distance (NaN if not
+ *             computed), or NULL.
+ * flags = VIO_TRACK_WITH_FB also runs the backward pass (template rebuilt on
+ * the target at the forward result, warp started at the forward estimate's
+ * inverse) and marks VIO_TRACK_FB_FAIL when the returned position is more
+ * than fb_max_dist from the original. */
+vio_status vio_track_patches(vio_ctx* ctx, const vio_pyr_layout* layout,
+                             const vio_pyr_batch* src, const vio_pyr_batch* dst,
+                             const float* d_pts, const float* d_init, const int32_t* d_count,
+                             int32_t capacity, int32_t flags, float* d_out, uint8_t* d_status,
+                             float* d_fb_dist, void* stream);
+
+/* Sec. III-E cross-camera matching: vio_track_patches with VIO_TRACK_WITH_FB
+ * from cam0 pyramids (src) to cam1 pyramids (dst) at the same time step.
+ * d_match: per keypoint float2 position in cam1. */
+vio_status vio_stereo_match(vio_ctx* ctx, const vio_pyr_layout* layout,
+                            const vio_pyr_batch* cam0, const vio_pyr_batch* cam1,
+                            const float* d_pts, const float* d_init, const int32_t* d_count,
+                            int32_t capacity, float* d_match, uint8_t* d_status,
+                            float* d_fb_dist, void* stream);
+
+/* Sec. III-E forward-backward check, for callers that run the backward pass
+ * themselves: d_back[i] is the backward result (float3) of keypoint d_orig[i]
+ * (float2). Where d_status[i] is VIO_TRACK_OK on entry, writes the distance
+ * |t_back - orig| to d_dist[i] (if non-NULL) and sets VIO_TRACK_FB_FAIL when
+ * it exceeds max_dist. Other statuses are left as they are. Indexing as in
+ * vio_track_patches (n_images x capacity, counts from d_count or all). */
+vio_status vio_fb_check(const float* d_orig, const float* d_back, const int32_t* d_count,
+                        int32_t capacity, int32_t n_images, float max_dist, uint8_t* d_status,
+                        float* d_dist, void* stream);
+
+/* ------------------------------------------------------------- frontend -- */
+/* The per-frame frontend of Sec. III-B for n_streams independent stereo
+ * streams of one size: pyramid of both cameras, temporal tracking of every
+ * camera's keypoints with the forward-backward check, detection on camera 0
+ * with the cells of surviving tracks counted against k, and stereo matching
+ * of the new keypoints into camera 1. State (keypoint lists, ids, pyramids)
+ * stays on the device between steps. */
+typedef struct vio_frontend vio_frontend;
+
+/* capacity: keypoint slots per camera per stream (>= gx*gy*k). */
+vio_status vio_frontend_create(vio_frontend** fe, const vio_params* p, int32_t w, int32_t h,
+                               int32_t n_streams, int32_t capacity);
+vio_status vio_frontend_destroy(vio_frontend* fe);
+
+/* One frame for every stream. d_frames: level-0 images, stream s camera c at
+ * d_frames + (2*s + c) * frame_stride, row pitch `pitch`. The buffer is read
+ * again by the NEXT step (as the previous frame): keep it unchanged until
+ * that step has run. The first step after create or reset only detects. */
+vio_status vio_frontend_step(vio_frontend* fe, const uint8_t* d_frames, int32_t pitch,
+                             int64_t frame_stride, void* stream);
+
+/* Forget all tracks (next step starts fresh). Enqueued on `stream`. */
+vio_status vio_frontend_reset(vio_frontend* fe, void* stream);
+
+/* Device views of the frontend's outputs after the last step, per stream s
+ * and camera c at slot base (2*s + c) * capacity:
+ *   tracks:  float2 positions, int32 ids, uint8 status (VIO_TRACK_OK for a
+ *            live track), int32 counts per (stream, camera) -- TR_t;
+ *   new:     per stream, float2 positions and int32 count of the keypoints
+ *            detected this step on camera 0 (slot base s * capacity) --
+ *            DET_t.
+ * The pointers stay valid until destroy; their contents change with every
+ * step. */
+typedef struct {
+  const float* d_track_xy;
+  const int32_t* d_track_id;
+  const uint8_t* d_track_status;
+  const int32_t* d_track_count;
+  const float* d_new_xy;
+  const int32_t* d_new_count;
+  int32_t capacity;
+  int32_t n_streams;
+} vio_frontend_view;
+
+vio_status vio_frontend_get_view(vio_frontend* fe, vio_frontend_view* out);
+
+/* Number of kernels one vio_frontend_step enqueues (for launch accounting). */
+int32_t vio_frontend_launches_per_step(const vio_frontend* fe);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VIO_H_ */

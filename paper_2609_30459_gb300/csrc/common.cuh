@@ -1,0 +1,90 @@
+// Internal declarations shared by the libvio translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "vio.h"
+
+namespace vio {
+
+constexpr int kWarp = 32;
+constexpr int kPatternMax = 64;   // 2 points per lane
+
+// Pyramid geometry + batch as kernel parameters (passed by value).
+struct Geom {
+  int n_levels;
+  int w[VIO_MAX_LEVELS], h[VIO_MAX_LEVELS], pitch[VIO_MAX_LEVELS];
+  long long off[VIO_MAX_LEVELS];
+};
+struct Batch {
+  const uint8_t* l0;
+  long long l0_stride;
+  uint8_t* upper;
+  long long upper_stride;
+  int n;
+};
+
+inline Geom make_geom(const vio_pyr_layout& L) {
+  Geom g{};
+  g.n_levels = L.n_levels;
+  for (int l = 0; l < VIO_MAX_LEVELS; ++l) {
+    g.w[l] = L.w[l];
+    g.h[l] = L.h[l];
+    g.pitch[l] = L.pitch[l];
+    g.off[l] = L.offset[l];
+  }
+  return g;
+}
+inline Batch make_batch(const vio_pyr_batch& b) {
+  return Batch{b.d_level0, (long long)b.level0_stride, b.d_upper, (long long)b.upper_stride,
+               b.n_images};
+}
+
+__device__ __forceinline__ const uint8_t* level_ptr(const Geom& g, const Batch& b, int img,
+                                                    int l) {
+  return l == 0 ? b.l0 + (long long)img * b.l0_stride
+                : b.upper + (long long)img * b.upper_stride + g.off[l];
+}
+__device__ __forceinline__ uint8_t* level_ptr_mut(const Geom& g, const Batch& b, int img,
+                                                  int l) {
+  return b.upper + (long long)img * b.upper_stride + g.off[l];
+}
+
+// Track parameters shared by the tracking kernels.
+struct TrackCfg {
+  int gn_iters;
+  int fb;
+  float fb_max_dist;
+};
+
+}  // namespace vio
+
+// The context: parameters plus scratch sized at creation.
+struct vio_ctx {
+  vio_params p;
+  int max_w, max_h, max_images;
+  int max_cells;
+  // detection scratch: per image, per cell, k packed candidate keys + count
+  unsigned long long* d_cand;
+  int32_t* d_cand_count;
+};
+
+namespace vio {
+// launchers (host side), implemented in the .cu files
+cudaError_t launch_pyramid(const Geom& g, const Batch& b, int round_mode, cudaStream_t s);
+cudaError_t launch_fast_scores(const uint8_t* img, int w, int h, int pitch, int16_t* out,
+                               cudaStream_t s);
+cudaError_t launch_detect(const vio_params& p, const Geom& g, const Batch& b,
+                          const uint8_t* occ, const uint8_t* mask, long long mask_stride,
+                          unsigned long long* cand, int32_t* cand_count, float* kp,
+                          int16_t* score, int32_t* count, int capacity, cudaStream_t s);
+cudaError_t launch_track(const Geom& g, const Batch& src, const Batch& dst, const float* pts,
+                         const float* init, const int32_t* count, int capacity,
+                         const TrackCfg& cfg, float* out3, float* out2, uint8_t* status,
+                         float* fb_dist, cudaStream_t s);
+cudaError_t launch_fb_check(const float* orig, const float* back, const int32_t* count,
+                            int capacity, int n_images, float max_dist, uint8_t* status,
+                            float* dist, cudaStream_t s);
+// pattern table upload (once per process and device)
+cudaError_t ensure_pattern(int pattern_id);
+}  // namespace vio

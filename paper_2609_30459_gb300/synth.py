@@ -29,7 +29,8 @@ def band_limited_texture(seed: int, h: int, w: int, sigma: float = 2.0, mean: fl
     """U[0,255] noise, Gaussian-filtered (periodic), rescaled to mean/std (FP64)."""
     rng = np.random.default_rng(seed)
     t = ndimage.gaussian_filter(rng.uniform(0.0, 255.0, (h, w)), sigma, mode="wrap")
-    t = (t - t.mean()) / t.std()
+    sd = t.std()
+    t = (t - t.mean()) / sd if sd > 0 else np.zeros_like(t)
     return mean + std * t
 
 

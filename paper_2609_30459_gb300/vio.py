@@ -1,0 +1,345 @@
+"""Thin ctypes binding of libvio (include/vio.h): argument marshalling only.
+
+Every function here takes torch CUDA tensors, passes their device pointers and
+the current CUDA stream to the C ABI, and returns. All computation happens in
+the library's kernels. There is no CPU fallback: if libvio.so is missing or no
+GPU is present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+from . import build_lib
+
+MAX_LEVELS = 8
+MAX_THRESHOLDS = 8
+
+OK, ERR_INVALID_ARG, ERR_CUDA, ERR_OOM, ERR_TIMEOUT, ERR_UNSUPPORTED = range(6)
+TRACK_STATUS = {"OK": 0, "OOB_TEMPLATE": 1, "OOB_WARP": 2, "DEGENERATE_H": 3, "ZERO_MEAN": 4,
+                "FB_FAIL": 5, "NAN": 6, "EMPTY": 255}
+TRACK_FORWARD, TRACK_WITH_FB = 0, 1
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("n_levels", ctypes.c_int32), ("round_mode", ctypes.c_int32),
+                ("gn_iters", ctypes.c_int32), ("pattern_id", ctypes.c_int32),
+                ("cell_w", ctypes.c_int32), ("cell_h", ctypes.c_int32),
+                ("k_per_cell", ctypes.c_int32), ("n_thresholds", ctypes.c_int32),
+                ("thresholds", ctypes.c_int32 * MAX_THRESHOLDS),
+                ("detect_border", ctypes.c_int32), ("fb_max_dist", ctypes.c_float)]
+
+
+class PyrLayout(ctypes.Structure):
+    _fields_ = [("n_levels", ctypes.c_int32), ("w", ctypes.c_int32 * MAX_LEVELS),
+                ("h", ctypes.c_int32 * MAX_LEVELS), ("pitch", ctypes.c_int32 * MAX_LEVELS),
+                ("offset", ctypes.c_int64 * MAX_LEVELS), ("upper_bytes", ctypes.c_int64)]
+
+
+class PyrBatch(ctypes.Structure):
+    _fields_ = [("d_level0", ctypes.c_void_p), ("level0_stride", ctypes.c_int64),
+                ("d_upper", ctypes.c_void_p), ("upper_stride", ctypes.c_int64),
+                ("n_images", ctypes.c_int32)]
+
+
+class FrontendView(ctypes.Structure):
+    _fields_ = [("d_track_xy", ctypes.c_void_p), ("d_track_id", ctypes.c_void_p),
+                ("d_track_status", ctypes.c_void_p), ("d_track_count", ctypes.c_void_p),
+                ("d_new_xy", ctypes.c_void_p), ("d_new_count", ctypes.c_void_p),
+                ("capacity", ctypes.c_int32), ("n_streams", ctypes.c_int32)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+_SIGS = {
+    "vio_params_default": (None, [ctypes.POINTER(Params)]),
+    "vio_status_string": (ctypes.c_char_p, [ctypes.c_int32]),
+    "vio_pyr_layout_make": (ctypes.c_int32, [ctypes.c_int32] * 4 + [ctypes.POINTER(PyrLayout)]),
+    "vio_ctx_create": (ctypes.c_int32, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(Params),
+                                        ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]),
+    "vio_ctx_destroy": (ctypes.c_int32, [ctypes.c_void_p]),
+    "vio_pyramid_build": (ctypes.c_int32, [ctypes.c_void_p, ctypes.POINTER(PyrLayout),
+                                           ctypes.POINTER(PyrBatch), ctypes.c_void_p]),
+    "vio_fast_scores": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
+                                         ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]),
+    "vio_detect_grid": (ctypes.c_int32, [ctypes.c_void_p, ctypes.POINTER(PyrLayout),
+                                         ctypes.POINTER(PyrBatch), ctypes.c_void_p,
+                                         ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                                         ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                         ctypes.c_void_p]),
+    "vio_track_patches": (ctypes.c_int32, [ctypes.c_void_p, ctypes.POINTER(PyrLayout),
+                                           ctypes.POINTER(PyrBatch), ctypes.POINTER(PyrBatch),
+                                           ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                           ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
+                                           ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "vio_stereo_match": (ctypes.c_int32, [ctypes.c_void_p, ctypes.POINTER(PyrLayout),
+                                          ctypes.POINTER(PyrBatch), ctypes.POINTER(PyrBatch),
+                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                          ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                          ctypes.c_void_p, ctypes.c_void_p]),
+    "vio_fb_check": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                      ctypes.c_int32, ctypes.c_int32, ctypes.c_float,
+                                      ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "vio_frontend_create": (ctypes.c_int32, [ctypes.POINTER(ctypes.c_void_p),
+                                             ctypes.POINTER(Params), ctypes.c_int32,
+                                             ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]),
+    "vio_frontend_destroy": (ctypes.c_int32, [ctypes.c_void_p]),
+    "vio_frontend_step": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                           ctypes.c_int64, ctypes.c_void_p]),
+    "vio_frontend_reset": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p]),
+    "vio_frontend_get_view": (ctypes.c_int32, [ctypes.c_void_p, ctypes.POINTER(FrontendView)]),
+    "vio_frontend_launches_per_step": (ctypes.c_int32, [ctypes.c_void_p]),
+}
+
+
+def lib_path() -> str:
+    return build_lib.LIB
+
+
+def load(build: bool = False) -> ctypes.CDLL:
+    """Load libvio.so (building it first if asked). Raises if it is missing."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if build:
+                build_lib.build()
+            if not os.path.exists(build_lib.LIB):
+                raise RuntimeError(f"libvio.so not built ({build_lib.LIB}); run "
+                                   "__graft_entry__.build() or build_lib.build()")
+            lib = ctypes.CDLL(build_lib.LIB)
+            for name, (res, args) in _SIGS.items():
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def exported_symbols() -> list[str]:
+    return list(_SIGS)
+
+
+class VioError(RuntimeError):
+    pass
+
+
+def _check(status: int, what: str):
+    if status != OK:
+        msg = load().vio_status_string(status).decode()
+        raise VioError(f"{what} failed: {msg} ({status})")
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def default_params(**kw) -> Params:
+    p = Params()
+    load().vio_params_default(ctypes.byref(p))
+    for k, v in kw.items():
+        if k == "thresholds":
+            p.n_thresholds = len(v)
+            for i, t in enumerate(v):
+                p.thresholds[i] = int(t)
+        else:
+            setattr(p, k, v)
+    return p
+
+
+def pyr_layout(w: int, h: int, n_levels: int, level0_pitch: int | None = None) -> PyrLayout:
+    L = PyrLayout()
+    _check(load().vio_pyr_layout_make(w, h, n_levels, level0_pitch or w, ctypes.byref(L)),
+           "vio_pyr_layout_make")
+    return L
+
+
+class Pyramids:
+    """n images of one size and their upper pyramid levels, on the device.
+
+    level0: uint8 tensor (n, h, pitch) holding level 0 (the frames)."""
+
+    def __init__(self, level0: torch.Tensor, n_levels: int, w: int | None = None):
+        if level0.dtype != torch.uint8 or level0.dim() != 3 or not level0.is_cuda:
+            raise ValueError("level0 must be a CUDA uint8 tensor (n, h, pitch)")
+        n, h, pitch = level0.shape
+        self.level0 = level0.contiguous()
+        self.w = w or pitch
+        self.h = h
+        self.n = n
+        self.layout = pyr_layout(self.w, h, n_levels, pitch)
+        ub = int(self.layout.upper_bytes)
+        self.upper = torch.empty(max(n * ub, 16), dtype=torch.uint8, device=level0.device)
+
+    def batch(self, start: int = 0, step: int = 1, count: int | None = None) -> PyrBatch:
+        count = count if count is not None else (self.n - start + step - 1) // step
+        b = PyrBatch()
+        ub = int(self.layout.upper_bytes)
+        b.d_level0 = self.level0.data_ptr() + start * self.level0[0].numel()
+        b.level0_stride = step * self.level0[0].numel()
+        b.d_upper = self.upper.data_ptr() + start * ub
+        b.upper_stride = step * ub
+        b.n_images = count
+        return b
+
+    def level(self, i: int, l: int) -> torch.Tensor:
+        """View of level l of image i as (h_l, w_l) uint8 (device)."""
+        L = self.layout
+        if l == 0:
+            return self.level0[i, :, : self.w]
+        ub = int(L.upper_bytes)
+        off = i * ub + int(L.offset[l])
+        flat = self.upper[off: off + L.pitch[l] * L.h[l]]
+        return flat.view(L.h[l], L.pitch[l])[:, : L.w[l]]
+
+
+class Context:
+    """vio_ctx: parameters plus the scratch the detection stage needs."""
+
+    def __init__(self, params: Params, max_w: int, max_h: int, max_images: int):
+        self.params = params
+        h = ctypes.c_void_p()
+        _check(load().vio_ctx_create(ctypes.byref(h), ctypes.byref(params), max_w, max_h,
+                                     max_images), "vio_ctx_create")
+        self.handle = h
+
+    def close(self):
+        if self.handle:
+            load().vio_ctx_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- stages --------------------------------------------------------------
+    def pyramid_build(self, pyr: Pyramids, batch: PyrBatch | None = None, stream=None):
+        _check(load().vio_pyramid_build(self.handle, ctypes.byref(pyr.layout),
+                                        ctypes.byref(batch or pyr.batch()), _stream(stream)),
+               "vio_pyramid_build")
+
+    def detect_grid(self, pyr: Pyramids, batch: PyrBatch, kp, score, count, capacity,
+                    occupancy=None, mask=None, mask_stride=0, stream=None):
+        _check(load().vio_detect_grid(self.handle, ctypes.byref(pyr.layout), ctypes.byref(batch),
+                                      _ptr(occupancy), _ptr(mask), mask_stride, _ptr(kp),
+                                      _ptr(score), _ptr(count), capacity, _stream(stream)),
+               "vio_detect_grid")
+
+    def track_patches(self, pyr: Pyramids, src: PyrBatch, dst: PyrBatch, pts, count, capacity,
+                      out, status, fb_dist=None, init=None, fb=True, stream=None):
+        _check(load().vio_track_patches(self.handle, ctypes.byref(pyr.layout), ctypes.byref(src),
+                                        ctypes.byref(dst), _ptr(pts), _ptr(init), _ptr(count),
+                                        capacity, TRACK_WITH_FB if fb else TRACK_FORWARD,
+                                        _ptr(out), _ptr(status), _ptr(fb_dist),
+                                        _stream(stream)), "vio_track_patches")
+
+    def stereo_match(self, pyr: Pyramids, cam0: PyrBatch, cam1: PyrBatch, pts, count, capacity,
+                     match, status, fb_dist=None, init=None, stream=None):
+        _check(load().vio_stereo_match(self.handle, ctypes.byref(pyr.layout), ctypes.byref(cam0),
+                                       ctypes.byref(cam1), _ptr(pts), _ptr(init), _ptr(count),
+                                       capacity, _ptr(match), _ptr(status), _ptr(fb_dist),
+                                       _stream(stream)), "vio_stereo_match")
+
+
+def fast_scores(img: torch.Tensor, out: torch.Tensor | None = None, w: int | None = None,
+                stream=None) -> torch.Tensor:
+    """FAST-9 score map of one uint8 image (h, pitch) -> int16 (h, w)."""
+    h, pitch = img.shape
+    w = w or pitch
+    if out is None:
+        out = torch.empty((h, w), dtype=torch.int16, device=img.device)
+    _check(load().vio_fast_scores(_ptr(img), w, h, pitch, _ptr(out), _stream(stream)),
+           "vio_fast_scores")
+    return out
+
+
+def fb_check(orig, back, count, capacity, n_images, max_dist, status, dist=None, stream=None):
+    _check(load().vio_fb_check(_ptr(orig), _ptr(back), _ptr(count), capacity, n_images,
+                               max_dist, _ptr(status), _ptr(dist), _stream(stream)),
+           "vio_fb_check")
+
+
+class Frontend:
+    """vio_frontend: the per-frame frontend over n_streams stereo streams."""
+
+    def __init__(self, params: Params, w: int, h: int, n_streams: int, capacity: int):
+        self.params, self.w, self.h = params, w, h
+        self.n_streams, self.capacity = n_streams, capacity
+        hdl = ctypes.c_void_p()
+        _check(load().vio_frontend_create(ctypes.byref(hdl), ctypes.byref(params), w, h,
+                                          n_streams, capacity), "vio_frontend_create")
+        self.handle = hdl
+
+    def close(self):
+        if self.handle:
+            load().vio_frontend_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, frames: torch.Tensor, stream=None):
+        """frames: uint8 CUDA tensor (n_streams, 2, h, pitch); kept alive by the
+        caller until the next step has run."""
+        if frames.dtype != torch.uint8 or frames.dim() != 4 or not frames.is_contiguous():
+            raise ValueError("frames must be a contiguous uint8 tensor (streams, 2, h, pitch)")
+        pitch = frames.shape[-1]
+        _check(load().vio_frontend_step(self.handle, _ptr(frames), pitch,
+                                        frames.shape[2] * pitch, _stream(stream)),
+               "vio_frontend_step")
+
+    def reset(self, stream=None):
+        _check(load().vio_frontend_reset(self.handle, _stream(stream)), "vio_frontend_reset")
+
+    def launches_per_step(self) -> int:
+        return int(load().vio_frontend_launches_per_step(self.handle))
+
+    def view(self) -> dict:
+        """Device tensors aliasing the frontend's outputs (no copies)."""
+        v = FrontendView()
+        _check(load().vio_frontend_get_view(self.handle, ctypes.byref(v)), "get_view")
+        dev = torch.device("cuda", torch.cuda.current_device())
+        ns, cap = self.n_streams, self.capacity
+        return {
+            "track_xy": _alias(v.d_track_xy, (ns, 2, cap, 2), torch.float32, dev),
+            "track_id": _alias(v.d_track_id, (ns, 2, cap), torch.int32, dev),
+            "track_status": _alias(v.d_track_status, (ns, 2, cap), torch.uint8, dev),
+            "track_count": _alias(v.d_track_count, (ns, 2), torch.int32, dev),
+            "new_xy": _alias(v.d_new_xy, (ns, cap, 2), torch.float32, dev),
+            "new_count": _alias(v.d_new_count, (ns,), torch.int32, dev),
+        }
+
+
+def _alias(ptr: int, shape, dtype, device) -> torch.Tensor:
+    """A tensor view of library-owned device memory (valid while the owner lives)."""
+    n = 1
+    for s in shape:
+        n *= s
+    nbytes = n * torch.empty((), dtype=dtype).element_size()
+
+    class _Holder:
+        __cuda_array_interface__ = {
+            "shape": (nbytes,), "typestr": "|u1", "data": (int(ptr), False), "version": 3,
+            "strides": None,
+        }
+    raw = torch.as_tensor(_Holder(), device=device)
+    return raw.view(dtype).view(*shape)

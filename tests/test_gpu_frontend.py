@@ -1,0 +1,126 @@
+"""GPU parity of the per-frame frontend (Sec. III-B) against the oracle's
+frontend, step by step: before each frame the oracle is given the GPU's state
+(keypoint lists and ids), so that one step's outputs are compared on the same
+inputs and a status decision on a threshold does not carry over."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle import frontend as ofe
+from paper_2609_30459_gb300 import synth
+from tests.parity_util import BAND, FLOW_TOL
+
+pytestmark = pytest.mark.gpu
+
+vio = pytest.importorskip("paper_2609_30459_gb300.vio")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    vio.load(build=True)
+    oracle.build()
+
+
+def _check_track_lists(g_xy, g_id, o_xy, o_id, explained_ids):
+    """Same ids in the same order, except ids whose decision was on a
+    threshold; positions of common ids within FLOW_TOL."""
+    gs, os_ = list(g_id), list(o_id)
+    diff = set(gs) ^ set(os_)
+    assert diff <= explained_ids, (sorted(diff - explained_ids)[:10], len(diff))
+    gpos = {i: p for i, p in zip(gs, g_xy)}
+    opos = {i: p for i, p in zip(os_, o_xy)}
+    common = [i for i in gs if i in opos]
+    assert [i for i in gs if i in opos] == [i for i in os_ if i in gpos]   # same order
+    if common:
+        err = max(np.abs(np.asarray(gpos[i], np.float64) - opos[i]).max() for i in common)
+        assert err < FLOW_TOL, err
+        return err
+    return 0.0
+
+
+def _explained(res, ids, fb_max):
+    if res is None:
+        return set()
+    with np.errstate(invalid="ignore"):
+        m = (np.abs(res["fb_dist"] - fb_max) <= BAND) | (res["margin"] <= BAND)
+    return set(np.asarray(ids)[m].tolist())
+
+
+@pytest.mark.parametrize("cfg", ["cfg2_small", "cfg1_k2"])
+def test_frontend_steps_match_oracle(cfg):
+    if cfg == "cfg2_small":
+        w, h, L, cw, ch, k, n_frames, motion = 752, 480, 4, 37, 32, 1, 8, 15.0
+    else:
+        w, h, L, cw, ch, k, n_frames, motion = 752, 480, 3, 94, 60, 2, 4, 3.0
+    seq = synth.make_sequence(4000 + n_frames, n_frames, w, h, 1, max_motion=motion,
+                              tex_size=2048)
+    p = vio.default_params(n_levels=L, cell_w=cw, cell_h=ch, k_per_cell=k)
+    op = ofe.Params(n_levels=L, cell_w=cw, cell_h=ch, k=k)
+    cap = 2 * (w // cw) * (h // ch) * k
+    fe = vio.Frontend(p, w, h, 1, cap)
+    frames = torch.from_numpy(seq.frames).cuda()                  # (F, 2, h, w)
+    st = ofe.StreamState()
+    prev_ids = [np.zeros(0, np.int32), np.zeros(0, np.int32)]
+    total_tracks = 0
+    for t in range(n_frames):
+        fe.step(frames[t: t + 1])
+        torch.cuda.synchronize()
+        v = fe.view()
+        res = ofe.step(st, seq.frames[t], op, cap, n_threads=8)
+        # new detections on camera 0: bit-exact whenever the occupancy agrees
+        g_new = int(v["new_count"][0])
+        g_new_xy = v["new_xy"][0, :g_new].cpu().numpy()
+        cnt = v["track_count"][0].cpu().numpy()
+        gx = [v["track_xy"][0, c, : cnt[c]].cpu().numpy() for c in range(2)]
+        gi = [v["track_id"][0, c, : cnt[c]].cpu().numpy() for c in range(2)]
+        surv0 = cnt[0] - g_new
+        g_occ = ofe.occupancy(gx[0][:max(surv0, 0)], w, h, cw, ch)
+        if np.array_equal(g_occ, res["occupancy"]):
+            assert np.array_equal(g_new_xy, res["new_xy"]), t
+        # temporal tracks: explained differences only
+        expl = set()
+        for c in range(2):
+            if res["track"][c] is not None:
+                expl |= _explained(res["track"][c], prev_ids[c], p.fb_max_dist)
+        expl |= _explained(res["match"], st.ids[0][-len(res["new_xy"]):] if len(res["new_xy"])
+                           else [], p.fb_max_dist)
+        for c in range(2):
+            _check_track_lists(gx[c], gi[c], st.xy[c], st.ids[c], expl)
+        total_tracks += cnt.sum()
+        # hand the GPU state to the oracle for the next step
+        st.xy = [gx[0].copy(), gx[1].copy()]
+        st.ids = [gi[0].copy(), gi[1].copy()]
+        prev_ids = [gi[0].copy(), gi[1].copy()]
+    assert total_tracks > 0
+    fe.close()
+
+
+def test_frontend_reset_and_two_streams():
+    w, h, L = 320, 240, 3
+    seq = synth.make_sequence(5001, 3, w, h, 2, max_motion=4.0, tex_size=1024)
+    p = vio.default_params(n_levels=L, cell_w=40, cell_h=40)
+    cap = 2 * (w // 40) * (h // 40)
+    fe = vio.Frontend(p, w, h, 2, cap)
+    frames = torch.from_numpy(seq.frames).cuda()                  # (F, 4, h, w): 2 streams
+    for t in range(3):
+        fe.step(frames[t].view(2, 2, h, w))
+    torch.cuda.synchronize()
+    c1 = fe.view()["track_count"].cpu().numpy().copy()
+    # stream-independence: the same frames alone give the same lists
+    fe_a = vio.Frontend(p, w, h, 1, cap)
+    alone = [frames[t, 2:4].reshape(1, 2, h, w).contiguous() for t in range(3)]  # kept alive
+    for t in range(3):
+        fe_a.step(alone[t])
+    torch.cuda.synchronize()
+    va, vb = fe_a.view(), fe.view()
+    assert np.array_equal(va["track_count"][0].cpu().numpy(), c1[1])
+    for c in range(2):
+        n = c1[1, c]
+        assert torch.equal(va["track_xy"][0, c, :n], vb["track_xy"][1, c, :n])
+        assert torch.equal(va["track_id"][0, c, :n], vb["track_id"][1, c, :n])
+    fe.reset()
+    torch.cuda.synchronize()
+    assert (fe.view()["track_count"] == 0).all()
