@@ -257,6 +257,30 @@ vio_status vio_frontend_get_view(vio_frontend* fe, vio_frontend_view* out);
 /* Number of kernels one vio_frontend_step enqueues (for launch accounting). */
 int32_t vio_frontend_launches_per_step(const vio_frontend* fe);
 
+/* Stage timing (the paper's per-stage GPU timestamps, Sec. IV-B, Fig. 5).
+ * While enabled, every step records CUDA events on its stream at the stage
+ * boundaries: 0 pyramid, 1 temporal tracking, 2 compaction, 3 detection,
+ * 4 stereo matching, 5 append. vio_frontend_read_timing waits for the
+ * recorded events, adds each stage's elapsed milliseconds into
+ * stage_ms[0..5] (overwritten), stores the number of timed steps in *n_steps
+ * and clears the record. Enabling, disabling and reading are host calls. */
+enum { VIO_STAGE_PYRAMID = 0, VIO_STAGE_TRACK, VIO_STAGE_COMPACT, VIO_STAGE_DETECT,
+       VIO_STAGE_STEREO, VIO_STAGE_APPEND, VIO_N_STAGES };
+vio_status vio_frontend_set_timing(vio_frontend* fe, int32_t enable);
+vio_status vio_frontend_read_timing(vio_frontend* fe, double* stage_ms, int64_t* n_steps);
+
+/* Per-step counters, written on the device by every step into a ring of
+ * VIO_STATS_RING entries (entry = step index mod the ring size), per stream,
+ * VIO_N_STATS int32 values: tracks attempted on cam0 and cam1, tracks that
+ * survived on cam0 and cam1, new detections, successful stereo matches.
+ * vio_frontend_read_stats copies the whole ring to host_out (blocking; size
+ * VIO_STATS_RING * n_streams * VIO_N_STATS) and returns the number of steps
+ * run since create in *n_steps. */
+#define VIO_STATS_RING 4096
+enum { VIO_STAT_TRK0 = 0, VIO_STAT_TRK1, VIO_STAT_OK0, VIO_STAT_OK1, VIO_STAT_NEW,
+       VIO_STAT_MATCHED, VIO_N_STATS };
+vio_status vio_frontend_read_stats(vio_frontend* fe, int32_t* host_out, int64_t* n_steps);
+
 #ifdef __cplusplus
 }
 #endif

@@ -12,7 +12,9 @@
 // counts, per cell, the surviving camera-0 tracks against k.
 #include <stdlib.h>
 
+#include <array>
 #include <new>
+#include <vector>
 
 #include "common.cuh"
 
@@ -35,7 +37,8 @@ __global__ void __launch_bounds__(CMP_THREADS) compact_kernel(
     const float* __restrict__ pos, const uint8_t* __restrict__ status,
     const int32_t* __restrict__ ids_in, const int32_t* __restrict__ count_in, int capacity,
     float* __restrict__ pos_out, int32_t* __restrict__ ids_out, int32_t* __restrict__ count_out,
-    uint8_t* __restrict__ occupancy, int gx, int gy, int cw, int ch) {
+    uint8_t* __restrict__ occupancy, int gx, int gy, int cw, int ch,
+    int32_t* __restrict__ stats) {
   extern __shared__ int occ_s[];
   __shared__ int warp_sums[CMP_THREADS / 32];
   __shared__ int carry_s;
@@ -87,7 +90,11 @@ __global__ void __launch_bounds__(CMP_THREADS) compact_kernel(
     if (threadIdx.x == CMP_THREADS - 1) carry_s = carry + warp_sums[CMP_THREADS / 32 - 1];
     __syncthreads();
   }
-  if (threadIdx.x == 0) count_out[list] = carry_s;
+  if (threadIdx.x == 0) {
+    count_out[list] = carry_s;
+    stats[stream * VIO_N_STATS + VIO_STAT_TRK0 + (list & 1)] = n;
+    stats[stream * VIO_N_STATS + VIO_STAT_OK0 + (list & 1)] = carry_s;
+  }
   if (cam0)
     for (int i = threadIdx.x; i < n_cells; i += CMP_THREADS)
       occupancy[(long long)stream * n_cells + i] = (uint8_t)min(occ_s[i], 255);
@@ -99,7 +106,8 @@ __global__ void __launch_bounds__(CMP_THREADS) append_kernel(
     const float* __restrict__ new_xy, const int32_t* __restrict__ new_count,
     const float* __restrict__ match_xy, const uint8_t* __restrict__ match_status,
     int capacity, float* __restrict__ pos, int32_t* __restrict__ ids,
-    uint8_t* __restrict__ lstatus, int32_t* __restrict__ count, int32_t* __restrict__ next_id) {
+    uint8_t* __restrict__ lstatus, int32_t* __restrict__ count, int32_t* __restrict__ next_id,
+    int32_t* __restrict__ stats, int first) {
   __shared__ int warp_sums[CMP_THREADS / 32];
   __shared__ int carry_s;
   const int s = blockIdx.x;
@@ -163,6 +171,10 @@ __global__ void __launch_bounds__(CMP_THREADS) append_kernel(
     count[2 * s] = n0;
     count[2 * s + 1] = n1;
     next_id[s] = id0 + nn;
+    int32_t* st = stats + s * VIO_N_STATS;
+    if (first) st[VIO_STAT_TRK0] = st[VIO_STAT_TRK1] = st[VIO_STAT_OK0] = st[VIO_STAT_OK1] = 0;
+    st[VIO_STAT_NEW] = nn;
+    st[VIO_STAT_MATCHED] = carry_s;
   }
 }
 
@@ -191,7 +203,12 @@ struct vio_frontend {
   float* match_xy;            // n_streams * capacity
   uint8_t* match_status;
   int32_t* next_id;           // n_streams
+  int32_t* stats;             // VIO_STATS_RING * n_streams * VIO_N_STATS
   // host state
+  int64_t steps;
+  bool timing;
+  std::vector<cudaEvent_t> ev_free;                    // event pool
+  std::vector<std::array<cudaEvent_t, VIO_N_STAGES + 1>> ev_rec;  // one row per timed step
   int cur_list;
   int cur_pyr;
   bool have_prev;
@@ -241,7 +258,8 @@ extern "C" vio_status vio_frontend_create(vio_frontend** out, const vio_params* 
       ns * nc,                                                  // occupancy
       ns * capacity * 8, ns * capacity * 2, ns * 4,             // new
       ns * capacity * 8, ns * capacity,                         // match
-      ns * 4};                                                  // next_id
+      ns * 4,                                                   // next_id
+      (size_t)VIO_STATS_RING * ns * VIO_N_STATS * 4};           // stats
   size_t total = 0;
   for (size_t s : sizes) total += align256(s);
   if (cudaMalloc(&fe->d_mem, total) != cudaSuccess) {
@@ -274,6 +292,9 @@ extern "C" vio_status vio_frontend_create(vio_frontend** out, const vio_params* 
   fe->match_xy = (float*)ptrs[15];
   fe->match_status = (uint8_t*)ptrs[16];
   fe->next_id = (int32_t*)ptrs[17];
+  fe->stats = (int32_t*)ptrs[18];
+  fe->steps = 0;
+  fe->timing = false;
   if (cudaMemset(fe->d_mem, 0, total) != cudaSuccess ||
       cudaMemset(fe->list_status, VIO_TRACK_EMPTY, slots) != cudaSuccess ||
       cudaDeviceSynchronize() != cudaSuccess) {
@@ -292,6 +313,9 @@ extern "C" vio_status vio_frontend_create(vio_frontend** out, const vio_params* 
 
 extern "C" vio_status vio_frontend_destroy(vio_frontend* fe) {
   if (!fe) return VIO_ERR_INVALID_ARG;
+  for (auto& row : fe->ev_rec)
+    for (cudaEvent_t e : row) cudaEventDestroy(e);
+  for (cudaEvent_t e : fe->ev_free) cudaEventDestroy(e);
   cudaFree(fe->d_mem);
   vio_ctx_destroy(fe->ctx);
   delete fe;
@@ -317,6 +341,19 @@ extern "C" int32_t vio_frontend_launches_per_step(const vio_frontend* fe) {
   return (fe->p.n_levels - 1) + 1 + 1 + 2 + 1 + 1;
 }
 
+namespace {
+cudaEvent_t take_event(vio_frontend* fe) {
+  if (!fe->ev_free.empty()) {
+    cudaEvent_t e = fe->ev_free.back();
+    fe->ev_free.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+}  // namespace
+
 extern "C" vio_status vio_frontend_step(vio_frontend* fe, const uint8_t* d_frames,
                                         int32_t pitch, int64_t frame_stride, void* stream) {
   using namespace vio;
@@ -332,20 +369,32 @@ extern "C" vio_status vio_frontend_step(vio_frontend* fe, const uint8_t* d_frame
   const long long ub = L.upper_bytes;
   const int cur = fe->cur_pyr, prv = cur ^ 1;
   const int li = fe->cur_list, lo = li ^ 1;
+  const int n_cells = fe->gx * fe->gy;
+  int32_t* stats = fe->stats + (fe->steps % VIO_STATS_RING) * ns * VIO_N_STATS;
+
+  std::array<cudaEvent_t, VIO_N_STAGES + 1> ev{};
+  if (fe->timing)
+    for (auto& e : ev)
+      if (!(e = take_event(fe))) return VIO_ERR_CUDA;
+  auto mark = [&](int i) {
+    if (fe->timing) cudaEventRecord(ev[i], s);
+  };
 
   // 1. pyramids of all 2*ns images of this frame
+  mark(VIO_STAGE_PYRAMID);
   Batch cur_all{d_frames, frame_stride, fe->pyr[cur], ub, 2 * ns};
   cudaError_t e = launch_pyramid(g, cur_all, fe->p.round_mode, s);
   if (e != cudaSuccess) return VIO_ERR_CUDA;
 
-  const int n_cells = fe->gx * fe->gy;
   // 2. temporal tracking with the forward-backward check, then compaction
+  mark(VIO_STAGE_TRACK);
   if (fe->have_prev) {
     Batch prev_all{fe->prev_frames, fe->prev_stride, fe->pyr[prv], ub, 2 * ns};
     TrackCfg cfg{fe->p.gn_iters, 1, fe->p.fb_max_dist};
     e = launch_track(g, prev_all, cur_all, fe->list_xy[li], nullptr, fe->list_count[li], cap,
                      cfg, nullptr, fe->trk_xy, fe->trk_status, nullptr, s);
     if (e != cudaSuccess) return VIO_ERR_CUDA;
+    mark(VIO_STAGE_COMPACT);
     const size_t smem = (size_t)n_cells * sizeof(int);
     if (smem > 48 * 1024) {
       e = cudaFuncSetAttribute(compact_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -355,14 +404,16 @@ extern "C" vio_status vio_frontend_step(vio_frontend* fe, const uint8_t* d_frame
     compact_kernel<<<2 * ns, CMP_THREADS, smem, s>>>(
         fe->trk_xy, fe->trk_status, fe->list_id[li], fe->list_count[li], cap, fe->list_xy[lo],
         fe->list_id[lo], fe->list_count[lo], fe->occupancy, fe->gx, fe->gy, fe->p.cell_w,
-        fe->p.cell_h);
+        fe->p.cell_h, stats);
   } else {
+    mark(VIO_STAGE_COMPACT);
     cudaMemsetAsync(fe->list_count[lo], 0, (size_t)2 * ns * 4, s);
     cudaMemsetAsync(fe->occupancy, 0, (size_t)ns * n_cells, s);
   }
   if (cudaGetLastError() != cudaSuccess) return VIO_ERR_CUDA;
 
   // 3. detection on camera 0 (every other image of the batch)
+  mark(VIO_STAGE_DETECT);
   Batch cam0{d_frames, 2 * frame_stride, fe->pyr[cur], 2 * ub, ns};
   Batch cam1{d_frames + frame_stride, 2 * frame_stride, fe->pyr[cur] + ub, 2 * ub, ns};
   e = launch_detect(fe->p, g, cam0, fe->occupancy, nullptr, 0, fe->ctx->d_cand,
@@ -370,17 +421,22 @@ extern "C" vio_status vio_frontend_step(vio_frontend* fe, const uint8_t* d_frame
   if (e != cudaSuccess) return VIO_ERR_CUDA;
 
   // 4. stereo matching of the new keypoints, camera 0 -> camera 1
+  mark(VIO_STAGE_STEREO);
   TrackCfg cfg{fe->p.gn_iters, 1, fe->p.fb_max_dist};
   e = launch_track(g, cam0, cam1, fe->new_xy, nullptr, fe->new_count, cap, cfg, nullptr,
                    fe->match_xy, fe->match_status, nullptr, s);
   if (e != cudaSuccess) return VIO_ERR_CUDA;
 
   // 5. append new keypoints and their matches
+  mark(VIO_STAGE_APPEND);
   append_kernel<<<ns, CMP_THREADS, 0, s>>>(fe->new_xy, fe->new_count, fe->match_xy,
                                            fe->match_status, cap, fe->list_xy[lo],
                                            fe->list_id[lo], fe->list_status,
-                                           fe->list_count[lo], fe->next_id);
+                                           fe->list_count[lo], fe->next_id, stats,
+                                           fe->have_prev ? 0 : 1);
+  mark(VIO_N_STAGES);
   if (cudaGetLastError() != cudaSuccess) return VIO_ERR_CUDA;
+  if (fe->timing) fe->ev_rec.push_back(ev);
 
   fe->cur_list = lo;
   fe->cur_pyr = prv;
@@ -388,6 +444,42 @@ extern "C" vio_status vio_frontend_step(vio_frontend* fe, const uint8_t* d_frame
   fe->prev_frames = d_frames;
   fe->prev_pitch = pitch;
   fe->prev_stride = frame_stride;
+  ++fe->steps;
+  return VIO_OK;
+}
+
+extern "C" vio_status vio_frontend_set_timing(vio_frontend* fe, int32_t enable) {
+  if (!fe) return VIO_ERR_INVALID_ARG;
+  fe->timing = enable != 0;
+  return VIO_OK;
+}
+
+extern "C" vio_status vio_frontend_read_timing(vio_frontend* fe, double* stage_ms,
+                                               int64_t* n_steps) {
+  if (!fe || !stage_ms || !n_steps) return VIO_ERR_INVALID_ARG;
+  for (int i = 0; i < VIO_N_STAGES; ++i) stage_ms[i] = 0.0;
+  vio_status st = VIO_OK;
+  for (auto& row : fe->ev_rec) {
+    if (cudaEventSynchronize(row[VIO_N_STAGES]) != cudaSuccess) st = VIO_ERR_CUDA;
+    for (int i = 0; i < VIO_N_STAGES; ++i) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, row[i], row[i + 1]) == cudaSuccess) stage_ms[i] += ms;
+    }
+    for (cudaEvent_t e : row) fe->ev_free.push_back(e);
+  }
+  *n_steps = (int64_t)fe->ev_rec.size();
+  fe->ev_rec.clear();
+  cudaGetLastError();
+  return st;
+}
+
+extern "C" vio_status vio_frontend_read_stats(vio_frontend* fe, int32_t* host_out,
+                                              int64_t* n_steps) {
+  if (!fe || !host_out || !n_steps) return VIO_ERR_INVALID_ARG;
+  const size_t bytes = (size_t)VIO_STATS_RING * fe->n_streams * VIO_N_STATS * 4;
+  if (cudaMemcpy(host_out, fe->stats, bytes, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return VIO_ERR_CUDA;
+  *n_steps = fe->steps;
   return VIO_OK;
 }
 

@@ -93,7 +93,17 @@ _SIGS = {
     "vio_frontend_reset": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p]),
     "vio_frontend_get_view": (ctypes.c_int32, [ctypes.c_void_p, ctypes.POINTER(FrontendView)]),
     "vio_frontend_launches_per_step": (ctypes.c_int32, [ctypes.c_void_p]),
+    "vio_frontend_set_timing": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32]),
+    "vio_frontend_read_timing": (ctypes.c_int32, [ctypes.c_void_p,
+                                                  ctypes.POINTER(ctypes.c_double),
+                                                  ctypes.POINTER(ctypes.c_int64)]),
+    "vio_frontend_read_stats": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p,
+                                                 ctypes.POINTER(ctypes.c_int64)]),
 }
+
+STAGES = ("pyramid", "track", "compact", "detect", "stereo", "append")
+STATS_RING = 4096
+STAT_NAMES = ("trk0", "trk1", "ok0", "ok1", "new", "matched")
 
 
 def lib_path() -> str:
@@ -312,6 +322,25 @@ class Frontend:
 
     def launches_per_step(self) -> int:
         return int(load().vio_frontend_launches_per_step(self.handle))
+
+    def set_timing(self, enable: bool):
+        _check(load().vio_frontend_set_timing(self.handle, 1 if enable else 0), "set_timing")
+
+    def read_timing(self) -> tuple[dict, int]:
+        """Summed per-stage milliseconds of the steps timed since the last read."""
+        ms = (ctypes.c_double * len(STAGES))()
+        n = ctypes.c_int64()
+        _check(load().vio_frontend_read_timing(self.handle, ms, ctypes.byref(n)), "read_timing")
+        return {k: ms[i] for i, k in enumerate(STAGES)}, int(n.value)
+
+    def read_stats(self):
+        """(ring array (STATS_RING, n_streams, 6) int32, steps run since create)."""
+        import numpy as np
+        out = np.zeros((STATS_RING, self.n_streams, len(STAT_NAMES)), np.int32)
+        n = ctypes.c_int64()
+        _check(load().vio_frontend_read_stats(self.handle, out.ctypes.data_as(ctypes.c_void_p),
+                                              ctypes.byref(n)), "read_stats")
+        return out, int(n.value)
 
     def view(self) -> dict:
         """Device tensors aliasing the frontend's outputs (no copies)."""
