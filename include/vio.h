@@ -160,6 +160,32 @@ vio_status vio_detect_grid(vio_ctx* ctx, const vio_pyr_layout* layout,
                            const uint8_t* d_mask, int64_t mask_stride, float* d_kp,
                            int16_t* d_score, int32_t* d_count, int32_t capacity, void* stream);
 
+/* Detection without any device allocation. The paper has no counterpart:
+ * this is a convenience for callers that cannot call cudaMalloc -- code
+ * inside a pre-sized memory pool or a budget that forbids new allocations,
+ * plugins whose host runtime owns all device memory, real-time loops where an
+ * allocation (which may synchronise the device) is not allowed. It computes
+ * exactly what vio_detect_grid computes, with the parameters passed directly
+ * instead of through a vio_ctx (creating a context allocates).
+ *   Scratch: a fixed array inside the library image, per device, sized for
+ *   VIO_NOALLOC_MAX_CELL_SLOTS cell slots (8 + 4 bytes each, 768 KiB), held
+ *   by every GPU that loads the library until the process exits. A call needs
+ *   n_images * cells * k_per_cell slots and n_images * cells counts, each at
+ *   most VIO_NOALLOC_MAX_CELL_SLOTS; larger calls return VIO_ERR_UNSUPPORTED.
+ *   Set-up: the first call on a device looks up the array's device address
+ *   (cudaGetSymbolAddress, with that device current); make it before any
+ *   stream capture. Later calls on that device reuse the address.
+ *   Sharing: all calls use the same array, which keeps the last call's
+ *   contents; each call writes every entry it reads. Calls that overlap on
+ *   the GPU race on the array: order them (one stream, or events).
+ * Other arguments, layouts and results as vio_detect_grid. */
+#define VIO_NOALLOC_MAX_CELL_SLOTS 65536
+vio_status vio_detect_grid_noalloc(const vio_params* p, const vio_pyr_layout* layout,
+                                   const vio_pyr_batch* batch, const uint8_t* d_occupancy,
+                                   const uint8_t* d_mask, int64_t mask_stride, float* d_kp,
+                                   int16_t* d_score, int32_t* d_count, int32_t capacity,
+                                   void* stream);
+
 /* Flags of vio_track_patches. */
 enum { VIO_TRACK_FORWARD = 0, VIO_TRACK_WITH_FB = 1 };
 

@@ -71,6 +71,12 @@ _SIGS = {
                                          ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
                                          ctypes.c_void_p]),
+    "vio_detect_grid_noalloc": (ctypes.c_int32, [ctypes.POINTER(Params), ctypes.POINTER(PyrLayout),
+                                                 ctypes.POINTER(PyrBatch), ctypes.c_void_p,
+                                                 ctypes.c_void_p, ctypes.c_int64,
+                                                 ctypes.c_void_p, ctypes.c_void_p,
+                                                 ctypes.c_void_p, ctypes.c_int32,
+                                                 ctypes.c_void_p]),
     "vio_track_patches": (ctypes.c_int32, [ctypes.c_void_p, ctypes.POINTER(PyrLayout),
                                            ctypes.POINTER(PyrBatch), ctypes.POINTER(PyrBatch),
                                            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
@@ -277,6 +283,21 @@ def fast_scores(img: torch.Tensor, out: torch.Tensor | None = None, w: int | Non
     _check(load().vio_fast_scores(_ptr(img), w, h, pitch, _ptr(out), _stream(stream)),
            "vio_fast_scores")
     return out
+
+
+NOALLOC_MAX_CELL_SLOTS = 65536
+
+
+def detect_grid_noalloc(params: Params, pyr: "Pyramids", batch: PyrBatch, kp, score, count,
+                        capacity, occupancy=None, mask=None, mask_stride=0, stream=None):
+    """vio_detect_grid_noalloc: detection for callers that cannot allocate
+    device memory (no vio_ctx; the scratch is a fixed array inside the library,
+    shared by all calls, so calls must not overlap on the GPU)."""
+    _check(load().vio_detect_grid_noalloc(ctypes.byref(params), ctypes.byref(pyr.layout),
+                                          ctypes.byref(batch), _ptr(occupancy), _ptr(mask),
+                                          mask_stride, _ptr(kp), _ptr(score), _ptr(count),
+                                          capacity, _stream(stream)),
+           "vio_detect_grid_noalloc")
 
 
 def fb_check(orig, back, count, capacity, n_images, max_dist, status, dist=None, stream=None):
