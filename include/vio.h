@@ -243,7 +243,7 @@ vio_status vio_fb_check(const float* d_orig, const float* d_back, const int32_t*
  * stays on the device between steps. */
 typedef struct vio_frontend vio_frontend;
 
-/* capacity: keypoint slots per camera per stream (>= gx*gy*k). */
+/* capacity: keypoint slots per camera per stream (gx*gy*k <= capacity <= 32767). */
 vio_status vio_frontend_create(vio_frontend** fe, const vio_params* p, int32_t w, int32_t h,
                                int32_t n_streams, int32_t capacity);
 vio_status vio_frontend_destroy(vio_frontend* fe);
@@ -254,6 +254,14 @@ vio_status vio_frontend_destroy(vio_frontend* fe);
  * that step has run. The first step after create or reset only detects. */
 vio_status vio_frontend_step(vio_frontend* fe, const uint8_t* d_frames, int32_t pitch,
                              int64_t frame_stride, void* stream);
+
+/* n_steps consecutive steps over frames already in device memory: step i
+ * reads d_frames + i * step_stride (same layout as vio_frontend_step). One
+ * call enqueues every step (no host work between frames); the usual keep-alive
+ * rule applies to the last frame. */
+vio_status vio_frontend_run(vio_frontend* fe, const uint8_t* d_frames, int32_t pitch,
+                            int64_t frame_stride, int64_t step_stride, int32_t n_steps,
+                            void* stream);
 
 /* Forget all tracks (next step starts fresh). Enqueued on `stream`. */
 vio_status vio_frontend_reset(vio_frontend* fe, void* stream);
@@ -285,26 +293,33 @@ int32_t vio_frontend_launches_per_step(const vio_frontend* fe);
 
 /* Stage timing (the paper's per-stage GPU timestamps, Sec. IV-B, Fig. 5).
  * While enabled, every step records CUDA events on its stream at the stage
- * boundaries: 0 pyramid, 1 temporal tracking, 2 compaction, 3 detection,
- * 4 stereo matching, 5 append. vio_frontend_read_timing waits for the
- * recorded events, adds each stage's elapsed milliseconds into
- * stage_ms[0..5] (overwritten), stores the number of timed steps in *n_steps
- * and clears the record. Enabling, disabling and reading are host calls. */
-enum { VIO_STAGE_PYRAMID = 0, VIO_STAGE_TRACK, VIO_STAGE_COMPACT, VIO_STAGE_DETECT,
-       VIO_STAGE_STEREO, VIO_STAGE_APPEND, VIO_N_STAGES };
+ * boundaries: 0 pyramid levels 1-2 and the per-cell detection candidates
+ * (one launch), 1 deeper pyramid levels, 2 temporal tracking and stereo
+ * matching (one launch), 3 finalisation (survivors, per-cell selection,
+ * appends). vio_frontend_read_timing waits for the recorded events, adds each
+ * stage's elapsed milliseconds into stage_ms[0..3] (overwritten), stores the
+ * number of timed steps in *n_steps and clears the record. Enabling,
+ * disabling and reading are host calls. */
+enum { VIO_STAGE_FRONT = 0, VIO_STAGE_PYRAMID_UPPER, VIO_STAGE_TRACK, VIO_STAGE_FINALIZE,
+       VIO_N_STAGES };
 vio_status vio_frontend_set_timing(vio_frontend* fe, int32_t enable);
-vio_status vio_frontend_read_timing(vio_frontend* fe, double* stage_ms, int64_t* n_steps);
+/* step_ms (may be NULL): per timed step, the time from its first to its last
+ * event, for up to step_ms_cap steps in order. */
+vio_status vio_frontend_read_timing(vio_frontend* fe, double* stage_ms, int64_t* n_steps,
+                                    float* step_ms, int64_t step_ms_cap);
 
 /* Per-step counters, written on the device by every step into a ring of
  * VIO_STATS_RING entries (entry = step index mod the ring size), per stream,
  * VIO_N_STATS int32 values: tracks attempted on cam0 and cam1, tracks that
- * survived on cam0 and cam1, new detections, successful stereo matches.
+ * survived on cam0 and cam1, new detections, successful stereo matches of the
+ * new detections, and detection candidates stereo-matched (every cell's top-k
+ * is matched while temporal tracking runs; the selection uses a subset).
  * vio_frontend_read_stats copies the whole ring to host_out (blocking; size
  * VIO_STATS_RING * n_streams * VIO_N_STATS) and returns the number of steps
  * run since create in *n_steps. */
 #define VIO_STATS_RING 4096
 enum { VIO_STAT_TRK0 = 0, VIO_STAT_TRK1, VIO_STAT_OK0, VIO_STAT_OK1, VIO_STAT_NEW,
-       VIO_STAT_MATCHED, VIO_N_STATS };
+       VIO_STAT_MATCHED, VIO_STAT_CAND, VIO_N_STATS };
 vio_status vio_frontend_read_stats(vio_frontend* fe, int32_t* host_out, int64_t* n_steps);
 
 #ifdef __cplusplus

@@ -24,6 +24,20 @@ struct Batch {
   int n;
 };
 
+// Row/column split of a linear index without an integer division: for
+// i < 2^22 the product (i + 0.5) * fl(1/w) is within (i/w) * 2^-23 of the
+// exact quotient, less than the 0.5/w that separates it from the next
+// integer, so its truncation is floor(i / w).
+struct Split {
+  float inv;
+  int w;
+  __device__ __forceinline__ explicit Split(int w_) : inv(1.f / (float)w_), w(w_) {}
+  __device__ __forceinline__ void operator()(int i, int& r, int& c) const {
+    r = (int)(((float)i + 0.5f) * inv);
+    c = i - r * w;
+  }
+};
+
 inline Geom make_geom(const vio_pyr_layout& L) {
   Geom g{};
   g.n_levels = L.n_levels;
@@ -72,6 +86,8 @@ struct vio_ctx {
 namespace vio {
 // launchers (host side), implemented in the .cu files
 cudaError_t launch_pyramid(const Geom& g, const Batch& b, int round_mode, cudaStream_t s);
+cudaError_t launch_pyramid_from(const Geom& g, const Batch& b, int s0, int round_mode,
+                                cudaStream_t s);
 cudaError_t launch_fast_scores(const uint8_t* img, int w, int h, int pitch, int16_t* out,
                                cudaStream_t s);
 cudaError_t launch_detect(const vio_params& p, const Geom& g, const Batch& b,
@@ -85,6 +101,4 @@ cudaError_t launch_track(const Geom& g, const Batch& src, const Batch& dst, cons
 cudaError_t launch_fb_check(const float* orig, const float* back, const int32_t* count,
                             int capacity, int n_images, float max_dist, uint8_t* status,
                             float* dist, cudaStream_t s);
-// pattern table upload (once per process and device)
-cudaError_t ensure_pattern(int pattern_id);
 }  // namespace vio

@@ -1,7 +1,6 @@
-// Per-frame frontend (Sec. III-B): stage order pyramid -> temporal tracking
-// -> detection -> cross-camera matching, for n_streams stereo streams of one
-// size, with all state resident on the device and nothing synchronised with
-// the host inside a step.
+// Per-frame frontend state and driver (Sec. III-B): n_streams stereo streams
+// of one size, all state resident on the device, nothing synchronised with
+// the host inside a step. The kernels of one frame are in frame.cu.
 //
 // Keypoint lists, per (stream, camera), in stable order:
 //   camera 0: surviving tracks, then this step's new detections
@@ -10,183 +9,17 @@
 //             passed the forward-backward check, at the matched position.
 // A track survives a step if its temporal track has status OK. Detection
 // counts, per cell, the surviving camera-0 tracks against k.
-#include <stdlib.h>
-
 #include <array>
 #include <new>
 #include <vector>
 
-#include "common.cuh"
-
-namespace vio {
-namespace {
-
-constexpr int CMP_THREADS = 256;
-
-// cell index of a position, exact: the largest cx with cx * cw <= x
-__device__ __forceinline__ int cell_of(float x, int cw) {
-  int c = (int)floorf(x / (float)cw);
-  if ((float)(c + 1) * (float)cw <= x) ++c;
-  if ((float)c * (float)cw > x) --c;
-  return c;
-}
-
-// One CTA per (stream, camera): keep the slots whose status is OK, in order.
-// Camera 0 also counts survivors per detection cell (saturating at 255).
-__global__ void __launch_bounds__(CMP_THREADS) compact_kernel(
-    const float* __restrict__ pos, const uint8_t* __restrict__ status,
-    const int32_t* __restrict__ ids_in, const int32_t* __restrict__ count_in, int capacity,
-    float* __restrict__ pos_out, int32_t* __restrict__ ids_out, int32_t* __restrict__ count_out,
-    uint8_t* __restrict__ occupancy, int gx, int gy, int cw, int ch,
-    int32_t* __restrict__ stats) {
-  extern __shared__ int occ_s[];
-  __shared__ int warp_sums[CMP_THREADS / 32];
-  __shared__ int carry_s;
-  const int list = blockIdx.x;           // 2 * stream + camera
-  const bool cam0 = (list & 1) == 0;
-  const int stream = list >> 1;
-  const int n_cells = gx * gy;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (cam0)
-    for (int i = threadIdx.x; i < n_cells; i += CMP_THREADS) occ_s[i] = 0;
-  if (threadIdx.x == 0) carry_s = 0;
-  __syncthreads();
-  const long long base = (long long)list * capacity;
-  const int n = min(count_in[list], capacity);
-  for (int c0 = 0; c0 < n; c0 += CMP_THREADS) {
-    const int i = c0 + threadIdx.x;
-    const int keep = (i < n && status[base + i] == VIO_TRACK_OK) ? 1 : 0;
-    int incl = keep;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int t = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += t;
-    }
-    if (lane == 31) warp_sums[warp] = incl;
-    __syncthreads();
-    if (warp == 0) {
-      int ws = lane < CMP_THREADS / 32 ? warp_sums[lane] : 0;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int t = __shfl_up_sync(0xffffffffu, ws, o);
-        if (lane >= o) ws += t;
-      }
-      if (lane < CMP_THREADS / 32) warp_sums[lane] = ws;
-    }
-    __syncthreads();
-    const int carry = carry_s;
-    if (keep) {
-      const int o = carry + (warp ? warp_sums[warp - 1] : 0) + incl - 1;
-      const float x = pos[2 * (base + i)], y = pos[2 * (base + i) + 1];
-      pos_out[2 * (base + o)] = x;
-      pos_out[2 * (base + o) + 1] = y;
-      ids_out[base + o] = ids_in[base + i];
-      if (cam0 && x >= 0.f && y >= 0.f) {
-        const int cx = cell_of(x, cw), cy = cell_of(y, ch);
-        if (cx < gx && cy < gy) atomicAdd(&occ_s[cy * gx + cx], 1);
-      }
-    }
-    __syncthreads();
-    if (threadIdx.x == CMP_THREADS - 1) carry_s = carry + warp_sums[CMP_THREADS / 32 - 1];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) {
-    count_out[list] = carry_s;
-    stats[stream * VIO_N_STATS + VIO_STAT_TRK0 + (list & 1)] = n;
-    stats[stream * VIO_N_STATS + VIO_STAT_OK0 + (list & 1)] = carry_s;
-  }
-  if (cam0)
-    for (int i = threadIdx.x; i < n_cells; i += CMP_THREADS)
-      occupancy[(long long)stream * n_cells + i] = (uint8_t)min(occ_s[i], 255);
-}
-
-// One CTA per stream: append the new detections to camera 0 and their
-// successful stereo matches to camera 1; assign ids.
-__global__ void __launch_bounds__(CMP_THREADS) append_kernel(
-    const float* __restrict__ new_xy, const int32_t* __restrict__ new_count,
-    const float* __restrict__ match_xy, const uint8_t* __restrict__ match_status,
-    int capacity, float* __restrict__ pos, int32_t* __restrict__ ids,
-    uint8_t* __restrict__ lstatus, int32_t* __restrict__ count, int32_t* __restrict__ next_id,
-    int32_t* __restrict__ stats, int first) {
-  __shared__ int warp_sums[CMP_THREADS / 32];
-  __shared__ int carry_s;
-  const int s = blockIdx.x;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int nn = min(new_count[s], capacity);
-  const int id0 = next_id[s];
-  const long long b0 = (long long)(2 * s) * capacity, b1 = b0 + capacity;
-  const long long bn = (long long)s * capacity;
-  const int c0 = count[2 * s], c1 = count[2 * s + 1];
-  for (int r = threadIdx.x; r < nn; r += CMP_THREADS) {
-    const int o = c0 + r;
-    if (o < capacity) {
-      pos[2 * (b0 + o)] = new_xy[2 * (bn + r)];
-      pos[2 * (b0 + o) + 1] = new_xy[2 * (bn + r) + 1];
-      ids[b0 + o] = id0 + r;
-    }
-  }
-  if (threadIdx.x == 0) carry_s = 0;
-  __syncthreads();
-  for (int r0 = 0; r0 < nn; r0 += CMP_THREADS) {
-    const int r = r0 + threadIdx.x;
-    const int keep = (r < nn && match_status[bn + r] == VIO_TRACK_OK) ? 1 : 0;
-    int incl = keep;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int t = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += t;
-    }
-    if (lane == 31) warp_sums[warp] = incl;
-    __syncthreads();
-    if (warp == 0) {
-      int ws = lane < CMP_THREADS / 32 ? warp_sums[lane] : 0;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int t = __shfl_up_sync(0xffffffffu, ws, o);
-        if (lane >= o) ws += t;
-      }
-      if (lane < CMP_THREADS / 32) warp_sums[lane] = ws;
-    }
-    __syncthreads();
-    const int carry = carry_s;
-    if (keep) {
-      const int o = c1 + carry + (warp ? warp_sums[warp - 1] : 0) + incl - 1;
-      if (o < capacity) {
-        pos[2 * (b1 + o)] = match_xy[2 * (bn + r)];
-        pos[2 * (b1 + o) + 1] = match_xy[2 * (bn + r) + 1];
-        ids[b1 + o] = id0 + r;
-      }
-    }
-    __syncthreads();
-    if (threadIdx.x == CMP_THREADS - 1) carry_s = carry + warp_sums[CMP_THREADS / 32 - 1];
-    __syncthreads();
-  }
-  const int n0 = min(c0 + nn, capacity), n1 = min(c1 + carry_s, capacity);
-  for (int i = threadIdx.x; i < capacity; i += CMP_THREADS) {
-    lstatus[b0 + i] = i < n0 ? VIO_TRACK_OK : VIO_TRACK_EMPTY;
-    lstatus[b1 + i] = i < n1 ? VIO_TRACK_OK : VIO_TRACK_EMPTY;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    count[2 * s] = n0;
-    count[2 * s + 1] = n1;
-    next_id[s] = id0 + nn;
-    int32_t* st = stats + s * VIO_N_STATS;
-    if (first) st[VIO_STAT_TRK0] = st[VIO_STAT_TRK1] = st[VIO_STAT_OK0] = st[VIO_STAT_OK1] = 0;
-    st[VIO_STAT_NEW] = nn;
-    st[VIO_STAT_MATCHED] = carry_s;
-  }
-}
-
-}  // namespace
-}  // namespace vio
+#include "frame.cuh"
 
 struct vio_frontend {
   vio_params p;
   int w, h, n_streams, capacity;
-  vio_pyr_layout layout;
-  vio_ctx* ctx;
   int gx, gy;
+  vio_pyr_layout layout;
   // device buffers (one allocation)
   void* d_mem;
   uint8_t* pyr[2];            // upper buffers, 2*n_streams images each, ring of 2 frames
@@ -196,41 +29,71 @@ struct vio_frontend {
   uint8_t* list_status;       // status of the current list (output view)
   float* trk_xy;              // temporal track result, float2 per slot
   uint8_t* trk_status;
-  uint8_t* occupancy;         // n_streams * n_cells
+  unsigned long long* cand;   // n_streams * cells * k candidate keys
+  int32_t* cand_count;        // n_streams * cells
+  float* spec_xy;             // stereo matches of the candidates
+  uint8_t* spec_status;
+  uint8_t* occupancy;         // n_streams * cells
   float* new_xy;              // n_streams * capacity
-  int16_t* new_score;
   int32_t* new_count;         // n_streams
-  float* match_xy;            // n_streams * capacity
-  uint8_t* match_status;
   int32_t* next_id;           // n_streams
   int32_t* stats;             // VIO_STATS_RING * n_streams * VIO_N_STATS
   // host state
-  int64_t steps;
-  bool timing;
-  std::vector<cudaEvent_t> ev_free;                    // event pool
-  std::vector<std::array<cudaEvent_t, VIO_N_STAGES + 1>> ev_rec;  // one row per timed step
   int cur_list;
   int cur_pyr;
   bool have_prev;
   const uint8_t* prev_frames;
   int32_t prev_pitch;
   int64_t prev_stride;
+  int64_t steps;
+  bool timing;
+  std::vector<cudaEvent_t> ev_free;
+  std::vector<std::array<cudaEvent_t, VIO_N_STAGES + 1>> ev_rec;
 };
 
 namespace {
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+bool frontend_params_ok(const vio_params* p) {
+  if (!p || p->n_levels < 1 || p->n_levels > VIO_MAX_LEVELS) return false;
+  if (p->round_mode != 0 && p->round_mode != 1) return false;
+  if (p->gn_iters < 0 || p->gn_iters > 1000 || p->pattern_id != 0) return false;
+  if (p->cell_w < 1 || p->cell_h < 1 || p->cell_w > 512 || p->cell_h > 512) return false;
+  if (p->k_per_cell < 1 || p->k_per_cell > VIO_MAX_K) return false;
+  if (p->n_thresholds < 1 || p->n_thresholds > VIO_MAX_THRESHOLDS) return false;
+  for (int i = 0; i < p->n_thresholds; ++i) {
+    if (p->thresholds[i] < 0 || p->thresholds[i] > 254) return false;
+    if (i > 0 && p->thresholds[i] > p->thresholds[i - 1]) return false;
+  }
+  return p->detect_border >= 0 && p->fb_max_dist >= 0.f;
+}
+
+cudaEvent_t take_event(vio_frontend* fe) {
+  if (!fe->ev_free.empty()) {
+    cudaEvent_t e = fe->ev_free.back();
+    fe->ev_free.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
 }  // namespace
 
 extern "C" vio_status vio_frontend_create(vio_frontend** out, const vio_params* p, int32_t w,
                                           int32_t h, int32_t n_streams, int32_t capacity) {
-  if (!out || !p || w <= 0 || h <= 0 || n_streams <= 0 || capacity <= 0)
+  // capacity < 2^15: the finalize kernel packs two per-camera counts in one int
+  if (!out || !frontend_params_ok(p) || w <= 0 || h <= 0 || n_streams <= 0 || capacity <= 0 ||
+      n_streams > 65535 || capacity > 32767)
     return VIO_ERR_INVALID_ARG;
   *out = nullptr;
   vio_pyr_layout L;
   vio_status st = vio_pyr_layout_make(w, h, p->n_levels, w, &L);
   if (st != VIO_OK) return st;
   const int gx = w / p->cell_w, gy = h / p->cell_h;
-  if ((long long)gx * gy * p->k_per_cell > capacity) return VIO_ERR_INVALID_ARG;
+  const long long n_cells = (long long)gx * gy;
+  if (n_cells * p->k_per_cell > capacity) return VIO_ERR_INVALID_ARG;
+  if (n_cells * 4 > 200 * 1024) return VIO_ERR_UNSUPPORTED;   // finalize's shared counters
   vio_frontend* fe = new (std::nothrow) vio_frontend();
   if (!fe) return VIO_ERR_OOM;
   fe->p = *p;
@@ -238,39 +101,35 @@ extern "C" vio_status vio_frontend_create(vio_frontend** out, const vio_params* 
   fe->h = h;
   fe->n_streams = n_streams;
   fe->capacity = capacity;
-  fe->layout = L;
   fe->gx = gx;
   fe->gy = gy;
-  st = vio_ctx_create(&fe->ctx, p, w, h, n_streams);
-  if (st != VIO_OK) {
-    delete fe;
-    return st;
-  }
+  fe->layout = L;
   const size_t nl = (size_t)2 * n_streams, slots = nl * capacity;
-  const size_t ns = (size_t)n_streams, nc = (size_t)gx * gy;
+  const size_t ns = (size_t)n_streams, nc = (size_t)n_cells, kk = (size_t)p->k_per_cell;
   const size_t sizes[] = {
-      (size_t)L.upper_bytes * nl, (size_t)L.upper_bytes * nl,   // pyr[0..1]
-      slots * 8, slots * 8,                                     // list_xy
-      slots * 4, slots * 4,                                     // list_id
-      nl * 4, nl * 4,                                           // list_count
-      slots,                                                    // list_status
-      slots * 8, slots,                                         // trk
-      ns * nc,                                                  // occupancy
-      ns * capacity * 8, ns * capacity * 2, ns * 4,             // new
-      ns * capacity * 8, ns * capacity,                         // match
-      ns * 4,                                                   // next_id
-      (size_t)VIO_STATS_RING * ns * VIO_N_STATS * 4};           // stats
+      (size_t)L.upper_bytes * nl, (size_t)L.upper_bytes * nl,   // 0-1 pyr
+      slots * 8, slots * 8,                                     // 2-3 list_xy
+      slots * 4, slots * 4,                                     // 4-5 list_id
+      nl * 4, nl * 4,                                           // 6-7 list_count
+      slots,                                                    // 8 list_status
+      slots * 8, slots,                                         // 9-10 trk
+      ns * nc * kk * 8, ns * nc * 4,                            // 11-12 cand
+      ns * nc * kk * 8, ns * nc * kk,                           // 13-14 spec
+      ns * nc,                                                  // 15 occupancy
+      ns * capacity * 8, ns * 4,                                // 16-17 new
+      ns * 4,                                                   // 18 next_id
+      (size_t)VIO_STATS_RING * ns * VIO_N_STATS * 4};           // 19 stats
+  constexpr size_t kN = sizeof(sizes) / sizeof(sizes[0]);
   size_t total = 0;
   for (size_t s : sizes) total += align256(s);
   if (cudaMalloc(&fe->d_mem, total) != cudaSuccess) {
     cudaGetLastError();
-    vio_ctx_destroy(fe->ctx);
     delete fe;
     return VIO_ERR_OOM;
   }
   uint8_t* q = (uint8_t*)fe->d_mem;
-  void* ptrs[sizeof(sizes) / sizeof(sizes[0])];
-  for (size_t i = 0; i < sizeof(sizes) / sizeof(sizes[0]); ++i) {
+  void* ptrs[kN];
+  for (size_t i = 0; i < kN; ++i) {
     ptrs[i] = q;
     q += align256(sizes[i]);
   }
@@ -285,28 +144,31 @@ extern "C" vio_status vio_frontend_create(vio_frontend** out, const vio_params* 
   fe->list_status = (uint8_t*)ptrs[8];
   fe->trk_xy = (float*)ptrs[9];
   fe->trk_status = (uint8_t*)ptrs[10];
-  fe->occupancy = (uint8_t*)ptrs[11];
-  fe->new_xy = (float*)ptrs[12];
-  fe->new_score = (int16_t*)ptrs[13];
-  fe->new_count = (int32_t*)ptrs[14];
-  fe->match_xy = (float*)ptrs[15];
-  fe->match_status = (uint8_t*)ptrs[16];
-  fe->next_id = (int32_t*)ptrs[17];
-  fe->stats = (int32_t*)ptrs[18];
-  fe->steps = 0;
-  fe->timing = false;
+  fe->cand = (unsigned long long*)ptrs[11];
+  fe->cand_count = (int32_t*)ptrs[12];
+  fe->spec_xy = (float*)ptrs[13];
+  fe->spec_status = (uint8_t*)ptrs[14];
+  fe->occupancy = (uint8_t*)ptrs[15];
+  fe->new_xy = (float*)ptrs[16];
+  fe->new_count = (int32_t*)ptrs[17];
+  fe->next_id = (int32_t*)ptrs[18];
+  fe->stats = (int32_t*)ptrs[19];
   if (cudaMemset(fe->d_mem, 0, total) != cudaSuccess ||
       cudaMemset(fe->list_status, VIO_TRACK_EMPTY, slots) != cudaSuccess ||
       cudaDeviceSynchronize() != cudaSuccess) {
     cudaGetLastError();
     cudaFree(fe->d_mem);
-    vio_ctx_destroy(fe->ctx);
     delete fe;
     return VIO_ERR_CUDA;
   }
   fe->cur_list = 0;
   fe->cur_pyr = 0;
   fe->have_prev = false;
+  fe->prev_frames = nullptr;
+  fe->prev_pitch = 0;
+  fe->prev_stride = 0;
+  fe->steps = 0;
+  fe->timing = false;
   *out = fe;
   return VIO_OK;
 }
@@ -317,7 +179,6 @@ extern "C" vio_status vio_frontend_destroy(vio_frontend* fe) {
     for (cudaEvent_t e : row) cudaEventDestroy(e);
   for (cudaEvent_t e : fe->ev_free) cudaEventDestroy(e);
   cudaFree(fe->d_mem);
-  vio_ctx_destroy(fe->ctx);
   delete fe;
   return VIO_OK;
 }
@@ -336,23 +197,10 @@ extern "C" vio_status vio_frontend_reset(vio_frontend* fe, void* stream) {
 
 extern "C" int32_t vio_frontend_launches_per_step(const vio_frontend* fe) {
   if (!fe) return 0;
-  // pyramid levels, temporal track, compaction, detect cells + select,
-  // stereo, append
-  return (fe->p.n_levels - 1) + 1 + 1 + 2 + 1 + 1;
+  vio_pyr_layout L;
+  if (vio_pyr_layout_make(fe->w, fe->h, fe->p.n_levels, fe->w, &L) != VIO_OK) return 0;
+  return vio::frame_launches(vio::make_geom(L));
 }
-
-namespace {
-cudaEvent_t take_event(vio_frontend* fe) {
-  if (!fe->ev_free.empty()) {
-    cudaEvent_t e = fe->ev_free.back();
-    fe->ev_free.pop_back();
-    return e;
-  }
-  cudaEvent_t e = nullptr;
-  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
-  return e;
-}
-}  // namespace
 
 extern "C" vio_status vio_frontend_step(vio_frontend* fe, const uint8_t* d_frames,
                                         int32_t pitch, int64_t frame_stride, void* stream) {
@@ -361,81 +209,47 @@ extern "C" vio_status vio_frontend_step(vio_frontend* fe, const uint8_t* d_frame
     return VIO_ERR_INVALID_ARG;
   if (fe->have_prev && fe->prev_pitch != pitch) return VIO_ERR_UNSUPPORTED;
   cudaStream_t s = (cudaStream_t)stream;
-  const int ns = fe->n_streams, cap = fe->capacity;
+  const int ns = fe->n_streams;
   vio_pyr_layout L;
   vio_status st = vio_pyr_layout_make(fe->w, fe->h, fe->p.n_levels, pitch, &L);
   if (st != VIO_OK) return st;
-  const Geom g = make_geom(L);
   const long long ub = L.upper_bytes;
   const int cur = fe->cur_pyr, prv = cur ^ 1;
   const int li = fe->cur_list, lo = li ^ 1;
-  const int n_cells = fe->gx * fe->gy;
-  int32_t* stats = fe->stats + (fe->steps % VIO_STATS_RING) * ns * VIO_N_STATS;
 
   std::array<cudaEvent_t, VIO_N_STAGES + 1> ev{};
   if (fe->timing)
     for (auto& e : ev)
       if (!(e = take_event(fe))) return VIO_ERR_CUDA;
-  auto mark = [&](int i) {
-    if (fe->timing) cudaEventRecord(ev[i], s);
-  };
 
-  // 1. pyramids of all 2*ns images of this frame
-  mark(VIO_STAGE_PYRAMID);
-  Batch cur_all{d_frames, frame_stride, fe->pyr[cur], ub, 2 * ns};
-  cudaError_t e = launch_pyramid(g, cur_all, fe->p.round_mode, s);
-  if (e != cudaSuccess) return VIO_ERR_CUDA;
-
-  // 2. temporal tracking with the forward-backward check, then compaction
-  mark(VIO_STAGE_TRACK);
-  if (fe->have_prev) {
-    Batch prev_all{fe->prev_frames, fe->prev_stride, fe->pyr[prv], ub, 2 * ns};
-    TrackCfg cfg{fe->p.gn_iters, 1, fe->p.fb_max_dist};
-    e = launch_track(g, prev_all, cur_all, fe->list_xy[li], nullptr, fe->list_count[li], cap,
-                     cfg, nullptr, fe->trk_xy, fe->trk_status, nullptr, s);
-    if (e != cudaSuccess) return VIO_ERR_CUDA;
-    mark(VIO_STAGE_COMPACT);
-    const size_t smem = (size_t)n_cells * sizeof(int);
-    if (smem > 48 * 1024) {
-      e = cudaFuncSetAttribute(compact_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)smem);
-      if (e != cudaSuccess) return VIO_ERR_CUDA;
-    }
-    compact_kernel<<<2 * ns, CMP_THREADS, smem, s>>>(
-        fe->trk_xy, fe->trk_status, fe->list_id[li], fe->list_count[li], cap, fe->list_xy[lo],
-        fe->list_id[lo], fe->list_count[lo], fe->occupancy, fe->gx, fe->gy, fe->p.cell_w,
-        fe->p.cell_h, stats);
-  } else {
-    mark(VIO_STAGE_COMPACT);
-    cudaMemsetAsync(fe->list_count[lo], 0, (size_t)2 * ns * 4, s);
-    cudaMemsetAsync(fe->occupancy, 0, (size_t)ns * n_cells, s);
-  }
-  if (cudaGetLastError() != cudaSuccess) return VIO_ERR_CUDA;
-
-  // 3. detection on camera 0 (every other image of the batch)
-  mark(VIO_STAGE_DETECT);
-  Batch cam0{d_frames, 2 * frame_stride, fe->pyr[cur], 2 * ub, ns};
-  Batch cam1{d_frames + frame_stride, 2 * frame_stride, fe->pyr[cur] + ub, 2 * ub, ns};
-  e = launch_detect(fe->p, g, cam0, fe->occupancy, nullptr, 0, fe->ctx->d_cand,
-                    fe->ctx->d_cand_count, fe->new_xy, fe->new_score, fe->new_count, cap, s);
-  if (e != cudaSuccess) return VIO_ERR_CUDA;
-
-  // 4. stereo matching of the new keypoints, camera 0 -> camera 1
-  mark(VIO_STAGE_STEREO);
-  TrackCfg cfg{fe->p.gn_iters, 1, fe->p.fb_max_dist};
-  e = launch_track(g, cam0, cam1, fe->new_xy, nullptr, fe->new_count, cap, cfg, nullptr,
-                   fe->match_xy, fe->match_status, nullptr, s);
-  if (e != cudaSuccess) return VIO_ERR_CUDA;
-
-  // 5. append new keypoints and their matches
-  mark(VIO_STAGE_APPEND);
-  append_kernel<<<ns, CMP_THREADS, 0, s>>>(fe->new_xy, fe->new_count, fe->match_xy,
-                                           fe->match_status, cap, fe->list_xy[lo],
-                                           fe->list_id[lo], fe->list_status,
-                                           fe->list_count[lo], fe->next_id, stats,
-                                           fe->have_prev ? 0 : 1);
-  mark(VIO_N_STAGES);
-  if (cudaGetLastError() != cudaSuccess) return VIO_ERR_CUDA;
+  FrameLaunch f{};
+  f.p = fe->p;
+  f.g = make_geom(L);
+  f.n_streams = ns;
+  f.cap = fe->capacity;
+  f.have_prev = fe->have_prev ? 1 : 0;
+  f.cur = Batch{d_frames, frame_stride, fe->pyr[cur], ub, 2 * ns};
+  f.prev = fe->have_prev ? Batch{fe->prev_frames, fe->prev_stride, fe->pyr[prv], ub, 2 * ns}
+                         : f.cur;
+  f.list_xy_in = fe->list_xy[li];
+  f.list_id_in = fe->list_id[li];
+  f.list_count_in = fe->list_count[li];
+  f.list_xy_out = fe->list_xy[lo];
+  f.list_id_out = fe->list_id[lo];
+  f.list_count_out = fe->list_count[lo];
+  f.list_status = fe->list_status;
+  f.trk_xy = fe->trk_xy;
+  f.trk_status = fe->trk_status;
+  f.cand = fe->cand;
+  f.cand_count = fe->cand_count;
+  f.spec_xy = fe->spec_xy;
+  f.spec_status = fe->spec_status;
+  f.new_xy = fe->new_xy;
+  f.new_count = fe->new_count;
+  f.next_id = fe->next_id;
+  f.occupancy = fe->occupancy;
+  f.stats = fe->stats + (fe->steps % VIO_STATS_RING) * ns * VIO_N_STATS;
+  if (launch_frame(f, s, fe->timing ? ev.data() : nullptr) != cudaSuccess) return VIO_ERR_CUDA;
   if (fe->timing) fe->ev_rec.push_back(ev);
 
   fe->cur_list = lo;
@@ -448,6 +262,20 @@ extern "C" vio_status vio_frontend_step(vio_frontend* fe, const uint8_t* d_frame
   return VIO_OK;
 }
 
+extern "C" vio_status vio_frontend_run(vio_frontend* fe, const uint8_t* d_frames, int32_t pitch,
+                                       int64_t frame_stride, int64_t step_stride,
+                                       int32_t n_steps, void* stream) {
+  if (!fe || !d_frames || n_steps < 0 || step_stride < 0) return VIO_ERR_INVALID_ARG;
+  if (n_steps > 1 && step_stride < (int64_t)2 * fe->n_streams * frame_stride)
+    return VIO_ERR_INVALID_ARG;
+  for (int32_t i = 0; i < n_steps; ++i) {
+    const vio_status st = vio_frontend_step(fe, d_frames + (int64_t)i * step_stride, pitch,
+                                            frame_stride, stream);
+    if (st != VIO_OK) return st;
+  }
+  return VIO_OK;
+}
+
 extern "C" vio_status vio_frontend_set_timing(vio_frontend* fe, int32_t enable) {
   if (!fe) return VIO_ERR_INVALID_ARG;
   fe->timing = enable != 0;
@@ -455,16 +283,24 @@ extern "C" vio_status vio_frontend_set_timing(vio_frontend* fe, int32_t enable) 
 }
 
 extern "C" vio_status vio_frontend_read_timing(vio_frontend* fe, double* stage_ms,
-                                               int64_t* n_steps) {
+                                               int64_t* n_steps, float* step_ms,
+                                               int64_t step_ms_cap) {
   if (!fe || !stage_ms || !n_steps) return VIO_ERR_INVALID_ARG;
   for (int i = 0; i < VIO_N_STAGES; ++i) stage_ms[i] = 0.0;
   vio_status st = VIO_OK;
+  int64_t k = 0;
   for (auto& row : fe->ev_rec) {
     if (cudaEventSynchronize(row[VIO_N_STAGES]) != cudaSuccess) st = VIO_ERR_CUDA;
     for (int i = 0; i < VIO_N_STAGES; ++i) {
       float ms = 0.f;
       if (cudaEventElapsedTime(&ms, row[i], row[i + 1]) == cudaSuccess) stage_ms[i] += ms;
     }
+    if (step_ms && k < step_ms_cap) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, row[0], row[VIO_N_STAGES]);
+      step_ms[k] = ms;
+    }
+    ++k;
     for (cudaEvent_t e : row) fe->ev_free.push_back(e);
   }
   *n_steps = (int64_t)fe->ev_rec.size();

@@ -1,0 +1,459 @@
+// Device code of the patch tracker (Sec. III-E, Eq. 4-5): one warp of 32
+// threads per keypoint, each lane owning up to two of the 52 pattern points.
+//
+// Algebra used on the device. With raw template samples s_i, raw gradients
+// g_i and J'_i = [g_x, g_y, g_y u_i - g_x v_i], the mean-normalised
+// quantities of Eq. 4 are J_i = J'_i / Ibar, H = H' / Ibar^2 (H' = sum
+// J'_i^T J'_i) and G_i = Ibar H'^-1 J'_i, so Eq. 5's increment
+//   delta = -sum_i G_i (r_i / rbar - s_i / Ibar)
+// equals  delta = c - (S / R) k,  with S = sum s_i, R = sum r_i,
+// c = H'^-1 sum J'_i s_i (per template) and k = sum (H'^-1 J'_i) r_i (per
+// iteration). Each Gauss-Newton step therefore needs ONE warp reduction of
+// four values (R, k), not two dependent ones.
+//
+// Positions keep an integer anchor plus a small float offset, so bilinear
+// weights carry full FP32 precision at any image size; template samples of
+// one keypoint share one sub-pixel offset and therefore one set of weights.
+// The rotation is carried as (cos, sin) and updated by the increment's
+// rotation, whose cosine, sine and the SE(2) left-Jacobian terms come from
+// their Taylor series for small angles (|phi| < 0.25, error < 1e-9), so a
+// Gauss-Newton step evaluates no trigonometric function.
+#pragma once
+#include <math.h>
+
+#include "common.cuh"
+
+namespace vio {
+namespace trk {
+
+// The sample pattern (Sec. III-E gives only its size, 52): the odd lattice
+// u, v in {+-1, +-3, +-5, +-7} with |u| + |v| <= 10, ordered by v then u.
+struct Pattern {
+  int8_t u[kPatternMax], v[kPatternMax];
+  int n;
+};
+constexpr Pattern make_pattern() {
+  Pattern p{};
+  int n = 0;
+  for (int v = -7; v <= 7; v += 2)
+    for (int u = -7; u <= 7; u += 2) {
+      const int au = u < 0 ? -u : u, av = v < 0 ? -v : v;
+      if (au + av <= 10) {
+        p.u[n] = (int8_t)u;
+        p.v[n] = (int8_t)v;
+        ++n;
+      }
+    }
+  p.n = n;
+  return p;
+}
+static_assert(make_pattern().n == 52, "pattern size");
+constexpr int kNP = 52;
+
+// Point i of the pattern, by rows: v = -7, -5, ..., 7 hold 4, 6, 8, 8, 8, 8,
+// 6, 4 points, u running from -hw to hw in steps of 2 (hw = 3, 5, 7, ...).
+__host__ __device__ constexpr void point_of(int i, int& u, int& v) {
+  int start = 0;
+  for (int r = 0; r < 8; ++r) {
+    const int hw = (r == 0 || r == 7) ? 3 : (r == 1 || r == 6) ? 5 : 7;
+    const int n = hw + 1;
+    if (i < start + n) {
+      v = -7 + 2 * r;
+      u = -hw + 2 * (i - start);
+      return;
+    }
+    start += n;
+  }
+  u = v = 0;
+}
+constexpr bool pattern_rows_match() {
+  const Pattern P = make_pattern();
+  for (int i = 0; i < kNP; ++i) {
+    int u = 0, v = 0;
+    point_of(i, u, v);
+    if (u != P.u[i] || v != P.v[i]) return false;
+  }
+  return true;
+}
+static_assert(pattern_rows_match(), "row form of the pattern");
+
+// The lane's two pattern points (the second exists for lanes 0..19).
+struct LanePts {
+  int iu[2], iv[2];
+  float u[2], v[2];
+};
+__device__ __forceinline__ LanePts lane_points(int lane) {
+  LanePts P;
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    const int i = lane + 32 * j;
+    int u = 0, v = 0;
+    if (i < kNP) point_of(i, u, v);
+    P.iu[j] = u;
+    P.iv[j] = v;
+    P.u[j] = (float)u;
+    P.v[j] = (float)v;
+  }
+  return P;
+}
+
+struct Lv {
+  const uint8_t* p;
+  int w, h, pitch;
+};
+
+template <int N>
+__device__ __forceinline__ void warp_sum(float (&v)[N]) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+    for (int i = 0; i < N; ++i) v[i] += __shfl_xor_sync(0xffffffffu, v[i], o);
+}
+
+// Sums four values over the warp and gives every lane all four totals, with
+// a transposed butterfly: after the xor-16 and xor-8 exchanges each lane
+// carries one of the four partial sums (value 2*bit4 + bit3 of its lane id),
+// three more xor rounds finish it, and four broadcasts hand it out.
+__device__ __forceinline__ void warp_sum4(float& a0, float& a1, float& a2, float& a3) {
+  const unsigned lane = threadIdx.x & 31u;
+  const bool h16 = lane & 16u, h8 = lane & 8u;
+  float k0 = h16 ? a2 : a0, k1 = h16 ? a3 : a1;
+  const float s0 = h16 ? a0 : a2, s1 = h16 ? a1 : a3;
+  k0 += __shfl_xor_sync(0xffffffffu, s0, 16);
+  k1 += __shfl_xor_sync(0xffffffffu, s1, 16);
+  float k = h8 ? k1 : k0;
+  k += __shfl_xor_sync(0xffffffffu, h8 ? k0 : k1, 8);
+  k += __shfl_xor_sync(0xffffffffu, k, 4);
+  k += __shfl_xor_sync(0xffffffffu, k, 2);
+  k += __shfl_xor_sync(0xffffffffu, k, 1);
+  a0 = __shfl_sync(0xffffffffu, k, 0);
+  a1 = __shfl_sync(0xffffffffu, k, 8);
+  a2 = __shfl_sync(0xffffffffu, k, 16);
+  a3 = __shfl_sync(0xffffffffu, k, 24);
+}
+
+// position = anchor (int) + offset (float)
+struct Pos {
+  int ax, ay;
+  float dx, dy;
+};
+
+__device__ __forceinline__ void rebase(Pos& t) {
+  const float fx = floorf(t.dx), fy = floorf(t.dy);
+  t.ax += (int)fx;
+  t.dx -= fx;
+  t.ay += (int)fy;
+  t.dy -= fy;
+}
+
+// (a + d) / 2^l as anchor Q + offset f in [0, 1)
+__device__ __forceinline__ void to_level1(int a, float d, int l, int& Q, float& f) {
+  const int Ql = a >> l;
+  const float frac = ((float)(a - Ql * (1 << l)) + d) * __int_as_float((127 - l) << 23);
+  const float fl = floorf(frac);
+  Q = Ql + (int)fl;
+  f = frac - fl;
+}
+
+__device__ __forceinline__ Pos split(float x, float y) {
+  Pos p;
+  const float fx = floorf(x), fy = floorf(y);
+  p.ax = (int)fx;
+  p.ay = (int)fy;
+  p.dx = x - fx;
+  p.dy = y - fy;
+  return p;
+}
+
+struct Tpl {
+  float K[2][3];   // H'^-1 J'_i for the lane's two points
+  float c0, c1, c2;  // H'^-1 sum J'_i s_i
+  float S;         // sum s_i
+};
+
+// Cholesky factor of H' with reciprocal diagonal (no divisions in solves).
+struct Chol {
+  float i00, l10, l20, i11, l21, i22;   // i.. = 1 / l..
+  __device__ __forceinline__ void solve(float b0, float b1, float b2, float& x0, float& x1,
+                                        float& x2) const {
+    const float y0 = b0 * i00;
+    const float y1 = (b1 - l10 * y0) * i11;
+    const float y2 = (b2 - l20 * y0 - l21 * y1) * i22;
+    x2 = y2 * i22;
+    x1 = (y1 - l21 * x2) * i11;
+    x0 = (y0 - l10 * x1 - l20 * x2) * i00;
+  }
+};
+
+// Sums N values over the warp with a transposed butterfly (N padded to 16):
+// the xor-16, -8, -4, -2 exchanges halve the values each lane carries, the
+// xor-1 exchange completes them (value j ends in lanes 2j and 2j+1), and N
+// broadcasts return every total to every lane.
+template <int N>
+__device__ __forceinline__ void warp_sum_t(float (&v)[N]) {
+  static_assert(N <= 16, "at most 16 values");
+  const unsigned lane = threadIdx.x & 31u;
+  float a[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) a[i] = i < N ? v[i] : 0.f;
+#pragma unroll
+  for (int half = 8, bit = 16; half >= 1; half >>= 1, bit >>= 1) {
+    const bool up = lane & (unsigned)bit;
+#pragma unroll
+    for (int i = 0; i < half; ++i) {
+      const float keep = up ? a[i + half] : a[i];
+      const float send = up ? a[i] : a[i + half];
+      a[i] = keep + __shfl_xor_sync(0xffffffffu, send, bit);
+    }
+  }
+  a[0] += __shfl_xor_sync(0xffffffffu, a[0], 1);
+  // lane L now holds value (L >> 1) read as bits 4..1 of L: value j is in lane 2j
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    // value index of lane L is its bits 4,3,2,1 in the order the rounds split
+    // them: bit4 -> 8, bit3 -> 4, bit2 -> 2, bit1 -> 1
+    v[i] = __shfl_sync(0xffffffffu, a[0], 2 * i);
+  }
+}
+
+// Template of keypoint q (level-0 anchor form) at level l of the source.
+// Returns a VIO_TRACK_* status, uniform across the warp.
+__device__ __forceinline__ int build_template(const Lv& L, const Pos& q, int l, int lane,
+                                              const LanePts& P, Tpl& T) {
+  int Qx, Qy;
+  float fx, fy;
+  to_level1(q.ax, q.dx, l, Qx, fx);
+  to_level1(q.ay, q.dy, l, Qy, fy);
+  // bilinear at c and c +- 1 needs 1 <= c < w - 2: on integers 1 <= Q + u <= w - 3;
+  // the pattern spans [-7, 7] in both axes, so the extreme points decide
+  const bool ok = Qx - 7 >= 1 && Qx + 7 <= L.w - 3 && Qy - 7 >= 1 && Qy + 7 <= L.h - 3;
+  if (!ok) return VIO_TRACK_OOB_TEMPLATE;   // same value in every lane
+
+  const float w00 = (1.f - fx) * (1.f - fy), w10 = fx * (1.f - fy);
+  const float w01 = (1.f - fx) * fy, w11 = fx * fy;
+  float Jp[2][3];
+  float acc[10];
+#pragma unroll
+  for (int i = 0; i < 10; ++i) acc[i] = 0.f;
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    const int i = lane + 32 * j;
+    Jp[j][0] = Jp[j][1] = Jp[j][2] = 0.f;
+    if (j == 0 || i < kNP) {
+      const float u = P.u[j], v = P.v[j];
+      const uint8_t* base =
+          L.p + (long long)(Qy + P.iv[j] - 1) * L.pitch + (Qx + P.iu[j] - 1);
+      float t[4][4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int cc = 0; cc < 4; ++cc)
+          t[r][cc] = (r == 0 || r == 3) && (cc == 0 || cc == 3)
+                         ? 0.f
+                         : (float)__ldg(base + (long long)r * L.pitch + cc);
+      auto bl = [&](float a, float b, float c, float d) {
+        return w00 * a + w10 * b + w01 * c + w11 * d;
+      };
+      const float s = bl(t[1][1], t[1][2], t[2][1], t[2][2]);
+      const float gx = 0.5f * (bl(t[1][2], t[1][3], t[2][2], t[2][3]) -
+                               bl(t[1][0], t[1][1], t[2][0], t[2][1]));
+      const float gy = 0.5f * (bl(t[2][1], t[2][2], t[3][1], t[3][2]) -
+                               bl(t[0][1], t[0][2], t[1][1], t[1][2]));
+      Jp[j][0] = gx;
+      Jp[j][1] = gy;
+      Jp[j][2] = gy * u - gx * v;
+      acc[0] += s;
+      acc[1] += gx * gx;
+      acc[2] += gx * gy;
+      acc[3] += gx * Jp[j][2];
+      acc[4] += gy * gy;
+      acc[5] += gy * Jp[j][2];
+      acc[6] += Jp[j][2] * Jp[j][2];
+      acc[7] += gx * s;
+      acc[8] += gy * s;
+      acc[9] += Jp[j][2] * s;
+    }
+  }
+  warp_sum_t(acc);
+  T.S = acc[0];
+  if (!(acc[0] > 0.f)) return VIO_TRACK_ZERO_MEAN;
+  // Cholesky of H'; a pivot <= 1e-9 trace marks a degenerate patch
+  const float eps = 1e-9f * (acc[1] + acc[4] + acc[6]);
+  Chol C;
+  if (!(acc[1] > eps)) return VIO_TRACK_DEGENERATE_H;
+  C.i00 = rsqrtf(acc[1]);
+  C.l10 = acc[2] * C.i00;
+  C.l20 = acc[3] * C.i00;
+  const float d1 = acc[4] - C.l10 * C.l10;
+  if (!(d1 > eps)) return VIO_TRACK_DEGENERATE_H;
+  C.i11 = rsqrtf(d1);
+  C.l21 = (acc[5] - C.l20 * C.l10) * C.i11;
+  const float d2 = acc[6] - C.l20 * C.l20 - C.l21 * C.l21;
+  if (!(d2 > eps)) return VIO_TRACK_DEGENERATE_H;
+  C.i22 = rsqrtf(d2);
+  C.solve(acc[7], acc[8], acc[9], T.c0, T.c1, T.c2);
+#pragma unroll
+  for (int j = 0; j < 2; ++j) C.solve(Jp[j][0], Jp[j][1], Jp[j][2], T.K[j][0], T.K[j][1],
+                                      T.K[j][2]);
+  return VIO_TRACK_OK;
+}
+
+// Warp state: translation (level coords, anchor form), angle and its cos/sin.
+struct Warp {
+  Pos t;
+  float th, cs, sn;
+};
+
+// cos, sin, sin(phi)/phi and (1 - cos(phi))/phi of a small angle
+__device__ __forceinline__ void small_rot(float p, float& c, float& s, float& a, float& b) {
+  if (fabsf(p) < 0.25f) {
+    const float p2 = p * p;
+    c = 1.f - p2 * (0.5f - p2 * (1.f / 24.f - p2 * (1.f / 720.f)));
+    a = 1.f - p2 * (1.f / 6.f - p2 * (1.f / 120.f - p2 * (1.f / 5040.f)));
+    s = p * a;
+    b = p * (0.5f - p2 * (1.f / 24.f - p2 * (1.f / 720.f - p2 * (1.f / 40320.f))));
+  } else {
+    sincosf(p, &s, &c);
+    a = s / p;
+    const float h = sinf(0.5f * p);
+    b = 2.f * h * h / p;
+  }
+}
+
+// One Gauss-Newton step (Eq. 4-5). Returns a VIO_TRACK_* status.
+__device__ __forceinline__ int gn_step(const Lv& L, const Tpl& T, int lane, const LanePts& P,
+                                       Warp& W) {
+  float r0 = 0.f, r1 = 0.f, r2 = 0.f, r3 = 0.f;
+  bool ok = true;
+  const unsigned xmax = (unsigned)(L.w - 2), ymax = (unsigned)(L.h - 2);
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    const int i = lane + 32 * j;
+    if (j == 0 || i < kNP) {
+      const float u = P.u[j], v = P.v[j];
+      const float vx = W.cs * u - W.sn * v + W.t.dx;
+      const float vy = W.sn * u + W.cs * v + W.t.dy;
+      const float flx = floorf(vx), fly = floorf(vy);
+      const int ix = W.t.ax + (int)flx, iy = W.t.ay + (int)fly;
+      const float fx = vx - flx, fy = vy - fly;
+      // 0 <= y < w - 1 on the integer part: 0 <= ix <= w - 2 (one unsigned test)
+      if ((unsigned)ix <= xmax && (unsigned)iy <= ymax) {
+        const uint8_t* p = L.p + (long long)iy * L.pitch + ix;
+        const float a = __ldg(p), b = __ldg(p + 1);
+        const float c = __ldg(p + L.pitch), d = __ldg(p + L.pitch + 1);
+        const float top = a + fx * (b - a), bot = c + fx * (d - c);
+        const float r = top + fy * (bot - top);
+        r0 += r;
+        r1 += T.K[j][0] * r;
+        r2 += T.K[j][1] * r;
+        r3 += T.K[j][2] * r;
+      } else {
+        ok = false;
+      }
+    }
+  }
+  if (!__all_sync(0xffffffffu, ok)) return VIO_TRACK_OOB_WARP;
+  warp_sum4(r0, r1, r2, r3);
+  if (!(r0 > 0.f)) return VIO_TRACK_ZERO_MEAN;
+  const float q = __fdividef(T.S, r0);
+  const float d0 = T.c0 - q * r1;
+  const float d1 = T.c1 - q * r2;
+  const float d2 = T.c2 - q * r3;
+  // a NaN or an infinity in any component fails the (finite) comparison
+  if (!(fabsf(d0) + fabsf(d1) + fabsf(d2) < 3.0e38f)) return VIO_TRACK_NAN;
+  // T <- T o exp(delta): t += R V(d2) (d0, d1), R <- R R(d2)
+  float cd, sd, a, b;
+  small_rot(d2, cd, sd, a, b);
+  const float vx = a * d0 - b * d1, vy = b * d0 + a * d1;
+  W.t.dx += W.cs * vx - W.sn * vy;
+  W.t.dy += W.sn * vx + W.cs * vy;
+  const float cs = W.cs * cd - W.sn * sd;
+  const float sn = W.sn * cd + W.cs * sd;
+  W.cs = cs;
+  W.sn = sn;
+  W.th += d2;
+  return VIO_TRACK_OK;
+}
+
+__device__ __forceinline__ Lv get_lv(const Geom& g, const Batch& b, int img, int l) {
+  return Lv{level_ptr(g, b, img, l), g.w[l], g.h[l], g.pitch[l]};
+}
+
+// Coarse-to-fine tracking of keypoint p (anchor form) of image src_img of the
+// source batch into image dst_img of the target batch, from warp (t0, th0) at
+// level 0. A level whose template is invalid is skipped, except level 0; any
+// warp failure ends the track.
+__device__ __forceinline__ int track_dir(const Geom& g, const Batch& src, int src_img,
+                                         const Batch& dst, int dst_img, const Pos& p, Pos t0,
+                                         float th0, int iters, int lane, Pos& t_out,
+                                         float& th_out) {
+  const int L = g.n_levels;
+  Warp W;
+  to_level1(t0.ax, t0.dx, L - 1, W.t.ax, W.t.dx);
+  to_level1(t0.ay, t0.dy, L - 1, W.t.ay, W.t.dy);
+  W.th = th0;
+  {
+    float a, b;
+    small_rot(th0, W.cs, W.sn, a, b);
+  }
+  const LanePts P = lane_points(lane);
+  Tpl T;
+  for (int l = L - 1; l >= 0; --l) {
+    const int ts = build_template(get_lv(g, src, src_img, l), p, l, lane, P, T);
+    if (ts != VIO_TRACK_OK) {
+      if (l == 0) return ts;
+    } else {
+      const Lv D = get_lv(g, dst, dst_img, l);
+      for (int it = 0; it < iters; ++it) {
+        const int st = gn_step(D, T, lane, P, W);
+        if (st != VIO_TRACK_OK) return st;
+      }
+      rebase(W.t);
+    }
+    if (l > 0) {
+      W.t.ax *= 2;
+      W.t.ay *= 2;
+      W.t.dx *= 2.f;
+      W.t.dy *= 2.f;
+      rebase(W.t);
+    }
+  }
+  t_out = W.t;
+  th_out = W.th;
+  return VIO_TRACK_OK;
+}
+
+// Forward track with the optional backward pass and distance check.
+// Returns the status; tf/thf hold the forward result when it exists.
+__device__ __forceinline__ int track_fb(const Geom& g, const Batch& src, int src_img,
+                                        const Batch& dst, int dst_img, float px, float py,
+                                        const float* init3, const TrackCfg& cfg, int lane,
+                                        Pos& tf, float& thf, bool& have, float& dist) {
+  const Pos p = split(px, py);
+  Pos t0 = p;
+  float th0 = 0.f;
+  if (init3) {
+    t0 = split(init3[0], init3[1]);
+    th0 = init3[2];
+  }
+  int st = track_dir(g, src, src_img, dst, dst_img, p, t0, th0, cfg.gn_iters, lane, tf, thf);
+  have = st == VIO_TRACK_OK;
+  dist = __int_as_float(0x7fc00000);
+  if (st == VIO_TRACK_OK && cfg.fb) {
+    // backward: template on the target at the forward result, unrotated;
+    // start at the forward estimate's inverse (t = p, theta = -theta_f)
+    Pos tb;
+    float thb;
+    st = track_dir(g, dst, dst_img, src, src_img, tf, p, -thf, cfg.gn_iters, lane, tb, thb);
+    if (st == VIO_TRACK_OK) {
+      const float ex = (float)(tb.ax - p.ax) + (tb.dx - p.dx);
+      const float ey = (float)(tb.ay - p.ay) + (tb.dy - p.dy);
+      dist = sqrtf(ex * ex + ey * ey);
+      if (dist > cfg.fb_max_dist) st = VIO_TRACK_FB_FAIL;
+    }
+  }
+  return st;
+}
+
+}  // namespace trk
+}  // namespace vio

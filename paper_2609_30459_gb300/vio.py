@@ -102,14 +102,18 @@ _SIGS = {
     "vio_frontend_set_timing": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32]),
     "vio_frontend_read_timing": (ctypes.c_int32, [ctypes.c_void_p,
                                                   ctypes.POINTER(ctypes.c_double),
-                                                  ctypes.POINTER(ctypes.c_int64)]),
+                                                  ctypes.POINTER(ctypes.c_int64),
+                                                  ctypes.c_void_p, ctypes.c_int64]),
+    "vio_frontend_run": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                          ctypes.c_int64, ctypes.c_int64, ctypes.c_int32,
+                                          ctypes.c_void_p]),
     "vio_frontend_read_stats": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p,
                                                  ctypes.POINTER(ctypes.c_int64)]),
 }
 
-STAGES = ("pyramid", "track", "compact", "detect", "stereo", "append")
+STAGES = ("front", "pyramid_upper", "track", "finalize")
 STATS_RING = 4096
-STAT_NAMES = ("trk0", "trk1", "ok0", "ok1", "new", "matched")
+STAT_NAMES = ("trk0", "trk1", "ok0", "ok1", "new", "matched", "cand")
 
 
 def lib_path() -> str:
@@ -347,12 +351,29 @@ class Frontend:
     def set_timing(self, enable: bool):
         _check(load().vio_frontend_set_timing(self.handle, 1 if enable else 0), "set_timing")
 
-    def read_timing(self) -> tuple[dict, int]:
-        """Summed per-stage milliseconds of the steps timed since the last read."""
+    def read_timing(self, max_steps: int = 0):
+        """(summed per-stage ms, number of timed steps, per-step ms list) of the
+        steps timed since the last read."""
+        import numpy as np
         ms = (ctypes.c_double * len(STAGES))()
         n = ctypes.c_int64()
-        _check(load().vio_frontend_read_timing(self.handle, ms, ctypes.byref(n)), "read_timing")
-        return {k: ms[i] for i, k in enumerate(STAGES)}, int(n.value)
+        steps = np.zeros(max(max_steps, 1), np.float32)
+        _check(load().vio_frontend_read_timing(self.handle, ms, ctypes.byref(n),
+                                               steps.ctypes.data_as(ctypes.c_void_p),
+                                               max_steps), "read_timing")
+        k = min(int(n.value), max_steps)
+        return {s: ms[i] for i, s in enumerate(STAGES)}, int(n.value), steps[:k].tolist()
+
+    def run(self, frames: torch.Tensor, stream=None):
+        """Every frame of frames (n_steps, n_streams, 2, h, pitch), one step each,
+        enqueued by one call."""
+        if frames.dtype != torch.uint8 or frames.dim() != 5 or not frames.is_contiguous():
+            raise ValueError("frames must be a contiguous uint8 tensor "
+                             "(steps, streams, 2, h, pitch)")
+        pitch = frames.shape[-1]
+        fs = frames.shape[3] * pitch
+        _check(load().vio_frontend_run(self.handle, _ptr(frames), pitch, fs, frames[0].numel(),
+                                       frames.shape[0], _stream(stream)), "vio_frontend_run")
 
     def read_stats(self):
         """(ring array (STATS_RING, n_streams, 6) int32, steps run since create)."""

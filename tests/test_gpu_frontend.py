@@ -124,3 +124,27 @@ def test_frontend_reset_and_two_streams():
     fe.reset()
     torch.cuda.synchronize()
     assert (fe.view()["track_count"] == 0).all()
+
+
+def test_frontend_run_equals_steps():
+    w, h, L = 376, 240, 3
+    seq = synth.make_sequence(5003, 6, w, h, 1, max_motion=5.0, tex_size=1024)
+    p = vio.default_params(n_levels=L, cell_w=47, cell_h=40)
+    cap = 2 * (w // 47) * (h // 40)
+    frames = torch.from_numpy(seq.frames).cuda().view(6, 1, 2, h, w)
+    a, b = vio.Frontend(p, w, h, 1, cap), vio.Frontend(p, w, h, 1, cap)
+    for t in range(6):
+        a.step(frames[t])
+    b.set_timing(True)
+    b.run(frames)
+    torch.cuda.synchronize()
+    stage_ms, n, per_step = b.read_timing(max_steps=6)
+    assert n == 6 and len(per_step) == 6 and all(x > 0 for x in per_step)
+    va, vb = a.view(), b.view()
+    assert torch.equal(va["track_count"], vb["track_count"])
+    n0, n1 = va["track_count"][0].tolist()
+    for c, nc in ((0, n0), (1, n1)):
+        assert torch.equal(va["track_xy"][0, c, :nc], vb["track_xy"][0, c, :nc])
+        assert torch.equal(va["track_id"][0, c, :nc], vb["track_id"][0, c, :nc])
+    stats, steps = b.read_stats()
+    assert steps == 6 and stats[5, 0, 4] == int(vb["new_count"][0])
