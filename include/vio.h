@@ -116,7 +116,9 @@ typedef struct vio_ctx vio_ctx;
 
 /* Allocates the scratch the calls below need for images up to max_w x
  * max_h and batches up to max_images. The only allocating calls are
- * vio_ctx_create and vio_frontend_create. */
+ * vio_ctx_create and vio_frontend_create. Cells whose per-block shared
+ * memory would exceed 200 KiB (about 125 x 125 px) return
+ * VIO_ERR_UNSUPPORTED. */
 vio_status vio_ctx_create(vio_ctx** ctx, const vio_params* p, int32_t max_w, int32_t max_h,
                           int32_t max_images);
 vio_status vio_ctx_destroy(vio_ctx* ctx);
@@ -159,6 +161,17 @@ vio_status vio_detect_grid(vio_ctx* ctx, const vio_pyr_layout* layout,
                            const vio_pyr_batch* batch, const uint8_t* d_occupancy,
                            const uint8_t* d_mask, int64_t mask_stride, float* d_kp,
                            int16_t* d_score, int32_t* d_count, int32_t capacity, void* stream);
+
+/* Sec. III-C and III-D fused: vio_pyramid_build and vio_detect_grid of the
+ * same batch in one pass over level 0 (one launch computes pyramid levels
+ * 1-4 and every cell's candidates; images with more than 5 levels take one
+ * more launch for the rest; one launch applies the occupancy and writes the
+ * keypoints). Arguments and results as the two calls. The pyramid needs
+ * n_levels == the context's n_levels. */
+vio_status vio_pyramid_detect(vio_ctx* ctx, const vio_pyr_layout* layout,
+                              const vio_pyr_batch* batch, const uint8_t* d_occupancy,
+                              const uint8_t* d_mask, int64_t mask_stride, float* d_kp,
+                              int16_t* d_score, int32_t* d_count, int32_t capacity, void* stream);
 
 /* Detection without any device allocation. The paper has no counterpart:
  * this is a convenience for callers that cannot call cudaMalloc -- code

@@ -4,6 +4,9 @@
 #include <new>
 
 #include "common.cuh"
+#include "detect_dev.cuh"
+#include "frame.cuh"
+#include "pyramid_dev.cuh"
 
 namespace {
 
@@ -111,6 +114,8 @@ extern "C" vio_status vio_ctx_create(vio_ctx** out, const vio_params* p, int32_t
                                      int32_t max_h, int32_t max_images) {
   if (!out || !params_ok(p) || max_w < 1 || max_h < 1 || max_images < 1)
     return VIO_ERR_INVALID_ARG;
+  if (vio::det::cell_smem_bytes(p->cell_w, p->cell_h) > vio::det::kMaxCellSmem)
+    return VIO_ERR_UNSUPPORTED;
   *out = nullptr;
   vio_ctx* c = new (std::nothrow) vio_ctx();
   if (!c) return VIO_ERR_OOM;
@@ -175,6 +180,37 @@ extern "C" vio_status vio_detect_grid(vio_ctx* ctx, const vio_pyr_layout* layout
                                         vio::make_batch(*batch), d_occupancy, d_mask,
                                         mask_stride, ctx->d_cand, ctx->d_cand_count, d_kp,
                                         d_score, d_count, capacity, (cudaStream_t)stream));
+}
+
+extern "C" vio_status vio_pyramid_detect(vio_ctx* ctx, const vio_pyr_layout* layout,
+                                         const vio_pyr_batch* batch, const uint8_t* d_occupancy,
+                                         const uint8_t* d_mask, int64_t mask_stride,
+                                         float* d_kp, int16_t* d_score, int32_t* d_count,
+                                         int32_t capacity, void* stream) {
+  if (!ctx || !layout_ok(layout) || !batch_ok(layout, batch) || !d_kp || !d_score ||
+      !d_count || capacity < 0)
+    return VIO_ERR_INVALID_ARG;
+  if (layout->n_levels != ctx->p.n_levels) return VIO_ERR_INVALID_ARG;
+  if (d_mask && batch->n_images > 1 && mask_stride < (int64_t)layout->w[0] * layout->h[0])
+    return VIO_ERR_INVALID_ARG;
+  if (layout->w[0] > ctx->max_w || layout->h[0] > ctx->max_h ||
+      batch->n_images > ctx->max_images)
+    return VIO_ERR_INVALID_ARG;
+  if (batch->n_images > 65535) return VIO_ERR_UNSUPPORTED;
+  const vio::Geom g = vio::make_geom(*layout);
+  const vio::Batch b = vio::make_batch(*batch);
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = vio::launch_front(ctx->p, g, b, 1, d_mask, mask_stride, ctx->d_cand,
+                                    ctx->d_cand_count, s);
+  if (e == cudaSuccess && layout->n_levels > 1 + vio::pyr::kMaxPass)
+    e = vio::launch_pyramid_from(g, b, vio::pyr::kMaxPass, ctx->p.round_mode, s);
+  if (e == cudaSuccess) {
+    const int n_cells = (layout->w[0] / ctx->p.cell_w) * (layout->h[0] / ctx->p.cell_h);
+    e = vio::launch_select(ctx->d_cand, ctx->d_cand_count, d_occupancy, n_cells,
+                           ctx->p.k_per_cell, layout->w[0], d_kp, d_score, d_count, capacity,
+                           batch->n_images, s);
+  }
+  return cuda_status(e);
 }
 
 extern "C" vio_status vio_track_patches(vio_ctx* ctx, const vio_pyr_layout* layout,

@@ -94,6 +94,10 @@ cudaError_t launch_detect(const vio_params& p, const Geom& g, const Batch& b,
                           const uint8_t* occ, const uint8_t* mask, long long mask_stride,
                           unsigned long long* cand, int32_t* cand_count, float* kp,
                           int16_t* score, int32_t* count, int capacity, cudaStream_t s);
+cudaError_t launch_select(const unsigned long long* cand, const int32_t* cand_count,
+                          const uint8_t* occ, int n_cells, int k, int w, float* kp,
+                          int16_t* score, int32_t* count, int capacity, int n_images,
+                          cudaStream_t s);
 cudaError_t launch_track(const Geom& g, const Batch& src, const Batch& dst, const float* pts,
                          const float* init, const int32_t* count, int capacity,
                          const TrackCfg& cfg, float* out3, float* out2, uint8_t* status,

@@ -141,8 +141,16 @@ cudaError_t launch_detect(const vio_params& p, const Geom& g, const Batch& b,
     dim3 grid(n_cells, b.n);
     detect_cells_kernel<<<grid, det::kThreads, smem, s>>>(a);
   }
-  select_kernel<<<b.n, SEL_THREADS, 0, s>>>(cand, cand_count, occ, n_cells, a.cg.k, g.w[0], kp,
-                                            score, count, capacity);
+  return launch_select(cand, cand_count, occ, n_cells, a.cg.k, g.w[0], kp, score, count,
+                       capacity, b.n, s);
+}
+
+cudaError_t launch_select(const unsigned long long* cand, const int32_t* cand_count,
+                          const uint8_t* occ, int n_cells, int k, int w, float* kp,
+                          int16_t* score, int32_t* count, int capacity, int n_images,
+                          cudaStream_t s) {
+  select_kernel<<<n_images, SEL_THREADS, 0, s>>>(cand, cand_count, occ, n_cells, k, w, kp, score,
+                                                 count, capacity);
   return cudaGetLastError();
 }
 

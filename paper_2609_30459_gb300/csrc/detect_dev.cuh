@@ -92,84 +92,190 @@ struct CellGeom {
   int cw, ch, gx, k, tmin, border;
 };
 
-__host__ __device__ inline int cell_smem_bytes(int cw, int ch) {
-  const int rs = pyr::up16(cw + 2 * kHalo + 16);
-  return rs * (ch + 2 * kHalo) + (cw + 2) * (ch + 2);
+// Shared memory of one cell: staged image, bound map, value map, queue of
+// evaluated pixels (u16) and candidate keys (u64), 16-byte aligned pieces.
+struct CellSmem {
+  int rs;                      // staged row stride
+  int stage, ubm, val, queue, keys, total;
+};
+__host__ __device__ inline CellSmem cell_smem(int cw, int ch) {
+  CellSmem S;
+  const int mw = cw + 2, mh = ch + 2, n = mw * mh;
+  S.rs = pyr::up16(cw + 2 * kHalo + 16);
+  S.stage = 0;
+  S.ubm = pyr::up16(S.rs * (ch + 2 * kHalo));
+  S.val = S.ubm + pyr::up16(n);
+  S.queue = S.val + pyr::up16(n);
+  S.keys = S.queue + pyr::up16(2 * n);
+  // strict 3x3 maxima never touch: at most one per 2x2 block of the cell
+  S.total = S.keys + 8 * (((cw + 1) / 2) * ((ch + 1) / 2));
+  return S;
+}
+constexpr int kMaxCellSmem = 200 * 1024;
+__host__ __device__ inline int cell_smem_bytes(int cw, int ch) { return cell_smem(cw, ch).total; }
+
+__device__ __forceinline__ unsigned block_max_u32(unsigned v, unsigned* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  v = lane < (kThreads / 32) ? red[lane] : 0u;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
 }
 
 // Detection in one cell of one image (blockDim.x == kThreads). Writes up to k
 // packed keys (best first) and the count.
+//
+// Exact branch-and-bound. A 9-arc holds one pixel of each opposite pair
+// (0,8) and (4,12) (the paper's early rejection), so with m = score + 1,
+//   m <= ub = max(min(max(v0,v8), max(v4,v12)) - c, c - max(min(v0,v8), min(v4,v12))).
+// Every pixel gets this bound (0 where it cannot reach T_min). Exact scores
+// are computed only for pixels whose bound reaches a threshold t, lowered in
+// steps until at least k candidates with m >= t are known (or t reaches
+// T_min + 1). After pixels with ub >= t are evaluated, every pixel with
+// m >= t has its 3x3 maximum test decided: a neighbour either is evaluated
+// (exact comparison) or has ub < t <= m. So the candidates with m >= t are
+// exactly known, and if there are k of them, no other pixel can enter the
+// top k. The value map holds the exact m where evaluated and ub elsewhere, so
+// the maximum test is "m > value of all 8 neighbours" in both cases.
 __device__ __forceinline__ void detect_cell(const uint8_t* __restrict__ src, int W, int H, int P,
                                             const CellGeom& cg, int cell,
                                             const uint8_t* __restrict__ mask,
                                             unsigned long long* __restrict__ out_keys,
                                             int32_t* __restrict__ out_count, uint8_t* smem,
-                                            unsigned long long* red) {
+                                            unsigned long long* red64) {
+  __shared__ int q_count, c_count;
+  unsigned* red = reinterpret_cast<unsigned*>(red64);
   const int cy = cell / cg.gx, cx = cell - cy * cg.gx;
   const int x0 = cx * cg.cw, y0 = cy * cg.ch;
   const int rx0 = x0 - kHalo, ry0 = y0 - kHalo;
   const int xa = rx0 & ~15;
-  const int RS = pyr::up16(cg.cw + 2 * kHalo + 16);
-  const int MW = cg.cw + 2, MH = cg.ch + 2;
-  uint8_t* reg = smem;
-  uint8_t* msc = smem + RS * (cg.ch + 2 * kHalo);
+  const CellSmem S = cell_smem(cg.cw, cg.ch);
+  const int RS = S.rs;
+  const int MW = cg.cw + 2, MH = cg.ch + 2, NR = MW * MH;
+  uint8_t* reg = smem + S.stage;
+  uint8_t* ubm = smem + S.ubm;      // bound of m (immutable)
+  uint8_t* val = smem + S.val;      // exact m where evaluated, else the bound
+  uint16_t* queue = reinterpret_cast<uint16_t*>(smem + S.queue);
+  unsigned long long* keys = reinterpret_cast<unsigned long long*>(smem + S.keys);
   pyr::stage_rect(src, W, H, P, rx0, x0 + cg.cw + kHalo, ry0, y0 + cg.ch + kHalo, reg, RS);
+  if (threadIdx.x == 0) {
+    q_count = 0;
+    c_count = 0;
+  }
   __syncthreads();
 
   const int T = cg.tmin;
+  const int b = cg.border;
   const Split sm(MW);
-  for (int i = threadIdx.x; i < MW * MH; i += kThreads) {
+  // pass A: bounds, and the largest bound of the cell's eligible pixels
+  unsigned umax = 0;
+  for (int i = threadIdx.x; i < NR; i += kThreads) {
     int r, c;
     sm(i, r, c);
     const int x = x0 - 1 + c, y = y0 - 1 + r;
-    int m = 0;
+    int u = 0;
     if (x >= 3 && x <= W - 4 && y >= 3 && y <= H - 4) {
       const uint8_t* q = reg + (y - ry0) * RS + (x - xa);
       const int ctr = q[0];
-      int v[16];
-#pragma unroll
-      for (int k = 0; k < 16; ++k) v[k] = q[ring_dy(k) * RS + ring_dx(k)];
-      const int hi = ctr + T, lo = ctr - T;
-      const bool bright = (v[0] > hi || v[8] > hi) && (v[4] > hi || v[12] > hi);
-      const bool dark = (v[0] < lo || v[8] < lo) && (v[4] < lo || v[12] < lo);
-      if (bright || dark) {
-        m = fast_m(v, ctr);
-        if (m - 1 < T) m = 0;
+      const int v0 = q[-3 * RS], v8 = q[3 * RS], v4 = q[3], v12 = q[-3];
+      const int hi = min(max(v0, v8), max(v4, v12));
+      const int lo = max(min(v0, v8), min(v4, v12));
+      u = max(hi - ctr, ctr - lo);          // >= m
+      if (u - 1 < T) u = 0;                  // cannot reach T_min
+    }
+    ubm[i] = (uint8_t)u;
+    val[i] = (uint8_t)u;
+    const bool in_cell = r >= 1 && r <= cg.ch && c >= 1 && c <= cg.cw && x >= b &&
+                         x <= W - 1 - b && y >= b && y <= H - 1 - b &&
+                         (!mask || mask[(long long)y * W + x] != 0);
+    if (in_cell) umax = max(umax, (unsigned)u);
+  }
+  umax = block_max_u32(umax, red);
+  int n_found = 0;
+  if (umax > 0) {
+    const int tmin1 = T + 1;   // smallest m of a candidate
+    int t_prev = 256;
+    int t = max((int)umax - 24, tmin1);
+    int q_done = 0;            // queue entries evaluated in earlier rounds
+    for (;;) {
+      // pass B: queue the pixels whose bound falls in [t, t_prev)
+      for (int base = 0; base < NR; base += kThreads) {
+        const int i = base + threadIdx.x;
+        const bool take = i < NR && ubm[i] >= t && ubm[i] < t_prev;
+        const unsigned ball = __ballot_sync(0xffffffffu, take);
+        if (ball) {
+          const int lane = threadIdx.x & 31;
+          int slot = 0;
+          if (lane == __ffs(ball) - 1) slot = atomicAdd(&q_count, __popc(ball));
+          slot = __shfl_sync(0xffffffffu, slot, __ffs(ball) - 1);
+          if (take) queue[slot + __popc(ball & ((1u << lane) - 1))] = (uint16_t)i;
+        }
       }
+      __syncthreads();
+      const int q_end = q_count;
+      // exact scores of the newly queued pixels
+      for (int e = q_done + threadIdx.x; e < q_end; e += kThreads) {
+        const int i = queue[e];
+        int r, c;
+        sm(i, r, c);
+        const int x = x0 - 1 + c, y = y0 - 1 + r;
+        const uint8_t* q = reg + (y - ry0) * RS + (x - xa);
+        int v[16];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) v[k] = q[ring_dy(k) * RS + ring_dx(k)];
+        int m = fast_m(v, q[0]);
+        if (m - 1 < T) m = 0;
+        val[i] = (uint8_t)m;
+      }
+      __syncthreads();
+      // pass C: candidates with m in [t, t_prev) among everything evaluated
+      for (int e = threadIdx.x; e < q_end; e += kThreads) {
+        const int i = queue[e];
+        const int m = val[i];
+        if (m < t || m >= t_prev) continue;
+        int r, c;
+        sm(i, r, c);
+        if (r < 1 || r > cg.ch || c < 1 || c > cg.cw) continue;
+        const int x = x0 - 1 + c, y = y0 - 1 + r;
+        if (x < b || x > W - 1 - b || y < b || y > H - 1 - b) continue;
+        const uint8_t* q = val + i;
+        const bool peak = m > q[-MW - 1] && m > q[-MW] && m > q[-MW + 1] && m > q[-1] &&
+                          m > q[1] && m > q[MW - 1] && m > q[MW] && m > q[MW + 1];
+        if (!peak) continue;
+        if (mask && mask[(long long)y * W + x] == 0) continue;
+        const int slot = atomicAdd(&c_count, 1);
+        keys[slot] = ((unsigned long long)(m - 1) << 32) | (unsigned)(~(unsigned)(y * W + x));
+      }
+      __syncthreads();
+      const int found = c_count;
+      if (found >= cg.k || t <= tmin1) break;
+      q_done = q_end;
+      t_prev = t;
+      t = max(t - 24, tmin1);
+      __syncthreads();
     }
-    msc[i] = (uint8_t)m;
-  }
-  __syncthreads();
-
-  const int b = cg.border;
-  unsigned long long last = ~0ull;
-  int n = 0;
-  const Split sc(cg.cw);
-  for (int round = 0; round < cg.k; ++round) {
-    unsigned long long best = 0;
-    for (int i = threadIdx.x; i < cg.cw * cg.ch; i += kThreads) {
-      int r, c;
-      sc(i, r, c);
-      const int x = x0 + c, y = y0 + r;
-      const uint8_t* q = msc + (r + 1) * MW + (c + 1);
-      const int m = q[0];
-      if (m == 0) continue;
-      if (x < b || x > W - 1 - b || y < b || y > H - 1 - b) continue;
-      const bool peak = m > q[-MW - 1] && m > q[-MW] && m > q[-MW + 1] && m > q[-1] &&
-                        m > q[1] && m > q[MW - 1] && m > q[MW] && m > q[MW + 1];
-      if (!peak) continue;
-      if (mask && mask[(long long)y * W + x] == 0) continue;
-      const unsigned long long key =
-          ((unsigned long long)(m - 1) << 32) | (unsigned)(~(unsigned)(y * W + x));
-      if (key < last && key > best) best = key;
+    // top k of the candidate keys: k rounds of a block maximum
+    const int nk = c_count;
+    unsigned long long last = ~0ull;
+    for (int round = 0; round < cg.k; ++round) {
+      unsigned long long best = 0;
+      for (int e = threadIdx.x; e < nk; e += kThreads) {
+        const unsigned long long key = keys[e];
+        if (key < last && key > best) best = key;
+      }
+      best = block_max_u64(best, red64);
+      if (best == 0) break;
+      if (threadIdx.x == 0) out_keys[round] = best;
+      last = best;
+      ++n_found;
     }
-    best = block_max_u64(best, red);
-    if (best == 0) break;
-    if (threadIdx.x == 0) out_keys[round] = best;
-    last = best;
-    ++n;
   }
-  if (threadIdx.x == 0) *out_count = n;
+  if (threadIdx.x == 0) *out_count = n_found;
 }
 
 }  // namespace det

@@ -33,34 +33,45 @@ static_assert(K1_THREADS == pyr::kThreads && K1_THREADS == det::kThreads, "block
 
 struct K1Args {
   Geom g;
-  Batch all;           // every image of the frame (2 per stream)
+  Batch all;           // every image of the batch
   int m;               // levels of the first pass (1..4; 0 = no pyramid)
   int ntx, nty;        // tiles of the first pass
-  int n_pyr_blocks;
+  int det_step;        // detection on every det_step-th image (1 or 2)
+  int blocks_per_unit; // det_step * tiles + cells
   det::CellGeom cg;
   int n_cells;
+  const uint8_t* mask; // per detected image, or null
+  long long mask_stride;
   unsigned long long* cand;
   int32_t* cand_count;
   int round_mode;
 };
 
+// Block layout: units of det_step images, each unit = the pyramid tiles of
+// its images followed by the detection cells of its first image, so that the
+// blocks reading one image run together and its level 0 is read from DRAM
+// about once.
 __global__ void __launch_bounds__(K1_THREADS) frame_front_kernel(K1Args a) {
   extern __shared__ __align__(16) uint8_t smem[];
   __shared__ unsigned long long red[K1_THREADS / 32];
-  if ((int)blockIdx.x < a.n_pyr_blocks) {
-    const int tiles = a.ntx * a.nty;
-    const int img = blockIdx.x / tiles;
-    const int t = blockIdx.x - img * tiles;
+  const int unit = blockIdx.x / a.blocks_per_unit;
+  const int rem = blockIdx.x - unit * a.blocks_per_unit;
+  const int tiles = a.ntx * a.nty;
+  const int n_pyr = a.m > 0 ? a.det_step * tiles : 0;
+  if (rem < n_pyr) {
+    const int img = unit * a.det_step + rem / tiles;
+    const int t = rem % tiles;
     const int ty = t / a.ntx, tx = t - ty * a.ntx;
-    pyr::pyramid_pass(a.g, a.all, img, 0, a.m, tx, ty, a.ntx, a.nty, a.round_mode, smem);
+    if (img < a.all.n)
+      pyr::pyramid_pass(a.g, a.all, img, 0, a.m, tx, ty, a.ntx, a.nty, a.round_mode, smem);
     return;
   }
-  const int d = blockIdx.x - a.n_pyr_blocks;
-  const int stream = d / a.n_cells;
-  const int cell = d - stream * a.n_cells;
-  const long long slot = (long long)stream * a.n_cells + cell;
-  det::detect_cell(level_ptr(a.g, a.all, 2 * stream, 0), a.g.w[0], a.g.h[0], a.g.pitch[0], a.cg,
-                   cell, nullptr, a.cand + slot * a.cg.k, a.cand_count + slot, smem, red);
+  const int cell = rem - n_pyr;
+  const int img = unit * a.det_step;
+  const long long slot = (long long)unit * a.n_cells + cell;
+  det::detect_cell(level_ptr(a.g, a.all, img, 0), a.g.w[0], a.g.h[0], a.g.pitch[0], a.cg, cell,
+                   a.mask ? a.mask + (long long)unit * a.mask_stride : nullptr,
+                   a.cand + slot * a.cg.k, a.cand_count + slot, smem, red);
 }
 
 struct K2Args {
@@ -333,6 +344,38 @@ __global__ void __launch_bounds__(K3_THREADS) frame_finalize_kernel(K3Args a) {
 
 }  // namespace
 
+cudaError_t launch_front(const vio_params& p, const Geom& g, const Batch& all, int det_step,
+                         const uint8_t* mask, long long mask_stride, unsigned long long* cand,
+                         int32_t* cand_count, cudaStream_t s) {
+  const int gx = g.w[0] / p.cell_w, gy = g.h[0] / p.cell_h;
+  K1Args a1{};
+  a1.g = g;
+  a1.all = all;
+  a1.m = g.n_levels > 1 ? pyr::pass_levels(g.n_levels, 0) : 0;
+  a1.ntx = a1.nty = 1;
+  if (a1.m > 0) pyr::pass_tiles(g.w, g.h, 0, a1.m, a1.ntx, a1.nty);
+  a1.det_step = det_step;
+  a1.n_cells = gx * gy;
+  a1.blocks_per_unit = (a1.m > 0 ? det_step * a1.ntx * a1.nty : 0) + a1.n_cells;
+  a1.cg = det::CellGeom{p.cell_w, p.cell_h, gx, p.k_per_cell, p.thresholds[p.n_thresholds - 1],
+                        p.detect_border};
+  a1.mask = mask;
+  a1.mask_stride = mask_stride;
+  a1.cand = cand;
+  a1.cand_count = cand_count;
+  a1.round_mode = p.round_mode;
+  const int smem = frame_front_smem(g, p);
+  if (smem > 48 * 1024) {
+    const cudaError_t e = cudaFuncSetAttribute(
+        frame_front_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+  }
+  const long long units = (all.n + det_step - 1) / det_step;
+  const long long blocks = units * a1.blocks_per_unit;
+  if (blocks > 0) frame_front_kernel<<<(unsigned)blocks, K1_THREADS, smem, s>>>(a1);
+  return cudaGetLastError();
+}
+
 int frame_front_smem(const Geom& g, const vio_params& p) {
   int smem = det::cell_smem_bytes(p.cell_w, p.cell_h);
   if (g.n_levels > 1) {
@@ -353,33 +396,10 @@ cudaError_t launch_frame(const FrameLaunch& f, cudaStream_t s, cudaEvent_t* mark
     if (marks) cudaEventRecord(marks[i], s);
   };
 
-  // K1: pyramid levels 1-2 + detection candidates (camera 0 of each stream)
+  // K1: pyramid levels 1-4 + detection candidates (camera 0 of each stream)
   mark(0);
-  K1Args a1{};
-  a1.g = g;
-  a1.all = f.cur;
-  a1.m = g.n_levels > 1 ? pyr::pass_levels(g.n_levels, 0) : 0;
-  a1.ntx = a1.nty = 0;
-  a1.n_pyr_blocks = 0;
-  if (a1.m > 0) {
-    pyr::pass_tiles(g.w, g.h, 0, a1.m, a1.ntx, a1.nty);
-    a1.n_pyr_blocks = a1.ntx * a1.nty * f.cur.n;
-  }
-  a1.cg = det::CellGeom{f.p.cell_w, f.p.cell_h, gx, k, f.p.thresholds[f.p.n_thresholds - 1],
-                        f.p.detect_border};
-  a1.n_cells = n_cells;
-  a1.cand = f.cand;
-  a1.cand_count = f.cand_count;
-  a1.round_mode = f.p.round_mode;
-  const int smem1 = frame_front_smem(g, f.p);
-  cudaError_t e;
-  if (smem1 > 48 * 1024) {
-    e = cudaFuncSetAttribute(frame_front_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             smem1);
-    if (e != cudaSuccess) return e;
-  }
-  const long long blocks1 = (long long)a1.n_pyr_blocks + (long long)ns * n_cells;
-  if (blocks1 > 0) frame_front_kernel<<<(unsigned)blocks1, K1_THREADS, smem1, s>>>(a1);
+  cudaError_t e = launch_front(f.p, g, f.cur, 2, nullptr, 0, f.cand, f.cand_count, s);
+  if (e != cudaSuccess) return e;
   // deeper pyramid levels
   mark(1);
   if (g.n_levels > 1 + pyr::kMaxPass) {

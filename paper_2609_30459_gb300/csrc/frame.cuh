@@ -33,6 +33,11 @@ struct FrameLaunch {
 // boundaries (or null).
 cudaError_t launch_frame(const FrameLaunch& f, cudaStream_t s, cudaEvent_t* marks);
 int frame_launches(const Geom& g);
+// Fused pyramid (levels 1-4) and per-cell detection candidates of every
+// det_step-th image of `all`, one launch.
+cudaError_t launch_front(const vio_params& p, const Geom& g, const Batch& all, int det_step,
+                         const uint8_t* mask, long long mask_stride, unsigned long long* cand,
+                         int32_t* cand_count, cudaStream_t s);
 int frame_front_smem(const Geom& g, const vio_params& p);
 
 }  // namespace vio

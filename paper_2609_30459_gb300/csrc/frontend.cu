@@ -13,6 +13,7 @@
 #include <new>
 #include <vector>
 
+#include "detect_dev.cuh"
 #include "frame.cuh"
 
 struct vio_frontend {
@@ -94,6 +95,8 @@ extern "C" vio_status vio_frontend_create(vio_frontend** out, const vio_params* 
   const long long n_cells = (long long)gx * gy;
   if (n_cells * p->k_per_cell > capacity) return VIO_ERR_INVALID_ARG;
   if (n_cells * 4 > 200 * 1024) return VIO_ERR_UNSUPPORTED;   // finalize's shared counters
+  if (vio::det::cell_smem_bytes(p->cell_w, p->cell_h) > vio::det::kMaxCellSmem)
+    return VIO_ERR_UNSUPPORTED;
   vio_frontend* fe = new (std::nothrow) vio_frontend();
   if (!fe) return VIO_ERR_OOM;
   fe->p = *p;

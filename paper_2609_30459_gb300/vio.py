@@ -71,6 +71,11 @@ _SIGS = {
                                          ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
                                          ctypes.c_void_p]),
+    "vio_pyramid_detect": (ctypes.c_int32, [ctypes.c_void_p, ctypes.POINTER(PyrLayout),
+                                            ctypes.POINTER(PyrBatch), ctypes.c_void_p,
+                                            ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                                            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                            ctypes.c_void_p]),
     "vio_detect_grid_noalloc": (ctypes.c_int32, [ctypes.POINTER(Params), ctypes.POINTER(PyrLayout),
                                                  ctypes.POINTER(PyrBatch), ctypes.c_void_p,
                                                  ctypes.c_void_p, ctypes.c_int64,
@@ -260,6 +265,15 @@ class Context:
                                       _ptr(occupancy), _ptr(mask), mask_stride, _ptr(kp),
                                       _ptr(score), _ptr(count), capacity, _stream(stream)),
                "vio_detect_grid")
+
+    def pyramid_detect(self, pyr: Pyramids, kp, score, count, capacity, occupancy=None,
+                       mask=None, mask_stride=0, batch: PyrBatch | None = None, stream=None):
+        """Pyramid and detection of every image of the batch, fused."""
+        _check(load().vio_pyramid_detect(self.handle, ctypes.byref(pyr.layout),
+                                         ctypes.byref(batch or pyr.batch()), _ptr(occupancy),
+                                         _ptr(mask), mask_stride, _ptr(kp), _ptr(score),
+                                         _ptr(count), capacity, _stream(stream)),
+               "vio_pyramid_detect")
 
     def track_patches(self, pyr: Pyramids, src: PyrBatch, dst: PyrBatch, pts, count, capacity,
                       out, status, fb_dist=None, init=None, fb=True, stream=None):

@@ -263,3 +263,56 @@ def test_fb_check_kernel():
     live = (status == 0) & (np.arange(cap)[None] < cnt[:, None])
     assert np.allclose(got[live], dist[live], atol=1e-5)
     assert (got[~live] == -1).all()
+
+
+@pytest.mark.parametrize("w,h,L,cw,ch,k", [(752, 480, 4, 37, 32, 1), (1920, 1080, 5, 48, 43, 1),
+                                           (640, 480, 6, 50, 50, 2), (300, 200, 2, 30, 25, 3),
+                                           (131, 77, 1, 20, 16, 1)])
+def test_pyramid_detect_fused_bitexact(w, h, L, cw, ch, k):
+    n = 3
+    imgs = np.stack([textured(300 + i, h, w, sigma=1.5) for i in range(n)])
+    gx, gy = w // cw, h // ch
+    rng = np.random.default_rng(w + L)
+    occ = rng.integers(0, k + 1, (n, gx * gy)).astype(np.uint8)
+    mask = (rng.random((n, h, w)) > 0.05).astype(np.uint8)
+    p = vio.default_params(n_levels=L, cell_w=cw, cell_h=ch, k_per_cell=k)
+    ctx = vio.Context(p, w, h, n)
+    pyr = vio.Pyramids(to_dev(imgs, w + 32), L, w=w)
+    cap = gx * gy * k
+    kp = torch.zeros((n, cap, 2), device=DEV)
+    sc = torch.zeros((n, cap), dtype=torch.int16, device=DEV)
+    cnt = torch.zeros(n, dtype=torch.int32, device=DEV)
+    ctx.pyramid_detect(pyr, kp, sc, cnt, cap, occupancy=torch.from_numpy(occ).to(DEV),
+                       mask=torch.from_numpy(mask).to(DEV), mask_stride=h * w)
+    torch.cuda.synchronize()
+    for i in range(n):
+        ref = oracle.pyramid(imgs[i], L)
+        for l in range(1, L):
+            assert np.array_equal(pyr.level(i, l).cpu().numpy(), ref[l]), (i, l)
+        rk, rs = oracle.detect_grid(imgs[i], cw, ch, k=k, border=p.detect_border,
+                                    occupancy=occ[i], mask=mask[i])
+        c = int(cnt[i])
+        assert c == len(rk)
+        assert np.array_equal(kp[i, :c].cpu().numpy(), rk)
+        assert np.array_equal(sc[i, :c].cpu().numpy(), rs)
+
+
+def test_detect_low_contrast_falls_back_to_all_thresholds():
+    # weak texture: most cells only reach the smaller thresholds, so the
+    # bound-driven search must go down to T_min
+    w, h = 400, 300
+    img = synth.quantize(128 + 0.08 * (synth.band_limited_texture(9, h, w, 2.0) - 128),
+                         np.random.default_rng(1), 1.0)
+    p = vio.default_params(n_levels=1, cell_w=40, cell_h=30, k_per_cell=3)
+    ctx = vio.Context(p, w, h, 1)
+    pyr = vio.Pyramids(to_dev(img[None]), 1)
+    cap = 10 * 10 * 3
+    kp = torch.zeros((1, cap, 2), device=DEV)
+    sc = torch.zeros((1, cap), dtype=torch.int16, device=DEV)
+    cnt = torch.zeros(1, dtype=torch.int32, device=DEV)
+    ctx.detect_grid(pyr, pyr.batch(), kp, sc, cnt, cap)
+    torch.cuda.synchronize()
+    rk, rs = oracle.detect_grid(img, 40, 30, k=3, border=p.detect_border)
+    c = int(cnt[0])
+    assert c == len(rk) and c > 0 and rs.min() < 20
+    assert np.array_equal(kp[0, :c].cpu().numpy(), rk) and np.array_equal(sc[0, :c].cpu().numpy(), rs)
