@@ -335,6 +335,69 @@ enum { VIO_STAT_TRK0 = 0, VIO_STAT_TRK1, VIO_STAT_OK0, VIO_STAT_OK1, VIO_STAT_NE
        VIO_STAT_MATCHED, VIO_STAT_CAND, VIO_N_STATS };
 vio_status vio_frontend_read_stats(vio_frontend* fe, int32_t* host_out, int64_t* n_steps);
 
+/* --------------------------------------------------------------- batch -- */
+/* Many stereo streams of mixed sizes in one step (the frontend of Sec. III-B
+ * for each stream; batching streams is not in the paper). Streams are
+ * grouped by size (up to 8 groups); every step runs the same three launches
+ * for all groups (one per stage), optionally replayed from a captured CUDA
+ * graph. Each stream keeps its own state on the device: its two frame
+ * slots, keypoint lists, ids and first-frame flag; a step advances only the
+ * streams marked active, the others keep their state untouched. */
+typedef struct vio_batch vio_batch;
+
+typedef struct {
+  vio_params params;   /* per-group frontend parameters                   */
+  int32_t w, h;        /* frame size; frames have pitch w                  */
+  int32_t n_streams;   /* streams of this size                             */
+  int32_t capacity;    /* keypoint slots per camera (gx*gy*k..32767)       */
+} vio_stream_group;
+
+/* Tunables of a batch step: threads per block of the tracking launch (64,
+ * 128, 256 or 512) and the pyramid tile scale (-1, 0, 1: half, default,
+ * double the deepest-level tile side). */
+typedef struct {
+  int32_t k2_threads;
+  int32_t pyr_tile_shift;
+} vio_batch_tune;
+
+vio_status vio_batch_create(vio_batch** out, const vio_stream_group* groups, int32_t n_groups);
+vio_status vio_batch_destroy(vio_batch* b);
+
+/* Device address of the frame (both cameras, 2 x h x w uint8, camera 1 at
+ * + h*w) that stream `s` of group `g` reads at its next active step. Upload
+ * the frame there (on the step's stream) before the step. The other slot
+ * holds the stream's previous frame and must not be written. */
+vio_status vio_batch_next_frame(vio_batch* b, int32_t g, int32_t s, uint8_t** d_frame);
+
+/* One step of every stream whose entry of `active` (host array, one int32
+ * per stream, groups in order) is nonzero; NULL = all streams. With graphs
+ * enabled (vio_batch_set_graph) the launches are replayed from two captured
+ * graphs; the first graph step captures them (make it outside any other
+ * capture, on a stream other than the legacy default stream, else
+ * VIO_ERR_INVALID_ARG). */
+vio_status vio_batch_step(vio_batch* b, const int32_t* active, void* stream);
+vio_status vio_batch_set_graph(vio_batch* b, int32_t enable);
+vio_status vio_batch_set_tune(vio_batch* b, const vio_batch_tune* t);
+vio_status vio_batch_get_tune(vio_batch* b, vio_batch_tune* t);
+
+/* Times every tunable combination over `reps` pairs of steps (a first frame,
+ * then a tracked frame, all streams active) on the frames the caller has put
+ * in BOTH slots of every stream, keeps the fastest, and resets every stream.
+ * *best_ms: the chosen combination's time per tracked step. Blocking. */
+vio_status vio_batch_autotune(vio_batch* b, int32_t reps, void* stream, float* best_ms);
+
+/* Forget stream s of group g (its next step only detects). Enqueued. */
+vio_status vio_batch_reset_stream(vio_batch* b, int32_t g, int32_t s, void* stream);
+
+/* Output views of group g (layout as vio_frontend_view; the lists shown are
+ * those of each stream's last step). Each stream's current list parity is
+ * returned in parity[s] (host array of the group's n_streams, may be NULL);
+ * the stream's lists are at slot base ((parity*n_streams + s)*2 + c) *
+ * capacity of d_track_*, counts at (parity*n_streams + s)*2 + c. */
+vio_status vio_batch_get_view(vio_batch* b, int32_t g, vio_frontend_view* out,
+                              int32_t* parity);
+int32_t vio_batch_launches_per_step(const vio_batch* b);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1,25 +1,31 @@
 // The per-frame frontend as three dependent launches (Sec. III-B's stage
-// order, with its data dependencies kept and its serialisation removed):
+// order, with its data dependencies kept and its serialisation removed), for
+// up to kMaxGroups groups of same-size stereo streams merged into each launch:
 //
-//  K1 frame_front_kernel   pyramid levels 1-4 of every image (one pyramid
-//                          pass per tile) and, in the same launch, the
-//                          per-cell FAST/NMS top-k candidates of camera 0.
-//                          Levels beyond 4 follow as a further pass.
-//  K2 frame_track_kernel   one warp per keypoint: temporal tracking of every
-//                          live track of both cameras (previous -> current
-//                          pyramid) AND stereo matching (camera 0 -> 1) of
-//                          every cell's top-k candidates.
+//  K1 frame_front_kernel    pyramid levels 1-4 of both cameras of every stream
+//                           (one pyramid pass per tile) and, in the same
+//                           launch, the per-cell FAST/NMS top-k candidates of
+//                           camera 0. Levels beyond 4 follow as a further pass.
+//  K2 frame_track_kernel    one warp per keypoint: temporal tracking of every
+//                           live track of both cameras (previous -> current
+//                           pyramid) AND stereo matching (camera 0 -> 1) of
+//                           every cell's top-k candidates.
 //  K3 frame_finalize_kernel one CTA per stream: keep the tracks that passed,
-//                          count them per cell, select per cell the first
-//                          k - count candidates (the detection of Sec. III-D
-//                          with the cell buffer), append them to camera 0 and
-//                          their successful matches to camera 1.
+//                           count them per cell, select per cell the first
+//                           k - count candidates (the detection of Sec. III-D
+//                           with the cell buffer), append them to camera 0 and
+//                           their successful matches to camera 1.
 //
 // Matching every candidate, rather than only the selected ones, lets stereo
 // matching run beside temporal tracking instead of after it. A keypoint's
 // match depends only on its position and the two current pyramids, so the
 // result for every selected keypoint is the one the sequential order gives;
 // the candidates that the occupancy rejects are simply not used.
+//
+// Streams are either stepped together with host-side parity (unslotted), or
+// each keeps its own parity, first-frame flag and activity in device memory
+// (slotted): inactive streams are skipped and keep their state, so one
+// captured launch sequence serves any subset of streams.
 #include "detect_dev.cuh"
 #include "frame.cuh"
 #include "pyramid_dev.cuh"
@@ -33,10 +39,10 @@ static_assert(K1_THREADS == pyr::kThreads && K1_THREADS == det::kThreads, "block
 
 struct K1Args {
   Geom g;
-  Batch all;           // every image of the batch
-  int m;               // levels of the first pass (1..4; 0 = no pyramid)
+  Batch all;           // images of the launch
+  int m, T;            // levels and deepest-level tile of the first pyramid pass (m = 0: none)
   int ntx, nty;        // tiles of the first pass
-  int det_step;        // detection on every det_step-th image (1 or 2)
+  int det_step;        // 1: every image is a unit; 2: stream units (camera 0 detects)
   int blocks_per_unit; // det_step * tiles + cells
   det::CellGeom cg;
   int n_cells;
@@ -45,97 +51,126 @@ struct K1Args {
   unsigned long long* cand;
   int32_t* cand_count;
   int round_mode;
+  // stream units (det_step == 2)
+  int slotted, n_streams;
+  const int32_t* parity;
+  const int32_t* active;
+  int32_t* step_ctr;   // incremented by block 0 (nullable)
 };
 
-// Block layout: units of det_step images, each unit = the pyramid tiles of
-// its images followed by the detection cells of its first image, so that the
-// blocks reading one image run together and its level 0 is read from DRAM
-// about once.
-__global__ void __launch_bounds__(K1_THREADS) frame_front_kernel(K1Args a) {
+struct MultiK1 {
+  int n;
+  long long block_end[kMaxGroups];
+  K1Args a[kMaxGroups];
+};
+
+template <typename M>
+__device__ __forceinline__ int group_of(const M& mm, long long i, long long& start) {
+  int g = 0;
+  while (g + 1 < mm.n && i >= mm.block_end[g]) ++g;
+  start = g ? mm.block_end[g - 1] : 0;
+  return g;
+}
+
+// Block layout per group: units, each unit = the pyramid tiles of its images
+// followed by the detection cells of its first image, so that the blocks
+// reading one image run together and its level 0 is read from DRAM about once.
+__global__ void __launch_bounds__(K1_THREADS) frame_front_kernel(const __grid_constant__ MultiK1 mm) {
   extern __shared__ __align__(16) uint8_t smem[];
   __shared__ unsigned long long red[K1_THREADS / 32];
-  const int unit = blockIdx.x / a.blocks_per_unit;
-  const int rem = blockIdx.x - unit * a.blocks_per_unit;
+  long long start;
+  const int gi = group_of(mm, blockIdx.x, start);
+  const K1Args& a = mm.a[gi];
+  const long long b = blockIdx.x - start;
+  if (b == 0 && threadIdx.x == 0 && a.step_ctr) *a.step_ctr += 1;
+  const int unit = (int)(b / a.blocks_per_unit);
+  const int rem = (int)(b - (long long)unit * a.blocks_per_unit);
+  int base = unit * a.det_step;
+  if (a.det_step == 2 && a.slotted) {
+    if (a.active && a.active[unit] == 0) return;
+    base = 2 * (a.parity[unit] * a.n_streams + unit);
+  }
   const int tiles = a.ntx * a.nty;
   const int n_pyr = a.m > 0 ? a.det_step * tiles : 0;
   if (rem < n_pyr) {
-    const int img = unit * a.det_step + rem / tiles;
+    const int img = base + rem / tiles;
     const int t = rem % tiles;
     const int ty = t / a.ntx, tx = t - ty * a.ntx;
-    if (img < a.all.n)
-      pyr::pyramid_pass(a.g, a.all, img, 0, a.m, tx, ty, a.ntx, a.nty, a.round_mode, smem);
+    if (a.det_step == 2 || img < a.all.n)
+      pyr::pyramid_pass(a.g, a.all, img, 0, a.m, a.T, tx, ty, a.ntx, a.nty, a.round_mode, smem);
     return;
   }
   const int cell = rem - n_pyr;
-  const int img = unit * a.det_step;
   const long long slot = (long long)unit * a.n_cells + cell;
-  det::detect_cell(level_ptr(a.g, a.all, img, 0), a.g.w[0], a.g.h[0], a.g.pitch[0], a.cg, cell,
+  det::detect_cell(level_ptr(a.g, a.all, base, 0), a.g.w[0], a.g.h[0], a.g.pitch[0], a.cg, cell,
                    a.mask ? a.mask + (long long)unit * a.mask_stride : nullptr,
                    a.cand + slot * a.cg.k, a.cand_count + slot, smem, red);
 }
 
-struct K2Args {
-  Geom g;
-  Batch prev, cur;
-  const float* list_xy;
-  const int32_t* list_count;
-  int cap;
-  long long n_temporal;     // warps of temporal work (0 on the first frame)
-  float* trk_xy;
-  uint8_t* trk_status;
-  const unsigned long long* cand;
-  const int32_t* cand_count;
-  int n_cells, k, W;
-  long long n_stereo;       // warps of stereo work
-  float* spec_xy;
-  uint8_t* spec_status;
-  TrackCfg cfg;
+struct MultiK2 {
+  int n;
+  long long block_end[kMaxGroups];   // in warps here
+  FrameLaunch f[kMaxGroups];
 };
 
-constexpr int K2_THREADS = 128;
-
-__global__ void __launch_bounds__(K2_THREADS) frame_track_kernel(K2Args a) {
-  const long long w = ((long long)blockIdx.x * K2_THREADS + threadIdx.x) >> 5;
+__global__ void frame_track_kernel(const __grid_constant__ MultiK2 mm) {
+  const long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
+  if (w >= mm.block_end[mm.n - 1]) return;
+  long long start;
+  const int gi = group_of(mm, w, start);
+  const FrameLaunch& f = mm.f[gi];
+  const long long wl = w - start;
   const float qnan = __int_as_float(0x7fc00000);
+  const TrackCfg cfg{f.p.gn_iters, 1, f.p.fb_max_dist};
+  const long long n_temporal = 2LL * f.n_streams * f.cap;
   trk::Pos tf;
   float thf, dist;
   bool have;
-  if (w < a.n_temporal) {
-    const int list = (int)(w / a.cap);
-    const int slot = (int)(w - (long long)list * a.cap);
-    if (slot >= a.list_count[list]) {
-      if (lane == 0) a.trk_status[w] = VIO_TRACK_EMPTY;
+  if (wl < n_temporal) {
+    const int list = (int)(wl / f.cap);       // 2s + c
+    const int slot = (int)(wl - (long long)list * f.cap);
+    const int s = list >> 1, c = list & 1;
+    const StreamRef r = stream_ref(f, s);
+    if (!r.active) return;
+    const long long in_list = ((long long)r.li * f.n_streams + s) * 2 + c;
+    if (!r.have_prev || slot >= f.list_count[in_list]) {
+      if (lane == 0) f.trk_status[wl] = VIO_TRACK_EMPTY;
       return;
     }
-    const int st = trk::track_fb(a.g, a.prev, list, a.cur, list, a.list_xy[2 * w],
-                                 a.list_xy[2 * w + 1], nullptr, a.cfg, lane, tf, thf, have, dist);
+    const long long src = in_list * f.cap + slot;
+    const int st = trk::track_fb(f.g, f.prev, r.prev_img + c, f.cur, r.cur_img + c,
+                                 f.list_xy[2 * src], f.list_xy[2 * src + 1], nullptr, cfg, lane,
+                                 tf, thf, have, dist);
     if (lane == 0) {
-      a.trk_status[w] = (uint8_t)st;
-      a.trk_xy[2 * w] = have ? (float)tf.ax + tf.dx : qnan;
-      a.trk_xy[2 * w + 1] = have ? (float)tf.ay + tf.dy : qnan;
+      f.trk_status[wl] = (uint8_t)st;
+      f.trk_xy[2 * wl] = have ? (float)tf.ax + tf.dx : qnan;
+      f.trk_xy[2 * wl + 1] = have ? (float)tf.ay + tf.dy : qnan;
     }
     return;
   }
-  const long long w2 = w - a.n_temporal;
-  if (w2 >= a.n_stereo) return;
-  const int per = a.n_cells * a.k;
-  const int stream = (int)(w2 / per);
-  const int rem = (int)(w2 - (long long)stream * per);
-  const int cell = rem / a.k, r = rem - cell * a.k;
-  if (r >= a.cand_count[(long long)stream * a.n_cells + cell]) {
-    if (lane == 0) a.spec_status[w2] = VIO_TRACK_EMPTY;
+  const long long w2 = wl - n_temporal;
+  const int k = f.p.k_per_cell;
+  const int n_cells = (f.g.w[0] / f.p.cell_w) * (f.g.h[0] / f.p.cell_h);
+  const int per = n_cells * k;
+  const int s = (int)(w2 / per);
+  const int rem = (int)(w2 - (long long)s * per);
+  const int cell = rem / k, rr = rem - cell * k;
+  const StreamRef r = stream_ref(f, s);
+  if (!r.active) return;
+  if (rr >= f.cand_count[(long long)s * n_cells + cell]) {
+    if (lane == 0) f.spec_status[w2] = VIO_TRACK_EMPTY;
     return;
   }
-  const unsigned long long key = a.cand[w2];
+  const unsigned long long key = f.cand[w2];
   const unsigned idx = ~(unsigned)(key & 0xffffffffu);
-  const float x = (float)(idx % (unsigned)a.W), y = (float)(idx / (unsigned)a.W);
-  const int st = trk::track_fb(a.g, a.cur, 2 * stream, a.cur, 2 * stream + 1, x, y, nullptr,
-                               a.cfg, lane, tf, thf, have, dist);
+  const float x = (float)(idx % (unsigned)f.g.w[0]), y = (float)(idx / (unsigned)f.g.w[0]);
+  const int st = trk::track_fb(f.g, f.cur, r.cur_img, f.cur, r.cur_img + 1, x, y, nullptr, cfg,
+                               lane, tf, thf, have, dist);
   if (lane == 0) {
-    a.spec_status[w2] = (uint8_t)st;
-    a.spec_xy[2 * w2] = have ? (float)tf.ax + tf.dx : qnan;
-    a.spec_xy[2 * w2 + 1] = have ? (float)tf.ay + tf.dy : qnan;
+    f.spec_status[w2] = (uint8_t)st;
+    f.spec_xy[2 * w2] = have ? (float)tf.ax + tf.dx : qnan;
+    f.spec_xy[2 * w2 + 1] = have ? (float)tf.ay + tf.dy : qnan;
   }
 }
 
@@ -175,48 +210,49 @@ __device__ __forceinline__ int cell_of(float x, int cw) {
   return c;
 }
 
-struct K3Args {
-  int have_prev, cap, k, W, gx, gy, cw, ch;
-  // temporal results and the lists they came from
-  const float* trk_xy;
-  const uint8_t* trk_status;
-  const int32_t* ids_in;
-  const int32_t* count_in;
-  // candidates and their matches
-  const unsigned long long* cand;
-  const int32_t* cand_count;
-  const float* spec_xy;
-  const uint8_t* spec_status;
-  // outputs
-  float* xy_out;
-  int32_t* ids_out;
-  int32_t* count_out;
-  uint8_t* status_out;
-  float* new_xy;
-  int32_t* new_count;
-  int32_t* next_id;
-  uint8_t* occupancy;
-  int32_t* stats;
-};
-
 constexpr int kRunMax = 16;   // slots (or cells) one thread owns in one pass
+
+struct MultiK3 {
+  int n;
+  long long block_end[kMaxGroups];   // in blocks (= streams)
+  FrameLaunch f[kMaxGroups];
+};
 
 // One CTA per stream. Each thread owns a contiguous run of list slots (then
 // of cells), so each phase is one block-wide scan of packed counts.
-__global__ void __launch_bounds__(K3_THREADS) frame_finalize_kernel(K3Args a) {
+__global__ void __launch_bounds__(K3_THREADS) frame_finalize_kernel(const __grid_constant__ MultiK3 mm) {
   extern __shared__ int occ_s[];
   __shared__ int ws32[K3_THREADS / 32];
   __shared__ unsigned long long ws64[K3_THREADS / 32];
-  const int s = blockIdx.x;
-  const int n_cells = a.gx * a.gy;
-  const long long cap = a.cap;
+  long long start;
+  const int gi = group_of(mm, blockIdx.x, start);
+  const FrameLaunch& f = mm.f[gi];
+  const int s = (int)(blockIdx.x - start);
+  const StreamRef sr = stream_ref(f, s);
+  const int k = f.p.k_per_cell;
+  const int gx = f.g.w[0] / f.p.cell_w, gy = f.g.h[0] / f.p.cell_h;
+  const int n_cells = gx * gy;
+  const int W = f.g.w[0];
+  const long long cap = f.cap;
   const int t = threadIdx.x;
+  const int ctr = *f.step_ctr;     // this launch's step index + 1 (K1 incremented it)
+  int32_t* st = f.stats + ((long long)((ctr - 1) % VIO_STATS_RING) * f.n_streams + s) * VIO_N_STATS;
+  if (!sr.active) {
+    if (t < VIO_N_STATS) st[t] = 0;
+    return;
+  }
   for (int i = t; i < n_cells; i += K3_THREADS) occ_s[i] = 0;
 
+  const long long in0 = (((long long)sr.li * f.n_streams + s) * 2) * cap;    // list in, camera 0
+  const long long out0 = (((long long)sr.lo * f.n_streams + s) * 2) * cap;   // list out, camera 0
+  const long long trk0 = (2LL * s) * cap;
+  const long long cnt_in = ((long long)sr.li * f.n_streams + s) * 2;
+  const long long cnt_out = ((long long)sr.lo * f.n_streams + s) * 2;
+
   // 1. survivors of temporal tracking of both cameras, in order: counts of
-  //    the two cameras packed in one int (each < 2^16)
-  const int n0 = a.have_prev ? min(a.count_in[2 * s], a.cap) : 0;
-  const int n1 = a.have_prev ? min(a.count_in[2 * s + 1], a.cap) : 0;
+  //    the two cameras packed in one int (each < 2^15)
+  const int n0 = sr.have_prev ? min(f.list_count[cnt_in], f.cap) : 0;
+  const int n1 = sr.have_prev ? min(f.list_count[cnt_in + 1], f.cap) : 0;
   const int run = (max(n0, n1) + K3_THREADS - 1) / K3_THREADS;
   int surv0 = 0, surv1 = 0;
   for (int r0 = 0; r0 < run; r0 += kRunMax) {
@@ -225,43 +261,42 @@ __global__ void __launch_bounds__(K3_THREADS) frame_finalize_kernel(K3Args a) {
     unsigned keep0 = 0, keep1 = 0;
     for (int j = 0; j < rl; ++j) {
       const int i = first + j;
-      if (i < n0 && a.trk_status[(2LL * s) * cap + i] == VIO_TRACK_OK) keep0 |= 1u << j;
-      if (i < n1 && a.trk_status[(2LL * s + 1) * cap + i] == VIO_TRACK_OK) keep1 |= 1u << j;
+      if (i < n0 && f.trk_status[trk0 + i] == VIO_TRACK_OK) keep0 |= 1u << j;
+      if (i < n1 && f.trk_status[trk0 + cap + i] == VIO_TRACK_OK) keep1 |= 1u << j;
     }
     int tot;
     const int ex = block_scan<int>(__popc(keep0) | (__popc(keep1) << 16), ws32, tot);
     int o0 = surv0 + (ex & 0xffff), o1 = surv1 + (ex >> 16);
     for (int j = 0; j < rl; ++j) {
-      const long long i0 = (2LL * s) * cap + first + j;
+      const int i = first + j;
       if (keep0 & (1u << j)) {
-        const float x = a.trk_xy[2 * i0], y = a.trk_xy[2 * i0 + 1];
-        const long long d = (2LL * s) * cap + o0++;
-        a.xy_out[2 * d] = x;
-        a.xy_out[2 * d + 1] = y;
-        a.ids_out[d] = a.ids_in[i0];
+        const float x = f.trk_xy[2 * (trk0 + i)], y = f.trk_xy[2 * (trk0 + i) + 1];
+        const long long d = out0 + o0++;
+        f.list_xy[2 * d] = x;
+        f.list_xy[2 * d + 1] = y;
+        f.list_id[d] = f.list_id[in0 + i];
         if (x >= 0.f && y >= 0.f) {
-          const int cx = cell_of(x, a.cw), cy = cell_of(y, a.ch);
-          if (cx < a.gx && cy < a.gy) atomicAdd(&occ_s[cy * a.gx + cx], 1);
+          const int cx = cell_of(x, f.p.cell_w), cy = cell_of(y, f.p.cell_h);
+          if (cx < gx && cy < gy) atomicAdd(&occ_s[cy * gx + cx], 1);
         }
       }
-      const long long i1 = i0 + cap;
       if (keep1 & (1u << j)) {
-        const long long d = (2LL * s + 1) * cap + o1++;
-        a.xy_out[2 * d] = a.trk_xy[2 * i1];
-        a.xy_out[2 * d + 1] = a.trk_xy[2 * i1 + 1];
-        a.ids_out[d] = a.ids_in[i1];
+        const long long d = out0 + cap + o1++;
+        f.list_xy[2 * d] = f.trk_xy[2 * (trk0 + cap + i)];
+        f.list_xy[2 * d + 1] = f.trk_xy[2 * (trk0 + cap + i) + 1];
+        f.list_id[d] = f.list_id[in0 + cap + i];
       }
     }
     surv0 += tot & 0xffff;
     surv1 += tot >> 16;
     __syncthreads();   // ws32 is reused by the next chunk
   }
-  __syncthreads();   // occupancy complete
+  __syncthreads();     // occupancy complete
 
   // 2. per cell: selection (k_eff = k - occupancy), matched subset, and the
   //    candidates matched; three counts packed in 21-bit fields
-  const int id0 = a.next_id[s];
-  const long long b0 = (2LL * s) * cap, b1 = b0 + cap, bn = (long long)s * cap;
+  const int id0 = f.next_id[s];
+  const long long bn = (long long)s * cap;
   const long long cbase = (long long)s * n_cells;
   const int crun = (n_cells + K3_THREADS - 1) / K3_THREADS;
   int new_tot = 0, m_tot = 0, c_tot = 0;
@@ -272,13 +307,12 @@ __global__ void __launch_bounds__(K3_THREADS) frame_finalize_kernel(K3Args a) {
     for (int j = 0; j < rl; ++j) {
       const int cell = first + j;
       if (cell >= n_cells) break;
-      const int nc = a.cand_count[cbase + cell];
+      const int nc = f.cand_count[cbase + cell];
       const int occ = min(occ_s[cell], 255);
-      a.occupancy[cbase + cell] = (uint8_t)occ;
-      const int nsel = max(0, min(a.k - occ, nc));
+      f.occupancy[cbase + cell] = (uint8_t)occ;
+      const int nsel = max(0, min(k - occ, nc));
       int nm = 0;
-      for (int r = 0; r < nsel; ++r)
-        nm += a.spec_status[(cbase + cell) * a.k + r] == VIO_TRACK_OK;
+      for (int r = 0; r < nsel; ++r) nm += f.spec_status[(cbase + cell) * k + r] == VIO_TRACK_OK;
       packed += (unsigned long long)nsel | ((unsigned long long)nm << 21) |
                 ((unsigned long long)nc << 42);
     }
@@ -290,27 +324,27 @@ __global__ void __launch_bounds__(K3_THREADS) frame_finalize_kernel(K3Args a) {
       const int cell = first + j;
       if (cell >= n_cells) break;
       const int occ = min(occ_s[cell], 255);
-      const int nsel = max(0, min(a.k - occ, (int)a.cand_count[cbase + cell]));
+      const int nsel = max(0, min(k - occ, (int)f.cand_count[cbase + cell]));
       for (int r = 0; r < nsel; ++r, ++o) {
-        const long long q = (cbase + cell) * a.k + r;
-        const unsigned idx = ~(unsigned)(a.cand[q] & 0xffffffffu);
-        const float x = (float)(idx % (unsigned)a.W), y = (float)(idx / (unsigned)a.W);
-        if (o < a.cap) {
-          a.new_xy[2 * (bn + o)] = x;
-          a.new_xy[2 * (bn + o) + 1] = y;
+        const long long q = (cbase + cell) * k + r;
+        const unsigned idx = ~(unsigned)(f.cand[q] & 0xffffffffu);
+        const float x = (float)(idx % (unsigned)W), y = (float)(idx / (unsigned)W);
+        if (o < f.cap) {
+          f.new_xy[2 * (bn + o)] = x;
+          f.new_xy[2 * (bn + o) + 1] = y;
         }
         const int o0 = surv0 + o;
-        if (o0 < a.cap) {
-          a.xy_out[2 * (b0 + o0)] = x;
-          a.xy_out[2 * (b0 + o0) + 1] = y;
-          a.ids_out[b0 + o0] = id0 + o;
+        if (o0 < f.cap) {
+          f.list_xy[2 * (out0 + o0)] = x;
+          f.list_xy[2 * (out0 + o0) + 1] = y;
+          f.list_id[out0 + o0] = id0 + o;
         }
-        if (a.spec_status[q] == VIO_TRACK_OK) {
+        if (f.spec_status[q] == VIO_TRACK_OK) {
           const int o1 = surv1 + om++;
-          if (o1 < a.cap) {
-            a.xy_out[2 * (b1 + o1)] = a.spec_xy[2 * q];
-            a.xy_out[2 * (b1 + o1) + 1] = a.spec_xy[2 * q + 1];
-            a.ids_out[b1 + o1] = id0 + o;
+          if (o1 < f.cap) {
+            f.list_xy[2 * (out0 + cap + o1)] = f.spec_xy[2 * q];
+            f.list_xy[2 * (out0 + cap + o1) + 1] = f.spec_xy[2 * q + 1];
+            f.list_id[out0 + cap + o1] = id0 + o;
           }
         }
       }
@@ -320,18 +354,17 @@ __global__ void __launch_bounds__(K3_THREADS) frame_finalize_kernel(K3Args a) {
     c_tot += (int)((tot >> 42) & 0x1fffff);
     __syncthreads();
   }
-  const int c0 = min(surv0 + new_tot, a.cap);
-  const int c1 = min(surv1 + m_tot, a.cap);
-  for (int i = t; i < a.cap; i += K3_THREADS) {
-    a.status_out[b0 + i] = i < c0 ? VIO_TRACK_OK : VIO_TRACK_EMPTY;
-    a.status_out[b1 + i] = i < c1 ? VIO_TRACK_OK : VIO_TRACK_EMPTY;
+  const int c0 = min(surv0 + new_tot, f.cap);
+  const int c1 = min(surv1 + m_tot, f.cap);
+  for (int i = t; i < f.cap; i += K3_THREADS) {
+    f.list_status[out0 + i] = i < c0 ? VIO_TRACK_OK : VIO_TRACK_EMPTY;
+    f.list_status[out0 + cap + i] = i < c1 ? VIO_TRACK_OK : VIO_TRACK_EMPTY;
   }
   if (t == 0) {
-    a.count_out[2 * s] = c0;
-    a.count_out[2 * s + 1] = c1;
-    a.new_count[s] = min(new_tot, a.cap);
-    a.next_id[s] = id0 + new_tot;
-    int32_t* st = a.stats + s * VIO_N_STATS;
+    f.list_count[cnt_out] = c0;
+    f.list_count[cnt_out + 1] = c1;
+    f.new_count[s] = min(new_tot, f.cap);
+    f.next_id[s] = id0 + new_tot;
     st[VIO_STAT_TRK0] = n0;
     st[VIO_STAT_TRK1] = n1;
     st[VIO_STAT_OK0] = surv0;
@@ -339,144 +372,158 @@ __global__ void __launch_bounds__(K3_THREADS) frame_finalize_kernel(K3Args a) {
     st[VIO_STAT_NEW] = new_tot;
     st[VIO_STAT_MATCHED] = m_tot;
     st[VIO_STAT_CAND] = c_tot;
+    if (f.slotted) {
+      f.parity[s] = sr.lo;
+      f.have_prev[s] = 1;
+    }
   }
 }
 
-}  // namespace
-
-cudaError_t launch_front(const vio_params& p, const Geom& g, const Batch& all, int det_step,
-                         const uint8_t* mask, long long mask_stride, unsigned long long* cand,
-                         int32_t* cand_count, cudaStream_t s) {
+K1Args front_args(const vio_params& p, const Geom& g, const Batch& all, int det_step,
+                  const uint8_t* mask, long long mask_stride, unsigned long long* cand,
+                  int32_t* cand_count, int tile_shift) {
   const int gx = g.w[0] / p.cell_w, gy = g.h[0] / p.cell_h;
-  K1Args a1{};
-  a1.g = g;
-  a1.all = all;
-  a1.m = g.n_levels > 1 ? pyr::pass_levels(g.n_levels, 0) : 0;
-  a1.ntx = a1.nty = 1;
-  if (a1.m > 0) pyr::pass_tiles(g.w, g.h, 0, a1.m, a1.ntx, a1.nty);
-  a1.det_step = det_step;
-  a1.n_cells = gx * gy;
-  a1.blocks_per_unit = (a1.m > 0 ? det_step * a1.ntx * a1.nty : 0) + a1.n_cells;
-  a1.cg = det::CellGeom{p.cell_w, p.cell_h, gx, p.k_per_cell, p.thresholds[p.n_thresholds - 1],
-                        p.detect_border};
-  a1.mask = mask;
-  a1.mask_stride = mask_stride;
-  a1.cand = cand;
-  a1.cand_count = cand_count;
-  a1.round_mode = p.round_mode;
-  const int smem = frame_front_smem(g, p);
+  K1Args a{};
+  a.g = g;
+  a.all = all;
+  a.m = g.n_levels > 1 ? pyr::pass_levels(g.n_levels, 0) : 0;
+  a.T = a.m > 0 ? pyr::top_tile(a.m, tile_shift) : 1;
+  a.ntx = a.nty = 1;
+  if (a.m > 0) pyr::pass_tiles(g.w, g.h, 0, a.m, a.T, a.ntx, a.nty);
+  a.det_step = det_step;
+  a.n_cells = gx * gy;
+  a.blocks_per_unit = (a.m > 0 ? det_step * a.ntx * a.nty : 0) + a.n_cells;
+  a.cg = det::CellGeom{p.cell_w, p.cell_h, gx, p.k_per_cell, p.thresholds[p.n_thresholds - 1],
+                       p.detect_border};
+  a.mask = mask;
+  a.mask_stride = mask_stride;
+  a.cand = cand;
+  a.cand_count = cand_count;
+  a.round_mode = p.round_mode;
+  return a;
+}
+
+cudaError_t launch_k1(const MultiK1& mm, int smem, cudaStream_t s) {
   if (smem > 48 * 1024) {
     const cudaError_t e = cudaFuncSetAttribute(
         frame_front_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
   }
-  const long long units = (all.n + det_step - 1) / det_step;
-  const long long blocks = units * a1.blocks_per_unit;
-  if (blocks > 0) frame_front_kernel<<<(unsigned)blocks, K1_THREADS, smem, s>>>(a1);
+  const long long blocks = mm.block_end[mm.n - 1];
+  if (blocks > 0) frame_front_kernel<<<(unsigned)blocks, K1_THREADS, smem, s>>>(mm);
   return cudaGetLastError();
 }
 
-int frame_front_smem(const Geom& g, const vio_params& p) {
+}  // namespace
+
+int frame_front_smem(const Geom& g, const vio_params& p, int tile_shift) {
   int smem = det::cell_smem_bytes(p.cell_w, p.cell_h);
   if (g.n_levels > 1) {
     const int m = pyr::pass_levels(g.n_levels, 0);
-    const int ps = pyr::pass_smem_max(g.w, g.h, 0, m);
+    const int ps = pyr::pass_smem_max(g.w, g.h, 0, m, pyr::top_tile(m, tile_shift));
     smem = ps > smem ? ps : smem;
   }
   return smem;
 }
 
-cudaError_t launch_frame(const FrameLaunch& f, cudaStream_t s, cudaEvent_t* marks) {
-  const Geom& g = f.g;
-  const int ns = f.n_streams;
-  const int gx = g.w[0] / f.p.cell_w, gy = g.h[0] / f.p.cell_h;
-  const int n_cells = gx * gy;
-  const int k = f.p.k_per_cell;
+cudaError_t launch_front(const vio_params& p, const Geom& g, const Batch& all, int det_step,
+                         const uint8_t* mask, long long mask_stride, unsigned long long* cand,
+                         int32_t* cand_count, cudaStream_t s) {
+  MultiK1 mm{};
+  mm.n = 1;
+  mm.a[0] = front_args(p, g, all, det_step, mask, mask_stride, cand, cand_count, 0);
+  const long long units = (all.n + det_step - 1) / det_step;
+  mm.block_end[0] = units * mm.a[0].blocks_per_unit;
+  return launch_k1(mm, frame_front_smem(g, p, 0), s);
+}
+
+cudaError_t launch_frames(const FrameLaunch* fl, int n_groups, const FrameTune& tune,
+                          cudaStream_t s, cudaEvent_t* marks) {
+  if (n_groups < 1 || n_groups > kMaxGroups) return cudaErrorInvalidValue;
   auto mark = [&](int i) {
     if (marks) cudaEventRecord(marks[i], s);
   };
 
   // K1: pyramid levels 1-4 + detection candidates (camera 0 of each stream)
   mark(0);
-  cudaError_t e = launch_front(f.p, g, f.cur, 2, nullptr, 0, f.cand, f.cand_count, s);
+  MultiK1 m1{};
+  m1.n = n_groups;
+  int smem1 = 0;
+  long long acc = 0;
+  for (int i = 0; i < n_groups; ++i) {
+    const FrameLaunch& f = fl[i];
+    K1Args a = front_args(f.p, f.g, f.cur, 2, nullptr, 0, f.cand, f.cand_count,
+                          tune.pyr_tile_shift);
+    a.slotted = f.slotted;
+    a.n_streams = f.n_streams;
+    a.parity = f.parity;
+    a.active = f.active;
+    a.step_ctr = f.step_ctr;
+    m1.a[i] = a;
+    acc += (long long)f.n_streams * a.blocks_per_unit;
+    m1.block_end[i] = acc;
+    const int sm = frame_front_smem(f.g, f.p, tune.pyr_tile_shift);
+    smem1 = sm > smem1 ? sm : smem1;
+  }
+  cudaError_t e = launch_k1(m1, smem1, s);
   if (e != cudaSuccess) return e;
-  // deeper pyramid levels
+  // levels beyond the first pass
   mark(1);
-  if (g.n_levels > 1 + pyr::kMaxPass) {
-    e = launch_pyramid_from(g, f.cur, pyr::kMaxPass, f.p.round_mode, s);
-    if (e != cudaSuccess) return e;
+  for (int i = 0; i < n_groups; ++i) {
+    const FrameLaunch& f = fl[i];
+    if (f.g.n_levels > 1 + pyr::kMaxPass) {
+      e = launch_pyramid_from(f.g, f.cur, pyr::kMaxPass, f.p.round_mode, s);
+      if (e != cudaSuccess) return e;
+    }
   }
 
   // K2: temporal tracking + stereo matching of all candidates
   mark(2);
-  K2Args a2{};
-  a2.g = g;
-  a2.prev = f.prev;
-  a2.cur = f.cur;
-  a2.list_xy = f.list_xy_in;
-  a2.list_count = f.list_count_in;
-  a2.cap = f.cap;
-  a2.n_temporal = f.have_prev ? 2LL * ns * f.cap : 0;
-  a2.trk_xy = f.trk_xy;
-  a2.trk_status = f.trk_status;
-  a2.cand = f.cand;
-  a2.cand_count = f.cand_count;
-  a2.n_cells = n_cells;
-  a2.k = k;
-  a2.W = g.w[0];
-  a2.n_stereo = (long long)ns * n_cells * k;
-  a2.spec_xy = f.spec_xy;
-  a2.spec_status = f.spec_status;
-  a2.cfg = TrackCfg{f.p.gn_iters, 1, f.p.fb_max_dist};
-  const long long warps = a2.n_temporal + a2.n_stereo;
-  if (warps > 0) {
-    const long long blocks2 = (warps * 32 + K2_THREADS - 1) / K2_THREADS;
-    frame_track_kernel<<<(unsigned)blocks2, K2_THREADS, 0, s>>>(a2);
+  MultiK2 m2{};
+  m2.n = n_groups;
+  acc = 0;
+  for (int i = 0; i < n_groups; ++i) {
+    const FrameLaunch& f = fl[i];
+    m2.f[i] = f;
+    const int n_cells = (f.g.w[0] / f.p.cell_w) * (f.g.h[0] / f.p.cell_h);
+    acc += 2LL * f.n_streams * f.cap + (long long)f.n_streams * n_cells * f.p.k_per_cell;
+    m2.block_end[i] = acc;
+  }
+  const int k2t = tune.k2_threads;
+  if (acc > 0) {
+    const long long blocks2 = (acc * 32 + k2t - 1) / k2t;
+    frame_track_kernel<<<(unsigned)blocks2, k2t, 0, s>>>(m2);
   }
 
   // K3: finalize
   mark(3);
-  K3Args a3{};
-  a3.have_prev = f.have_prev;
-  a3.cap = f.cap;
-  a3.k = k;
-  a3.W = g.w[0];
-  a3.gx = gx;
-  a3.gy = gy;
-  a3.cw = f.p.cell_w;
-  a3.ch = f.p.cell_h;
-  a3.trk_xy = f.trk_xy;
-  a3.trk_status = f.trk_status;
-  a3.ids_in = f.list_id_in;
-  a3.count_in = f.list_count_in;
-  a3.cand = f.cand;
-  a3.cand_count = f.cand_count;
-  a3.spec_xy = f.spec_xy;
-  a3.spec_status = f.spec_status;
-  a3.xy_out = f.list_xy_out;
-  a3.ids_out = f.list_id_out;
-  a3.count_out = f.list_count_out;
-  a3.status_out = f.list_status;
-  a3.new_xy = f.new_xy;
-  a3.new_count = f.new_count;
-  a3.next_id = f.next_id;
-  a3.occupancy = f.occupancy;
-  a3.stats = f.stats;
-  const int smem3 = n_cells * (int)sizeof(int);
+  MultiK3 m3{};
+  m3.n = n_groups;
+  acc = 0;
+  int smem3 = 0;
+  for (int i = 0; i < n_groups; ++i) {
+    const FrameLaunch& f = fl[i];
+    m3.f[i] = f;
+    acc += f.n_streams;
+    m3.block_end[i] = acc;
+    const int sm = (f.g.w[0] / f.p.cell_w) * (f.g.h[0] / f.p.cell_h) * (int)sizeof(int);
+    smem3 = sm > smem3 ? sm : smem3;
+  }
   if (smem3 > 48 * 1024) {
     e = cudaFuncSetAttribute(frame_finalize_kernel,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, smem3);
     if (e != cudaSuccess) return e;
   }
-  frame_finalize_kernel<<<ns, K3_THREADS, smem3, s>>>(a3);
+  frame_finalize_kernel<<<(unsigned)acc, K3_THREADS, smem3, s>>>(m3);
   mark(4);
   return cudaGetLastError();
 }
 
-int frame_launches(const Geom& g) {
-  int n = 1;                                   // K1
-  for (int s0 = pyr::kMaxPass; s0 + 1 < g.n_levels; s0 += pyr::kMaxPass) ++n;
-  return n + 2;                                // K2, K3
+int frame_launches(const Geom* g, int n_groups) {
+  int n = 3;                                   // K1, K2, K3
+  for (int i = 0; i < n_groups; ++i)
+    if (g[i].n_levels > 1 + pyr::kMaxPass) ++n;
+  return n;
 }
 
 }  // namespace vio

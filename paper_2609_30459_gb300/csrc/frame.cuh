@@ -1,22 +1,39 @@
-// Launch description of one frontend frame (frame.cu).
+// Launch description of one frontend frame (frame.cu), for one or more
+// groups of same-size stereo streams merged into the same three launches.
 #pragma once
 #include "common.cuh"
 
 namespace vio {
 
+constexpr int kMaxGroups = 8;
+
+// Launch tunables (chosen by the autotuner of a batch).
+struct FrameTune {
+  int k2_threads;      // threads per block of the tracking launch (64..512)
+  int pyr_tile_shift;  // deepest-level pyramid tile side = (32 >> (m-1)) << shift
+};
+
 struct FrameLaunch {
   vio_params p;
   Geom g;
-  int n_streams, cap, have_prev;
-  Batch prev, cur;                 // previous / current frame: 2 images per stream
-  const float* list_xy_in;         // lists of the previous step, (2*ns) x cap
-  const int32_t* list_id_in;
-  const int32_t* list_count_in;
-  float* list_xy_out;              // lists after this step
-  int32_t* list_id_out;
-  int32_t* list_count_out;
+  int n_streams, cap;
+  // Images. Unslotted: stream s camera c is image 2s+c of `cur` (this frame)
+  // and of `prev` (previous frame). Slotted: `cur` == `prev` holds two frame
+  // slots per stream and stream s at parity q uses image 2(q*ns + s) + c,
+  // the previous frame being at parity 1 - q.
+  Batch cur, prev;
+  int slotted;
+  int host_parity, host_have_prev;  // unslotted: list parity and first-frame flag
+  int32_t* parity;                  // slotted, per stream (flipped by finalize)
+  int32_t* have_prev;               // slotted, per stream
+  const int32_t* active;            // slotted, per stream, nonzero = step it (null: all)
+  // keypoint lists [parity][stream][camera] x cap
+  float* list_xy;
+  int32_t* list_id;
+  int32_t* list_count;
   uint8_t* list_status;
-  float* trk_xy;                   // temporal results, (2*ns) x cap
+  // temporal results [stream][camera] x cap
+  float* trk_xy;
   uint8_t* trk_status;
   unsigned long long* cand;        // candidates, ns x cells x k
   int32_t* cand_count;             // ns x cells
@@ -26,18 +43,53 @@ struct FrameLaunch {
   int32_t* new_count;              // ns
   int32_t* next_id;                // ns
   uint8_t* occupancy;              // ns x cells
-  int32_t* stats;                  // ns x VIO_N_STATS
+  int32_t* stats;                  // ring, VIO_STATS_RING x ns x VIO_N_STATS
+  int32_t* step_ctr;               // incremented once per launch of the frame
 };
 
-// Enqueues the frame on `s`. marks: 5 events recorded at the stage
+// Per-stream view of a FrameLaunch.
+struct StreamRef {
+  int cur_img, prev_img;   // image index of camera 0
+  int li, lo;              // list parity in / out
+  bool have_prev, active;
+};
+
+__host__ __device__ inline StreamRef stream_ref(const FrameLaunch& f, int s) {
+  StreamRef r;
+  if (!f.slotted) {
+    r.cur_img = 2 * s;
+    r.prev_img = 2 * s;
+    r.li = f.host_parity;
+    r.lo = f.host_parity ^ 1;
+    r.have_prev = f.host_have_prev != 0;
+    r.active = true;
+    return r;
+  }
+#ifdef __CUDA_ARCH__
+  const int q = f.parity[s];
+  r.cur_img = 2 * (q * f.n_streams + s);
+  r.prev_img = 2 * ((q ^ 1) * f.n_streams + s);
+  r.li = q;
+  r.lo = q ^ 1;
+  r.have_prev = f.have_prev[s] != 0;
+  r.active = f.active ? f.active[s] != 0 : true;
+#else
+  r = StreamRef{};
+#endif
+  return r;
+}
+
+// Enqueues one frame of every group on `s` (3 launches, plus one pyramid
+// pass per group for levels beyond 5). marks: 5 events recorded at the stage
 // boundaries (or null).
-cudaError_t launch_frame(const FrameLaunch& f, cudaStream_t s, cudaEvent_t* marks);
-int frame_launches(const Geom& g);
+cudaError_t launch_frames(const FrameLaunch* f, int n_groups, const FrameTune& tune,
+                          cudaStream_t s, cudaEvent_t* marks);
+int frame_launches(const Geom* g, int n_groups);
+int frame_front_smem(const Geom& g, const vio_params& p, int tile_shift);
 // Fused pyramid (levels 1-4) and per-cell detection candidates of every
 // det_step-th image of `all`, one launch.
 cudaError_t launch_front(const vio_params& p, const Geom& g, const Batch& all, int det_step,
                          const uint8_t* mask, long long mask_stride, unsigned long long* cand,
                          int32_t* cand_count, cudaStream_t s);
-int frame_front_smem(const Geom& g, const vio_params& p);
 
 }  // namespace vio

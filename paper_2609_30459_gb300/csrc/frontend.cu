@@ -24,10 +24,10 @@ struct vio_frontend {
   // device buffers (one allocation)
   void* d_mem;
   uint8_t* pyr[2];            // upper buffers, 2*n_streams images each, ring of 2 frames
-  float* list_xy[2];          // float2 per slot, (2*n_streams) * capacity
-  int32_t* list_id[2];
-  int32_t* list_count[2];     // 2*n_streams
-  uint8_t* list_status;       // status of the current list (output view)
+  float* list_xy;             // float2 per slot, [parity][stream][camera] x capacity
+  int32_t* list_id;
+  int32_t* list_count;        // [parity][stream][camera]
+  uint8_t* list_status;
   float* trk_xy;              // temporal track result, float2 per slot
   uint8_t* trk_status;
   unsigned long long* cand;   // n_streams * cells * k candidate keys
@@ -39,6 +39,7 @@ struct vio_frontend {
   int32_t* new_count;         // n_streams
   int32_t* next_id;           // n_streams
   int32_t* stats;             // VIO_STATS_RING * n_streams * VIO_N_STATS
+  int32_t* step_ctr;          // device count of launched steps
   // host state
   int cur_list;
   int cur_pyr;
@@ -111,10 +112,13 @@ extern "C" vio_status vio_frontend_create(vio_frontend** out, const vio_params* 
   const size_t ns = (size_t)n_streams, nc = (size_t)n_cells, kk = (size_t)p->k_per_cell;
   const size_t sizes[] = {
       (size_t)L.upper_bytes * nl, (size_t)L.upper_bytes * nl,   // 0-1 pyr
-      slots * 8, slots * 8,                                     // 2-3 list_xy
-      slots * 4, slots * 4,                                     // 4-5 list_id
-      nl * 4, nl * 4,                                           // 6-7 list_count
-      slots,                                                    // 8 list_status
+      2 * slots * 8,                                            // 2 list_xy
+      2 * slots * 4,                                            // 3 list_id
+      2 * nl * 4,                                               // 4 list_count
+      2 * slots,                                                // 5 list_status
+      16,                                                       // 6 step_ctr
+      16,                                                       // 7 (spare)
+      16,                                                       // 8 (spare)
       slots * 8, slots,                                         // 9-10 trk
       ns * nc * kk * 8, ns * nc * 4,                            // 11-12 cand
       ns * nc * kk * 8, ns * nc * kk,                           // 13-14 spec
@@ -138,13 +142,11 @@ extern "C" vio_status vio_frontend_create(vio_frontend** out, const vio_params* 
   }
   fe->pyr[0] = (uint8_t*)ptrs[0];
   fe->pyr[1] = (uint8_t*)ptrs[1];
-  fe->list_xy[0] = (float*)ptrs[2];
-  fe->list_xy[1] = (float*)ptrs[3];
-  fe->list_id[0] = (int32_t*)ptrs[4];
-  fe->list_id[1] = (int32_t*)ptrs[5];
-  fe->list_count[0] = (int32_t*)ptrs[6];
-  fe->list_count[1] = (int32_t*)ptrs[7];
-  fe->list_status = (uint8_t*)ptrs[8];
+  fe->list_xy = (float*)ptrs[2];
+  fe->list_id = (int32_t*)ptrs[3];
+  fe->list_count = (int32_t*)ptrs[4];
+  fe->list_status = (uint8_t*)ptrs[5];
+  fe->step_ctr = (int32_t*)ptrs[6];
   fe->trk_xy = (float*)ptrs[9];
   fe->trk_status = (uint8_t*)ptrs[10];
   fe->cand = (unsigned long long*)ptrs[11];
@@ -157,7 +159,7 @@ extern "C" vio_status vio_frontend_create(vio_frontend** out, const vio_params* 
   fe->next_id = (int32_t*)ptrs[18];
   fe->stats = (int32_t*)ptrs[19];
   if (cudaMemset(fe->d_mem, 0, total) != cudaSuccess ||
-      cudaMemset(fe->list_status, VIO_TRACK_EMPTY, slots) != cudaSuccess ||
+      cudaMemset(fe->list_status, VIO_TRACK_EMPTY, 2 * slots) != cudaSuccess ||
       cudaDeviceSynchronize() != cudaSuccess) {
     cudaGetLastError();
     cudaFree(fe->d_mem);
@@ -190,9 +192,8 @@ extern "C" vio_status vio_frontend_reset(vio_frontend* fe, void* stream) {
   if (!fe) return VIO_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   const size_t nl = (size_t)2 * fe->n_streams;
-  cudaMemsetAsync(fe->list_count[0], 0, nl * 4, s);
-  cudaMemsetAsync(fe->list_count[1], 0, nl * 4, s);
-  cudaMemsetAsync(fe->list_status, VIO_TRACK_EMPTY, nl * fe->capacity, s);
+  cudaMemsetAsync(fe->list_count, 0, 2 * nl * 4, s);
+  cudaMemsetAsync(fe->list_status, VIO_TRACK_EMPTY, 2 * nl * fe->capacity, s);
   cudaMemsetAsync(fe->next_id, 0, (size_t)fe->n_streams * 4, s);
   fe->have_prev = false;
   return cudaGetLastError() == cudaSuccess ? VIO_OK : VIO_ERR_CUDA;
@@ -202,7 +203,8 @@ extern "C" int32_t vio_frontend_launches_per_step(const vio_frontend* fe) {
   if (!fe) return 0;
   vio_pyr_layout L;
   if (vio_pyr_layout_make(fe->w, fe->h, fe->p.n_levels, fe->w, &L) != VIO_OK) return 0;
-  return vio::frame_launches(vio::make_geom(L));
+  const vio::Geom g = vio::make_geom(L);
+  return vio::frame_launches(&g, 1);
 }
 
 extern "C" vio_status vio_frontend_step(vio_frontend* fe, const uint8_t* d_frames,
@@ -230,16 +232,15 @@ extern "C" vio_status vio_frontend_step(vio_frontend* fe, const uint8_t* d_frame
   f.g = make_geom(L);
   f.n_streams = ns;
   f.cap = fe->capacity;
-  f.have_prev = fe->have_prev ? 1 : 0;
   f.cur = Batch{d_frames, frame_stride, fe->pyr[cur], ub, 2 * ns};
   f.prev = fe->have_prev ? Batch{fe->prev_frames, fe->prev_stride, fe->pyr[prv], ub, 2 * ns}
                          : f.cur;
-  f.list_xy_in = fe->list_xy[li];
-  f.list_id_in = fe->list_id[li];
-  f.list_count_in = fe->list_count[li];
-  f.list_xy_out = fe->list_xy[lo];
-  f.list_id_out = fe->list_id[lo];
-  f.list_count_out = fe->list_count[lo];
+  f.slotted = 0;
+  f.host_parity = li;
+  f.host_have_prev = fe->have_prev ? 1 : 0;
+  f.list_xy = fe->list_xy;
+  f.list_id = fe->list_id;
+  f.list_count = fe->list_count;
   f.list_status = fe->list_status;
   f.trk_xy = fe->trk_xy;
   f.trk_status = fe->trk_status;
@@ -251,8 +252,11 @@ extern "C" vio_status vio_frontend_step(vio_frontend* fe, const uint8_t* d_frame
   f.new_count = fe->new_count;
   f.next_id = fe->next_id;
   f.occupancy = fe->occupancy;
-  f.stats = fe->stats + (fe->steps % VIO_STATS_RING) * ns * VIO_N_STATS;
-  if (launch_frame(f, s, fe->timing ? ev.data() : nullptr) != cudaSuccess) return VIO_ERR_CUDA;
+  f.stats = fe->stats;
+  f.step_ctr = fe->step_ctr;
+  const FrameTune tune{128, 0};
+  if (launch_frames(&f, 1, tune, s, fe->timing ? ev.data() : nullptr) != cudaSuccess)
+    return VIO_ERR_CUDA;
   if (fe->timing) fe->ev_rec.push_back(ev);
 
   fe->cur_list = lo;
@@ -324,11 +328,11 @@ extern "C" vio_status vio_frontend_read_stats(vio_frontend* fe, int32_t* host_ou
 
 extern "C" vio_status vio_frontend_get_view(vio_frontend* fe, vio_frontend_view* out) {
   if (!fe || !out) return VIO_ERR_INVALID_ARG;
-  const int li = fe->cur_list;
-  out->d_track_xy = fe->list_xy[li];
-  out->d_track_id = fe->list_id[li];
-  out->d_track_status = fe->list_status;
-  out->d_track_count = fe->list_count[li];
+  const size_t nl = (size_t)2 * fe->n_streams, li = (size_t)fe->cur_list;
+  out->d_track_xy = fe->list_xy + 2 * li * nl * fe->capacity;
+  out->d_track_id = fe->list_id + li * nl * fe->capacity;
+  out->d_track_status = fe->list_status + li * nl * fe->capacity;
+  out->d_track_count = fe->list_count + li * nl;
   out->d_new_xy = fe->new_xy;
   out->d_new_count = fe->new_count;
   out->capacity = fe->capacity;

@@ -9,14 +9,14 @@ namespace vio {
 namespace {
 
 __global__ void __launch_bounds__(pyr::kThreads) pyr_pass_kernel(Geom g, Batch b, int s, int m,
-                                                                 int ntx, int nty,
+                                                                 int T, int ntx, int nty,
                                                                  int round_mode) {
   extern __shared__ __align__(16) uint8_t smem[];
   const int tiles = ntx * nty;
   const int img = blockIdx.x / tiles;
   const int t = blockIdx.x - img * tiles;
   const int ty = t / ntx, tx = t - ty * ntx;
-  pyr::pyramid_pass(g, b, img, s, m, tx, ty, ntx, nty, round_mode, smem);
+  pyr::pyramid_pass(g, b, img, s, m, T, tx, ty, ntx, nty, round_mode, smem);
 }
 
 }  // namespace
@@ -25,16 +25,17 @@ cudaError_t launch_pyramid_from(const Geom& g, const Batch& b, int s0, int round
                                 cudaStream_t st) {
   for (int s = s0; s + 1 < g.n_levels; s += pyr::kMaxPass) {
     const int m = pyr::pass_levels(g.n_levels, s);
+    const int T = pyr::top_tile(m);
     int ntx, nty;
-    pyr::pass_tiles(g.w, g.h, s, m, ntx, nty);
-    const int smem = pyr::pass_smem_max(g.w, g.h, s, m);
+    pyr::pass_tiles(g.w, g.h, s, m, T, ntx, nty);
+    const int smem = pyr::pass_smem_max(g.w, g.h, s, m, T);
     if (smem > 48 * 1024) {
       cudaError_t e = cudaFuncSetAttribute(pyr_pass_kernel,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
       if (e != cudaSuccess) return e;
     }
     const long long blocks = (long long)ntx * nty * b.n;
-    pyr_pass_kernel<<<(unsigned)blocks, pyr::kThreads, smem, st>>>(g, b, s, m, ntx, nty,
+    pyr_pass_kernel<<<(unsigned)blocks, pyr::kThreads, smem, st>>>(g, b, s, m, T, ntx, nty,
                                                                    round_mode);
   }
   return cudaGetLastError();

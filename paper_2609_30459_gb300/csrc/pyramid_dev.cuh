@@ -19,8 +19,13 @@ namespace pyr {
 constexpr int kMaxPass = 4;   // levels one pass computes
 constexpr int kThreads = 256;
 
-// deepest-level tile side of a pass of m levels: 32, 16, 8, 4
-__host__ __device__ inline int top_tile(int m) { return 32 >> (m - 1); }
+// deepest-level tile side of a pass of m levels: 32, 16, 8, 4, scaled by
+// 2^shift (shift in -1..1), at least 1
+__host__ __device__ inline int top_tile(int m, int shift = 0) {
+  const int base = 32 >> (m - 1);
+  const int t = shift >= 0 ? base << shift : base >> (-shift);
+  return t > 0 ? t : 1;
+}
 
 struct Range {
   int s, e;   // [s, e)
@@ -58,9 +63,8 @@ struct PassRegions {
 };
 
 __host__ __device__ inline PassRegions pass_regions(const int* wl, const int* hl, int s, int m,
-                                                    int tx, int ty, int ntx, int nty) {
+                                                    int T, int tx, int ty, int ntx, int nty) {
   PassRegions R;
-  const int T = top_tile(m);
   // deepest level of the pass: s + m
   R.x[m] = owned(tx, ntx, T, 0, wl[s + m]);
   R.y[m] = owned(ty, nty, T, 0, hl[s + m]);
@@ -160,9 +164,9 @@ __device__ __forceinline__ void stage_rect(const uint8_t* __restrict__ img, int 
 // levels s+1..s+m (m <= kMaxPass) to global memory. All threads of the block
 // must call it; `smem` is 16-byte aligned and holds pass_smem(...).total bytes.
 __device__ __forceinline__ void pyramid_pass(const Geom& g, const Batch& b, int img, int s,
-                                             int m, int tx, int ty, int ntx, int nty,
+                                             int m, int T, int tx, int ty, int ntx, int nty,
                                              int round_mode, uint8_t* smem) {
-  const PassRegions R = pass_regions(g.w, g.h, s, m, tx, ty, ntx, nty);
+  const PassRegions R = pass_regions(g.w, g.h, s, m, T, tx, ty, ntx, nty);
   const PassSmem S = pass_smem(R, m);
   const uint8_t* src = level_ptr(g, b, img, s);
   const int xa = R.x[0].s & ~15;
@@ -217,7 +221,6 @@ __device__ __forceinline__ void pyramid_pass(const Geom& g, const Batch& b, int 
     const int os = S.lv_stride[k];
     uint8_t* dst = level_ptr_mut(g, b, img, s + k);
     const int dpitch = g.pitch[s + k];
-    const int T = top_tile(m);
     const Range wx = owned(tx, ntx, T, m - k, g.w[s + k]);
     const Range wy = owned(ty, nty, T, m - k, g.h[s + k]);
     for (int i = threadIdx.x; i < oh * ow; i += blockDim.x) {
@@ -246,9 +249,8 @@ __device__ __forceinline__ void pyramid_pass(const Geom& g, const Batch& b, int 
 }
 
 // Tile counts of a pass that ends at level s + m.
-__host__ __device__ inline void pass_tiles(const int* wl, const int* hl, int s, int m, int& ntx,
-                                           int& nty) {
-  const int T = top_tile(m);
+__host__ __device__ inline void pass_tiles(const int* wl, const int* hl, int s, int m, int T,
+                                           int& ntx, int& nty) {
   ntx = (wl[s + m] + T - 1) / T;
   nty = (hl[s + m] + T - 1) / T;
 }
@@ -261,15 +263,15 @@ __host__ __device__ inline int pass_levels(int n_levels, int s) {
 
 // Largest shared memory a pass over this geometry needs (interior and edge
 // tiles).
-inline int pass_smem_max(const int* wl, const int* hl, int s, int m) {
+inline int pass_smem_max(const int* wl, const int* hl, int s, int m, int T) {
   int ntx, nty;
-  pass_tiles(wl, hl, s, m, ntx, nty);
+  pass_tiles(wl, hl, s, m, T, ntx, nty);
   int best = 0;
   const int txs[3] = {0, ntx > 1 ? ntx - 2 : 0, ntx - 1};
   const int tys[3] = {0, nty > 1 ? nty - 2 : 0, nty - 1};
   for (int a = 0; a < 3; ++a)
     for (int c = 0; c < 3; ++c) {
-      const PassRegions R = pass_regions(wl, hl, s, m, txs[a], tys[c], ntx, nty);
+      const PassRegions R = pass_regions(wl, hl, s, m, T, txs[a], tys[c], ntx, nty);
       const int t = pass_smem(R, m).total;
       best = t > best ? t : best;
     }

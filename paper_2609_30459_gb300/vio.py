@@ -52,6 +52,15 @@ class FrontendView(ctypes.Structure):
                 ("capacity", ctypes.c_int32), ("n_streams", ctypes.c_int32)]
 
 
+class StreamGroup(ctypes.Structure):
+    _fields_ = [("params", Params), ("w", ctypes.c_int32), ("h", ctypes.c_int32),
+                ("n_streams", ctypes.c_int32), ("capacity", ctypes.c_int32)]
+
+
+class BatchTune(ctypes.Structure):
+    _fields_ = [("k2_threads", ctypes.c_int32), ("pyr_tile_shift", ctypes.c_int32)]
+
+
 _lib = None
 _lock = threading.Lock()
 
@@ -114,6 +123,22 @@ _SIGS = {
                                           ctypes.c_void_p]),
     "vio_frontend_read_stats": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p,
                                                  ctypes.POINTER(ctypes.c_int64)]),
+    "vio_batch_create": (ctypes.c_int32, [ctypes.POINTER(ctypes.c_void_p),
+                                          ctypes.POINTER(StreamGroup), ctypes.c_int32]),
+    "vio_batch_destroy": (ctypes.c_int32, [ctypes.c_void_p]),
+    "vio_batch_next_frame": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
+                                              ctypes.POINTER(ctypes.c_void_p)]),
+    "vio_batch_step": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "vio_batch_set_graph": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32]),
+    "vio_batch_set_tune": (ctypes.c_int32, [ctypes.c_void_p, ctypes.POINTER(BatchTune)]),
+    "vio_batch_get_tune": (ctypes.c_int32, [ctypes.c_void_p, ctypes.POINTER(BatchTune)]),
+    "vio_batch_autotune": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
+                                            ctypes.POINTER(ctypes.c_float)]),
+    "vio_batch_reset_stream": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32,
+                                                ctypes.c_int32, ctypes.c_void_p]),
+    "vio_batch_get_view": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32,
+                                            ctypes.POINTER(FrontendView), ctypes.c_void_p]),
+    "vio_batch_launches_per_step": (ctypes.c_int32, [ctypes.c_void_p]),
 }
 
 STAGES = ("front", "pyramid_upper", "track", "finalize")
@@ -428,3 +453,104 @@ def _alias(ptr: int, shape, dtype, device) -> torch.Tensor:
         }
     raw = torch.as_tensor(_Holder(), device=device)
     return raw.view(dtype).view(*shape)
+
+
+class Batch:
+    """vio_batch: stereo streams of mixed sizes stepped together (size groups).
+
+    groups: list of (params, w, h, n_streams, capacity)."""
+
+    def __init__(self, groups):
+        arr = (StreamGroup * len(groups))()
+        for i, (p, w, h, n, cap) in enumerate(groups):
+            arr[i].params = p
+            arr[i].w, arr[i].h, arr[i].n_streams, arr[i].capacity = w, h, n, cap
+        self.groups = [(w, h, n, cap) for (_, w, h, n, cap) in groups]
+        self.total = sum(g[2] for g in self.groups)
+        hdl = ctypes.c_void_p()
+        _check(load().vio_batch_create(ctypes.byref(hdl), arr, len(groups)), "vio_batch_create")
+        self.handle = hdl
+
+    def close(self):
+        if self.handle:
+            load().vio_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def next_frame(self, g: int, s: int) -> torch.Tensor:
+        """Device view (2, h, w) uint8 of the slot stream s of group g reads next."""
+        ptr = ctypes.c_void_p()
+        _check(load().vio_batch_next_frame(self.handle, g, s, ctypes.byref(ptr)), "next_frame")
+        w, h, _, _ = self.groups[g]
+        dev = torch.device("cuda", torch.cuda.current_device())
+        return _alias(ptr.value, (2, h, w), torch.uint8, dev)
+
+    def step(self, active=None, stream=None):
+        if active is None:
+            arg = None
+        else:
+            import numpy as np
+            a = np.ascontiguousarray(active, dtype=np.int32)
+            if a.size != self.total:
+                raise ValueError("one activity flag per stream")
+            arg = a.ctypes.data_as(ctypes.c_void_p)
+            self._keep = a
+        _check(load().vio_batch_step(self.handle, arg, _stream(stream)), "vio_batch_step")
+
+    def set_graph(self, enable: bool):
+        _check(load().vio_batch_set_graph(self.handle, 1 if enable else 0), "set_graph")
+
+    def set_tune(self, k2_threads: int, pyr_tile_shift: int):
+        t = BatchTune(k2_threads, pyr_tile_shift)
+        _check(load().vio_batch_set_tune(self.handle, ctypes.byref(t)), "set_tune")
+
+    def get_tune(self) -> tuple[int, int]:
+        t = BatchTune()
+        _check(load().vio_batch_get_tune(self.handle, ctypes.byref(t)), "get_tune")
+        return t.k2_threads, t.pyr_tile_shift
+
+    def autotune(self, reps: int = 3, stream=None) -> float:
+        ms = ctypes.c_float()
+        _check(load().vio_batch_autotune(self.handle, reps, _stream(stream), ctypes.byref(ms)),
+               "vio_batch_autotune")
+        return float(ms.value)
+
+    def reset_stream(self, g: int, s: int, stream=None):
+        _check(load().vio_batch_reset_stream(self.handle, g, s, _stream(stream)), "reset")
+
+    def launches_per_step(self) -> int:
+        return int(load().vio_batch_launches_per_step(self.handle))
+
+    def view(self, g: int) -> dict:
+        """Device tensors of group g's lists; 'parity' selects each stream's
+        current lists: track_xy[parity[s], s, c]."""
+        import numpy as np
+        v = FrontendView()
+        _, _, n, cap = self.groups[g]
+        par = np.zeros(n, np.int32)
+        _check(load().vio_batch_get_view(self.handle, g, ctypes.byref(v),
+                                         par.ctypes.data_as(ctypes.c_void_p)), "get_view")
+        dev = torch.device("cuda", torch.cuda.current_device())
+        return {
+            "track_xy": _alias(v.d_track_xy, (2, n, 2, cap, 2), torch.float32, dev),
+            "track_id": _alias(v.d_track_id, (2, n, 2, cap), torch.int32, dev),
+            "track_status": _alias(v.d_track_status, (2, n, 2, cap), torch.uint8, dev),
+            "track_count": _alias(v.d_track_count, (2, n, 2), torch.int32, dev),
+            "new_xy": _alias(v.d_new_xy, (n, cap, 2), torch.float32, dev),
+            "new_count": _alias(v.d_new_count, (n,), torch.int32, dev),
+            "parity": par,
+        }
+
+    def stream_lists(self, g: int, s: int):
+        """(xy list per camera, id list per camera) of stream s of group g (host numpy)."""
+        v = self.view(g)
+        q = int(v["parity"][s])
+        cnt = v["track_count"][q, s].cpu().numpy()
+        xy = [v["track_xy"][q, s, c, : cnt[c]].cpu().numpy() for c in range(2)]
+        ids = [v["track_id"][q, s, c, : cnt[c]].cpu().numpy() for c in range(2)]
+        return xy, ids

@@ -1,0 +1,136 @@
+"""Batched multi-stream frontend (mixed sizes, per-stream state, graph
+replay, autotuner): every stream's result in the batch equals the same
+stream run alone through vio_frontend on the same frames, bit for bit."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2609_30459_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+vio = pytest.importorskip("paper_2609_30459_gb300.vio")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    vio.load(build=True)
+
+
+GROUPS = [  # w, h, n_streams, cell, levels
+    (376, 240, 2, 37, 4),
+    (320, 256, 3, 40, 3),
+]
+N_FRAMES = 5
+
+
+def _make():
+    seqs, groups = [], []
+    for gi, (w, h, n, cell, L) in enumerate(GROUPS):
+        p = vio.default_params(n_levels=L, cell_w=cell, cell_h=cell)
+        cap = 2 * (w // cell) * (h // cell)
+        groups.append((p, w, h, n, cap))
+        seqs.append([synth.make_sequence(6000 + 10 * gi + s, N_FRAMES, w, h, 1,
+                                         max_motion=6.0, tex_size=1024).frames
+                     for s in range(n)])
+    return groups, seqs
+
+
+def _alone(p, w, h, cap, frames, steps):
+    """Lists of one stream run alone over frames[t] for t in steps."""
+    fe = vio.Frontend(p, w, h, 1, cap)
+    keep = []
+    for t in steps:
+        f = torch.from_numpy(frames[t]).cuda().view(1, 2, h, w)
+        keep.append(f)
+        fe.step(f)
+    torch.cuda.synchronize()
+    v = fe.view()
+    cnt = v["track_count"][0].cpu().numpy()
+    out = ([v["track_xy"][0, c, : cnt[c]].cpu().numpy() for c in range(2)],
+           [v["track_id"][0, c, : cnt[c]].cpu().numpy() for c in range(2)])
+    fe.close()
+    return out
+
+
+def _run_batch(b, seqs, schedule, stream=None):
+    """schedule: list of activity lists (one flag per stream, groups in order)."""
+    t_of = [[0] * len(g) for g in seqs]
+    for act in schedule:
+        k = 0
+        for gi, g in enumerate(seqs):
+            for s in range(len(g)):
+                if act[k]:
+                    b.next_frame(gi, s).copy_(torch.from_numpy(g[s][t_of[gi][s]]).cuda())
+                    t_of[gi][s] += 1
+                k += 1
+        b.step(act, stream=stream)
+    torch.cuda.synchronize()
+
+
+def _check_equal(b, groups, seqs, schedule):
+    k = 0
+    for gi, (p, w, h, n, cap) in enumerate(groups):
+        for s in range(n):
+            steps = [i for i, act in enumerate(schedule) if act[k]]
+            ref_xy, ref_id = _alone(p, w, h, cap, seqs[gi][s], range(len(steps)))
+            xy, ids = b.stream_lists(gi, s)
+            for c in range(2):
+                assert np.array_equal(ids[c], ref_id[c]), (gi, s, c)
+                assert np.array_equal(xy[c], ref_xy[c]), (gi, s, c)
+            assert len(ids[0]) > 0
+            k += 1
+
+
+def test_batch_equals_streams_alone():
+    groups, seqs = _make()
+    b = vio.Batch(groups)
+    total = sum(g[3] for g in groups)
+    schedule = [[1] * total for _ in range(N_FRAMES)]
+    _run_batch(b, seqs, schedule)
+    _check_equal(b, groups, seqs, schedule)
+
+
+def test_batch_skipped_streams_keep_their_state():
+    groups, seqs = _make()
+    b = vio.Batch(groups)
+    rng = np.random.default_rng(0)
+    total = sum(g[3] for g in groups)
+    schedule = [[1] * total] + [list((rng.random(total) < 0.6).astype(int)) for _ in range(6)]
+    # at most N_FRAMES active steps per stream
+    for k in range(total):
+        n_act = 0
+        for act in schedule:
+            if act[k]:
+                n_act += 1
+                if n_act > N_FRAMES:
+                    act[k] = 0
+    _run_batch(b, seqs, schedule)
+    _check_equal(b, groups, seqs, schedule)
+
+
+def test_batch_graph_replay_and_autotune():
+    groups, seqs = _make()
+    total = sum(g[3] for g in groups)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        b = vio.Batch(groups)
+        # frames in both slots for the autotuner
+        for gi, g in enumerate(seqs):
+            for st in range(len(g)):
+                for t in range(2):
+                    b.next_frame(gi, st).copy_(torch.from_numpy(g[st][t]).cuda())
+                    b.step([1 if (i == sum(x[3] for x in groups[:gi]) + st) else 0
+                            for i in range(total)], stream=s)
+        best = b.autotune(reps=1, stream=s)
+        assert best > 0
+        k2, shift = b.get_tune()
+        assert k2 in (64, 128, 256, 512) and shift in (-1, 0, 1)
+        b.set_graph(True)
+        schedule = [[1] * total for _ in range(N_FRAMES)]
+        _run_batch(b, seqs, schedule, stream=s)
+    s.synchronize()
+    _check_equal(b, groups, seqs, schedule)
+    assert b.launches_per_step() == 3
