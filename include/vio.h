@@ -199,8 +199,11 @@ vio_status vio_detect_grid_noalloc(const vio_params* p, const vio_pyr_layout* la
                                    int16_t* d_score, int32_t* d_count, int32_t capacity,
                                    void* stream);
 
-/* Flags of vio_track_patches. */
+/* Flags of vio_track_patches: VIO_TRACK_FORWARD or VIO_TRACK_WITH_FB, or'ed
+ * with VIO_TRACK_FROM_LEVEL(l) to track over levels l..0 only (both
+ * directions) instead of the whole pyramid; l < n_levels. */
 enum { VIO_TRACK_FORWARD = 0, VIO_TRACK_WITH_FB = 1 };
+#define VIO_TRACK_FROM_LEVEL(l) (((l) + 1) << 4)
 
 /* Sec. III-E, Eq. 4-5: pyramidal inverse-compositional KLT of 52-point
  * patches with an SE(2) warp (t_x, t_y, theta), coarse to fine, gn_iters
@@ -306,15 +309,16 @@ int32_t vio_frontend_launches_per_step(const vio_frontend* fe);
 
 /* Stage timing (the paper's per-stage GPU timestamps, Sec. IV-B, Fig. 5).
  * While enabled, every step records CUDA events on its stream at the stage
- * boundaries: 0 pyramid levels 1-2 and the per-cell detection candidates
- * (one launch), 1 deeper pyramid levels, 2 temporal tracking and stereo
- * matching (one launch), 3 finalisation (survivors, per-cell selection,
- * appends). vio_frontend_read_timing waits for the recorded events, adds each
- * stage's elapsed milliseconds into stage_ms[0..3] (overwritten), stores the
- * number of timed steps in *n_steps and clears the record. Enabling,
+ * boundaries: 0 pyramid levels 1-4 and the per-cell detection candidates
+ * (one launch), 1 deeper pyramid levels, 2 learned flow proposals (when the
+ * initializer is on), 3 temporal tracking and stereo matching (one launch),
+ * 4 finalisation (survivors, per-cell selection, appends).
+ * vio_frontend_read_timing waits for the recorded events, adds each stage's
+ * elapsed milliseconds into stage_ms[0..VIO_N_STAGES-1] (overwritten), stores
+ * the number of timed steps in *n_steps and clears the record. Enabling,
  * disabling and reading are host calls. */
-enum { VIO_STAGE_FRONT = 0, VIO_STAGE_PYRAMID_UPPER, VIO_STAGE_TRACK, VIO_STAGE_FINALIZE,
-       VIO_N_STAGES };
+enum { VIO_STAGE_FRONT = 0, VIO_STAGE_PYRAMID_UPPER, VIO_STAGE_INITNET, VIO_STAGE_TRACK,
+       VIO_STAGE_FINALIZE, VIO_N_STAGES };
 vio_status vio_frontend_set_timing(vio_frontend* fe, int32_t enable);
 /* step_ms (may be NULL): per timed step, the time from its first to its last
  * event, for up to step_ms_cap steps in order. */
@@ -325,15 +329,38 @@ vio_status vio_frontend_read_timing(vio_frontend* fe, double* stage_ms, int64_t*
  * VIO_STATS_RING entries (entry = step index mod the ring size), per stream,
  * VIO_N_STATS int32 values: tracks attempted on cam0 and cam1, tracks that
  * survived on cam0 and cam1, new detections, successful stereo matches of the
- * new detections, and detection candidates stereo-matched (every cell's top-k
- * is matched while temporal tracking runs; the selection uses a subset).
+ * new detections, detection candidates stereo-matched (every cell's top-k is
+ * matched while temporal tracking runs; the selection uses a subset), and
+ * surviving tracks (both cameras) that were tracked from the learned
+ * initializer's proposal rather than by the plain fallback.
  * vio_frontend_read_stats copies the whole ring to host_out (blocking; size
  * VIO_STATS_RING * n_streams * VIO_N_STATS) and returns the number of steps
  * run since create in *n_steps. */
 #define VIO_STATS_RING 4096
 enum { VIO_STAT_TRK0 = 0, VIO_STAT_TRK1, VIO_STAT_OK0, VIO_STAT_OK1, VIO_STAT_NEW,
-       VIO_STAT_MATCHED, VIO_STAT_CAND, VIO_N_STATS };
+       VIO_STAT_MATCHED, VIO_STAT_CAND, VIO_STAT_LEARNED, VIO_N_STATS };
 vio_status vio_frontend_read_stats(vio_frontend* fe, int32_t* host_out, int64_t* n_steps);
+
+/* Learned start of temporal tracking (an addition; the paper starts from a
+ * camera-model prediction, Sec. III-E). When on, every step runs the flow
+ * network (vio_initnet_*) on each keypoint to be tracked, between its
+ * previous and current frame of the same camera, before tracking. A keypoint
+ * whose proposal has confidence >= min_conf is tracked, with the
+ * forward-backward check, over levels start_level..0 only, from p + flow; if
+ * that track does not end VIO_TRACK_OK, or the confidence is lower, the
+ * keypoint is tracked exactly as without the network (whole pyramid, start
+ * at p). Stereo matching is unchanged. d_packed: the packed weights
+ * (vio_initnet_pack, 16-byte aligned), read by every step and owned by the
+ * caller, which keeps them alive while the initializer is on; NULL turns it
+ * off. Levels must lie below n_levels. */
+typedef struct {
+  int32_t level_a, level_b;  /* pyramid levels of the network input          */
+  int32_t start_level;       /* LK levels tracked from the proposal          */
+  float min_conf;            /* confidence gate                              */
+} vio_initnet_cfg;
+
+vio_status vio_frontend_set_initnet(vio_frontend* fe, const void* d_packed,
+                                    const vio_initnet_cfg* cfg);
 
 /* --------------------------------------------------------------- batch -- */
 /* Many stereo streams of mixed sizes in one step (the frontend of Sec. III-B
@@ -397,6 +424,74 @@ vio_status vio_batch_reset_stream(vio_batch* b, int32_t g, int32_t s, void* stre
 vio_status vio_batch_get_view(vio_batch* b, int32_t g, vio_frontend_view* out,
                               int32_t* parity);
 int32_t vio_batch_launches_per_step(const vio_batch* b);
+
+/* vio_frontend_set_initnet for every stream of the batch (one network and
+ * configuration for all groups; every group needs the levels). Captured
+ * graphs are re-captured at the next graph step. */
+vio_status vio_batch_set_initnet(vio_batch* b, const void* d_packed, const vio_initnet_cfg* cfg);
+
+
+/* ---------------------------------------------------------------------------
+ * Learned flow initializer. Not in the paper: its tracker starts each
+ * keypoint from a position predicted through the camera model and the pose
+ * (Sec. III-E); without that prediction, the starting point of a large motion
+ * is where a plain zero start fails. This small network proposes the start:
+ *
+ *   input  4 x 16 x 16: source and target patch at pyramid levels a and b,
+ *          16 x 16 integer grid from floor(p / 2^l + 0.5) - 8, value
+ *          (v - 128) / 64, 0 outside the level;
+ *   conv   3 x (3x3, stride 2, zero padding 1, 32 channels, ReLU),
+ *          16 -> 8 -> 4 -> 2;
+ *   fc     flatten (channel, row, column) 128 -> 64 + ReLU -> 3;
+ *   output flow = 16 px * (o0, o1) (level-0 pixels), confidence = sigmoid(o2);
+ *   loss   (o0 - fx/16)^2 + (o1 - fy/16)^2 + BCE(sigmoid(o2), y), y = 1 when
+ *          the predicted flow is within 1 px of the target (no gradient
+ *          through y); the batch loss is the mean.
+ *
+ * Parameters: FP32 master vector of VIO_INITNET_N_PARAMS floats in the order
+ * w1 (32,4,3,3), b1, w2 (32,32,3,3), b2, w3 (32,32,3,3), b3, w4 (64,128), b4,
+ * w5 (3,64), b5 (row-major). Inference and the training forward pass run on
+ * a packed copy (VIO_INITNET_PACKED_BYTES, 16-byte aligned): BF16 weights and
+ * FP32 biases, written by vio_initnet_pack. Activations are BF16 between
+ * layers, accumulation is FP32. Inputs x are BF16 bit patterns (uint16),
+ * [n][4][16][16]. All calls are enqueued on `stream`; pointers are device
+ * pointers owned by the caller.
+ * ------------------------------------------------------------------------- */
+#define VIO_INITNET_N_PARAMS 28131
+#define VIO_INITNET_PACKED_BYTES 58016
+
+vio_status vio_initnet_pack(const float* d_master, void* d_packed, void* stream);
+
+/* Network inputs of n_images x capacity keypoints: image i's points at
+ * d_pts[2*(i*capacity + k)] (level-0 x, y), its count at d_count[i] (NULL =
+ * all capacity); `src` and `dst` are pyramids of one layout with n_images
+ * each; point k of image i reads src image i and dst image i. Rows beyond
+ * the count are zero. d_x: [n_images*capacity][4][16][16] bf16. */
+vio_status vio_initnet_extract(const vio_pyr_layout* layout, const vio_pyr_batch* src,
+                               const vio_pyr_batch* dst, const float* d_pts,
+                               const int32_t* d_count, int32_t capacity, int32_t level_a,
+                               int32_t level_b, uint16_t* d_x, void* stream);
+
+/* d_out[3*i..3*i+2] = (dx, dy, confidence) of input i, i < n. */
+vio_status vio_initnet_forward(const void* d_packed, const uint16_t* d_x, int32_t n,
+                               float* d_out, void* stream);
+
+/* Adds grad_scale * (sum over the n samples d_index[0..n-1] (NULL = 0..n-1)
+ * of dL_i/dparams) to d_grad (VIO_INITNET_N_PARAMS floats, gradient with
+ * respect to the master parameters through the BF16 packing taken as the
+ * identity) and the sum of the n losses to *d_loss. Targets: d_flow[2*j] =
+ * (fx, fy) of sample j in level-0 pixels. The caller zeroes d_grad and
+ * d_loss first. The forward pass is that of vio_initnet_forward. */
+vio_status vio_initnet_train_step(const void* d_packed, const uint16_t* d_x,
+                                  const float* d_flow, const int32_t* d_index, int32_t n,
+                                  float grad_scale, float* d_grad, float* d_loss, void* stream);
+
+/* Adam (Kingma and Ba, 2015) on the master parameters, step t >= 1:
+ * m = b1 m + (1-b1) g; v = b2 v + (1-b2) g^2;
+ * w -= lr (m / (1-b1^t)) / (sqrt(v / (1-b2^t)) + eps). */
+vio_status vio_initnet_adam(float* d_master, const float* d_grad, float* d_m, float* d_v,
+                            int32_t step, float lr, float beta1, float beta2, float eps,
+                            void* stream);
 
 #ifdef __cplusplus
 }

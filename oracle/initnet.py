@@ -15,6 +15,13 @@ oracle states plainly, in FP64, for the GPU forward and gradient checks:
 * loss per sample: (o0 - fx/S)^2 + (o1 - fy/S)^2 + BCE(sigmoid(o2), y) with
   y = 1 if the predicted flow is within 1 px of the target (y carries no
   gradient); the batch loss is the mean.
+
+Precision: the network's weights and inputs are BF16 values and its
+activations are stored as BF16 between layers (accumulation wider). The
+oracle computes in FP64 on weights the caller rounds with ``bf16_round``;
+``forward(..., act_bf16=True)`` also rounds each stored activation to BF16, so
+that decisions taken on the outputs (the confidence gate) are taken in the
+network's own precision.
 """
 from __future__ import annotations
 
@@ -42,6 +49,16 @@ def unflatten(flat: np.ndarray) -> dict:
 
 def flatten(p: dict) -> np.ndarray:
     return np.concatenate([np.asarray(p[k], np.float64).reshape(-1) for k in ORDER])
+
+
+def bf16_round(a) -> np.ndarray:
+    """Nearest BF16 value (ties to even) of each element, via float32: BF16 is
+    the upper 16 bits of an IEEE binary32, so rounding adds 0x7fff plus the
+    lowest kept bit to the bit pattern and clears the low 16 bits."""
+    f = np.ascontiguousarray(a, np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
 
 
 def conv_s2(x, w, b):
@@ -80,17 +97,18 @@ def sigmoid(z):
     return 1.0 / (1.0 + np.exp(-z))
 
 
-def forward(p: dict, x: np.ndarray, keep: bool = False):
+def forward(p: dict, x: np.ndarray, keep: bool = False, act_bf16: bool = False):
     """x: (4, 16, 16). Returns o (3,) and, if keep, the activations."""
+    q = bf16_round if act_bf16 else (lambda v: v)
     a1 = conv_s2(x, p["w1"], p["b1"])
-    h1 = np.maximum(a1, 0)
+    h1 = q(np.maximum(a1, 0))
     a2 = conv_s2(h1, p["w2"], p["b2"])
-    h2 = np.maximum(a2, 0)
+    h2 = q(np.maximum(a2, 0))
     a3 = conv_s2(h2, p["w3"], p["b3"])
-    h3 = np.maximum(a3, 0)
+    h3 = q(np.maximum(a3, 0))
     f = h3.reshape(-1)
     a4 = p["w4"] @ f + p["b4"]
-    h4 = np.maximum(a4, 0)
+    h4 = q(np.maximum(a4, 0))
     o = p["w5"] @ h4 + p["b5"]
     if keep:
         return o, dict(x=x, a1=a1, h1=h1, a2=a2, h2=h2, a3=a3, h3=h3, f=f, a4=a4, h4=h4)
@@ -132,12 +150,12 @@ def backward(p: dict, act: dict, do: np.ndarray) -> dict:
     return g
 
 
-def batch_loss_grad(p: dict, xs: np.ndarray, flows: np.ndarray):
+def batch_loss_grad(p: dict, xs: np.ndarray, flows: np.ndarray, act_bf16: bool = False):
     """Mean loss and gradient (dict) over a batch."""
     total = 0.0
     acc = {k: np.zeros(SHAPES[k]) for k in ORDER}
     for x, f in zip(xs, flows):
-        o, act = forward(p, x, keep=True)
+        o, act = forward(p, x, keep=True, act_bf16=act_bf16)
         loss, do = loss_and_grad_out(o, f)
         total += loss
         g = backward(p, act, do)

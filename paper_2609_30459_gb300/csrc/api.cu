@@ -223,8 +223,12 @@ extern "C" vio_status vio_track_patches(vio_ctx* ctx, const vio_pyr_layout* layo
     return VIO_ERR_INVALID_ARG;
   if (src->n_images != dst->n_images || !d_pts || !d_out || !d_status || capacity < 0)
     return VIO_ERR_INVALID_ARG;
-  if (flags != VIO_TRACK_FORWARD && flags != VIO_TRACK_WITH_FB) return VIO_ERR_INVALID_ARG;
-  vio::TrackCfg cfg{ctx->p.gn_iters, flags == VIO_TRACK_WITH_FB ? 1 : 0, ctx->p.fb_max_dist};
+  const int mode = flags & 0xf, from = (flags >> 4) & 0xf;
+  if ((mode != VIO_TRACK_FORWARD && mode != VIO_TRACK_WITH_FB) || (flags & ~0xff) ||
+      from > layout->n_levels)
+    return VIO_ERR_INVALID_ARG;
+  vio::TrackCfg cfg{ctx->p.gn_iters, mode == VIO_TRACK_WITH_FB ? 1 : 0, ctx->p.fb_max_dist,
+                    from - 1};
   return cuda_status(vio::launch_track(vio::make_geom(*layout), vio::make_batch(*src),
                                        vio::make_batch(*dst), d_pts, d_init, d_count, capacity,
                                        cfg, d_out, nullptr, d_status, d_fb_dist,
@@ -240,7 +244,7 @@ extern "C" vio_status vio_stereo_match(vio_ctx* ctx, const vio_pyr_layout* layou
     return VIO_ERR_INVALID_ARG;
   if (cam0->n_images != cam1->n_images || !d_pts || !d_match || !d_status || capacity < 0)
     return VIO_ERR_INVALID_ARG;
-  vio::TrackCfg cfg{ctx->p.gn_iters, 1, ctx->p.fb_max_dist};
+  vio::TrackCfg cfg{ctx->p.gn_iters, 1, ctx->p.fb_max_dist, -1};
   return cuda_status(vio::launch_track(vio::make_geom(*layout), vio::make_batch(*cam0),
                                        vio::make_batch(*cam1), d_pts, d_init, d_count, capacity,
                                        cfg, nullptr, d_match, d_status, d_fb_dist,

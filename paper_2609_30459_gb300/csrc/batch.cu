@@ -45,6 +45,8 @@ struct Group {
   int32_t* parity;
   int32_t* have_prev;
   int32_t* active;            // points into the batch's device mask
+  float* net_out;             // flow proposals, [stream][camera] x cap x 3
+  uint8_t* trk_learned;
   std::vector<int32_t> host_parity;
 };
 
@@ -62,6 +64,8 @@ struct vio_batch {
   cudaGraphExec_t graph[2];
   cudaEvent_t graph_done[2];
   bool graph_ready;
+  const void* net;            // packed initializer weights (null: off)
+  vio_initnet_cfg net_cfg;
 };
 
 namespace {
@@ -122,7 +126,18 @@ cudaError_t enqueue_step(vio_batch* b, const int32_t* h_mask, cudaStream_t s) {
   if (e != cudaSuccess) return e;
   vio::FrameLaunch fl[vio::kMaxGroups];
   const int n = (int)b->groups.size();
-  for (int i = 0; i < n; ++i) fl[i] = launch_of(b->groups[i]);
+  for (int i = 0; i < n; ++i) {
+    fl[i] = launch_of(b->groups[i]);
+    if (b->net) {
+      fl[i].net = b->net;
+      fl[i].net_la = b->net_cfg.level_a;
+      fl[i].net_lb = b->net_cfg.level_b;
+      fl[i].net_top = b->net_cfg.start_level;
+      fl[i].net_tau = b->net_cfg.min_conf;
+      fl[i].net_out = b->groups[i].net_out;
+      fl[i].trk_learned = b->groups[i].trk_learned;
+    }
+  }
   return vio::launch_frames(fl, n, b->tune, s, nullptr);
 }
 
@@ -186,7 +201,8 @@ extern "C" vio_status vio_batch_create(vio_batch** out, const vio_stream_group* 
                 ns * cap * 8, ns * 4, ns * 4,                  // new, next_id
                 (size_t)VIO_STATS_RING * ns * VIO_N_STATS * 4, // stats
                 16, ns * 4, ns * 4,                            // step_ctr, parity, have_prev
-                0, 0, 0, 0, 0, 0};
+                ns * 2 * cap * 12, ns * 2 * cap,               // net_out, trk_learned
+                0, 0, 0, 0};
     for (size_t v : sizes[i]) total += align256(v);
     b->total_streams += sp.n_streams;
   }
@@ -235,6 +251,8 @@ extern "C" vio_status vio_batch_create(vio_batch** out, const vio_stream_group* 
     G.step_ctr = (int32_t*)take(z[17]);
     G.parity = (int32_t*)take(z[18]);
     G.have_prev = (int32_t*)take(z[19]);
+    G.net_out = (float*)take(z[20]);
+    G.trk_learned = take(z[21]);
     G.host_parity.assign(G.spec.n_streams, 0);
   }
   b->d_active = (int32_t*)take((size_t)b->total_streams * 4);
@@ -259,6 +277,8 @@ extern "C" vio_status vio_batch_create(vio_batch** out, const vio_stream_group* 
   b->use_graph = false;
   b->graph_ready = false;
   b->graph_done[0] = b->graph_done[1] = nullptr;
+  b->net = nullptr;
+  b->net_cfg = vio_initnet_cfg{};
   if (cudaEventCreateWithFlags(&b->graph_done[0], cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&b->graph_done[1], cudaEventDisableTiming) != cudaSuccess ||
       cudaDeviceSynchronize() != cudaSuccess) {
@@ -450,5 +470,19 @@ extern "C" int32_t vio_batch_launches_per_step(const vio_batch* b) {
   if (!b) return 0;
   std::vector<vio::Geom> g;
   for (const auto& G : b->groups) g.push_back(vio::make_geom(G.layout));
-  return vio::frame_launches(g.data(), (int)g.size());
+  return vio::frame_launches(g.data(), (int)g.size(), b->net != nullptr);
+}
+
+extern "C" vio_status vio_batch_set_initnet(vio_batch* b, const void* d_packed,
+                                            const vio_initnet_cfg* cfg) {
+  if (!b) return VIO_ERR_INVALID_ARG;
+  if (d_packed) {
+    for (const auto& G : b->groups)
+      if (!vio::initnet_cfg_ok(cfg, G.spec.params.n_levels, d_packed))
+        return VIO_ERR_INVALID_ARG;
+    b->net_cfg = *cfg;
+  }
+  b->net = d_packed;
+  drop_graphs(b);
+  return VIO_OK;
 }

@@ -69,7 +69,12 @@ struct TrackCfg {
   int gn_iters;
   int fb;
   float fb_max_dist;
+  int top;            // first (coarsest) level tracked; -1 = n_levels - 1
 };
+
+__host__ __device__ inline int top_level(const TrackCfg& c, const Geom& g) {
+  return c.top < 0 ? g.n_levels - 1 : c.top;
+}
 
 }  // namespace vio
 

@@ -6,10 +6,16 @@
 //                           (one pyramid pass per tile) and, in the same
 //                           launch, the per-cell FAST/NMS top-k candidates of
 //                           camera 0. Levels beyond 4 follow as a further pass.
+//  KN frame_initnet_kernel  (only with the learned initializer) one warp per
+//                           live track of both cameras: network input from
+//                           the previous and current pyramids, forward pass
+//                           on the tensor cores -> flow proposal + confidence.
 //  K2 frame_track_kernel    one warp per keypoint: temporal tracking of every
 //                           live track of both cameras (previous -> current
-//                           pyramid) AND stereo matching (camera 0 -> 1) of
-//                           every cell's top-k candidates.
+//                           pyramid; from the proposal over the lower levels
+//                           when it is confident, the plain track otherwise
+//                           or when that fails) AND stereo matching (camera 0
+//                           -> 1) of every cell's top-k candidates.
 //  K3 frame_finalize_kernel one CTA per stream: keep the tracks that passed,
 //                           count them per cell, select per cell the first
 //                           k - count candidates (the detection of Sec. III-D
@@ -28,6 +34,7 @@
 // captured launch sequence serves any subset of streams.
 #include "detect_dev.cuh"
 #include "frame.cuh"
+#include "initnet_dev.cuh"
 #include "pyramid_dev.cuh"
 #include "track_dev.cuh"
 
@@ -113,6 +120,44 @@ struct MultiK2 {
   FrameLaunch f[kMaxGroups];
 };
 
+constexpr int KN_WARPS = 4;
+
+// Flow proposals of every live track (same warp numbering as the temporal
+// part of frame_track_kernel); each warp loops over keypoints, so its
+// activation buffers are cleared once.
+__global__ void __launch_bounds__(KN_WARPS * 32) frame_initnet_kernel(const __grid_constant__ MultiK2 mm) {
+  __shared__ __align__(16) uint8_t smem[KN_WARPS][net::WARP_SMEM];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  uint8_t* ws = smem[warp];
+  net::clear_warp_smem(ws, lane);
+  const long long total = mm.block_end[mm.n - 1];
+  for (long long w = (long long)blockIdx.x * KN_WARPS + warp; w < total;
+       w += (long long)gridDim.x * KN_WARPS) {
+    long long start;
+    const int gi = group_of(mm, w, start);
+    const FrameLaunch& f = mm.f[gi];
+    const long long wl = w - start;
+    const int list = (int)(wl / f.cap);
+    const int slot = (int)(wl - (long long)list * f.cap);
+    const int s = list >> 1, c = list & 1;
+    const StreamRef r = stream_ref(f, s);
+    if (!r.active || !r.have_prev) continue;
+    const long long in_list = ((long long)r.li * f.n_streams + s) * 2 + c;
+    if (slot >= f.list_count[in_list]) continue;
+    const long long src = in_list * f.cap + slot;
+    net::extract_warp(f.g, f.prev, r.prev_img + c, f.cur, r.cur_img + c, f.list_xy[2 * src],
+                      f.list_xy[2 * src + 1], f.net_la, f.net_lb, ws, lane);
+    float o[3];
+    net::forward_warp(net::packed(f.net), ws, lane, o);
+    if (lane == 0) {
+      f.net_out[3 * wl] = o[0] * net::kScale;
+      f.net_out[3 * wl + 1] = o[1] * net::kScale;
+      f.net_out[3 * wl + 2] = 1.f / (1.f + expf(-o[2]));
+    }
+    __syncwarp();
+  }
+}
+
 __global__ void frame_track_kernel(const __grid_constant__ MultiK2 mm) {
   const long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
@@ -122,7 +167,8 @@ __global__ void frame_track_kernel(const __grid_constant__ MultiK2 mm) {
   const FrameLaunch& f = mm.f[gi];
   const long long wl = w - start;
   const float qnan = __int_as_float(0x7fc00000);
-  const TrackCfg cfg{f.p.gn_iters, 1, f.p.fb_max_dist};
+  const TrackCfg cfg{f.p.gn_iters, 1, f.p.fb_max_dist, -1};
+  const int top = f.g.n_levels - 1;
   const long long n_temporal = 2LL * f.n_streams * f.cap;
   trk::Pos tf;
   float thf, dist;
@@ -139,10 +185,23 @@ __global__ void frame_track_kernel(const __grid_constant__ MultiK2 mm) {
       return;
     }
     const long long src = in_list * f.cap + slot;
-    const int st = trk::track_fb(f.g, f.prev, r.prev_img + c, f.cur, r.cur_img + c,
-                                 f.list_xy[2 * src], f.list_xy[2 * src + 1], nullptr, cfg, lane,
-                                 tf, thf, have, dist);
+    const float px = f.list_xy[2 * src], py = f.list_xy[2 * src + 1];
+    int st = VIO_TRACK_EMPTY;
+    bool learned = false;
+    if (f.net) {
+      const float* q = f.net_out + 3 * wl;
+      if (q[2] >= f.net_tau) {
+        st = trk::track_fb(f.g, f.prev, r.prev_img + c, f.cur, r.cur_img + c, px, py, true,
+                           px + q[0], py + q[1], 0.f, cfg, f.net_top, lane, tf, thf, have,
+                           dist);
+        learned = st == VIO_TRACK_OK;
+      }
+    }
+    if (!learned)
+      st = trk::track_fb(f.g, f.prev, r.prev_img + c, f.cur, r.cur_img + c, px, py, false,
+                         0.f, 0.f, 0.f, cfg, top, lane, tf, thf, have, dist);
     if (lane == 0) {
+      if (f.net) f.trk_learned[wl] = learned ? 1 : 0;
       f.trk_status[wl] = (uint8_t)st;
       f.trk_xy[2 * wl] = have ? (float)tf.ax + tf.dx : qnan;
       f.trk_xy[2 * wl + 1] = have ? (float)tf.ay + tf.dy : qnan;
@@ -165,8 +224,8 @@ __global__ void frame_track_kernel(const __grid_constant__ MultiK2 mm) {
   const unsigned long long key = f.cand[w2];
   const unsigned idx = ~(unsigned)(key & 0xffffffffu);
   const float x = (float)(idx % (unsigned)f.g.w[0]), y = (float)(idx / (unsigned)f.g.w[0]);
-  const int st = trk::track_fb(f.g, f.cur, r.cur_img, f.cur, r.cur_img + 1, x, y, nullptr, cfg,
-                               lane, tf, thf, have, dist);
+  const int st = trk::track_fb(f.g, f.cur, r.cur_img, f.cur, r.cur_img + 1, x, y, false, 0.f,
+                               0.f, 0.f, cfg, top, lane, tf, thf, have, dist);
   if (lane == 0) {
     f.spec_status[w2] = (uint8_t)st;
     f.spec_xy[2 * w2] = have ? (float)tf.ax + tf.dx : qnan;
@@ -241,7 +300,10 @@ __global__ void __launch_bounds__(K3_THREADS) frame_finalize_kernel(const __grid
     if (t < VIO_N_STATS) st[t] = 0;
     return;
   }
+  __shared__ int learned_s;
   for (int i = t; i < n_cells; i += K3_THREADS) occ_s[i] = 0;
+  if (t == 0) learned_s = 0;
+  __syncthreads();
 
   const long long in0 = (((long long)sr.li * f.n_streams + s) * 2) * cap;    // list in, camera 0
   const long long out0 = (((long long)sr.lo * f.n_streams + s) * 2) * cap;   // list out, camera 0
@@ -254,7 +316,7 @@ __global__ void __launch_bounds__(K3_THREADS) frame_finalize_kernel(const __grid
   const int n0 = sr.have_prev ? min(f.list_count[cnt_in], f.cap) : 0;
   const int n1 = sr.have_prev ? min(f.list_count[cnt_in + 1], f.cap) : 0;
   const int run = (max(n0, n1) + K3_THREADS - 1) / K3_THREADS;
-  int surv0 = 0, surv1 = 0;
+  int surv0 = 0, surv1 = 0, n_learned = 0;
   for (int r0 = 0; r0 < run; r0 += kRunMax) {
     const int rl = min(kRunMax, run - r0);
     const int first = t * run + r0;
@@ -263,6 +325,10 @@ __global__ void __launch_bounds__(K3_THREADS) frame_finalize_kernel(const __grid
       const int i = first + j;
       if (i < n0 && f.trk_status[trk0 + i] == VIO_TRACK_OK) keep0 |= 1u << j;
       if (i < n1 && f.trk_status[trk0 + cap + i] == VIO_TRACK_OK) keep1 |= 1u << j;
+      if (f.net) {
+        if (keep0 & (1u << j)) n_learned += f.trk_learned[trk0 + i];
+        if (keep1 & (1u << j)) n_learned += f.trk_learned[trk0 + cap + i];
+      }
     }
     int tot;
     const int ex = block_scan<int>(__popc(keep0) | (__popc(keep1) << 16), ws32, tot);
@@ -291,7 +357,8 @@ __global__ void __launch_bounds__(K3_THREADS) frame_finalize_kernel(const __grid
     surv1 += tot >> 16;
     __syncthreads();   // ws32 is reused by the next chunk
   }
-  __syncthreads();     // occupancy complete
+  if (n_learned) atomicAdd(&learned_s, n_learned);
+  __syncthreads();     // occupancy and learned_s complete
 
   // 2. per cell: selection (k_eff = k - occupancy), matched subset, and the
   //    candidates matched; three counts packed in 21-bit fields
@@ -372,6 +439,7 @@ __global__ void __launch_bounds__(K3_THREADS) frame_finalize_kernel(const __grid
     st[VIO_STAT_NEW] = new_tot;
     st[VIO_STAT_MATCHED] = m_tot;
     st[VIO_STAT_CAND] = c_tot;
+    st[VIO_STAT_LEARNED] = learned_s;
     if (f.slotted) {
       f.parity[s] = sr.lo;
       f.have_prev[s] = 1;
@@ -477,8 +545,31 @@ cudaError_t launch_frames(const FrameLaunch* fl, int n_groups, const FrameTune& 
     }
   }
 
-  // K2: temporal tracking + stereo matching of all candidates
+  // KN: flow proposals (every group has the initializer on, or none)
   mark(2);
+  if (fl[0].net) {
+    MultiK2 mn{};
+    mn.n = n_groups;
+    acc = 0;
+    for (int i = 0; i < n_groups; ++i) {
+      mn.f[i] = fl[i];
+      acc += 2LL * fl[i].n_streams * fl[i].cap;
+      mn.block_end[i] = acc;
+    }
+    static int sms = 0;
+    if (!sms) {
+      int dev = 0;
+      if (cudaGetDevice(&dev) != cudaSuccess ||
+          cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return cudaErrorUnknown;
+    }
+    const long long need = (acc + KN_WARPS - 1) / KN_WARPS;
+    const long long blocks = need < 4LL * sms ? need : 4LL * sms;
+    if (blocks > 0) frame_initnet_kernel<<<(unsigned)blocks, KN_WARPS * 32, 0, s>>>(mn);
+  }
+
+  // K2: temporal tracking + stereo matching of all candidates
+  mark(3);
   MultiK2 m2{};
   m2.n = n_groups;
   acc = 0;
@@ -496,7 +587,7 @@ cudaError_t launch_frames(const FrameLaunch* fl, int n_groups, const FrameTune& 
   }
 
   // K3: finalize
-  mark(3);
+  mark(4);
   MultiK3 m3{};
   m3.n = n_groups;
   acc = 0;
@@ -515,12 +606,12 @@ cudaError_t launch_frames(const FrameLaunch* fl, int n_groups, const FrameTune& 
     if (e != cudaSuccess) return e;
   }
   frame_finalize_kernel<<<(unsigned)acc, K3_THREADS, smem3, s>>>(m3);
-  mark(4);
+  mark(5);
   return cudaGetLastError();
 }
 
-int frame_launches(const Geom* g, int n_groups) {
-  int n = 3;                                   // K1, K2, K3
+int frame_launches(const Geom* g, int n_groups, bool with_net) {
+  int n = with_net ? 4 : 3;                    // K1, (KN), K2, K3
   for (int i = 0; i < n_groups; ++i)
     if (g[i].n_levels > 1 + pyr::kMaxPass) ++n;
   return n;

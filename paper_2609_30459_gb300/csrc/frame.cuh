@@ -45,6 +45,12 @@ struct FrameLaunch {
   uint8_t* occupancy;              // ns x cells
   int32_t* stats;                  // ring, VIO_STATS_RING x ns x VIO_N_STATS
   int32_t* step_ctr;               // incremented once per launch of the frame
+  // learned flow initializer of temporal tracking (net == null: off)
+  const void* net;                 // packed weights
+  int net_la, net_lb, net_top;
+  float net_tau;
+  float* net_out;                  // [stream][camera] x cap x (dx, dy, conf)
+  uint8_t* trk_learned;            // [stream][camera] x cap: 1 = tracked from the proposal
 };
 
 // Per-stream view of a FrameLaunch.
@@ -80,11 +86,22 @@ __host__ __device__ inline StreamRef stream_ref(const FrameLaunch& f, int s) {
 }
 
 // Enqueues one frame of every group on `s` (3 launches, plus one pyramid
-// pass per group for levels beyond 5). marks: 5 events recorded at the stage
-// boundaries (or null).
+// pass per group for levels beyond 5, plus the flow proposals when the
+// groups' initializer is on). marks: VIO_N_STAGES + 1 events recorded at the
+// stage boundaries (or null).
 cudaError_t launch_frames(const FrameLaunch* f, int n_groups, const FrameTune& tune,
                           cudaStream_t s, cudaEvent_t* marks);
-int frame_launches(const Geom* g, int n_groups);
+int frame_launches(const Geom* g, int n_groups, bool with_net);
+
+// Initializer configuration check: levels below n_levels, a finite gate,
+// 16-byte aligned weights.
+inline bool initnet_cfg_ok(const vio_initnet_cfg* c, int n_levels, const void* packed) {
+  if (!c || ((uintptr_t)packed & 15)) return false;
+  if (c->level_a < 0 || c->level_b < 0 || c->start_level < 0) return false;
+  if (c->level_a >= n_levels || c->level_b >= n_levels || c->start_level >= n_levels)
+    return false;
+  return c->min_conf == c->min_conf;   // not NaN
+}
 int frame_front_smem(const Geom& g, const vio_params& p, int tile_shift);
 // Fused pyramid (levels 1-4) and per-cell detection candidates of every
 // det_step-th image of `all`, one launch.

@@ -40,6 +40,10 @@ struct vio_frontend {
   int32_t* next_id;           // n_streams
   int32_t* stats;             // VIO_STATS_RING * n_streams * VIO_N_STATS
   int32_t* step_ctr;          // device count of launched steps
+  float* net_out;             // flow proposals, [stream][camera] x capacity x 3
+  uint8_t* trk_learned;       // per slot: tracked from the proposal
+  const void* net;            // packed initializer weights (null: off)
+  vio_initnet_cfg net_cfg;
   // host state
   int cur_list;
   int cur_pyr;
@@ -117,8 +121,8 @@ extern "C" vio_status vio_frontend_create(vio_frontend** out, const vio_params* 
       2 * nl * 4,                                               // 4 list_count
       2 * slots,                                                // 5 list_status
       16,                                                       // 6 step_ctr
-      16,                                                       // 7 (spare)
-      16,                                                       // 8 (spare)
+      slots * 12,                                               // 7 net_out
+      slots,                                                    // 8 trk_learned
       slots * 8, slots,                                         // 9-10 trk
       ns * nc * kk * 8, ns * nc * 4,                            // 11-12 cand
       ns * nc * kk * 8, ns * nc * kk,                           // 13-14 spec
@@ -147,6 +151,10 @@ extern "C" vio_status vio_frontend_create(vio_frontend** out, const vio_params* 
   fe->list_count = (int32_t*)ptrs[4];
   fe->list_status = (uint8_t*)ptrs[5];
   fe->step_ctr = (int32_t*)ptrs[6];
+  fe->net_out = (float*)ptrs[7];
+  fe->trk_learned = (uint8_t*)ptrs[8];
+  fe->net = nullptr;
+  fe->net_cfg = vio_initnet_cfg{};
   fe->trk_xy = (float*)ptrs[9];
   fe->trk_status = (uint8_t*)ptrs[10];
   fe->cand = (unsigned long long*)ptrs[11];
@@ -204,7 +212,18 @@ extern "C" int32_t vio_frontend_launches_per_step(const vio_frontend* fe) {
   vio_pyr_layout L;
   if (vio_pyr_layout_make(fe->w, fe->h, fe->p.n_levels, fe->w, &L) != VIO_OK) return 0;
   const vio::Geom g = vio::make_geom(L);
-  return vio::frame_launches(&g, 1);
+  return vio::frame_launches(&g, 1, fe->net != nullptr);
+}
+
+extern "C" vio_status vio_frontend_set_initnet(vio_frontend* fe, const void* d_packed,
+                                               const vio_initnet_cfg* cfg) {
+  if (!fe) return VIO_ERR_INVALID_ARG;
+  if (d_packed) {
+    if (!vio::initnet_cfg_ok(cfg, fe->p.n_levels, d_packed)) return VIO_ERR_INVALID_ARG;
+    fe->net_cfg = *cfg;
+  }
+  fe->net = d_packed;
+  return VIO_OK;
 }
 
 extern "C" vio_status vio_frontend_step(vio_frontend* fe, const uint8_t* d_frames,
@@ -254,6 +273,15 @@ extern "C" vio_status vio_frontend_step(vio_frontend* fe, const uint8_t* d_frame
   f.occupancy = fe->occupancy;
   f.stats = fe->stats;
   f.step_ctr = fe->step_ctr;
+  if (fe->net) {
+    f.net = fe->net;
+    f.net_la = fe->net_cfg.level_a;
+    f.net_lb = fe->net_cfg.level_b;
+    f.net_top = fe->net_cfg.start_level;
+    f.net_tau = fe->net_cfg.min_conf;
+    f.net_out = fe->net_out;
+    f.trk_learned = fe->trk_learned;
+  }
   const FrameTune tune{128, 0};
   if (launch_frames(&f, 1, tune, s, fe->timing ? ev.data() : nullptr) != cudaSuccess)
     return VIO_ERR_CUDA;

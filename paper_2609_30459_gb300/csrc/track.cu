@@ -43,9 +43,11 @@ __global__ void __launch_bounds__(TRK_THREADS) track_kernel(TrackArgs a) {
   trk::Pos tf;
   float thf = 0.f, dist;
   bool have;
+  const bool hi = a.init != nullptr;
   const int st = trk::track_fb(a.g, a.src, img, a.dst, img, a.pts[2 * wid], a.pts[2 * wid + 1],
-                               a.init ? a.init + 3 * wid : nullptr, a.cfg, lane, tf, thf, have,
-                               dist);
+                               hi, hi ? a.init[3 * wid] : 0.f, hi ? a.init[3 * wid + 1] : 0.f,
+                               hi ? a.init[3 * wid + 2] : 0.f, a.cfg, top_level(a.cfg, a.g),
+                               lane, tf, thf, have, dist);
   if (lane == 0) {
     a.status[wid] = (uint8_t)st;
     const float ox = have ? (float)tf.ax + tf.dx : nanf_;

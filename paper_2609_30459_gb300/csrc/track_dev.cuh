@@ -381,16 +381,16 @@ __device__ __forceinline__ Lv get_lv(const Geom& g, const Batch& b, int img, int
 
 // Coarse-to-fine tracking of keypoint p (anchor form) of image src_img of the
 // source batch into image dst_img of the target batch, from warp (t0, th0) at
-// level 0. A level whose template is invalid is skipped, except level 0; any
-// warp failure ends the track.
+// level 0, over levels top..0 (top = n_levels - 1 is the whole pyramid). A
+// level whose template is invalid is skipped, except level 0; any warp
+// failure ends the track.
 __device__ __forceinline__ int track_dir(const Geom& g, const Batch& src, int src_img,
                                          const Batch& dst, int dst_img, const Pos& p, Pos t0,
-                                         float th0, int iters, int lane, Pos& t_out,
+                                         float th0, int iters, int top, int lane, Pos& t_out,
                                          float& th_out) {
-  const int L = g.n_levels;
   Warp W;
-  to_level1(t0.ax, t0.dx, L - 1, W.t.ax, W.t.dx);
-  to_level1(t0.ay, t0.dy, L - 1, W.t.ay, W.t.dy);
+  to_level1(t0.ax, t0.dx, top, W.t.ax, W.t.dx);
+  to_level1(t0.ay, t0.dy, top, W.t.ay, W.t.dy);
   W.th = th0;
   {
     float a, b;
@@ -398,7 +398,7 @@ __device__ __forceinline__ int track_dir(const Geom& g, const Batch& src, int sr
   }
   const LanePts P = lane_points(lane);
   Tpl T;
-  for (int l = L - 1; l >= 0; --l) {
+  for (int l = top; l >= 0; --l) {
     const int ts = build_template(get_lv(g, src, src_img, l), p, l, lane, P, T);
     if (ts != VIO_TRACK_OK) {
       if (l == 0) return ts;
@@ -423,20 +423,23 @@ __device__ __forceinline__ int track_dir(const Geom& g, const Batch& src, int sr
   return VIO_TRACK_OK;
 }
 
-// Forward track with the optional backward pass and distance check.
-// Returns the status; tf/thf hold the forward result when it exists.
+// Forward track with the optional backward pass and distance check, both
+// over levels top..0, from warp (ix, iy, ith) if has_init, else from p. Returns the status; tf/thf hold the forward result when
+// it exists.
 __device__ __forceinline__ int track_fb(const Geom& g, const Batch& src, int src_img,
                                         const Batch& dst, int dst_img, float px, float py,
-                                        const float* init3, const TrackCfg& cfg, int lane,
-                                        Pos& tf, float& thf, bool& have, float& dist) {
+                                        bool has_init, float ix, float iy, float ith,
+                                        const TrackCfg& cfg, int top, int lane, Pos& tf,
+                                        float& thf, bool& have, float& dist) {
   const Pos p = split(px, py);
   Pos t0 = p;
   float th0 = 0.f;
-  if (init3) {
-    t0 = split(init3[0], init3[1]);
-    th0 = init3[2];
+  if (has_init) {
+    t0 = split(ix, iy);
+    th0 = ith;
   }
-  int st = track_dir(g, src, src_img, dst, dst_img, p, t0, th0, cfg.gn_iters, lane, tf, thf);
+  int st = track_dir(g, src, src_img, dst, dst_img, p, t0, th0, cfg.gn_iters, top, lane, tf,
+                     thf);
   have = st == VIO_TRACK_OK;
   dist = __int_as_float(0x7fc00000);
   if (st == VIO_TRACK_OK && cfg.fb) {
@@ -444,7 +447,8 @@ __device__ __forceinline__ int track_fb(const Geom& g, const Batch& src, int src
     // start at the forward estimate's inverse (t = p, theta = -theta_f)
     Pos tb;
     float thb;
-    st = track_dir(g, dst, dst_img, src, src_img, tf, p, -thf, cfg.gn_iters, lane, tb, thb);
+    st = track_dir(g, dst, dst_img, src, src_img, tf, p, -thf, cfg.gn_iters, top, lane, tb,
+                   thb);
     if (st == VIO_TRACK_OK) {
       const float ex = (float)(tb.ax - p.ax) + (tb.dx - p.dx);
       const float ey = (float)(tb.ay - p.ay) + (tb.dy - p.dy);

@@ -61,6 +61,11 @@ class BatchTune(ctypes.Structure):
     _fields_ = [("k2_threads", ctypes.c_int32), ("pyr_tile_shift", ctypes.c_int32)]
 
 
+class InitNetCfg(ctypes.Structure):
+    _fields_ = [("level_a", ctypes.c_int32), ("level_b", ctypes.c_int32),
+                ("start_level", ctypes.c_int32), ("min_conf", ctypes.c_float)]
+
+
 _lib = None
 _lock = threading.Lock()
 
@@ -139,11 +144,31 @@ _SIGS = {
     "vio_batch_get_view": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32,
                                             ctypes.POINTER(FrontendView), ctypes.c_void_p]),
     "vio_batch_launches_per_step": (ctypes.c_int32, [ctypes.c_void_p]),
+    "vio_frontend_set_initnet": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p,
+                                                  ctypes.POINTER(InitNetCfg)]),
+    "vio_batch_set_initnet": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p,
+                                               ctypes.POINTER(InitNetCfg)]),
+    "vio_initnet_pack": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "vio_initnet_extract": (ctypes.c_int32, [ctypes.POINTER(PyrLayout), ctypes.POINTER(PyrBatch),
+                                             ctypes.POINTER(PyrBatch), ctypes.c_void_p,
+                                             ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
+                                             ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]),
+    "vio_initnet_forward": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                             ctypes.c_void_p, ctypes.c_void_p]),
+    "vio_initnet_train_step": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p,
+                                                ctypes.c_void_p, ctypes.c_void_p,
+                                                ctypes.c_int32, ctypes.c_float,
+                                                ctypes.c_void_p, ctypes.c_void_p,
+                                                ctypes.c_void_p]),
+    "vio_initnet_adam": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                          ctypes.c_void_p, ctypes.c_int32, ctypes.c_float,
+                                          ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                          ctypes.c_void_p]),
 }
 
-STAGES = ("front", "pyramid_upper", "track", "finalize")
+STAGES = ("front", "pyramid_upper", "initnet", "track", "finalize")
 STATS_RING = 4096
-STAT_NAMES = ("trk0", "trk1", "ok0", "ok1", "new", "matched", "cand")
+STAT_NAMES = ("trk0", "trk1", "ok0", "ok1", "new", "matched", "cand", "learned")
 
 
 def lib_path() -> str:
@@ -301,11 +326,15 @@ class Context:
                "vio_pyramid_detect")
 
     def track_patches(self, pyr: Pyramids, src: PyrBatch, dst: PyrBatch, pts, count, capacity,
-                      out, status, fb_dist=None, init=None, fb=True, stream=None):
+                      out, status, fb_dist=None, init=None, fb=True, from_level=None,
+                      stream=None):
+        """from_level: track over levels from_level..0 only (default: all)."""
+        flags = TRACK_WITH_FB if fb else TRACK_FORWARD
+        if from_level is not None:
+            flags |= (int(from_level) + 1) << 4
         _check(load().vio_track_patches(self.handle, ctypes.byref(pyr.layout), ctypes.byref(src),
                                         ctypes.byref(dst), _ptr(pts), _ptr(init), _ptr(count),
-                                        capacity, TRACK_WITH_FB if fb else TRACK_FORWARD,
-                                        _ptr(out), _ptr(status), _ptr(fb_dist),
+                                        capacity, flags, _ptr(out), _ptr(status), _ptr(fb_dist),
                                         _stream(stream)), "vio_track_patches")
 
     def stereo_match(self, pyr: Pyramids, cam0: PyrBatch, cam1: PyrBatch, pts, count, capacity,
@@ -349,6 +378,104 @@ def fb_check(orig, back, count, capacity, n_images, max_dist, status, dist=None,
            "vio_fb_check")
 
 
+INITNET_N_PARAMS = 28131
+INITNET_PACKED_BYTES = 58016
+
+
+def initnet_pack(master, packed, stream=None):
+    """FP32 master parameters (INITNET_N_PARAMS) -> packed BF16 weights."""
+    _check(load().vio_initnet_pack(_ptr(master), _ptr(packed), _stream(stream)),
+           "vio_initnet_pack")
+
+
+def initnet_extract(pyr: Pyramids, src: PyrBatch, dst: PyrBatch, pts, count, capacity,
+                    level_a, level_b, x, stream=None):
+    """Network inputs (bf16 bits as int16, [n][4][16][16]) of keypoints."""
+    _check(load().vio_initnet_extract(ctypes.byref(pyr.layout), ctypes.byref(src),
+                                      ctypes.byref(dst), _ptr(pts), _ptr(count), capacity,
+                                      level_a, level_b, _ptr(x), _stream(stream)),
+           "vio_initnet_extract")
+
+
+def initnet_forward(packed, x, n, out, stream=None):
+    _check(load().vio_initnet_forward(_ptr(packed), _ptr(x), n, _ptr(out), _stream(stream)),
+           "vio_initnet_forward")
+
+
+def initnet_train_step(packed, x, flow, index, n, grad_scale, grad, loss, stream=None):
+    _check(load().vio_initnet_train_step(_ptr(packed), _ptr(x), _ptr(flow), _ptr(index), n,
+                                         grad_scale, _ptr(grad), _ptr(loss), _stream(stream)),
+           "vio_initnet_train_step")
+
+
+def initnet_adam(master, grad, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    _check(load().vio_initnet_adam(_ptr(master), _ptr(grad), _ptr(m), _ptr(v), step, lr, beta1,
+                                   beta2, eps, _stream(stream)), "vio_initnet_adam")
+
+
+class InitNet:
+    """Learned flow initializer on the device: FP32 master parameters, their
+    packed BF16 copy (what the kernels read) and the gate configuration.
+
+    Checkpoints are .npz files holding ``master`` (and, for resuming
+    training, the Adam moments ``m``, ``v`` and the step count) plus the
+    configuration; no pickled objects."""
+
+    def __init__(self, master=None, level_a=2, level_b=3, start_level=1, min_conf=0.5,
+                 device="cuda"):
+        if master is None:
+            master = torch.zeros(INITNET_N_PARAMS, dtype=torch.float32)
+        master = torch.as_tensor(master, dtype=torch.float32).reshape(-1)
+        if master.numel() != INITNET_N_PARAMS:
+            raise ValueError(f"expected {INITNET_N_PARAMS} parameters, got {master.numel()}")
+        self.master = master.to(device).contiguous()
+        self.packed = torch.empty(INITNET_PACKED_BYTES, dtype=torch.uint8, device=device)
+        self.cfg = InitNetCfg(level_a, level_b, start_level, min_conf)
+        self.m = None
+        self.v = None
+        self.step = 0
+        self.pack()
+
+    def pack(self, stream=None):
+        initnet_pack(self.master, self.packed, stream)
+
+    def configure(self, **kw):
+        for k, v in kw.items():
+            setattr(self.cfg, k, v)
+
+    def forward(self, x, out=None, stream=None):
+        """x: int16 CUDA tensor (n, 4, 16, 16) of BF16 bits -> (n, 3) dx, dy, conf."""
+        n = x.shape[0]
+        if out is None:
+            out = torch.empty((n, 3), dtype=torch.float32, device=x.device)
+        initnet_forward(self.packed, x, n, out, stream)
+        return out
+
+    def save(self, path):
+        import numpy as np
+        extra = {}
+        if self.m is not None:
+            extra = {"m": self.m.cpu().numpy(), "v": self.v.cpu().numpy()}
+        np.savez(path, master=self.master.cpu().numpy(),
+                 cfg=np.array([self.cfg.level_a, self.cfg.level_b, self.cfg.start_level],
+                              np.int32),
+                 min_conf=np.array([self.cfg.min_conf], np.float32),
+                 step=np.array([self.step], np.int64), **extra)
+
+    @classmethod
+    def load(cls, path, device="cuda"):
+        import numpy as np
+        with np.load(path, allow_pickle=False) as z:
+            cfg = z["cfg"]
+            net = cls(z["master"], int(cfg[0]), int(cfg[1]), int(cfg[2]),
+                      float(z["min_conf"][0]), device)
+            net.step = int(z["step"][0])
+            if "m" in z:
+                net.m = torch.from_numpy(z["m"]).to(device)
+                net.v = torch.from_numpy(z["v"]).to(device)
+        return net
+
+
 class Frontend:
     """vio_frontend: the per-frame frontend over n_streams stereo streams."""
 
@@ -386,6 +513,14 @@ class Frontend:
 
     def launches_per_step(self) -> int:
         return int(load().vio_frontend_launches_per_step(self.handle))
+
+    def set_initnet(self, net: "InitNet | None"):
+        """Turn the learned start of temporal tracking on (net) or off (None).
+        The frontend reads net.packed at every step: keep net alive."""
+        self._net = net
+        _check(load().vio_frontend_set_initnet(self.handle, _ptr(net.packed) if net else None,
+                                               ctypes.byref(net.cfg) if net else None),
+               "vio_frontend_set_initnet")
 
     def set_timing(self, enable: bool):
         _check(load().vio_frontend_set_timing(self.handle, 1 if enable else 0), "set_timing")
@@ -525,6 +660,13 @@ class Batch:
 
     def launches_per_step(self) -> int:
         return int(load().vio_batch_launches_per_step(self.handle))
+
+    def set_initnet(self, net: "InitNet | None"):
+        """Learned start of temporal tracking for every stream (see Frontend)."""
+        self._net = net
+        _check(load().vio_batch_set_initnet(self.handle, _ptr(net.packed) if net else None,
+                                            ctypes.byref(net.cfg) if net else None),
+               "vio_batch_set_initnet")
 
     def view(self, g: int) -> dict:
         """Device tensors of group g's lists; 'parity' selects each stream's

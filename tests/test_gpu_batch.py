@@ -38,9 +38,11 @@ def _make():
     return groups, seqs
 
 
-def _alone(p, w, h, cap, frames, steps):
+def _alone(p, w, h, cap, frames, steps, net=None):
     """Lists of one stream run alone over frames[t] for t in steps."""
     fe = vio.Frontend(p, w, h, 1, cap)
+    if net is not None:
+        fe.set_initnet(net)
     keep = []
     for t in steps:
         f = torch.from_numpy(frames[t]).cuda().view(1, 2, h, w)
@@ -70,12 +72,12 @@ def _run_batch(b, seqs, schedule, stream=None):
     torch.cuda.synchronize()
 
 
-def _check_equal(b, groups, seqs, schedule):
+def _check_equal(b, groups, seqs, schedule, net=None):
     k = 0
     for gi, (p, w, h, n, cap) in enumerate(groups):
         for s in range(n):
             steps = [i for i, act in enumerate(schedule) if act[k]]
-            ref_xy, ref_id = _alone(p, w, h, cap, seqs[gi][s], range(len(steps)))
+            ref_xy, ref_id = _alone(p, w, h, cap, seqs[gi][s], range(len(steps)), net)
             xy, ids = b.stream_lists(gi, s)
             for c in range(2):
                 assert np.array_equal(ids[c], ref_id[c]), (gi, s, c)
@@ -134,3 +136,33 @@ def test_batch_graph_replay_and_autotune():
     s.synchronize()
     _check_equal(b, groups, seqs, schedule)
     assert b.launches_per_step() == 3
+
+
+def test_batch_with_initnet_equals_streams_alone():
+    """With the learned start on (every group, graphs on), each stream's lists
+    equal the same stream alone through vio_frontend with the same network."""
+    groups, seqs = _make()
+    rng = np.random.default_rng(3)
+    flat = (rng.normal(0, 0.05, vio.INITNET_N_PARAMS)).astype(np.float32)
+    flat[-1] = 3.0                                   # confident proposals
+    net = vio.InitNet(flat, 1, 2, 1, 0.5)
+    total = sum(g[3] for g in groups)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        b = vio.Batch(groups)
+        b.set_initnet(net)
+        b.set_graph(True)
+        assert b.launches_per_step() == 4
+        rng2 = np.random.default_rng(1)
+        schedule = [[1] * total] + [list((rng2.random(total) < 0.7).astype(int))
+                                    for _ in range(5)]
+        for k in range(total):
+            n_act = 0
+            for act in schedule:
+                if act[k]:
+                    n_act += 1
+                    if n_act > N_FRAMES:
+                        act[k] = 0
+        _run_batch(b, seqs, schedule, stream=s)
+    s.synchronize()
+    _check_equal(b, groups, seqs, schedule, net)

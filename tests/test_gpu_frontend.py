@@ -148,3 +148,168 @@ def test_frontend_run_equals_steps():
         assert torch.equal(va["track_id"][0, c, :nc], vb["track_id"][0, c, :nc])
     stats, steps = b.read_stats()
     assert steps == 6 and stats[5, 0, 4] == int(vb["new_count"][0])
+
+
+# ------------------------------------------------ learned start of tracking ---
+
+CONF_BAND = 1e-3   # |GPU - oracle| confidence: <= 0.25 * the raw-output tolerance
+
+
+def _band(res, fb_max):
+    with np.errstate(invalid="ignore"):
+        return (np.abs(res["fb_dist"] - fb_max) <= BAND) | (res["margin"] <= BAND)
+
+
+def _explained_net(res, ids, fb_max, tau):
+    """Ids whose outcome may differ: confidence on the gate, or a threshold
+    decision of the proposed or the plain track."""
+    if res is None:
+        return set()
+    ids = np.asarray(ids)
+    m = np.abs(res["conf"] - tau) <= CONF_BAND
+    gate, rl = res["learned_track"]
+    if rl is not None:
+        m[gate] |= _band(rl, fb_max)
+    rest, rp = res["plain_track"]
+    if rp is not None:
+        m[rest] |= _band(rp, fb_max)
+    return set(ids[m].tolist())
+
+
+def _net_master(kind):
+    from oracle import initnet as onet
+    rng = np.random.default_rng(12)
+    if kind == "const":
+        # all weights zero: every proposal is zero flow with confidence 0.95
+        p = {k: np.zeros(onet.SHAPES[k]) for k in onet.ORDER}
+        p["b5"] = np.array([0.0, 0.0, 3.0])
+    else:
+        fan = {"w1": 36, "w2": 288, "w3": 288, "w4": 128, "w5": 64}
+        p = {k: (rng.normal(0, np.sqrt(2.0 / fan[k]), onet.SHAPES[k]) if k in fan
+                 else rng.normal(0, 0.1, onet.SHAPES[k])) for k in onet.ORDER}
+        p["b5"] = np.array([0.0, 0.0, 0.0])
+    flat = onet.flatten(p).astype(np.float32)
+    q = onet.unflatten(flat.astype(np.float64))
+    q = {k: (onet.bf16_round(v) if k.startswith("w") else v) for k, v in q.items()}
+    return flat, q
+
+
+PROPOSAL_TOL = 16 * 4e-3   # px: GPU vs oracle proposal (raw-output tolerance x 16)
+
+
+def _start_spread(prev, cur, xy, flow, op, net):
+    """How far the oracle's track from a proposal moves when the proposal
+    moves by PROPOSAL_TOL (the network's own arithmetic tolerance): a track
+    that has not converged in its iterations inherits such differences."""
+    top = net.start_level + 1
+    base = np.asarray(xy, np.float64) + flow
+    inits = [base] + [base + d for d in ([PROPOSAL_TOL, 0], [-PROPOSAL_TOL, 0],
+                                         [0, PROPOSAL_TOL], [0, -PROPOSAL_TOL])]
+    init = np.zeros((5, 3), np.float32)
+    init[:, :2] = np.array(inits, np.float32)
+    r = oracle.track(prev[:top], cur[:top], np.repeat(np.asarray(xy, np.float32)[None], 5, 0),
+                     init=init, gn_iters=op.gn_iters, fb=True, fb_max_dist=op.fb_max_dist)
+    ok = r["status"] == 0
+    if not ok[0] or ok.sum() < 2:
+        return np.inf
+    return float(np.abs(r["warp"][ok, :2] - r["warp"][0, :2]).max())
+
+
+@pytest.mark.parametrize("kind", ["const", "random"])
+def test_frontend_learned_start_matches_oracle(kind):
+    """Positions within 1e-3 px of the oracle's; a track started from a
+    proposal may differ by as much as the oracle's own result moves when the
+    proposal moves within the network's tolerance (tracks that did not
+    converge in their iterations)."""
+    w, h, L, cw, ch, n_frames, motion = 640, 480, 5, 32, 32, 5, 12.0
+    seq = synth.make_sequence(4100, n_frames, w, h, 1, max_motion=motion, tex_size=2048)
+    p = vio.default_params(n_levels=L, cell_w=cw, cell_h=ch)
+    op = ofe.Params(n_levels=L, cell_w=cw, cell_h=ch)
+    cap = 2 * (w // cw) * (h // ch)
+    flat, q = _net_master(kind)
+    tau = 0.5
+    net = vio.InitNet(flat, 2, 3, 1, tau)
+    onet_cfg = ofe.NetCfg(q, 2, 3, 1, tau)
+    fe = vio.Frontend(p, w, h, 1, cap)
+    fe.set_initnet(net)
+    assert fe.launches_per_step() == 4
+    frames = torch.from_numpy(seq.frames).cuda()
+    st = ofe.StreamState()
+    prev_ids = [np.zeros(0, np.int32), np.zeros(0, np.int32)]
+    n_learned_o = n_learned_g = n_common = n_spread = 0
+    worst = 0.0
+    for t in range(n_frames):
+        fe.step(frames[t: t + 1])
+        torch.cuda.synchronize()
+        v = fe.view()
+        prev_pyr = st.pyr
+        prev_xy = [x.copy() for x in st.xy]
+        res = ofe.step(st, seq.frames[t], op, cap, n_threads=8, net=onet_cfg)
+        cnt = v["track_count"][0].cpu().numpy()
+        gx = [v["track_xy"][0, c, : cnt[c]].cpu().numpy() for c in range(2)]
+        gi = [v["track_id"][0, c, : cnt[c]].cpu().numpy() for c in range(2)]
+        expl = set()
+        for c in range(2):
+            expl |= _explained_net(res["track"][c], prev_ids[c], p.fb_max_dist, tau)
+            if res["track"][c] is not None:
+                n_learned_o += int(res["track"][c]["learned"].sum())
+        expl |= _explained(res["match"], st.ids[0][-len(res["new_xy"]):] if len(res["new_xy"])
+                           else [], p.fb_max_dist)
+        for c in range(2):
+            gs, os_ = list(gi[c]), list(st.ids[c])
+            diff = set(gs) ^ set(os_)
+            assert diff <= expl, (t, c, sorted(diff - expl)[:10], len(diff))
+            opos = {i: xy for i, xy in zip(os_, st.xy[c])}
+            row = {i: j for j, i in enumerate(prev_ids[c])}
+            for i, xy in zip(gs, gx[c]):
+                if i in opos and i not in expl:
+                    e = float(np.abs(np.asarray(xy, np.float64) - opos[i]).max())
+                    n_common += 1
+                    if e >= FLOW_TOL:
+                        r = res["track"][c]
+                        j = row[i]
+                        assert r is not None and r["learned"][j], (t, c, i, e)
+                        sp = _start_spread(prev_pyr[c], st.pyr[c], prev_xy[c][j], r["flow"][j],
+                                           op, onet_cfg)
+                        assert e < FLOW_TOL + 2 * sp, (t, c, i, e, sp)
+                        n_spread += 1
+                    else:
+                        worst = max(worst, e)
+        stats, _ = fe.read_stats()
+        n_learned_g += int(stats[t, 0, vio.STAT_NAMES.index("learned")])
+        st.xy = [gx[0].copy(), gx[1].copy()]
+        st.ids = [gi[0].copy(), gi[1].copy()]
+        prev_ids = [gi[0].copy(), gi[1].copy()]
+    assert worst < FLOW_TOL, worst
+    assert n_common > 500
+    assert n_spread <= 0.05 * n_common, (n_spread, n_common)
+    assert n_learned_o > 100
+    assert abs(n_learned_g - n_learned_o) <= max(3, 0.01 * n_learned_o)
+    fe.close()
+
+
+def test_frontend_initnet_off_is_plain():
+    """Turning the initializer on with a gate nothing reaches, then off,
+    gives the plain frontend's lists bit for bit."""
+    w, h, L = 376, 240, 4
+    seq = synth.make_sequence(5007, 4, w, h, 1, max_motion=6.0, tex_size=1024)
+    p = vio.default_params(n_levels=L, cell_w=47, cell_h=40)
+    cap = 2 * (w // 47) * (h // 40)
+    frames = torch.from_numpy(seq.frames).cuda().view(4, 1, 2, h, w)
+    flat, _ = _net_master("random")
+    net = vio.InitNet(flat, 2, 3, 1, 2.0)        # confidence never reaches 2
+    a, b = vio.Frontend(p, w, h, 1, cap), vio.Frontend(p, w, h, 1, cap)
+    b.set_initnet(net)
+    for t in range(4):
+        if t == 2:
+            b.set_initnet(None)
+        a.step(frames[t])
+        b.step(frames[t])
+    torch.cuda.synchronize()
+    va, vb = a.view(), b.view()
+    assert torch.equal(va["track_count"], vb["track_count"])
+    for c in range(2):
+        n = int(va["track_count"][0, c])
+        assert torch.equal(va["track_xy"][0, c, :n], vb["track_xy"][0, c, :n])
+        assert torch.equal(va["track_id"][0, c, :n], vb["track_id"][0, c, :n])
+    assert b.launches_per_step() == 3

@@ -88,3 +88,27 @@ def test_extract_samples_integer_grid():
     # level 0 window starts at round(20.4)-8 = 12, round(30.6)-8 = 23
     assert x[0, 0, 0] == ((23 * 64 + 12) % 256 - 128) / 64
     assert np.all(x[1] == 0.0) and np.all(x[2] == 1.0) and np.all(x[3] == -1.0)
+
+
+def test_bf16_round_special_values_and_library():
+    import torch
+    # exact values stay, ties go to the even neighbour, halfway+ goes up
+    assert net.bf16_round([1.0, -2.5, 0.0])[0] == 1.0
+    assert net.bf16_round([1 + 2 ** -8])[0] == 1.0                    # tie, 1.0 is even
+    assert net.bf16_round([1 + 3 * 2 ** -8])[0] == 1 + 2 ** -6        # tie, rounds up to even
+    assert net.bf16_round([1 + 2 ** -8 + 2 ** -20])[0] == 1 + 2 ** -7
+    rng = np.random.default_rng(3)
+    v = (rng.normal(size=4096) * 10.0 ** rng.integers(-6, 6, 4096)).astype(np.float32)
+    lib = torch.from_numpy(v).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(net.bf16_round(v), lib)
+
+
+def test_bf16_activations_only_round_the_stored_values():
+    p = {k: net.bf16_round(v) for k, v in rand_params(4, 0.2).items()}
+    x = net.bf16_round(np.random.default_rng(5).normal(size=(4, 16, 16)))
+    o64 = net.forward(p, x)
+    o16, act = net.forward(p, x, keep=True, act_bf16=True)
+    for k in ("h1", "h2", "h3", "h4"):
+        assert np.array_equal(net.bf16_round(act[k]), act[k])
+    # BF16 storage perturbs each activation by at most 2^-9 relative
+    assert np.max(np.abs(o16 - o64)) < 0.05 * (1 + np.max(np.abs(o64)))

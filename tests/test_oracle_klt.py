@@ -205,3 +205,54 @@ def test_skipped_coarse_level_near_border():
                      [[12.0, 80.0]], gn_iters=30)
     assert r["status"][0] == 0
     assert np.abs(r["warp"][0, :2] - (12 + 1, 81)).max() < 1e-9
+
+
+# ---------------------------------------------- learned start (host logic) ---
+
+def _const_net(fx, fy, logit, start_level=1, min_conf=0.5):
+    """A network whose weights are all zero: every proposal is the output
+    bias, i.e. flow (16 bx, 16 by) with confidence sigmoid(logit)."""
+    from oracle import initnet
+    from oracle.frontend import NetCfg
+    p = {k: np.zeros(initnet.SHAPES[k]) for k in initnet.ORDER}
+    p["b5"] = np.array([fx / 16.0, fy / 16.0, logit])
+    return NetCfg(p, 2, 3, start_level, min_conf)
+
+
+def _shift_pair(seed, dx, dy, w=200, h=160):
+    tex = synth.band_limited_texture(seed, h + 64, w + 64)
+    a = synth.quantize(tex[32:32 + h, 32:32 + w], None, 0)
+    b = synth.quantize(tex[32 - dy:32 - dy + h, 32 - dx:32 - dx + w], None, 0)
+    return oracle.pyramid(a, 4), oracle.pyramid(b, 4)
+
+
+def test_learned_start_gate_and_fallback():
+    from oracle.frontend import Params, temporal
+    prev, cur = _shift_pair(71, 6, -5)
+    rng = np.random.default_rng(0)
+    pts = np.stack([rng.uniform(40, 160, 30), rng.uniform(40, 120, 30)], 1).astype(np.float32)
+    p = Params(n_levels=4)
+    plain = temporal(prev, cur, pts, p)
+    assert (plain["status"] == 0).mean() > 0.8
+    assert np.allclose(plain["warp"][plain["status"] == 0, :2] - pts[plain["status"] == 0],
+                       [6, -5], atol=0.05)
+    # a gate that nothing reaches: exactly the plain track
+    r = temporal(prev, cur, pts, p, _const_net(6, -5, 0.0, min_conf=0.9))
+    assert not r["learned"].any()
+    assert np.array_equal(r["status"], plain["status"]) and np.array_equal(r["warp"], plain["warp"])
+    # the right flow, confident, from level 0 alone: tracked from the proposal,
+    # to the plain track's result
+    r = temporal(prev, cur, pts, p, _const_net(6, -5, 4.0, start_level=0))
+    both = r["learned"] & (plain["status"] == 0)
+    assert both.mean() > 0.75
+    assert np.abs(r["warp"][both, :2] - plain["warp"][both, :2]).max() < 1e-3
+    assert np.allclose(r["conf"], 1 / (1 + np.exp(-4.0)))
+    # a proposal 26 px off, from level 0: almost every keypoint fails and
+    # falls back to the plain track. (A few pass: the backward track starts
+    # at p itself, so a forward track stuck on a weak wrong optimum can still
+    # pass the forward-backward check; this is why proposals are gated.)
+    r = temporal(prev, cur, pts, p, _const_net(-14, 12, 4.0, start_level=0))
+    assert r["learned"].mean() <= 0.1
+    rest = ~r["learned"]
+    assert np.array_equal(r["status"][rest], plain["status"][rest])
+    assert np.array_equal(r["warp"][rest], plain["warp"][rest])
