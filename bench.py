@@ -206,6 +206,120 @@ def pyramid_detect_roofline(torch, vio, frames_dev, peaks, peak_src):
                     "and 10 B per keypoint written"}
 
 
+# Batched + learned initializer: 16 streams, 4 each of these sizes, cells for
+# 300 / 300 / 600 / 1000 keypoints per image, 5 levels, motion up to 40 px
+CFG4_CLASSES = [(640, 480, 32, 32), (752, 480, 37, 32), (1280, 720, 42, 36), (1920, 1080, 48, 43)]
+CFG4_STREAMS, CFG4_FRAMES, CFG4_LEVELS, CFG4_MOTION = 4, 24, 5, 40.0
+
+
+def _render_cfg4(job):
+    from paper_2609_30459_gb300 import synth
+    seed, w, h = job
+    return synth.make_sequence(seed, CFG4_FRAMES, w, h, 1, max_motion=CFG4_MOTION,
+                               tex_size=2048).frames
+
+
+def cfg4_frames():
+    """Per class, per stream: (F, 2, h, w) uint8 frames (seed 4000 + stream),
+    rendered by a spawned pool of host processes."""
+    import multiprocessing as mp
+    jobs = [(4000 + k * CFG4_STREAMS + i, w, h)
+            for k, (w, h, _, _) in enumerate(CFG4_CLASSES) for i in range(CFG4_STREAMS)]
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
+        out = pool.map(_render_cfg4, jobs)
+    return [out[k * CFG4_STREAMS:(k + 1) * CFG4_STREAMS] for k in range(len(CFG4_CLASSES))]
+
+
+def batched_compare(torch, vio, steps, warmup, net):
+    """The 16-stream batch, plain and with the learned initializer: each step
+    uploads one frame per stream into its slot (device to device, frames
+    resident) and runs the batch's captured graph; per-step CUDA events give
+    the step latency (every frame of a step completes with it)."""
+    import numpy as np
+    seqs = cfg4_frames()
+    dev = [[torch.from_numpy(f).cuda() for f in cls] for cls in seqs]
+    groups = []
+    for (w, h, cw, ch) in CFG4_CLASSES:
+        p = vio.default_params(n_levels=CFG4_LEVELS, cell_w=cw, cell_h=ch)
+        groups.append((p, w, h, CFG4_STREAMS, 2 * (w // cw) * (h // ch)))
+    n_streams = CFG4_STREAMS * len(CFG4_CLASSES)
+    F = CFG4_FRAMES
+    order = list(range(F)) + list(range(F - 2, 0, -1))   # forward and back: motion stays smooth
+    res = {"streams": n_streams, "classes": [f"{w}x{h}" for (w, h, _, _) in CFG4_CLASSES],
+           "levels": CFG4_LEVELS, "max_motion_px": CFG4_MOTION, "steps": steps}
+    for mode in ("plain", "learned"):
+        if mode == "learned" and net is None:
+            res[mode] = None
+            continue
+        s = torch.cuda.Stream()
+        with torch.cuda.stream(s):
+            b = vio.Batch(groups)
+            if mode == "learned":
+                b.set_initnet(net)
+
+            def upload(t):
+                for g in range(len(CFG4_CLASSES)):
+                    for i in range(CFG4_STREAMS):
+                        b.next_frame(g, i).copy_(dev[g][i][order[t % len(order)]],
+                                                 non_blocking=True)
+
+            for t in range(2):                 # frames in both slots for the autotuner
+                upload(t)
+                b.step(None, stream=s)
+            tune_ms = b.autotune(reps=2, stream=s)
+            b.set_graph(True)
+            for t in range(warmup):
+                upload(t)
+                b.step(None, stream=s)
+            s.synchronize()
+            for g in range(len(CFG4_CLASSES)):
+                for i in range(CFG4_STREAMS):
+                    b.reset_stream(g, i, stream=s)
+            _, steps0 = b.read_stats(0)
+            evs = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+            s.synchronize()
+            evs[0].record(s)
+            for t in range(steps):
+                upload(t)
+                b.step(None, stream=s)
+                evs[t + 1].record(s)
+            s.synchronize()
+        lat = [evs[t].elapsed_time(evs[t + 1]) for t in range(steps)]
+        total_s = evs[0].elapsed_time(evs[steps]) / 1000.0
+        tracked = learned = survived = 0
+        for g in range(len(CFG4_CLASSES)):
+            st, n = b.read_stats(g)
+            idx = [(steps0 + k) % vio.STATS_RING for k in range(steps)]
+            a = st[idx].astype(np.int64)
+            tracked += int(a[..., 0].sum() + a[..., 1].sum())
+            survived += int(a[..., 2].sum() + a[..., 3].sum())
+            learned += int(a[..., 7].sum())
+        k2, shift = b.get_tune()
+        res[mode] = {"frames_per_s": n_streams * steps / total_s,
+                     "p50_ms": percentile(lat, 50), "p99_ms": percentile(lat, 99),
+                     "tracked_keypoints_per_s": tracked / total_s,
+                     "survived_per_step": survived / steps,
+                     "learned_share_of_survivors": learned / max(survived, 1),
+                     "launches_per_step": b.launches_per_step(),
+                     "tune": {"k2_threads": k2, "pyr_tile_shift": shift,
+                              "best_ms": tune_ms}}
+        b.close()
+    if res.get("learned") and res.get("plain"):
+        res["learned_vs_plain_fps"] = (res["learned"]["frames_per_s"] /
+                                       res["plain"]["frames_per_s"])
+        res["learned_vs_plain_p99"] = res["learned"]["p99_ms"] / res["plain"]["p99_ms"]
+    if net is not None:
+        from paper_2609_30459_gb300 import initnet_train
+        flat = [f for cls in seqs for f in cls[:1]]          # one stream of each size
+        g = initnet_train.gain_eval(net, flat, n_levels=CFG4_LEVELS, cell=32,
+                                    start_levels=(net.cfg.start_level,),
+                                    taus=(net.cfg.min_conf,))
+        key = f"start{net.cfg.start_level}_tau{net.cfg.min_conf}"
+        res["accuracy"] = {"sample": "one stream of each size, all frame pairs, 32x32 cells",
+                           "keypoints": g["n"], **g[key]}
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -214,6 +328,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-frames", type=int, default=60)
+    ap.add_argument("--batched-steps", type=int, default=300)
+    ap.add_argument("--no-batched", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -360,6 +476,14 @@ def main():
 
     pd = pyramid_detect_roofline(torch, vio, frames, peaks, peak_src) if rank == 0 else None
 
+    batched = None
+    if rank == 0 and not args.no_batched:
+        from paper_2609_30459_gb300 import initnet_train
+        net = None
+        if os.path.exists(initnet_train.DEFAULT_WEIGHTS):
+            net = vio.InitNet.load(initnet_train.DEFAULT_WEIGHTS)
+        batched = batched_compare(torch, vio, args.batched_steps, args.warmup, net)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         fps, cores, _ = oracle_frames_per_s(frames_np, args.cpu_frames)
@@ -383,6 +507,7 @@ def main():
                                    "stereo_candidates": stereo_in / args.steps},
             "gpu_launches": args.steps * fe.launches_per_step(),
             "e2e": e2e, "roofline": roofline, "pyramid_detect_roofline": pd,
+            "batched_16_streams": batched,
             "cpu_baseline": cpu, "clocks": clk.summary(),
             "host_wall_s": wall,
         }

@@ -388,6 +388,10 @@ typedef struct {
 } vio_batch_tune;
 
 vio_status vio_batch_create(vio_batch** out, const vio_stream_group* groups, int32_t n_groups);
+/* Device bytes vio_batch_create would allocate for these groups (host only;
+ * the same validation, the same errors). */
+vio_status vio_batch_device_bytes(const vio_stream_group* groups, int32_t n_groups,
+                                  int64_t* bytes);
 vio_status vio_batch_destroy(vio_batch* b);
 
 /* Device address of the frame (both cameras, 2 x h x w uint8, camera 1 at
@@ -425,11 +429,89 @@ vio_status vio_batch_get_view(vio_batch* b, int32_t g, vio_frontend_view* out,
                               int32_t* parity);
 int32_t vio_batch_launches_per_step(const vio_batch* b);
 
+/* Per-step counters of group g (layout and meaning as vio_frontend_read_stats;
+ * a stream's entry of a step in which it was inactive is all zero). Blocking.
+ * *n_steps: the group's steps since create (the ring entry of step i is
+ * i mod VIO_STATS_RING). */
+vio_status vio_batch_read_stats(vio_batch* b, int32_t g, int32_t* host_out, int64_t* n_steps);
+
 /* vio_frontend_set_initnet for every stream of the batch (one network and
  * configuration for all groups; every group needs the levels). Captured
  * graphs are re-captured at the next graph step. */
 vio_status vio_batch_set_initnet(vio_batch* b, const void* d_packed, const vio_initnet_cfg* cfg);
 
+
+/* ---------------------------------------------------------------- serving -- */
+/* A request loop over a vio_batch (an addition; the paper runs one camera
+ * rig per process). Size classes are vio_stream_group entries whose
+ * n_streams is the number of concurrent sessions wanted; vio_server_plan
+ * fits them into a device-memory budget (every class keeps at least one
+ * slot; beyond that all classes scale down together) and vio_server_create
+ * allocates exactly that. A session (one client stereo stream) is admitted
+ * to a free slot of its class at open, or waits in the class's FIFO until a
+ * session of that class closes; its pyramids, lists and frames stay on the
+ * device while it holds the slot. Frames are uploaded as they arrive, from
+ * PINNED host memory that the caller keeps until the frame's completion,
+ * into per-slot staging buffers on an upload stream; whenever no step is on
+ * the GPU, every admitted session with an uploaded frame joins the next
+ * batch step (continuous batching), so uploads overlap the step in flight.
+ * Each session's results are those of the same stream run alone through
+ * vio_frontend. Host-side calls are not thread-safe: drive a server from one
+ * thread. Times are seconds of vio_server_now()'s clock. */
+typedef struct vio_server vio_server;
+
+#define VIO_SERVER_LAST 1   /* submit flag: the session closes after this frame */
+
+typedef struct {
+  int64_t session;
+  double t_offset;          /* arrival, seconds after the trace starts (ascending) */
+  const uint8_t* host_frame;  /* pinned, 2 x h x w (camera 1 at + h*w)             */
+  int64_t tag;
+  int32_t flags;
+} vio_server_req;
+
+typedef struct {
+  int64_t session, tag;
+  double t_arrival, t_launch, t_done;  /* arrival, its step's launch, completion seen */
+  int32_t n_tracks[2];                 /* list lengths of cameras 0 and 1 after it   */
+  int32_t n_new;                       /* detections of this frame                   */
+  int32_t status;                      /* VIO_OK, or the error of its step           */
+} vio_server_done;
+
+double vio_server_now(void);
+/* Host only: slots per class (slots_out[n_classes]) and their device bytes
+ * for a budget; VIO_ERR_OOM if even one slot per class does not fit. */
+vio_status vio_server_plan(const vio_stream_group* classes, int32_t n_classes,
+                           int64_t budget_bytes, int32_t* slots_out, int64_t* bytes_out);
+vio_status vio_server_create(vio_server** out, const vio_stream_group* classes,
+                             int32_t n_classes, int64_t budget_bytes);
+vio_status vio_server_destroy(vio_server* s);
+vio_status vio_server_slots(const vio_server* s, int32_t cls, int32_t* n_slots,
+                            int64_t* device_bytes);
+vio_status vio_server_set_initnet(vio_server* s, const void* d_packed,
+                                  const vio_initnet_cfg* cfg);
+vio_status vio_server_set_tune(vio_server* s, const vio_batch_tune* t);
+/* New session of class cls; *admitted = 1 if it holds a slot now. */
+vio_status vio_server_open(vio_server* s, int32_t cls, int64_t* session, int32_t* admitted);
+/* Optional host buffers that receive the session's lists after each of its
+ * frames: xy 2 x capacity float2, id 2 x capacity int32, count 2 int32. */
+vio_status vio_server_set_output(vio_server* s, int64_t session, float* host_xy,
+                                 int32_t* host_id, int32_t* host_count);
+vio_status vio_server_submit(vio_server* s, int64_t session, const uint8_t* host_frame,
+                             double t_arrival, int64_t tag, int32_t flags);
+/* The session's queued frames still run; then its slot goes to the next
+ * waiting session of its class. A waiting session leaves the queue. */
+vio_status vio_server_close(vio_server* s, int64_t session);
+/* Non-blocking progress: completes the step in flight if it has finished,
+ * starts uploads, launches the next step if none is in flight. *n_done:
+ * completions waiting to be taken. */
+vio_status vio_server_poll(vio_server* s, int32_t* n_done);
+int32_t vio_server_take(vio_server* s, vio_server_done* out, int32_t max);
+/* Replays n requests in real time (submitting each at its offset, polling in
+ * between) until all n have completed; out receives the n completions in
+ * completion order. VIO_ERR_TIMEOUT after timeout_s seconds. */
+vio_status vio_server_run_trace(vio_server* s, const vio_server_req* reqs, int64_t n,
+                                vio_server_done* out, double timeout_s, int64_t* n_steps);
 
 /* ---------------------------------------------------------------------------
  * Learned flow initializer. Not in the paper: its tracker starts each
@@ -445,8 +527,10 @@ vio_status vio_batch_set_initnet(vio_batch* b, const void* d_packed, const vio_i
  *   fc     flatten (channel, row, column) 128 -> 64 + ReLU -> 3;
  *   output flow = 16 px * (o0, o1) (level-0 pixels), confidence = sigmoid(o2);
  *   loss   (o0 - fx/16)^2 + (o1 - fy/16)^2 + BCE(sigmoid(o2), y), y = 1 when
- *          the predicted flow is within 1 px of the target (no gradient
- *          through y); the batch loss is the mean.
+ *          the predicted flow is within the label radius r of the target (no
+ *          gradient through y); the batch loss is the mean. The confidence
+ *          thus estimates the chance that the proposal lies within r px; r
+ *          is chosen to match the tracking start level's reach.
  *
  * Parameters: FP32 master vector of VIO_INITNET_N_PARAMS floats in the order
  * w1 (32,4,3,3), b1, w2 (32,32,3,3), b2, w3 (32,32,3,3), b3, w4 (64,128), b4,
@@ -477,14 +561,15 @@ vio_status vio_initnet_forward(const void* d_packed, const uint16_t* d_x, int32_
                                float* d_out, void* stream);
 
 /* Adds grad_scale * (sum over the n samples d_index[0..n-1] (NULL = 0..n-1)
- * of dL_i/dparams) to d_grad (VIO_INITNET_N_PARAMS floats, gradient with
+ * of dL_i/dparams), labels at radius label_radius px (> 0), to d_grad (VIO_INITNET_N_PARAMS floats, gradient with
  * respect to the master parameters through the BF16 packing taken as the
  * identity) and the sum of the n losses to *d_loss. Targets: d_flow[2*j] =
  * (fx, fy) of sample j in level-0 pixels. The caller zeroes d_grad and
  * d_loss first. The forward pass is that of vio_initnet_forward. */
 vio_status vio_initnet_train_step(const void* d_packed, const uint16_t* d_x,
                                   const float* d_flow, const int32_t* d_index, int32_t n,
-                                  float grad_scale, float* d_grad, float* d_loss, void* stream);
+                                  float grad_scale, float label_radius, float* d_grad,
+                                  float* d_loss, void* stream);
 
 /* Adam (Kingma and Ba, 2015) on the master parameters, step t >= 1:
  * m = b1 m + (1-b1) g; v = b2 v + (1-b2) g^2;

@@ -13,8 +13,9 @@ oracle states plainly, in FP64, for the GPU forward and gradient checks:
 * outputs: flow = (o0, o1) * S (S = 16 px, level-0 pixels), confidence =
   sigmoid(o2);
 * loss per sample: (o0 - fx/S)^2 + (o1 - fy/S)^2 + BCE(sigmoid(o2), y) with
-  y = 1 if the predicted flow is within 1 px of the target (y carries no
-  gradient); the batch loss is the mean.
+  y = 1 if the predicted flow is within r px of the target (r = the label
+  radius, 1 px unless set; y carries no gradient); the batch loss is the
+  mean.
 
 Precision: the network's weights and inputs are BF16 values and its
 activations are stored as BF16 between layers (accumulation wider). The
@@ -120,10 +121,10 @@ def outputs(o):
     return o[0] * SCALE, o[1] * SCALE, sigmoid(o[2])
 
 
-def loss_and_grad_out(o, flow):
-    """Loss of one sample and dL/do (the 1 px label carries no gradient)."""
+def loss_and_grad_out(o, flow, radius=1.0):
+    """Loss of one sample and dL/do (the label carries no gradient)."""
     t0, t1 = flow[0] / SCALE, flow[1] / SCALE
-    y = 1.0 if np.hypot(o[0] * SCALE - flow[0], o[1] * SCALE - flow[1]) < 1.0 else 0.0
+    y = 1.0 if np.hypot(o[0] * SCALE - flow[0], o[1] * SCALE - flow[1]) < radius else 0.0
     s = sigmoid(o[2])
     eps = 1e-12
     loss = (o[0] - t0) ** 2 + (o[1] - t1) ** 2 - (y * np.log(s + eps) +
@@ -150,13 +151,14 @@ def backward(p: dict, act: dict, do: np.ndarray) -> dict:
     return g
 
 
-def batch_loss_grad(p: dict, xs: np.ndarray, flows: np.ndarray, act_bf16: bool = False):
+def batch_loss_grad(p: dict, xs: np.ndarray, flows: np.ndarray, act_bf16: bool = False,
+                    radius: float = 1.0):
     """Mean loss and gradient (dict) over a batch."""
     total = 0.0
     acc = {k: np.zeros(SHAPES[k]) for k in ORDER}
     for x, f in zip(xs, flows):
         o, act = forward(p, x, keep=True, act_bf16=act_bf16)
-        loss, do = loss_and_grad_out(o, f)
+        loss, do = loss_and_grad_out(o, f, radius)
         total += loss
         g = backward(p, act, do)
         for k in ORDER:

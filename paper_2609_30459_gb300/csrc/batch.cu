@@ -84,6 +84,38 @@ bool batch_params_ok(const vio_params* p) {
   return p->detect_border >= 0 && p->fb_max_dist >= 0.f;
 }
 
+// Validates one group and lists the sizes of its device buffers.
+vio_status group_sizes(const vio_stream_group& sp, vio_pyr_layout& layout, int& n_cells,
+                       std::array<size_t, 26>& z) {
+  if (!batch_params_ok(&sp.params) || sp.w < 1 || sp.h < 1 || sp.n_streams < 1 ||
+      sp.capacity < 1 || sp.capacity > 32767)
+    return VIO_ERR_INVALID_ARG;
+  if (vio_pyr_layout_make(sp.w, sp.h, sp.params.n_levels, sp.w, &layout) != VIO_OK)
+    return VIO_ERR_INVALID_ARG;
+  const long long gx = sp.w / sp.params.cell_w, gy = sp.h / sp.params.cell_h;
+  n_cells = (int)(gx * gy);
+  if ((long long)n_cells * sp.params.k_per_cell > sp.capacity ||
+      (long long)n_cells * 4 > 200 * 1024 ||
+      vio::det::cell_smem_bytes(sp.params.cell_w, sp.params.cell_h) > vio::det::kMaxCellSmem)
+    return VIO_ERR_UNSUPPORTED;
+  const size_t ns = sp.n_streams, cap = sp.capacity, nc = n_cells;
+  const size_t kk = sp.params.k_per_cell, fb = (size_t)sp.w * sp.h;
+  const size_t lists = 2 * ns * 2 * cap;
+  z = {4 * ns * fb,                                  // frames
+       4 * ns * (size_t)layout.upper_bytes,          // pyr
+       lists * 8, lists * 4, 2 * ns * 2 * 4, lists,  // lists
+       ns * 2 * cap * 8, ns * 2 * cap,               // trk
+       ns * nc * kk * 8, ns * nc * 4,                // cand
+       ns * nc * kk * 8, ns * nc * kk,               // spec
+       ns * nc,                                      // occupancy
+       ns * cap * 8, ns * 4, ns * 4,                 // new, next_id
+       (size_t)VIO_STATS_RING * ns * VIO_N_STATS * 4,  // stats
+       16, ns * 4, ns * 4,                           // step_ctr, parity, have_prev
+       ns * 2 * cap * 12, ns * 2 * cap,              // net_out, trk_learned
+       0, 0, 0, 0};
+  return VIO_OK;
+}
+
 vio::FrameLaunch launch_of(Group& G) {
   using namespace vio;
   const vio_stream_group& sp = G.spec;
@@ -171,38 +203,11 @@ extern "C" vio_status vio_batch_create(vio_batch** out, const vio_stream_group* 
     const vio_stream_group& sp = groups[i];
     Group& G = b->groups[i];
     G.spec = sp;
-    if (!batch_params_ok(&sp.params) || sp.w < 1 || sp.h < 1 || sp.n_streams < 1 ||
-        sp.capacity < 1 || sp.capacity > 32767) {
+    const vio_status st = group_sizes(sp, G.layout, G.n_cells, sizes[i]);
+    if (st != VIO_OK) {
       delete b;
-      return VIO_ERR_INVALID_ARG;
+      return st;
     }
-    if (vio_pyr_layout_make(sp.w, sp.h, sp.params.n_levels, sp.w, &G.layout) != VIO_OK) {
-      delete b;
-      return VIO_ERR_INVALID_ARG;
-    }
-    const long long gx = sp.w / sp.params.cell_w, gy = sp.h / sp.params.cell_h;
-    G.n_cells = (int)(gx * gy);
-    if ((long long)G.n_cells * sp.params.k_per_cell > sp.capacity ||
-        (long long)G.n_cells * 4 > 200 * 1024 ||
-        vio::det::cell_smem_bytes(sp.params.cell_w, sp.params.cell_h) > vio::det::kMaxCellSmem) {
-      delete b;
-      return VIO_ERR_UNSUPPORTED;
-    }
-    const size_t ns = sp.n_streams, cap = sp.capacity, nc = G.n_cells;
-    const size_t kk = sp.params.k_per_cell, fb = (size_t)sp.w * sp.h;
-    const size_t lists = 2 * ns * 2 * cap;
-    sizes[i] = {4 * ns * fb,                                  // frames
-                4 * ns * (size_t)G.layout.upper_bytes,         // pyr
-                lists * 8, lists * 4, 2 * ns * 2 * 4, lists,   // lists
-                ns * 2 * cap * 8, ns * 2 * cap,                // trk
-                ns * nc * kk * 8, ns * nc * 4,                 // cand
-                ns * nc * kk * 8, ns * nc * kk,                // spec
-                ns * nc,                                       // occupancy
-                ns * cap * 8, ns * 4, ns * 4,                  // new, next_id
-                (size_t)VIO_STATS_RING * ns * VIO_N_STATS * 4, // stats
-                16, ns * 4, ns * 4,                            // step_ctr, parity, have_prev
-                ns * 2 * cap * 12, ns * 2 * cap,               // net_out, trk_learned
-                0, 0, 0, 0};
     for (size_t v : sizes[i]) total += align256(v);
     b->total_streams += sp.n_streams;
   }
@@ -471,6 +476,37 @@ extern "C" int32_t vio_batch_launches_per_step(const vio_batch* b) {
   std::vector<vio::Geom> g;
   for (const auto& G : b->groups) g.push_back(vio::make_geom(G.layout));
   return vio::frame_launches(g.data(), (int)g.size(), b->net != nullptr);
+}
+
+extern "C" vio_status vio_batch_device_bytes(const vio_stream_group* groups, int32_t n_groups,
+                                             int64_t* bytes) {
+  if (!groups || !bytes || n_groups < 1 || n_groups > vio::kMaxGroups) return VIO_ERR_INVALID_ARG;
+  int64_t total = 0, streams = 0;
+  for (int i = 0; i < n_groups; ++i) {
+    vio_pyr_layout L;
+    int nc = 0;
+    std::array<size_t, 26> z;
+    const vio_status st = group_sizes(groups[i], L, nc, z);
+    if (st != VIO_OK) return st;
+    for (size_t v : z) total += (int64_t)align256(v);
+    streams += groups[i].n_streams;
+  }
+  *bytes = total + (int64_t)align256((size_t)streams * 4);
+  return VIO_OK;
+}
+
+extern "C" vio_status vio_batch_read_stats(vio_batch* b, int32_t g, int32_t* host_out,
+                                           int64_t* n_steps) {
+  if (!b || !host_out || !n_steps || g < 0 || g >= (int)b->groups.size())
+    return VIO_ERR_INVALID_ARG;
+  const Group& G = b->groups[g];
+  const size_t bytes = (size_t)VIO_STATS_RING * G.spec.n_streams * VIO_N_STATS * 4;
+  int32_t ctr = 0;
+  if (cudaMemcpy(host_out, G.stats, bytes, cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(&ctr, G.step_ctr, 4, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return VIO_ERR_CUDA;
+  *n_steps = ctr;
+  return VIO_OK;
 }
 
 extern "C" vio_status vio_batch_set_initnet(vio_batch* b, const void* d_packed,

@@ -121,7 +121,7 @@ __device__ __forceinline__ float wgt(const uint16_t* W, int K, int n, int k) {
 __global__ void __launch_bounds__(TRAIN_WARPS * 32) train_kernel(
     const void* __restrict__ packed_w, const uint16_t* __restrict__ x,
     const float* __restrict__ flow, const int32_t* __restrict__ index, int n, float grad_scale,
-    float* __restrict__ grad, float* __restrict__ loss_sum) {
+    float radius, float* __restrict__ grad, float* __restrict__ loss_sum) {
   extern __shared__ __align__(16) uint8_t dsm[];
   float* gacc = reinterpret_cast<float*>(dsm);                       // N_MASTER
   uint8_t* wsm = dsm + ((N_MASTER * 4 + 127) & ~127);               // TRAIN_WARPS x WARP_SMEM
@@ -150,10 +150,10 @@ __global__ void __launch_bounds__(TRAIN_WARPS * 32) train_kernel(
     float o[3];
     forward_warp(P, ws, lane, o);
     __syncwarp();
-    // loss and dL/do (the 1 px label carries no gradient)
+    // loss and dL/do (the label carries no gradient)
     const float fx = flow[2 * sample], fy = flow[2 * sample + 1];
     const float t0 = fx / kScale, t1 = fy / kScale;
-    const float y = hypotf(o[0] * kScale - fx, o[1] * kScale - fy) < 1.f ? 1.f : 0.f;
+    const float y = hypotf(o[0] * kScale - fx, o[1] * kScale - fy) < radius ? 1.f : 0.f;
     const float sg = 1.f / (1.f + expf(-o[2]));
     const float loss = (o[0] - t0) * (o[0] - t0) + (o[1] - t1) * (o[1] - t1) -
                        (y * logf(sg + 1e-12f) + (1.f - y) * logf(1.f - sg + 1e-12f));
@@ -334,9 +334,10 @@ extern "C" vio_status vio_initnet_forward(const void* d_packed, const uint16_t* 
 
 extern "C" vio_status vio_initnet_train_step(const void* d_packed, const uint16_t* d_x,
                                              const float* d_flow, const int32_t* d_index,
-                                             int32_t n, float grad_scale, float* d_grad,
-                                             float* d_loss, void* stream) {
-  if (!d_packed || !d_x || !d_flow || !d_grad || !d_loss || n < 0) return VIO_ERR_INVALID_ARG;
+                                             int32_t n, float grad_scale, float label_radius,
+                                             float* d_grad, float* d_loss, void* stream) {
+  if (!d_packed || !d_x || !d_flow || !d_grad || !d_loss || n < 0 || !(label_radius > 0.f))
+    return VIO_ERR_INVALID_ARG;
   if (n == 0) return VIO_OK;
   const int smem = vio::initnet_train_smem();
   cudaError_t e = cudaFuncSetAttribute(vio::train_kernel,
@@ -348,7 +349,7 @@ extern "C" vio_status vio_initnet_train_step(const void* d_packed, const uint16_
   const int blocks = (int)std::min<long long>((long long)sms, (n + vio::TRAIN_WARPS - 1) /
                                                                   vio::TRAIN_WARPS);
   vio::train_kernel<<<blocks, vio::TRAIN_WARPS * 32, smem, (cudaStream_t)stream>>>(
-      d_packed, d_x, d_flow, d_index, n, grad_scale, d_grad, d_loss);
+      d_packed, d_x, d_flow, d_index, n, grad_scale, label_radius, d_grad, d_loss);
   return cudaGetLastError() == cudaSuccess ? VIO_OK : VIO_ERR_CUDA;
 }
 

@@ -1,0 +1,526 @@
+// Serving loop over a vio_batch (host runtime; the paper has no serving
+// layer). Sessions are client stereo streams of a few size classes; each
+// class is one group of the batch with a fixed number of resident slots,
+// sized from a device-memory budget. A session holds a slot from admission
+// to close (its pyramids, lists and frame slots stay on the device), and
+// waits in its class's FIFO while no slot is free.
+//
+// Continuous batching: frames are uploaded as they arrive (pinned host ->
+// a per-slot staging buffer, on the upload stream, overlapping the step in
+// flight); whenever no step is in flight, every admitted session with an
+// uploaded frame joins the next step: staging -> its batch slot (device to
+// device, on the compute stream after the upload's event), one batch step
+// (its captured graph), then the lists of every group are read back into
+// pinned buffers before the step's completion event. Completions carry the
+// frame's arrival, launch and completion times.
+#include <string.h>
+
+#include <chrono>
+#include <deque>
+#include <new>
+#include <vector>
+
+#include "frame.cuh"
+
+namespace {
+
+double now_s() {
+  using namespace std::chrono;
+  return duration<double>(steady_clock::now().time_since_epoch()).count();
+}
+
+struct Req {
+  const uint8_t* host;
+  double t_arrival;
+  int64_t tag;
+  int32_t flags;
+};
+
+struct Session {
+  int cls = -1, slot = -1;
+  bool open = false, closing = false;
+  std::deque<Req> queue;               // arrived, not yet uploaded
+  float* out_xy = nullptr;             // caller's host buffers (optional)
+  int32_t* out_id = nullptr;
+  int32_t* out_count = nullptr;
+};
+
+enum StageState { kFree = 0, kUploaded = 1, kInStep = 2 };
+
+struct Slot {
+  int64_t session = -1;
+  uint8_t* staging[2] = {nullptr, nullptr};
+  cudaEvent_t up_ev[2] = {nullptr, nullptr};
+  int state[2] = {kFree, kFree};
+  Req req[2];
+  int order = 0;                       // staging buffer of the oldest uploaded frame
+};
+
+struct Class {
+  vio_stream_group spec;
+  size_t frame_bytes = 0;
+  std::vector<Slot> slots;
+  std::deque<int64_t> waiting;
+  // pinned copies of the group's outputs after each step
+  float* h_xy = nullptr;
+  int32_t* h_id = nullptr;
+  int32_t* h_count = nullptr;
+  int32_t* h_new = nullptr;
+  std::vector<int32_t> parity;
+};
+
+struct Member {
+  int cls, slot, buf;
+  int64_t session;
+  Req req;
+};
+
+}  // namespace
+
+struct vio_server {
+  vio_batch* batch = nullptr;
+  std::vector<Class> cls;
+  std::vector<Session> sessions;
+  cudaStream_t cs = nullptr, us = nullptr;
+  cudaEvent_t step_ev = nullptr;
+  bool in_flight = false;
+  double t_launch = 0;
+  std::vector<Member> members;
+  std::vector<int32_t> active;
+  std::vector<vio_server_done> done;
+  std::vector<int64_t> closing;        // sessions closing while they hold a slot
+  uint8_t* d_staging = nullptr;
+  int64_t steps = 0;
+  int64_t budget = 0, used = 0;
+};
+
+namespace {
+
+int64_t slot_bytes(const vio_stream_group& g) {
+  vio_stream_group one = g;
+  one.n_streams = 1;
+  int64_t b = 0;
+  if (vio_batch_device_bytes(&one, 1, &b) != VIO_OK) return -1;
+  return b + 2 * 2 * (int64_t)g.w * g.h + 512;   // plus two staging frames
+}
+
+int stream_index(const vio_server* s, int c, int j) {
+  int k = 0;
+  for (int i = 0; i < c; ++i) k += (int)s->cls[i].slots.size();
+  return k + j;
+}
+
+void admit_waiting(vio_server* s, int c) {
+  Class& C = s->cls[c];
+  for (size_t j = 0; j < C.slots.size() && !C.waiting.empty(); ++j) {
+    if (C.slots[j].session >= 0) continue;
+    const int64_t id = C.waiting.front();
+    C.waiting.pop_front();
+    C.slots[j].session = id;
+    s->sessions[id].slot = (int)j;
+    if (s->sessions[id].closing) s->closing.push_back(id);
+    vio_batch_reset_stream(s->batch, c, (int)j, s->cs);   // a new stream starts fresh
+  }
+}
+
+void release_if_done(vio_server* s, int64_t id) {
+  Session& S = s->sessions[id];
+  if (!S.closing || S.slot < 0 || !S.queue.empty()) return;
+  Slot& L = s->cls[S.cls].slots[S.slot];
+  if (L.state[0] != kFree || L.state[1] != kFree) return;
+  L.session = -1;
+  S.slot = -1;
+  S.open = false;
+  admit_waiting(s, S.cls);
+}
+
+// Releases the slots of closing sessions whose frames are all done.
+void release_closing(vio_server* s) {
+  std::vector<int64_t> keep;
+  for (int64_t id : s->closing) {
+    release_if_done(s, id);
+    if (s->sessions[id].slot >= 0) keep.push_back(id);
+  }
+  s->closing.swap(keep);
+}
+
+// Completion of the step in flight: records, caller outputs, stage buffers.
+void complete_step(vio_server* s, int32_t status) {
+  const double t = now_s();
+  for (const Member& m : s->members) {
+    Class& C = s->cls[m.cls];
+    Slot& L = C.slots[m.slot];
+    Session& S = s->sessions[m.session];
+    vio_server_done d{};
+    d.session = m.session;
+    d.tag = m.req.tag;
+    d.t_arrival = m.req.t_arrival;
+    d.t_launch = s->t_launch;
+    d.t_done = t;
+    d.status = status;
+    if (status == VIO_OK) {
+      const int ns = C.spec.n_streams, cap = C.spec.capacity;
+      const int q = C.parity[m.slot];
+      const size_t base = ((size_t)q * ns + m.slot) * 2;
+      d.n_tracks[0] = C.h_count[base];
+      d.n_tracks[1] = C.h_count[base + 1];
+      d.n_new = C.h_new[m.slot];
+      if (S.out_count) {
+        S.out_count[0] = d.n_tracks[0];
+        S.out_count[1] = d.n_tracks[1];
+      }
+      for (int c = 0; c < 2; ++c) {
+        const size_t off = (base + c) * cap;
+        const int n = d.n_tracks[c] < cap ? d.n_tracks[c] : cap;
+        if (S.out_xy) memcpy(S.out_xy + 2 * (size_t)c * cap, C.h_xy + 2 * off, (size_t)n * 8);
+        if (S.out_id) memcpy(S.out_id + (size_t)c * cap, C.h_id + off, (size_t)n * 4);
+      }
+    }
+    s->done.push_back(d);
+    L.state[m.buf] = kFree;
+  }
+  s->members.clear();
+  s->in_flight = false;
+  release_closing(s);
+}
+
+// Uploads of arrived frames into free staging buffers.
+vio_status start_uploads(vio_server* s) {
+  for (size_t c = 0; c < s->cls.size(); ++c) {
+    Class& C = s->cls[c];
+    for (Slot& L : C.slots) {
+      if (L.session < 0) continue;
+      Session& S = s->sessions[L.session];
+      // buffers fill from L.order on, so the oldest uploaded frame is always
+      // the one at L.order (a launch takes it and moves L.order on)
+      for (int k = 0; k < 2 && !S.queue.empty(); ++k) {
+        const int b = (L.order + k) & 1;
+        if (L.state[b] != kFree) continue;
+        const Req r = S.queue.front();
+        if (cudaMemcpyAsync(L.staging[b], r.host, C.frame_bytes, cudaMemcpyHostToDevice,
+                            s->us) != cudaSuccess ||
+            cudaEventRecord(L.up_ev[b], s->us) != cudaSuccess)
+          return VIO_ERR_CUDA;
+        L.state[b] = kUploaded;
+        L.req[b] = r;
+        S.queue.pop_front();
+      }
+    }
+  }
+  return VIO_OK;
+}
+
+vio_status launch_step(vio_server* s) {
+  s->members.clear();
+  std::fill(s->active.begin(), s->active.end(), 0);
+  for (size_t c = 0; c < s->cls.size(); ++c) {
+    Class& C = s->cls[c];
+    for (size_t j = 0; j < C.slots.size(); ++j) {
+      Slot& L = C.slots[j];
+      if (L.session < 0) continue;
+      const int b = L.order;
+      if (L.state[b] != kUploaded) continue;
+      uint8_t* d_frame = nullptr;
+      if (vio_batch_next_frame(s->batch, (int)c, (int)j, &d_frame) != VIO_OK ||
+          cudaStreamWaitEvent(s->cs, L.up_ev[b], 0) != cudaSuccess ||
+          cudaMemcpyAsync(d_frame, L.staging[b], C.frame_bytes, cudaMemcpyDeviceToDevice,
+                          s->cs) != cudaSuccess)
+        return VIO_ERR_CUDA;
+      L.state[b] = kInStep;
+      L.order ^= 1;
+      s->members.push_back(Member{(int)c, (int)j, b, L.session, L.req[b]});
+      s->active[stream_index(s, (int)c, (int)j)] = 1;
+    }
+  }
+  if (s->members.empty()) return VIO_OK;
+  s->t_launch = now_s();
+  vio_status st = vio_batch_step(s->batch, s->active.data(), s->cs);
+  if (st != VIO_OK) return st;
+  std::vector<char> has(s->cls.size(), 0);
+  for (const Member& m : s->members) has[m.cls] = 1;
+  for (size_t c = 0; c < s->cls.size(); ++c) {
+    if (!has[c]) continue;
+    Class& C = s->cls[c];
+    vio_frontend_view v;
+    if (vio_batch_get_view(s->batch, (int)c, &v, C.parity.data()) != VIO_OK) return VIO_ERR_CUDA;
+    const size_t ns = C.spec.n_streams, cap = C.spec.capacity, lists = 2 * ns * 2;
+    if (cudaMemcpyAsync(C.h_count, v.d_track_count, lists * 4, cudaMemcpyDeviceToHost, s->cs) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(C.h_new, v.d_new_count, ns * 4, cudaMemcpyDeviceToHost, s->cs) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(C.h_xy, v.d_track_xy, lists * cap * 8, cudaMemcpyDeviceToHost, s->cs) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(C.h_id, v.d_track_id, lists * cap * 4, cudaMemcpyDeviceToHost, s->cs) !=
+            cudaSuccess)
+      return VIO_ERR_CUDA;
+  }
+  if (cudaEventRecord(s->step_ev, s->cs) != cudaSuccess) return VIO_ERR_CUDA;
+  s->in_flight = true;
+  ++s->steps;
+  return VIO_OK;
+}
+
+void destroy(vio_server* s) {
+  if (!s) return;
+  if (s->cs) cudaStreamSynchronize(s->cs);
+  if (s->us) cudaStreamSynchronize(s->us);
+  for (Class& C : s->cls) {
+    for (Slot& L : C.slots)
+      for (int b = 0; b < 2; ++b)
+        if (L.up_ev[b]) cudaEventDestroy(L.up_ev[b]);
+    cudaFreeHost(C.h_xy);
+    cudaFreeHost(C.h_id);
+    cudaFreeHost(C.h_count);
+    cudaFreeHost(C.h_new);
+  }
+  if (s->batch) vio_batch_destroy(s->batch);
+  cudaFree(s->d_staging);
+  if (s->step_ev) cudaEventDestroy(s->step_ev);
+  if (s->cs) cudaStreamDestroy(s->cs);
+  if (s->us) cudaStreamDestroy(s->us);
+  delete s;
+}
+
+}  // namespace
+
+extern "C" double vio_server_now(void) { return now_s(); }
+
+extern "C" vio_status vio_server_plan(const vio_stream_group* classes, int32_t n_classes,
+                                      int64_t budget_bytes, int32_t* slots_out,
+                                      int64_t* bytes_out) {
+  if (!classes || !slots_out || n_classes < 1 || n_classes > vio::kMaxGroups || budget_bytes < 0)
+    return VIO_ERR_INVALID_ARG;
+  std::vector<int64_t> per(n_classes);
+  int64_t want = 0;
+  for (int k = 0; k < n_classes; ++k) {
+    if (classes[k].n_streams < 1) return VIO_ERR_INVALID_ARG;
+    per[k] = slot_bytes(classes[k]);
+    if (per[k] < 0) return VIO_ERR_INVALID_ARG;
+    want += per[k] * classes[k].n_streams;
+  }
+  // every class keeps at least one slot; beyond that the slots scale down
+  // together until the budget holds them
+  int64_t total = 0;
+  for (int k = 0; k < n_classes; ++k) {
+    int64_t n = classes[k].n_streams;
+    if (want > budget_bytes) n = (int64_t)((double)n * (double)budget_bytes / (double)want);
+    if (n < 1) n = 1;
+    slots_out[k] = (int32_t)n;
+    total += n * per[k];
+  }
+  if (bytes_out) *bytes_out = total;
+  return total <= budget_bytes ? VIO_OK : VIO_ERR_OOM;
+}
+
+extern "C" vio_status vio_server_create(vio_server** out, const vio_stream_group* classes,
+                                        int32_t n_classes, int64_t budget_bytes) {
+  if (!out) return VIO_ERR_INVALID_ARG;
+  *out = nullptr;
+  std::vector<int32_t> slots(n_classes > 0 ? n_classes : 1);
+  int64_t bytes = 0;
+  vio_status st = vio_server_plan(classes, n_classes, budget_bytes, slots.data(), &bytes);
+  if (st != VIO_OK) return st;
+  vio_server* s = new (std::nothrow) vio_server();
+  if (!s) return VIO_ERR_OOM;
+  s->budget = budget_bytes;
+  s->used = bytes;
+  std::vector<vio_stream_group> groups(classes, classes + n_classes);
+  size_t staging = 0;
+  for (int k = 0; k < n_classes; ++k) {
+    groups[k].n_streams = slots[k];
+    staging += (size_t)slots[k] * 2 * 2 * groups[k].w * groups[k].h;
+  }
+  if (vio_batch_create(&s->batch, groups.data(), n_classes) != VIO_OK ||
+      cudaMalloc(&s->d_staging, staging) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&s->cs, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&s->us, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&s->step_ev, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    destroy(s);
+    return VIO_ERR_OOM;
+  }
+  vio_batch_set_graph(s->batch, 1);
+  uint8_t* q = s->d_staging;
+  int total = 0;
+  s->cls.resize(n_classes);
+  for (int k = 0; k < n_classes; ++k) {
+    Class& C = s->cls[k];
+    C.spec = groups[k];
+    C.frame_bytes = (size_t)2 * C.spec.w * C.spec.h;
+    C.slots.resize(slots[k]);
+    C.parity.assign(slots[k], 0);
+    for (Slot& L : C.slots)
+      for (int b = 0; b < 2; ++b) {
+        L.staging[b] = q;
+        q += C.frame_bytes;
+        if (cudaEventCreateWithFlags(&L.up_ev[b], cudaEventDisableTiming) != cudaSuccess) {
+          destroy(s);
+          return VIO_ERR_CUDA;
+        }
+      }
+    const size_t lists = (size_t)2 * slots[k] * 2, cap = C.spec.capacity;
+    if (cudaMallocHost(&C.h_xy, lists * cap * 8) != cudaSuccess ||
+        cudaMallocHost(&C.h_id, lists * cap * 4) != cudaSuccess ||
+        cudaMallocHost(&C.h_count, lists * 4) != cudaSuccess ||
+        cudaMallocHost(&C.h_new, (size_t)slots[k] * 4) != cudaSuccess) {
+      cudaGetLastError();
+      destroy(s);
+      return VIO_ERR_OOM;
+    }
+    total += slots[k];
+  }
+  s->active.assign(total, 0);
+  *out = s;
+  return VIO_OK;
+}
+
+extern "C" vio_status vio_server_destroy(vio_server* s) {
+  if (!s) return VIO_ERR_INVALID_ARG;
+  destroy(s);
+  return VIO_OK;
+}
+
+extern "C" vio_status vio_server_slots(const vio_server* s, int32_t cls, int32_t* n_slots,
+                                       int64_t* device_bytes) {
+  if (!s || cls < 0 || cls >= (int)s->cls.size()) return VIO_ERR_INVALID_ARG;
+  if (n_slots) *n_slots = (int32_t)s->cls[cls].slots.size();
+  if (device_bytes) *device_bytes = s->used;
+  return VIO_OK;
+}
+
+extern "C" vio_status vio_server_set_initnet(vio_server* s, const void* d_packed,
+                                             const vio_initnet_cfg* cfg) {
+  if (!s) return VIO_ERR_INVALID_ARG;
+  if (s->in_flight && cudaStreamSynchronize(s->cs) != cudaSuccess) return VIO_ERR_CUDA;
+  return vio_batch_set_initnet(s->batch, d_packed, cfg);
+}
+
+extern "C" vio_status vio_server_set_tune(vio_server* s, const vio_batch_tune* t) {
+  if (!s) return VIO_ERR_INVALID_ARG;
+  if (s->in_flight && cudaStreamSynchronize(s->cs) != cudaSuccess) return VIO_ERR_CUDA;
+  return vio_batch_set_tune(s->batch, t);
+}
+
+extern "C" vio_status vio_server_open(vio_server* s, int32_t cls, int64_t* session,
+                                      int32_t* admitted) {
+  if (!s || !session || cls < 0 || cls >= (int)s->cls.size()) return VIO_ERR_INVALID_ARG;
+  const int64_t id = (int64_t)s->sessions.size();
+  s->sessions.emplace_back();
+  Session& S = s->sessions.back();
+  S.cls = cls;
+  S.open = true;
+  s->cls[cls].waiting.push_back(id);
+  admit_waiting(s, cls);
+  *session = id;
+  if (admitted) *admitted = s->sessions[id].slot >= 0;
+  return VIO_OK;
+}
+
+extern "C" vio_status vio_server_set_output(vio_server* s, int64_t session, float* host_xy,
+                                            int32_t* host_id, int32_t* host_count) {
+  if (!s || session < 0 || session >= (int64_t)s->sessions.size()) return VIO_ERR_INVALID_ARG;
+  Session& S = s->sessions[session];
+  S.out_xy = host_xy;
+  S.out_id = host_id;
+  S.out_count = host_count;
+  return VIO_OK;
+}
+
+extern "C" vio_status vio_server_submit(vio_server* s, int64_t session,
+                                        const uint8_t* host_frame, double t_arrival, int64_t tag,
+                                        int32_t flags) {
+  if (!s || !host_frame || session < 0 || session >= (int64_t)s->sessions.size())
+    return VIO_ERR_INVALID_ARG;
+  Session& S = s->sessions[session];
+  if (!S.open || S.closing) return VIO_ERR_INVALID_ARG;
+  S.queue.push_back(Req{host_frame, t_arrival, tag, flags});
+  if (flags & VIO_SERVER_LAST) {
+    S.closing = true;
+    if (S.slot >= 0) s->closing.push_back(session);
+  }
+  return VIO_OK;
+}
+
+extern "C" vio_status vio_server_close(vio_server* s, int64_t session) {
+  if (!s || session < 0 || session >= (int64_t)s->sessions.size()) return VIO_ERR_INVALID_ARG;
+  Session& S = s->sessions[session];
+  if (!S.open) return VIO_OK;
+  S.closing = true;
+  if (S.slot < 0) {               // still waiting: leave the queue
+    auto& w = s->cls[S.cls].waiting;
+    for (auto it = w.begin(); it != w.end(); ++it)
+      if (*it == session) {
+        w.erase(it);
+        break;
+      }
+    S.queue.clear();
+    S.open = false;
+    return VIO_OK;
+  }
+  s->closing.push_back(session);
+  if (!s->in_flight) release_closing(s);
+  return VIO_OK;
+}
+
+extern "C" vio_status vio_server_poll(vio_server* s, int32_t* n_done) {
+  if (!s) return VIO_ERR_INVALID_ARG;
+  vio_status st = VIO_OK;
+  if (s->in_flight) {
+    const cudaError_t e = cudaEventQuery(s->step_ev);
+    if (e == cudaSuccess) {
+      complete_step(s, VIO_OK);
+    } else if (e != cudaErrorNotReady) {
+      cudaGetLastError();
+      complete_step(s, VIO_ERR_CUDA);
+      st = VIO_ERR_CUDA;
+    }
+  }
+  if (st == VIO_OK) st = start_uploads(s);
+  if (st == VIO_OK && !s->in_flight) {
+    st = launch_step(s);
+    if (st != VIO_OK) complete_step(s, st);   // report the frames that did not run
+  }
+  if (n_done) *n_done = (int32_t)s->done.size();
+  return st;
+}
+
+extern "C" int32_t vio_server_take(vio_server* s, vio_server_done* out, int32_t max) {
+  if (!s || !out || max <= 0) return 0;
+  const int32_t n = (int32_t)std::min<size_t>((size_t)max, s->done.size());
+  for (int32_t i = 0; i < n; ++i) out[i] = s->done[i];
+  s->done.erase(s->done.begin(), s->done.begin() + n);
+  return n;
+}
+
+extern "C" vio_status vio_server_run_trace(vio_server* s, const vio_server_req* reqs,
+                                           int64_t n, vio_server_done* out, double timeout_s,
+                                           int64_t* n_steps) {
+  if (!s || (!reqs && n) || (!out && n) || n < 0) return VIO_ERR_INVALID_ARG;
+  for (int64_t i = 1; i < n; ++i)
+    if (reqs[i].t_offset < reqs[i - 1].t_offset) return VIO_ERR_INVALID_ARG;
+  const int64_t steps0 = s->steps;
+  const double t0 = now_s();
+  int64_t next = 0, got = 0;
+  vio_status st = VIO_OK;
+  while (got < n) {
+    const double t = now_s() - t0;
+    if (t > timeout_s) {
+      st = VIO_ERR_TIMEOUT;
+      break;
+    }
+    while (next < n && reqs[next].t_offset <= t) {
+      const vio_server_req& r = reqs[next];
+      st = vio_server_submit(s, r.session, r.host_frame, t0 + r.t_offset, r.tag, r.flags);
+      if (st != VIO_OK) break;
+      ++next;
+    }
+    if (st != VIO_OK) break;
+    int32_t nd = 0;
+    const vio_status ps = vio_server_poll(s, &nd);
+    if (ps != VIO_OK && st == VIO_OK) st = ps;
+    got += vio_server_take(s, out + got, (int32_t)(n - got));
+    if (st != VIO_OK) break;
+  }
+  if (n_steps) *n_steps = s->steps - steps0;
+  return st;
+}

@@ -66,6 +66,19 @@ class InitNetCfg(ctypes.Structure):
                 ("start_level", ctypes.c_int32), ("min_conf", ctypes.c_float)]
 
 
+class ServerReq(ctypes.Structure):
+    _fields_ = [("session", ctypes.c_int64), ("t_offset", ctypes.c_double),
+                ("host_frame", ctypes.c_void_p), ("tag", ctypes.c_int64),
+                ("flags", ctypes.c_int32)]
+
+
+class ServerDone(ctypes.Structure):
+    _fields_ = [("session", ctypes.c_int64), ("tag", ctypes.c_int64),
+                ("t_arrival", ctypes.c_double), ("t_launch", ctypes.c_double),
+                ("t_done", ctypes.c_double), ("n_tracks", ctypes.c_int32 * 2),
+                ("n_new", ctypes.c_int32), ("status", ctypes.c_int32)]
+
+
 _lib = None
 _lock = threading.Lock()
 
@@ -144,10 +157,42 @@ _SIGS = {
     "vio_batch_get_view": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32,
                                             ctypes.POINTER(FrontendView), ctypes.c_void_p]),
     "vio_batch_launches_per_step": (ctypes.c_int32, [ctypes.c_void_p]),
+    "vio_batch_read_stats": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
+                                              ctypes.POINTER(ctypes.c_int64)]),
     "vio_frontend_set_initnet": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p,
                                                   ctypes.POINTER(InitNetCfg)]),
     "vio_batch_set_initnet": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p,
                                                ctypes.POINTER(InitNetCfg)]),
+    "vio_batch_device_bytes": (ctypes.c_int32, [ctypes.POINTER(StreamGroup), ctypes.c_int32,
+                                                ctypes.POINTER(ctypes.c_int64)]),
+    "vio_server_now": (ctypes.c_double, []),
+    "vio_server_plan": (ctypes.c_int32, [ctypes.POINTER(StreamGroup), ctypes.c_int32,
+                                         ctypes.c_int64, ctypes.c_void_p,
+                                         ctypes.POINTER(ctypes.c_int64)]),
+    "vio_server_create": (ctypes.c_int32, [ctypes.POINTER(ctypes.c_void_p),
+                                           ctypes.POINTER(StreamGroup), ctypes.c_int32,
+                                           ctypes.c_int64]),
+    "vio_server_destroy": (ctypes.c_int32, [ctypes.c_void_p]),
+    "vio_server_slots": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32,
+                                          ctypes.POINTER(ctypes.c_int32),
+                                          ctypes.POINTER(ctypes.c_int64)]),
+    "vio_server_set_initnet": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p,
+                                                ctypes.POINTER(InitNetCfg)]),
+    "vio_server_set_tune": (ctypes.c_int32, [ctypes.c_void_p, ctypes.POINTER(BatchTune)]),
+    "vio_server_open": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32,
+                                         ctypes.POINTER(ctypes.c_int64),
+                                         ctypes.POINTER(ctypes.c_int32)]),
+    "vio_server_set_output": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                                               ctypes.c_void_p, ctypes.c_void_p]),
+    "vio_server_submit": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                                           ctypes.c_double, ctypes.c_int64, ctypes.c_int32]),
+    "vio_server_close": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int64]),
+    "vio_server_poll": (ctypes.c_int32, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32)]),
+    "vio_server_take": (ctypes.c_int32, [ctypes.c_void_p, ctypes.POINTER(ServerDone),
+                                         ctypes.c_int32]),
+    "vio_server_run_trace": (ctypes.c_int32, [ctypes.c_void_p, ctypes.POINTER(ServerReq),
+                                              ctypes.c_int64, ctypes.POINTER(ServerDone),
+                                              ctypes.c_double, ctypes.POINTER(ctypes.c_int64)]),
     "vio_initnet_pack": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "vio_initnet_extract": (ctypes.c_int32, [ctypes.POINTER(PyrLayout), ctypes.POINTER(PyrBatch),
                                              ctypes.POINTER(PyrBatch), ctypes.c_void_p,
@@ -157,7 +202,7 @@ _SIGS = {
                                              ctypes.c_void_p, ctypes.c_void_p]),
     "vio_initnet_train_step": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p,
                                                 ctypes.c_void_p, ctypes.c_void_p,
-                                                ctypes.c_int32, ctypes.c_float,
+                                                ctypes.c_int32, ctypes.c_float, ctypes.c_float,
                                                 ctypes.c_void_p, ctypes.c_void_p,
                                                 ctypes.c_void_p]),
     "vio_initnet_adam": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
@@ -402,10 +447,11 @@ def initnet_forward(packed, x, n, out, stream=None):
            "vio_initnet_forward")
 
 
-def initnet_train_step(packed, x, flow, index, n, grad_scale, grad, loss, stream=None):
+def initnet_train_step(packed, x, flow, index, n, grad_scale, grad, loss, label_radius=1.0,
+                       stream=None):
     _check(load().vio_initnet_train_step(_ptr(packed), _ptr(x), _ptr(flow), _ptr(index), n,
-                                         grad_scale, _ptr(grad), _ptr(loss), _stream(stream)),
-           "vio_initnet_train_step")
+                                         grad_scale, label_radius, _ptr(grad), _ptr(loss),
+                                         _stream(stream)), "vio_initnet_train_step")
 
 
 def initnet_adam(master, grad, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
@@ -451,11 +497,12 @@ class InitNet:
         initnet_forward(self.packed, x, n, out, stream)
         return out
 
-    def save(self, path):
+    def save(self, path, **meta):
+        """meta: further named values stored beside the weights (numbers)."""
         import numpy as np
-        extra = {}
+        extra = {k: np.asarray(v) for k, v in meta.items()}
         if self.m is not None:
-            extra = {"m": self.m.cpu().numpy(), "v": self.v.cpu().numpy()}
+            extra.update(m=self.m.cpu().numpy(), v=self.v.cpu().numpy())
         np.savez(path, master=self.master.cpu().numpy(),
                  cfg=np.array([self.cfg.level_a, self.cfg.level_b, self.cfg.start_level],
                               np.int32),
@@ -661,6 +708,16 @@ class Batch:
     def launches_per_step(self) -> int:
         return int(load().vio_batch_launches_per_step(self.handle))
 
+    def read_stats(self, g: int):
+        """(ring array (STATS_RING, n_streams_g, len(STAT_NAMES)), steps run)."""
+        import numpy as np
+        n = self.groups[g][2]
+        out = np.zeros((STATS_RING, n, len(STAT_NAMES)), np.int32)
+        steps = ctypes.c_int64()
+        _check(load().vio_batch_read_stats(self.handle, g, out.ctypes.data_as(ctypes.c_void_p),
+                                           ctypes.byref(steps)), "vio_batch_read_stats")
+        return out, int(steps.value)
+
     def set_initnet(self, net: "InitNet | None"):
         """Learned start of temporal tracking for every stream (see Frontend)."""
         self._net = net
@@ -696,3 +753,149 @@ class Batch:
         xy = [v["track_xy"][q, s, c, : cnt[c]].cpu().numpy() for c in range(2)]
         ids = [v["track_id"][q, s, c, : cnt[c]].cpu().numpy() for c in range(2)]
         return xy, ids
+
+
+# ------------------------------------------------------------------ serving --
+
+SERVER_LAST = 1
+DONE_FIELDS = ("session", "tag", "t_arrival", "t_launch", "t_done", "n_tracks0", "n_tracks1",
+               "n_new", "status")
+
+
+def _groups_array(classes):
+    arr = (StreamGroup * len(classes))()
+    for i, (p, w, h, n, cap) in enumerate(classes):
+        arr[i].params = p
+        arr[i].w, arr[i].h, arr[i].n_streams, arr[i].capacity = w, h, n, cap
+    return arr
+
+
+def _hptr(a):
+    """Address of a contiguous host buffer (numpy array or CPU tensor)."""
+    if isinstance(a, torch.Tensor):
+        if a.is_cuda or not a.is_contiguous():
+            raise ValueError("expected a contiguous CPU tensor")
+        return ctypes.c_void_p(a.data_ptr())
+    if not a.flags["C_CONTIGUOUS"]:
+        raise ValueError("expected a contiguous array")
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def batch_device_bytes(classes) -> int:
+    b = ctypes.c_int64()
+    _check(load().vio_batch_device_bytes(_groups_array(classes), len(classes), ctypes.byref(b)),
+           "vio_batch_device_bytes")
+    return int(b.value)
+
+
+def server_plan(classes, budget_bytes: int):
+    """(slots per class, device bytes) that vio_server_create would use; raises
+    VioError (out of memory) if one slot per class exceeds the budget."""
+    import numpy as np
+    slots = np.zeros(len(classes), np.int32)
+    b = ctypes.c_int64()
+    _check(load().vio_server_plan(_groups_array(classes), len(classes), int(budget_bytes),
+                                  slots.ctypes.data_as(ctypes.c_void_p), ctypes.byref(b)),
+           "vio_server_plan")
+    return slots.tolist(), int(b.value)
+
+
+def server_now() -> float:
+    return float(load().vio_server_now())
+
+
+def _done_rows(arr, n):
+    import numpy as np
+    out = np.zeros(n, dtype=[(k, np.float64 if k.startswith("t_") else np.int64)
+                             for k in DONE_FIELDS])
+    for i in range(n):
+        d = arr[i]
+        out[i] = (d.session, d.tag, d.t_arrival, d.t_launch, d.t_done, d.n_tracks[0],
+                  d.n_tracks[1], d.n_new, d.status)
+    return out
+
+
+class Server:
+    """vio_server: sessions of a few size classes, admitted by a device-memory
+    budget, served by continuous batching. classes: list of (params, w, h,
+    sessions wanted, capacity). Host frames must be pinned."""
+
+    def __init__(self, classes, budget_bytes: int):
+        self.classes = [(w, h, n, cap) for (_, w, h, n, cap) in classes]
+        hdl = ctypes.c_void_p()
+        _check(load().vio_server_create(ctypes.byref(hdl), _groups_array(classes), len(classes),
+                                        int(budget_bytes)), "vio_server_create")
+        self.handle = hdl
+        self._keep = {}
+
+    def close_server(self):
+        if self.handle:
+            load().vio_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close_server()
+        except Exception:
+            pass
+
+    def slots(self, cls: int):
+        n = ctypes.c_int32()
+        b = ctypes.c_int64()
+        _check(load().vio_server_slots(self.handle, cls, ctypes.byref(n), ctypes.byref(b)),
+               "vio_server_slots")
+        return int(n.value), int(b.value)
+
+    def set_initnet(self, net: "InitNet | None"):
+        self._net = net
+        _check(load().vio_server_set_initnet(self.handle, _ptr(net.packed) if net else None,
+                                             ctypes.byref(net.cfg) if net else None),
+               "vio_server_set_initnet")
+
+    def set_tune(self, k2_threads: int, pyr_tile_shift: int):
+        t = BatchTune(k2_threads, pyr_tile_shift)
+        _check(load().vio_server_set_tune(self.handle, ctypes.byref(t)), "vio_server_set_tune")
+
+    def open(self, cls: int):
+        sid = ctypes.c_int64()
+        adm = ctypes.c_int32()
+        _check(load().vio_server_open(self.handle, cls, ctypes.byref(sid), ctypes.byref(adm)),
+               "vio_server_open")
+        return int(sid.value), bool(adm.value)
+
+    def set_output(self, session: int, xy, ids, count):
+        self._keep[("out", session)] = (xy, ids, count)
+        _check(load().vio_server_set_output(self.handle, session, _hptr(xy), _hptr(ids),
+                                            _hptr(count)), "vio_server_set_output")
+
+    def submit(self, session: int, frame, t_arrival: float, tag: int, flags: int = 0):
+        _check(load().vio_server_submit(self.handle, session, _hptr(frame), t_arrival, tag,
+                                        flags), "vio_server_submit")
+
+    def close(self, session: int):
+        _check(load().vio_server_close(self.handle, session), "vio_server_close")
+
+    def poll(self) -> int:
+        n = ctypes.c_int32()
+        _check(load().vio_server_poll(self.handle, ctypes.byref(n)), "vio_server_poll")
+        return int(n.value)
+
+    def take(self, max_n: int = 1024):
+        arr = (ServerDone * max_n)()
+        n = load().vio_server_take(self.handle, arr, max_n)
+        return _done_rows(arr, n)
+
+    def run_trace(self, reqs, timeout_s: float = 600.0):
+        """reqs: list of (session, t_offset, pinned frame, tag, flags), ascending
+        t_offset. Returns (completions structured array, steps run)."""
+        n = len(reqs)
+        arr = (ServerReq * max(n, 1))()
+        for i, (sid, t, fr, tag, fl) in enumerate(reqs):
+            arr[i].session, arr[i].t_offset = sid, t
+            arr[i].host_frame = _hptr(fr).value
+            arr[i].tag, arr[i].flags = tag, fl
+        out = (ServerDone * max(n, 1))()
+        steps = ctypes.c_int64()
+        _check(load().vio_server_run_trace(self.handle, arr, n, out, timeout_s,
+                                           ctypes.byref(steps)), "vio_server_run_trace")
+        return _done_rows(out, n), int(steps.value)

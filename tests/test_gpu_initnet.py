@@ -154,7 +154,8 @@ def test_forward_matches_oracle(n):
     assert np.median(err[:, :2]) < 16 * 1e-4
 
 
-def test_train_gradient_matches_oracle():
+@pytest.mark.parametrize("radius", [1.0, 3.0])
+def test_train_gradient_matches_oracle(radius):
     n = 48
     flat = onet.flatten(he_params(2))
     _, packed = packed_of(flat)
@@ -162,20 +163,20 @@ def test_train_gradient_matches_oracle():
     x = _inputs(n, 7)
     rng = np.random.default_rng(8)
     # targets at a chosen distance from the oracle's prediction, away from the
-    # 1 px label boundary so that both sides give every sample the same label
+    # label boundary so that both sides give every sample the same label
     flows = []
     for xi in x:
         o = onet.forward(p, xi, act_bf16=True)
-        r = rng.choice([rng.uniform(0.0, 0.8), rng.uniform(1.2, 6.0)])
+        r = rng.choice([rng.uniform(0.0, 0.8 * radius), rng.uniform(1.2 * radius, 6.0 * radius)])
         a = rng.uniform(0, 2 * np.pi)
         flows.append([o[0] * 16 + r * np.cos(a), o[1] * 16 + r * np.sin(a)])
     flows = np.array(flows, np.float32).astype(np.float64)
-    loss_ref, g_ref = onet.batch_loss_grad(p, x, flows, act_bf16=True)
+    loss_ref, g_ref = onet.batch_loss_grad(p, x, flows, act_bf16=True, radius=radius)
     xb = torch.from_numpy(bits_of(x.reshape(n, -1)).view(np.int16)).to(DEV)
     grad = torch.zeros(vio.INITNET_N_PARAMS, dtype=torch.float32, device=DEV)
     loss = torch.zeros(1, dtype=torch.float32, device=DEV)
     vio.initnet_train_step(packed, xb, torch.from_numpy(flows.astype(np.float32)).to(DEV), None,
-                           n, 1.0 / n, grad, loss)
+                           n, 1.0 / n, grad, loss, label_radius=radius)
     torch.cuda.synchronize()
     assert loss.item() / n == pytest.approx(loss_ref, rel=1e-3)
     g = onet.unflatten(grad.cpu().numpy().astype(np.float64))

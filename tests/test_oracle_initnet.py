@@ -112,3 +112,14 @@ def test_bf16_activations_only_round_the_stored_values():
         assert np.array_equal(net.bf16_round(act[k]), act[k])
     # BF16 storage perturbs each activation by at most 2^-9 relative
     assert np.max(np.abs(o16 - o64)) < 0.05 * (1 + np.max(np.abs(o64)))
+
+
+def test_label_radius_sets_the_confidence_target():
+    o = np.array([0.2, -0.1, 0.3])
+    flow = np.array([2.0, -3.0])              # about 1.8 px from the prediction (3.2, -1.6)
+    d = np.hypot(0.2 * 16 - 2.0, -0.1 * 16 + 3.0)
+    s = 1 / (1 + np.exp(-0.3))
+    _, do_in = net.loss_and_grad_out(o, flow, radius=d + 0.01)
+    _, do_out = net.loss_and_grad_out(o, flow, radius=d - 0.01)
+    assert do_in[2] == pytest.approx(s - 1) and do_out[2] == pytest.approx(s)
+    assert do_in[0] == do_out[0] and do_in[1] == do_out[1]
