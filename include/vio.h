@@ -538,8 +538,8 @@ vio_status vio_server_run_trace(vio_server* s, const vio_server_req* reqs, int64
  * a packed copy (VIO_INITNET_PACKED_BYTES, 16-byte aligned): BF16 weights and
  * FP32 biases, written by vio_initnet_pack. Activations are BF16 between
  * layers, accumulation is FP32. Inputs x are BF16 bit patterns (uint16),
- * [n][4][16][16]. All calls are enqueued on `stream`; pointers are device
- * pointers owned by the caller.
+ * [n][4][16][16], 16-byte aligned. All calls are enqueued on `stream`;
+ * pointers are device pointers owned by the caller.
  * ------------------------------------------------------------------------- */
 #define VIO_INITNET_N_PARAMS 28131
 #define VIO_INITNET_PACKED_BYTES 58016

@@ -120,41 +120,49 @@ struct MultiK2 {
   FrameLaunch f[kMaxGroups];
 };
 
-constexpr int KN_WARPS = 4;
+// Flow proposals of every live track: persistent CTAs over tiles of TT
+// consecutive slots of one keypoint list (the temporal numbering of
+// frame_track_kernel: list (2 stream + camera), slot); tiles past a list's
+// count are skipped whole.
+struct MultiKN {
+  int n;
+  long long block_end[kMaxGroups];   // in tiles
+  FrameLaunch f[kMaxGroups];
+};
 
-// Flow proposals of every live track (same warp numbering as the temporal
-// part of frame_track_kernel); each warp loops over keypoints, so its
-// activation buffers are cleared once.
-__global__ void __launch_bounds__(KN_WARPS * 32) frame_initnet_kernel(const __grid_constant__ MultiK2 mm) {
-  __shared__ __align__(16) uint8_t smem[KN_WARPS][net::WARP_SMEM];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  uint8_t* ws = smem[warp];
-  net::clear_warp_smem(ws, lane);
+__global__ void __launch_bounds__(net::TILE_THREADS, 1) frame_initnet_kernel(
+    const __grid_constant__ MultiKN mm) {
+  extern __shared__ __align__(16) uint8_t sm[];
+  net::tile_setup(net::packed(mm.f[0].net), sm);
+  const net::TileSmem S = net::tile_smem(sm);
   const long long total = mm.block_end[mm.n - 1];
-  for (long long w = (long long)blockIdx.x * KN_WARPS + warp; w < total;
-       w += (long long)gridDim.x * KN_WARPS) {
+  for (long long tile = blockIdx.x; tile < total; tile += gridDim.x) {
     long long start;
-    const int gi = group_of(mm, w, start);
+    const int gi = group_of(mm, tile, start);
     const FrameLaunch& f = mm.f[gi];
-    const long long wl = w - start;
-    const int list = (int)(wl / f.cap);
-    const int slot = (int)(wl - (long long)list * f.cap);
+    const int tpl = (f.cap + net::TT - 1) / net::TT;
+    const long long lt = tile - start;
+    const int list = (int)(lt / tpl);
+    const int j = (int)(lt - (long long)list * tpl);
     const int s = list >> 1, c = list & 1;
     const StreamRef r = stream_ref(f, s);
     if (!r.active || !r.have_prev) continue;
     const long long in_list = ((long long)r.li * f.n_streams + s) * 2 + c;
-    if (slot >= f.list_count[in_list]) continue;
-    const long long src = in_list * f.cap + slot;
-    net::extract_warp(f.g, f.prev, r.prev_img + c, f.cur, r.cur_img + c, f.list_xy[2 * src],
-                      f.list_xy[2 * src + 1], f.net_la, f.net_lb, ws, lane);
-    float o[3];
-    net::forward_warp(net::packed(f.net), ws, lane, o);
-    if (lane == 0) {
-      f.net_out[3 * wl] = o[0] * net::kScale;
-      f.net_out[3 * wl + 1] = o[1] * net::kScale;
-      f.net_out[3 * wl + 2] = 1.f / (1.f + expf(-o[2]));
+    const int count = min(f.list_count[in_list], f.cap);
+    const int s0 = j * net::TT;
+    if (s0 >= count) continue;
+    const int nv = min(net::TT, count - s0);
+    const float* xy = f.list_xy + 2 * (in_list * f.cap + s0);
+    net::tile_clear_input_border(S);
+    for (int e = threadIdx.x; e < nv * 64; e += blockDim.x) {   // (keypoint, channel, row)
+      const int k = e >> 6;
+      net::tile_input_row(S, k, (e >> 4) & 3, e & 15, f.g, f.prev, r.prev_img + c, f.cur,
+                          r.cur_img + c, xy[2 * k], xy[2 * k + 1], f.net_la, f.net_lb);
     }
-    __syncwarp();
+    __syncthreads();
+    net::tile_forward(S);
+    float* o = f.net_out + 3 * ((long long)list * f.cap + s0);
+    for (int i = threadIdx.x; i < nv * 3; i += blockDim.x) o[i] = S.out[i];
   }
 }
 
@@ -548,24 +556,26 @@ cudaError_t launch_frames(const FrameLaunch* fl, int n_groups, const FrameTune& 
   // KN: flow proposals (every group has the initializer on, or none)
   mark(2);
   if (fl[0].net) {
-    MultiK2 mn{};
+    MultiKN mn{};
     mn.n = n_groups;
     acc = 0;
     for (int i = 0; i < n_groups; ++i) {
       mn.f[i] = fl[i];
-      acc += 2LL * fl[i].n_streams * fl[i].cap;
+      acc += 2LL * fl[i].n_streams * ((fl[i].cap + net::TT - 1) / net::TT);
       mn.block_end[i] = acc;
     }
     static int sms = 0;
     if (!sms) {
       int dev = 0;
       if (cudaGetDevice(&dev) != cudaSuccess ||
-          cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+          cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+          cudaFuncSetAttribute(frame_initnet_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               net::TILE_SMEM) != cudaSuccess)
         return cudaErrorUnknown;
     }
-    const long long need = (acc + KN_WARPS - 1) / KN_WARPS;
-    const long long blocks = need < 4LL * sms ? need : 4LL * sms;
-    if (blocks > 0) frame_initnet_kernel<<<(unsigned)blocks, KN_WARPS * 32, 0, s>>>(mn);
+    const long long blocks = acc < sms ? acc : sms;
+    if (blocks > 0)
+      frame_initnet_kernel<<<(unsigned)blocks, net::TILE_THREADS, net::TILE_SMEM, s>>>(mn);
   }
 
   // K2: temporal tracking + stereo matching of all candidates

@@ -92,21 +92,34 @@ __device__ __forceinline__ void load_input(const uint16_t* __restrict__ x, uint8
   __syncwarp();
 }
 
-__global__ void forward_kernel(const void* __restrict__ packed_w, const uint16_t* __restrict__ x,
-                               int n, float* __restrict__ out) {
-  __shared__ __align__(16) uint8_t smem[4][WARP_SMEM];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const long long wid = (long long)blockIdx.x * 4 + warp;
-  if (wid >= n) return;
-  uint8_t* ws = smem[warp];
-  clear_warp_smem(ws, lane);
-  load_input(x + wid * 1024, ws, lane);
-  float o[3];
-  forward_warp(packed(packed_w), ws, lane, o);
-  if (lane == 0) {
-    out[3 * wid] = o[0] * kScale;
-    out[3 * wid + 1] = o[1] * kScale;
-    out[3 * wid + 2] = 1.f / (1.f + expf(-o[2]));
+// Tiled inference over n inputs ([n][4][16][16] BF16): persistent CTAs, TT
+// inputs per tile.
+__global__ void __launch_bounds__(TILE_THREADS, 1) forward_tile_kernel(
+    const void* __restrict__ packed_w, const uint16_t* __restrict__ x, int n,
+    float* __restrict__ out) {
+  extern __shared__ __align__(16) uint8_t sm[];
+  tile_setup(packed(packed_w), sm);
+  const TileSmem S = tile_smem(sm);
+  const int n_tiles = (n + TT - 1) / TT;
+  for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+    const int s0 = tile * TT, nv = min(TT, n - s0);
+    tile_clear_input_border(S);
+    for (int e = threadIdx.x; e < nv * 64; e += blockDim.x) {   // (sample, channel, row)
+      const int sidx = e >> 6, ch = (e >> 4) & 3, r = e & 15;
+      const uint4* src = reinterpret_cast<const uint4*>(x + (long long)(s0 + sidx) * 1024 +
+                                                        ch * 256 + r * 16);
+      const uint4 lo = __ldg(src), hi = __ldg(src + 1);
+      const uint32_t wv[8] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
+      uint16_t* out = S.x + sidx * XR_SAMPLE + (r + 1) * X_ROW + X_PIX + ch;
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        out[(2 * c) * X_PIX] = (uint16_t)(wv[c] & 0xffffu);
+        out[(2 * c + 1) * X_PIX] = (uint16_t)(wv[c] >> 16);
+      }
+    }
+    __syncthreads();
+    tile_forward(S);
+    for (int i = threadIdx.x; i < nv * 3; i += blockDim.x) out[(long long)s0 * 3 + i] = S.out[i];
   }
 }
 
@@ -326,9 +339,20 @@ extern "C" vio_status vio_initnet_extract(const vio_pyr_layout* layout, const vi
 
 extern "C" vio_status vio_initnet_forward(const void* d_packed, const uint16_t* d_x, int32_t n,
                                           float* d_out, void* stream) {
-  if (!d_packed || !d_x || !d_out || n < 0) return VIO_ERR_INVALID_ARG;
+  using namespace vio::net;
+  if (!d_packed || !d_x || !d_out || n < 0 || ((uintptr_t)d_packed & 15) ||
+      ((uintptr_t)d_x & 15))
+    return VIO_ERR_INVALID_ARG;
   if (n == 0) return VIO_OK;
-  vio::forward_kernel<<<(n + 3) / 4, 128, 0, (cudaStream_t)stream>>>(d_packed, d_x, n, d_out);
+  if (cudaFuncSetAttribute(vio::forward_tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           TILE_SMEM) != cudaSuccess)
+    return VIO_ERR_CUDA;
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int tiles = (n + TT - 1) / TT;
+  vio::forward_tile_kernel<<<tiles < sms ? tiles : sms, TILE_THREADS, TILE_SMEM,
+                             (cudaStream_t)stream>>>(d_packed, d_x, n, d_out);
   return cudaGetLastError() == cudaSuccess ? VIO_OK : VIO_ERR_CUDA;
 }
 

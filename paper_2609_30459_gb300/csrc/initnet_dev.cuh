@@ -262,3 +262,322 @@ __device__ __forceinline__ void extract_warp(const Geom& g, const Batch& src, in
 
 }  // namespace net
 }  // namespace vio
+
+namespace vio {
+namespace net {
+
+// ---------------------------------------------------------------------------
+// Tiled inference: one CTA evaluates TT samples at a time, layer by layer,
+// with the weights staged once per CTA in shared memory and every MMA tile
+// filled with 16 rows (conv1: 64 positions x TT samples, conv2: 16 x TT,
+// conv3: 4 x TT, dense layers: TT samples).
+//
+// Activations are channel-last (HWC) BF16 maps with a zero border, and the
+// convolution weights are staged with their K axis in (tap, channel) order,
+// so the two K values of an A-fragment register are two adjacent channels of
+// one tap: one 32-bit shared load at an offset that is a compile-time
+// constant of the K step plus the row's base. Pixel, row and sample strides
+// are padded so that the 8 rows x 4 channel pairs of a fragment load hit 32
+// distinct banks; weight rows are padded by 8 elements for the same reason.
+// ---------------------------------------------------------------------------
+constexpr int TT = 16;
+constexpr int TILE_THREADS = 512;
+constexpr int TILE_WARPS = TILE_THREADS / 32;
+constexpr int PK1 = K1 + 8, PK2 = K2 + 8, PK3 = K3 + 8, PK4 = K4 + 8, PK5 = K5 + 8;
+constexpr int SW1 = 0;
+constexpr int SW2 = SW1 + N1 * PK1;
+constexpr int SW3 = SW2 + N2 * PK2;
+constexpr int SW4 = SW3 + N3 * PK3;
+constexpr int SW5 = SW4 + N4 * PK4;
+constexpr int SW_END = SW5 + N5 * PK5;          // elements
+// map geometry (elements): pixel stride, row stride, sample stride
+constexpr int X_PIX = 4, X_ROW = XP * X_PIX;                 // input 18 x 18 x 4
+constexpr int H1_PIX = 36, H1_ROW = H1P * H1_PIX + 8;        // 10 x 10 x 32 (+pad)
+constexpr int H1_SAMPLE = H1P * H1_ROW;
+constexpr int H2_PIX = 36, H2_ROW = H2P * H2_PIX + 16;       // 6 x 6 x 32 (+pad)
+constexpr int XR_SAMPLE = 1440;                              // input / H2 region per sample
+constexpr int H3_SAMPLE = 136, H4_SAMPLE = 72;
+static_assert(XP * X_ROW <= XR_SAMPLE && H2P * H2_ROW <= XR_SAMPLE, "region");
+constexpr int T_W = 0;                                       // byte offsets
+constexpr int T_B = T_W + SW_END * 2;
+constexpr int T_X = ((T_B + N_BIAS * 4) + 15) & ~15;
+constexpr int T_H1 = T_X + TT * XR_SAMPLE * 2;
+constexpr int T_H3 = T_H1 + TT * H1_SAMPLE * 2;
+constexpr int T_H4 = T_H3 + TT * H3_SAMPLE * 2;
+constexpr int T_OUT = T_H4 + TT * H4_SAMPLE * 2;             // TT x 3 floats
+constexpr int T_ZERO = T_OUT + TT * 3 * 4;
+constexpr int TILE_SMEM = T_ZERO + 16;
+static_assert(TILE_SMEM <= 227 * 1024, "tile shared memory");
+
+struct TileSmem {
+  uint16_t* w;
+  float* b;
+  uint16_t* x;      // input, then conv2's output
+  uint16_t* h1;
+  uint16_t* h3;
+  uint16_t* h4;
+  float* out;
+  const uint16_t* zero;
+};
+
+__device__ __forceinline__ TileSmem tile_smem(uint8_t* sm) {
+  return TileSmem{reinterpret_cast<uint16_t*>(sm + T_W), reinterpret_cast<float*>(sm + T_B),
+                  reinterpret_cast<uint16_t*>(sm + T_X), reinterpret_cast<uint16_t*>(sm + T_H1),
+                  reinterpret_cast<uint16_t*>(sm + T_H3), reinterpret_cast<uint16_t*>(sm + T_H4),
+                  reinterpret_cast<float*>(sm + T_OUT),
+                  reinterpret_cast<const uint16_t*>(sm + T_ZERO)};
+}
+
+// Weights into padded rows (convolutions re-ordered to K = tap * CIN + c),
+// biases, and zeros everywhere else (H1's border is never written again).
+// Ends with a barrier.
+__device__ __forceinline__ void tile_setup(const Packed& P, uint8_t* sm) {
+  uint32_t* z = reinterpret_cast<uint32_t*>(sm + T_X);
+  for (int i = threadIdx.x; i < (TILE_SMEM - T_X) / 4; i += blockDim.x) z[i] = 0u;
+  const TileSmem S = tile_smem(sm);
+  // convolutions: element (n, tap*CIN + c) <- packed (n, c*9 + tap)
+  for (int i = threadIdx.x; i < N1 * 36; i += blockDim.x) {
+    const int n = i / 36, k = i - n * 36, tap = k >> 2, c = k & 3;
+    S.w[SW1 + n * PK1 + k] = P.w[OFF_W1 + n * K1 + c * 9 + tap];
+  }
+  for (int i = threadIdx.x; i < N1 * (K1 - 36); i += blockDim.x) {
+    const int n = i / (K1 - 36), k = 36 + i - n * (K1 - 36);
+    S.w[SW1 + n * PK1 + k] = 0;
+  }
+  for (int i = threadIdx.x; i < 2 * N2 * K2; i += blockDim.x) {
+    const int l = i / (N2 * K2), r = i - l * (N2 * K2);
+    const int n = r / K2, k = r - n * K2, tap = k >> 5, c = k & 31;
+    const int off = l ? OFF_W3 : OFF_W2, sw = l ? SW3 : SW2;
+    S.w[sw + n * PK2 + k] = P.w[off + n * K2 + c * 9 + tap];
+  }
+  // dense layers: rows as packed
+  for (int i = threadIdx.x; i < N4 * K4 / 2; i += blockDim.x) {
+    const int n = i / (K4 / 2), c = i - n * (K4 / 2);
+    reinterpret_cast<uint32_t*>(S.w + SW4 + n * PK4)[c] =
+        __ldg(reinterpret_cast<const uint32_t*>(P.w + OFF_W4) + i);
+  }
+  for (int i = threadIdx.x; i < N5 * K5 / 2; i += blockDim.x) {
+    const int n = i / (K5 / 2), c = i - n * (K5 / 2);
+    reinterpret_cast<uint32_t*>(S.w + SW5 + n * PK5)[c] =
+        __ldg(reinterpret_cast<const uint32_t*>(P.w + OFF_W5) + i);
+  }
+  for (int i = threadIdx.x; i < N_BIAS; i += blockDim.x) S.b[i] = __ldg(P.b + i);
+  __syncthreads();
+}
+
+__device__ __forceinline__ uint32_t lds32(const uint16_t* p) {
+  return *reinterpret_cast<const uint32_t*>(p);
+}
+
+// Epilogue of one accumulator tile: bias, ReLU, BF16 pairs (n, n+1) stored as
+// one word at out_row[h] + n (the caller's per-row base).
+__device__ __forceinline__ void store_pairs(const float (&acc)[4], const float* bias, int n0,
+                                            uint16_t* row0, uint16_t* row1) {
+  const float b0 = bias[n0], b1 = bias[n0 + 1];
+  const uint32_t lo = (uint32_t)f2bf(fmaxf(acc[0] + b0, 0.f)) |
+                      ((uint32_t)f2bf(fmaxf(acc[1] + b1, 0.f)) << 16);
+  const uint32_t hi = (uint32_t)f2bf(fmaxf(acc[2] + b0, 0.f)) |
+                      ((uint32_t)f2bf(fmaxf(acc[3] + b1, 0.f)) << 16);
+  *reinterpret_cast<uint32_t*>(row0 + n0) = lo;
+  *reinterpret_cast<uint32_t*>(row1 + n0) = hi;
+}
+
+// conv1 on one M tile: rows mt*16.. of TT*64 (sample, 8x8 position), all 32
+// output channels into H1 (HWC).
+__device__ __forceinline__ void tile_conv1(const TileSmem& S, int mt, int lane) {
+  const int g = lane >> 2, t = lane & 3;
+  int base[2];
+  uint16_t* orow[2];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int r = mt * 16 + g + 8 * h, s = r >> 6, p = r & 63, i = p >> 3, j = p & 7;
+    base[h] = s * XR_SAMPLE + (2 * i) * X_ROW + (2 * j) * X_PIX;
+    orow[h] = S.h1 + s * H1_SAMPLE + (i + 1) * H1_ROW + (j + 1) * H1_PIX;
+  }
+  float acc[4][4] = {};
+#pragma unroll
+  for (int ks = 0; ks < K1 / 16; ++ks) {
+    // lane's K pairs: taps 4 ks + t/2 and that + 2, channels 2 (t & 1) + {0, 1}
+    uint32_t a[4];
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+      const int tap = 4 * ks + (t >> 1) + 2 * half;
+      const int off = (tap / 3) * X_ROW + (tap % 3) * X_PIX + 2 * (t & 1);
+#pragma unroll
+      for (int h = 0; h < 2; ++h)
+        a[h + 2 * half] = tap < 9 ? lds32(S.x + base[h] + off) : 0u;
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const uint16_t* wr = S.w + SW1 + (q * 8 + g) * PK1 + ks * 16 + 2 * t;
+      mma16816(acc[q], a, lds32(wr), lds32(wr + 8));
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) store_pairs(acc[q], S.b + OFF_B1, q * 8 + 2 * t, orow[0], orow[1]);
+}
+
+// conv2 on one sample's 16 positions (one M tile), all 32 channels into the
+// X region as H2 (HWC, 6x6 bordered).
+__device__ __forceinline__ void tile_conv2(const TileSmem& S, int s, int lane) {
+  const int g = lane >> 2, t = lane & 3;
+  int base[2];
+  uint16_t* orow[2];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int p = g + 8 * h, i = p >> 2, j = p & 3;
+    base[h] = s * H1_SAMPLE + (2 * i) * H1_ROW + (2 * j) * H1_PIX + 2 * t;
+    orow[h] = S.x + s * XR_SAMPLE + (i + 1) * H2_ROW + (j + 1) * H2_PIX;
+  }
+  float acc[4][4] = {};
+#pragma unroll
+  for (int ks = 0; ks < K2 / 16; ++ks) {
+    const int tap = ks >> 1, c0 = (ks & 1) * 16;
+    const int off = (tap / 3) * H1_ROW + (tap % 3) * H1_PIX + c0;
+    uint32_t a[4];
+    a[0] = lds32(S.h1 + base[0] + off);
+    a[1] = lds32(S.h1 + base[1] + off);
+    a[2] = lds32(S.h1 + base[0] + off + 8);
+    a[3] = lds32(S.h1 + base[1] + off + 8);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const uint16_t* wr = S.w + SW2 + (q * 8 + g) * PK2 + ks * 16 + 2 * t;
+      mma16816(acc[q], a, lds32(wr), lds32(wr + 8));
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) store_pairs(acc[q], S.b + OFF_B2, q * 8 + 2 * t, orow[0], orow[1]);
+}
+
+// conv3 on one M tile (4 samples x 2x2 positions), one n-tile, into H3 as
+// (channel, row, column) vectors.
+__device__ __forceinline__ void tile_conv3(const TileSmem& S, int mt, int nt, int lane) {
+  const int g = lane >> 2, t = lane & 3;
+  int base[2], orow[2];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int r = mt * 16 + g + 8 * h, s = r >> 2, p = r & 3, i = p >> 1, j = p & 1;
+    base[h] = s * XR_SAMPLE + (2 * i) * H2_ROW + (2 * j) * H2_PIX + 2 * t;
+    orow[h] = s * H3_SAMPLE + p;
+  }
+  float acc[4] = {};
+#pragma unroll
+  for (int ks = 0; ks < K3 / 16; ++ks) {
+    const int tap = ks >> 1, c0 = (ks & 1) * 16;
+    const int off = (tap / 3) * H2_ROW + (tap % 3) * H2_PIX + c0;
+    uint32_t a[4];
+    a[0] = lds32(S.x + base[0] + off);
+    a[1] = lds32(S.x + base[1] + off);
+    a[2] = lds32(S.x + base[0] + off + 8);
+    a[3] = lds32(S.x + base[1] + off + 8);
+    const uint16_t* wr = S.w + SW3 + (nt * 8 + g) * PK3 + ks * 16 + 2 * t;
+    mma16816(acc, a, lds32(wr), lds32(wr + 8));
+  }
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const int n = nt * 8 + 2 * t + (e & 1);
+    S.h3[orow[e >> 1] + n * 4] = f2bf(fmaxf(acc[e] + S.b[OFF_B3 + n], 0.f));
+  }
+}
+
+// Dense layer over the TT samples (rows), n-tile nt.
+template <int K, int PK, int STRIDE>
+__device__ __forceinline__ void fc_ntile(const uint16_t* in, const uint16_t* W, int nt, int lane,
+                                         float (&acc)[4]) {
+  const int g = lane >> 2, t = lane & 3;
+#pragma unroll
+  for (int e = 0; e < 4; ++e) acc[e] = 0.f;
+#pragma unroll
+  for (int ks = 0; ks < K / 16; ++ks) {
+    uint32_t a[4];
+    a[0] = lds32(in + g * STRIDE + ks * 16 + 2 * t);
+    a[1] = lds32(in + (g + 8) * STRIDE + ks * 16 + 2 * t);
+    a[2] = lds32(in + g * STRIDE + ks * 16 + 2 * t + 8);
+    a[3] = lds32(in + (g + 8) * STRIDE + ks * 16 + 2 * t + 8);
+    const uint16_t* wr = W + (nt * 8 + g) * PK + ks * 16 + 2 * t;
+    mma16816(acc, a, lds32(wr), lds32(wr + 8));
+  }
+}
+
+// Zero border pixels of the input maps (the region held conv2's output).
+__device__ __forceinline__ void tile_clear_input_border(const TileSmem& S) {
+  for (int i = threadIdx.x; i < TT * 68; i += blockDim.x) {
+    const int s = i / 68, k = i - s * 68;
+    const int y = k < 18 ? 0 : (k < 36 ? 17 : 1 + (k - 36) / 2);
+    const int x = k < 36 ? k % 18 : ((k - 36) & 1) * 17;
+    *reinterpret_cast<uint2*>(S.x + s * XR_SAMPLE + y * X_ROW + x * X_PIX) = make_uint2(0u, 0u);
+  }
+}
+
+// The network on the TT inputs in S.x (interior written by the caller and
+// the border cleared by tile_clear_input_border, then a barrier); results
+// (dx, dy, conf) in S.out[3 s ..]. Ends with a barrier.
+__device__ __forceinline__ void tile_forward(const TileSmem& S) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int mt = warp; mt < TT * 4; mt += TILE_WARPS) tile_conv1(S, mt, lane);
+  __syncthreads();
+  // conv2 writes into the input region: clear its border pixels first
+  // (20 per sample, 32 channels = 8 words each)
+  for (int i = threadIdx.x; i < TT * 20 * 8; i += blockDim.x) {
+    const int s = i / 160, r = i - s * 160, k = r >> 3, w4 = r & 7;
+    const int y = k < 6 ? 0 : (k < 12 ? 5 : 1 + (k - 12) / 2);
+    const int x = k < 12 ? k % 6 : ((k - 12) & 1) * 5;
+    *reinterpret_cast<uint2*>(S.x + s * XR_SAMPLE + y * H2_ROW + x * H2_PIX + 4 * w4) =
+        make_uint2(0u, 0u);
+  }
+  for (int s = warp; s < TT; s += TILE_WARPS) tile_conv2(S, s, lane);
+  __syncthreads();
+  for (int it = warp; it < (TT / 4) * 4; it += TILE_WARPS) tile_conv3(S, it >> 2, it & 3, lane);
+  __syncthreads();
+  const int g = lane >> 2, t = lane & 3;
+  if (warp < 8) {                       // fc1: 8 n-tiles of 8 outputs
+    float acc[4];
+    fc_ntile<K4, PK4, H3_SAMPLE>(S.h3, S.w + SW4, warp, lane, acc);
+    const int n0 = warp * 8 + 2 * t;
+    store_pairs(acc, S.b + OFF_B4, n0, S.h4 + g * H4_SAMPLE, S.h4 + (g + 8) * H4_SAMPLE);
+  }
+  __syncthreads();
+  if (warp == 0) {                      // fc2: one n-tile, outputs 0..2
+    float acc[4];
+    fc_ntile<K5, PK5, H4_SAMPLE>(S.h4, S.w + SW5, 0, lane, acc);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int row = g + 8 * (e >> 1), n = 2 * t + (e & 1);
+      if (n < 3) {
+        const float o = acc[e] + S.b[OFF_B5 + n];
+        S.out[row * 3 + n] = n < 2 ? o * kScale : 1.f / (1.f + expf(-o));
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// Writes row r (0..15) of channel ch of sample s's input map from the level
+// images: 16 values (v - 128) / 64 of the integer grid of keypoint (px, py),
+// 0 outside the level (the sampling of extract_warp).
+__device__ __forceinline__ void tile_input_row(const TileSmem& S, int s, int ch, int r,
+                                               const Geom& g, const Batch& src, int src_img,
+                                               const Batch& dst, int dst_img, float px,
+                                               float py, int la, int lb) {
+  const int lv = ch < 2 ? la : lb;
+  const float sc = __int_as_float((127 - lv) << 23);
+  const int cx = (int)floorf(px * sc + 0.5f) - 8;
+  const int cy = (int)floorf(py * sc + 0.5f) - 8 + r;
+  const bool in_row = cy >= 0 && cy < g.h[lv];
+  const uint8_t* row = nullptr;
+  if (in_row)
+    row = level_ptr(g, (ch & 1) ? dst : src, (ch & 1) ? dst_img : src_img, lv) +
+          (long long)cy * g.pitch[lv];
+  uint8_t v[16];
+#pragma unroll
+  for (int c = 0; c < 16; ++c) {
+    const int x = cx + c;
+    v[c] = (in_row && x >= 0 && x < g.w[lv]) ? __ldg(row + x) : (uint8_t)128;
+  }
+  uint16_t* out = S.x + s * XR_SAMPLE + (r + 1) * X_ROW + X_PIX + ch;
+#pragma unroll
+  for (int c = 0; c < 16; ++c) out[c * X_PIX] = f2bf(((float)v[c] - 128.f) * (1.f / 64.f));
+}
+
+}  // namespace net
+}  // namespace vio

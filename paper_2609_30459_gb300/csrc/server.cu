@@ -136,12 +136,12 @@ void release_if_done(vio_server* s, int64_t id) {
 
 // Releases the slots of closing sessions whose frames are all done.
 void release_closing(vio_server* s) {
-  std::vector<int64_t> keep;
-  for (int64_t id : s->closing) {
+  std::vector<int64_t> cur;
+  cur.swap(s->closing);           // admissions below append to s->closing
+  for (int64_t id : cur) {
     release_if_done(s, id);
-    if (s->sessions[id].slot >= 0) keep.push_back(id);
+    if (s->sessions[id].slot >= 0) s->closing.push_back(id);
   }
-  s->closing.swap(keep);
 }
 
 // Completion of the step in flight: records, caller outputs, stage buffers.
