@@ -294,7 +294,7 @@ def batched_compare(torch, vio, steps, warmup, net):
             tracked += int(a[..., 0].sum() + a[..., 1].sum())
             survived += int(a[..., 2].sum() + a[..., 3].sum())
             learned += int(a[..., 7].sum())
-        k2, shift = b.get_tune()
+        k2, shift, after = b.get_tune()
         res[mode] = {"frames_per_s": n_streams * steps / total_s,
                      "p50_ms": percentile(lat, 50), "p99_ms": percentile(lat, 99),
                      "tracked_keypoints_per_s": tracked / total_s,
@@ -302,7 +302,7 @@ def batched_compare(torch, vio, steps, warmup, net):
                      "learned_share_of_survivors": learned / max(survived, 1),
                      "launches_per_step": b.launches_per_step(),
                      "tune": {"k2_threads": k2, "pyr_tile_shift": shift,
-                              "best_ms": tune_ms}}
+                              "stereo_after_select": after, "best_ms": tune_ms}}
         b.close()
     if res.get("learned") and res.get("plain"):
         res["learned_vs_plain_fps"] = (res["learned"]["frames_per_s"] /
@@ -320,6 +320,58 @@ def batched_compare(torch, vio, steps, warmup, net):
     return res
 
 
+def serving_run(torch, vio, seconds, net, tune, seqs=None):
+    """Config 5: 32 sessions (8 of each cfg-4 size) sending frames as Poisson
+    processes of rate U[30, 200] Hz each for `seconds`, served by vio_server
+    (device memory budget, continuous batching, learned start with the plain
+    fallback). Frames come from pinned host memory (each session replays its
+    sequence forward and back); latency is arrival -> completion seen by the
+    server loop, which includes the upload, the queueing and the read-back."""
+    import numpy as np
+    from paper_2609_30459_gb300 import serving
+    per_class = 8
+    classes = []
+    for (w, h, cw, ch) in CFG4_CLASSES:
+        p = vio.default_params(n_levels=CFG4_LEVELS, cell_w=cw, cell_h=ch)
+        classes.append((p, w, h, per_class, 2 * (w // cw) * (h // ch)))
+    budget = 4 << 30                              # fixed device-memory budget
+    slots, used = vio.server_plan(classes, budget)
+    srv = vio.Server(classes, budget)
+    if net is not None:
+        srv.set_initnet(net)
+    if tune is not None:
+        srv.set_tune(*tune)
+    seqs = seqs or cfg4_frames()
+    pinned = [[torch.from_numpy(f).pin_memory() for f in cls] for cls in seqs]
+    sessions, pools = [], []
+    for c in range(len(CFG4_CLASSES)):
+        for i in range(per_class):
+            sid, adm = srv.open(c)
+            sessions.append(sid)
+            pools.append(pinned[c][i % len(pinned[c])])
+    rng = np.random.default_rng(5000)
+    rates = rng.uniform(30.0, 200.0, len(sessions))
+    trace = serving.poisson_trace(rates, seconds, seed=5001)
+    reqs = []
+    for (t, i, k) in trace:
+        pool = pools[i]
+        reqs.append((sessions[i], t, pool[serving.pingpong(pool.shape[0], k)], k, 0))
+    # warm-up: one frame per session (graph capture, first-frame detection)
+    warm = [(sessions[i], 0.0, pools[i][0], -1, 0) for i in range(len(sessions))]
+    srv.run_trace(warm, timeout_s=60.0)
+    t0 = time.perf_counter()
+    done, steps = srv.run_trace(reqs, timeout_s=seconds + 120.0)
+    wall = time.perf_counter() - t0
+    summ = serving.latency_summary(done)
+    srv.close_server()
+    return {"sessions": len(sessions), "classes": [f"{w}x{h}" for (w, h, _, _) in CFG4_CLASSES],
+            "rate_hz": "U[30,200] per session", "offered_fps": float(rates.sum()),
+            "seconds": seconds, "requests": len(reqs), "steps": steps,
+            "mean_batch": len(reqs) / max(steps, 1), "wall_s": wall,
+            "budget_bytes": budget, "device_bytes": used, "slots": slots,
+            "learned": net is not None, **summ}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -330,6 +382,8 @@ def main():
     ap.add_argument("--cpu-frames", type=int, default=60)
     ap.add_argument("--batched-steps", type=int, default=300)
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--serve-seconds", type=float, default=60.0)
+    ap.add_argument("--no-serve", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -483,6 +537,17 @@ def main():
         if os.path.exists(initnet_train.DEFAULT_WEIGHTS):
             net = vio.InitNet.load(initnet_train.DEFAULT_WEIGHTS)
         batched = batched_compare(torch, vio, args.batched_steps, args.warmup, net)
+    serve = None
+    if rank == 0 and not args.no_serve:
+        from paper_2609_30459_gb300 import initnet_train
+        net = None
+        if os.path.exists(initnet_train.DEFAULT_WEIGHTS):
+            net = vio.InitNet.load(initnet_train.DEFAULT_WEIGHTS)
+        tune = None
+        if batched and batched.get("learned"):
+            t = batched["learned"]["tune"]
+            tune = (t["k2_threads"], t["pyr_tile_shift"], t["stereo_after_select"])
+        serve = serving_run(torch, vio, args.serve_seconds, net, tune)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -507,7 +572,7 @@ def main():
                                    "stereo_candidates": stereo_in / args.steps},
             "gpu_launches": args.steps * fe.launches_per_step(),
             "e2e": e2e, "roofline": roofline, "pyramid_detect_roofline": pd,
-            "batched_16_streams": batched,
+            "batched_16_streams": batched, "serving_32_streams": serve,
             "cpu_baseline": cpu, "clocks": clk.summary(),
             "host_wall_s": wall,
         }

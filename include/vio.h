@@ -352,7 +352,9 @@ vio_status vio_frontend_read_stats(vio_frontend* fe, int32_t* host_out, int64_t*
  * at p). Stereo matching is unchanged. d_packed: the packed weights
  * (vio_initnet_pack, 16-byte aligned), read by every step and owned by the
  * caller, which keeps them alive while the initializer is on; NULL turns it
- * off. Levels must lie below n_levels. */
+ * off. level_a and level_b must lie in 1 .. n_levels - 1 (upper levels),
+ * start_level below n_levels; at most 128 streams (else
+ * VIO_ERR_UNSUPPORTED). */
 typedef struct {
   int32_t level_a, level_b;  /* pyramid levels of the network input          */
   int32_t start_level;       /* LK levels tracked from the proposal          */
@@ -379,12 +381,16 @@ typedef struct {
   int32_t capacity;    /* keypoint slots per camera (gx*gy*k..32767)       */
 } vio_stream_group;
 
-/* Tunables of a batch step: threads per block of the tracking launch (64,
- * 128, 256 or 512) and the pyramid tile scale (-1, 0, 1: half, default,
- * double the deepest-level tile side). */
+/* Tunables of a batch step: threads per block of the tracking launches (64,
+ * 128, 256 or 512), the pyramid tile scale (-1, 0, 1: half, default, double
+ * the deepest-level tile side), and the order of stereo matching (0: every
+ * cell's candidates are matched beside temporal tracking; 1: only the
+ * selected keypoints are matched, after selection, in two more launches).
+ * Every setting gives the same lists bit for bit. */
 typedef struct {
   int32_t k2_threads;
   int32_t pyr_tile_shift;
+  int32_t stereo_after_select;
 } vio_batch_tune;
 
 vio_status vio_batch_create(vio_batch** out, const vio_stream_group* groups, int32_t n_groups);
@@ -411,7 +417,7 @@ vio_status vio_batch_set_graph(vio_batch* b, int32_t enable);
 vio_status vio_batch_set_tune(vio_batch* b, const vio_batch_tune* t);
 vio_status vio_batch_get_tune(vio_batch* b, vio_batch_tune* t);
 
-/* Times every tunable combination over `reps` pairs of steps (a first frame,
+/* Times every tunable combination (24) over `reps` pairs of steps (a first frame,
  * then a tracked frame, all streams active) on the frames the caller has put
  * in BOTH slots of every stream, keeps the fastest, and resets every stream.
  * *best_ms: the chosen combination's time per tracked step. Blocking. */

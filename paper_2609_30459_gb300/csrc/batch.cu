@@ -278,7 +278,7 @@ extern "C" vio_status vio_batch_create(vio_batch** out, const vio_stream_group* 
     cudaMemset(G.list_status, VIO_TRACK_EMPTY, lists);
   }
   b->mask_slot = 0;
-  b->tune = vio::FrameTune{128, 0};
+  b->tune = vio::FrameTune{128, 0, 0};
   b->use_graph = false;
   b->graph_ready = false;
   b->graph_done[0] = b->graph_done[1] = nullptr;
@@ -367,7 +367,8 @@ extern "C" vio_status vio_batch_set_tune(vio_batch* b, const vio_batch_tune* t) 
       t->k2_threads != 512)
     return VIO_ERR_INVALID_ARG;
   if (t->pyr_tile_shift < -1 || t->pyr_tile_shift > 1) return VIO_ERR_INVALID_ARG;
-  b->tune = vio::FrameTune{t->k2_threads, t->pyr_tile_shift};
+  if (t->stereo_after_select != 0 && t->stereo_after_select != 1) return VIO_ERR_INVALID_ARG;
+  b->tune = vio::FrameTune{t->k2_threads, t->pyr_tile_shift, t->stereo_after_select};
   drop_graphs(b);
   return VIO_OK;
 }
@@ -376,6 +377,7 @@ extern "C" vio_status vio_batch_get_tune(vio_batch* b, vio_batch_tune* t) {
   if (!b || !t) return VIO_ERR_INVALID_ARG;
   t->k2_threads = b->tune.k2_threads;
   t->pyr_tile_shift = b->tune.pyr_tile_shift;
+  t->stereo_after_select = b->tune.stereo_after;
   return VIO_OK;
 }
 
@@ -414,9 +416,10 @@ extern "C" vio_status vio_batch_autotune(vio_batch* b, int32_t reps, void* strea
   float best = 1e30f;
   vio::FrameTune best_t = b->tune;
   vio_status st = VIO_OK;
-  for (int ti = 0; ti < 4 && st == VIO_OK; ++ti) {
-    for (int shift = -1; shift <= 1 && st == VIO_OK; ++shift) {
-      b->tune = vio::FrameTune{threads[ti], shift};
+  for (int combo = 0; combo < 24 && st == VIO_OK; ++combo) {
+    const int ti = combo % 4, shift = (combo / 4) % 3 - 1, after = combo / 12;
+    {
+      b->tune = vio::FrameTune{threads[ti], shift, after};
       float total = 0.f;
       for (int r = 0; r < reps; ++r) {
         reset_all(b, s);
@@ -475,7 +478,8 @@ extern "C" int32_t vio_batch_launches_per_step(const vio_batch* b) {
   if (!b) return 0;
   std::vector<vio::Geom> g;
   for (const auto& G : b->groups) g.push_back(vio::make_geom(G.layout));
-  return vio::frame_launches(g.data(), (int)g.size(), b->net != nullptr);
+  return vio::frame_launches(g.data(), (int)g.size(), b->net != nullptr,
+                            b->tune.stereo_after != 0);
 }
 
 extern "C" vio_status vio_batch_device_bytes(const vio_stream_group* groups, int32_t n_groups,
@@ -516,6 +520,7 @@ extern "C" vio_status vio_batch_set_initnet(vio_batch* b, const void* d_packed,
     for (const auto& G : b->groups)
       if (!vio::initnet_cfg_ok(cfg, G.spec.params.n_levels, d_packed))
         return VIO_ERR_INVALID_ARG;
+    if (2 * b->total_streams > vio::KN_MAX_LISTS) return VIO_ERR_UNSUPPORTED;
     b->net_cfg = *cfg;
   }
   b->net = d_packed;

@@ -26,7 +26,14 @@
 // matching run beside temporal tracking instead of after it. A keypoint's
 // match depends only on its position and the two current pyramids, so the
 // result for every selected keypoint is the one the sequential order gives;
-// the candidates that the occupancy rejects are simply not used.
+// the candidates that the occupancy rejects are simply not used. That costs
+// a match per cell per frame where only a few cells take new keypoints, so
+// the other order is a tunable (stereo_after): K2 tracks temporally only,
+// K3 selects and appends to camera 0, then
+//  K4 frame_stereo_kernel   one warp per selected keypoint: stereo matching;
+//  K5 frame_append_kernel   one CTA per stream: the successful matches, in
+//                           order, appended to camera 1.
+// Both orders give the same lists bit for bit.
 //
 // Streams are either stepped together with host-side parity (unslotted), or
 // each keeps its own parity, first-frame flag and activity in device memory
@@ -126,43 +133,143 @@ struct MultiK2 {
 // count are skipped whole.
 struct MultiKN {
   int n;
-  long long block_end[kMaxGroups];   // in tiles
+  long long block_end[kMaxGroups];   // in keypoint lists (2 per stream)
   FrameLaunch f[kMaxGroups];
 };
 
+// Tile of the launch: a list's slots s0 .. s0 + nv - 1.
+struct NetTile {
+  int gi, list, s0, nv;
+  StreamRef r;
+  long long in_list;
+};
+
+static_assert(KN_MAX_LISTS * 4 + net::TILE_SMEM <= 227 * 1024,
+              "shared memory of the proposal kernel");
+
+// Per-list tile counts, prefix-summed in shared memory (every CTA), so that
+// the tiles that hold keypoints are dealt out evenly over the CTAs.
+struct NetLists {
+  int n;                              // lists
+  int* end;                           // inclusive prefix of tiles per list
+};
+
+__device__ __forceinline__ int list_tiles(const MultiKN& mm, int li, int& gi, int& list,
+                                          long long& in_list, StreamRef& r) {
+  long long start;
+  gi = group_of(mm, li, start);       // block_end counts lists here
+  const FrameLaunch& f = mm.f[gi];
+  list = (int)(li - start);
+  const int s = list >> 1, c = list & 1;
+  r = stream_ref(f, s);
+  if (!r.active || !r.have_prev) return 0;
+  in_list = ((long long)r.li * f.n_streams + s) * 2 + c;
+  const int count = min(f.list_count[in_list], f.cap);
+  return (count + net::TT - 1) / net::TT;
+}
+
+__device__ __forceinline__ NetTile net_tile(const MultiKN& mm, const NetLists& L, int v) {
+  // the list holding valid tile v: first prefix end above v
+  int lo = 0, hi = L.n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (L.end[mid] > v) hi = mid; else lo = mid + 1;
+  }
+  NetTile T{};
+  const int n_tiles = list_tiles(mm, lo, T.gi, T.list, T.in_list, T.r);
+  const int j = v - (L.end[lo] - n_tiles);
+  const FrameLaunch& f = mm.f[T.gi];
+  const int count = min(f.list_count[T.in_list], f.cap);
+  T.s0 = j * net::TT;
+  T.nv = min(net::TT, count - T.s0);
+  return T;
+}
+
+// This thread's rows of a tile: items e = threadIdx.x + k * TILE_THREADS
+// over (keypoint, channel, row).
+constexpr int KN_ROWS = net::TT * 64 / net::TILE_THREADS;
+
+__device__ __forceinline__ void net_prefetch(const MultiKN& mm, const NetTile& T,
+                                             net::RowWords (&R)[KN_ROWS]) {
+  const FrameLaunch& f = mm.f[T.gi];
+  const int c = T.list & 1;
+  const float* xy = f.list_xy + 2 * (T.in_list * f.cap + T.s0);
+#pragma unroll
+  for (int k = 0; k < KN_ROWS; ++k) {
+    const int e = threadIdx.x + k * net::TILE_THREADS, kp = e >> 6, ch = (e >> 4) & 3;
+    if (kp < T.nv)
+      net::row_prefetch(R[k], f.g, (ch & 1) ? f.cur : f.prev,
+                        ((ch & 1) ? T.r.cur_img : T.r.prev_img) + c, ch < 2 ? f.net_la : f.net_lb,
+                        xy[2 * kp], xy[2 * kp + 1], e & 15);
+  }
+}
+
+// Persistent CTAs over the tiles that hold keypoints (valid tile v goes to
+// CTA v mod gridDim.x); the input rows of the next tile are loaded into
+// registers while the current tile computes. Needs level_a, level_b >= 1.
 __global__ void __launch_bounds__(net::TILE_THREADS, 1) frame_initnet_kernel(
     const __grid_constant__ MultiKN mm) {
   extern __shared__ __align__(16) uint8_t sm[];
+  __shared__ int ends[KN_MAX_LISTS];
+  int* warp_tot = reinterpret_cast<int*>(sm + net::T_X);   // before tile_setup uses it
+  const int n_lists = (int)mm.block_end[mm.n - 1];
+  // per-list tile counts and their inclusive prefix (chunks of blockDim.x)
+  int carry = 0;
+  for (int base = 0; base < n_lists; base += blockDim.x) {
+    const int li = base + threadIdx.x;
+    int nt = 0;
+    if (li < n_lists) {
+      int gi, list;
+      long long in_list;
+      StreamRef r;
+      nt = list_tiles(mm, li, gi, list, in_list, r);
+    }
+    int incl = nt;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    if (lane == 31) warp_tot[warp] = incl;
+    __syncthreads();
+    int before = carry;
+    for (int w = 0; w < warp; ++w) before += warp_tot[w];
+    if (li < n_lists) ends[li] = before + incl;
+    int tot = 0;
+    for (int w = 0; w < net::TILE_WARPS; ++w) tot += warp_tot[w];
+    carry += tot;
+    __syncthreads();
+  }
+  const NetLists L{n_lists, ends};
+  const int n_valid = carry;
+  int v = blockIdx.x;
+  if (v >= n_valid) return;
+  NetTile cur = net_tile(mm, L, v);
+  net::RowWords R[KN_ROWS];
+  net_prefetch(mm, cur, R);
   net::tile_setup(net::packed(mm.f[0].net), sm);
   const net::TileSmem S = net::tile_smem(sm);
-  const long long total = mm.block_end[mm.n - 1];
-  for (long long tile = blockIdx.x; tile < total; tile += gridDim.x) {
-    long long start;
-    const int gi = group_of(mm, tile, start);
-    const FrameLaunch& f = mm.f[gi];
-    const int tpl = (f.cap + net::TT - 1) / net::TT;
-    const long long lt = tile - start;
-    const int list = (int)(lt / tpl);
-    const int j = (int)(lt - (long long)list * tpl);
-    const int s = list >> 1, c = list & 1;
-    const StreamRef r = stream_ref(f, s);
-    if (!r.active || !r.have_prev) continue;
-    const long long in_list = ((long long)r.li * f.n_streams + s) * 2 + c;
-    const int count = min(f.list_count[in_list], f.cap);
-    const int s0 = j * net::TT;
-    if (s0 >= count) continue;
-    const int nv = min(net::TT, count - s0);
-    const float* xy = f.list_xy + 2 * (in_list * f.cap + s0);
+  while (true) {
     net::tile_clear_input_border(S);
-    for (int e = threadIdx.x; e < nv * 64; e += blockDim.x) {   // (keypoint, channel, row)
-      const int k = e >> 6;
-      net::tile_input_row(S, k, (e >> 4) & 3, e & 15, f.g, f.prev, r.prev_img + c, f.cur,
-                          r.cur_img + c, xy[2 * k], xy[2 * k + 1], f.net_la, f.net_lb);
+#pragma unroll
+    for (int k = 0; k < KN_ROWS; ++k) {
+      const int e = threadIdx.x + k * net::TILE_THREADS;
+      if ((e >> 6) < cur.nv) net::row_store(R[k], S, e >> 6, (e >> 4) & 3, e & 15);
     }
     __syncthreads();
+    v += gridDim.x;
+    NetTile next{};
+    if (v < n_valid) {
+      next = net_tile(mm, L, v);
+      net_prefetch(mm, next, R);
+    }
     net::tile_forward(S);
-    float* o = f.net_out + 3 * ((long long)list * f.cap + s0);
-    for (int i = threadIdx.x; i < nv * 3; i += blockDim.x) o[i] = S.out[i];
+    const FrameLaunch& f = mm.f[cur.gi];
+    float* o = f.net_out + 3 * ((long long)cur.list * f.cap + cur.s0);
+    for (int i = threadIdx.x; i < cur.nv * 3; i += blockDim.x) o[i] = S.out[i];
+    if (v >= n_valid) break;
+    cur = next;
   }
 }
 
@@ -387,7 +494,8 @@ __global__ void __launch_bounds__(K3_THREADS) frame_finalize_kernel(const __grid
       f.occupancy[cbase + cell] = (uint8_t)occ;
       const int nsel = max(0, min(k - occ, nc));
       int nm = 0;
-      for (int r = 0; r < nsel; ++r) nm += f.spec_status[(cbase + cell) * k + r] == VIO_TRACK_OK;
+      if (!f.stereo_after)
+        for (int r = 0; r < nsel; ++r) nm += f.spec_status[(cbase + cell) * k + r] == VIO_TRACK_OK;
       packed += (unsigned long long)nsel | ((unsigned long long)nm << 21) |
                 ((unsigned long long)nc << 42);
     }
@@ -414,7 +522,7 @@ __global__ void __launch_bounds__(K3_THREADS) frame_finalize_kernel(const __grid
           f.list_xy[2 * (out0 + o0) + 1] = y;
           f.list_id[out0 + o0] = id0 + o;
         }
-        if (f.spec_status[q] == VIO_TRACK_OK) {
+        if (!f.stereo_after && f.spec_status[q] == VIO_TRACK_OK) {
           const int o1 = surv1 + om++;
           if (o1 < f.cap) {
             f.list_xy[2 * (out0 + cap + o1)] = f.spec_xy[2 * q];
@@ -448,6 +556,99 @@ __global__ void __launch_bounds__(K3_THREADS) frame_finalize_kernel(const __grid
     st[VIO_STAT_MATCHED] = m_tot;
     st[VIO_STAT_CAND] = c_tot;
     st[VIO_STAT_LEARNED] = learned_s;
+    if (f.slotted && !f.stereo_after) {   // else the append kernel ends the step
+      f.parity[s] = sr.lo;
+      f.have_prev[s] = 1;
+    }
+  }
+}
+
+// ---- the after-selection order: stereo matching of the selected keypoints
+
+// Selected keypoints a stream can have: every cell's k, at most the capacity.
+__host__ __device__ inline int max_new(const FrameLaunch& f) {
+  const int n = (f.g.w[0] / f.p.cell_w) * (f.g.h[0] / f.p.cell_h) * f.p.k_per_cell;
+  return n < f.cap ? n : f.cap;
+}
+
+__global__ void frame_stereo_kernel(const __grid_constant__ MultiK2 mm) {
+  const long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= mm.block_end[mm.n - 1]) return;
+  long long start;
+  const int gi = group_of(mm, w, start);
+  const FrameLaunch& f = mm.f[gi];
+  const int mn = max_new(f);
+  const long long wl = w - start;
+  const int s = (int)(wl / mn), slot = (int)(wl - (long long)s * mn);
+  const StreamRef r = stream_ref(f, s);
+  if (!r.active || slot >= f.new_count[s]) return;
+  const long long q = (long long)s * f.cap + slot;
+  const TrackCfg cfg{f.p.gn_iters, 1, f.p.fb_max_dist, -1};
+  trk::Pos tf;
+  float thf, dist;
+  bool have;
+  const int st = trk::track_fb(f.g, f.cur, r.cur_img, f.cur, r.cur_img + 1, f.new_xy[2 * q],
+                               f.new_xy[2 * q + 1], false, 0.f, 0.f, 0.f, cfg,
+                               f.g.n_levels - 1, lane, tf, thf, have, dist);
+  if (lane == 0) {
+    const long long o = (long long)s * mn + slot;
+    f.spec_status[o] = (uint8_t)st;
+    f.spec_xy[2 * o] = have ? (float)tf.ax + tf.dx : __int_as_float(0x7fc00000);
+    f.spec_xy[2 * o + 1] = have ? (float)tf.ay + tf.dy : __int_as_float(0x7fc00000);
+  }
+}
+
+// Appends the successful matches of a stream's selected keypoints, in their
+// order, to camera 1 after its surviving tracks, and ends the stream's step.
+__global__ void __launch_bounds__(K3_THREADS) frame_append_kernel(const __grid_constant__ MultiK3 mm) {
+  __shared__ int ws32[K3_THREADS / 32];
+  long long start;
+  const int gi = group_of(mm, blockIdx.x, start);
+  const FrameLaunch& f = mm.f[gi];
+  const int s = (int)(blockIdx.x - start);
+  const StreamRef sr = stream_ref(f, s);
+  if (!sr.active) return;
+  const int t = threadIdx.x;
+  const long long cap = f.cap;
+  const int mn = max_new(f);
+  const long long cnt_out = ((long long)sr.lo * f.n_streams + s) * 2;
+  const long long out1 = (cnt_out + 1) * cap;
+  const int surv1 = f.list_count[cnt_out + 1];           // K3 left the survivors' count
+  const int ctr = *f.step_ctr;
+  int32_t* st = f.stats + ((long long)((ctr - 1) % VIO_STATS_RING) * f.n_streams + s) * VIO_N_STATS;
+  const int n_new = f.new_count[s];
+  const int id0 = f.next_id[s] - st[VIO_STAT_NEW];
+  const int run = (n_new + K3_THREADS - 1) / K3_THREADS;
+  int m_tot = 0;
+  for (int r0 = 0; r0 < run; r0 += kRunMax) {
+    const int rl = min(kRunMax, run - r0);
+    const int first = t * run + r0;
+    unsigned keep = 0;
+    for (int j = 0; j < rl; ++j) {
+      const int i = first + j;
+      if (i < n_new && f.spec_status[(long long)s * mn + i] == VIO_TRACK_OK) keep |= 1u << j;
+    }
+    int tot;
+    int o = m_tot + block_scan<int>(__popc(keep), ws32, tot);
+    for (int j = 0; j < rl; ++j) {
+      if (!(keep & (1u << j))) continue;
+      const int i = first + j;
+      const int o1 = surv1 + o++;
+      if (o1 < f.cap) {
+        const long long q = (long long)s * mn + i;
+        f.list_xy[2 * (out1 + o1)] = f.spec_xy[2 * q];
+        f.list_xy[2 * (out1 + o1) + 1] = f.spec_xy[2 * q + 1];
+        f.list_id[out1 + o1] = id0 + i;
+        f.list_status[out1 + o1] = VIO_TRACK_OK;
+      }
+    }
+    m_tot += tot;
+    __syncthreads();
+  }
+  if (t == 0) {
+    f.list_count[cnt_out + 1] = min(surv1 + m_tot, f.cap);
+    st[VIO_STAT_MATCHED] = m_tot;
     if (f.slotted) {
       f.parity[s] = sr.lo;
       f.have_prev[s] = 1;
@@ -558,12 +759,15 @@ cudaError_t launch_frames(const FrameLaunch* fl, int n_groups, const FrameTune& 
   if (fl[0].net) {
     MultiKN mn{};
     mn.n = n_groups;
-    acc = 0;
+    acc = 0;                                    // keypoint lists
+    long long tiles = 0;                        // tiles if every list were full
     for (int i = 0; i < n_groups; ++i) {
       mn.f[i] = fl[i];
-      acc += 2LL * fl[i].n_streams * ((fl[i].cap + net::TT - 1) / net::TT);
+      acc += 2LL * fl[i].n_streams;
+      tiles += 2LL * fl[i].n_streams * ((fl[i].cap + net::TT - 1) / net::TT);
       mn.block_end[i] = acc;
     }
+    if (acc > KN_MAX_LISTS) return cudaErrorInvalidValue;
     static int sms = 0;
     if (!sms) {
       int dev = 0;
@@ -573,7 +777,7 @@ cudaError_t launch_frames(const FrameLaunch* fl, int n_groups, const FrameTune& 
                                net::TILE_SMEM) != cudaSuccess)
         return cudaErrorUnknown;
     }
-    const long long blocks = acc < sms ? acc : sms;
+    const long long blocks = tiles < sms ? tiles : sms;
     if (blocks > 0)
       frame_initnet_kernel<<<(unsigned)blocks, net::TILE_THREADS, net::TILE_SMEM, s>>>(mn);
   }
@@ -586,8 +790,10 @@ cudaError_t launch_frames(const FrameLaunch* fl, int n_groups, const FrameTune& 
   for (int i = 0; i < n_groups; ++i) {
     const FrameLaunch& f = fl[i];
     m2.f[i] = f;
+    m2.f[i].stereo_after = tune.stereo_after;
     const int n_cells = (f.g.w[0] / f.p.cell_w) * (f.g.h[0] / f.p.cell_h);
-    acc += 2LL * f.n_streams * f.cap + (long long)f.n_streams * n_cells * f.p.k_per_cell;
+    acc += 2LL * f.n_streams * f.cap +
+           (tune.stereo_after ? 0LL : (long long)f.n_streams * n_cells * f.p.k_per_cell);
     m2.block_end[i] = acc;
   }
   const int k2t = tune.k2_threads;
@@ -605,6 +811,7 @@ cudaError_t launch_frames(const FrameLaunch* fl, int n_groups, const FrameTune& 
   for (int i = 0; i < n_groups; ++i) {
     const FrameLaunch& f = fl[i];
     m3.f[i] = f;
+    m3.f[i].stereo_after = tune.stereo_after;
     acc += f.n_streams;
     m3.block_end[i] = acc;
     const int sm = (f.g.w[0] / f.p.cell_w) * (f.g.h[0] / f.p.cell_h) * (int)sizeof(int);
@@ -616,12 +823,28 @@ cudaError_t launch_frames(const FrameLaunch* fl, int n_groups, const FrameTune& 
     if (e != cudaSuccess) return e;
   }
   frame_finalize_kernel<<<(unsigned)acc, K3_THREADS, smem3, s>>>(m3);
+  if (tune.stereo_after) {
+    // K4: stereo matching of the selected keypoints; K5: append to camera 1
+    MultiK2 m4{};
+    m4.n = n_groups;
+    long long w4 = 0;
+    for (int i = 0; i < n_groups; ++i) {
+      m4.f[i] = m3.f[i];
+      w4 += (long long)fl[i].n_streams * max_new(fl[i]);
+      m4.block_end[i] = w4;
+    }
+    if (w4 > 0) {
+      const long long blocks4 = (w4 * 32 + k2t - 1) / k2t;
+      frame_stereo_kernel<<<(unsigned)blocks4, k2t, 0, s>>>(m4);
+    }
+    frame_append_kernel<<<(unsigned)acc, K3_THREADS, 0, s>>>(m3);
+  }
   mark(5);
   return cudaGetLastError();
 }
 
-int frame_launches(const Geom* g, int n_groups, bool with_net) {
-  int n = with_net ? 4 : 3;                    // K1, (KN), K2, K3
+int frame_launches(const Geom* g, int n_groups, bool with_net, bool stereo_after) {
+  int n = (with_net ? 4 : 3) + (stereo_after ? 2 : 0);   // K1, (KN), K2, K3, (K4, K5)
   for (int i = 0; i < n_groups; ++i)
     if (g[i].n_levels > 1 + pyr::kMaxPass) ++n;
   return n;

@@ -11,6 +11,7 @@ constexpr int kMaxGroups = 8;
 struct FrameTune {
   int k2_threads;      // threads per block of the tracking launch (64..512)
   int pyr_tile_shift;  // deepest-level pyramid tile side = (32 >> (m-1)) << shift
+  int stereo_after;    // 1: stereo-match only the selected keypoints, after selection
 };
 
 struct FrameLaunch {
@@ -51,6 +52,7 @@ struct FrameLaunch {
   float net_tau;
   float* net_out;                  // [stream][camera] x cap x (dx, dy, conf)
   uint8_t* trk_learned;            // [stream][camera] x cap: 1 = tracked from the proposal
+  int stereo_after;                // set by launch_frames from the tune
 };
 
 // Per-stream view of a FrameLaunch.
@@ -91,13 +93,17 @@ __host__ __device__ inline StreamRef stream_ref(const FrameLaunch& f, int s) {
 // stage boundaries (or null).
 cudaError_t launch_frames(const FrameLaunch* f, int n_groups, const FrameTune& tune,
                           cudaStream_t s, cudaEvent_t* marks);
-int frame_launches(const Geom* g, int n_groups, bool with_net);
+int frame_launches(const Geom* g, int n_groups, bool with_net, bool stereo_after);
 
-// Initializer configuration check: levels below n_levels, a finite gate,
-// 16-byte aligned weights.
+// Keypoint lists (2 per stream) one launch of the proposal kernel handles.
+constexpr int KN_MAX_LISTS = 256;
+
+// Initializer configuration check: input levels in 1 .. n_levels - 1, start
+// level below n_levels, a finite gate, 16-byte aligned weights.
 inline bool initnet_cfg_ok(const vio_initnet_cfg* c, int n_levels, const void* packed) {
   if (!c || ((uintptr_t)packed & 15)) return false;
-  if (c->level_a < 0 || c->level_b < 0 || c->start_level < 0) return false;
+  // the network reads upper pyramid levels only (aligned rows)
+  if (c->level_a < 1 || c->level_b < 1 || c->start_level < 0) return false;
   if (c->level_a >= n_levels || c->level_b >= n_levels || c->start_level >= n_levels)
     return false;
   return c->min_conf == c->min_conf;   // not NaN

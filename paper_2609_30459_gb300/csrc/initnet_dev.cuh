@@ -334,21 +334,31 @@ __device__ __forceinline__ TileSmem tile_smem(uint8_t* sm) {
 __device__ __forceinline__ void tile_setup(const Packed& P, uint8_t* sm) {
   uint32_t* z = reinterpret_cast<uint32_t*>(sm + T_X);
   for (int i = threadIdx.x; i < (TILE_SMEM - T_X) / 4; i += blockDim.x) z[i] = 0u;
+  uint32_t* zw = reinterpret_cast<uint32_t*>(sm + T_W + SW1 * 2);
+  for (int i = threadIdx.x; i < N1 * PK1 / 2; i += blockDim.x) zw[i] = 0u;
+  __syncthreads();
   const TileSmem S = tile_smem(sm);
-  // convolutions: element (n, tap*CIN + c) <- packed (n, c*9 + tap)
-  for (int i = threadIdx.x; i < N1 * 36; i += blockDim.x) {
-    const int n = i / 36, k = i - n * 36, tap = k >> 2, c = k & 3;
-    S.w[SW1 + n * PK1 + k] = P.w[OFF_W1 + n * K1 + c * 9 + tap];
+  // convolutions: packed (n, c*9 + tap) -> staged (n, tap*CIN + c); reads
+  // are coalesced words of the packed rows, the permutation is in the stores
+  // (the padding columns 36..47 of conv1 stay zero from the clear above)
+  for (int i = threadIdx.x; i < N1 * K1 / 2; i += blockDim.x) {
+    const uint32_t v = __ldg(reinterpret_cast<const uint32_t*>(P.w + OFF_W1) + i);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int e = 2 * i + h, n = e / K1, kc = e - n * K1;
+      const int c = kc / 9, tap = kc - 9 * c;
+      if (kc < 36) S.w[SW1 + n * PK1 + tap * 4 + c] = (uint16_t)(v >> (16 * h));
+    }
   }
-  for (int i = threadIdx.x; i < N1 * (K1 - 36); i += blockDim.x) {
-    const int n = i / (K1 - 36), k = 36 + i - n * (K1 - 36);
-    S.w[SW1 + n * PK1 + k] = 0;
-  }
-  for (int i = threadIdx.x; i < 2 * N2 * K2; i += blockDim.x) {
-    const int l = i / (N2 * K2), r = i - l * (N2 * K2);
-    const int n = r / K2, k = r - n * K2, tap = k >> 5, c = k & 31;
-    const int off = l ? OFF_W3 : OFF_W2, sw = l ? SW3 : SW2;
-    S.w[sw + n * PK2 + k] = P.w[off + n * K2 + c * 9 + tap];
+  for (int i = threadIdx.x; i < N2 * K2; i += blockDim.x) {   // conv2 and conv3 words
+    const int l = i >= N2 * K2 / 2, j = i - l * (N2 * K2 / 2);
+    const uint32_t v = __ldg(reinterpret_cast<const uint32_t*>(P.w + (l ? OFF_W3 : OFF_W2)) + j);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int e = 2 * j + h, n = e / K2, kc = e - n * K2;
+      const int c = kc / 9, tap = kc - 9 * c;
+      S.w[(l ? SW3 : SW2) + n * PK2 + tap * 32 + c] = (uint16_t)(v >> (16 * h));
+    }
   }
   // dense layers: rows as packed
   for (int i = threadIdx.x; i < N4 * K4 / 2; i += blockDim.x) {
@@ -577,6 +587,51 @@ __device__ __forceinline__ void tile_input_row(const TileSmem& S, int s, int ch,
   uint16_t* out = S.x + s * XR_SAMPLE + (r + 1) * X_ROW + X_PIX + ch;
 #pragma unroll
   for (int c = 0; c < 16; ++c) out[c * X_PIX] = f2bf(((float)v[c] - 128.f) * (1.f / 64.f));
+}
+
+
+// Prefetch of one input row into registers, so that the loads of the next
+// tile are in flight while the current tile computes: the five aligned
+// 32-bit words that cover the row's 16 pixels. Only for upper pyramid levels
+// (rows start 128-byte aligned and the pitch is a multiple of 128 bytes, so
+// a word that starts inside the level lies inside the row's pitch).
+struct RowWords {
+  uint32_t w[5];
+  int cx, x4, wl;     // first pixel, first word's pixel, level width
+  bool row_ok;        // the row lies inside the level
+};
+
+__device__ __forceinline__ void row_prefetch(RowWords& R, const Geom& g, const Batch& b, int img,
+                                             int lv, float px, float py, int r) {
+  const float sc = __int_as_float((127 - lv) << 23);
+  R.cx = (int)floorf(px * sc + 0.5f) - 8;
+  const int cy = (int)floorf(py * sc + 0.5f) - 8 + r;
+  R.wl = g.w[lv];
+  R.row_ok = cy >= 0 && cy < g.h[lv];
+  R.x4 = R.cx & ~3;
+  const uint8_t* row = level_ptr(g, b, img, lv) + (long long)(R.row_ok ? cy : 0) * g.pitch[lv];
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    const int x = R.x4 + 4 * k;
+    R.w[k] = (R.row_ok && x >= 0 && x < R.wl)
+                 ? __ldg(reinterpret_cast<const uint32_t*>(row + x)) : 0x80808080u;
+  }
+}
+
+__device__ __forceinline__ void row_store(const RowWords& R, const TileSmem& S, int s, int ch,
+                                          int r) {
+  uint16_t* out = S.x + s * XR_SAMPLE + (r + 1) * X_ROW + X_PIX + ch;
+  const unsigned sh = 8u * (unsigned)(R.cx - R.x4);
+  uint32_t a[4];      // the 16 pixels, aligned to the row's first pixel
+#pragma unroll
+  for (int k = 0; k < 4; ++k) a[k] = __funnelshift_r(R.w[k], R.w[k + 1], sh);
+#pragma unroll
+  for (int c = 0; c < 16; ++c) {
+    const int x = R.cx + c;
+    uint32_t v = (a[c >> 2] >> (8 * (c & 3))) & 0xffu;
+    if (!R.row_ok || x < 0 || x >= R.wl) v = 128u;
+    out[c * X_PIX] = f2bf(((float)v - 128.f) * (1.f / 64.f));
+  }
 }
 
 }  // namespace net

@@ -128,14 +128,50 @@ def test_batch_graph_replay_and_autotune():
                             for i in range(total)], stream=s)
         best = b.autotune(reps=1, stream=s)
         assert best > 0
-        k2, shift = b.get_tune()
-        assert k2 in (64, 128, 256, 512) and shift in (-1, 0, 1)
+        k2, shift, after = b.get_tune()
+        assert k2 in (64, 128, 256, 512) and shift in (-1, 0, 1) and after in (0, 1)
         b.set_graph(True)
         schedule = [[1] * total for _ in range(N_FRAMES)]
         _run_batch(b, seqs, schedule, stream=s)
     s.synchronize()
     _check_equal(b, groups, seqs, schedule)
-    assert b.launches_per_step() == 3
+    assert b.launches_per_step() == 3 + 2 * after
+
+
+@pytest.mark.parametrize("learned", [False, True])
+def test_batch_stereo_after_selection_equals_streams_alone(learned):
+    """Matching only the selected keypoints, after selection, gives the same
+    lists as the frontend's order (every candidate matched beside temporal
+    tracking), with and without the learned start, skipped streams included."""
+    groups, seqs = _make()
+    net = None
+    if learned:
+        rng = np.random.default_rng(5)
+        flat = (rng.normal(0, 0.05, vio.INITNET_N_PARAMS)).astype(np.float32)
+        flat[-1] = 3.0
+        net = vio.InitNet(flat, 1, 2, 1, 0.5)
+    total = sum(g[3] for g in groups)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        b = vio.Batch(groups)
+        if net is not None:
+            b.set_initnet(net)
+        b.set_tune(128, 0, 1)
+        b.set_graph(True)
+        assert b.launches_per_step() == (4 if learned else 3) + 2
+        rng2 = np.random.default_rng(2)
+        schedule = [[1] * total] + [list((rng2.random(total) < 0.7).astype(int))
+                                    for _ in range(5)]
+        for k in range(total):
+            n_act = 0
+            for act in schedule:
+                if act[k]:
+                    n_act += 1
+                    if n_act > N_FRAMES:
+                        act[k] = 0
+        _run_batch(b, seqs, schedule, stream=s)
+    s.synchronize()
+    _check_equal(b, groups, seqs, schedule, net)
 
 
 def test_batch_with_initnet_equals_streams_alone():
