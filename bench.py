@@ -46,6 +46,9 @@ CONFIG = {"workload": WORKLOAD, "frames": N_FRAMES, "w": W, "h": H, "levels": LE
 # algorithmic FP32 operations of one keypoint through one direction at one
 # level of the KLT: template 52 x ~72 + 5 Gauss-Newton steps of 52 x ~26
 FLOPS_PER_KP_DIR_LEVEL = 52 * 72 + 5 * 52 * 26
+# DRAM bytes (read + write) of one frame_track_kernel launch of this workload,
+# from the ncu capture summarised in profiles/frame_kernels_752x480.md
+TRACK_TRAFFIC_BYTES = 1928448
 
 
 def seq_seed(rank: int) -> int:
@@ -372,6 +375,29 @@ def serving_run(torch, vio, seconds, net, tune, seqs=None):
             "learned": net is not None, **summ}
 
 
+def profile_frontend(w, h, n_streams, learned, steps=3):
+    """A few frontend steps of one size (5 levels, cells for ~1000 keypoints
+    per 1920x1080 image, motion up to 40 px), for kernel profiles."""
+    import torch
+    from paper_2609_30459_gb300 import initnet_train, synth, vio
+    vio.load(build=True)
+    cw, ch = {1920: (48, 43), 1280: (42, 36), 752: (37, 32)}.get(w, (32, 32))
+    seq = synth.make_sequence(4012, steps, w, h, 1, max_motion=40.0, tex_size=2048)
+    fr = torch.from_numpy(seq.frames).cuda()
+    p = vio.default_params(n_levels=5, cell_w=cw, cell_h=ch)
+    fe = vio.Frontend(p, w, h, n_streams, 2 * (w // cw) * (h // ch))
+    net = vio.InitNet.load(initnet_train.DEFAULT_WEIGHTS) if learned else None
+    if net is not None:
+        fe.set_initnet(net)
+    frames = fr.view(steps, 1, 2, h, w).expand(steps, n_streams, 2, h, w).contiguous()
+    for t in range(steps):
+        fe.step(frames[t])
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_frontend": [w, h, n_streams], "learned": learned,
+                      "tracks": int(fe.view()["track_count"].sum().item())}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -384,7 +410,12 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=60.0)
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--profile-frontend", nargs=3, type=int, metavar=("W", "H", "STREAMS"),
+                    help="only run 3 frontend steps of this size (for kernel profiles)")
+    ap.add_argument("--learned", action="store_true", help="with --profile-frontend")
     args = ap.parse_args()
+    if args.profile_frontend:
+        return profile_frontend(*args.profile_frontend, args.learned)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
@@ -473,7 +504,9 @@ def main():
     if flops is not None and t_launch:
         ach = flops / t_launch / 1e12
         roofline = {"bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s",
-                    "frac": ach / fp32_peak, "traffic": None, "kernel": "frame_track_kernel",
+                    "frac": ach / fp32_peak, "traffic": TRACK_TRAFFIC_BYTES,
+                    "traffic_note": "DRAM bytes per launch from one ncu capture (cold caches "
+                                    "between ncu passes)", "kernel": "frame_track_kernel",
                     "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x max SM clock "
                                    f"{sm_max:.0f} MHz ({peak_src} clock)",
                     "avg_launch_us": 1e6 * t_launch / args.steps}

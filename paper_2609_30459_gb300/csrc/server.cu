@@ -6,13 +6,16 @@
 // waits in its class's FIFO while no slot is free.
 //
 // Continuous batching: frames are uploaded as they arrive (pinned host ->
-// a per-slot staging buffer, on the upload stream, overlapping the step in
-// flight); whenever no step is in flight, every admitted session with an
-// uploaded frame joins the next step: staging -> its batch slot (device to
-// device, on the compute stream after the upload's event), one batch step
-// (its captured graph), then the lists of every group are read back into
-// pinned buffers before the step's completion event. Completions carry the
-// frame's arrival, launch and completion times.
+// a per-slot staging buffer, on the upload stream, overlapping the steps in
+// flight); while fewer than two steps are in flight, every admitted session
+// with an uploaded frame joins the next step: staging -> its batch slot
+// (device to device, on the compute stream after the upload's event), one
+// batch step (its captured graph), then the lists of the groups in the step
+// are read back into one of two sets of pinned buffers before the step's
+// completion event. With two steps in flight the GPU goes from one step to
+// the next without waiting for the host; a session can be in both (its
+// frames run in stream order). Completions carry the frame's arrival, launch
+// and completion times.
 #include <string.h>
 
 #include <chrono>
@@ -56,23 +59,31 @@ struct Slot {
   int order = 0;                       // staging buffer of the oldest uploaded frame
 };
 
+constexpr int kInFlight = 2;
+
 struct Class {
   vio_stream_group spec;
   size_t frame_bytes = 0;
   std::vector<Slot> slots;
   std::deque<int64_t> waiting;
-  // pinned copies of the group's outputs after each step
-  float* h_xy = nullptr;
-  int32_t* h_id = nullptr;
-  int32_t* h_count = nullptr;
-  int32_t* h_new = nullptr;
-  std::vector<int32_t> parity;
+  // pinned copies of the group's outputs after a step (one set per step in flight)
+  float* h_xy[kInFlight] = {};
+  int32_t* h_id[kInFlight] = {};
+  int32_t* h_count[kInFlight] = {};
+  int32_t* h_new[kInFlight] = {};
 };
 
 struct Member {
   int cls, slot, buf;
   int64_t session;
   Req req;
+};
+
+struct StepRec {
+  std::vector<Member> members;
+  std::vector<std::vector<int32_t>> parity;   // per class, list parity after the step
+  double t_launch = 0;
+  int out = 0;                                // output buffer set and event index
 };
 
 }  // namespace
@@ -82,10 +93,9 @@ struct vio_server {
   std::vector<Class> cls;
   std::vector<Session> sessions;
   cudaStream_t cs = nullptr, us = nullptr;
-  cudaEvent_t step_ev = nullptr;
-  bool in_flight = false;
-  double t_launch = 0;
-  std::vector<Member> members;
+  cudaEvent_t step_ev[kInFlight] = {};
+  std::deque<StepRec> flight;
+  int next_out = 0;
   std::vector<int32_t> active;
   std::vector<vio_server_done> done;
   std::vector<int64_t> closing;        // sessions closing while they hold a slot
@@ -144,10 +154,12 @@ void release_closing(vio_server* s) {
   }
 }
 
-// Completion of the step in flight: records, caller outputs, stage buffers.
+// Completion of the oldest step in flight: records, caller outputs, stage
+// buffers.
 void complete_step(vio_server* s, int32_t status) {
   const double t = now_s();
-  for (const Member& m : s->members) {
+  const StepRec& R = s->flight.front();
+  for (const Member& m : R.members) {
     Class& C = s->cls[m.cls];
     Slot& L = C.slots[m.slot];
     Session& S = s->sessions[m.session];
@@ -155,16 +167,16 @@ void complete_step(vio_server* s, int32_t status) {
     d.session = m.session;
     d.tag = m.req.tag;
     d.t_arrival = m.req.t_arrival;
-    d.t_launch = s->t_launch;
+    d.t_launch = R.t_launch;
     d.t_done = t;
     d.status = status;
     if (status == VIO_OK) {
-      const int ns = C.spec.n_streams, cap = C.spec.capacity;
-      const int q = C.parity[m.slot];
+      const int ns = C.spec.n_streams, cap = C.spec.capacity, o = R.out;
+      const int q = R.parity[m.cls][m.slot];
       const size_t base = ((size_t)q * ns + m.slot) * 2;
-      d.n_tracks[0] = C.h_count[base];
-      d.n_tracks[1] = C.h_count[base + 1];
-      d.n_new = C.h_new[m.slot];
+      d.n_tracks[0] = C.h_count[o][base];
+      d.n_tracks[1] = C.h_count[o][base + 1];
+      d.n_new = C.h_new[o][m.slot];
       if (S.out_count) {
         S.out_count[0] = d.n_tracks[0];
         S.out_count[1] = d.n_tracks[1];
@@ -172,16 +184,32 @@ void complete_step(vio_server* s, int32_t status) {
       for (int c = 0; c < 2; ++c) {
         const size_t off = (base + c) * cap;
         const int n = d.n_tracks[c] < cap ? d.n_tracks[c] : cap;
-        if (S.out_xy) memcpy(S.out_xy + 2 * (size_t)c * cap, C.h_xy + 2 * off, (size_t)n * 8);
-        if (S.out_id) memcpy(S.out_id + (size_t)c * cap, C.h_id + off, (size_t)n * 4);
+        if (S.out_xy)
+          memcpy(S.out_xy + 2 * (size_t)c * cap, C.h_xy[o] + 2 * off, (size_t)n * 8);
+        if (S.out_id) memcpy(S.out_id + (size_t)c * cap, C.h_id[o] + off, (size_t)n * 4);
       }
     }
     s->done.push_back(d);
     L.state[m.buf] = kFree;
   }
-  s->members.clear();
-  s->in_flight = false;
+  s->flight.pop_front();
   release_closing(s);
+}
+
+// Completion of every step in flight whose event has passed (in order).
+vio_status drain(vio_server* s, bool wait) {
+  while (!s->flight.empty()) {
+    cudaEvent_t ev = s->step_ev[s->flight.front().out];
+    const cudaError_t e = wait ? cudaEventSynchronize(ev) : cudaEventQuery(ev);
+    if (e == cudaErrorNotReady) return VIO_OK;
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      while (!s->flight.empty()) complete_step(s, VIO_ERR_CUDA);
+      return VIO_ERR_CUDA;
+    }
+    complete_step(s, VIO_OK);
+  }
+  return VIO_OK;
 }
 
 // Uploads of arrived frames into free staging buffers.
@@ -211,7 +239,7 @@ vio_status start_uploads(vio_server* s) {
 }
 
 vio_status launch_step(vio_server* s) {
-  s->members.clear();
+  StepRec R;
   std::fill(s->active.begin(), s->active.end(), 0);
   for (size_t c = 0; c < s->cls.size(); ++c) {
     Class& C = s->cls[c];
@@ -228,34 +256,41 @@ vio_status launch_step(vio_server* s) {
         return VIO_ERR_CUDA;
       L.state[b] = kInStep;
       L.order ^= 1;
-      s->members.push_back(Member{(int)c, (int)j, b, L.session, L.req[b]});
+      R.members.push_back(Member{(int)c, (int)j, b, L.session, L.req[b]});
       s->active[stream_index(s, (int)c, (int)j)] = 1;
     }
   }
-  if (s->members.empty()) return VIO_OK;
-  s->t_launch = now_s();
+  if (R.members.empty()) return VIO_OK;
+  R.t_launch = now_s();
+  R.out = s->next_out;
+  R.parity.resize(s->cls.size());
+  s->flight.push_back(R);          // from here on a failure completes it with the error
+  StepRec& F = s->flight.back();
   vio_status st = vio_batch_step(s->batch, s->active.data(), s->cs);
   if (st != VIO_OK) return st;
   std::vector<char> has(s->cls.size(), 0);
-  for (const Member& m : s->members) has[m.cls] = 1;
+  for (const Member& m : F.members) has[m.cls] = 1;
+  const int o = F.out;
   for (size_t c = 0; c < s->cls.size(); ++c) {
     if (!has[c]) continue;
     Class& C = s->cls[c];
     vio_frontend_view v;
-    if (vio_batch_get_view(s->batch, (int)c, &v, C.parity.data()) != VIO_OK) return VIO_ERR_CUDA;
+    F.parity[c].assign(C.slots.size(), 0);
+    if (vio_batch_get_view(s->batch, (int)c, &v, F.parity[c].data()) != VIO_OK)
+      return VIO_ERR_CUDA;
     const size_t ns = C.spec.n_streams, cap = C.spec.capacity, lists = 2 * ns * 2;
-    if (cudaMemcpyAsync(C.h_count, v.d_track_count, lists * 4, cudaMemcpyDeviceToHost, s->cs) !=
+    if (cudaMemcpyAsync(C.h_count[o], v.d_track_count, lists * 4, cudaMemcpyDeviceToHost,
+                        s->cs) != cudaSuccess ||
+        cudaMemcpyAsync(C.h_new[o], v.d_new_count, ns * 4, cudaMemcpyDeviceToHost, s->cs) !=
             cudaSuccess ||
-        cudaMemcpyAsync(C.h_new, v.d_new_count, ns * 4, cudaMemcpyDeviceToHost, s->cs) !=
-            cudaSuccess ||
-        cudaMemcpyAsync(C.h_xy, v.d_track_xy, lists * cap * 8, cudaMemcpyDeviceToHost, s->cs) !=
-            cudaSuccess ||
-        cudaMemcpyAsync(C.h_id, v.d_track_id, lists * cap * 4, cudaMemcpyDeviceToHost, s->cs) !=
-            cudaSuccess)
+        cudaMemcpyAsync(C.h_xy[o], v.d_track_xy, lists * cap * 8, cudaMemcpyDeviceToHost,
+                        s->cs) != cudaSuccess ||
+        cudaMemcpyAsync(C.h_id[o], v.d_track_id, lists * cap * 4, cudaMemcpyDeviceToHost,
+                        s->cs) != cudaSuccess)
       return VIO_ERR_CUDA;
   }
-  if (cudaEventRecord(s->step_ev, s->cs) != cudaSuccess) return VIO_ERR_CUDA;
-  s->in_flight = true;
+  if (cudaEventRecord(s->step_ev[o], s->cs) != cudaSuccess) return VIO_ERR_CUDA;
+  s->next_out ^= 1;
   ++s->steps;
   return VIO_OK;
 }
@@ -268,14 +303,17 @@ void destroy(vio_server* s) {
     for (Slot& L : C.slots)
       for (int b = 0; b < 2; ++b)
         if (L.up_ev[b]) cudaEventDestroy(L.up_ev[b]);
-    cudaFreeHost(C.h_xy);
-    cudaFreeHost(C.h_id);
-    cudaFreeHost(C.h_count);
-    cudaFreeHost(C.h_new);
+    for (int o = 0; o < kInFlight; ++o) {
+      cudaFreeHost(C.h_xy[o]);
+      cudaFreeHost(C.h_id[o]);
+      cudaFreeHost(C.h_count[o]);
+      cudaFreeHost(C.h_new[o]);
+    }
   }
   if (s->batch) vio_batch_destroy(s->batch);
   cudaFree(s->d_staging);
-  if (s->step_ev) cudaEventDestroy(s->step_ev);
+  for (int o = 0; o < kInFlight; ++o)
+    if (s->step_ev[o]) cudaEventDestroy(s->step_ev[o]);
   if (s->cs) cudaStreamDestroy(s->cs);
   if (s->us) cudaStreamDestroy(s->us);
   delete s;
@@ -334,7 +372,8 @@ extern "C" vio_status vio_server_create(vio_server** out, const vio_stream_group
       cudaMalloc(&s->d_staging, staging) != cudaSuccess ||
       cudaStreamCreateWithFlags(&s->cs, cudaStreamNonBlocking) != cudaSuccess ||
       cudaStreamCreateWithFlags(&s->us, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaEventCreateWithFlags(&s->step_ev, cudaEventDisableTiming) != cudaSuccess) {
+      cudaEventCreateWithFlags(&s->step_ev[0], cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&s->step_ev[1], cudaEventDisableTiming) != cudaSuccess) {
     cudaGetLastError();
     destroy(s);
     return VIO_ERR_OOM;
@@ -348,7 +387,6 @@ extern "C" vio_status vio_server_create(vio_server** out, const vio_stream_group
     C.spec = groups[k];
     C.frame_bytes = (size_t)2 * C.spec.w * C.spec.h;
     C.slots.resize(slots[k]);
-    C.parity.assign(slots[k], 0);
     for (Slot& L : C.slots)
       for (int b = 0; b < 2; ++b) {
         L.staging[b] = q;
@@ -359,14 +397,15 @@ extern "C" vio_status vio_server_create(vio_server** out, const vio_stream_group
         }
       }
     const size_t lists = (size_t)2 * slots[k] * 2, cap = C.spec.capacity;
-    if (cudaMallocHost(&C.h_xy, lists * cap * 8) != cudaSuccess ||
-        cudaMallocHost(&C.h_id, lists * cap * 4) != cudaSuccess ||
-        cudaMallocHost(&C.h_count, lists * 4) != cudaSuccess ||
-        cudaMallocHost(&C.h_new, (size_t)slots[k] * 4) != cudaSuccess) {
-      cudaGetLastError();
-      destroy(s);
-      return VIO_ERR_OOM;
-    }
+    for (int o = 0; o < kInFlight; ++o)
+      if (cudaMallocHost(&C.h_xy[o], lists * cap * 8) != cudaSuccess ||
+          cudaMallocHost(&C.h_id[o], lists * cap * 4) != cudaSuccess ||
+          cudaMallocHost(&C.h_count[o], lists * 4) != cudaSuccess ||
+          cudaMallocHost(&C.h_new[o], (size_t)slots[k] * 4) != cudaSuccess) {
+        cudaGetLastError();
+        destroy(s);
+        return VIO_ERR_OOM;
+      }
     total += slots[k];
   }
   s->active.assign(total, 0);
@@ -391,13 +430,13 @@ extern "C" vio_status vio_server_slots(const vio_server* s, int32_t cls, int32_t
 extern "C" vio_status vio_server_set_initnet(vio_server* s, const void* d_packed,
                                              const vio_initnet_cfg* cfg) {
   if (!s) return VIO_ERR_INVALID_ARG;
-  if (s->in_flight && cudaStreamSynchronize(s->cs) != cudaSuccess) return VIO_ERR_CUDA;
+  if (drain(s, true) != VIO_OK) return VIO_ERR_CUDA;
   return vio_batch_set_initnet(s->batch, d_packed, cfg);
 }
 
 extern "C" vio_status vio_server_set_tune(vio_server* s, const vio_batch_tune* t) {
   if (!s) return VIO_ERR_INVALID_ARG;
-  if (s->in_flight && cudaStreamSynchronize(s->cs) != cudaSuccess) return VIO_ERR_CUDA;
+  if (drain(s, true) != VIO_OK) return VIO_ERR_CUDA;
   return vio_batch_set_tune(s->batch, t);
 }
 
@@ -458,27 +497,21 @@ extern "C" vio_status vio_server_close(vio_server* s, int64_t session) {
     return VIO_OK;
   }
   s->closing.push_back(session);
-  if (!s->in_flight) release_closing(s);
+  release_closing(s);
   return VIO_OK;
 }
 
 extern "C" vio_status vio_server_poll(vio_server* s, int32_t* n_done) {
   if (!s) return VIO_ERR_INVALID_ARG;
-  vio_status st = VIO_OK;
-  if (s->in_flight) {
-    const cudaError_t e = cudaEventQuery(s->step_ev);
-    if (e == cudaSuccess) {
-      complete_step(s, VIO_OK);
-    } else if (e != cudaErrorNotReady) {
-      cudaGetLastError();
-      complete_step(s, VIO_ERR_CUDA);
-      st = VIO_ERR_CUDA;
-    }
-  }
+  vio_status st = drain(s, false);
   if (st == VIO_OK) st = start_uploads(s);
-  if (st == VIO_OK && !s->in_flight) {
+  if (st == VIO_OK && (int)s->flight.size() < kInFlight) {
     st = launch_step(s);
-    if (st != VIO_OK) complete_step(s, st);   // report the frames that did not run
+    if (st != VIO_OK) {   // report the frames of the failed step and of any before it
+      cudaStreamSynchronize(s->cs);
+      cudaGetLastError();
+      while (!s->flight.empty()) complete_step(s, st);
+    }
   }
   if (n_done) *n_done = (int32_t)s->done.size();
   return st;
