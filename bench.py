@@ -297,7 +297,7 @@ def batched_compare(torch, vio, steps, warmup, net):
             tracked += int(a[..., 0].sum() + a[..., 1].sum())
             survived += int(a[..., 2].sum() + a[..., 3].sum())
             learned += int(a[..., 7].sum())
-        k2, shift, after = b.get_tune()
+        k2, shift, after, first = b.get_tune()
         res[mode] = {"frames_per_s": n_streams * steps / total_s,
                      "p50_ms": percentile(lat, 50), "p99_ms": percentile(lat, 99),
                      "tracked_keypoints_per_s": tracked / total_s,
@@ -305,7 +305,8 @@ def batched_compare(torch, vio, steps, warmup, net):
                      "learned_share_of_survivors": learned / max(survived, 1),
                      "launches_per_step": b.launches_per_step(),
                      "tune": {"k2_threads": k2, "pyr_tile_shift": shift,
-                              "stereo_after_select": after, "best_ms": tune_ms}}
+                              "stereo_after_select": after, "pyr_first_levels": first,
+                              "best_ms": tune_ms}}
         b.close()
     if res.get("learned") and res.get("plain"):
         res["learned_vs_plain_fps"] = (res["learned"]["frames_per_s"] /
@@ -579,7 +580,8 @@ def main():
         tune = None
         if batched and batched.get("learned"):
             t = batched["learned"]["tune"]
-            tune = (t["k2_threads"], t["pyr_tile_shift"], t["stereo_after_select"])
+            tune = (t["k2_threads"], t["pyr_tile_shift"], t["stereo_after_select"],
+                    t["pyr_first_levels"])
         serve = serving_run(torch, vio, args.serve_seconds, net, tune)
 
     cpu = None

@@ -383,14 +383,18 @@ typedef struct {
 
 /* Tunables of a batch step: threads per block of the tracking launches (64,
  * 128, 256 or 512), the pyramid tile scale (-1, 0, 1: half, default, double
- * the deepest-level tile side), and the order of stereo matching (0: every
+ * the deepest-level tile side), the order of stereo matching (0: every
  * cell's candidates are matched beside temporal tracking; 1: only the
- * selected keypoints are matched, after selection, in two more launches).
- * Every setting gives the same lists bit for bit. */
+ * selected keypoints are matched, after selection, in two more launches),
+ * and the pyramid levels the fused pyramid+detection launch computes (1..4,
+ * 0 = up to 4; the rest follow in further pyramid launches: fewer levels per
+ * pass recompute less of the halo of level 0). Every setting gives the same
+ * lists bit for bit. */
 typedef struct {
   int32_t k2_threads;
   int32_t pyr_tile_shift;
   int32_t stereo_after_select;
+  int32_t pyr_first_levels;
 } vio_batch_tune;
 
 vio_status vio_batch_create(vio_batch** out, const vio_stream_group* groups, int32_t n_groups);
@@ -417,7 +421,7 @@ vio_status vio_batch_set_graph(vio_batch* b, int32_t enable);
 vio_status vio_batch_set_tune(vio_batch* b, const vio_batch_tune* t);
 vio_status vio_batch_get_tune(vio_batch* b, vio_batch_tune* t);
 
-/* Times every tunable combination (24) over `reps` pairs of steps (a first frame,
+/* Times every tunable combination (72) over `reps` pairs of steps (a first frame,
  * then a tracked frame, all streams active) on the frames the caller has put
  * in BOTH slots of every stream, keeps the fastest, and resets every stream.
  * *best_ms: the chosen combination's time per tracked step. Blocking. */

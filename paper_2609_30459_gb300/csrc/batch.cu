@@ -278,7 +278,7 @@ extern "C" vio_status vio_batch_create(vio_batch** out, const vio_stream_group* 
     cudaMemset(G.list_status, VIO_TRACK_EMPTY, lists);
   }
   b->mask_slot = 0;
-  b->tune = vio::FrameTune{128, 0, 0};
+  b->tune = vio::FrameTune{128, 0, 0, 0};
   b->use_graph = false;
   b->graph_ready = false;
   b->graph_done[0] = b->graph_done[1] = nullptr;
@@ -368,7 +368,9 @@ extern "C" vio_status vio_batch_set_tune(vio_batch* b, const vio_batch_tune* t) 
     return VIO_ERR_INVALID_ARG;
   if (t->pyr_tile_shift < -1 || t->pyr_tile_shift > 1) return VIO_ERR_INVALID_ARG;
   if (t->stereo_after_select != 0 && t->stereo_after_select != 1) return VIO_ERR_INVALID_ARG;
-  b->tune = vio::FrameTune{t->k2_threads, t->pyr_tile_shift, t->stereo_after_select};
+  if (t->pyr_first_levels < 0 || t->pyr_first_levels > 4) return VIO_ERR_INVALID_ARG;
+  b->tune = vio::FrameTune{t->k2_threads, t->pyr_tile_shift, t->stereo_after_select,
+                           t->pyr_first_levels};
   drop_graphs(b);
   return VIO_OK;
 }
@@ -378,6 +380,7 @@ extern "C" vio_status vio_batch_get_tune(vio_batch* b, vio_batch_tune* t) {
   t->k2_threads = b->tune.k2_threads;
   t->pyr_tile_shift = b->tune.pyr_tile_shift;
   t->stereo_after_select = b->tune.stereo_after;
+  t->pyr_first_levels = b->tune.pyr_first;
   return VIO_OK;
 }
 
@@ -416,10 +419,12 @@ extern "C" vio_status vio_batch_autotune(vio_batch* b, int32_t reps, void* strea
   float best = 1e30f;
   vio::FrameTune best_t = b->tune;
   vio_status st = VIO_OK;
-  for (int combo = 0; combo < 24 && st == VIO_OK; ++combo) {
-    const int ti = combo % 4, shift = (combo / 4) % 3 - 1, after = combo / 12;
+  const int firsts[3] = {0, 2, 1};
+  for (int combo = 0; combo < 72 && st == VIO_OK; ++combo) {
+    const int ti = combo % 4, shift = (combo / 4) % 3 - 1, after = (combo / 12) % 2;
+    const int first = firsts[combo / 24];
     {
-      b->tune = vio::FrameTune{threads[ti], shift, after};
+      b->tune = vio::FrameTune{threads[ti], shift, after, first};
       float total = 0.f;
       for (int r = 0; r < reps; ++r) {
         reset_all(b, s);
@@ -479,7 +484,7 @@ extern "C" int32_t vio_batch_launches_per_step(const vio_batch* b) {
   std::vector<vio::Geom> g;
   for (const auto& G : b->groups) g.push_back(vio::make_geom(G.layout));
   return vio::frame_launches(g.data(), (int)g.size(), b->net != nullptr,
-                            b->tune.stereo_after != 0);
+                            b->tune.stereo_after != 0, b->tune.pyr_first);
 }
 
 extern "C" vio_status vio_batch_device_bytes(const vio_stream_group* groups, int32_t n_groups,

@@ -656,14 +656,20 @@ __global__ void __launch_bounds__(K3_THREADS) frame_append_kernel(const __grid_c
   }
 }
 
+// Levels the fused pass of K1 computes (the rest follow in further passes).
+int first_levels(const Geom& g, int pyr_first) {
+  const int m = g.n_levels > 1 ? pyr::pass_levels(g.n_levels, 0) : 0;
+  return (pyr_first > 0 && pyr_first < m) ? pyr_first : m;
+}
+
 K1Args front_args(const vio_params& p, const Geom& g, const Batch& all, int det_step,
                   const uint8_t* mask, long long mask_stride, unsigned long long* cand,
-                  int32_t* cand_count, int tile_shift) {
+                  int32_t* cand_count, int tile_shift, int pyr_first) {
   const int gx = g.w[0] / p.cell_w, gy = g.h[0] / p.cell_h;
   K1Args a{};
   a.g = g;
   a.all = all;
-  a.m = g.n_levels > 1 ? pyr::pass_levels(g.n_levels, 0) : 0;
+  a.m = first_levels(g, pyr_first);
   a.T = a.m > 0 ? pyr::top_tile(a.m, tile_shift) : 1;
   a.ntx = a.nty = 1;
   if (a.m > 0) pyr::pass_tiles(g.w, g.h, 0, a.m, a.T, a.ntx, a.nty);
@@ -693,10 +699,10 @@ cudaError_t launch_k1(const MultiK1& mm, int smem, cudaStream_t s) {
 
 }  // namespace
 
-int frame_front_smem(const Geom& g, const vio_params& p, int tile_shift) {
+int frame_front_smem(const Geom& g, const vio_params& p, int tile_shift, int pyr_first) {
   int smem = det::cell_smem_bytes(p.cell_w, p.cell_h);
-  if (g.n_levels > 1) {
-    const int m = pyr::pass_levels(g.n_levels, 0);
+  const int m = first_levels(g, pyr_first);
+  if (m > 0) {
     const int ps = pyr::pass_smem_max(g.w, g.h, 0, m, pyr::top_tile(m, tile_shift));
     smem = ps > smem ? ps : smem;
   }
@@ -708,10 +714,10 @@ cudaError_t launch_front(const vio_params& p, const Geom& g, const Batch& all, i
                          int32_t* cand_count, cudaStream_t s) {
   MultiK1 mm{};
   mm.n = 1;
-  mm.a[0] = front_args(p, g, all, det_step, mask, mask_stride, cand, cand_count, 0);
+  mm.a[0] = front_args(p, g, all, det_step, mask, mask_stride, cand, cand_count, 0, 0);
   const long long units = (all.n + det_step - 1) / det_step;
   mm.block_end[0] = units * mm.a[0].blocks_per_unit;
-  return launch_k1(mm, frame_front_smem(g, p, 0), s);
+  return launch_k1(mm, frame_front_smem(g, p, 0, 0), s);
 }
 
 cudaError_t launch_frames(const FrameLaunch* fl, int n_groups, const FrameTune& tune,
@@ -730,7 +736,7 @@ cudaError_t launch_frames(const FrameLaunch* fl, int n_groups, const FrameTune& 
   for (int i = 0; i < n_groups; ++i) {
     const FrameLaunch& f = fl[i];
     K1Args a = front_args(f.p, f.g, f.cur, 2, nullptr, 0, f.cand, f.cand_count,
-                          tune.pyr_tile_shift);
+                          tune.pyr_tile_shift, tune.pyr_first);
     a.slotted = f.slotted;
     a.n_streams = f.n_streams;
     a.parity = f.parity;
@@ -739,7 +745,7 @@ cudaError_t launch_frames(const FrameLaunch* fl, int n_groups, const FrameTune& 
     m1.a[i] = a;
     acc += (long long)f.n_streams * a.blocks_per_unit;
     m1.block_end[i] = acc;
-    const int sm = frame_front_smem(f.g, f.p, tune.pyr_tile_shift);
+    const int sm = frame_front_smem(f.g, f.p, tune.pyr_tile_shift, tune.pyr_first);
     smem1 = sm > smem1 ? sm : smem1;
   }
   cudaError_t e = launch_k1(m1, smem1, s);
@@ -748,8 +754,9 @@ cudaError_t launch_frames(const FrameLaunch* fl, int n_groups, const FrameTune& 
   mark(1);
   for (int i = 0; i < n_groups; ++i) {
     const FrameLaunch& f = fl[i];
-    if (f.g.n_levels > 1 + pyr::kMaxPass) {
-      e = launch_pyramid_from(f.g, f.cur, pyr::kMaxPass, f.p.round_mode, s);
+    const int m1 = first_levels(f.g, tune.pyr_first);
+    if (f.g.n_levels > 1 + m1) {
+      e = launch_pyramid_from(f.g, f.cur, m1, f.p.round_mode, s);
       if (e != cudaSuccess) return e;
     }
   }
@@ -843,10 +850,13 @@ cudaError_t launch_frames(const FrameLaunch* fl, int n_groups, const FrameTune& 
   return cudaGetLastError();
 }
 
-int frame_launches(const Geom* g, int n_groups, bool with_net, bool stereo_after) {
+int frame_launches(const Geom* g, int n_groups, bool with_net, bool stereo_after,
+                   int pyr_first) {
   int n = (with_net ? 4 : 3) + (stereo_after ? 2 : 0);   // K1, (KN), K2, K3, (K4, K5)
-  for (int i = 0; i < n_groups; ++i)
-    if (g[i].n_levels > 1 + pyr::kMaxPass) ++n;
+  for (int i = 0; i < n_groups; ++i) {
+    const int rest = g[i].n_levels - 1 - first_levels(g[i], pyr_first);
+    if (rest > 0) n += (rest + pyr::kMaxPass - 1) / pyr::kMaxPass;
+  }
   return n;
 }
 

@@ -12,6 +12,7 @@ struct FrameTune {
   int k2_threads;      // threads per block of the tracking launch (64..512)
   int pyr_tile_shift;  // deepest-level pyramid tile side = (32 >> (m-1)) << shift
   int stereo_after;    // 1: stereo-match only the selected keypoints, after selection
+  int pyr_first;       // pyramid levels of K1's fused pass (1..4; 0 = as many as fit)
 };
 
 struct FrameLaunch {
@@ -93,7 +94,8 @@ __host__ __device__ inline StreamRef stream_ref(const FrameLaunch& f, int s) {
 // stage boundaries (or null).
 cudaError_t launch_frames(const FrameLaunch* f, int n_groups, const FrameTune& tune,
                           cudaStream_t s, cudaEvent_t* marks);
-int frame_launches(const Geom* g, int n_groups, bool with_net, bool stereo_after);
+int frame_launches(const Geom* g, int n_groups, bool with_net, bool stereo_after,
+                   int pyr_first);
 
 // Keypoint lists (2 per stream) one launch of the proposal kernel handles.
 constexpr int KN_MAX_LISTS = 256;
@@ -108,7 +110,7 @@ inline bool initnet_cfg_ok(const vio_initnet_cfg* c, int n_levels, const void* p
     return false;
   return c->min_conf == c->min_conf;   // not NaN
 }
-int frame_front_smem(const Geom& g, const vio_params& p, int tile_shift);
+int frame_front_smem(const Geom& g, const vio_params& p, int tile_shift, int pyr_first);
 // Fused pyramid (levels 1-4) and per-cell detection candidates of every
 // det_step-th image of `all`, one launch.
 cudaError_t launch_front(const vio_params& p, const Geom& g, const Batch& all, int det_step,

@@ -212,7 +212,7 @@ extern "C" int32_t vio_frontend_launches_per_step(const vio_frontend* fe) {
   vio_pyr_layout L;
   if (vio_pyr_layout_make(fe->w, fe->h, fe->p.n_levels, fe->w, &L) != VIO_OK) return 0;
   const vio::Geom g = vio::make_geom(L);
-  return vio::frame_launches(&g, 1, fe->net != nullptr, false);
+  return vio::frame_launches(&g, 1, fe->net != nullptr, false, 0);
 }
 
 extern "C" vio_status vio_frontend_set_initnet(vio_frontend* fe, const void* d_packed,
@@ -283,7 +283,7 @@ extern "C" vio_status vio_frontend_step(vio_frontend* fe, const uint8_t* d_frame
     f.net_out = fe->net_out;
     f.trk_learned = fe->trk_learned;
   }
-  const FrameTune tune{128, 0, 0};
+  const FrameTune tune{128, 0, 0, 0};
   if (launch_frames(&f, 1, tune, s, fe->timing ? ev.data() : nullptr) != cudaSuccess)
     return VIO_ERR_CUDA;
   if (fe->timing) fe->ev_rec.push_back(ev);

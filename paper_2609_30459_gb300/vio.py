@@ -59,7 +59,7 @@ class StreamGroup(ctypes.Structure):
 
 class BatchTune(ctypes.Structure):
     _fields_ = [("k2_threads", ctypes.c_int32), ("pyr_tile_shift", ctypes.c_int32),
-                ("stereo_after_select", ctypes.c_int32)]
+                ("stereo_after_select", ctypes.c_int32), ("pyr_first_levels", ctypes.c_int32)]
 
 
 class InitNetCfg(ctypes.Structure):
@@ -688,15 +688,16 @@ class Batch:
     def set_graph(self, enable: bool):
         _check(load().vio_batch_set_graph(self.handle, 1 if enable else 0), "set_graph")
 
-    def set_tune(self, k2_threads: int, pyr_tile_shift: int, stereo_after_select: int = 0):
-        t = BatchTune(k2_threads, pyr_tile_shift, stereo_after_select)
+    def set_tune(self, k2_threads: int, pyr_tile_shift: int, stereo_after_select: int = 0,
+                 pyr_first_levels: int = 0):
+        t = BatchTune(k2_threads, pyr_tile_shift, stereo_after_select, pyr_first_levels)
         _check(load().vio_batch_set_tune(self.handle, ctypes.byref(t)), "set_tune")
 
-    def get_tune(self) -> tuple[int, int, int]:
-        """(k2_threads, pyr_tile_shift, stereo_after_select)."""
+    def get_tune(self) -> tuple[int, int, int, int]:
+        """(k2_threads, pyr_tile_shift, stereo_after_select, pyr_first_levels)."""
         t = BatchTune()
         _check(load().vio_batch_get_tune(self.handle, ctypes.byref(t)), "get_tune")
-        return t.k2_threads, t.pyr_tile_shift, t.stereo_after_select
+        return t.k2_threads, t.pyr_tile_shift, t.stereo_after_select, t.pyr_first_levels
 
     def autotune(self, reps: int = 3, stream=None) -> float:
         ms = ctypes.c_float()
@@ -854,8 +855,9 @@ class Server:
                                              ctypes.byref(net.cfg) if net else None),
                "vio_server_set_initnet")
 
-    def set_tune(self, k2_threads: int, pyr_tile_shift: int, stereo_after_select: int = 0):
-        t = BatchTune(k2_threads, pyr_tile_shift, stereo_after_select)
+    def set_tune(self, k2_threads: int, pyr_tile_shift: int, stereo_after_select: int = 0,
+                 pyr_first_levels: int = 0):
+        t = BatchTune(k2_threads, pyr_tile_shift, stereo_after_select, pyr_first_levels)
         _check(load().vio_server_set_tune(self.handle, ctypes.byref(t)), "vio_server_set_tune")
 
     def open(self, cls: int):

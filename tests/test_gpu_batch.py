@@ -128,14 +128,32 @@ def test_batch_graph_replay_and_autotune():
                             for i in range(total)], stream=s)
         best = b.autotune(reps=1, stream=s)
         assert best > 0
-        k2, shift, after = b.get_tune()
+        k2, shift, after, first = b.get_tune()
         assert k2 in (64, 128, 256, 512) and shift in (-1, 0, 1) and after in (0, 1)
+        assert first in (0, 1, 2)
         b.set_graph(True)
         schedule = [[1] * total for _ in range(N_FRAMES)]
         _run_batch(b, seqs, schedule, stream=s)
     s.synchronize()
     _check_equal(b, groups, seqs, schedule)
-    assert b.launches_per_step() == 3 + 2 * after
+    assert b.launches_per_step() >= 3 + 2 * after
+
+
+@pytest.mark.parametrize("first", [1, 2])
+def test_batch_pyramid_split_equals_streams_alone(first):
+    """Fewer levels in the fused pyramid+detection launch (the rest in
+    further pyramid launches) gives the same lists."""
+    groups, seqs = _make()
+    total = sum(g[3] for g in groups)
+    b = vio.Batch(groups)
+    b.set_tune(256, 1, 0, first)
+    assert b.get_tune() == (256, 1, 0, first)
+    schedule = [[1] * total for _ in range(N_FRAMES)]
+    _run_batch(b, seqs, schedule)
+    _check_equal(b, groups, seqs, schedule)
+    # 4 levels (group 0) and 3 (group 1): one more pyramid launch per group
+    # whose levels do not all fit in the first pass
+    assert b.launches_per_step() == 3 + (2 if first == 1 else 1)
 
 
 @pytest.mark.parametrize("learned", [False, True])
