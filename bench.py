@@ -12,7 +12,7 @@ resident in HBM (144 MB, above the 129 MB L2; each frame is read once per
 pass of the sequence).
 
 Reported beside it: end to end through the C ABI from pinned host memory
-(upload, step, read-back, one host wait per frame), per-stage times, the
+(upload, step, read-back; pipelined, and with one host wait per frame), the
 roofline of the dominant kernel, a pyramid+detection HBM roofline pass over a
 1.1 GB device-resident batch, and the CPU oracle timed on the host.
 
@@ -297,7 +297,7 @@ def batched_compare(torch, vio, steps, warmup, net):
             tracked += int(a[..., 0].sum() + a[..., 1].sum())
             survived += int(a[..., 2].sum() + a[..., 3].sum())
             learned += int(a[..., 7].sum())
-        k2, shift, after, first = b.get_tune()
+        k2, shift, after, first, k1 = b.get_tune()
         res[mode] = {"frames_per_s": n_streams * steps / total_s,
                      "p50_ms": percentile(lat, 50), "p99_ms": percentile(lat, 99),
                      "tracked_keypoints_per_s": tracked / total_s,
@@ -306,7 +306,7 @@ def batched_compare(torch, vio, steps, warmup, net):
                      "launches_per_step": b.launches_per_step(),
                      "tune": {"k2_threads": k2, "pyr_tile_shift": shift,
                               "stereo_after_select": after, "pyr_first_levels": first,
-                              "best_ms": tune_ms}}
+                              "k1_threads": k1, "best_ms": tune_ms}}
         b.close()
     if res.get("learned") and res.get("plain"):
         res["learned_vs_plain_fps"] = (res["learned"]["frames_per_s"] /
@@ -512,55 +512,69 @@ def main():
                                    f"{sm_max:.0f} MHz ({peak_src} clock)",
                     "avg_launch_us": 1e6 * t_launch / args.steps}
 
-    # end to end through the C ABI from pinned host memory, one wait per frame
+    # end to end through the C ABI from pinned host memory: every step uploads
+    # its stereo pair and reads back the keypoint lists and new detections
+    # (vio_frontend_step_host: copy in, step, copy out, all enqueued).
+    # Throughput: steps issued back to back over a ring of 4 frame and result
+    # slots, the host waiting for (and reading) the results of the step two
+    # back. Latency: the same steps with one host wait per frame.
     e2e = None
     if rank == 0 or world > 1:
+        R = 4
         host = torch.from_numpy(frames_np).pin_memory()
-        slots = torch.empty((2, 1, 2, H, W), dtype=torch.uint8, device="cuda")
-        out_xy = torch.empty((1, 2, CAPACITY, 2), dtype=torch.float32).pin_memory()
-        out_id = torch.empty((1, 2, CAPACITY), dtype=torch.int32).pin_memory()
-        out_cnt = torch.empty((1, 2), dtype=torch.int32).pin_memory()
-        out_new = torch.empty((1, CAPACITY, 2), dtype=torch.float32).pin_memory()
-        out_nc = torch.empty((1,), dtype=torch.int32).pin_memory()
+        slots = torch.empty((R, 1, 2, H, W), dtype=torch.uint8, device="cuda")
+        outs = [fe.host_outputs() for _ in range(R)]
+        evs = [torch.cuda.Event() for _ in range(R)]
         fe.reset()
-        v = fe.view()
-        lat = []
+        got = [0]
 
-        def one(k):
+        def issue(k):
+            r = k % R
             f = k % N_FRAMES
-            slot = slots[k % 2]
-            slot.copy_(host[f: f + 1], non_blocking=True)
-            fe.step(slot)
-            vv = fe.view()
-            out_xy.copy_(vv["track_xy"], non_blocking=True)
-            out_id.copy_(vv["track_id"], non_blocking=True)
-            out_cnt.copy_(vv["track_count"], non_blocking=True)
-            out_new.copy_(vv["new_xy"], non_blocking=True)
-            out_nc.copy_(vv["new_count"], non_blocking=True)
-            stream.synchronize()
+            fe.step_host(host[f: f + 1], slots[r], outs[r])
+            evs[r].record(stream)
 
-        for k in range(args.warmup):
-            one(N_FRAMES - args.warmup + k)
+        def consume(k):
+            evs[k % R].synchronize()
+            got[0] += int(outs[k % R]["count"].sum())    # the host reads the result
+
+        def run(n, sync_each):
+            lat = []
+            for k in range(n):
+                ts = time.perf_counter()
+                if not sync_each and k >= 2:
+                    consume(k - 2)
+                issue(k)
+                if sync_each:
+                    consume(k)
+                    lat.append(time.perf_counter() - ts)
+            if not sync_each:
+                for k in range(max(n - 2, 0), n):
+                    consume(k)
+            return lat
+
+        run(args.warmup, True)
         fe.reset()
         torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
         t0 = time.perf_counter()
-        for k in range(args.steps):
-            ts = time.perf_counter()
-            one(k)
-            lat.append(time.perf_counter() - ts)
+        run(args.steps, False)
         e2e_s = time.perf_counter() - t0
+        fe.reset()
+        torch.cuda.synchronize()
+        lat = run(min(args.steps, 1000), True)
         if world > 1:
             tt = torch.tensor([e2e_s], device="cuda")
             dist.all_reduce(tt, op=dist.ReduceOp.MAX)
             e2e_s = float(tt.item())
-        del v
-        bo = sum(t.numel() * t.element_size() for t in (out_xy, out_id, out_cnt, out_new,
-                                                          out_nc))
+        bo = sum(t.numel() * t.element_size() for t in outs[0].values())
         e2e = {"value": world * args.steps / e2e_s, "unit": UNIT,
                "h2d_bytes_per_step": 2 * H * W, "d2h_bytes_per_step": bo,
-               "p50_ms": 1000 * percentile(lat, 50), "p99_ms": 1000 * percentile(lat, 99)}
+               "mode": "vio_frontend_step_host issued back to back, results read two steps later",
+               "sync_per_frame": {"frames_per_s": len(lat) / sum(lat),
+                                  "p50_ms": 1000 * percentile(lat, 50),
+                                  "p99_ms": 1000 * percentile(lat, 99)}}
 
     pd = pyramid_detect_roofline(torch, vio, frames, peaks, peak_src) if rank == 0 else None
 
@@ -577,12 +591,9 @@ def main():
         net = None
         if os.path.exists(initnet_train.DEFAULT_WEIGHTS):
             net = vio.InitNet.load(initnet_train.DEFAULT_WEIGHTS)
-        tune = None
-        if batched and batched.get("learned"):
-            t = batched["learned"]["tune"]
-            tune = (t["k2_threads"], t["pyr_tile_shift"], t["stereo_after_select"],
-                    t["pyr_first_levels"])
-        serve = serving_run(torch, vio, args.serve_seconds, net, tune)
+        # the batch's default tune: steps here hold one or two frames, for which
+        # the fewest launches per step are best (the batched tune is for full steps)
+        serve = serving_run(torch, vio, args.serve_seconds, net, None)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -282,6 +282,20 @@ vio_status vio_frontend_run(vio_frontend* fe, const uint8_t* d_frames, int32_t p
 /* Forget all tracks (next step starts fresh). Enqueued on `stream`. */
 vio_status vio_frontend_reset(vio_frontend* fe, void* stream);
 
+/* One step from and to host memory: copies the n_streams stereo frames from
+ * h_frames (pinned host memory, the layout of vio_frontend_step) into the
+ * caller's device buffer d_frames (kept alive until the next step has run),
+ * runs the step, and copies the outputs into the caller's pinned host
+ * buffers: track positions, ids and counts of every (stream, camera) list
+ * (2 * n_streams * capacity float2 / int32, 2 * n_streams int32; list of
+ * stream s camera c at slot (2 s + c) * capacity) and the new detections
+ * (n_streams * capacity float2, n_streams int32). All enqueued on `stream`:
+ * the host buffers hold the step's results once the stream has passed it. */
+vio_status vio_frontend_step_host(vio_frontend* fe, const uint8_t* h_frames, uint8_t* d_frames,
+                                  int32_t pitch, int64_t frame_stride, float* h_track_xy,
+                                  int32_t* h_track_id, int32_t* h_track_count, float* h_new_xy,
+                                  int32_t* h_new_count, void* stream);
+
 /* Device views of the frontend's outputs after the last step, per stream s
  * and camera c at slot base (2*s + c) * capacity:
  *   tracks:  float2 positions, int32 ids, uint8 status (VIO_TRACK_OK for a
@@ -386,15 +400,16 @@ typedef struct {
  * the deepest-level tile side), the order of stereo matching (0: every
  * cell's candidates are matched beside temporal tracking; 1: only the
  * selected keypoints are matched, after selection, in two more launches),
- * and the pyramid levels the fused pyramid+detection launch computes (1..4,
+ * the pyramid levels the fused pyramid+detection launch computes (1..4,
  * 0 = up to 4; the rest follow in further pyramid launches: fewer levels per
- * pass recompute less of the halo of level 0). Every setting gives the same
- * lists bit for bit. */
+ * pass recompute less of the halo of level 0), and the CTA size of that
+ * launch (128 or 256). Every setting gives the same lists bit for bit. */
 typedef struct {
   int32_t k2_threads;
   int32_t pyr_tile_shift;
   int32_t stereo_after_select;
   int32_t pyr_first_levels;
+  int32_t k1_threads;
 } vio_batch_tune;
 
 vio_status vio_batch_create(vio_batch** out, const vio_stream_group* groups, int32_t n_groups);
@@ -421,7 +436,7 @@ vio_status vio_batch_set_graph(vio_batch* b, int32_t enable);
 vio_status vio_batch_set_tune(vio_batch* b, const vio_batch_tune* t);
 vio_status vio_batch_get_tune(vio_batch* b, vio_batch_tune* t);
 
-/* Times every tunable combination (72) over `reps` pairs of steps (a first frame,
+/* Times every tunable combination (144) over `reps` pairs of steps (a first frame,
  * then a tracked frame, all streams active) on the frames the caller has put
  * in BOTH slots of every stream, keeps the fastest, and resets every stream.
  * *best_ms: the chosen combination's time per tracked step. Blocking. */

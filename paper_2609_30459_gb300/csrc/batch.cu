@@ -278,7 +278,7 @@ extern "C" vio_status vio_batch_create(vio_batch** out, const vio_stream_group* 
     cudaMemset(G.list_status, VIO_TRACK_EMPTY, lists);
   }
   b->mask_slot = 0;
-  b->tune = vio::FrameTune{128, 0, 0, 0};
+  b->tune = vio::FrameTune{128, 0, 0, 0, 256};
   b->use_graph = false;
   b->graph_ready = false;
   b->graph_done[0] = b->graph_done[1] = nullptr;
@@ -369,8 +369,9 @@ extern "C" vio_status vio_batch_set_tune(vio_batch* b, const vio_batch_tune* t) 
   if (t->pyr_tile_shift < -1 || t->pyr_tile_shift > 1) return VIO_ERR_INVALID_ARG;
   if (t->stereo_after_select != 0 && t->stereo_after_select != 1) return VIO_ERR_INVALID_ARG;
   if (t->pyr_first_levels < 0 || t->pyr_first_levels > 4) return VIO_ERR_INVALID_ARG;
+  if (t->k1_threads != 128 && t->k1_threads != 256) return VIO_ERR_INVALID_ARG;
   b->tune = vio::FrameTune{t->k2_threads, t->pyr_tile_shift, t->stereo_after_select,
-                           t->pyr_first_levels};
+                           t->pyr_first_levels, t->k1_threads};
   drop_graphs(b);
   return VIO_OK;
 }
@@ -381,6 +382,7 @@ extern "C" vio_status vio_batch_get_tune(vio_batch* b, vio_batch_tune* t) {
   t->pyr_tile_shift = b->tune.pyr_tile_shift;
   t->stereo_after_select = b->tune.stereo_after;
   t->pyr_first_levels = b->tune.pyr_first;
+  t->k1_threads = b->tune.k1_threads;
   return VIO_OK;
 }
 
@@ -420,11 +422,11 @@ extern "C" vio_status vio_batch_autotune(vio_batch* b, int32_t reps, void* strea
   vio::FrameTune best_t = b->tune;
   vio_status st = VIO_OK;
   const int firsts[3] = {0, 2, 1};
-  for (int combo = 0; combo < 72 && st == VIO_OK; ++combo) {
+  for (int combo = 0; combo < 144 && st == VIO_OK; ++combo) {
     const int ti = combo % 4, shift = (combo / 4) % 3 - 1, after = (combo / 12) % 2;
-    const int first = firsts[combo / 24];
+    const int first = firsts[(combo / 24) % 3], k1 = combo < 72 ? 256 : 128;
     {
-      b->tune = vio::FrameTune{threads[ti], shift, after, first};
+      b->tune = vio::FrameTune{threads[ti], shift, after, first, k1};
       float total = 0.f;
       for (int r = 0; r < reps; ++r) {
         reset_all(b, s);

@@ -30,7 +30,7 @@ namespace vio {
 namespace det {
 
 constexpr int kHalo = 4;
-constexpr int kThreads = 256;
+constexpr int kThreads = 128;   // CTA size of the standalone detection launches
 
 // score + 1 in [0, 255], 0 = no corner at tau >= 0
 __device__ __forceinline__ int fast_m(const int v[16], int c) {
@@ -68,6 +68,7 @@ __device__ __forceinline__ int ring_dy(int k) {
   return d[k];
 }
 
+template <int NT>
 __device__ __forceinline__ unsigned long long block_max_u64(unsigned long long v,
                                                             unsigned long long* red) {
 #pragma unroll
@@ -79,7 +80,7 @@ __device__ __forceinline__ unsigned long long block_max_u64(unsigned long long v
   __syncthreads();   // red[] may still be read from the previous round
   if (lane == 0) red[warp] = v;
   __syncthreads();
-  v = lane < (kThreads / 32) ? red[lane] : 0ull;
+  v = lane < (NT / 32) ? red[lane] : 0ull;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     const unsigned long long t = __shfl_xor_sync(0xffffffffu, v, o);
@@ -114,6 +115,7 @@ __host__ __device__ inline CellSmem cell_smem(int cw, int ch) {
 constexpr int kMaxCellSmem = 200 * 1024;
 __host__ __device__ inline int cell_smem_bytes(int cw, int ch) { return cell_smem(cw, ch).total; }
 
+template <int NT>
 __device__ __forceinline__ unsigned block_max_u32(unsigned v, unsigned* red) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
@@ -121,13 +123,13 @@ __device__ __forceinline__ unsigned block_max_u32(unsigned v, unsigned* red) {
   __syncthreads();
   if (lane == 0) red[warp] = v;
   __syncthreads();
-  v = lane < (kThreads / 32) ? red[lane] : 0u;
+  v = lane < (NT / 32) ? red[lane] : 0u;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
   return v;
 }
 
-// Detection in one cell of one image (blockDim.x == kThreads). Writes up to k
+// Detection in one cell of one image (blockDim.x == NT). Writes up to k
 // packed keys (best first) and the count.
 //
 // Exact branch-and-bound. A 9-arc holds one pixel of each opposite pair
@@ -142,6 +144,7 @@ __device__ __forceinline__ unsigned block_max_u32(unsigned v, unsigned* red) {
 // exactly known, and if there are k of them, no other pixel can enter the
 // top k. The value map holds the exact m where evaluated and ub elsewhere, so
 // the maximum test is "m > value of all 8 neighbours" in both cases.
+template <int NT>
 __device__ __forceinline__ void detect_cell(const uint8_t* __restrict__ src, int W, int H, int P,
                                             const CellGeom& cg, int cell,
                                             const uint8_t* __restrict__ mask,
@@ -174,7 +177,7 @@ __device__ __forceinline__ void detect_cell(const uint8_t* __restrict__ src, int
   const Split sm(MW);
   // pass A: bounds, and the largest bound of the cell's eligible pixels
   unsigned umax = 0;
-  for (int i = threadIdx.x; i < NR; i += kThreads) {
+  for (int i = threadIdx.x; i < NR; i += NT) {
     int r, c;
     sm(i, r, c);
     const int x = x0 - 1 + c, y = y0 - 1 + r;
@@ -195,7 +198,7 @@ __device__ __forceinline__ void detect_cell(const uint8_t* __restrict__ src, int
                          (!mask || mask[(long long)y * W + x] != 0);
     if (in_cell) umax = max(umax, (unsigned)u);
   }
-  umax = block_max_u32(umax, red);
+  umax = block_max_u32<NT>(umax, red);
   int n_found = 0;
   if (umax > 0) {
     const int tmin1 = T + 1;   // smallest m of a candidate
@@ -204,7 +207,7 @@ __device__ __forceinline__ void detect_cell(const uint8_t* __restrict__ src, int
     int q_done = 0;            // queue entries evaluated in earlier rounds
     for (;;) {
       // pass B: queue the pixels whose bound falls in [t, t_prev)
-      for (int base = 0; base < NR; base += kThreads) {
+      for (int base = 0; base < NR; base += NT) {
         const int i = base + threadIdx.x;
         const bool take = i < NR && ubm[i] >= t && ubm[i] < t_prev;
         const unsigned ball = __ballot_sync(0xffffffffu, take);
@@ -219,7 +222,7 @@ __device__ __forceinline__ void detect_cell(const uint8_t* __restrict__ src, int
       __syncthreads();
       const int q_end = q_count;
       // exact scores of the newly queued pixels
-      for (int e = q_done + threadIdx.x; e < q_end; e += kThreads) {
+      for (int e = q_done + threadIdx.x; e < q_end; e += NT) {
         const int i = queue[e];
         int r, c;
         sm(i, r, c);
@@ -234,7 +237,7 @@ __device__ __forceinline__ void detect_cell(const uint8_t* __restrict__ src, int
       }
       __syncthreads();
       // pass C: candidates with m in [t, t_prev) among everything evaluated
-      for (int e = threadIdx.x; e < q_end; e += kThreads) {
+      for (int e = threadIdx.x; e < q_end; e += NT) {
         const int i = queue[e];
         const int m = val[i];
         if (m < t || m >= t_prev) continue;
@@ -264,11 +267,11 @@ __device__ __forceinline__ void detect_cell(const uint8_t* __restrict__ src, int
     unsigned long long last = ~0ull;
     for (int round = 0; round < cg.k; ++round) {
       unsigned long long best = 0;
-      for (int e = threadIdx.x; e < nk; e += kThreads) {
+      for (int e = threadIdx.x; e < nk; e += NT) {
         const unsigned long long key = keys[e];
         if (key < last && key > best) best = key;
       }
-      best = block_max_u64(best, red64);
+      best = block_max_u64<NT>(best, red64);
       if (best == 0) break;
       if (threadIdx.x == 0) out_keys[round] = best;
       last = best;

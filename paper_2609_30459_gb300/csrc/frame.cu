@@ -48,8 +48,6 @@
 namespace vio {
 namespace {
 
-constexpr int K1_THREADS = 256;
-static_assert(K1_THREADS == pyr::kThreads && K1_THREADS == det::kThreads, "block size");
 
 struct K1Args {
   Geom g;
@@ -89,9 +87,12 @@ __device__ __forceinline__ int group_of(const M& mm, long long i, long long& sta
 // Block layout per group: units, each unit = the pyramid tiles of its images
 // followed by the detection cells of its first image, so that the blocks
 // reading one image run together and its level 0 is read from DRAM about once.
-__global__ void __launch_bounds__(K1_THREADS) frame_front_kernel(const __grid_constant__ MultiK1 mm) {
+// NT threads per CTA: 256 for a single frame's latency, 128 for throughput
+// over many streams (a tunable of the batch).
+template <int NT>
+__global__ void __launch_bounds__(NT) frame_front_kernel(const __grid_constant__ MultiK1 mm) {
   extern __shared__ __align__(16) uint8_t smem[];
-  __shared__ unsigned long long red[K1_THREADS / 32];
+  __shared__ unsigned long long red[NT / 32];
   long long start;
   const int gi = group_of(mm, blockIdx.x, start);
   const K1Args& a = mm.a[gi];
@@ -116,7 +117,7 @@ __global__ void __launch_bounds__(K1_THREADS) frame_front_kernel(const __grid_co
   }
   const int cell = rem - n_pyr;
   const long long slot = (long long)unit * a.n_cells + cell;
-  det::detect_cell(level_ptr(a.g, a.all, base, 0), a.g.w[0], a.g.h[0], a.g.pitch[0], a.cg, cell,
+  det::detect_cell<NT>(level_ptr(a.g, a.all, base, 0), a.g.w[0], a.g.h[0], a.g.pitch[0], a.cg, cell,
                    a.mask ? a.mask + (long long)unit * a.mask_stride : nullptr,
                    a.cand + slot * a.cg.k, a.cand_count + slot, smem, red);
 }
@@ -273,7 +274,15 @@ __global__ void __launch_bounds__(net::TILE_THREADS, 1) frame_initnet_kernel(
   }
 }
 
-__global__ void frame_track_kernel(const __grid_constant__ MultiK2 mm) {
+// Occupancy hint of the tracking launch (blocks of up to 512 threads, this
+// many per SM: 2 caps registers at 64 per thread); unset = compiler's choice.
+#ifdef VIO_TRACK_MIN_BLOCKS
+#define VIO_TRACK_BOUNDS __launch_bounds__(512, VIO_TRACK_MIN_BLOCKS)
+#else
+#define VIO_TRACK_BOUNDS
+#endif
+
+__global__ void VIO_TRACK_BOUNDS frame_track_kernel(const __grid_constant__ MultiK2 mm) {
   const long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (w >= mm.block_end[mm.n - 1]) return;
@@ -686,15 +695,20 @@ K1Args front_args(const vio_params& p, const Geom& g, const Batch& all, int det_
   return a;
 }
 
-cudaError_t launch_k1(const MultiK1& mm, int smem, cudaStream_t s) {
+template <int NT>
+cudaError_t launch_k1_nt(const MultiK1& mm, int smem, cudaStream_t s) {
   if (smem > 48 * 1024) {
     const cudaError_t e = cudaFuncSetAttribute(
-        frame_front_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        frame_front_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
   }
   const long long blocks = mm.block_end[mm.n - 1];
-  if (blocks > 0) frame_front_kernel<<<(unsigned)blocks, K1_THREADS, smem, s>>>(mm);
+  if (blocks > 0) frame_front_kernel<NT><<<(unsigned)blocks, NT, smem, s>>>(mm);
   return cudaGetLastError();
+}
+
+cudaError_t launch_k1(const MultiK1& mm, int smem, int threads, cudaStream_t s) {
+  return threads == 128 ? launch_k1_nt<128>(mm, smem, s) : launch_k1_nt<256>(mm, smem, s);
 }
 
 }  // namespace
@@ -717,7 +731,7 @@ cudaError_t launch_front(const vio_params& p, const Geom& g, const Batch& all, i
   mm.a[0] = front_args(p, g, all, det_step, mask, mask_stride, cand, cand_count, 0, 0);
   const long long units = (all.n + det_step - 1) / det_step;
   mm.block_end[0] = units * mm.a[0].blocks_per_unit;
-  return launch_k1(mm, frame_front_smem(g, p, 0, 0), s);
+  return launch_k1(mm, frame_front_smem(g, p, 0, 0), 128, s);
 }
 
 cudaError_t launch_frames(const FrameLaunch* fl, int n_groups, const FrameTune& tune,
@@ -748,7 +762,7 @@ cudaError_t launch_frames(const FrameLaunch* fl, int n_groups, const FrameTune& 
     const int sm = frame_front_smem(f.g, f.p, tune.pyr_tile_shift, tune.pyr_first);
     smem1 = sm > smem1 ? sm : smem1;
   }
-  cudaError_t e = launch_k1(m1, smem1, s);
+  cudaError_t e = launch_k1(m1, smem1, tune.k1_threads, s);
   if (e != cudaSuccess) return e;
   // levels beyond the first pass
   mark(1);

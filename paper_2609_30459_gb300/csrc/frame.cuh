@@ -13,6 +13,7 @@ struct FrameTune {
   int pyr_tile_shift;  // deepest-level pyramid tile side = (32 >> (m-1)) << shift
   int stereo_after;    // 1: stereo-match only the selected keypoints, after selection
   int pyr_first;       // pyramid levels of K1's fused pass (1..4; 0 = as many as fit)
+  int k1_threads;      // CTA size of K1: 128 or 256
 };
 
 struct FrameLaunch {

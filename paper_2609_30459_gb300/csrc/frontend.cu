@@ -283,7 +283,7 @@ extern "C" vio_status vio_frontend_step(vio_frontend* fe, const uint8_t* d_frame
     f.net_out = fe->net_out;
     f.trk_learned = fe->trk_learned;
   }
-  const FrameTune tune{128, 0, 0, 0};
+  const FrameTune tune{128, 0, 0, 0, 256};
   if (launch_frames(&f, 1, tune, s, fe->timing ? ev.data() : nullptr) != cudaSuccess)
     return VIO_ERR_CUDA;
   if (fe->timing) fe->ev_rec.push_back(ev);
@@ -295,6 +295,38 @@ extern "C" vio_status vio_frontend_step(vio_frontend* fe, const uint8_t* d_frame
   fe->prev_pitch = pitch;
   fe->prev_stride = frame_stride;
   ++fe->steps;
+  return VIO_OK;
+}
+
+extern "C" vio_status vio_frontend_step_host(vio_frontend* fe, const uint8_t* h_frames,
+                                             uint8_t* d_frames, int32_t pitch,
+                                             int64_t frame_stride, float* h_track_xy,
+                                             int32_t* h_track_id, int32_t* h_track_count,
+                                             float* h_new_xy, int32_t* h_new_count,
+                                             void* stream) {
+  if (!fe || !h_frames || !d_frames || !h_track_xy || !h_track_id || !h_track_count ||
+      !h_new_xy || !h_new_count || pitch < fe->w || frame_stride < (int64_t)pitch * fe->h)
+    return VIO_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t in_bytes = (size_t)2 * fe->n_streams * frame_stride;
+  if (cudaMemcpyAsync(d_frames, h_frames, in_bytes, cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return VIO_ERR_CUDA;
+  const vio_status st = vio_frontend_step(fe, d_frames, pitch, frame_stride, stream);
+  if (st != VIO_OK) return st;
+  vio_frontend_view v;
+  vio_frontend_get_view(fe, &v);
+  const size_t nl = (size_t)2 * fe->n_streams, cap = fe->capacity;
+  if (cudaMemcpyAsync(h_track_xy, v.d_track_xy, nl * cap * 8, cudaMemcpyDeviceToHost, s) !=
+          cudaSuccess ||
+      cudaMemcpyAsync(h_track_id, v.d_track_id, nl * cap * 4, cudaMemcpyDeviceToHost, s) !=
+          cudaSuccess ||
+      cudaMemcpyAsync(h_track_count, v.d_track_count, nl * 4, cudaMemcpyDeviceToHost, s) !=
+          cudaSuccess ||
+      cudaMemcpyAsync(h_new_xy, v.d_new_xy, (size_t)fe->n_streams * cap * 8,
+                      cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaMemcpyAsync(h_new_count, v.d_new_count, (size_t)fe->n_streams * 4,
+                      cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    return VIO_ERR_CUDA;
   return VIO_OK;
 }
 

@@ -17,7 +17,7 @@ namespace vio {
 namespace pyr {
 
 constexpr int kMaxPass = 4;   // levels one pass computes
-constexpr int kThreads = 256;
+constexpr int kThreads = 128;   // CTA size of the standalone pyramid launches
 
 // deepest-level tile side of a pass of m levels: 32, 16, 8, 4, scaled by
 // 2^shift (shift in -1..1), at least 1

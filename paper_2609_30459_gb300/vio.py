@@ -59,7 +59,8 @@ class StreamGroup(ctypes.Structure):
 
 class BatchTune(ctypes.Structure):
     _fields_ = [("k2_threads", ctypes.c_int32), ("pyr_tile_shift", ctypes.c_int32),
-                ("stereo_after_select", ctypes.c_int32), ("pyr_first_levels", ctypes.c_int32)]
+                ("stereo_after_select", ctypes.c_int32), ("pyr_first_levels", ctypes.c_int32),
+                ("k1_threads", ctypes.c_int32)]
 
 
 class InitNetCfg(ctypes.Structure):
@@ -130,6 +131,12 @@ _SIGS = {
     "vio_frontend_step": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
                                            ctypes.c_int64, ctypes.c_void_p]),
     "vio_frontend_reset": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p]),
+    "vio_frontend_step_host": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p,
+                                                ctypes.c_void_p, ctypes.c_int32,
+                                                ctypes.c_int64, ctypes.c_void_p,
+                                                ctypes.c_void_p, ctypes.c_void_p,
+                                                ctypes.c_void_p, ctypes.c_void_p,
+                                                ctypes.c_void_p]),
     "vio_frontend_get_view": (ctypes.c_int32, [ctypes.c_void_p, ctypes.POINTER(FrontendView)]),
     "vio_frontend_launches_per_step": (ctypes.c_int32, [ctypes.c_void_p]),
     "vio_frontend_set_timing": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32]),
@@ -559,6 +566,27 @@ class Frontend:
     def reset(self, stream=None):
         _check(load().vio_frontend_reset(self.handle, _stream(stream)), "vio_frontend_reset")
 
+    def host_outputs(self):
+        """Pinned host buffers for step_host: dict of xy, id, count, new_xy, new_count."""
+        ns, cap = self.n_streams, self.capacity
+        pin = dict(dtype=torch.float32, pin_memory=True)
+        return {"xy": torch.empty((ns, 2, cap, 2), **pin),
+                "id": torch.empty((ns, 2, cap), dtype=torch.int32, pin_memory=True),
+                "count": torch.empty((ns, 2), dtype=torch.int32, pin_memory=True),
+                "new_xy": torch.empty((ns, cap, 2), **pin),
+                "new_count": torch.empty((ns,), dtype=torch.int32, pin_memory=True)}
+
+    def step_host(self, h_frames: torch.Tensor, d_frames: torch.Tensor, out: dict, stream=None):
+        """One step from pinned host frames (streams, 2, h, pitch) through the
+        device buffer d_frames (same shape, kept alive until the next step) to
+        the pinned buffers of host_outputs(); asynchronous on the stream."""
+        pitch = h_frames.shape[-1]
+        _check(load().vio_frontend_step_host(self.handle, _hptr(h_frames), _ptr(d_frames), pitch,
+                                             h_frames.shape[2] * pitch, _hptr(out["xy"]),
+                                             _hptr(out["id"]), _hptr(out["count"]),
+                                             _hptr(out["new_xy"]), _hptr(out["new_count"]),
+                                             _stream(stream)), "vio_frontend_step_host")
+
     def launches_per_step(self) -> int:
         return int(load().vio_frontend_launches_per_step(self.handle))
 
@@ -689,15 +717,17 @@ class Batch:
         _check(load().vio_batch_set_graph(self.handle, 1 if enable else 0), "set_graph")
 
     def set_tune(self, k2_threads: int, pyr_tile_shift: int, stereo_after_select: int = 0,
-                 pyr_first_levels: int = 0):
-        t = BatchTune(k2_threads, pyr_tile_shift, stereo_after_select, pyr_first_levels)
+                 pyr_first_levels: int = 0, k1_threads: int = 256):
+        t = BatchTune(k2_threads, pyr_tile_shift, stereo_after_select, pyr_first_levels,
+                      k1_threads)
         _check(load().vio_batch_set_tune(self.handle, ctypes.byref(t)), "set_tune")
 
-    def get_tune(self) -> tuple[int, int, int, int]:
-        """(k2_threads, pyr_tile_shift, stereo_after_select, pyr_first_levels)."""
+    def get_tune(self) -> tuple[int, int, int, int, int]:
+        """(k2_threads, pyr_tile_shift, stereo_after_select, pyr_first_levels, k1_threads)."""
         t = BatchTune()
         _check(load().vio_batch_get_tune(self.handle, ctypes.byref(t)), "get_tune")
-        return t.k2_threads, t.pyr_tile_shift, t.stereo_after_select, t.pyr_first_levels
+        return (t.k2_threads, t.pyr_tile_shift, t.stereo_after_select, t.pyr_first_levels,
+                t.k1_threads)
 
     def autotune(self, reps: int = 3, stream=None) -> float:
         ms = ctypes.c_float()
@@ -856,8 +886,9 @@ class Server:
                "vio_server_set_initnet")
 
     def set_tune(self, k2_threads: int, pyr_tile_shift: int, stereo_after_select: int = 0,
-                 pyr_first_levels: int = 0):
-        t = BatchTune(k2_threads, pyr_tile_shift, stereo_after_select, pyr_first_levels)
+                 pyr_first_levels: int = 0, k1_threads: int = 256):
+        t = BatchTune(k2_threads, pyr_tile_shift, stereo_after_select, pyr_first_levels,
+                      k1_threads)
         _check(load().vio_server_set_tune(self.handle, ctypes.byref(t)), "vio_server_set_tune")
 
     def open(self, cls: int):

@@ -313,3 +313,31 @@ def test_frontend_initnet_off_is_plain():
         assert torch.equal(va["track_xy"][0, c, :n], vb["track_xy"][0, c, :n])
         assert torch.equal(va["track_id"][0, c, :n], vb["track_id"][0, c, :n])
     assert b.launches_per_step() == 3
+
+
+def test_step_host_equals_step_and_view():
+    """vio_frontend_step_host (copy in, step, copy out) gives the lists of
+    vio_frontend_step read through the view."""
+    w, h, L = 376, 240, 3
+    seq = synth.make_sequence(5011, 4, w, h, 1, max_motion=5.0, tex_size=1024)
+    p = vio.default_params(n_levels=L, cell_w=47, cell_h=40)
+    cap = 2 * (w // 47) * (h // 40)
+    a, b = vio.Frontend(p, w, h, 1, cap), vio.Frontend(p, w, h, 1, cap)
+    host = torch.from_numpy(seq.frames).view(4, 1, 2, h, w).pin_memory()
+    dev = torch.from_numpy(seq.frames).cuda().view(4, 1, 2, h, w)
+    slots = torch.empty((2, 1, 2, h, w), dtype=torch.uint8, device="cuda")
+    out = b.host_outputs()
+    for t in range(4):
+        a.step(dev[t])
+        b.step_host(host[t], slots[t % 2], out)
+    torch.cuda.synchronize()
+    va = a.view()
+    assert torch.equal(va["track_count"].cpu(), out["count"])
+    for c in range(2):
+        n = int(out["count"][0, c])
+        assert n > 0
+        assert torch.equal(va["track_xy"][0, c, :n].cpu(), out["xy"][0, c, :n])
+        assert torch.equal(va["track_id"][0, c, :n].cpu(), out["id"][0, c, :n])
+    nn = int(out["new_count"][0])
+    assert int(va["new_count"][0]) == nn
+    assert torch.equal(va["new_xy"][0, :nn].cpu(), out["new_xy"][0, :nn])
