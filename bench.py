@@ -52,7 +52,18 @@ TRACK_TRAFFIC_BYTES = 1928448
 
 
 def seq_seed(rank: int) -> int:
+    """Each rank runs its own sequence (weak scaling: streams are independent)."""
     return 1000 * 2 + rank
+
+
+def max_over_ranks(value: float, dist=None, device: str = "cpu") -> float:
+    """The largest of every rank's value (the job's time is its slowest rank's)."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
 
 
 def load_peaks():
@@ -486,9 +497,7 @@ def main():
 
     t_max = total_s
     if world > 1:
-        tt = torch.tensor([total_s], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max = float(tt.item())
+        t_max = max_over_ranks(total_s, dist, "cuda")
     value = world * args.steps / t_max
 
     # dominant kernel: the stage with the largest share of the step
@@ -565,9 +574,7 @@ def main():
         torch.cuda.synchronize()
         lat = run(min(args.steps, 1000), True)
         if world > 1:
-            tt = torch.tensor([e2e_s], device="cuda")
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            e2e_s = float(tt.item())
+            e2e_s = max_over_ranks(e2e_s, dist, "cuda")
         bo = sum(t.numel() * t.element_size() for t in outs[0].values())
         e2e = {"value": world * args.steps / e2e_s, "unit": UNIT,
                "h2d_bytes_per_step": 2 * H * W, "d2h_bytes_per_step": bo,

@@ -281,3 +281,30 @@ def test_training_reduces_loss():
     err = torch.linalg.norm(out[:, :2] - F, dim=1)
     zero = torch.linalg.norm(F, dim=1)
     assert err.median().item() < 0.3 * zero.median().item(), (err.median(), zero.median())
+
+
+def test_checkpoint_save_load_resume(tmp_path):
+    """Weights, Adam moments, step count and gate configuration survive a
+    save/load; training resumes from the loaded state."""
+    flat = onet.flatten(he_params(8)).astype(np.float32)
+    net = vio.InitNet(flat, 2, 3, 1, 0.4)
+    x = _inputs(64, 3)
+    xb = torch.from_numpy(bits_of(x.reshape(64, -1)).view(np.int16)).to(DEV)
+    flows = torch.from_numpy(np.random.default_rng(2).normal(0, 4, (64, 2)).astype(np.float32)).to(DEV)
+    from paper_2609_30459_gb300 import initnet_train
+    initnet_train.train(net, xb, flows, epochs=1, batch=32, lr=1e-3, log=lambda *_: None)
+    path = tmp_path / "ck.npz"
+    net.save(path, label_radius=3.0)
+    back = vio.InitNet.load(path)
+    assert back.step == net.step == 2
+    assert torch.equal(back.master, net.master) and torch.equal(back.m, net.m)
+    assert torch.equal(back.v, net.v)
+    assert (back.cfg.level_a, back.cfg.level_b, back.cfg.start_level) == (2, 3, 1)
+    assert back.cfg.min_conf == pytest.approx(0.4)
+    assert torch.equal(back.packed, net.packed)
+    # one more epoch from either copy: the same update (up to the order of
+    # the floating-point gradient sums)
+    initnet_train.train(net, xb, flows, epochs=1, batch=32, lr=1e-3, log=lambda *_: None)
+    initnet_train.train(back, xb, flows, epochs=1, batch=32, lr=1e-3, log=lambda *_: None)
+    assert back.step == net.step == 4
+    assert torch.allclose(back.master, net.master, rtol=1e-4, atol=1e-6)

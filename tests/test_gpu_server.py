@@ -155,3 +155,35 @@ def test_admission_waits_for_a_slot():
             first_b = done[done["session"] == b]["t_launch"].min()
             assert first_b >= last_a
     srv.close_server()
+
+
+def test_server_rejects_bad_requests_on_the_host():
+    """Failures are reported on the host before anything is enqueued: an
+    unknown session, a frame after the session's last, a missing frame; a
+    waiting session that closes leaves the queue without running."""
+    cl = _classes(2)
+    slots, _ = vio.server_plan(_classes(1), 1 << 34)
+    _, bytes1 = vio.server_plan(_classes(1), 1 << 34)
+    srv = vio.Server(cl, bytes1 + 1024)               # one slot per class
+    a, adm_a = srv.open(0)
+    b, adm_b = srv.open(0)
+    assert adm_a and not adm_b
+    fr = _frames(0, 0)
+    with pytest.raises(vio.VioError):
+        srv.submit(12345, fr[0], vio.server_now(), 0)
+    srv.submit(a, fr[0], vio.server_now(), 0, vio.SERVER_LAST)
+    with pytest.raises(vio.VioError):
+        srv.submit(a, fr[1], vio.server_now(), 1)      # after its last frame
+    srv.close(b)                                        # waiting: leaves the queue
+    with pytest.raises(vio.VioError):
+        srv.submit(b, fr[0], vio.server_now(), 0)
+    done = []
+    t0 = vio.server_now()
+    while len(done) < 1 and vio.server_now() - t0 < 30:
+        srv.poll()
+        done.extend(srv.take())
+    assert len(done) == 1 and done[0]["session"] == a and done[0]["status"] == 0
+    # the slot is free again: a new session is admitted at once
+    c, adm_c = srv.open(0)
+    assert adm_c
+    srv.close_server()
