@@ -410,6 +410,30 @@ def profile_frontend(w, h, n_streams, learned, steps=3):
     return 0
 
 
+def autotune_frontend(torch, fe, frames, n=40):
+    import itertools
+    frames5 = frames.view(N_FRAMES, 1, 2, H, W)
+    best, best_t = None, None
+    for k2, shift, first, k1 in itertools.product((64, 128, 256), (-1, 0, 1), (0, 1, 2),
+                                                  (128, 256)):
+        fe.set_tune(k2, shift, first, k1)
+        fe.reset()
+        fe.run(frames5[:3])
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fe.run(frames5[3:3 + n])
+        e1.record()
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1)
+        if best_t is None or t < best_t:
+            best, best_t = (k2, shift, first, k1), t
+    fe.set_tune(*best)
+    fe.reset()
+    torch.cuda.synchronize()
+    return {"k2_threads": best[0], "pyr_tile_shift": best[1], "pyr_first_levels": best[2],
+            "k1_threads": best[3], "ms_per_step": best_t / n}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -454,6 +478,10 @@ def main():
                                 k_per_cell=K_CELL)
     fe = vio.Frontend(params, W, H, 1, CAPACITY)
     stream = torch.cuda.current_stream()
+
+    # launch shapes of the frontend (results do not depend on them): every
+    # combination timed over 40 frames, the fastest kept
+    fe_tune = autotune_frontend(torch, fe, frames)
 
     # warm-up on the last frames of the sequence, then a fresh start at frame 0
     for i in range(args.warmup):
@@ -625,6 +653,7 @@ def main():
                                    "stereo_candidates": stereo_in / args.steps},
             "gpu_launches": args.steps * fe.launches_per_step(),
             "e2e": e2e, "roofline": roofline, "pyramid_detect_roofline": pd,
+            "frontend_tune": fe_tune,
             "batched_16_streams": batched, "serving_32_streams": serve,
             "cpu_baseline": cpu, "clocks": clk.summary(),
             "host_wall_s": wall,

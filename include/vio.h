@@ -321,6 +321,13 @@ vio_status vio_frontend_get_view(vio_frontend* fe, vio_frontend_view* out);
 /* Number of kernels one vio_frontend_step enqueues (for launch accounting). */
 int32_t vio_frontend_launches_per_step(const vio_frontend* fe);
 
+/* Launch shapes of the frontend's steps (vio_batch_tune, defined with the
+ * batch below; stereo_after_select must be 0: the frontend keeps the
+ * speculative order). Default {128, 0, 0, 0, 256}. Results do not depend on
+ * it. A host call between steps. */
+struct vio_batch_tune_s;
+vio_status vio_frontend_set_tune(vio_frontend* fe, const struct vio_batch_tune_s* t);
+
 /* Stage timing (the paper's per-stage GPU timestamps, Sec. IV-B, Fig. 5).
  * While enabled, every step records CUDA events on its stream at the stage
  * boundaries: 0 pyramid levels 1-4 and the per-cell detection candidates
@@ -404,7 +411,7 @@ typedef struct {
  * 0 = up to 4; the rest follow in further pyramid launches: fewer levels per
  * pass recompute less of the halo of level 0), and the CTA size of that
  * launch (128 or 256). Every setting gives the same lists bit for bit. */
-typedef struct {
+typedef struct vio_batch_tune_s {
   int32_t k2_threads;
   int32_t pyr_tile_shift;
   int32_t stereo_after_select;

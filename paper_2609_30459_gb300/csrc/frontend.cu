@@ -44,6 +44,7 @@ struct vio_frontend {
   uint8_t* trk_learned;       // per slot: tracked from the proposal
   const void* net;            // packed initializer weights (null: off)
   vio_initnet_cfg net_cfg;
+  vio::FrameTune tune;        // launch shapes (the frontend keeps the frame order)
   // host state
   int cur_list;
   int cur_pyr;
@@ -155,6 +156,7 @@ extern "C" vio_status vio_frontend_create(vio_frontend** out, const vio_params* 
   fe->trk_learned = (uint8_t*)ptrs[8];
   fe->net = nullptr;
   fe->net_cfg = vio_initnet_cfg{};
+  fe->tune = vio::FrameTune{128, 0, 0, 0, 256};
   fe->trk_xy = (float*)ptrs[9];
   fe->trk_status = (uint8_t*)ptrs[10];
   fe->cand = (unsigned long long*)ptrs[11];
@@ -212,7 +214,21 @@ extern "C" int32_t vio_frontend_launches_per_step(const vio_frontend* fe) {
   vio_pyr_layout L;
   if (vio_pyr_layout_make(fe->w, fe->h, fe->p.n_levels, fe->w, &L) != VIO_OK) return 0;
   const vio::Geom g = vio::make_geom(L);
-  return vio::frame_launches(&g, 1, fe->net != nullptr, false, 0);
+  return vio::frame_launches(&g, 1, fe->net != nullptr, false, fe->tune.pyr_first);
+}
+
+extern "C" vio_status vio_frontend_set_tune(vio_frontend* fe, const vio_batch_tune* t) {
+  if (!fe || !t) return VIO_ERR_INVALID_ARG;
+  if (t->k2_threads != 64 && t->k2_threads != 128 && t->k2_threads != 256 &&
+      t->k2_threads != 512)
+    return VIO_ERR_INVALID_ARG;
+  if (t->pyr_tile_shift < -1 || t->pyr_tile_shift > 1 || t->stereo_after_select != 0 ||
+      t->pyr_first_levels < 0 || t->pyr_first_levels > 4 ||
+      (t->k1_threads != 128 && t->k1_threads != 256))
+    return VIO_ERR_INVALID_ARG;
+  fe->tune = vio::FrameTune{t->k2_threads, t->pyr_tile_shift, 0, t->pyr_first_levels,
+                            t->k1_threads};
+  return VIO_OK;
 }
 
 extern "C" vio_status vio_frontend_set_initnet(vio_frontend* fe, const void* d_packed,
@@ -283,8 +299,7 @@ extern "C" vio_status vio_frontend_step(vio_frontend* fe, const uint8_t* d_frame
     f.net_out = fe->net_out;
     f.trk_learned = fe->trk_learned;
   }
-  const FrameTune tune{128, 0, 0, 0, 256};
-  if (launch_frames(&f, 1, tune, s, fe->timing ? ev.data() : nullptr) != cudaSuccess)
+  if (launch_frames(&f, 1, fe->tune, s, fe->timing ? ev.data() : nullptr) != cudaSuccess)
     return VIO_ERR_CUDA;
   if (fe->timing) fe->ev_rec.push_back(ev);
 

@@ -139,6 +139,7 @@ _SIGS = {
                                                 ctypes.c_void_p]),
     "vio_frontend_get_view": (ctypes.c_int32, [ctypes.c_void_p, ctypes.POINTER(FrontendView)]),
     "vio_frontend_launches_per_step": (ctypes.c_int32, [ctypes.c_void_p]),
+    "vio_frontend_set_tune": (ctypes.c_int32, [ctypes.c_void_p, ctypes.POINTER(BatchTune)]),
     "vio_frontend_set_timing": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32]),
     "vio_frontend_read_timing": (ctypes.c_int32, [ctypes.c_void_p,
                                                   ctypes.POINTER(ctypes.c_double),
@@ -589,6 +590,12 @@ class Frontend:
 
     def launches_per_step(self) -> int:
         return int(load().vio_frontend_launches_per_step(self.handle))
+
+    def set_tune(self, k2_threads: int = 128, pyr_tile_shift: int = 0,
+                 pyr_first_levels: int = 0, k1_threads: int = 256):
+        t = BatchTune(k2_threads, pyr_tile_shift, 0, pyr_first_levels, k1_threads)
+        _check(load().vio_frontend_set_tune(self.handle, ctypes.byref(t)),
+               "vio_frontend_set_tune")
 
     def set_initnet(self, net: "InitNet | None"):
         """Turn the learned start of temporal tracking on (net) or off (None).

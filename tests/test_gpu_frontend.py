@@ -341,3 +341,23 @@ def test_step_host_equals_step_and_view():
     nn = int(out["new_count"][0])
     assert int(va["new_count"][0]) == nn
     assert torch.equal(va["new_xy"][0, :nn].cpu(), out["new_xy"][0, :nn])
+
+
+@pytest.mark.parametrize("tune", [(64, -1, 1, 128), (256, 1, 2, 256)])
+def test_frontend_tune_does_not_change_results(tune):
+    w, h, L = 376, 240, 4
+    seq = synth.make_sequence(5013, 5, w, h, 1, max_motion=6.0, tex_size=1024)
+    p = vio.default_params(n_levels=L, cell_w=47, cell_h=40)
+    cap = 2 * (w // 47) * (h // 40)
+    frames = torch.from_numpy(seq.frames).cuda().view(5, 1, 2, h, w)
+    a, b = vio.Frontend(p, w, h, 1, cap), vio.Frontend(p, w, h, 1, cap)
+    b.set_tune(*tune)
+    a.run(frames)
+    b.run(frames)
+    torch.cuda.synchronize()
+    va, vb = a.view(), b.view()
+    assert torch.equal(va["track_count"], vb["track_count"])
+    for c in range(2):
+        n = int(va["track_count"][0, c])
+        assert torch.equal(va["track_xy"][0, c, :n], vb["track_xy"][0, c, :n])
+        assert torch.equal(va["track_id"][0, c, :n], vb["track_id"][0, c, :n])
