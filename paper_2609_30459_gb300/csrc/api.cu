@@ -201,9 +201,7 @@ extern "C" vio_status vio_pyramid_detect(vio_ctx* ctx, const vio_pyr_layout* lay
   const vio::Batch b = vio::make_batch(*batch);
   cudaStream_t s = (cudaStream_t)stream;
   cudaError_t e = vio::launch_front(ctx->p, g, b, 1, d_mask, mask_stride, ctx->d_cand,
-                                    ctx->d_cand_count, s);
-  if (e == cudaSuccess && layout->n_levels > 1 + vio::pyr::kMaxPass)
-    e = vio::launch_pyramid_from(g, b, vio::pyr::kMaxPass, ctx->p.round_mode, s);
+                                    ctx->d_cand_count, s);   // all levels
   if (e == cudaSuccess) {
     const int n_cells = (layout->w[0] / ctx->p.cell_w) * (layout->h[0] / ctx->p.cell_h);
     e = vio::launch_select(ctx->d_cand, ctx->d_cand_count, d_occupancy, n_cells,

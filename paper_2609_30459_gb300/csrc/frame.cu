@@ -723,15 +723,31 @@ int frame_front_smem(const Geom& g, const vio_params& p, int tile_shift, int pyr
   return smem;
 }
 
+// Launch shapes of vio_pyramid_detect (batches of images: throughput).
+#ifndef VIO_FRONT_FIRST
+#define VIO_FRONT_FIRST 2
+#endif
+#ifndef VIO_FRONT_SHIFT
+#define VIO_FRONT_SHIFT 0
+#endif
+#ifndef VIO_FRONT_THREADS
+#define VIO_FRONT_THREADS 128
+#endif
+
 cudaError_t launch_front(const vio_params& p, const Geom& g, const Batch& all, int det_step,
                          const uint8_t* mask, long long mask_stride, unsigned long long* cand,
                          int32_t* cand_count, cudaStream_t s) {
   MultiK1 mm{};
   mm.n = 1;
-  mm.a[0] = front_args(p, g, all, det_step, mask, mask_stride, cand, cand_count, 0, 0);
+  mm.a[0] = front_args(p, g, all, det_step, mask, mask_stride, cand, cand_count,
+                       VIO_FRONT_SHIFT, VIO_FRONT_FIRST);
   const long long units = (all.n + det_step - 1) / det_step;
   mm.block_end[0] = units * mm.a[0].blocks_per_unit;
-  return launch_k1(mm, frame_front_smem(g, p, 0, 0), 128, s);
+  const cudaError_t e = launch_k1(mm, frame_front_smem(g, p, VIO_FRONT_SHIFT, VIO_FRONT_FIRST),
+                                  VIO_FRONT_THREADS, s);
+  if (e != cudaSuccess) return e;
+  const int m1 = first_levels(g, VIO_FRONT_FIRST);
+  return g.n_levels > 1 + m1 ? launch_pyramid_from(g, all, m1, p.round_mode, s) : cudaSuccess;
 }
 
 cudaError_t launch_frames(const FrameLaunch* fl, int n_groups, const FrameTune& tune,
