@@ -593,9 +593,10 @@ vio_status vio_initnet_forward(const void* d_packed, const uint16_t* d_x, int32_
                                float* d_out, void* stream);
 
 /* Adds grad_scale * (sum over the n samples d_index[0..n-1] (NULL = 0..n-1)
- * of dL_i/dparams), labels at radius label_radius px (> 0), to d_grad (VIO_INITNET_N_PARAMS floats, gradient with
- * respect to the master parameters through the BF16 packing taken as the
- * identity) and the sum of the n losses to *d_loss. Targets: d_flow[2*j] =
+ * of dL_i/dparams), labels at radius label_radius px (> 0), to d_grad
+ * (VIO_INITNET_N_PARAMS floats, gradient with respect to the master
+ * parameters through the BF16 packing taken as the identity) and the sum of
+ * the n losses to *d_loss. Targets: d_flow[2*j] =
  * (fx, fy) of sample j in level-0 pixels. The caller zeroes d_grad and
  * d_loss first. The forward pass is that of vio_initnet_forward. */
 vio_status vio_initnet_train_step(const void* d_packed, const uint16_t* d_x,

@@ -39,9 +39,10 @@ __global__ void __launch_bounds__(det::kThreads) detect_cells_kernel(DetectArgs 
   __shared__ unsigned long long red[det::kThreads / 32];
   const int cell = blockIdx.x, img = blockIdx.y;
   const long long slot = (long long)img * a.n_cells + cell;
-  det::detect_cell<det::kThreads>(level_ptr(a.g, a.b, img, 0), a.g.w[0], a.g.h[0], a.g.pitch[0], a.cg, cell,
-                   a.mask ? a.mask + (long long)img * a.mask_stride : nullptr,
-                   a.cand + slot * a.cg.k, a.cand_count + slot, smem, red);
+  det::detect_cell<det::kThreads>(level_ptr(a.g, a.b, img, 0), a.g.w[0], a.g.h[0],
+                                  a.g.pitch[0], a.cg, cell,
+                                  a.mask ? a.mask + (long long)img * a.mask_stride : nullptr,
+                                  a.cand + slot * a.cg.k, a.cand_count + slot, smem, red);
 }
 
 constexpr int SEL_THREADS = 512;

@@ -403,7 +403,8 @@ struct MultiK3 {
 
 // One CTA per stream. Each thread owns a contiguous run of list slots (then
 // of cells), so each phase is one block-wide scan of packed counts.
-__global__ void __launch_bounds__(K3_THREADS) frame_finalize_kernel(const __grid_constant__ MultiK3 mm) {
+__global__ void __launch_bounds__(K3_THREADS)
+    frame_finalize_kernel(const __grid_constant__ MultiK3 mm) {
   extern __shared__ int occ_s[];
   __shared__ int ws32[K3_THREADS / 32];
   __shared__ unsigned long long ws64[K3_THREADS / 32];
@@ -610,7 +611,8 @@ __global__ void frame_stereo_kernel(const __grid_constant__ MultiK2 mm) {
 
 // Appends the successful matches of a stream's selected keypoints, in their
 // order, to camera 1 after its surviving tracks, and ends the stream's step.
-__global__ void __launch_bounds__(K3_THREADS) frame_append_kernel(const __grid_constant__ MultiK3 mm) {
+__global__ void __launch_bounds__(K3_THREADS)
+    frame_append_kernel(const __grid_constant__ MultiK3 mm) {
   __shared__ int ws32[K3_THREADS / 32];
   long long start;
   const int gi = group_of(mm, blockIdx.x, start);

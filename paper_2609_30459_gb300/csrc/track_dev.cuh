@@ -424,8 +424,8 @@ __device__ __forceinline__ int track_dir(const Geom& g, const Batch& src, int sr
 }
 
 // Forward track with the optional backward pass and distance check, both
-// over levels top..0, from warp (ix, iy, ith) if has_init, else from p. Returns the status; tf/thf hold the forward result when
-// it exists.
+// over levels top..0, from warp (ix, iy, ith) if has_init, else from p.
+// Returns the status; tf/thf hold the forward result when it exists.
 __device__ __forceinline__ int track_fb(const Geom& g, const Batch& src, int src_img,
                                         const Batch& dst, int dst_img, float px, float py,
                                         bool has_init, float ix, float iy, float ith,
