@@ -434,6 +434,31 @@ def autotune_frontend(torch, fe, frames, n=40):
             "k1_threads": best[3], "ms_per_step": best_t / n}
 
 
+def profile_detect(n=64, reps=3):
+    """Standalone detection (vio_detect_grid) of a device-resident batch of n
+    images of the headline sequence, pyramids built first, for kernel
+    profiles."""
+    import torch
+    from paper_2609_30459_gb300 import synth, vio
+    vio.load(build=True)
+    seq = synth.make_sequence(2000, 4, W, H, 1, max_motion=MOTION, tex_size=2048)
+    imgs = torch.from_numpy(seq.frames.reshape(-1, H, W)).cuda().repeat(n // 8, 1, 1)
+    imgs = imgs.contiguous()
+    p = vio.default_params(n_levels=LEVELS, cell_w=CELL_W, cell_h=CELL_H, k_per_cell=K_CELL)
+    ctx = vio.Context(p, W, H, n)
+    pyr = vio.Pyramids(imgs, LEVELS)
+    ctx.pyramid_build(pyr)
+    cap = (W // CELL_W) * (H // CELL_H) * K_CELL
+    kp = torch.empty((n, cap, 2), dtype=torch.float32, device="cuda")
+    sc = torch.empty((n, cap), dtype=torch.int16, device="cuda")
+    cnt = torch.empty(n, dtype=torch.int32, device="cuda")
+    for _ in range(reps):
+        ctx.detect_grid(pyr, pyr.batch(), kp, sc, cnt, cap)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_detect": n, "keypoints": int(cnt.sum().item())}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -449,7 +474,11 @@ def main():
     ap.add_argument("--profile-frontend", nargs=3, type=int, metavar=("W", "H", "STREAMS"),
                     help="only run 3 frontend steps of this size (for kernel profiles)")
     ap.add_argument("--learned", action="store_true", help="with --profile-frontend")
+    ap.add_argument("--profile-detect", action="store_true",
+                    help="only run 3 detections of a 64-image batch (for kernel profiles)")
     args = ap.parse_args()
+    if args.profile_detect:
+        return profile_detect()
     if args.profile_frontend:
         return profile_frontend(*args.profile_frontend, args.learned)
     if args.warmup < 3:
