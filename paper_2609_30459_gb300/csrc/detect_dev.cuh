@@ -151,7 +151,8 @@ __device__ __forceinline__ void detect_cell(const uint8_t* __restrict__ src, int
                                             unsigned long long* __restrict__ out_keys,
                                             int32_t* __restrict__ out_count, uint8_t* smem,
                                             unsigned long long* red64) {
-  __shared__ int q_count, c_count;
+  __shared__ int c_count;
+  __shared__ int wtot[NT / 32];
   unsigned* red = reinterpret_cast<unsigned*>(red64);
   const int cy = cell / cg.gx, cx = cell - cy * cg.gx;
   const int x0 = cx * cg.cw, y0 = cy * cg.ch;
@@ -166,10 +167,7 @@ __device__ __forceinline__ void detect_cell(const uint8_t* __restrict__ src, int
   uint16_t* queue = reinterpret_cast<uint16_t*>(smem + S.queue);
   unsigned long long* keys = reinterpret_cast<unsigned long long*>(smem + S.keys);
   pyr::stage_rect(src, W, H, P, rx0, x0 + cg.cw + kHalo, ry0, y0 + cg.ch + kHalo, reg, RS);
-  if (threadIdx.x == 0) {
-    q_count = 0;
-    c_count = 0;
-  }
+  if (threadIdx.x == 0) c_count = 0;
   __syncthreads();
 
   const int T = cg.tmin;
@@ -205,22 +203,32 @@ __device__ __forceinline__ void detect_cell(const uint8_t* __restrict__ src, int
     int t_prev = 256;
     int t = max((int)umax - 24, tmin1);
     int q_done = 0;            // queue entries evaluated in earlier rounds
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (;;) {
-      // pass B: queue the pixels whose bound falls in [t, t_prev)
+      // pass B: queue the pixels whose bound falls in [t, t_prev): count per
+      // warp, offsets from the warp totals, then write (no atomics)
+      int wcount = 0;
+      for (int base = 0; base < NR; base += NT) {
+        const int i = base + threadIdx.x;
+        const bool take = i < NR && ubm[i] >= t && ubm[i] < t_prev;
+        wcount += __popc(__ballot_sync(0xffffffffu, take));
+      }
+      if (lane == 0) wtot[warp] = wcount;
+      __syncthreads();
+      int off = q_done, q_end = q_done;
+#pragma unroll 4
+      for (int w2 = 0; w2 < NT / 32; ++w2) {
+        off += w2 < warp ? wtot[w2] : 0;
+        q_end += wtot[w2];
+      }
       for (int base = 0; base < NR; base += NT) {
         const int i = base + threadIdx.x;
         const bool take = i < NR && ubm[i] >= t && ubm[i] < t_prev;
         const unsigned ball = __ballot_sync(0xffffffffu, take);
-        if (ball) {
-          const int lane = threadIdx.x & 31;
-          int slot = 0;
-          if (lane == __ffs(ball) - 1) slot = atomicAdd(&q_count, __popc(ball));
-          slot = __shfl_sync(0xffffffffu, slot, __ffs(ball) - 1);
-          if (take) queue[slot + __popc(ball & ((1u << lane) - 1))] = (uint16_t)i;
-        }
+        if (take) queue[off + __popc(ball & ((1u << lane) - 1))] = (uint16_t)i;
+        off += __popc(ball);
       }
       __syncthreads();
-      const int q_end = q_count;
       // exact scores of the newly queued pixels
       for (int e = q_done + threadIdx.x; e < q_end; e += NT) {
         const int i = queue[e];
