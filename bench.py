@@ -244,6 +244,70 @@ def cfg4_frames():
     return [out[k * CFG4_STREAMS:(k + 1) * CFG4_STREAMS] for k in range(len(CFG4_CLASSES))]
 
 
+def frontend_config_run(torch, vio, name, w, h, n_streams, levels, cw, ch, n_frames, motion,
+                        seed0, steps, params_kw=None):
+    """One frontend configuration over its own synthetic sequences (each
+    stream its own seed), autotuned launch shapes, device-resident frames
+    played forward and back: stereo frames/s (n_streams frames per step) and
+    per-step latency from a separate per-stage-events pass."""
+    import numpy as np
+    from paper_2609_30459_gb300 import synth
+    seqs = [synth.make_sequence(seed0 + i, n_frames, w, h, 1, max_motion=motion,
+                                tex_size=2048).frames for i in range(n_streams)]
+    frames = torch.from_numpy(np.stack(seqs, 1)).cuda()      # (F, streams, 2, h, w)
+    order = list(range(n_frames)) + list(range(n_frames - 2, 0, -1))
+    p = vio.default_params(n_levels=levels, cell_w=cw, cell_h=ch, **(params_kw or {}))
+    cap = 2 * (w // cw) * (h // ch) * p.k_per_cell
+    fe = vio.Frontend(p, w, h, n_streams, cap)
+    best = None
+    for k2 in (64, 128, 256):
+        for first in (0, 2):
+            for k1 in (128, 256):
+                fe.set_tune(k2, 0, first, k1)
+                fe.reset()
+                for t in range(3):
+                    fe.step(frames[order[t]])
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                for t in range(3, 23):
+                    fe.step(frames[order[t % len(order)]])
+                e1.record()
+                torch.cuda.synchronize()
+                if best is None or e0.elapsed_time(e1) < best[0]:
+                    best = (e0.elapsed_time(e1), (k2, 0, first, k1))
+    fe.set_tune(*best[1])
+    fe.reset()
+    for t in range(3):
+        fe.step(frames[order[t]])
+    torch.cuda.synchronize()
+    _, steps0 = fe.read_stats()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for t in range(steps):
+        fe.step(frames[order[(t + 3) % len(order)]])
+    e1.record()
+    torch.cuda.synchronize()
+    total_s = e0.elapsed_time(e1) / 1000.0
+    stats, _ = fe.read_stats()
+    idx = [(steps0 + k) % vio.STATS_RING for k in range(steps)]
+    st = stats[idx].astype(np.int64)
+    fe.set_timing(True)
+    fe.reset()
+    for t in range(min(steps, 200)):
+        fe.step(frames[order[t % len(order)]])
+    stage_ms, n_t, step_ms = fe.read_timing(max_steps=200)
+    fe.close()
+    return {"config": name, "w": w, "h": h, "stereo_streams": n_streams, "levels": levels,
+            "cells": f"{w // cw}x{h // ch} of {cw}x{ch} px", "frames": n_frames,
+            "max_motion_px": motion, "params": params_kw or {},
+            "frames_per_s": n_streams * steps / total_s, "ms_per_step": 1000 * total_s / steps,
+            "p50_ms": percentile(step_ms, 50), "p99_ms": percentile(step_ms, 99),
+            "tracked_keypoints_per_s": float(st[..., 0].sum() + st[..., 1].sum()) / total_s,
+            "survived_per_step": float(st[..., 2].sum() + st[..., 3].sum()) / steps,
+            "tune": dict(zip(("k2_threads", "pyr_tile_shift", "pyr_first_levels", "k1_threads"),
+                             best[1]))}
+
+
 def batched_compare(torch, vio, steps, warmup, net):
     """The 16-stream batch, plain and with the learned initializer: each step
     uploads one frame per stream into its slot (device to device, frames
@@ -651,6 +715,20 @@ def main():
 
     pd = pyramid_detect_roofline(torch, vio, frames, peaks, peak_src) if rank == 0 else None
 
+    # config 3 (4 cameras = two stereo pairs at 1920x1080, motion up to 40 px)
+    # and the paper's lite parameters on 752x480 sequences like the headline's
+    extra_cfgs = None
+    if rank == 0 and not args.no_batched:
+        extra_cfgs = [
+            frontend_config_run(torch, vio, "cfg3 high-pixel: 4 cameras (2 stereo pairs) "
+                                "1920x1080, 100 frames, motion up to 40 px, 5 levels, 40x25 "
+                                "cells (1000 keypoints/image)", 1920, 1080, 2, 5, 48, 43, 100,
+                                40.0, 3000, args.batched_steps),
+            frontend_config_run(torch, vio, "lite parameters (Sec. IV-D): minimum FAST threshold "
+                                "20, 82-px cells, 3 Gauss-Newton iterations; 752x480, 4 levels",
+                                752, 480, 1, 4, 82, 82, 100, 15.0, 2000, args.batched_steps,
+                                params_kw={"gn_iters": 3, "thresholds": (40, 20)})]
+
     batched = None
     if rank == 0 and not args.no_batched:
         from paper_2609_30459_gb300 import initnet_train
@@ -693,6 +771,7 @@ def main():
             "e2e": e2e, "roofline": roofline, "pyramid_detect_roofline": pd,
             "frontend_tune": fe_tune,
             "batched_16_streams": batched, "serving_32_streams": serve,
+            "other_configs": extra_cfgs,
             "cpu_baseline": cpu, "clocks": clk.summary(),
             "host_wall_s": wall,
         }
