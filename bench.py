@@ -373,8 +373,10 @@ def batched_compare(torch, vio, steps, warmup, net):
             survived += int(a[..., 2].sum() + a[..., 3].sum())
             learned += int(a[..., 7].sum())
         k2, shift, after, first, k1 = b.get_tune()
+        slow = sorted(range(steps), key=lambda i: -lat[i])[:5]
         res[mode] = {"frames_per_s": n_streams * steps / total_s,
                      "p50_ms": percentile(lat, 50), "p99_ms": percentile(lat, 99),
+                     "slowest_steps": [[i, round(lat[i], 4)] for i in slow],
                      "tracked_keypoints_per_s": tracked / total_s,
                      "survived_per_step": survived / steps,
                      "learned_share_of_survivors": learned / max(survived, 1),
@@ -498,6 +500,35 @@ def autotune_frontend(torch, fe, frames, n=40):
             "k1_threads": best[3], "ms_per_step": best_t / n}
 
 
+def profile_batch(mode, steps=18):
+    """The 16-stream batch (cfg 4) stepped `steps` times without graphs, plain
+    or with the learned start, so that every kernel is its own launch (for
+    launch lists)."""
+    import torch
+    from paper_2609_30459_gb300 import initnet_train, vio
+    vio.load(build=True)
+    seqs = cfg4_frames()
+    dev = [[torch.from_numpy(f).cuda() for f in cls] for cls in seqs]
+    groups = []
+    for (w, h, cw, ch) in CFG4_CLASSES:
+        p = vio.default_params(n_levels=CFG4_LEVELS, cell_w=cw, cell_h=ch)
+        groups.append((p, w, h, CFG4_STREAMS, 2 * (w // cw) * (h // ch)))
+    order = list(range(CFG4_FRAMES)) + list(range(CFG4_FRAMES - 2, 0, -1))
+    b = vio.Batch(groups)
+    if mode == "learned":
+        b.set_initnet(vio.InitNet.load(initnet_train.DEFAULT_WEIGHTS))
+    b.set_tune(128, 0, 1, 2, 128)
+    for t in range(steps):
+        for g in range(len(CFG4_CLASSES)):
+            for i in range(CFG4_STREAMS):
+                b.next_frame(g, i).copy_(dev[g][i][order[t % len(order)]])
+        b.step(None)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_batch": mode, "steps": steps}))
+    b.close()
+    return 0
+
+
 def profile_detect(n=64, reps=3):
     """Standalone detection (vio_detect_grid) of a device-resident batch of n
     images of the headline sequence, pyramids built first, for kernel
@@ -538,11 +569,17 @@ def main():
     ap.add_argument("--profile-frontend", nargs=3, type=int, metavar=("W", "H", "STREAMS"),
                     help="only run 3 frontend steps of this size (for kernel profiles)")
     ap.add_argument("--learned", action="store_true", help="with --profile-frontend")
-    ap.add_argument("--profile-detect", action="store_true",
-                    help="only run 3 detections of a 64-image batch (for kernel profiles)")
+    ap.add_argument("--profile-batch", choices=["plain", "learned"],
+                    help="only step the 16-stream batch 18 times without graphs (launch lists)")
+    ap.add_argument("--profile-detect", type=int, nargs="?", const=64, default=None,
+                    metavar="IMAGES",
+                    help="only run 3 detections of a batch of IMAGES images (default 64; "
+                         "for kernel profiles)")
     args = ap.parse_args()
     if args.profile_detect:
-        return profile_detect()
+        return profile_detect(args.profile_detect)
+    if args.profile_batch:
+        return profile_batch(args.profile_batch)
     if args.profile_frontend:
         return profile_frontend(*args.profile_frontend, args.learned)
     if args.warmup < 3:

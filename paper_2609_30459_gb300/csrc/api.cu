@@ -114,7 +114,7 @@ extern "C" vio_status vio_ctx_create(vio_ctx** out, const vio_params* p, int32_t
                                      int32_t max_h, int32_t max_images) {
   if (!out || !params_ok(p) || max_w < 1 || max_h < 1 || max_images < 1)
     return VIO_ERR_INVALID_ARG;
-  if (vio::det::cell_smem_bytes(p->cell_w, p->cell_h) > vio::det::kMaxCellSmem)
+  if (!vio::det::detect_fits(p->cell_w, p->cell_h, p->k_per_cell))
     return VIO_ERR_UNSUPPORTED;
   *out = nullptr;
   vio_ctx* c = new (std::nothrow) vio_ctx();

@@ -96,7 +96,7 @@ vio_status group_sizes(const vio_stream_group& sp, vio_pyr_layout& layout, int& 
   n_cells = (int)(gx * gy);
   if ((long long)n_cells * sp.params.k_per_cell > sp.capacity ||
       (long long)n_cells * 4 > 200 * 1024 ||
-      vio::det::cell_smem_bytes(sp.params.cell_w, sp.params.cell_h) > vio::det::kMaxCellSmem)
+      !vio::det::detect_fits(sp.params.cell_w, sp.params.cell_h, sp.params.k_per_cell))
     return VIO_ERR_UNSUPPORTED;
   const size_t ns = sp.n_streams, cap = sp.capacity, nc = n_cells;
   const size_t kk = sp.params.k_per_cell, fb = (size_t)sp.w * sp.h;
@@ -322,10 +322,15 @@ extern "C" vio_status vio_batch_step(vio_batch* b, const int32_t* active, void* 
   if (!b) return VIO_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   const int slot = b->mask_slot;
-  // the pinned buffer of this slot was last read by the step two calls ago
-  if (cudaEventSynchronize(b->graph_done[slot]) != cudaSuccess) return VIO_ERR_CUDA;
   int32_t* hm = b->h_active[slot];
-  for (int i = 0; i < b->total_streams; ++i) hm[i] = active ? (active[i] != 0) : 1;
+  bool same = true;   // an unchanged mask needs no rewrite, so no wait
+  for (int i = 0; i < b->total_streams && same; ++i)
+    same = hm[i] == (active ? (active[i] != 0) : 1);
+  if (!same) {
+    // the pinned buffer of this slot was last read by the step two calls ago
+    if (cudaEventSynchronize(b->graph_done[slot]) != cudaSuccess) return VIO_ERR_CUDA;
+    for (int i = 0; i < b->total_streams; ++i) hm[i] = active ? (active[i] != 0) : 1;
+  }
   cudaError_t e;
   if (b->use_graph) {
     if (!s) return VIO_ERR_INVALID_ARG;   // the legacy default stream cannot be captured

@@ -38,6 +38,20 @@ struct Split {
   }
 };
 
+// SMs of the current device (cached per device; 152 if the query fails).
+inline int sm_count() {
+  static int n[32] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 32) return 152;
+  if (n[dev] == 0) {
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v < 1)
+      v = 152;
+    n[dev] = v;
+  }
+  return n[dev];
+}
+
 inline Geom make_geom(const vio_pyr_layout& L) {
   Geom g{};
   g.n_levels = L.n_levels;

@@ -1,5 +1,6 @@
 // Grid-cell FAST-9 detection entry points (Sec. III-D): the per-pixel score
-// map, the per-cell candidate kernel (device code in detect_dev.cuh) and the
+// map, the per-cell candidate kernel (one warp per cell, blocks of cells per
+// CTA; device code in detect_dev.cuh) and the
 // per-image selection that applies k_eff = k - occupancy and writes the
 // survivors in cell raster order with a block-wide prefix sum.
 #include "detect_dev.cuh"
@@ -31,18 +32,17 @@ struct DetectArgs {
   unsigned long long* cand;   // [img][cell][k]
   int32_t* cand_count;        // [img][cell]
   det::CellGeom cg;
-  int n_cells;
+  int n_cells, gy;
 };
 
-__global__ void __launch_bounds__(det::kThreads) detect_cells_kernel(DetectArgs a) {
+__global__ void __launch_bounds__(det::kThreads, 6) detect_cells_kernel(DetectArgs a) {
   extern __shared__ __align__(16) uint8_t smem[];
-  __shared__ unsigned long long red[det::kThreads / 32];
-  const int cell = blockIdx.x, img = blockIdx.y;
-  const long long slot = (long long)img * a.n_cells + cell;
-  det::detect_cell<det::kThreads>(level_ptr(a.g, a.b, img, 0), a.g.w[0], a.g.h[0],
-                                  a.g.pitch[0], a.cg, cell,
-                                  a.mask ? a.mask + (long long)img * a.mask_stride : nullptr,
-                                  a.cand + slot * a.cg.k, a.cand_count + slot, smem, red);
+  const int img = blockIdx.y;
+  det::detect_block(
+      level_ptr(a.g, a.b, img, 0), a.g.w[0], a.g.h[0], a.g.pitch[0], a.cg, a.gy, blockIdx.x,
+      a.mask ? a.mask + (long long)img * a.mask_stride : nullptr,
+      a.cand + (long long)img * a.n_cells * a.cg.k, a.cand_count + (long long)img * a.n_cells,
+      smem);
 }
 
 constexpr int SEL_THREADS = 512;
@@ -129,17 +129,27 @@ cudaError_t launch_detect(const vio_params& p, const Geom& g, const Batch& b,
   a.cand = cand;
   a.cand_count = cand_count;
   a.cg = det::CellGeom{p.cell_w, p.cell_h, g.w[0] / p.cell_w, p.k_per_cell,
-                       p.thresholds[p.n_thresholds - 1], p.detect_border};
-  const int n_cells = a.cg.gx * (g.h[0] / p.cell_h);
+                       p.thresholds[p.n_thresholds - 1], p.detect_border, 1, 1, 1};
+  a.gy = g.h[0] / p.cell_h;
+  const int n_cells = a.cg.gx * a.gy;
   a.n_cells = n_cells;
+  const int smem = det::detect_setup(a.cg, det::kThreads, (long long)n_cells * b.n, sm_count());
+  if (smem < 0) return cudaErrorInvalidValue;
   if (n_cells > 0) {
-    const int smem = det::cell_smem_bytes(p.cell_w, p.cell_h);
+    static bool carveout = false;   // as much shared memory as the SM has: more CTAs
+    if (!carveout) {
+      const cudaError_t e = cudaFuncSetAttribute(detect_cells_kernel,
+                                                 cudaFuncAttributePreferredSharedMemoryCarveout,
+                                                 (int)cudaSharedmemCarveoutMaxShared);
+      if (e != cudaSuccess) return e;
+      carveout = true;
+    }
     if (smem > 48 * 1024) {
       cudaError_t e = cudaFuncSetAttribute(detect_cells_kernel,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
       if (e != cudaSuccess) return e;
     }
-    dim3 grid(n_cells, b.n);
+    dim3 grid(det::detect_blocks(a.cg.gx, a.gy, a.cg.bcx, a.cg.bcy), b.n);
     detect_cells_kernel<<<grid, det::kThreads, smem, s>>>(a);
   }
   return launch_select(cand, cand_count, occ, n_cells, a.cg.k, g.w[0], kp, score, count,

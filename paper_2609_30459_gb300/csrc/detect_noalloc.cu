@@ -86,7 +86,7 @@ extern "C" vio_status vio_detect_grid_noalloc(const vio_params* p, const vio_pyr
     return VIO_ERR_INVALID_ARG;
   if (d_mask && batch->n_images > 1 && mask_stride < (int64_t)layout->w[0] * layout->h[0])
     return VIO_ERR_INVALID_ARG;
-  if (vio::det::cell_smem_bytes(p->cell_w, p->cell_h) > vio::det::kMaxCellSmem)
+  if (!vio::det::detect_fits(p->cell_w, p->cell_h, p->k_per_cell))
     return VIO_ERR_UNSUPPORTED;
   const long long cells = (long long)(layout->w[0] / p->cell_w) * (layout->h[0] / p->cell_h);
   // the fixed scratch bounds the work of one call

@@ -55,9 +55,9 @@ struct K1Args {
   int m, T;            // levels and deepest-level tile of the first pyramid pass (m = 0: none)
   int ntx, nty;        // tiles of the first pass
   int det_step;        // 1: every image is a unit; 2: stream units (camera 0 detects)
-  int blocks_per_unit; // det_step * tiles + cells
+  int blocks_per_unit; // det_step * tiles + detection blocks
   det::CellGeom cg;
-  int n_cells;
+  int n_cells, gy;
   const uint8_t* mask; // per detected image, or null
   long long mask_stride;
   unsigned long long* cand;
@@ -90,9 +90,8 @@ __device__ __forceinline__ int group_of(const M& mm, long long i, long long& sta
 // NT threads per CTA: 256 for a single frame's latency, 128 for throughput
 // over many streams (a tunable of the batch).
 template <int NT>
-__global__ void __launch_bounds__(NT) frame_front_kernel(const __grid_constant__ MultiK1 mm) {
+__global__ void __launch_bounds__(NT, 768 / NT) frame_front_kernel(const __grid_constant__ MultiK1 mm) {
   extern __shared__ __align__(16) uint8_t smem[];
-  __shared__ unsigned long long red[NT / 32];
   long long start;
   const int gi = group_of(mm, blockIdx.x, start);
   const K1Args& a = mm.a[gi];
@@ -115,11 +114,11 @@ __global__ void __launch_bounds__(NT) frame_front_kernel(const __grid_constant__
       pyr::pyramid_pass(a.g, a.all, img, 0, a.m, a.T, tx, ty, a.ntx, a.nty, a.round_mode, smem);
     return;
   }
-  const int cell = rem - n_pyr;
-  const long long slot = (long long)unit * a.n_cells + cell;
-  det::detect_cell<NT>(level_ptr(a.g, a.all, base, 0), a.g.w[0], a.g.h[0], a.g.pitch[0], a.cg, cell,
-                   a.mask ? a.mask + (long long)unit * a.mask_stride : nullptr,
-                   a.cand + slot * a.cg.k, a.cand_count + slot, smem, red);
+  det::detect_block(level_ptr(a.g, a.all, base, 0), a.g.w[0], a.g.h[0], a.g.pitch[0], a.cg,
+                        a.gy, rem - n_pyr,
+                        a.mask ? a.mask + (long long)unit * a.mask_stride : nullptr,
+                        a.cand + (long long)unit * a.n_cells * a.cg.k,
+                        a.cand_count + (long long)unit * a.n_cells, smem);
 }
 
 struct MultiK2 {
@@ -675,7 +674,8 @@ int first_levels(const Geom& g, int pyr_first) {
 
 K1Args front_args(const vio_params& p, const Geom& g, const Batch& all, int det_step,
                   const uint8_t* mask, long long mask_stride, unsigned long long* cand,
-                  int32_t* cand_count, int tile_shift, int pyr_first) {
+                  int32_t* cand_count, int tile_shift, int pyr_first, int threads,
+                  long long launch_cells) {
   const int gx = g.w[0] / p.cell_w, gy = g.h[0] / p.cell_h;
   K1Args a{};
   a.g = g;
@@ -686,9 +686,12 @@ K1Args front_args(const vio_params& p, const Geom& g, const Batch& all, int det_
   if (a.m > 0) pyr::pass_tiles(g.w, g.h, 0, a.m, a.T, a.ntx, a.nty);
   a.det_step = det_step;
   a.n_cells = gx * gy;
-  a.blocks_per_unit = (a.m > 0 ? det_step * a.ntx * a.nty : 0) + a.n_cells;
+  a.gy = gy;
   a.cg = det::CellGeom{p.cell_w, p.cell_h, gx, p.k_per_cell, p.thresholds[p.n_thresholds - 1],
-                       p.detect_border};
+                       p.detect_border, 1, 1, 1};
+  det::detect_setup(a.cg, threads, launch_cells, sm_count());
+  a.blocks_per_unit = (a.m > 0 ? det_step * a.ntx * a.nty : 0) +
+                      (a.n_cells > 0 ? det::detect_blocks(gx, gy, a.cg.bcx, a.cg.bcy) : 0);
   a.mask = mask;
   a.mask_stride = mask_stride;
   a.cand = cand;
@@ -699,6 +702,14 @@ K1Args front_args(const vio_params& p, const Geom& g, const Batch& all, int det_
 
 template <int NT>
 cudaError_t launch_k1_nt(const MultiK1& mm, int smem, cudaStream_t s) {
+  static bool carveout = false;   // as much shared memory as the SM has: more CTAs
+  if (!carveout) {
+    const cudaError_t e = cudaFuncSetAttribute(frame_front_kernel<NT>,
+                                               cudaFuncAttributePreferredSharedMemoryCarveout,
+                                               (int)cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess) return e;
+    carveout = true;
+  }
   if (smem > 48 * 1024) {
     const cudaError_t e = cudaFuncSetAttribute(
         frame_front_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -715,8 +726,10 @@ cudaError_t launch_k1(const MultiK1& mm, int smem, int threads, cudaStream_t s) 
 
 }  // namespace
 
-int frame_front_smem(const Geom& g, const vio_params& p, int tile_shift, int pyr_first) {
-  int smem = det::cell_smem_bytes(p.cell_w, p.cell_h);
+int frame_front_smem(const Geom& g, const vio_params& p, int tile_shift, int pyr_first,
+                     int threads, long long launch_cells) {
+  det::CellGeom cg{p.cell_w, p.cell_h, g.w[0] / p.cell_w, p.k_per_cell, 0, 0, 1, 1, 1};
+  int smem = det::detect_setup(cg, threads, launch_cells, sm_count());
   const int m = first_levels(g, pyr_first);
   if (m > 0) {
     const int ps = pyr::pass_smem_max(g.w, g.h, 0, m, pyr::top_tile(m, tile_shift));
@@ -741,12 +754,14 @@ cudaError_t launch_front(const vio_params& p, const Geom& g, const Batch& all, i
                          int32_t* cand_count, cudaStream_t s) {
   MultiK1 mm{};
   mm.n = 1;
-  mm.a[0] = front_args(p, g, all, det_step, mask, mask_stride, cand, cand_count,
-                       VIO_FRONT_SHIFT, VIO_FRONT_FIRST);
   const long long units = (all.n + det_step - 1) / det_step;
+  const long long cells = units * (g.w[0] / p.cell_w) * (g.h[0] / p.cell_h);
+  mm.a[0] = front_args(p, g, all, det_step, mask, mask_stride, cand, cand_count,
+                       VIO_FRONT_SHIFT, VIO_FRONT_FIRST, VIO_FRONT_THREADS, cells);
   mm.block_end[0] = units * mm.a[0].blocks_per_unit;
-  const cudaError_t e = launch_k1(mm, frame_front_smem(g, p, VIO_FRONT_SHIFT, VIO_FRONT_FIRST),
-                                  VIO_FRONT_THREADS, s);
+  const cudaError_t e = launch_k1(
+      mm, frame_front_smem(g, p, VIO_FRONT_SHIFT, VIO_FRONT_FIRST, VIO_FRONT_THREADS, cells),
+      VIO_FRONT_THREADS, s);
   if (e != cudaSuccess) return e;
   const int m1 = first_levels(g, VIO_FRONT_FIRST);
   return g.n_levels > 1 + m1 ? launch_pyramid_from(g, all, m1, p.round_mode, s) : cudaSuccess;
@@ -764,11 +779,14 @@ cudaError_t launch_frames(const FrameLaunch* fl, int n_groups, const FrameTune& 
   MultiK1 m1{};
   m1.n = n_groups;
   int smem1 = 0;
-  long long acc = 0;
+  long long acc = 0, cells = 0;
+  for (int i = 0; i < n_groups; ++i)
+    cells += (long long)fl[i].n_streams * (fl[i].g.w[0] / fl[i].p.cell_w) *
+             (fl[i].g.h[0] / fl[i].p.cell_h);
   for (int i = 0; i < n_groups; ++i) {
     const FrameLaunch& f = fl[i];
     K1Args a = front_args(f.p, f.g, f.cur, 2, nullptr, 0, f.cand, f.cand_count,
-                          tune.pyr_tile_shift, tune.pyr_first);
+                          tune.pyr_tile_shift, tune.pyr_first, tune.k1_threads, cells);
     a.slotted = f.slotted;
     a.n_streams = f.n_streams;
     a.parity = f.parity;
@@ -777,7 +795,8 @@ cudaError_t launch_frames(const FrameLaunch* fl, int n_groups, const FrameTune& 
     m1.a[i] = a;
     acc += (long long)f.n_streams * a.blocks_per_unit;
     m1.block_end[i] = acc;
-    const int sm = frame_front_smem(f.g, f.p, tune.pyr_tile_shift, tune.pyr_first);
+    const int sm = frame_front_smem(f.g, f.p, tune.pyr_tile_shift, tune.pyr_first,
+                                    tune.k1_threads, cells);
     smem1 = sm > smem1 ? sm : smem1;
   }
   cudaError_t e = launch_k1(m1, smem1, tune.k1_threads, s);

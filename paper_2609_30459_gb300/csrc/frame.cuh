@@ -111,7 +111,8 @@ inline bool initnet_cfg_ok(const vio_initnet_cfg* c, int n_levels, const void* p
     return false;
   return c->min_conf == c->min_conf;   // not NaN
 }
-int frame_front_smem(const Geom& g, const vio_params& p, int tile_shift, int pyr_first);
+int frame_front_smem(const Geom& g, const vio_params& p, int tile_shift, int pyr_first,
+                     int threads, long long launch_cells);
 // Fused pyramid and per-cell detection candidates of every det_step-th
 // image of `all` (one launch), then the pyramid levels beyond the fused pass.
 cudaError_t launch_front(const vio_params& p, const Geom& g, const Batch& all, int det_step,

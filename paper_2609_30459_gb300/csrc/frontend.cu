@@ -101,7 +101,7 @@ extern "C" vio_status vio_frontend_create(vio_frontend** out, const vio_params* 
   const long long n_cells = (long long)gx * gy;
   if (n_cells * p->k_per_cell > capacity) return VIO_ERR_INVALID_ARG;
   if (n_cells * 4 > 200 * 1024) return VIO_ERR_UNSUPPORTED;   // finalize's shared counters
-  if (vio::det::cell_smem_bytes(p->cell_w, p->cell_h) > vio::det::kMaxCellSmem)
+  if (!vio::det::detect_fits(p->cell_w, p->cell_h, p->k_per_cell))
     return VIO_ERR_UNSUPPORTED;
   vio_frontend* fe = new (std::nothrow) vio_frontend();
   if (!fe) return VIO_ERR_OOM;

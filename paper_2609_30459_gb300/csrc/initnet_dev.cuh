@@ -308,6 +308,11 @@ constexpr int T_OUT = T_H4 + TT * H4_SAMPLE * 2;             // TT x 3 floats
 constexpr int T_ZERO = T_OUT + TT * 3 * 4;
 constexpr int TILE_SMEM = T_ZERO + 16;
 static_assert(TILE_SMEM <= 227 * 1024, "tile shared memory");
+// ldmatrix rows: 16-byte aligned weight rows and layer bases
+static_assert((PK1 * 2) % 16 == 0 && (PK2 * 2) % 16 == 0 && (PK4 * 2) % 16 == 0 &&
+                  (PK5 * 2) % 16 == 0 && (SW2 * 2) % 16 == 0 && (SW3 * 2) % 16 == 0 &&
+                  (SW4 * 2) % 16 == 0 && (SW5 * 2) % 16 == 0 && T_W % 16 == 0,
+              "ldmatrix alignment");
 
 struct TileSmem {
   uint16_t* w;
@@ -379,6 +384,31 @@ __device__ __forceinline__ uint32_t lds32(const uint16_t* p) {
   return *reinterpret_cast<const uint32_t*>(p);
 }
 
+// B fragments of two n-tiles (rows n0 .. n0+15 of a weight matrix W[n][k]
+// with row stride PK, columns k0 .. k0+15) by one ldmatrix: b[0], b[1] for
+// n-tile n0, b[2], b[3] for n0 + 8. Rows are 16-byte aligned (PK * 2 and k0
+// * 2 multiples of 16).
+__device__ __forceinline__ void ldsm_b2(uint32_t (&b)[4], const uint16_t* W, int PK, int n0,
+                                        int k0, int lane) {
+  const int m = lane >> 3, row = lane & 7;
+  const uint16_t* p = W + (n0 + (m >> 1) * 8 + row) * PK + k0 + (m & 1) * 8;
+  const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(b[0]), "=r"(b[1]), "=r"(b[2]), "=r"(b[3])
+               : "r"(a));
+}
+
+// B fragment of one n-tile (rows n0 .. n0+7, columns k0 .. k0+15).
+__device__ __forceinline__ void ldsm_b1(uint32_t (&b)[2], const uint16_t* W, int PK, int n0,
+                                        int k0, int lane) {
+  const int m = (lane >> 3) & 1, row = lane & 7;
+  const uint16_t* p = W + (n0 + row) * PK + k0 + m * 8;
+  const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];\n"
+               : "=r"(b[0]), "=r"(b[1])
+               : "r"(a));
+}
+
 // Epilogue of one accumulator tile: bias, ReLU, BF16 pairs (n, n+1) stored as
 // one word at out_row[h] + n (the caller's per-row base).
 __device__ __forceinline__ void store_pairs(const float (&acc)[4], const float* bias, int n0,
@@ -418,9 +448,11 @@ __device__ __forceinline__ void tile_conv1(const TileSmem& S, int mt, int lane) 
         a[h + 2 * half] = tap < 9 ? lds32(S.x + base[h] + off) : 0u;
     }
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const uint16_t* wr = S.w + SW1 + (q * 8 + g) * PK1 + ks * 16 + 2 * t;
-      mma16816(acc[q], a, lds32(wr), lds32(wr + 8));
+    for (int q = 0; q < 4; q += 2) {
+      uint32_t b[4];
+      ldsm_b2(b, S.w + SW1, PK1, q * 8, ks * 16, lane);
+      mma16816(acc[q], a, b[0], b[1]);
+      mma16816(acc[q + 1], a, b[2], b[3]);
     }
   }
 #pragma unroll
@@ -450,9 +482,11 @@ __device__ __forceinline__ void tile_conv2(const TileSmem& S, int s, int lane) {
     a[2] = lds32(S.h1 + base[0] + off + 8);
     a[3] = lds32(S.h1 + base[1] + off + 8);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const uint16_t* wr = S.w + SW2 + (q * 8 + g) * PK2 + ks * 16 + 2 * t;
-      mma16816(acc[q], a, lds32(wr), lds32(wr + 8));
+    for (int q = 0; q < 4; q += 2) {
+      uint32_t b[4];
+      ldsm_b2(b, S.w + SW2, PK2, q * 8, ks * 16, lane);
+      mma16816(acc[q], a, b[0], b[1]);
+      mma16816(acc[q + 1], a, b[2], b[3]);
     }
   }
 #pragma unroll
@@ -480,8 +514,9 @@ __device__ __forceinline__ void tile_conv3(const TileSmem& S, int mt, int nt, in
     a[1] = lds32(S.x + base[1] + off);
     a[2] = lds32(S.x + base[0] + off + 8);
     a[3] = lds32(S.x + base[1] + off + 8);
-    const uint16_t* wr = S.w + SW3 + (nt * 8 + g) * PK3 + ks * 16 + 2 * t;
-    mma16816(acc, a, lds32(wr), lds32(wr + 8));
+    uint32_t b[2];
+    ldsm_b1(b, S.w + SW3, PK3, nt * 8, ks * 16, lane);
+    mma16816(acc, a, b[0], b[1]);
   }
 #pragma unroll
   for (int e = 0; e < 4; ++e) {
@@ -504,8 +539,9 @@ __device__ __forceinline__ void fc_ntile(const uint16_t* in, const uint16_t* W, 
     a[1] = lds32(in + (g + 8) * STRIDE + ks * 16 + 2 * t);
     a[2] = lds32(in + g * STRIDE + ks * 16 + 2 * t + 8);
     a[3] = lds32(in + (g + 8) * STRIDE + ks * 16 + 2 * t + 8);
-    const uint16_t* wr = W + (nt * 8 + g) * PK + ks * 16 + 2 * t;
-    mma16816(acc, a, lds32(wr), lds32(wr + 8));
+    uint32_t b[2];
+    ldsm_b1(b, W, PK, nt * 8, ks * 16, lane);
+    mma16816(acc, a, b[0], b[1]);
   }
 }
 
