@@ -309,10 +309,13 @@ def frontend_config_run(torch, vio, name, w, h, n_streams, levels, cw, ch, n_fra
 
 
 def batched_compare(torch, vio, steps, warmup, net):
-    """The 16-stream batch, plain and with the learned initializer: each step
-    uploads one frame per stream into its slot (device to device, frames
-    resident) and runs the batch's captured graph; per-step CUDA events give
-    the step latency (every frame of a step completes with it)."""
+    """The 16-stream batch, plain and with the learned initializer (trained
+    gate, tracking from the proposal over levels 1..0, and the same network
+    with the start at level 0): each step uploads one frame per stream into
+    its slot (device to device, frames resident) and runs the batch's captured
+    graph; per-step CUDA events give the step latency (every frame of a step
+    completes with it). Steady state: the streams run `warmup` + 8 steps
+    before the timed ones (no reset), as continuous streams do."""
     import numpy as np
     seqs = cfg4_frames()
     dev = [[torch.from_numpy(f).cuda() for f in cls] for cls in seqs]
@@ -324,15 +327,19 @@ def batched_compare(torch, vio, steps, warmup, net):
     F = CFG4_FRAMES
     order = list(range(F)) + list(range(F - 2, 0, -1))   # forward and back: motion stays smooth
     res = {"streams": n_streams, "classes": [f"{w}x{h}" for (w, h, _, _) in CFG4_CLASSES],
-           "levels": CFG4_LEVELS, "max_motion_px": CFG4_MOTION, "steps": steps}
-    for mode in ("plain", "learned"):
-        if mode == "learned" and net is None:
-            res[mode] = None
-            continue
+           "levels": CFG4_LEVELS, "max_motion_px": CFG4_MOTION, "steps": steps,
+           "timing": "steady state: warm-up steps, no reset before the timed steps"}
+    start0 = net.cfg.start_level if net is not None else None
+    modes = [("plain", None)]
+    if net is not None:
+        modes += [("learned", start0), ("learned_start0", 0)]
+    for mode, start in modes:
+        if net is not None:
+            net.configure(start_level=start if start is not None else start0)
         s = torch.cuda.Stream()
         with torch.cuda.stream(s):
             b = vio.Batch(groups)
-            if mode == "learned":
+            if start is not None:
                 b.set_initnet(net)
 
             def upload(t):
@@ -346,19 +353,17 @@ def batched_compare(torch, vio, steps, warmup, net):
                 b.step(None, stream=s)
             tune_ms = b.autotune(reps=2, stream=s)
             b.set_graph(True)
-            for t in range(warmup):
+            n_warm = warmup + 8
+            for t in range(n_warm):
                 upload(t)
                 b.step(None, stream=s)
             s.synchronize()
-            for g in range(len(CFG4_CLASSES)):
-                for i in range(CFG4_STREAMS):
-                    b.reset_stream(g, i, stream=s)
             _, steps0 = b.read_stats(0)
             evs = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
             s.synchronize()
             evs[0].record(s)
             for t in range(steps):
-                upload(t)
+                upload(n_warm + t)
                 b.step(None, stream=s)
                 evs[t + 1].record(s)
             s.synchronize()
@@ -381,23 +386,25 @@ def batched_compare(torch, vio, steps, warmup, net):
                      "survived_per_step": survived / steps,
                      "learned_share_of_survivors": learned / max(survived, 1),
                      "launches_per_step": b.launches_per_step(),
+                     "start_level": start, "min_conf": net.cfg.min_conf if start is not None
+                     else None,
                      "tune": {"k2_threads": k2, "pyr_tile_shift": shift,
                               "stereo_after_select": after, "pyr_first_levels": first,
                               "k1_threads": k1, "best_ms": tune_ms}}
         b.close()
-    if res.get("learned") and res.get("plain"):
-        res["learned_vs_plain_fps"] = (res["learned"]["frames_per_s"] /
-                                       res["plain"]["frames_per_s"])
-        res["learned_vs_plain_p99"] = res["learned"]["p99_ms"] / res["plain"]["p99_ms"]
     if net is not None:
+        net.configure(start_level=start0)
+        for mode in ("learned", "learned_start0"):
+            res[mode + "_vs_plain_fps"] = res[mode]["frames_per_s"] / res["plain"]["frames_per_s"]
+            res[mode + "_vs_plain_p99"] = res[mode]["p99_ms"] / res["plain"]["p99_ms"]
         from paper_2609_30459_gb300 import initnet_train
         flat = [f for cls in seqs for f in cls[:1]]          # one stream of each size
         g = initnet_train.gain_eval(net, flat, n_levels=CFG4_LEVELS, cell=32,
-                                    start_levels=(net.cfg.start_level,),
-                                    taus=(net.cfg.min_conf,))
-        key = f"start{net.cfg.start_level}_tau{net.cfg.min_conf}"
+                                    start_levels=(start0, 0), taus=(net.cfg.min_conf,))
         res["accuracy"] = {"sample": "one stream of each size, all frame pairs, 32x32 cells",
-                           "keypoints": g["n"], **g[key]}
+                           "keypoints": g["n"]}
+        for mode, sl in (("learned", start0), ("learned_start0", 0)):
+            res["accuracy"][mode] = g[f"start{sl}_tau{net.cfg.min_conf}"]
     return res
 
 
