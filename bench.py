@@ -377,7 +377,7 @@ def batched_compare(torch, vio, steps, warmup, net):
             tracked += int(a[..., 0].sum() + a[..., 1].sum())
             survived += int(a[..., 2].sum() + a[..., 3].sum())
             learned += int(a[..., 7].sum())
-        k2, shift, after, first, k1 = b.get_tune()
+        k2, shift, after, first, k1, dw = b.get_tune()
         slow = sorted(range(steps), key=lambda i: -lat[i])[:5]
         res[mode] = {"frames_per_s": n_streams * steps / total_s,
                      "p50_ms": percentile(lat, 50), "p99_ms": percentile(lat, 99),
@@ -390,7 +390,7 @@ def batched_compare(torch, vio, steps, warmup, net):
                      else None,
                      "tune": {"k2_threads": k2, "pyr_tile_shift": shift,
                               "stereo_after_select": after, "pyr_first_levels": first,
-                              "k1_threads": k1, "best_ms": tune_ms}}
+                              "k1_threads": k1, "det_warps": dw, "best_ms": tune_ms}}
         b.close()
     if net is not None:
         net.configure(start_level=start0)

@@ -409,14 +409,17 @@ typedef struct {
  * selected keypoints are matched, after selection, in two more launches),
  * the pyramid levels the fused pyramid+detection launch computes (1..4,
  * 0 = up to 4; the rest follow in further pyramid launches: fewer levels per
- * pass recompute less of the halo of level 0), and the CTA size of that
- * launch (128 or 256). Every setting gives the same lists bit for bit. */
+ * pass recompute less of the halo of level 0), the CTA size of that launch
+ * (128 or 256) and the warps that score one detection cell (1, 2, 4 or 8, at
+ * most CTA size / 32; 0 = chosen from the launch: one when its cells fill the
+ * GPU, more for few cells). Every setting gives the same lists bit for bit. */
 typedef struct vio_batch_tune_s {
   int32_t k2_threads;
   int32_t pyr_tile_shift;
   int32_t stereo_after_select;
   int32_t pyr_first_levels;
   int32_t k1_threads;
+  int32_t det_warps;
 } vio_batch_tune;
 
 vio_status vio_batch_create(vio_batch** out, const vio_stream_group* groups, int32_t n_groups);

@@ -375,8 +375,11 @@ extern "C" vio_status vio_batch_set_tune(vio_batch* b, const vio_batch_tune* t) 
   if (t->stereo_after_select != 0 && t->stereo_after_select != 1) return VIO_ERR_INVALID_ARG;
   if (t->pyr_first_levels < 0 || t->pyr_first_levels > 4) return VIO_ERR_INVALID_ARG;
   if (t->k1_threads != 128 && t->k1_threads != 256) return VIO_ERR_INVALID_ARG;
+  if (t->det_warps != 0 && t->det_warps != 1 && t->det_warps != 2 && t->det_warps != 4 &&
+      t->det_warps != 8)
+    return VIO_ERR_INVALID_ARG;
   b->tune = vio::FrameTune{t->k2_threads, t->pyr_tile_shift, t->stereo_after_select,
-                           t->pyr_first_levels, t->k1_threads};
+                           t->pyr_first_levels, t->k1_threads, t->det_warps};
   drop_graphs(b);
   return VIO_OK;
 }
@@ -388,6 +391,7 @@ extern "C" vio_status vio_batch_get_tune(vio_batch* b, vio_batch_tune* t) {
   t->stereo_after_select = b->tune.stereo_after;
   t->pyr_first_levels = b->tune.pyr_first;
   t->k1_threads = b->tune.k1_threads;
+  t->det_warps = b->tune.det_warps;
   return VIO_OK;
 }
 
@@ -431,7 +435,7 @@ extern "C" vio_status vio_batch_autotune(vio_batch* b, int32_t reps, void* strea
     const int ti = combo % 4, shift = (combo / 4) % 3 - 1, after = (combo / 12) % 2;
     const int first = firsts[(combo / 24) % 3], k1 = combo < 72 ? 256 : 128;
     {
-      b->tune = vio::FrameTune{threads[ti], shift, after, first, k1};
+      b->tune = vio::FrameTune{threads[ti], shift, after, first, k1, best_t.det_warps};
       float total = 0.f;
       for (int r = 0; r < reps; ++r) {
         reset_all(b, s);

@@ -38,11 +38,15 @@ struct DetectArgs {
 __global__ void __launch_bounds__(det::kThreads, 6) detect_cells_kernel(DetectArgs a) {
   extern __shared__ __align__(16) uint8_t smem[];
   const int img = blockIdx.y;
-  det::detect_block(
-      level_ptr(a.g, a.b, img, 0), a.g.w[0], a.g.h[0], a.g.pitch[0], a.cg, a.gy, blockIdx.x,
-      a.mask ? a.mask + (long long)img * a.mask_stride : nullptr,
-      a.cand + (long long)img * a.n_cells * a.cg.k, a.cand_count + (long long)img * a.n_cells,
-      smem);
+  const uint8_t* src = level_ptr(a.g, a.b, img, 0);
+  unsigned long long* cand = a.cand + (long long)img * a.n_cells * a.cg.k;
+  int32_t* count = a.cand_count + (long long)img * a.n_cells;
+  if (a.mask)
+    det::detect_block<true>(src, a.g.w[0], a.g.h[0], a.g.pitch[0], a.cg, a.gy, blockIdx.x,
+                            a.mask + (long long)img * a.mask_stride, cand, count, smem);
+  else
+    det::detect_block<false>(src, a.g.w[0], a.g.h[0], a.g.pitch[0], a.cg, a.gy, blockIdx.x,
+                             nullptr, cand, count, smem);
 }
 
 constexpr int SEL_THREADS = 512;
@@ -133,7 +137,8 @@ cudaError_t launch_detect(const vio_params& p, const Geom& g, const Batch& b,
   a.gy = g.h[0] / p.cell_h;
   const int n_cells = a.cg.gx * a.gy;
   a.n_cells = n_cells;
-  const int smem = det::detect_setup(a.cg, det::kThreads, (long long)n_cells * b.n, sm_count());
+  const int smem = det::detect_setup(
+      a.cg, det::kThreads, det::warps_per_cell((long long)n_cells * b.n, sm_count()));
   if (smem < 0) return cudaErrorInvalidValue;
   if (n_cells > 0) {
     static bool carveout = false;   // as much shared memory as the SM has: more CTAs

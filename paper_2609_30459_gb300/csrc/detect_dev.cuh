@@ -532,7 +532,8 @@ __device__ __forceinline__ void detect_cell(const uint8_t* __restrict__ st, int 
 
 // Detection CTA `blk` of an image: block blk (raster order over blocks of
 // bcx x bcy cells), g warps per cell. All threads call it; smem holds
-// block_smem(...).total bytes.
+// block_smem(...).total bytes. MASKED: the per-pixel mask is read (non-null).
+template <bool MASKED>
 __device__ __forceinline__ void detect_block(const uint8_t* __restrict__ src, int W, int H, int P,
                                              const CellGeom& cg, int gy, int blk,
                                              const uint8_t* __restrict__ mask,
@@ -554,19 +555,14 @@ __device__ __forceinline__ void detect_block(const uint8_t* __restrict__ src, in
   const int cx = c0x + wx, cy = c0y + wy, cell = cy * cg.gx + cx;
   uint8_t* csm = smem + S.stage_bytes + ci * S.per_cell;
   uint8_t* wsm = smem + S.stage_bytes + S.cells_bytes + warp * S.per_warp;
-  if (mask)
-    detect_cell<true>(smem, S.rs, (bx0 - 8) & ~15, by0 - kHalo, W, H, cg, cx, cy, gw, 1 + ci,
+  detect_cell<MASKED>(smem, S.rs, (bx0 - 8) & ~15, by0 - kHalo, W, H, cg, cx, cy, gw, 1 + ci,
                       mask, cand + (long long)cell * cg.k, cand_count + cell, csm, wsm, S);
-  else
-    detect_cell<false>(smem, S.rs, (bx0 - 8) & ~15, by0 - kHalo, W, H, cg, cx, cy, gw, 1 + ci,
-                       nullptr, cand + (long long)cell * cg.k, cand_count + cell, csm, wsm, S);
 }
 
-// Fills the launch shape of cg (bcx, bcy, g) for NT threads and a launch of
-// n_cells cells; returns the dynamic shared memory, or -1.
-inline int detect_setup(CellGeom& cg, int nt, long long n_cells, int n_sms) {
-  if (!pick_block(cg.cw, cg.ch, cg.k, nt, warps_per_cell(n_cells, n_sms), cg.bcx, cg.bcy, cg.g))
-    return -1;
+// Fills the launch shape of cg (bcx, bcy, g) for NT threads and g_want warps
+// per cell; returns the dynamic shared memory, or -1.
+inline int detect_setup(CellGeom& cg, int nt, int g_want) {
+  if (!pick_block(cg.cw, cg.ch, cg.k, nt, g_want, cg.bcx, cg.bcy, cg.g)) return -1;
   return block_smem(cg.cw, cg.ch, cg.k, cg.bcx, cg.bcy, cg.g).total;
 }
 

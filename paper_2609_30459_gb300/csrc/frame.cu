@@ -89,7 +89,7 @@ __device__ __forceinline__ int group_of(const M& mm, long long i, long long& sta
 // reading one image run together and its level 0 is read from DRAM about once.
 // NT threads per CTA: 256 for a single frame's latency, 128 for throughput
 // over many streams (a tunable of the batch).
-template <int NT>
+template <int NT, bool MASKED>
 __global__ void __launch_bounds__(NT, 768 / NT) frame_front_kernel(const __grid_constant__ MultiK1 mm) {
   extern __shared__ __align__(16) uint8_t smem[];
   long long start;
@@ -114,11 +114,11 @@ __global__ void __launch_bounds__(NT, 768 / NT) frame_front_kernel(const __grid_
       pyr::pyramid_pass(a.g, a.all, img, 0, a.m, a.T, tx, ty, a.ntx, a.nty, a.round_mode, smem);
     return;
   }
-  det::detect_block(level_ptr(a.g, a.all, base, 0), a.g.w[0], a.g.h[0], a.g.pitch[0], a.cg,
-                        a.gy, rem - n_pyr,
-                        a.mask ? a.mask + (long long)unit * a.mask_stride : nullptr,
-                        a.cand + (long long)unit * a.n_cells * a.cg.k,
-                        a.cand_count + (long long)unit * a.n_cells, smem);
+  det::detect_block<MASKED>(level_ptr(a.g, a.all, base, 0), a.g.w[0], a.g.h[0], a.g.pitch[0],
+                            a.cg, a.gy, rem - n_pyr,
+                            MASKED ? a.mask + (long long)unit * a.mask_stride : nullptr,
+                            a.cand + (long long)unit * a.n_cells * a.cg.k,
+                            a.cand_count + (long long)unit * a.n_cells, smem);
 }
 
 struct MultiK2 {
@@ -675,7 +675,7 @@ int first_levels(const Geom& g, int pyr_first) {
 K1Args front_args(const vio_params& p, const Geom& g, const Batch& all, int det_step,
                   const uint8_t* mask, long long mask_stride, unsigned long long* cand,
                   int32_t* cand_count, int tile_shift, int pyr_first, int threads,
-                  long long launch_cells) {
+                  int det_warps) {
   const int gx = g.w[0] / p.cell_w, gy = g.h[0] / p.cell_h;
   K1Args a{};
   a.g = g;
@@ -689,7 +689,7 @@ K1Args front_args(const vio_params& p, const Geom& g, const Batch& all, int det_
   a.gy = gy;
   a.cg = det::CellGeom{p.cell_w, p.cell_h, gx, p.k_per_cell, p.thresholds[p.n_thresholds - 1],
                        p.detect_border, 1, 1, 1};
-  det::detect_setup(a.cg, threads, launch_cells, sm_count());
+  det::detect_setup(a.cg, threads, det_warps);
   a.blocks_per_unit = (a.m > 0 ? det_step * a.ntx * a.nty : 0) +
                       (a.n_cells > 0 ? det::detect_blocks(gx, gy, a.cg.bcx, a.cg.bcy) : 0);
   a.mask = mask;
@@ -700,11 +700,11 @@ K1Args front_args(const vio_params& p, const Geom& g, const Batch& all, int det_
   return a;
 }
 
-template <int NT>
+template <int NT, bool MASKED>
 cudaError_t launch_k1_nt(const MultiK1& mm, int smem, cudaStream_t s) {
   static bool carveout = false;   // as much shared memory as the SM has: more CTAs
   if (!carveout) {
-    const cudaError_t e = cudaFuncSetAttribute(frame_front_kernel<NT>,
+    const cudaError_t e = cudaFuncSetAttribute(frame_front_kernel<NT, MASKED>,
                                                cudaFuncAttributePreferredSharedMemoryCarveout,
                                                (int)cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return e;
@@ -712,24 +712,31 @@ cudaError_t launch_k1_nt(const MultiK1& mm, int smem, cudaStream_t s) {
   }
   if (smem > 48 * 1024) {
     const cudaError_t e = cudaFuncSetAttribute(
-        frame_front_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        frame_front_kernel<NT, MASKED>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
   }
   const long long blocks = mm.block_end[mm.n - 1];
-  if (blocks > 0) frame_front_kernel<NT><<<(unsigned)blocks, NT, smem, s>>>(mm);
+  if (blocks > 0) frame_front_kernel<NT, MASKED><<<(unsigned)blocks, NT, smem, s>>>(mm);
   return cudaGetLastError();
 }
 
+// MASKED when any group of the launch has a per-pixel detection mask.
 cudaError_t launch_k1(const MultiK1& mm, int smem, int threads, cudaStream_t s) {
-  return threads == 128 ? launch_k1_nt<128>(mm, smem, s) : launch_k1_nt<256>(mm, smem, s);
+  bool masked = false;
+  for (int i = 0; i < mm.n; ++i) masked = masked || mm.a[i].mask != nullptr;
+  if (masked)
+    return threads == 128 ? launch_k1_nt<128, true>(mm, smem, s)
+                          : launch_k1_nt<256, true>(mm, smem, s);
+  return threads == 128 ? launch_k1_nt<128, false>(mm, smem, s)
+                        : launch_k1_nt<256, false>(mm, smem, s);
 }
 
 }  // namespace
 
 int frame_front_smem(const Geom& g, const vio_params& p, int tile_shift, int pyr_first,
-                     int threads, long long launch_cells) {
+                     int threads, int det_warps) {
   det::CellGeom cg{p.cell_w, p.cell_h, g.w[0] / p.cell_w, p.k_per_cell, 0, 0, 1, 1, 1};
-  int smem = det::detect_setup(cg, threads, launch_cells, sm_count());
+  int smem = det::detect_setup(cg, threads, det_warps);
   const int m = first_levels(g, pyr_first);
   if (m > 0) {
     const int ps = pyr::pass_smem_max(g.w, g.h, 0, m, pyr::top_tile(m, tile_shift));
@@ -755,12 +762,13 @@ cudaError_t launch_front(const vio_params& p, const Geom& g, const Batch& all, i
   MultiK1 mm{};
   mm.n = 1;
   const long long units = (all.n + det_step - 1) / det_step;
-  const long long cells = units * (g.w[0] / p.cell_w) * (g.h[0] / p.cell_h);
+  const int gw =
+      det::warps_per_cell(units * (g.w[0] / p.cell_w) * (g.h[0] / p.cell_h), sm_count());
   mm.a[0] = front_args(p, g, all, det_step, mask, mask_stride, cand, cand_count,
-                       VIO_FRONT_SHIFT, VIO_FRONT_FIRST, VIO_FRONT_THREADS, cells);
+                       VIO_FRONT_SHIFT, VIO_FRONT_FIRST, VIO_FRONT_THREADS, gw);
   mm.block_end[0] = units * mm.a[0].blocks_per_unit;
   const cudaError_t e = launch_k1(
-      mm, frame_front_smem(g, p, VIO_FRONT_SHIFT, VIO_FRONT_FIRST, VIO_FRONT_THREADS, cells),
+      mm, frame_front_smem(g, p, VIO_FRONT_SHIFT, VIO_FRONT_FIRST, VIO_FRONT_THREADS, gw),
       VIO_FRONT_THREADS, s);
   if (e != cudaSuccess) return e;
   const int m1 = first_levels(g, VIO_FRONT_FIRST);
@@ -783,10 +791,11 @@ cudaError_t launch_frames(const FrameLaunch* fl, int n_groups, const FrameTune& 
   for (int i = 0; i < n_groups; ++i)
     cells += (long long)fl[i].n_streams * (fl[i].g.w[0] / fl[i].p.cell_w) *
              (fl[i].g.h[0] / fl[i].p.cell_h);
+  const int gw = tune.det_warps > 0 ? tune.det_warps : det::warps_per_cell(cells, sm_count());
   for (int i = 0; i < n_groups; ++i) {
     const FrameLaunch& f = fl[i];
     K1Args a = front_args(f.p, f.g, f.cur, 2, nullptr, 0, f.cand, f.cand_count,
-                          tune.pyr_tile_shift, tune.pyr_first, tune.k1_threads, cells);
+                          tune.pyr_tile_shift, tune.pyr_first, tune.k1_threads, gw);
     a.slotted = f.slotted;
     a.n_streams = f.n_streams;
     a.parity = f.parity;
@@ -796,7 +805,7 @@ cudaError_t launch_frames(const FrameLaunch* fl, int n_groups, const FrameTune& 
     acc += (long long)f.n_streams * a.blocks_per_unit;
     m1.block_end[i] = acc;
     const int sm = frame_front_smem(f.g, f.p, tune.pyr_tile_shift, tune.pyr_first,
-                                    tune.k1_threads, cells);
+                                    tune.k1_threads, gw);
     smem1 = sm > smem1 ? sm : smem1;
   }
   cudaError_t e = launch_k1(m1, smem1, tune.k1_threads, s);

@@ -14,6 +14,7 @@ struct FrameTune {
   int stereo_after;    // 1: stereo-match only the selected keypoints, after selection
   int pyr_first;       // pyramid levels of K1's fused pass (1..4; 0 = as many as fit)
   int k1_threads;      // CTA size of K1: 128 or 256
+  int det_warps;       // warps per detection cell (1, 2, 4, 8; 0 = from the launch size)
 };
 
 struct FrameLaunch {
@@ -112,7 +113,7 @@ inline bool initnet_cfg_ok(const vio_initnet_cfg* c, int n_levels, const void* p
   return c->min_conf == c->min_conf;   // not NaN
 }
 int frame_front_smem(const Geom& g, const vio_params& p, int tile_shift, int pyr_first,
-                     int threads, long long launch_cells);
+                     int threads, int det_warps);
 // Fused pyramid and per-cell detection candidates of every det_step-th
 // image of `all` (one launch), then the pyramid levels beyond the fused pass.
 cudaError_t launch_front(const vio_params& p, const Geom& g, const Batch& all, int det_step,

@@ -224,10 +224,12 @@ extern "C" vio_status vio_frontend_set_tune(vio_frontend* fe, const vio_batch_tu
     return VIO_ERR_INVALID_ARG;
   if (t->pyr_tile_shift < -1 || t->pyr_tile_shift > 1 || t->stereo_after_select != 0 ||
       t->pyr_first_levels < 0 || t->pyr_first_levels > 4 ||
-      (t->k1_threads != 128 && t->k1_threads != 256))
+      (t->k1_threads != 128 && t->k1_threads != 256) ||
+      (t->det_warps != 0 && t->det_warps != 1 && t->det_warps != 2 && t->det_warps != 4 &&
+       t->det_warps != 8))
     return VIO_ERR_INVALID_ARG;
   fe->tune = vio::FrameTune{t->k2_threads, t->pyr_tile_shift, 0, t->pyr_first_levels,
-                            t->k1_threads};
+                            t->k1_threads, t->det_warps};
   return VIO_OK;
 }
 

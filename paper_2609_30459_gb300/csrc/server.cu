@@ -379,6 +379,13 @@ extern "C" vio_status vio_server_create(vio_server** out, const vio_stream_group
     return VIO_ERR_OOM;
   }
   vio_batch_set_graph(s->batch, 1);
+  {
+    // steps hold a frame or two: score each detection cell with 4 warps
+    vio_batch_tune t;
+    vio_batch_get_tune(s->batch, &t);
+    t.det_warps = 4;
+    vio_batch_set_tune(s->batch, &t);
+  }
   uint8_t* q = s->d_staging;
   int total = 0;
   s->cls.resize(n_classes);

@@ -60,7 +60,8 @@ class StreamGroup(ctypes.Structure):
 class BatchTune(ctypes.Structure):
     _fields_ = [("k2_threads", ctypes.c_int32), ("pyr_tile_shift", ctypes.c_int32),
                 ("stereo_after_select", ctypes.c_int32), ("pyr_first_levels", ctypes.c_int32),
-                ("k1_threads", ctypes.c_int32)]
+                ("k1_threads", ctypes.c_int32),
+                ("det_warps", ctypes.c_int32)]
 
 
 class InitNetCfg(ctypes.Structure):
@@ -592,8 +593,8 @@ class Frontend:
         return int(load().vio_frontend_launches_per_step(self.handle))
 
     def set_tune(self, k2_threads: int = 128, pyr_tile_shift: int = 0,
-                 pyr_first_levels: int = 0, k1_threads: int = 256):
-        t = BatchTune(k2_threads, pyr_tile_shift, 0, pyr_first_levels, k1_threads)
+                 pyr_first_levels: int = 0, k1_threads: int = 256, det_warps: int = 0):
+        t = BatchTune(k2_threads, pyr_tile_shift, 0, pyr_first_levels, k1_threads, det_warps)
         _check(load().vio_frontend_set_tune(self.handle, ctypes.byref(t)),
                "vio_frontend_set_tune")
 
@@ -724,17 +725,18 @@ class Batch:
         _check(load().vio_batch_set_graph(self.handle, 1 if enable else 0), "set_graph")
 
     def set_tune(self, k2_threads: int, pyr_tile_shift: int, stereo_after_select: int = 0,
-                 pyr_first_levels: int = 0, k1_threads: int = 256):
+                 pyr_first_levels: int = 0, k1_threads: int = 256, det_warps: int = 0):
         t = BatchTune(k2_threads, pyr_tile_shift, stereo_after_select, pyr_first_levels,
-                      k1_threads)
+                      k1_threads, det_warps)
         _check(load().vio_batch_set_tune(self.handle, ctypes.byref(t)), "set_tune")
 
-    def get_tune(self) -> tuple[int, int, int, int, int]:
-        """(k2_threads, pyr_tile_shift, stereo_after_select, pyr_first_levels, k1_threads)."""
+    def get_tune(self) -> tuple[int, int, int, int, int, int]:
+        """(k2_threads, pyr_tile_shift, stereo_after_select, pyr_first_levels, k1_threads,
+        det_warps)."""
         t = BatchTune()
         _check(load().vio_batch_get_tune(self.handle, ctypes.byref(t)), "get_tune")
         return (t.k2_threads, t.pyr_tile_shift, t.stereo_after_select, t.pyr_first_levels,
-                t.k1_threads)
+                t.k1_threads, t.det_warps)
 
     def autotune(self, reps: int = 3, stream=None) -> float:
         ms = ctypes.c_float()
@@ -893,9 +895,9 @@ class Server:
                "vio_server_set_initnet")
 
     def set_tune(self, k2_threads: int, pyr_tile_shift: int, stereo_after_select: int = 0,
-                 pyr_first_levels: int = 0, k1_threads: int = 256):
+                 pyr_first_levels: int = 0, k1_threads: int = 256, det_warps: int = 4):
         t = BatchTune(k2_threads, pyr_tile_shift, stereo_after_select, pyr_first_levels,
-                      k1_threads)
+                      k1_threads, det_warps)
         _check(load().vio_server_set_tune(self.handle, ctypes.byref(t)), "vio_server_set_tune")
 
     def open(self, cls: int):

@@ -128,7 +128,7 @@ def test_batch_graph_replay_and_autotune():
                             for i in range(total)], stream=s)
         best = b.autotune(reps=1, stream=s)
         assert best > 0
-        k2, shift, after, first, k1 = b.get_tune()
+        k2, shift, after, first, k1, dw = b.get_tune()
         assert k2 in (64, 128, 256, 512) and shift in (-1, 0, 1) and after in (0, 1)
         assert first in (0, 1, 2) and k1 in (128, 256)
         b.set_graph(True)
@@ -146,8 +146,8 @@ def test_batch_pyramid_split_equals_streams_alone(first):
     groups, seqs = _make()
     total = sum(g[3] for g in groups)
     b = vio.Batch(groups)
-    b.set_tune(256, 1, 0, first, 128)
-    assert b.get_tune() == (256, 1, 0, first, 128)
+    b.set_tune(256, 1, 0, first, 128, 2)
+    assert b.get_tune() == (256, 1, 0, first, 128, 2)
     schedule = [[1] * total for _ in range(N_FRAMES)]
     _run_batch(b, seqs, schedule)
     _check_equal(b, groups, seqs, schedule)

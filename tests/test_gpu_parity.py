@@ -118,6 +118,41 @@ def test_detect_bitexact(w, h, cw, ch, k, thr, border):
         assert np.array_equal(sc[i, :c].cpu().numpy(), rs)
 
 
+@pytest.mark.parametrize("masked", [False, True])
+def test_detect_many_large_cells_bitexact(masked):
+    """A batch with enough cells that each gets a single warp, with large
+    cells and the full threshold sequence: a warp scores more pixels than its
+    queue holds, so candidates come from the scan of its part of the map.
+    Every image bit-exact against the oracle."""
+    n, w, h, cw, ch, k, thr = 56, 752, 480, 82, 82, 2, (40, 20, 10, 5)
+    imgs = np.stack([textured(900 + i, h, w, sigma=1.2, noise=3.0) for i in range(n)])
+    gx, gy = w // cw, h // ch
+    mask = None
+    if masked:
+        mask = (np.random.default_rng(7).random((n, h, w)) > 0.1).astype(np.uint8)
+    p = vio.default_params(n_levels=1, cell_w=cw, cell_h=ch, k_per_cell=k, thresholds=thr,
+                           detect_border=9)
+    ctx = vio.Context(p, w, h, n)
+    pyr = vio.Pyramids(to_dev(imgs), 1)
+    cap = gx * gy * k
+    kp = torch.full((n, cap, 2), -1.0, device=DEV)
+    sc = torch.zeros((n, cap), dtype=torch.int16, device=DEV)
+    cnt = torch.zeros(n, dtype=torch.int32, device=DEV)
+    if masked:
+        ctx.detect_grid(pyr, pyr.batch(), kp, sc, cnt, cap,
+                        mask=torch.from_numpy(mask).to(DEV), mask_stride=h * w)
+    else:
+        ctx.detect_grid(pyr, pyr.batch(), kp, sc, cnt, cap)
+    torch.cuda.synchronize()
+    for i in range(n):
+        rk, rs = oracle.detect_grid(imgs[i], cw, ch, k=k, thresholds=thr, border=9,
+                                    mask=mask[i] if masked else None)
+        c = int(cnt[i])
+        assert c == len(rk), (i, c, len(rk))
+        assert np.array_equal(kp[i, :c].cpu().numpy(), rk)
+        assert np.array_equal(sc[i, :c].cpu().numpy(), rs)
+
+
 def test_detect_capacity_truncates_in_raster_order():
     w, h = 400, 300
     img = textured(5, h, w)
