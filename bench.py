@@ -308,7 +308,7 @@ def frontend_config_run(torch, vio, name, w, h, n_streams, levels, cw, ch, n_fra
                              best[1]))}
 
 
-def batched_compare(torch, vio, steps, warmup, net):
+def batched_compare(torch, vio, steps, warmup, net, seqs=None):
     """The 16-stream batch, plain and with the learned initializer (trained
     gate, tracking from the proposal over levels 1..0, and the same network
     with the start at level 0): each step uploads one frame per stream into
@@ -317,7 +317,7 @@ def batched_compare(torch, vio, steps, warmup, net):
     completes with it). Steady state: the streams run `warmup` + 8 steps
     before the timed ones (no reset), as continuous streams do."""
     import numpy as np
-    seqs = cfg4_frames()
+    seqs = seqs or cfg4_frames()
     dev = [[torch.from_numpy(f).cuda() for f in cls] for cls in seqs]
     groups = []
     for (w, h, cw, ch) in CFG4_CLASSES:
@@ -447,9 +447,17 @@ def serving_run(torch, vio, seconds, net, tune, seqs=None):
     # warm-up: one frame per session (graph capture, first-frame detection)
     warm = [(sessions[i], 0.0, pools[i][0], -1, 0) for i in range(len(sessions))]
     srv.run_trace(warm, timeout_s=60.0)
+    import gc
+    gc.collect()
+    gc.disable()                 # no collector pauses in the host process meanwhile
+    time.sleep(1.0)
     t0 = time.perf_counter()
-    done, steps = srv.run_trace(reqs, timeout_s=seconds + 120.0)
+    try:
+        done, steps = srv.run_trace(reqs, timeout_s=seconds + 120.0)
+    finally:
+        gc.enable()
     wall = time.perf_counter() - t0
+    gap, n_gaps = srv.loop_stats()
     summ = serving.latency_summary(done)
     srv.close_server()
     return {"sessions": len(sessions), "classes": [f"{w}x{h}" for (w, h, _, _) in CFG4_CLASSES],
@@ -457,7 +465,11 @@ def serving_run(torch, vio, seconds, net, tune, seqs=None):
             "seconds": seconds, "requests": len(reqs), "steps": steps,
             "mean_batch": len(reqs) / max(steps, 1), "wall_s": wall,
             "budget_bytes": budget, "device_bytes": used, "slots": slots,
-            "learned": net is not None, **summ}
+            "learned": net is not None,
+            "host_loop": {"max_gap_ms": 1e3 * gap, "passes_over_1ms": n_gaps,
+                          "note": "the server's host loop polls continuously; a gap is time "
+                                  "the process was not running (shared host CPUs)"},
+            **summ}
 
 
 def profile_frontend(w, h, n_streams, learned, steps=3):
@@ -773,13 +785,18 @@ def main():
                                 752, 480, 1, 4, 82, 82, 100, 15.0, 2000, args.batched_steps,
                                 params_kw={"gn_iters": 3, "thresholds": (40, 20)})]
 
+    # the 16 mixed-size sequences of cfg 4 (also the sessions' frames of cfg 5),
+    # rendered once by a pool of host processes
+    seqs4 = None
+    if rank == 0 and not (args.no_batched and args.no_serve):
+        seqs4 = cfg4_frames()
     batched = None
     if rank == 0 and not args.no_batched:
         from paper_2609_30459_gb300 import initnet_train
         net = None
         if os.path.exists(initnet_train.DEFAULT_WEIGHTS):
             net = vio.InitNet.load(initnet_train.DEFAULT_WEIGHTS)
-        batched = batched_compare(torch, vio, args.batched_steps, args.warmup, net)
+        batched = batched_compare(torch, vio, args.batched_steps, args.warmup, net, seqs=seqs4)
     serve = None
     if rank == 0 and not args.no_serve:
         from paper_2609_30459_gb300 import initnet_train
@@ -788,7 +805,7 @@ def main():
             net = vio.InitNet.load(initnet_train.DEFAULT_WEIGHTS)
         # the batch's default tune: steps here hold one or two frames, for which
         # the fewest launches per step are best (the batched tune is for full steps)
-        serve = serving_run(torch, vio, args.serve_seconds, net, None)
+        serve = serving_run(torch, vio, args.serve_seconds, net, None, seqs=seqs4)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -547,6 +547,10 @@ int32_t vio_server_take(vio_server* s, vio_server_done* out, int32_t max);
  * completion order. VIO_ERR_TIMEOUT after timeout_s seconds. */
 vio_status vio_server_run_trace(vio_server* s, const vio_server_req* reqs, int64_t n,
                                 vio_server_done* out, double timeout_s, int64_t* n_steps);
+/* Host side of the last vio_server_run_trace: the longest time between two
+ * passes of its loop (a loop that was not scheduled on a CPU delays every
+ * request it holds) and the number of passes that took longer than 1 ms. */
+vio_status vio_server_loop_stats(const vio_server* s, double* max_gap_s, int64_t* n_over_1ms);
 
 /* ---------------------------------------------------------------------------
  * Learned flow initializer. Not in the paper: its tracker starts each

@@ -102,6 +102,8 @@ struct vio_server {
   uint8_t* d_staging = nullptr;
   int64_t steps = 0;
   int64_t budget = 0, used = 0;
+  double loop_max_gap = 0.0;           // host loop of the last trace
+  int64_t loop_over_1ms = 0;
 };
 
 namespace {
@@ -532,6 +534,14 @@ extern "C" int32_t vio_server_take(vio_server* s, vio_server_done* out, int32_t 
   return n;
 }
 
+extern "C" vio_status vio_server_loop_stats(const vio_server* s, double* max_gap_s,
+                                           int64_t* n_over_1ms) {
+  if (!s || !max_gap_s || !n_over_1ms) return VIO_ERR_INVALID_ARG;
+  *max_gap_s = s->loop_max_gap;
+  *n_over_1ms = s->loop_over_1ms;
+  return VIO_OK;
+}
+
 extern "C" vio_status vio_server_run_trace(vio_server* s, const vio_server_req* reqs,
                                            int64_t n, vio_server_done* out, double timeout_s,
                                            int64_t* n_steps) {
@@ -542,8 +552,15 @@ extern "C" vio_status vio_server_run_trace(vio_server* s, const vio_server_req* 
   const double t0 = now_s();
   int64_t next = 0, got = 0;
   vio_status st = VIO_OK;
+  s->loop_max_gap = 0.0;
+  s->loop_over_1ms = 0;
+  double t_prev = 0.0;
   while (got < n) {
     const double t = now_s() - t0;
+    const double gap = t - t_prev;
+    t_prev = t;
+    if (gap > s->loop_max_gap) s->loop_max_gap = gap;
+    if (gap > 1e-3) ++s->loop_over_1ms;
     if (t > timeout_s) {
       st = VIO_ERR_TIMEOUT;
       break;

@@ -203,6 +203,8 @@ _SIGS = {
     "vio_server_run_trace": (ctypes.c_int32, [ctypes.c_void_p, ctypes.POINTER(ServerReq),
                                               ctypes.c_int64, ctypes.POINTER(ServerDone),
                                               ctypes.c_double, ctypes.POINTER(ctypes.c_int64)]),
+    "vio_server_loop_stats": (ctypes.c_int32, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
+                                               ctypes.POINTER(ctypes.c_int64)]),
     "vio_initnet_pack": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "vio_initnet_extract": (ctypes.c_int32, [ctypes.POINTER(PyrLayout), ctypes.POINTER(PyrBatch),
                                              ctypes.POINTER(PyrBatch), ctypes.c_void_p,
@@ -943,3 +945,11 @@ class Server:
         _check(load().vio_server_run_trace(self.handle, arr, n, out, timeout_s,
                                            ctypes.byref(steps)), "vio_server_run_trace")
         return _done_rows(out, n), int(steps.value)
+
+    def loop_stats(self):
+        """(longest gap between passes of the last trace's host loop in seconds,
+        passes longer than 1 ms)."""
+        gap, n = ctypes.c_double(), ctypes.c_int64()
+        _check(load().vio_server_loop_stats(self.handle, ctypes.byref(gap), ctypes.byref(n)),
+               "vio_server_loop_stats")
+        return float(gap.value), int(n.value)
