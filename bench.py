@@ -215,9 +215,9 @@ def pyramid_detect_roofline(torch, vio, frames_dev, peaks, peak_src):
             "images": n, "batch_bytes_in": n * W * H, "algorithmic_bytes": alg,
             "algorithmic_bytes_per_image": W * H + upper + n_kp * 10 / n,
             "ms": 1000 * t, "peak_source": peak_src,
-            "note": "vio_pyramid_detect: pyramid levels 1-3 and per-cell FAST/NMS/top-k in one "
-                    "launch, then the per-image selection; level 0 read once, upper levels "
-                    "and 10 B per keypoint written"}
+            "note": "vio_pyramid_detect: pyramid levels 1-2 and per-cell FAST/NMS/top-k in one "
+                    "launch, level 3 in one more pyramid launch, then the per-image selection; "
+                    "level 0 read once, upper levels and 10 B per keypoint written"}
 
 
 # Batched + learned initializer: 16 streams, 4 each of these sizes, cells for
@@ -519,6 +519,29 @@ def autotune_frontend(torch, fe, frames, n=40):
             "k1_threads": best[3], "ms_per_step": best_t / n}
 
 
+def profile_pyramid_detect(n=512, reps=3):
+    """vio_pyramid_detect of a device-resident batch of n images of the
+    headline sequence, `reps` times (for launch lists and kernel profiles)."""
+    import torch
+    from paper_2609_30459_gb300 import synth, vio
+    vio.load(build=True)
+    seq = synth.make_sequence(2000, 4, W, H, 1, max_motion=MOTION, tex_size=2048)
+    imgs = torch.from_numpy(seq.frames.reshape(-1, H, W)).cuda().repeat(n // 8, 1, 1)
+    imgs = imgs.contiguous()
+    p = vio.default_params(n_levels=LEVELS, cell_w=CELL_W, cell_h=CELL_H, k_per_cell=K_CELL)
+    ctx = vio.Context(p, W, H, n)
+    pyr = vio.Pyramids(imgs, LEVELS)
+    cap = (W // CELL_W) * (H // CELL_H) * K_CELL
+    kp = torch.empty((n, cap, 2), dtype=torch.float32, device="cuda")
+    sc = torch.empty((n, cap), dtype=torch.int16, device="cuda")
+    cnt = torch.empty(n, dtype=torch.int32, device="cuda")
+    for _ in range(reps):
+        ctx.pyramid_detect(pyr, kp, sc, cnt, cap)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_pyramid_detect": n, "keypoints": int(cnt.sum().item())}))
+    return 0
+
+
 def profile_batch(mode, steps=18):
     """The 16-stream batch (cfg 4) stepped `steps` times without graphs, plain
     or with the learned start, so that every kernel is its own launch (for
@@ -588,6 +611,9 @@ def main():
     ap.add_argument("--profile-frontend", nargs=3, type=int, metavar=("W", "H", "STREAMS"),
                     help="only run 3 frontend steps of this size (for kernel profiles)")
     ap.add_argument("--learned", action="store_true", help="with --profile-frontend")
+    ap.add_argument("--profile-pyramid-detect", type=int, nargs="?", const=512, default=None,
+                    metavar="IMAGES",
+                    help="only run vio_pyramid_detect 3 times on IMAGES images (default 512)")
     ap.add_argument("--profile-batch", choices=["plain", "learned"],
                     help="only step the 16-stream batch 18 times without graphs (launch lists)")
     ap.add_argument("--profile-detect", type=int, nargs="?", const=64, default=None,
@@ -599,6 +625,8 @@ def main():
         return profile_detect(args.profile_detect)
     if args.profile_batch:
         return profile_batch(args.profile_batch)
+    if args.profile_pyramid_detect:
+        return profile_pyramid_detect(args.profile_pyramid_detect)
     if args.profile_frontend:
         return profile_frontend(*args.profile_frontend, args.learned)
     if args.warmup < 3:
