@@ -177,18 +177,23 @@ def run_reference(args):
     return 0
 
 
-def pyramid_detect_roofline(torch, vio, frames_dev, peaks, peak_src):
-    """Pyramid and detection of a device-resident batch well above L2 (the 400
-    images of the sequence, repeated to ~1.1 GB): vio_pyramid_detect, one fused
-    launch plus the selection launch, timed with CUDA events."""
-    reps = 8
-    imgs = frames_dev.reshape(-1, H, W).repeat(reps, 1, 1).contiguous()   # (3200, H, W)
+def pyramid_detect_roofline(torch, vio, frames_dev, peaks, peak_src, w=None, h=None,
+                            levels=None, cw=None, ch=None, reps=8):
+    """Pyramid and detection of a device-resident batch well above L2 (the
+    headline's 400 images repeated to ~1.1 GB, or cfg 3's 400 images of
+    1920x1080): vio_pyramid_detect, one fused launch plus the selection launch,
+    timed with CUDA events."""
+    w, h = w or W, h or H
+    levels, cw, ch = levels or LEVELS, cw or CELL_W, ch or CELL_H
+    imgs = frames_dev.reshape(-1, h, w)
+    if reps > 1:
+        imgs = imgs.repeat(reps, 1, 1)
+    imgs = imgs.contiguous()
     n = imgs.shape[0]
-    params = vio.default_params(n_levels=LEVELS, cell_w=CELL_W, cell_h=CELL_H,
-                                k_per_cell=K_CELL)
-    ctx = vio.Context(params, W, H, n)
-    pyr = vio.Pyramids(imgs, LEVELS)
-    gx, gy = W // CELL_W, H // CELL_H
+    params = vio.default_params(n_levels=levels, cell_w=cw, cell_h=ch, k_per_cell=K_CELL)
+    ctx = vio.Context(params, w, h, n)
+    pyr = vio.Pyramids(imgs, levels)
+    gx, gy = w // cw, h // ch
     cap = gx * gy * K_CELL
     kp = torch.empty((n, cap, 2), dtype=torch.float32, device=imgs.device)
     sc = torch.empty((n, cap), dtype=torch.int16, device=imgs.device)
@@ -204,20 +209,21 @@ def pyramid_detect_roofline(torch, vio, frames_dev, peaks, peak_src):
         if it >= 2:
             times.append(ev[0].elapsed_time(ev[1]) / 1000)
     L = pyr.layout
-    upper = sum(L.w[l] * L.h[l] for l in range(1, LEVELS))
+    upper = sum(L.w[l] * L.h[l] for l in range(1, levels))
     n_kp = int(cnt.sum().item())
-    alg = n * (W * H + upper) + n_kp * 10
+    alg = n * (w * h + upper) + n_kp * 10
     t = statistics.median(times)
     gbs = alg / t / 1e9
     ctx.close()
     return {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
             "frac": gbs / peaks["hbm_gbs"], "traffic": None, "kernel": "frame_front_kernel",
-            "images": n, "batch_bytes_in": n * W * H, "algorithmic_bytes": alg,
-            "algorithmic_bytes_per_image": W * H + upper + n_kp * 10 / n,
+            "images": n, "image": f"{w}x{h}, {levels} levels, {gx}x{gy} cells",
+            "batch_bytes_in": n * w * h, "algorithmic_bytes": alg,
+            "algorithmic_bytes_per_image": w * h + upper + n_kp * 10 / n,
             "ms": 1000 * t, "peak_source": peak_src,
             "note": "vio_pyramid_detect: pyramid levels 1-2 and per-cell FAST/NMS/top-k in one "
-                    "launch, level 3 in one more pyramid launch, then the per-image selection; "
-                    "level 0 read once, upper levels and 10 B per keypoint written"}
+                    "launch, the deeper levels in one more pyramid launch, then the per-image "
+                    "selection; level 0 read once, upper levels and 10 B per keypoint written"}
 
 
 # Batched + learned initializer: 16 streams, 4 each of these sizes, cells for
@@ -244,8 +250,42 @@ def cfg4_frames():
     return [out[k * CFG4_STREAMS:(k + 1) * CFG4_STREAMS] for k in range(len(CFG4_CLASSES))]
 
 
+# useful FLOPs of one forward pass of the flow network: three 3x3 stride-2
+# convolutions (4 -> 32 channels at 8x8, 32 -> 32 at 4x4 and at 2x2) and the
+# dense layers 128 -> 64 -> 3
+INITNET_FLOP = (2 * 8 * 8 * 32 * 4 * 9 + 2 * 4 * 4 * 32 * 32 * 9 + 2 * 2 * 2 * 32 * 32 * 9
+                + 2 * 128 * 64 + 2 * 64 * 3)
+
+
+def initnet_tensor_roofline(torch, vio, net, peaks, n=1 << 16, reps=5):
+    """The flow network's tiled forward pass (BF16 mma.sync, FP32 accumulate) over
+    n random inputs, useful FLOPs against the measured dense BF16 peak."""
+    g = torch.Generator(device="cuda").manual_seed(11)
+    x = (0.5 * torch.randn((n, 4, 16, 16), device="cuda", generator=g)).to(torch.bfloat16)
+    x = x.view(torch.int16)
+    out = torch.empty((n, 3), dtype=torch.float32, device="cuda")
+    s = torch.cuda.current_stream()
+    for _ in range(2):
+        net.forward(x, out)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    for _ in range(reps):
+        net.forward(x, out)
+    e1.record(s)
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / 1000.0 / reps
+    ach = n * INITNET_FLOP / t / 1e12
+    peak = peaks.get("bf16_tflops", 1900.0)
+    return {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+            "frac": ach / peak, "kernel": "forward_tile_kernel", "samples": n,
+            "flop_per_sample": INITNET_FLOP, "ms": 1000 * t,
+            "peak_source": "measured dense BF16 (burst)",
+            "note": "legacy mma.sync m16n8k16 tiles of 16 samples per 512-thread CTA; the "
+                    "forward pass of the frame step uses the same tiles"}
+
+
 def frontend_config_run(torch, vio, name, w, h, n_streams, levels, cw, ch, n_frames, motion,
-                        seed0, steps, params_kw=None):
+                        seed0, steps, params_kw=None, roofline=None):
     """One frontend configuration over its own synthetic sequences (each
     stream its own seed), autotuned launch shapes, device-resident frames
     played forward and back: stereo frames/s (n_streams frames per step) and
@@ -297,7 +337,11 @@ def frontend_config_run(torch, vio, name, w, h, n_streams, levels, cw, ch, n_fra
         fe.step(frames[order[t % len(order)]])
     stage_ms, n_t, step_ms = fe.read_timing(max_steps=200)
     fe.close()
-    return {"config": name, "w": w, "h": h, "stereo_streams": n_streams, "levels": levels,
+    pd = None
+    if roofline is not None:       # all frames of all cameras as one detection batch
+        pd = pyramid_detect_roofline(torch, vio, frames, *roofline, w=w, h=h, levels=levels,
+                                     cw=cw, ch=ch, reps=1)
+    return {"config": name, "pyramid_detect_roofline": pd, "w": w, "h": h, "stereo_streams": n_streams, "levels": levels,
             "cells": f"{w // cw}x{h // ch} of {cw}x{ch} px", "frames": n_frames,
             "max_motion_px": motion, "params": params_kw or {},
             "frames_per_s": n_streams * steps / total_s, "ms_per_step": 1000 * total_s / steps,
@@ -807,7 +851,7 @@ def main():
             frontend_config_run(torch, vio, "cfg3 high-pixel: 4 cameras (2 stereo pairs) "
                                 "1920x1080, 100 frames, motion up to 40 px, 5 levels, 40x25 "
                                 "cells (1000 keypoints/image)", 1920, 1080, 2, 5, 48, 43, 100,
-                                40.0, 3000, args.batched_steps),
+                                40.0, 3000, args.batched_steps, roofline=(peaks, peak_src)),
             frontend_config_run(torch, vio, "lite parameters (Sec. IV-D): minimum FAST threshold "
                                 "20, 82-px cells, 3 Gauss-Newton iterations; 752x480, 4 levels",
                                 752, 480, 1, 4, 82, 82, 100, 15.0, 2000, args.batched_steps,
@@ -825,6 +869,8 @@ def main():
         if os.path.exists(initnet_train.DEFAULT_WEIGHTS):
             net = vio.InitNet.load(initnet_train.DEFAULT_WEIGHTS)
         batched = batched_compare(torch, vio, args.batched_steps, args.warmup, net, seqs=seqs4)
+        if net is not None:
+            batched["initnet_tensor_roofline"] = initnet_tensor_roofline(torch, vio, net, peaks)
     serve = None
     if rank == 0 and not args.no_serve:
         from paper_2609_30459_gb300 import initnet_train
