@@ -68,6 +68,7 @@ struct K1Args {
   const int32_t* parity;
   const int32_t* active;
   int32_t* step_ctr;   // incremented by block 0 (nullable)
+  int32_t* ctr_copy;   // nullable: the new count is also stored here
 };
 
 struct MultiK1 {
@@ -96,7 +97,11 @@ __global__ void __launch_bounds__(NT, 768 / NT) frame_front_kernel(const __grid_
   const int gi = group_of(mm, blockIdx.x, start);
   const K1Args& a = mm.a[gi];
   const long long b = blockIdx.x - start;
-  if (b == 0 && threadIdx.x == 0 && a.step_ctr) *a.step_ctr += 1;
+  if (b == 0 && threadIdx.x == 0 && a.step_ctr) {
+    const int c = *a.step_ctr + 1;
+    *a.step_ctr = c;
+    if (a.ctr_copy) *a.ctr_copy = c;
+  }
   const int unit = (int)(b / a.blocks_per_unit);
   const int rem = (int)(b - (long long)unit * a.blocks_per_unit);
   int base = unit * a.det_step;
@@ -418,7 +423,8 @@ __global__ void __launch_bounds__(K3_THREADS)
   const int W = f.g.w[0];
   const long long cap = f.cap;
   const int t = threadIdx.x;
-  const int ctr = *f.step_ctr;     // this launch's step index + 1 (K1 incremented it)
+  // this launch's step index + 1 (K1 incremented it)
+  const int ctr = *(f.ctr_copy ? f.ctr_copy : f.step_ctr);
   int32_t* st = f.stats + ((long long)((ctr - 1) % VIO_STATS_RING) * f.n_streams + s) * VIO_N_STATS;
   if (!sr.active) {
     if (t < VIO_N_STATS) st[t] = 0;
@@ -625,7 +631,7 @@ __global__ void __launch_bounds__(K3_THREADS)
   const long long cnt_out = ((long long)sr.lo * f.n_streams + s) * 2;
   const long long out1 = (cnt_out + 1) * cap;
   const int surv1 = f.list_count[cnt_out + 1];           // K3 left the survivors' count
-  const int ctr = *f.step_ctr;
+  const int ctr = *(f.ctr_copy ? f.ctr_copy : f.step_ctr);
   int32_t* st = f.stats + ((long long)((ctr - 1) % VIO_STATS_RING) * f.n_streams + s) * VIO_N_STATS;
   const int n_new = f.new_count[s];
   const int id0 = f.next_id[s] - st[VIO_STAT_NEW];
@@ -776,50 +782,56 @@ cudaError_t launch_front(const vio_params& p, const Geom& g, const Batch& all, i
 }
 
 cudaError_t launch_frames(const FrameLaunch* fl, int n_groups, const FrameTune& tune,
-                          cudaStream_t s, cudaEvent_t* marks) {
+                          cudaStream_t s, cudaEvent_t* marks, int part) {
   if (n_groups < 1 || n_groups > kMaxGroups) return cudaErrorInvalidValue;
   auto mark = [&](int i) {
     if (marks) cudaEventRecord(marks[i], s);
   };
 
-  // K1: pyramid levels 1-4 + detection candidates (camera 0 of each stream)
-  mark(0);
-  MultiK1 m1{};
-  m1.n = n_groups;
-  int smem1 = 0;
-  long long acc = 0, cells = 0;
-  for (int i = 0; i < n_groups; ++i)
-    cells += (long long)fl[i].n_streams * (fl[i].g.w[0] / fl[i].p.cell_w) *
-             (fl[i].g.h[0] / fl[i].p.cell_h);
-  const int gw = tune.det_warps > 0 ? tune.det_warps : det::warps_per_cell(cells, sm_count());
-  for (int i = 0; i < n_groups; ++i) {
-    const FrameLaunch& f = fl[i];
-    K1Args a = front_args(f.p, f.g, f.cur, 2, nullptr, 0, f.cand, f.cand_count,
-                          tune.pyr_tile_shift, tune.pyr_first, tune.k1_threads, gw);
-    a.slotted = f.slotted;
-    a.n_streams = f.n_streams;
-    a.parity = f.parity;
-    a.active = f.active;
-    a.step_ctr = f.step_ctr;
-    m1.a[i] = a;
-    acc += (long long)f.n_streams * a.blocks_per_unit;
-    m1.block_end[i] = acc;
-    const int sm = frame_front_smem(f.g, f.p, tune.pyr_tile_shift, tune.pyr_first,
-                                    tune.k1_threads, gw);
-    smem1 = sm > smem1 ? sm : smem1;
-  }
-  cudaError_t e = launch_k1(m1, smem1, tune.k1_threads, s);
-  if (e != cudaSuccess) return e;
-  // levels beyond the first pass
-  mark(1);
-  for (int i = 0; i < n_groups; ++i) {
-    const FrameLaunch& f = fl[i];
-    const int m1 = first_levels(f.g, tune.pyr_first);
-    if (f.g.n_levels > 1 + m1) {
-      e = launch_pyramid_from(f.g, f.cur, m1, f.p.round_mode, s);
-      if (e != cudaSuccess) return e;
+  cudaError_t e = cudaSuccess;
+  long long acc = 0;
+  if (part != 2) {
+    // K1: pyramid levels 1-4 + detection candidates (camera 0 of each stream)
+    mark(0);
+    MultiK1 m1{};
+    m1.n = n_groups;
+    int smem1 = 0;
+    long long cells = 0;
+    for (int i = 0; i < n_groups; ++i)
+      cells += (long long)fl[i].n_streams * (fl[i].g.w[0] / fl[i].p.cell_w) *
+               (fl[i].g.h[0] / fl[i].p.cell_h);
+    const int gw = tune.det_warps > 0 ? tune.det_warps : det::warps_per_cell(cells, sm_count());
+    for (int i = 0; i < n_groups; ++i) {
+      const FrameLaunch& f = fl[i];
+      K1Args a = front_args(f.p, f.g, f.cur, 2, nullptr, 0, f.cand, f.cand_count,
+                            tune.pyr_tile_shift, tune.pyr_first, tune.k1_threads, gw);
+      a.slotted = f.slotted;
+      a.n_streams = f.n_streams;
+      a.parity = f.parity;
+      a.active = f.active;
+      a.step_ctr = f.step_ctr;
+      a.ctr_copy = f.ctr_copy;
+      m1.a[i] = a;
+      acc += (long long)f.n_streams * a.blocks_per_unit;
+      m1.block_end[i] = acc;
+      const int sm = frame_front_smem(f.g, f.p, tune.pyr_tile_shift, tune.pyr_first,
+                                      tune.k1_threads, gw);
+      smem1 = sm > smem1 ? sm : smem1;
+    }
+    e = launch_k1(m1, smem1, tune.k1_threads, s);
+    if (e != cudaSuccess) return e;
+    // levels beyond the first pass
+    mark(1);
+    for (int i = 0; i < n_groups; ++i) {
+      const FrameLaunch& f = fl[i];
+      const int m1 = first_levels(f.g, tune.pyr_first);
+      if (f.g.n_levels > 1 + m1) {
+        e = launch_pyramid_from(f.g, f.cur, m1, f.p.round_mode, s);
+        if (e != cudaSuccess) return e;
+      }
     }
   }
+  if (part == 1) return cudaGetLastError();
 
   // KN: flow proposals (every group has the initializer on, or none)
   mark(2);

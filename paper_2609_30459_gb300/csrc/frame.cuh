@@ -49,6 +49,9 @@ struct FrameLaunch {
   uint8_t* occupancy;              // ns x cells
   int32_t* stats;                  // ring, VIO_STATS_RING x ns x VIO_N_STATS
   int32_t* step_ctr;               // incremented once per launch of the frame
+  int32_t* ctr_copy;               // nullable: K1 also stores the new count here and the
+                                   // later launches of the step read it from here (so the
+                                   // next step's K1 may run beside them)
   // learned flow initializer of temporal tracking (net == null: off)
   const void* net;                 // packed weights
   int net_la, net_lb, net_top;
@@ -94,8 +97,13 @@ __host__ __device__ inline StreamRef stream_ref(const FrameLaunch& f, int s) {
 // pass per group for levels beyond 5, plus the flow proposals when the
 // groups' initializer is on). marks: VIO_N_STAGES + 1 events recorded at the
 // stage boundaries (or null).
+// part: 0 the whole step; 1 only its front (pyramids and detection
+// candidates: K1 and the deeper pyramid levels); 2 the rest. The front of a
+// step reads only its own frames and writes the current pyramid ring slot and
+// the candidate buffers, so it may run beside the rest of the previous step
+// when those are not the previous step's.
 cudaError_t launch_frames(const FrameLaunch* f, int n_groups, const FrameTune& tune,
-                          cudaStream_t s, cudaEvent_t* marks);
+                          cudaStream_t s, cudaEvent_t* marks, int part = 0);
 int frame_launches(const Geom* g, int n_groups, bool with_net, bool stereo_after,
                    int pyr_first);
 

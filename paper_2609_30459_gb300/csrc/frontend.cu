@@ -23,15 +23,17 @@ struct vio_frontend {
   vio_pyr_layout layout;
   // device buffers (one allocation)
   void* d_mem;
-  uint8_t* pyr[2];            // upper buffers, 2*n_streams images each, ring of 2 frames
+  uint8_t* pyr[3];            // upper buffers, 2*n_streams images each, ring of 3 frames
+                              // (a step's front may run while the previous step tracks
+                              // between the two slots before it)
   float* list_xy;             // float2 per slot, [parity][stream][camera] x capacity
   int32_t* list_id;
   int32_t* list_count;        // [parity][stream][camera]
   uint8_t* list_status;
   float* trk_xy;              // temporal track result, float2 per slot
   uint8_t* trk_status;
-  unsigned long long* cand;   // n_streams * cells * k candidate keys
-  int32_t* cand_count;        // n_streams * cells
+  unsigned long long* cand[2];   // n_streams * cells * k candidate keys, per step parity
+  int32_t* cand_count[2];        // n_streams * cells
   float* spec_xy;             // stereo matches of the candidates
   uint8_t* spec_status;
   uint8_t* occupancy;         // n_streams * cells
@@ -39,7 +41,7 @@ struct vio_frontend {
   int32_t* new_count;         // n_streams
   int32_t* next_id;           // n_streams
   int32_t* stats;             // VIO_STATS_RING * n_streams * VIO_N_STATS
-  int32_t* step_ctr;          // device count of launched steps
+  int32_t* step_ctr;          // device count of launched steps, then its copy per parity
   float* net_out;             // flow proposals, [stream][camera] x capacity x 3
   uint8_t* trk_learned;       // per slot: tracked from the proposal
   const void* net;            // packed initializer weights (null: off)
@@ -47,7 +49,9 @@ struct vio_frontend {
   vio::FrameTune tune;        // launch shapes (the frontend keeps the frame order)
   // host state
   int cur_list;
-  int cur_pyr;
+  int cur_pyr, prev_pyr;
+  cudaStream_t side = nullptr;   // fronts of pipelined steps (vio_frontend_run)
+  cudaEvent_t ev_entry = nullptr, ev_front[2] = {}, ev_back[3] = {};
   bool have_prev;
   const uint8_t* prev_frames;
   int32_t prev_pitch;
@@ -116,7 +120,8 @@ extern "C" vio_status vio_frontend_create(vio_frontend** out, const vio_params* 
   const size_t nl = (size_t)2 * n_streams, slots = nl * capacity;
   const size_t ns = (size_t)n_streams, nc = (size_t)n_cells, kk = (size_t)p->k_per_cell;
   const size_t sizes[] = {
-      (size_t)L.upper_bytes * nl, (size_t)L.upper_bytes * nl,   // 0-1 pyr
+      (size_t)L.upper_bytes * nl * 3,                           // 0 pyr (ring of 3)
+      0,                                                        // 1 (unused)
       2 * slots * 8,                                            // 2 list_xy
       2 * slots * 4,                                            // 3 list_id
       2 * nl * 4,                                               // 4 list_count
@@ -125,7 +130,7 @@ extern "C" vio_status vio_frontend_create(vio_frontend** out, const vio_params* 
       slots * 12,                                               // 7 net_out
       slots,                                                    // 8 trk_learned
       slots * 8, slots,                                         // 9-10 trk
-      ns * nc * kk * 8, ns * nc * 4,                            // 11-12 cand
+      2 * ns * nc * kk * 8, 2 * ns * nc * 4,                    // 11-12 cand (2 parities)
       ns * nc * kk * 8, ns * nc * kk,                           // 13-14 spec
       ns * nc,                                                  // 15 occupancy
       ns * capacity * 8, ns * 4,                                // 16-17 new
@@ -145,8 +150,7 @@ extern "C" vio_status vio_frontend_create(vio_frontend** out, const vio_params* 
     ptrs[i] = q;
     q += align256(sizes[i]);
   }
-  fe->pyr[0] = (uint8_t*)ptrs[0];
-  fe->pyr[1] = (uint8_t*)ptrs[1];
+  for (int i = 0; i < 3; ++i) fe->pyr[i] = (uint8_t*)ptrs[0] + (size_t)i * L.upper_bytes * nl;
   fe->list_xy = (float*)ptrs[2];
   fe->list_id = (int32_t*)ptrs[3];
   fe->list_count = (int32_t*)ptrs[4];
@@ -159,8 +163,10 @@ extern "C" vio_status vio_frontend_create(vio_frontend** out, const vio_params* 
   fe->tune = vio::FrameTune{128, 0, 0, 0, 256};
   fe->trk_xy = (float*)ptrs[9];
   fe->trk_status = (uint8_t*)ptrs[10];
-  fe->cand = (unsigned long long*)ptrs[11];
-  fe->cand_count = (int32_t*)ptrs[12];
+  for (int i = 0; i < 2; ++i) {
+    fe->cand[i] = (unsigned long long*)ptrs[11] + (size_t)i * ns * nc * kk;
+    fe->cand_count[i] = (int32_t*)ptrs[12] + (size_t)i * ns * nc;
+  }
   fe->spec_xy = (float*)ptrs[13];
   fe->spec_status = (uint8_t*)ptrs[14];
   fe->occupancy = (uint8_t*)ptrs[15];
@@ -178,6 +184,7 @@ extern "C" vio_status vio_frontend_create(vio_frontend** out, const vio_params* 
   }
   fe->cur_list = 0;
   fe->cur_pyr = 0;
+  fe->prev_pyr = 0;
   fe->have_prev = false;
   fe->prev_frames = nullptr;
   fe->prev_pitch = 0;
@@ -193,6 +200,13 @@ extern "C" vio_status vio_frontend_destroy(vio_frontend* fe) {
   for (auto& row : fe->ev_rec)
     for (cudaEvent_t e : row) cudaEventDestroy(e);
   for (cudaEvent_t e : fe->ev_free) cudaEventDestroy(e);
+  if (fe->side) {
+    cudaStreamSynchronize(fe->side);
+    cudaStreamDestroy(fe->side);
+    cudaEventDestroy(fe->ev_entry);
+    for (cudaEvent_t e : fe->ev_front) cudaEventDestroy(e);
+    for (cudaEvent_t e : fe->ev_back) cudaEventDestroy(e);
+  }
   cudaFree(fe->d_mem);
   delete fe;
   return VIO_OK;
@@ -245,36 +259,33 @@ extern "C" vio_status vio_frontend_set_initnet(vio_frontend* fe, const void* d_p
   return VIO_OK;
 }
 
-extern "C" vio_status vio_frontend_step(vio_frontend* fe, const uint8_t* d_frames,
-                                        int32_t pitch, int64_t frame_stride, void* stream) {
+namespace {
+
+// The launch description of the frontend's next step on frames d_frames
+// (pyramid ring slot, candidate buffers and step-count copy of its parity).
+vio_status next_launch(vio_frontend* fe, const uint8_t* d_frames, int32_t pitch,
+                       int64_t frame_stride, vio::FrameLaunch& f) {
   using namespace vio;
   if (!fe || !d_frames || pitch < fe->w || frame_stride < (int64_t)pitch * fe->h)
     return VIO_ERR_INVALID_ARG;
   if (fe->have_prev && fe->prev_pitch != pitch) return VIO_ERR_UNSUPPORTED;
-  cudaStream_t s = (cudaStream_t)stream;
   const int ns = fe->n_streams;
   vio_pyr_layout L;
   vio_status st = vio_pyr_layout_make(fe->w, fe->h, fe->p.n_levels, pitch, &L);
   if (st != VIO_OK) return st;
   const long long ub = L.upper_bytes;
-  const int cur = fe->cur_pyr, prv = cur ^ 1;
-  const int li = fe->cur_list, lo = li ^ 1;
-
-  std::array<cudaEvent_t, VIO_N_STAGES + 1> ev{};
-  if (fe->timing)
-    for (auto& e : ev)
-      if (!(e = take_event(fe))) return VIO_ERR_CUDA;
-
-  FrameLaunch f{};
+  const int par = (int)(fe->steps & 1);
+  f = FrameLaunch{};
   f.p = fe->p;
   f.g = make_geom(L);
   f.n_streams = ns;
   f.cap = fe->capacity;
-  f.cur = Batch{d_frames, frame_stride, fe->pyr[cur], ub, 2 * ns};
-  f.prev = fe->have_prev ? Batch{fe->prev_frames, fe->prev_stride, fe->pyr[prv], ub, 2 * ns}
-                         : f.cur;
+  f.cur = Batch{d_frames, frame_stride, fe->pyr[fe->cur_pyr], ub, 2 * ns};
+  f.prev = fe->have_prev
+               ? Batch{fe->prev_frames, fe->prev_stride, fe->pyr[fe->prev_pyr], ub, 2 * ns}
+               : f.cur;
   f.slotted = 0;
-  f.host_parity = li;
+  f.host_parity = fe->cur_list;
   f.host_have_prev = fe->have_prev ? 1 : 0;
   f.list_xy = fe->list_xy;
   f.list_id = fe->list_id;
@@ -282,8 +293,8 @@ extern "C" vio_status vio_frontend_step(vio_frontend* fe, const uint8_t* d_frame
   f.list_status = fe->list_status;
   f.trk_xy = fe->trk_xy;
   f.trk_status = fe->trk_status;
-  f.cand = fe->cand;
-  f.cand_count = fe->cand_count;
+  f.cand = fe->cand[par];
+  f.cand_count = fe->cand_count[par];
   f.spec_xy = fe->spec_xy;
   f.spec_status = fe->spec_status;
   f.new_xy = fe->new_xy;
@@ -292,6 +303,7 @@ extern "C" vio_status vio_frontend_step(vio_frontend* fe, const uint8_t* d_frame
   f.occupancy = fe->occupancy;
   f.stats = fe->stats;
   f.step_ctr = fe->step_ctr;
+  f.ctr_copy = fe->step_ctr + 1 + par;
   if (fe->net) {
     f.net = fe->net;
     f.net_la = fe->net_cfg.level_a;
@@ -301,17 +313,38 @@ extern "C" vio_status vio_frontend_step(vio_frontend* fe, const uint8_t* d_frame
     f.net_out = fe->net_out;
     f.trk_learned = fe->trk_learned;
   }
-  if (launch_frames(&f, 1, fe->tune, s, fe->timing ? ev.data() : nullptr) != cudaSuccess)
-    return VIO_ERR_CUDA;
-  if (fe->timing) fe->ev_rec.push_back(ev);
+  return VIO_OK;
+}
 
-  fe->cur_list = lo;
-  fe->cur_pyr = prv;
+// Host state after a step on frames d_frames has been enqueued.
+void advance(vio_frontend* fe, const uint8_t* d_frames, int32_t pitch, int64_t frame_stride) {
+  fe->cur_list ^= 1;
+  fe->prev_pyr = fe->cur_pyr;
+  fe->cur_pyr = (fe->cur_pyr + 1) % 3;
   fe->have_prev = true;
   fe->prev_frames = d_frames;
   fe->prev_pitch = pitch;
   fe->prev_stride = frame_stride;
   ++fe->steps;
+}
+
+}  // namespace
+
+extern "C" vio_status vio_frontend_step(vio_frontend* fe, const uint8_t* d_frames,
+                                        int32_t pitch, int64_t frame_stride, void* stream) {
+  using namespace vio;
+  FrameLaunch f;
+  const vio_status st = next_launch(fe, d_frames, pitch, frame_stride, f);
+  if (st != VIO_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  std::array<cudaEvent_t, VIO_N_STAGES + 1> ev{};
+  if (fe->timing)
+    for (auto& e : ev)
+      if (!(e = take_event(fe))) return VIO_ERR_CUDA;
+  if (launch_frames(&f, 1, fe->tune, s, fe->timing ? ev.data() : nullptr) != cudaSuccess)
+    return VIO_ERR_CUDA;
+  if (fe->timing) fe->ev_rec.push_back(ev);
+  advance(fe, d_frames, pitch, frame_stride);
   return VIO_OK;
 }
 
@@ -350,13 +383,53 @@ extern "C" vio_status vio_frontend_step_host(vio_frontend* fe, const uint8_t* h_
 extern "C" vio_status vio_frontend_run(vio_frontend* fe, const uint8_t* d_frames, int32_t pitch,
                                        int64_t frame_stride, int64_t step_stride,
                                        int32_t n_steps, void* stream) {
+  using namespace vio;
   if (!fe || !d_frames || n_steps < 0 || step_stride < 0) return VIO_ERR_INVALID_ARG;
   if (n_steps > 1 && step_stride < (int64_t)2 * fe->n_streams * frame_stride)
     return VIO_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  // Pipelined steps: the front of step t (pyramids and detection candidates
+  // of its own frames) runs on a side stream beside the tracking and
+  // finalisation of step t-1; it waits for the end of step t-2, the last
+  // reader of its pyramid ring slot and candidate buffers. Stage timing keeps
+  // the steps whole.
+  const bool pipe = n_steps > 1 && !fe->timing;
+  if (pipe && !fe->side) {
+    if (cudaStreamCreateWithFlags(&fe->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&fe->ev_entry, cudaEventDisableTiming) != cudaSuccess)
+      return VIO_ERR_CUDA;
+    for (cudaEvent_t& e : fe->ev_front)
+      if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess)
+        return VIO_ERR_CUDA;
+    for (cudaEvent_t& e : fe->ev_back)
+      if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess)
+        return VIO_ERR_CUDA;
+  }
+  if (pipe) {
+    // everything already on the caller's stream comes first
+    if (cudaEventRecord(fe->ev_entry, s) != cudaSuccess ||
+        cudaStreamWaitEvent(fe->side, fe->ev_entry, 0) != cudaSuccess)
+      return VIO_ERR_CUDA;
+  }
   for (int32_t i = 0; i < n_steps; ++i) {
-    const vio_status st = vio_frontend_step(fe, d_frames + (int64_t)i * step_stride, pitch,
-                                            frame_stride, stream);
+    const uint8_t* fr = d_frames + (int64_t)i * step_stride;
+    if (!pipe) {
+      const vio_status st = vio_frontend_step(fe, fr, pitch, frame_stride, stream);
+      if (st != VIO_OK) return st;
+      continue;
+    }
+    FrameLaunch f;
+    const vio_status st = next_launch(fe, fr, pitch, frame_stride, f);
     if (st != VIO_OK) return st;
+    if (i >= 2 && cudaStreamWaitEvent(fe->side, fe->ev_back[(i - 2) % 3], 0) != cudaSuccess)
+      return VIO_ERR_CUDA;
+    if (launch_frames(&f, 1, fe->tune, fe->side, nullptr, 1) != cudaSuccess ||
+        cudaEventRecord(fe->ev_front[i % 2], fe->side) != cudaSuccess ||
+        cudaStreamWaitEvent(s, fe->ev_front[i % 2], 0) != cudaSuccess ||
+        launch_frames(&f, 1, fe->tune, s, nullptr, 2) != cudaSuccess ||
+        cudaEventRecord(fe->ev_back[i % 3], s) != cudaSuccess)
+      return VIO_ERR_CUDA;
+    advance(fe, fr, pitch, frame_stride);
   }
   return VIO_OK;
 }

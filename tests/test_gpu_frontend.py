@@ -126,6 +126,41 @@ def test_frontend_reset_and_two_streams():
     assert (fe.view()["track_count"] == 0).all()
 
 
+@pytest.mark.parametrize("learned", [False, True])
+def test_frontend_pipelined_run_equals_steps(learned):
+    """vio_frontend_run without stage timing overlaps the front of each step
+    (pyramids, detection) with the tracking of the step before: same lists,
+    ids and stats as one step at a time, also across several run calls."""
+    w, h, L = 376, 240, 4
+    n = 11
+    seq = synth.make_sequence(5007, n, w, h, 1, max_motion=6.0, tex_size=1024)
+    p = vio.default_params(n_levels=L, cell_w=47, cell_h=40)
+    cap = 2 * (w // 47) * (h // 40)
+    frames = torch.from_numpy(seq.frames).cuda().view(n, 1, 2, h, w)
+    a, b = vio.Frontend(p, w, h, 1, cap), vio.Frontend(p, w, h, 1, cap)
+    if learned:
+        from paper_2609_30459_gb300 import initnet_train
+        net = vio.InitNet.load(initnet_train.DEFAULT_WEIGHTS)
+        a.set_initnet(net)
+        b.set_initnet(net)
+    for t in range(n):
+        a.step(frames[t])
+    b.run(frames[:4].contiguous())
+    b.run(frames[4:].contiguous())
+    torch.cuda.synchronize()
+    va, vb = a.view(), b.view()
+    assert torch.equal(va["track_count"], vb["track_count"])
+    for c in range(2):
+        nc = int(va["track_count"][0, c])
+        assert nc > 0
+        assert torch.equal(va["track_xy"][0, c, :nc], vb["track_xy"][0, c, :nc])
+        assert torch.equal(va["track_id"][0, c, :nc], vb["track_id"][0, c, :nc])
+    assert torch.equal(va["new_count"], vb["new_count"])
+    sa, na = a.read_stats()
+    sb, nb = b.read_stats()
+    assert na == nb == n and np.array_equal(sa[:n], sb[:n])
+
+
 def test_frontend_run_equals_steps():
     w, h, L = 376, 240, 3
     seq = synth.make_sequence(5003, 6, w, h, 1, max_motion=5.0, tex_size=1024)
