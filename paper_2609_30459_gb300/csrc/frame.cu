@@ -708,14 +708,6 @@ K1Args front_args(const vio_params& p, const Geom& g, const Batch& all, int det_
 
 template <int NT, bool MASKED>
 cudaError_t launch_k1_nt(const MultiK1& mm, int smem, cudaStream_t s) {
-  static bool carveout = false;   // as much shared memory as the SM has: more CTAs
-  if (!carveout) {
-    const cudaError_t e = cudaFuncSetAttribute(frame_front_kernel<NT, MASKED>,
-                                               cudaFuncAttributePreferredSharedMemoryCarveout,
-                                               (int)cudaSharedmemCarveoutMaxShared);
-    if (e != cudaSuccess) return e;
-    carveout = true;
-  }
   if (smem > 48 * 1024) {
     const cudaError_t e = cudaFuncSetAttribute(
         frame_front_kernel<NT, MASKED>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
