@@ -550,14 +550,16 @@ def autotune_frontend(torch, fe, frames, n=40):
     for k2, shift, first, k1 in itertools.product((64, 128, 256), (-1, 0, 1), (0, 1, 2),
                                                   (128, 256)):
         fe.set_tune(k2, shift, first, k1)
-        fe.reset()
-        fe.run(frames5[:3])
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        fe.run(frames5[3:3 + n])
-        e1.record()
-        torch.cuda.synchronize()
-        t = e0.elapsed_time(e1)
+        t = None
+        for rep in range(2):                   # the better of two passes
+            fe.reset()
+            fe.run(frames5[:3])
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fe.run(frames5[3:3 + n])
+            e1.record()
+            torch.cuda.synchronize()
+            t = e0.elapsed_time(e1) if t is None else min(t, e0.elapsed_time(e1))
         if best_t is None or t < best_t:
             best, best_t = (k2, shift, first, k1), t
     fe.set_tune(*best)

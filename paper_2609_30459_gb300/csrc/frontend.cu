@@ -50,8 +50,9 @@ struct vio_frontend {
   // host state
   int cur_list;
   int cur_pyr, prev_pyr;
-  cudaStream_t side = nullptr;   // fronts of pipelined steps (vio_frontend_run)
-  cudaEvent_t ev_entry = nullptr, ev_front[2] = {}, ev_back[3] = {};
+  cudaStream_t side = nullptr;   // fronts of pipelined steps (vio_frontend_run), low priority
+  cudaStream_t main_s = nullptr; // the rest of those steps, high priority (the critical path)
+  cudaEvent_t ev_entry = nullptr, ev_exit = nullptr, ev_front[2] = {}, ev_back[3] = {};
   bool have_prev;
   const uint8_t* prev_frames;
   int32_t prev_pitch;
@@ -202,8 +203,11 @@ extern "C" vio_status vio_frontend_destroy(vio_frontend* fe) {
   for (cudaEvent_t e : fe->ev_free) cudaEventDestroy(e);
   if (fe->side) {
     cudaStreamSynchronize(fe->side);
+    cudaStreamSynchronize(fe->main_s);
     cudaStreamDestroy(fe->side);
+    cudaStreamDestroy(fe->main_s);
     cudaEventDestroy(fe->ev_entry);
+    cudaEventDestroy(fe->ev_exit);
     for (cudaEvent_t e : fe->ev_front) cudaEventDestroy(e);
     for (cudaEvent_t e : fe->ev_back) cudaEventDestroy(e);
   }
@@ -389,14 +393,20 @@ extern "C" vio_status vio_frontend_run(vio_frontend* fe, const uint8_t* d_frames
     return VIO_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   // Pipelined steps: the front of step t (pyramids and detection candidates
-  // of its own frames) runs on a side stream beside the tracking and
-  // finalisation of step t-1; it waits for the end of step t-2, the last
-  // reader of its pyramid ring slot and candidate buffers. Stage timing keeps
-  // the steps whole.
+  // of its own frames) runs on a low-priority side stream beside the tracking
+  // and finalisation of step t-1 (on a high-priority stream: the critical
+  // path); it waits for the end of step t-2, the last reader of its pyramid
+  // ring slot and candidate buffers. The caller's stream waits for the last
+  // step. Stage timing keeps the steps whole.
   const bool pipe = n_steps > 1 && !fe->timing;
   if (pipe && !fe->side) {
-    if (cudaStreamCreateWithFlags(&fe->side, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreateWithFlags(&fe->ev_entry, cudaEventDisableTiming) != cudaSuccess)
+    int least = 0, greatest = 0;
+    if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess ||
+        cudaStreamCreateWithPriority(&fe->side, cudaStreamNonBlocking, least) != cudaSuccess ||
+        cudaStreamCreateWithPriority(&fe->main_s, cudaStreamNonBlocking, greatest) !=
+            cudaSuccess ||
+        cudaEventCreateWithFlags(&fe->ev_entry, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&fe->ev_exit, cudaEventDisableTiming) != cudaSuccess)
       return VIO_ERR_CUDA;
     for (cudaEvent_t& e : fe->ev_front)
       if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess)
@@ -408,9 +418,11 @@ extern "C" vio_status vio_frontend_run(vio_frontend* fe, const uint8_t* d_frames
   if (pipe) {
     // everything already on the caller's stream comes first
     if (cudaEventRecord(fe->ev_entry, s) != cudaSuccess ||
-        cudaStreamWaitEvent(fe->side, fe->ev_entry, 0) != cudaSuccess)
+        cudaStreamWaitEvent(fe->side, fe->ev_entry, 0) != cudaSuccess ||
+        cudaStreamWaitEvent(fe->main_s, fe->ev_entry, 0) != cudaSuccess)
       return VIO_ERR_CUDA;
   }
+  cudaStream_t ms = pipe ? fe->main_s : s;
   for (int32_t i = 0; i < n_steps; ++i) {
     const uint8_t* fr = d_frames + (int64_t)i * step_stride;
     if (!pipe) {
@@ -425,12 +437,15 @@ extern "C" vio_status vio_frontend_run(vio_frontend* fe, const uint8_t* d_frames
       return VIO_ERR_CUDA;
     if (launch_frames(&f, 1, fe->tune, fe->side, nullptr, 1) != cudaSuccess ||
         cudaEventRecord(fe->ev_front[i % 2], fe->side) != cudaSuccess ||
-        cudaStreamWaitEvent(s, fe->ev_front[i % 2], 0) != cudaSuccess ||
-        launch_frames(&f, 1, fe->tune, s, nullptr, 2) != cudaSuccess ||
-        cudaEventRecord(fe->ev_back[i % 3], s) != cudaSuccess)
+        cudaStreamWaitEvent(ms, fe->ev_front[i % 2], 0) != cudaSuccess ||
+        launch_frames(&f, 1, fe->tune, ms, nullptr, 2) != cudaSuccess ||
+        cudaEventRecord(fe->ev_back[i % 3], ms) != cudaSuccess)
       return VIO_ERR_CUDA;
     advance(fe, fr, pitch, frame_stride);
   }
+  if (pipe && (cudaEventRecord(fe->ev_exit, ms) != cudaSuccess ||
+               cudaStreamWaitEvent(s, fe->ev_exit, 0) != cudaSuccess))
+    return VIO_ERR_CUDA;
   return VIO_OK;
 }
 
