@@ -430,6 +430,25 @@ __global__ void __launch_bounds__(K3_THREADS)
     if (t < VIO_N_STATS) st[t] = 0;
     return;
   }
+  // the inputs of part 2 for this thread's first cell and its first
+  // candidate, loaded now: they do not depend on part 1
+  const long long cbase = (long long)s * n_cells;
+  const int crun = (n_cells + K3_THREADS - 1) / K3_THREADS;
+  const int pc = t * crun;
+  const int id0 = f.next_id[s];
+  int pre_nc = 0, pre_sst = 0;
+  unsigned long long pre_key = 0;
+  float pre_sx = 0.f, pre_sy = 0.f;
+  if (pc < n_cells) {
+    const long long q = (cbase + pc) * k;
+    pre_nc = f.cand_count[cbase + pc];
+    pre_key = f.cand[q];
+    if (!f.stereo_after) {
+      pre_sst = f.spec_status[q];
+      pre_sx = f.spec_xy[2 * q];
+      pre_sy = f.spec_xy[2 * q + 1];
+    }
+  }
   __shared__ int learned_s;
   for (int i = t; i < n_cells; i += K3_THREADS) occ_s[i] = 0;
   if (t == 0) learned_s = 0;
@@ -451,6 +470,35 @@ __global__ void __launch_bounds__(K3_THREADS)
     const int rl = min(kRunMax, run - r0);
     const int first = t * run + r0;
     unsigned keep0 = 0, keep1 = 0;
+    // positions and ids of the first two entries, loaded with their status
+    float ax0 = 0.f, ay0 = 0.f, ax1 = 0.f, ay1 = 0.f, bx0 = 0.f, by0 = 0.f, bx1 = 0.f, by1 = 0.f;
+    int aid0 = 0, aid1 = 0, bid0 = 0, bid1 = 0;
+    if (rl > 0) {
+      const int i = first;
+      if (i < n0) {
+        ax0 = f.trk_xy[2 * (trk0 + i)];
+        ay0 = f.trk_xy[2 * (trk0 + i) + 1];
+        aid0 = f.list_id[in0 + i];
+      }
+      if (i < n1) {
+        ax1 = f.trk_xy[2 * (trk0 + cap + i)];
+        ay1 = f.trk_xy[2 * (trk0 + cap + i) + 1];
+        aid1 = f.list_id[in0 + cap + i];
+      }
+    }
+    if (rl > 1) {
+      const int i = first + 1;
+      if (i < n0) {
+        bx0 = f.trk_xy[2 * (trk0 + i)];
+        by0 = f.trk_xy[2 * (trk0 + i) + 1];
+        bid0 = f.list_id[in0 + i];
+      }
+      if (i < n1) {
+        bx1 = f.trk_xy[2 * (trk0 + cap + i)];
+        by1 = f.trk_xy[2 * (trk0 + cap + i) + 1];
+        bid1 = f.list_id[in0 + cap + i];
+      }
+    }
     for (int j = 0; j < rl; ++j) {
       const int i = first + j;
       if (i < n0 && f.trk_status[trk0 + i] == VIO_TRACK_OK) keep0 |= 1u << j;
@@ -466,11 +514,12 @@ __global__ void __launch_bounds__(K3_THREADS)
     for (int j = 0; j < rl; ++j) {
       const int i = first + j;
       if (keep0 & (1u << j)) {
-        const float x = f.trk_xy[2 * (trk0 + i)], y = f.trk_xy[2 * (trk0 + i) + 1];
+        const float x = j == 0 ? ax0 : (j == 1 ? bx0 : f.trk_xy[2 * (trk0 + i)]);
+        const float y = j == 0 ? ay0 : (j == 1 ? by0 : f.trk_xy[2 * (trk0 + i) + 1]);
         const long long d = out0 + o0++;
         f.list_xy[2 * d] = x;
         f.list_xy[2 * d + 1] = y;
-        f.list_id[d] = f.list_id[in0 + i];
+        f.list_id[d] = j == 0 ? aid0 : (j == 1 ? bid0 : f.list_id[in0 + i]);
         if (x >= 0.f && y >= 0.f) {
           const int cx = cell_of(x, f.p.cell_w), cy = cell_of(y, f.p.cell_h);
           if (cx < gx && cy < gy) atomicAdd(&occ_s[cy * gx + cx], 1);
@@ -478,9 +527,10 @@ __global__ void __launch_bounds__(K3_THREADS)
       }
       if (keep1 & (1u << j)) {
         const long long d = out0 + cap + o1++;
-        f.list_xy[2 * d] = f.trk_xy[2 * (trk0 + cap + i)];
-        f.list_xy[2 * d + 1] = f.trk_xy[2 * (trk0 + cap + i) + 1];
-        f.list_id[d] = f.list_id[in0 + cap + i];
+        f.list_xy[2 * d] = j == 0 ? ax1 : (j == 1 ? bx1 : f.trk_xy[2 * (trk0 + cap + i)]);
+        f.list_xy[2 * d + 1] =
+            j == 0 ? ay1 : (j == 1 ? by1 : f.trk_xy[2 * (trk0 + cap + i) + 1]);
+        f.list_id[d] = j == 0 ? aid1 : (j == 1 ? bid1 : f.list_id[in0 + cap + i]);
       }
     }
     surv0 += tot & 0xffff;
@@ -492,10 +542,7 @@ __global__ void __launch_bounds__(K3_THREADS)
 
   // 2. per cell: selection (k_eff = k - occupancy), matched subset, and the
   //    candidates matched; three counts packed in 21-bit fields
-  const int id0 = f.next_id[s];
   const long long bn = (long long)s * cap;
-  const long long cbase = (long long)s * n_cells;
-  const int crun = (n_cells + K3_THREADS - 1) / K3_THREADS;
   int new_tot = 0, m_tot = 0, c_tot = 0;
   for (int r0 = 0; r0 < crun; r0 += kRunMax) {
     const int rl = min(kRunMax, crun - r0);
@@ -504,13 +551,16 @@ __global__ void __launch_bounds__(K3_THREADS)
     for (int j = 0; j < rl; ++j) {
       const int cell = first + j;
       if (cell >= n_cells) break;
-      const int nc = f.cand_count[cbase + cell];
+      const bool pre = r0 == 0 && j == 0;   // the prefetched cell
+      const int nc = pre ? pre_nc : f.cand_count[cbase + cell];
       const int occ = min(occ_s[cell], 255);
       f.occupancy[cbase + cell] = (uint8_t)occ;
       const int nsel = max(0, min(k - occ, nc));
       int nm = 0;
       if (!f.stereo_after)
-        for (int r = 0; r < nsel; ++r) nm += f.spec_status[(cbase + cell) * k + r] == VIO_TRACK_OK;
+        for (int r = 0; r < nsel; ++r)
+          nm += (pre && r == 0 ? pre_sst : (int)f.spec_status[(cbase + cell) * k + r]) ==
+                VIO_TRACK_OK;
       packed += (unsigned long long)nsel | ((unsigned long long)nm << 21) |
                 ((unsigned long long)nc << 42);
     }
@@ -521,11 +571,13 @@ __global__ void __launch_bounds__(K3_THREADS)
     for (int j = 0; j < rl; ++j) {
       const int cell = first + j;
       if (cell >= n_cells) break;
+      const bool pre = r0 == 0 && j == 0;
       const int occ = min(occ_s[cell], 255);
-      const int nsel = max(0, min(k - occ, (int)f.cand_count[cbase + cell]));
+      const int nsel = max(0, min(k - occ, pre ? pre_nc : (int)f.cand_count[cbase + cell]));
       for (int r = 0; r < nsel; ++r, ++o) {
         const long long q = (cbase + cell) * k + r;
-        const unsigned idx = ~(unsigned)(f.cand[q] & 0xffffffffu);
+        const bool pr = pre && r == 0;
+        const unsigned idx = ~(unsigned)((pr ? pre_key : f.cand[q]) & 0xffffffffu);
         const float x = (float)(idx % (unsigned)W), y = (float)(idx / (unsigned)W);
         if (o < f.cap) {
           f.new_xy[2 * (bn + o)] = x;
@@ -537,11 +589,11 @@ __global__ void __launch_bounds__(K3_THREADS)
           f.list_xy[2 * (out0 + o0) + 1] = y;
           f.list_id[out0 + o0] = id0 + o;
         }
-        if (!f.stereo_after && f.spec_status[q] == VIO_TRACK_OK) {
+        if (!f.stereo_after && (pr ? pre_sst : (int)f.spec_status[q]) == VIO_TRACK_OK) {
           const int o1 = surv1 + om++;
           if (o1 < f.cap) {
-            f.list_xy[2 * (out0 + cap + o1)] = f.spec_xy[2 * q];
-            f.list_xy[2 * (out0 + cap + o1) + 1] = f.spec_xy[2 * q + 1];
+            f.list_xy[2 * (out0 + cap + o1)] = pr ? pre_sx : f.spec_xy[2 * q];
+            f.list_xy[2 * (out0 + cap + o1) + 1] = pr ? pre_sy : f.spec_xy[2 * q + 1];
             f.list_id[out0 + cap + o1] = id0 + o;
           }
         }
