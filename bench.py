@@ -300,7 +300,7 @@ def frontend_config_run(torch, vio, name, w, h, n_streams, levels, cw, ch, n_fra
     cap = 2 * (w // cw) * (h // ch) * p.k_per_cell
     fe = vio.Frontend(p, w, h, n_streams, cap)
     best = None
-    for k2 in (64, 128, 256):
+    for k2 in (32, 64, 128, 256):
         for first in (0, 2):
             for k1 in (128, 256):
                 fe.set_tune(k2, 0, first, k1)
@@ -547,7 +547,7 @@ def autotune_frontend(torch, fe, frames, n=40):
     import itertools
     frames5 = frames.view(N_FRAMES, 1, 2, H, W)
     best, best_t = None, None
-    for k2, shift, first, k1 in itertools.product((64, 128, 256), (-1, 0, 1), (0, 1, 2),
+    for k2, shift, first, k1 in itertools.product((32, 64, 128, 256), (-1, 0, 1), (0, 1, 2),
                                                   (128, 256)):
         fe.set_tune(k2, shift, first, k1)
         t = None

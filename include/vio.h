@@ -402,8 +402,9 @@ typedef struct {
   int32_t capacity;    /* keypoint slots per camera (gx*gy*k..32767)       */
 } vio_stream_group;
 
-/* Tunables of a batch step: threads per block of the tracking launches (64,
- * 128, 256 or 512), the pyramid tile scale (-1, 0, 1: half, default, double
+/* Tunables of a batch step: threads per block of the tracking launches (32,
+ * 64, 128, 256 or 512; one warp tracks one keypoint, so small blocks spread
+ * the warps evenly over the SMs), the pyramid tile scale (-1, 0, 1: half, default, double
  * the deepest-level tile side), the order of stereo matching (0: every
  * cell's candidates are matched beside temporal tracking; 1: only the
  * selected keypoints are matched, after selection, in two more launches),
@@ -446,7 +447,7 @@ vio_status vio_batch_set_graph(vio_batch* b, int32_t enable);
 vio_status vio_batch_set_tune(vio_batch* b, const vio_batch_tune* t);
 vio_status vio_batch_get_tune(vio_batch* b, vio_batch_tune* t);
 
-/* Times every tunable combination (144) over `reps` pairs of steps (a first frame,
+/* Times every tunable combination (180) over `reps` pairs of steps (a first frame,
  * then a tracked frame, all streams active) on the frames the caller has put
  * in BOTH slots of every stream, keeps the fastest, and resets every stream.
  * *best_ms: the chosen combination's time per tracked step. Blocking. */

@@ -368,8 +368,8 @@ extern "C" vio_status vio_batch_set_graph(vio_batch* b, int32_t enable) {
 
 extern "C" vio_status vio_batch_set_tune(vio_batch* b, const vio_batch_tune* t) {
   if (!b || !t) return VIO_ERR_INVALID_ARG;
-  if (t->k2_threads != 64 && t->k2_threads != 128 && t->k2_threads != 256 &&
-      t->k2_threads != 512)
+  if (t->k2_threads != 32 && t->k2_threads != 64 && t->k2_threads != 128 &&
+      t->k2_threads != 256 && t->k2_threads != 512)
     return VIO_ERR_INVALID_ARG;
   if (t->pyr_tile_shift < -1 || t->pyr_tile_shift > 1) return VIO_ERR_INVALID_ARG;
   if (t->stereo_after_select != 0 && t->stereo_after_select != 1) return VIO_ERR_INVALID_ARG;
@@ -426,14 +426,14 @@ extern "C" vio_status vio_batch_autotune(vio_batch* b, int32_t reps, void* strea
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
     return VIO_ERR_CUDA;
-  const int threads[4] = {64, 128, 256, 512};
+  const int threads[5] = {32, 64, 128, 256, 512};
   float best = 1e30f;
   vio::FrameTune best_t = b->tune;
   vio_status st = VIO_OK;
   const int firsts[3] = {0, 2, 1};
-  for (int combo = 0; combo < 144 && st == VIO_OK; ++combo) {
-    const int ti = combo % 4, shift = (combo / 4) % 3 - 1, after = (combo / 12) % 2;
-    const int first = firsts[(combo / 24) % 3], k1 = combo < 72 ? 256 : 128;
+  for (int combo = 0; combo < 180 && st == VIO_OK; ++combo) {
+    const int ti = combo % 5, shift = (combo / 5) % 3 - 1, after = (combo / 15) % 2;
+    const int first = firsts[(combo / 30) % 3], k1 = combo < 90 ? 256 : 128;
     {
       b->tune = vio::FrameTune{threads[ti], shift, after, first, k1, best_t.det_warps};
       float total = 0.f;

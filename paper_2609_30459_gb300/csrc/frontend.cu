@@ -237,8 +237,8 @@ extern "C" int32_t vio_frontend_launches_per_step(const vio_frontend* fe) {
 
 extern "C" vio_status vio_frontend_set_tune(vio_frontend* fe, const vio_batch_tune* t) {
   if (!fe || !t) return VIO_ERR_INVALID_ARG;
-  if (t->k2_threads != 64 && t->k2_threads != 128 && t->k2_threads != 256 &&
-      t->k2_threads != 512)
+  if (t->k2_threads != 32 && t->k2_threads != 64 && t->k2_threads != 128 &&
+      t->k2_threads != 256 && t->k2_threads != 512)
     return VIO_ERR_INVALID_ARG;
   if (t->pyr_tile_shift < -1 || t->pyr_tile_shift > 1 || t->stereo_after_select != 0 ||
       t->pyr_first_levels < 0 || t->pyr_first_levels > 4 ||

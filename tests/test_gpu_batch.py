@@ -129,7 +129,7 @@ def test_batch_graph_replay_and_autotune():
         best = b.autotune(reps=1, stream=s)
         assert best > 0
         k2, shift, after, first, k1, dw = b.get_tune()
-        assert k2 in (64, 128, 256, 512) and shift in (-1, 0, 1) and after in (0, 1)
+        assert k2 in (32, 64, 128, 256, 512) and shift in (-1, 0, 1) and after in (0, 1)
         assert first in (0, 1, 2) and k1 in (128, 256)
         b.set_graph(True)
         schedule = [[1] * total for _ in range(N_FRAMES)]

@@ -379,7 +379,7 @@ def test_step_host_equals_step_and_view():
 
 
 @pytest.mark.parametrize("tune", [(64, -1, 1, 128), (256, 1, 2, 256), (128, 0, 0, 128, 1),
-                                  (128, 0, 0, 256, 8)])
+                                  (128, 0, 0, 256, 8), (32, 0, 0, 128)])
 def test_frontend_tune_does_not_change_results(tune):
     w, h, L = 376, 240, 4
     seq = synth.make_sequence(5013, 5, w, h, 1, max_motion=6.0, tex_size=1024)
