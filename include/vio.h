@@ -274,7 +274,10 @@ vio_status vio_frontend_step(vio_frontend* fe, const uint8_t* d_frames, int32_t 
 /* n_steps consecutive steps over frames already in device memory: step i
  * reads d_frames + i * step_stride (same layout as vio_frontend_step). One
  * call enqueues every step (no host work between frames); the usual keep-alive
- * rule applies to the last frame. */
+ * rule applies to the last frame. Without stage timing the steps are
+ * pipelined on the frontend's own streams (the pyramids and detection of
+ * frame i beside the tracking of frame i-1); they follow the work already on
+ * `stream`, and `stream` waits for the last of them. */
 vio_status vio_frontend_run(vio_frontend* fe, const uint8_t* d_frames, int32_t pitch,
                             int64_t frame_stride, int64_t step_stride, int32_t n_steps,
                             void* stream);
@@ -295,6 +298,23 @@ vio_status vio_frontend_step_host(vio_frontend* fe, const uint8_t* h_frames, uin
                                   int32_t pitch, int64_t frame_stride, float* h_track_xy,
                                   int32_t* h_track_id, int32_t* h_track_count, float* h_new_xy,
                                   int32_t* h_new_count, void* stream);
+
+/* The same step, pipelined across calls: the upload, pyramids and detection
+ * of this step run on the frontend's own low-priority stream beside the
+ * tracking of the previous step, the rest on its own high-priority stream,
+ * and `done_event` (a cudaEvent_t of the caller, may be NULL) is recorded
+ * when the host buffers hold this step's results. The call orders itself
+ * after the frontend's own earlier work, and after work the frontend's other
+ * calls put on a caller's stream (those in turn wait for the pipelined
+ * steps), but not after other work on any caller stream: upload nothing the
+ * step reads on another stream without synchronising first. d_frames must
+ * stay untouched until done_event of the next step (which reads it as the
+ * previous frame). Not with stage timing (VIO_ERR_UNSUPPORTED). */
+vio_status vio_frontend_step_host_async(vio_frontend* fe, const uint8_t* h_frames,
+                                        uint8_t* d_frames, int32_t pitch, int64_t frame_stride,
+                                        float* h_track_xy, int32_t* h_track_id,
+                                        int32_t* h_track_count, float* h_new_xy,
+                                        int32_t* h_new_count, void* done_event);
 
 /* Device views of the frontend's outputs after the last step, per stream s
  * and camera c at slot base (2*s + c) * capacity:

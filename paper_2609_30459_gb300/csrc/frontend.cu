@@ -37,8 +37,8 @@ struct vio_frontend {
   float* spec_xy;             // stereo matches of the candidates
   uint8_t* spec_status;
   uint8_t* occupancy;         // n_streams * cells
-  float* new_xy;              // n_streams * capacity
-  int32_t* new_count;         // n_streams
+  float* new_xy[2];           // n_streams * capacity, per output list parity
+  int32_t* new_count[2];      // n_streams, per output list parity
   int32_t* next_id;           // n_streams
   int32_t* stats;             // VIO_STATS_RING * n_streams * VIO_N_STATS
   int32_t* step_ctr;          // device count of launched steps, then its copy per parity
@@ -52,7 +52,12 @@ struct vio_frontend {
   int cur_pyr, prev_pyr;
   cudaStream_t side = nullptr;   // fronts of pipelined steps (vio_frontend_run), low priority
   cudaStream_t main_s = nullptr; // the rest of those steps, high priority (the critical path)
+  cudaStream_t copy_s = nullptr; // read-back of pipelined host steps
+  cudaEvent_t ev_copied[2] = {}; // read-back of the step of this parity done
   cudaEvent_t ev_entry = nullptr, ev_exit = nullptr, ev_front[2] = {}, ev_back[3] = {};
+  cudaEvent_t ev_caller = nullptr;   // the last work enqueued on a caller's stream
+  bool caller_pending = false;       // the internal streams must wait for ev_caller
+  bool internal_pending = false;     // a caller's stream must wait for ev_exit
   bool have_prev;
   const uint8_t* prev_frames;
   int32_t prev_pitch;
@@ -134,7 +139,7 @@ extern "C" vio_status vio_frontend_create(vio_frontend** out, const vio_params* 
       2 * ns * nc * kk * 8, 2 * ns * nc * 4,                    // 11-12 cand (2 parities)
       ns * nc * kk * 8, ns * nc * kk,                           // 13-14 spec
       ns * nc,                                                  // 15 occupancy
-      ns * capacity * 8, ns * 4,                                // 16-17 new
+      2 * ns * capacity * 8, 2 * ns * 4,                        // 16-17 new (2 parities)
       ns * 4,                                                   // 18 next_id
       (size_t)VIO_STATS_RING * ns * VIO_N_STATS * 4};           // 19 stats
   constexpr size_t kN = sizeof(sizes) / sizeof(sizes[0]);
@@ -171,8 +176,10 @@ extern "C" vio_status vio_frontend_create(vio_frontend** out, const vio_params* 
   fe->spec_xy = (float*)ptrs[13];
   fe->spec_status = (uint8_t*)ptrs[14];
   fe->occupancy = (uint8_t*)ptrs[15];
-  fe->new_xy = (float*)ptrs[16];
-  fe->new_count = (int32_t*)ptrs[17];
+  for (int i = 0; i < 2; ++i) {
+    fe->new_xy[i] = (float*)ptrs[16] + (size_t)i * ns * capacity * 2;
+    fe->new_count[i] = (int32_t*)ptrs[17] + (size_t)i * ns;
+  }
   fe->next_id = (int32_t*)ptrs[18];
   fe->stats = (int32_t*)ptrs[19];
   if (cudaMemset(fe->d_mem, 0, total) != cudaSuccess ||
@@ -204,10 +211,14 @@ extern "C" vio_status vio_frontend_destroy(vio_frontend* fe) {
   if (fe->side) {
     cudaStreamSynchronize(fe->side);
     cudaStreamSynchronize(fe->main_s);
+    cudaStreamSynchronize(fe->copy_s);
     cudaStreamDestroy(fe->side);
     cudaStreamDestroy(fe->main_s);
+    cudaStreamDestroy(fe->copy_s);
+    for (cudaEvent_t e : fe->ev_copied) cudaEventDestroy(e);
     cudaEventDestroy(fe->ev_entry);
     cudaEventDestroy(fe->ev_exit);
+    cudaEventDestroy(fe->ev_caller);
     for (cudaEvent_t e : fe->ev_front) cudaEventDestroy(e);
     for (cudaEvent_t e : fe->ev_back) cudaEventDestroy(e);
   }
@@ -216,14 +227,21 @@ extern "C" vio_status vio_frontend_destroy(vio_frontend* fe) {
   return VIO_OK;
 }
 
+namespace {
+bool caller_enter(vio_frontend* fe, cudaStream_t s);
+bool caller_leave(vio_frontend* fe, cudaStream_t s);
+}  // namespace
+
 extern "C" vio_status vio_frontend_reset(vio_frontend* fe, void* stream) {
   if (!fe) return VIO_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
+  if (!caller_enter(fe, s)) return VIO_ERR_CUDA;
   const size_t nl = (size_t)2 * fe->n_streams;
   cudaMemsetAsync(fe->list_count, 0, 2 * nl * 4, s);
   cudaMemsetAsync(fe->list_status, VIO_TRACK_EMPTY, 2 * nl * fe->capacity, s);
   cudaMemsetAsync(fe->next_id, 0, (size_t)fe->n_streams * 4, s);
   fe->have_prev = false;
+  if (!caller_leave(fe, s)) return VIO_ERR_CUDA;
   return cudaGetLastError() == cudaSuccess ? VIO_OK : VIO_ERR_CUDA;
 }
 
@@ -301,8 +319,8 @@ vio_status next_launch(vio_frontend* fe, const uint8_t* d_frames, int32_t pitch,
   f.cand_count = fe->cand_count[par];
   f.spec_xy = fe->spec_xy;
   f.spec_status = fe->spec_status;
-  f.new_xy = fe->new_xy;
-  f.new_count = fe->new_count;
+  f.new_xy = fe->new_xy[fe->cur_list ^ 1];       // the step's output parity
+  f.new_count = fe->new_count[fe->cur_list ^ 1];
   f.next_id = fe->next_id;
   f.occupancy = fe->occupancy;
   f.stats = fe->stats;
@@ -332,6 +350,80 @@ void advance(vio_frontend* fe, const uint8_t* d_frames, int32_t pitch, int64_t f
   ++fe->steps;
 }
 
+// Internal streams of pipelined steps (created once): the fronts on a
+// low-priority stream, the rest on a high-priority one (the critical path).
+bool ensure_pipe(vio_frontend* fe) {
+  if (fe->side) return true;
+  int least = 0, greatest = 0;
+  if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess ||
+      cudaStreamCreateWithPriority(&fe->side, cudaStreamNonBlocking, least) != cudaSuccess ||
+      cudaStreamCreateWithPriority(&fe->main_s, cudaStreamNonBlocking, greatest) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&fe->copy_s, cudaStreamNonBlocking) != cudaSuccess)
+    return false;
+  cudaEvent_t* evs[] = {&fe->ev_entry,    &fe->ev_exit,     &fe->ev_caller,
+                        &fe->ev_front[0], &fe->ev_front[1], &fe->ev_back[0],
+                        &fe->ev_back[1],  &fe->ev_back[2],  &fe->ev_copied[0],
+                        &fe->ev_copied[1]};
+  for (cudaEvent_t* e : evs)
+    if (cudaEventCreateWithFlags(e, cudaEventDisableTiming) != cudaSuccess) return false;
+  return true;
+}
+
+// Work on a caller's stream s follows the frontend's pipelined steps, and
+// pipelined steps follow work on a caller's stream.
+bool caller_enter(vio_frontend* fe, cudaStream_t s) {
+  if (fe->internal_pending) {
+    if (cudaStreamWaitEvent(s, fe->ev_exit, 0) != cudaSuccess) return false;
+    fe->internal_pending = false;
+  }
+  return true;
+}
+bool caller_leave(vio_frontend* fe, cudaStream_t s) {
+  if (!fe->side) return true;   // no pipelined step yet: nothing to order
+  if (cudaEventRecord(fe->ev_caller, s) != cudaSuccess) return false;
+  fe->caller_pending = true;
+  return true;
+}
+bool internal_enter(vio_frontend* fe) {
+  if (fe->caller_pending) {
+    if (cudaStreamWaitEvent(fe->side, fe->ev_caller, 0) != cudaSuccess ||
+        cudaStreamWaitEvent(fe->main_s, fe->ev_caller, 0) != cudaSuccess ||
+        cudaStreamWaitEvent(fe->copy_s, fe->ev_caller, 0) != cudaSuccess)
+      return false;
+    fe->caller_pending = false;
+  }
+  return true;
+}
+
+// One pipelined step on the internal streams: optional upload (h_frames ->
+// d_frames) and front on the low-priority stream, after the end of the step
+// two back; the rest on the high-priority stream; then ev_back of this step.
+vio_status pipelined_step(vio_frontend* fe, const uint8_t* h_frames, const uint8_t* d_frames,
+                          int32_t pitch, int64_t frame_stride) {
+  using namespace vio;
+  FrameLaunch f;
+  const vio_status st = next_launch(fe, d_frames, pitch, frame_stride, f);
+  if (st != VIO_OK) return st;
+  const int64_t t = fe->steps;
+  if (t >= 2 && cudaStreamWaitEvent(fe->side, fe->ev_back[(t - 2) % 3], 0) != cudaSuccess)
+    return VIO_ERR_CUDA;
+  if (h_frames && cudaMemcpyAsync(const_cast<uint8_t*>(d_frames), h_frames,
+                                  (size_t)2 * fe->n_streams * frame_stride,
+                                  cudaMemcpyHostToDevice, fe->side) != cudaSuccess)
+    return VIO_ERR_CUDA;
+  // the lists this step writes were read back (if at all) after step t-2
+  if (t >= 2 && cudaStreamWaitEvent(fe->main_s, fe->ev_copied[t % 2], 0) != cudaSuccess)
+    return VIO_ERR_CUDA;
+  if (launch_frames(&f, 1, fe->tune, fe->side, nullptr, 1) != cudaSuccess ||
+      cudaEventRecord(fe->ev_front[t % 2], fe->side) != cudaSuccess ||
+      cudaStreamWaitEvent(fe->main_s, fe->ev_front[t % 2], 0) != cudaSuccess ||
+      launch_frames(&f, 1, fe->tune, fe->main_s, nullptr, 2) != cudaSuccess ||
+      cudaEventRecord(fe->ev_back[t % 3], fe->main_s) != cudaSuccess)
+    return VIO_ERR_CUDA;
+  advance(fe, d_frames, pitch, frame_stride);
+  return VIO_OK;
+}
+
 }  // namespace
 
 extern "C" vio_status vio_frontend_step(vio_frontend* fe, const uint8_t* d_frames,
@@ -341,6 +433,7 @@ extern "C" vio_status vio_frontend_step(vio_frontend* fe, const uint8_t* d_frame
   const vio_status st = next_launch(fe, d_frames, pitch, frame_stride, f);
   if (st != VIO_OK) return st;
   cudaStream_t s = (cudaStream_t)stream;
+  if (!caller_enter(fe, s)) return VIO_ERR_CUDA;
   std::array<cudaEvent_t, VIO_N_STAGES + 1> ev{};
   if (fe->timing)
     for (auto& e : ev)
@@ -349,8 +442,38 @@ extern "C" vio_status vio_frontend_step(vio_frontend* fe, const uint8_t* d_frame
     return VIO_ERR_CUDA;
   if (fe->timing) fe->ev_rec.push_back(ev);
   advance(fe, d_frames, pitch, frame_stride);
-  return VIO_OK;
+  return caller_leave(fe, s) ? VIO_OK : VIO_ERR_CUDA;
 }
+
+namespace {
+
+// Lists and new detections of the last step into pinned host buffers.
+bool copy_outputs(vio_frontend* fe, float* h_track_xy, int32_t* h_track_id,
+                  int32_t* h_track_count, float* h_new_xy, int32_t* h_new_count,
+                  cudaStream_t s) {
+  vio_frontend_view v;
+  vio_frontend_get_view(fe, &v);
+  const size_t nl = (size_t)2 * fe->n_streams, cap = fe->capacity;
+  return cudaMemcpyAsync(h_track_xy, v.d_track_xy, nl * cap * 8, cudaMemcpyDeviceToHost, s) ==
+             cudaSuccess &&
+         cudaMemcpyAsync(h_track_id, v.d_track_id, nl * cap * 4, cudaMemcpyDeviceToHost, s) ==
+             cudaSuccess &&
+         cudaMemcpyAsync(h_track_count, v.d_track_count, nl * 4, cudaMemcpyDeviceToHost, s) ==
+             cudaSuccess &&
+         cudaMemcpyAsync(h_new_xy, v.d_new_xy, (size_t)fe->n_streams * cap * 8,
+                         cudaMemcpyDeviceToHost, s) == cudaSuccess &&
+         cudaMemcpyAsync(h_new_count, v.d_new_count, (size_t)fe->n_streams * 4,
+                         cudaMemcpyDeviceToHost, s) == cudaSuccess;
+}
+
+bool host_args_ok(const vio_frontend* fe, const uint8_t* h_frames, const uint8_t* d_frames,
+                  int32_t pitch, int64_t frame_stride, const void* a, const void* b,
+                  const void* c, const void* d, const void* e) {
+  return fe && h_frames && d_frames && a && b && c && d && e && pitch >= fe->w &&
+         frame_stride >= (int64_t)pitch * fe->h;
+}
+
+}  // namespace
 
 extern "C" vio_status vio_frontend_step_host(vio_frontend* fe, const uint8_t* h_frames,
                                              uint8_t* d_frames, int32_t pitch,
@@ -358,29 +481,45 @@ extern "C" vio_status vio_frontend_step_host(vio_frontend* fe, const uint8_t* h_
                                              int32_t* h_track_id, int32_t* h_track_count,
                                              float* h_new_xy, int32_t* h_new_count,
                                              void* stream) {
-  if (!fe || !h_frames || !d_frames || !h_track_xy || !h_track_id || !h_track_count ||
-      !h_new_xy || !h_new_count || pitch < fe->w || frame_stride < (int64_t)pitch * fe->h)
+  if (!host_args_ok(fe, h_frames, d_frames, pitch, frame_stride, h_track_xy, h_track_id,
+                    h_track_count, h_new_xy, h_new_count))
     return VIO_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
+  if (!caller_enter(fe, s)) return VIO_ERR_CUDA;
   const size_t in_bytes = (size_t)2 * fe->n_streams * frame_stride;
   if (cudaMemcpyAsync(d_frames, h_frames, in_bytes, cudaMemcpyHostToDevice, s) != cudaSuccess)
     return VIO_ERR_CUDA;
   const vio_status st = vio_frontend_step(fe, d_frames, pitch, frame_stride, stream);
   if (st != VIO_OK) return st;
-  vio_frontend_view v;
-  vio_frontend_get_view(fe, &v);
-  const size_t nl = (size_t)2 * fe->n_streams, cap = fe->capacity;
-  if (cudaMemcpyAsync(h_track_xy, v.d_track_xy, nl * cap * 8, cudaMemcpyDeviceToHost, s) !=
-          cudaSuccess ||
-      cudaMemcpyAsync(h_track_id, v.d_track_id, nl * cap * 4, cudaMemcpyDeviceToHost, s) !=
-          cudaSuccess ||
-      cudaMemcpyAsync(h_track_count, v.d_track_count, nl * 4, cudaMemcpyDeviceToHost, s) !=
-          cudaSuccess ||
-      cudaMemcpyAsync(h_new_xy, v.d_new_xy, (size_t)fe->n_streams * cap * 8,
-                      cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-      cudaMemcpyAsync(h_new_count, v.d_new_count, (size_t)fe->n_streams * 4,
-                      cudaMemcpyDeviceToHost, s) != cudaSuccess)
+  if (!copy_outputs(fe, h_track_xy, h_track_id, h_track_count, h_new_xy, h_new_count, s))
     return VIO_ERR_CUDA;
+  return caller_leave(fe, s) ? VIO_OK : VIO_ERR_CUDA;
+}
+
+extern "C" vio_status vio_frontend_step_host_async(vio_frontend* fe, const uint8_t* h_frames,
+                                                   uint8_t* d_frames, int32_t pitch,
+                                                   int64_t frame_stride, float* h_track_xy,
+                                                   int32_t* h_track_id, int32_t* h_track_count,
+                                                   float* h_new_xy, int32_t* h_new_count,
+                                                   void* done_event) {
+  if (!host_args_ok(fe, h_frames, d_frames, pitch, frame_stride, h_track_xy, h_track_id,
+                    h_track_count, h_new_xy, h_new_count))
+    return VIO_ERR_INVALID_ARG;
+  if (fe->timing) return VIO_ERR_UNSUPPORTED;   // stage timing keeps steps whole
+  if (!ensure_pipe(fe) || !internal_enter(fe)) return VIO_ERR_CUDA;
+  const int64_t t = fe->steps;
+  const vio_status st = pipelined_step(fe, h_frames, d_frames, pitch, frame_stride);
+  if (st != VIO_OK) return st;
+  // read-back beside the next step's tracking, before the step after it
+  // overwrites these lists
+  if (cudaStreamWaitEvent(fe->copy_s, fe->ev_back[t % 3], 0) != cudaSuccess ||
+      !copy_outputs(fe, h_track_xy, h_track_id, h_track_count, h_new_xy, h_new_count,
+                    fe->copy_s) ||
+      cudaEventRecord(fe->ev_copied[t % 2], fe->copy_s) != cudaSuccess ||
+      (done_event && cudaEventRecord((cudaEvent_t)done_event, fe->copy_s) != cudaSuccess) ||
+      cudaEventRecord(fe->ev_exit, fe->copy_s) != cudaSuccess)
+    return VIO_ERR_CUDA;
+  fe->internal_pending = true;
   return VIO_OK;
 }
 
@@ -393,59 +532,34 @@ extern "C" vio_status vio_frontend_run(vio_frontend* fe, const uint8_t* d_frames
     return VIO_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   // Pipelined steps: the front of step t (pyramids and detection candidates
-  // of its own frames) runs on a low-priority side stream beside the tracking
-  // and finalisation of step t-1 (on a high-priority stream: the critical
-  // path); it waits for the end of step t-2, the last reader of its pyramid
-  // ring slot and candidate buffers. The caller's stream waits for the last
-  // step. Stage timing keeps the steps whole.
-  const bool pipe = n_steps > 1 && !fe->timing;
-  if (pipe && !fe->side) {
-    int least = 0, greatest = 0;
-    if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess ||
-        cudaStreamCreateWithPriority(&fe->side, cudaStreamNonBlocking, least) != cudaSuccess ||
-        cudaStreamCreateWithPriority(&fe->main_s, cudaStreamNonBlocking, greatest) !=
-            cudaSuccess ||
-        cudaEventCreateWithFlags(&fe->ev_entry, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&fe->ev_exit, cudaEventDisableTiming) != cudaSuccess)
-      return VIO_ERR_CUDA;
-    for (cudaEvent_t& e : fe->ev_front)
-      if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess)
-        return VIO_ERR_CUDA;
-    for (cudaEvent_t& e : fe->ev_back)
-      if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess)
-        return VIO_ERR_CUDA;
-  }
-  if (pipe) {
-    // everything already on the caller's stream comes first
-    if (cudaEventRecord(fe->ev_entry, s) != cudaSuccess ||
-        cudaStreamWaitEvent(fe->side, fe->ev_entry, 0) != cudaSuccess ||
-        cudaStreamWaitEvent(fe->main_s, fe->ev_entry, 0) != cudaSuccess)
-      return VIO_ERR_CUDA;
-  }
-  cudaStream_t ms = pipe ? fe->main_s : s;
-  for (int32_t i = 0; i < n_steps; ++i) {
-    const uint8_t* fr = d_frames + (int64_t)i * step_stride;
-    if (!pipe) {
-      const vio_status st = vio_frontend_step(fe, fr, pitch, frame_stride, stream);
+  // of its own frames) runs on a low-priority stream beside the tracking and
+  // finalisation of step t-1 (on a high-priority stream: the critical path);
+  // it waits for the end of step t-2, the last reader of its pyramid ring
+  // slot and candidate buffers. The run follows the work already on the
+  // caller's stream, and the caller's stream waits for its last step. Stage
+  // timing keeps the steps whole.
+  if (n_steps < 2 || fe->timing) {
+    for (int32_t i = 0; i < n_steps; ++i) {
+      const vio_status st =
+          vio_frontend_step(fe, d_frames + (int64_t)i * step_stride, pitch, frame_stride, stream);
       if (st != VIO_OK) return st;
-      continue;
     }
-    FrameLaunch f;
-    const vio_status st = next_launch(fe, fr, pitch, frame_stride, f);
-    if (st != VIO_OK) return st;
-    if (i >= 2 && cudaStreamWaitEvent(fe->side, fe->ev_back[(i - 2) % 3], 0) != cudaSuccess)
-      return VIO_ERR_CUDA;
-    if (launch_frames(&f, 1, fe->tune, fe->side, nullptr, 1) != cudaSuccess ||
-        cudaEventRecord(fe->ev_front[i % 2], fe->side) != cudaSuccess ||
-        cudaStreamWaitEvent(ms, fe->ev_front[i % 2], 0) != cudaSuccess ||
-        launch_frames(&f, 1, fe->tune, ms, nullptr, 2) != cudaSuccess ||
-        cudaEventRecord(fe->ev_back[i % 3], ms) != cudaSuccess)
-      return VIO_ERR_CUDA;
-    advance(fe, fr, pitch, frame_stride);
+    return VIO_OK;
   }
-  if (pipe && (cudaEventRecord(fe->ev_exit, ms) != cudaSuccess ||
-               cudaStreamWaitEvent(s, fe->ev_exit, 0) != cudaSuccess))
+  if (!ensure_pipe(fe) || !caller_enter(fe, s) ||
+      cudaEventRecord(fe->ev_caller, s) != cudaSuccess)
     return VIO_ERR_CUDA;
+  fe->caller_pending = true;
+  if (!internal_enter(fe)) return VIO_ERR_CUDA;
+  for (int32_t i = 0; i < n_steps; ++i) {
+    const vio_status st =
+        pipelined_step(fe, nullptr, d_frames + (int64_t)i * step_stride, pitch, frame_stride);
+    if (st != VIO_OK) return st;
+  }
+  if (cudaEventRecord(fe->ev_exit, fe->main_s) != cudaSuccess ||
+      cudaStreamWaitEvent(s, fe->ev_exit, 0) != cudaSuccess)
+    return VIO_ERR_CUDA;
+  fe->internal_pending = false;
   return VIO_OK;
 }
 
@@ -499,8 +613,8 @@ extern "C" vio_status vio_frontend_get_view(vio_frontend* fe, vio_frontend_view*
   out->d_track_id = fe->list_id + li * nl * fe->capacity;
   out->d_track_status = fe->list_status + li * nl * fe->capacity;
   out->d_track_count = fe->list_count + li * nl;
-  out->d_new_xy = fe->new_xy;
-  out->d_new_count = fe->new_count;
+  out->d_new_xy = fe->new_xy[li];
+  out->d_new_count = fe->new_count[li];
   out->capacity = fe->capacity;
   out->n_streams = fe->n_streams;
   return VIO_OK;

@@ -138,6 +138,12 @@ _SIGS = {
                                                 ctypes.c_void_p, ctypes.c_void_p,
                                                 ctypes.c_void_p, ctypes.c_void_p,
                                                 ctypes.c_void_p]),
+    "vio_frontend_step_host_async": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p,
+                                                ctypes.c_void_p, ctypes.c_int32,
+                                                ctypes.c_int64, ctypes.c_void_p,
+                                                ctypes.c_void_p, ctypes.c_void_p,
+                                                ctypes.c_void_p, ctypes.c_void_p,
+                                                ctypes.c_void_p]),
     "vio_frontend_get_view": (ctypes.c_int32, [ctypes.c_void_p, ctypes.POINTER(FrontendView)]),
     "vio_frontend_launches_per_step": (ctypes.c_int32, [ctypes.c_void_p]),
     "vio_frontend_set_tune": (ctypes.c_int32, [ctypes.c_void_p, ctypes.POINTER(BatchTune)]),
@@ -590,6 +596,19 @@ class Frontend:
                                              _hptr(out["id"]), _hptr(out["count"]),
                                              _hptr(out["new_xy"]), _hptr(out["new_count"]),
                                              _stream(stream)), "vio_frontend_step_host")
+
+    def step_host_async(self, h_frames: torch.Tensor, d_frames: torch.Tensor, out: dict,
+                        done: "torch.cuda.Event | None" = None):
+        """step_host pipelined across calls on the frontend's own streams; `done`
+        (a recorded-once torch.cuda.Event) is recorded when `out` holds this
+        step's results. d_frames must stay untouched until the next step's
+        event."""
+        pitch = h_frames.shape[-1]
+        ev = ctypes.c_void_p(done.cuda_event) if done is not None else None
+        _check(load().vio_frontend_step_host_async(
+            self.handle, _hptr(h_frames), _ptr(d_frames), pitch, h_frames.shape[2] * pitch,
+            _hptr(out["xy"]), _hptr(out["id"]), _hptr(out["count"]), _hptr(out["new_xy"]),
+            _hptr(out["new_count"]), ev), "vio_frontend_step_host_async")
 
     def launches_per_step(self) -> int:
         return int(load().vio_frontend_launches_per_step(self.handle))

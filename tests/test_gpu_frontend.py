@@ -161,6 +161,46 @@ def test_frontend_pipelined_run_equals_steps(learned):
     assert na == nb == n and np.array_equal(sa[:n], sb[:n])
 
 
+def test_frontend_step_host_async_equals_step_host():
+    """Pipelined host steps (uploads, fronts and the rest on the frontend's own
+    streams, a done event per step) give each step's host outputs exactly as
+    the plain host step, with a reset and a plain host step in between."""
+    w, h, L = 376, 240, 4
+    n, R = 10, 3
+    seq = synth.make_sequence(5011, n, w, h, 1, max_motion=6.0, tex_size=1024)
+    p = vio.default_params(n_levels=L, cell_w=47, cell_h=40)
+    cap = 2 * (w // 47) * (h // 40)
+    host = torch.from_numpy(seq.frames).view(n, 1, 2, h, w).pin_memory()
+    a, b = vio.Frontend(p, w, h, 1, cap), vio.Frontend(p, w, h, 1, cap)
+    da = torch.empty((R, 1, 2, h, w), dtype=torch.uint8, device="cuda")
+    db = torch.empty_like(da)
+    oa = [a.host_outputs() for _ in range(n)]
+    ob = [b.host_outputs() for _ in range(n)]
+    evs = [torch.cuda.Event() for _ in range(n)]
+    for e in evs:
+        e.record()
+    for t in range(n):
+        if t == 5:
+            a.reset()
+            b.reset()
+        a.step_host(host[t], da[t % R], oa[t])
+        if t == 7:
+            b.step_host(host[t], db[t % R], ob[t])
+        else:
+            b.step_host_async(host[t], db[t % R], ob[t], evs[t])
+    torch.cuda.synchronize()
+    for t in range(n):
+        assert torch.equal(oa[t]["count"], ob[t]["count"]), t
+        assert torch.equal(oa[t]["new_count"], ob[t]["new_count"]), t
+        for c in range(2):
+            nc = int(oa[t]["count"][0, c])
+            assert torch.equal(oa[t]["xy"][0, c, :nc], ob[t]["xy"][0, c, :nc]), (t, c)
+            assert torch.equal(oa[t]["id"][0, c, :nc], ob[t]["id"][0, c, :nc]), (t, c)
+        nn = int(oa[t]["new_count"][0])
+        assert torch.equal(oa[t]["new_xy"][0, :nn], ob[t]["new_xy"][0, :nn]), t
+    assert int(oa[n - 1]["count"].sum()) > 0
+
+
 def test_frontend_run_equals_steps():
     w, h, L = 376, 240, 3
     seq = synth.make_sequence(5003, 6, w, h, 1, max_motion=5.0, tex_size=1024)
