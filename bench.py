@@ -136,12 +136,13 @@ def make_frames(rank: int):
     return seq.frames                                    # (F, 2, H, W) uint8
 
 
-def oracle_frames_per_s(frames, n_frames, warmup=2):
-    """The CPU oracle frontend, as it stands, over a bounded sample of frames."""
+def oracle_frames_per_s(frames, n_frames, warmup=2, cores=None):
+    """The CPU oracle frontend, as it stands, over a bounded sample of frames
+    (tracking threaded over `cores` host cores, all of them by default)."""
     import oracle
     from oracle import frontend as ofe
     oracle.build()
-    cores = os.cpu_count() or 1
+    cores = cores or os.cpu_count() or 1
     p = ofe.Params(n_levels=LEVELS, cell_w=CELL_W, cell_h=CELL_H, k=K_CELL)
     st = ofe.StreamState()
     for f in range(warmup):
@@ -898,10 +899,13 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         fps, cores, _ = oracle_frames_per_s(frames_np, args.cpu_frames)
+        fps1, _, _ = oracle_frames_per_s(frames_np, 8, cores=1)
         cpu = {"value": fps, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"{args.cpu_frames} consecutive frames of the same sequence through the "
                          f"FP64 oracle frontend (after 2 warm-up frames), tracking threaded "
-                         f"over {cores} cores"}
+                         f"over {cores} cores",
+               "single_core": {"value": fps1, "unit": UNIT,
+                               "sample": "8 frames after 2 warm-up frames, one thread"}}
 
     if rank == 0:
         line = {
