@@ -255,26 +255,54 @@ __global__ void __launch_bounds__(net::TILE_THREADS, 1) frame_initnet_kernel(
   net_prefetch(mm, cur, R);
   net::tile_setup(net::packed(mm.f[0].net), sm);
   const net::TileSmem S = net::tile_smem(sm);
-  while (true) {
-    net::tile_clear_input_border(S);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // the first tile's input; the rows of each later tile are stored while
+  // fc1 of the tile before it runs (S.x is free after conv3), and loaded
+  // into registers one tile ahead of that
+  net::tile_clear_input_border(S);
 #pragma unroll
-    for (int k = 0; k < KN_ROWS; ++k) {
-      const int e = threadIdx.x + k * net::TILE_THREADS;
-      if ((e >> 6) < cur.nv) net::row_store(R[k], S, e >> 6, (e >> 4) & 3, e & 15);
+  for (int k = 0; k < KN_ROWS; ++k) {
+    const int e = threadIdx.x + k * net::TILE_THREADS;
+    if ((e >> 6) < cur.nv) net::row_store(R[k], S, e >> 6, (e >> 4) & 3, e & 15);
+  }
+  v += gridDim.x;
+  NetTile next{};
+  if (v < n_valid) {
+    next = net_tile(mm, L, v);
+    net_prefetch(mm, next, R);
+  }
+  __syncthreads();
+  while (true) {
+    net::tile_convs(S);
+    if (warp < 8) net::tile_fc1(S, warp, lane);
+    const bool more = v < n_valid;
+    if (more) {
+      net::tile_clear_input_border(S);
+#pragma unroll
+      for (int k = 0; k < KN_ROWS; ++k) {
+        const int e = threadIdx.x + k * net::TILE_THREADS;
+        if ((e >> 6) < next.nv) net::row_store(R[k], S, e >> 6, (e >> 4) & 3, e & 15);
+      }
     }
     __syncthreads();
+    // fc2 of this tile by warp 0, writing the proposals straight to the
+    // output, while the other warps go on with the next tile's conv1 (fc2
+    // reads only H4, which is rewritten after the next tile's conv3)
+    if (warp == 0) {
+      const FrameLaunch& f = mm.f[cur.gi];
+      float* o = f.net_out + 3 * ((long long)cur.list * f.cap + cur.s0);
+      const int nv = cur.nv;
+      net::tile_fc2(S, lane, [&](int row, int n, float val) {
+        if (row < nv) o[row * 3 + n] = val;
+      });
+    }
+    if (!more) break;
+    cur = next;
     v += gridDim.x;
-    NetTile next{};
     if (v < n_valid) {
       next = net_tile(mm, L, v);
       net_prefetch(mm, next, R);
     }
-    net::tile_forward(S);
-    const FrameLaunch& f = mm.f[cur.gi];
-    float* o = f.net_out + 3 * ((long long)cur.list * f.cap + cur.s0);
-    for (int i = threadIdx.x; i < cur.nv * 3; i += blockDim.x) o[i] = S.out[i];
-    if (v >= n_valid) break;
-    cur = next;
   }
 }
 

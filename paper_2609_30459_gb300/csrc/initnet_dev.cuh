@@ -504,7 +504,9 @@ __device__ __forceinline__ void tile_conv3(const TileSmem& S, int mt, int nt, in
     base[h] = s * XR_SAMPLE + (2 * i) * H2_ROW + (2 * j) * H2_PIX + 2 * t;
     orow[h] = s * H3_SAMPLE + p;
   }
-  float acc[4] = {};
+  // two accumulators (the two channel halves of each tap): two independent
+  // MMA chains of nine instead of one of eighteen
+  float acc[2][4] = {};
 #pragma unroll
   for (int ks = 0; ks < K3 / 16; ++ks) {
     const int tap = ks >> 1, c0 = (ks & 1) * 16;
@@ -516,12 +518,12 @@ __device__ __forceinline__ void tile_conv3(const TileSmem& S, int mt, int nt, in
     a[3] = lds32(S.x + base[1] + off + 8);
     uint32_t b[2];
     ldsm_b1(b, S.w + SW3, PK3, nt * 8, ks * 16, lane);
-    mma16816(acc, a, b[0], b[1]);
+    mma16816(acc[ks & 1], a, b[0], b[1]);
   }
 #pragma unroll
   for (int e = 0; e < 4; ++e) {
     const int n = nt * 8 + 2 * t + (e & 1);
-    S.h3[orow[e >> 1] + n * 4] = f2bf(fmaxf(acc[e] + S.b[OFF_B3 + n], 0.f));
+    S.h3[orow[e >> 1] + n * 4] = f2bf(fmaxf(acc[0][e] + acc[1][e] + S.b[OFF_B3 + n], 0.f));
   }
 }
 
@@ -530,8 +532,7 @@ template <int K, int PK, int STRIDE>
 __device__ __forceinline__ void fc_ntile(const uint16_t* in, const uint16_t* W, int nt, int lane,
                                          float (&acc)[4]) {
   const int g = lane >> 2, t = lane & 3;
-#pragma unroll
-  for (int e = 0; e < 4; ++e) acc[e] = 0.f;
+  float part[2][4] = {};        // even and odd K steps: two independent chains
 #pragma unroll
   for (int ks = 0; ks < K / 16; ++ks) {
     uint32_t a[4];
@@ -541,8 +542,10 @@ __device__ __forceinline__ void fc_ntile(const uint16_t* in, const uint16_t* W, 
     a[3] = lds32(in + (g + 8) * STRIDE + ks * 16 + 2 * t + 8);
     uint32_t b[2];
     ldsm_b1(b, W, PK, nt * 8, ks * 16, lane);
-    mma16816(acc, a, b[0], b[1]);
+    mma16816(part[ks & 1], a, b[0], b[1]);
   }
+#pragma unroll
+  for (int e = 0; e < 4; ++e) acc[e] = part[0][e] + part[1][e];
 }
 
 // Zero border pixels of the input maps (the region held conv2's output).
@@ -555,10 +558,10 @@ __device__ __forceinline__ void tile_clear_input_border(const TileSmem& S) {
   }
 }
 
-// The network on the TT inputs in S.x (interior written by the caller and
-// the border cleared by tile_clear_input_border, then a barrier); results
-// (dx, dy, conf) in S.out[3 s ..]. Ends with a barrier.
-__device__ __forceinline__ void tile_forward(const TileSmem& S) {
+// conv1, conv2 and conv3 of the TT inputs in S.x (interior written by the
+// caller and the border cleared by tile_clear_input_border, then a barrier):
+// H3 in S.h3. Ends with a barrier, after which S.x is free.
+__device__ __forceinline__ void tile_convs(const TileSmem& S) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int mt = warp; mt < TT * 4; mt += TILE_WARPS) tile_conv1(S, mt, lane);
   __syncthreads();
@@ -575,26 +578,43 @@ __device__ __forceinline__ void tile_forward(const TileSmem& S) {
   __syncthreads();
   for (int it = warp; it < (TT / 4) * 4; it += TILE_WARPS) tile_conv3(S, it >> 2, it & 3, lane);
   __syncthreads();
+}
+
+// fc1, one n-tile of 8 outputs per warp (warps 0..7): H3 -> H4. The caller
+// places the barrier before fc2.
+__device__ __forceinline__ void tile_fc1(const TileSmem& S, int warp, int lane) {
   const int g = lane >> 2, t = lane & 3;
-  if (warp < 8) {                       // fc1: 8 n-tiles of 8 outputs
-    float acc[4];
-    fc_ntile<K4, PK4, H3_SAMPLE>(S.h3, S.w + SW4, warp, lane, acc);
-    const int n0 = warp * 8 + 2 * t;
-    store_pairs(acc, S.b + OFF_B4, n0, S.h4 + g * H4_SAMPLE, S.h4 + (g + 8) * H4_SAMPLE);
-  }
-  __syncthreads();
-  if (warp == 0) {                      // fc2: one n-tile, outputs 0..2
-    float acc[4];
-    fc_ntile<K5, PK5, H4_SAMPLE>(S.h4, S.w + SW5, 0, lane, acc);
+  float acc[4];
+  fc_ntile<K4, PK4, H3_SAMPLE>(S.h3, S.w + SW4, warp, lane, acc);
+  store_pairs(acc, S.b + OFF_B4, warp * 8 + 2 * t, S.h4 + g * H4_SAMPLE,
+              S.h4 + (g + 8) * H4_SAMPLE);
+}
+
+// fc2 by one warp: out(sample, n, value) for the TT samples and n < 3, value
+// (dx, dy, conf) = (16 o0, 16 o1, sigmoid(o2)).
+template <class Out>
+__device__ __forceinline__ void tile_fc2(const TileSmem& S, int lane, Out out) {
+  const int g = lane >> 2, t = lane & 3;
+  float acc[4];
+  fc_ntile<K5, PK5, H4_SAMPLE>(S.h4, S.w + SW5, 0, lane, acc);
 #pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      const int row = g + 8 * (e >> 1), n = 2 * t + (e & 1);
-      if (n < 3) {
-        const float o = acc[e] + S.b[OFF_B5 + n];
-        S.out[row * 3 + n] = n < 2 ? o * kScale : 1.f / (1.f + expf(-o));
-      }
+  for (int e = 0; e < 4; ++e) {
+    const int row = g + 8 * (e >> 1), n = 2 * t + (e & 1);
+    if (n < 3) {
+      const float o = acc[e] + S.b[OFF_B5 + n];
+      out(row, n, n < 2 ? o * kScale : 1.f / (1.f + expf(-o)));
     }
   }
+}
+
+// The network on the TT inputs in S.x (as for tile_convs); results
+// (dx, dy, conf) in S.out[3 s ..]. Ends with a barrier.
+__device__ __forceinline__ void tile_forward(const TileSmem& S) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  tile_convs(S);
+  if (warp < 8) tile_fc1(S, warp, lane);
+  __syncthreads();
+  if (warp == 0) tile_fc2(S, lane, [&](int row, int n, float v) { S.out[row * 3 + n] = v; });
   __syncthreads();
 }
 
