@@ -1,6 +1,6 @@
 """What the trained initializer gains over the plain tracker (the shipped
 weights, held-out sequences with motion up to 40 px, 5 levels): the plain
-pyramidal KLT from a zero start is the judge. Where both end OK the learned
+pyramidal KLT from a zero start is the yardstick. Where both end OK the learned
 start's final flow must equal the plain result within 1e-3 px for nearly all
 keypoints; the learned start must track over fewer levels; and the tracks it
 keeps that the plain tracker loses must be right (ground truth of the
