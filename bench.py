@@ -300,24 +300,8 @@ def frontend_config_run(torch, vio, name, w, h, n_streams, levels, cw, ch, n_fra
     p = vio.default_params(n_levels=levels, cell_w=cw, cell_h=ch, **(params_kw or {}))
     cap = 2 * (w // cw) * (h // ch) * p.k_per_cell
     fe = vio.Frontend(p, w, h, n_streams, cap)
-    best = None
-    for k2 in (32, 64, 128, 256):
-        for first in (0, 2):
-            for k1 in (128, 256):
-                fe.set_tune(k2, 0, first, k1)
-                fe.reset()
-                for t in range(3):
-                    fe.step(frames[order[t]])
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record()
-                for t in range(3, 23):
-                    fe.step(frames[order[t % len(order)]])
-                e1.record()
-                torch.cuda.synchronize()
-                if best is None or e0.elapsed_time(e1) < best[0]:
-                    best = (e0.elapsed_time(e1), (k2, 0, first, k1))
-    fe.set_tune(*best[1])
-    fe.reset()
+    tune, _ = tune_frontend(torch, fe, frames, [(k2, 0, first, k1) for k2 in (32, 64, 128, 256)
+                                                for first in (0, 2) for k1 in (128, 256)])
     for t in range(3):
         fe.step(frames[order[t]])
     torch.cuda.synchronize()
@@ -354,7 +338,7 @@ def frontend_config_run(torch, vio, name, w, h, n_streams, levels, cw, ch, n_fra
             "tracked_keypoints_per_s": float(st[..., 0].sum() + st[..., 1].sum()) / total_s,
             "survived_per_step": float(st[..., 2].sum() + st[..., 3].sum()) / steps,
             "tune": dict(zip(("k2_threads", "pyr_tile_shift", "pyr_first_levels", "k1_threads"),
-                             best[1]))}
+                             tune))}
 
 
 def batched_compare(torch, vio, steps, warmup, net, seqs=None):
@@ -544,30 +528,46 @@ def profile_frontend(w, h, n_streams, learned, steps=3):
     return 0
 
 
-def autotune_frontend(torch, fe, frames, n=40):
-    import itertools
-    frames5 = frames.view(N_FRAMES, 1, 2, H, W)
-    best, best_t = None, None
-    for k2, shift, first, k1 in itertools.product((32, 64, 128, 256), (-1, 0, 1), (0, 1, 2),
-                                                  (128, 256)):
-        fe.set_tune(k2, shift, first, k1)
+def tune_frontend(torch, fe, frames5, combos, n=40, finalists=3, n_final=120):
+    """Launch shapes of a frontend, timed on the path the bench times
+    (`fe.run`, pipelined across frames): every candidate over frames5[3:3+n]
+    after 3 warm-up frames, the better of two passes; the `finalists` fastest
+    again over up to n_final frames, the best of three passes, so that a
+    candidate that won one short pass by noise does not decide. frames5 is
+    (frames, streams, 2, h, w). Returns (tune, ms per step)."""
+    def timed(c, m, reps):
+        fe.set_tune(*c)
         t = None
-        for rep in range(2):                   # the better of two passes
+        for _ in range(reps):
             fe.reset()
             fe.run(frames5[:3])
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
-            fe.run(frames5[3:3 + n])
+            fe.run(frames5[3:3 + m])
             e1.record()
             torch.cuda.synchronize()
-            t = e0.elapsed_time(e1) if t is None else min(t, e0.elapsed_time(e1))
-        if best_t is None or t < best_t:
-            best, best_t = (k2, shift, first, k1), t
+            dt = e0.elapsed_time(e1) / m
+            t = dt if t is None else min(t, dt)
+        return t
+
+    m1 = min(n, len(frames5) - 3)
+    first = sorted(((timed(c, m1, 2), c) for c in combos), key=lambda x: x[0])
+    m2 = min(n_final, len(frames5) - 3)
+    final = sorted(((timed(c, m2, 3), c) for _, c in first[:finalists]), key=lambda x: x[0])
+    best_t, best = final[0]
     fe.set_tune(*best)
     fe.reset()
     torch.cuda.synchronize()
+    return best, best_t
+
+
+def autotune_frontend(torch, fe, frames, n=40):
+    import itertools
+    frames5 = frames.view(N_FRAMES, 1, 2, H, W)
+    combos = list(itertools.product((32, 64, 128, 256), (-1, 0, 1), (0, 1, 2), (128, 256)))
+    best, best_t = tune_frontend(torch, fe, frames5, combos, n)
     return {"k2_threads": best[0], "pyr_tile_shift": best[1], "pyr_first_levels": best[2],
-            "k1_threads": best[3], "ms_per_step": best_t / n}
+            "k1_threads": best[3], "ms_per_step": best_t}
 
 
 def profile_pyramid_detect(n=512, reps=3):
