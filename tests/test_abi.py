@@ -90,3 +90,42 @@ def test_product_has_no_cpu_fallback():
     for f in os.listdir(os.path.join(ROOT, "paper_2609_30459_gb300", "csrc")):
         assert "oracle" not in open(os.path.join(ROOT, "paper_2609_30459_gb300", "csrc",
                                                  f)).read().lower()
+
+
+def test_host_validation_of_frontend_batch_and_server_calls(lib):
+    """The frontend, batch, server and network entry points refuse null
+    handles, misaligned buffers and out-of-range arguments on the host, before
+    any device work."""
+    from paper_2609_30459_gb300 import vio
+    E = vio.ERR_INVALID_ARG
+    buf = ctypes.create_string_buffer(64)
+    # pipelined frontend calls: a null frontend
+    assert lib.vio_frontend_run(None, buf, 16, 16, 32, 2, None) == E
+    assert lib.vio_frontend_step_host_async(None, buf, buf, 16, 16, buf, buf, buf, buf, buf,
+                                            None) == E
+    # launch-shape tunes: a null handle
+    good = vio.BatchTune(128, 0, 0, 0, 128, 0)
+    assert lib.vio_frontend_set_tune(None, ctypes.byref(good)) == E
+    assert lib.vio_batch_set_tune(None, ctypes.byref(good)) == E
+    assert lib.vio_batch_get_tune(None, ctypes.byref(good)) == E
+    # the network: null or misaligned buffers, a negative count
+    assert lib.vio_initnet_forward(None, buf, 1, buf, None) == E
+    addr = ctypes.addressof(buf)
+    aligned = (addr + 15) & ~15
+    assert lib.vio_initnet_forward(aligned, aligned + 2, 1, aligned, None) == E
+    assert lib.vio_initnet_forward(aligned + 2, aligned, 1, aligned, None) == E
+    assert lib.vio_initnet_forward(aligned, aligned, -1, aligned, None) == E
+    # device-memory sizing and the server: null arguments, empty or oversized
+    # class lists, requests out of time order
+    b = ctypes.c_int64()
+    assert lib.vio_batch_device_bytes(None, 1, ctypes.byref(b)) == E
+    cls = vio._groups_array([(vio.default_params(n_levels=4, cell_w=32, cell_h=32), 640, 480,
+                              2, 600)])
+    assert lib.vio_batch_device_bytes(cls, 0, ctypes.byref(b)) == E
+    assert lib.vio_batch_device_bytes(cls, 1, ctypes.byref(b)) == vio.OK and b.value > 0
+    gap, over = ctypes.c_double(), ctypes.c_int64()
+    assert lib.vio_server_loop_stats(None, ctypes.byref(gap), ctypes.byref(over)) == E
+    reqs = (vio.ServerReq * 2)()
+    done = (vio.ServerDone * 2)()
+    n = ctypes.c_int64()
+    assert lib.vio_server_run_trace(None, reqs, 2, done, 1.0, ctypes.byref(n)) == E
