@@ -1,6 +1,7 @@
 // Grid-cell FAST-9 detection entry points (Sec. III-D): the per-pixel score
-// map, the per-cell candidate kernel (one warp per cell, blocks of cells per
-// CTA; device code in detect_dev.cuh) and the
+// map, the per-cell candidate kernel (one to eight warps per cell, chosen
+// from the launch size, blocks of cells per CTA; device code in
+// detect_dev.cuh) and the
 // per-image selection that applies k_eff = k - occupancy and writes the
 // survivors in cell raster order with a block-wide prefix sum.
 #include "detect_dev.cuh"

@@ -6,10 +6,11 @@
 //                           (one pyramid pass per tile) and, in the same
 //                           launch, the per-cell FAST/NMS top-k candidates of
 //                           camera 0. Levels beyond 4 follow as a further pass.
-//  KN frame_initnet_kernel  (only with the learned initializer) one warp per
-//                           live track of both cameras: network input from
-//                           the previous and current pyramids, forward pass
-//                           on the tensor cores -> flow proposal + confidence.
+//  KN frame_initnet_kernel  (only with the learned initializer) persistent
+//                           CTAs over tiles of 16 live tracks of both
+//                           cameras: network input from the previous and
+//                           current pyramids, forward pass on the tensor
+//                           cores -> flow proposal + confidence.
 //  K2 frame_track_kernel    one warp per keypoint: temporal tracking of every
 //                           live track of both cameras (previous -> current
 //                           pyramid; from the proposal over the lower levels

@@ -3,8 +3,10 @@
 //
 //  pack     FP32 master parameters -> BF16 [N][K] matrices + FP32 biases
 //  extract  network inputs of keypoints from two pyramids
-//  forward  one warp per sample, tensor cores (BF16 in, FP32 accumulate)
-//  train    forward as above, then the backward pass in FP32 per warp, with
+//  forward  persistent CTAs of 512 threads over tiles of 16 samples, layer
+//           by layer on the tensor cores (BF16 in, FP32 accumulate)
+//  train    the forward pass of one sample per warp (the same arithmetic),
+//           then the backward pass in FP32 per warp, with
 //           the weight gradients summed in shared memory per CTA and added to
 //           the global gradient once per CTA
 //  adam     Adam update of the master parameters
