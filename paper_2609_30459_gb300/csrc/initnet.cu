@@ -5,8 +5,8 @@
 //  extract  network inputs of keypoints from two pyramids
 //  forward  persistent CTAs of 512 threads over tiles of 16 samples, layer
 //           by layer on the tensor cores (BF16 in, FP32 accumulate)
-//  train    the forward pass of one sample per warp (the same arithmetic),
-//           then the backward pass in FP32 per warp, with
+//  train    the forward pass of one sample per warp (same layers, BF16
+//           activations), then the backward pass in FP32 per warp, with
 //           the weight gradients summed in shared memory per CTA and added to
 //           the global gradient once per CTA
 //  adam     Adam update of the master parameters
