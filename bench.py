@@ -158,6 +158,94 @@ def oracle_frames_per_s(frames, n_frames, warmup=2, cores=None, budget_s=None):
     return len(times) / sum(times), cores, times
 
 
+def accuracy_vs_oracle(torch, vio, frames, levels, cw, ch, k, n_frames, params_kw=None):
+    """Flow error and track-status agreement of the GPU frontend against the
+    FP64 oracle frontend, step by step on the first n_frames of `frames`
+    ((F, 2 * streams, h, w) uint8): before each frame the oracle receives the
+    GPU's lists, so each step is compared on the same inputs. Per step and
+    stream: every temporal track and every stereo match of a new keypoint is
+    compared by id (position error where both keep it; agreement = both keep
+    it or both drop it); new detections are compared bit for bit."""
+    import numpy as np
+    import oracle
+    from oracle import frontend as ofe
+    oracle.build()
+    params_kw = dict(params_kw or {})
+    F, C, h, w = frames.shape
+    ns = C // 2
+    p = vio.default_params(n_levels=levels, cell_w=cw, cell_h=ch, k_per_cell=k, **params_kw)
+    op = ofe.Params(n_levels=levels, cell_w=cw, cell_h=ch, k=k,
+                    thresholds=tuple(params_kw.get("thresholds", (40, 20, 10, 5))),
+                    gn_iters=params_kw.get("gn_iters", 5))
+    cap = 2 * (w // cw) * (h // ch) * k
+    fe = vio.Frontend(p, w, h, ns, cap)
+    dev = torch.from_numpy(np.ascontiguousarray(frames[:n_frames])).cuda().view(
+        n_frames, ns, 2, h, w)
+    states = [ofe.StreamState() for _ in range(ns)]
+    errs, agree, n_cmp, new_same, new_total = [], 0, 0, 0, 0
+    for t in range(n_frames):
+        fe.step(dev[t])
+        torch.cuda.synchronize()
+        v = fe.view()
+        for s in range(ns):
+            st = states[s]
+            prev_ids = [st.ids[0].copy(), st.ids[1].copy()]
+            ofe.step(st, frames[t, 2 * s: 2 * s + 2], op, cap, n_threads=os.cpu_count() or 1)
+            cnt = v["track_count"][s].cpu().numpy()
+            gxy = [v["track_xy"][s, c, : cnt[c]].cpu().numpy() for c in range(2)]
+            gid = [v["track_id"][s, c, : cnt[c]].cpu().numpy() for c in range(2)]
+            g_new = int(v["new_count"][s])
+            for c in range(2):
+                gpos = dict(zip(gid[c].tolist(), gxy[c].astype(np.float64)))
+                opos = dict(zip(st.ids[c].tolist(), st.xy[c].astype(np.float64)))
+                judged = set(prev_ids[c].tolist())
+                if c == 1:                       # this step's stereo matches too
+                    judged |= set(gid[0][len(gid[0]) - g_new:].tolist())
+                for i in judged:
+                    n_cmp += 1
+                    agree += (i in gpos) == (i in opos)
+                    if i in gpos and i in opos:
+                        errs.append(float(np.abs(gpos[i] - opos[i]).max()))
+            # detections: the oracle's, given the GPU's camera-0 survivors
+            g_new_xy = v["new_xy"][s, :g_new].cpu().numpy()
+            occ = ofe.occupancy(gxy[0][: max(int(cnt[0]) - g_new, 0)], w, h, cw, ch)
+            o_new_xy, _ = oracle.detect_grid(frames[t, 2 * s], cw, ch, k=k,
+                                             thresholds=op.thresholds, border=p.detect_border,
+                                             occupancy=occ)
+            new_total += 1
+            new_same += int(np.array_equal(g_new_xy, o_new_xy))
+            # the next step starts from the GPU's lists
+            st.xy = [gxy[0].copy(), gxy[1].copy()]
+            st.ids = [gid[0].copy(), gid[1].copy()]
+    fe.close()
+    e = np.array(errs) if errs else np.zeros(1)
+    return {"frames": n_frames, "streams": ns, "compared_tracks": n_cmp,
+            "max_flow_err_px": float(e.max()), "p99_flow_err_px": float(np.percentile(e, 99)),
+            "status_agree": agree / max(n_cmp, 1),
+            "detections_bit_exact": new_same / max(new_total, 1)}
+
+
+def accuracy_report(torch, vio, frames_np):
+    """Flow error and status agreement against the FP64 oracle for cfg 1, 2
+    and 3 and the lite parameters (accuracy_vs_oracle on a few frames each)."""
+    import numpy as np
+    from paper_2609_30459_gb300 import synth
+    out = {}
+    d = synth.stereo_pair_small_motion(1001, W, H)               # cfg 1: t and t + 1
+    out["cfg1"] = accuracy_vs_oracle(torch, vio, d["images"], 3, 94, 60, 2, 2)
+    out["cfg2"] = accuracy_vs_oracle(torch, vio, frames_np, LEVELS, CELL_W, CELL_H, K_CELL, 12)
+    seqs = [synth.make_sequence(3000 + i, 4, 1920, 1080, 1, max_motion=40.0,
+                                tex_size=2048).frames for i in range(2)]
+    out["cfg3"] = accuracy_vs_oracle(torch, vio, np.concatenate(seqs, 1), 5, 48, 43, 1, 4)
+    out["lite"] = accuracy_vs_oracle(torch, vio, frames_np, LEVELS, 82, 82, 1, 12,
+                                     params_kw={"gn_iters": 3, "thresholds": (40, 20)})
+    out["note"] = ("GPU frontend vs the FP64 oracle frontend, step by step with the GPU's lists "
+                   "handed to the oracle before each frame; flow error in level-0 px over the "
+                   "tracks both keep; status_agree over every temporal track and stereo match; "
+                   "cfg3 = the same seeds as other_configs[0]")
+    return out
+
+
 # the reference arm's timed frames end after this long, whatever the step count
 REFERENCE_BUDGET_S = 150.0
 
@@ -907,6 +995,7 @@ def main():
         serve = serving_run(torch, vio, args.serve_seconds, net, None, seqs=seqs4)
 
     cpu = None
+    accuracy = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         fps, cores, _ = oracle_frames_per_s(frames_np, args.cpu_frames)
         fps1, _, _ = oracle_frames_per_s(frames_np, 8, cores=1)
@@ -916,6 +1005,9 @@ def main():
                          f"over {cores} cores",
                "single_core": {"value": fps1, "unit": UNIT,
                                "sample": "8 frames after 2 warm-up frames, one thread"}}
+        # oracle-side accuracy of the same configs (the oracle runs on the host
+        # here, beside its timing)
+        accuracy = accuracy_report(torch, vio, frames_np)
 
     if rank == 0:
         line = {
@@ -935,7 +1027,7 @@ def main():
             "frontend_tune": fe_tune,
             "batched_16_streams": batched, "serving_32_streams": serve,
             "other_configs": extra_cfgs,
-            "cpu_baseline": cpu, "clocks": clk.summary(),
+            "cpu_baseline": cpu, "accuracy": accuracy, "clocks": clk.summary(),
             "host_wall_s": wall,
         }
         print(json.dumps(line), flush=True)

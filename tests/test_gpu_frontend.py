@@ -49,52 +49,77 @@ def _explained(res, ids, fb_max):
     return set(np.asarray(ids)[m].tolist())
 
 
-@pytest.mark.parametrize("cfg", ["cfg2_small", "cfg1_k2"])
+# Step-by-step cases: (w, h, levels, cell w, cell h, k, frames, max motion px,
+# stereo streams, thresholds, Gauss-Newton iterations).
+#  cfg2_small: the 752x480 sequence workload (4 levels, 20x15 cells, k = 1);
+#  cfg1_k2:    cfg 1 (3 levels, 8x8 cells of 94x60, k = 2, small motion);
+#  cfg3_rig:   the high-pixel rig, two stereo pairs at 1920x1080, 5 levels,
+#              40x25 cells of 48x43 px (1000 keypoints per image), motion 40 px;
+#  lite:       the paper's lite parameters (Sec. IV-D): minimum FAST threshold
+#              20, 82-px cells, 3 Gauss-Newton iterations.
+FRONTEND_CASES = {
+    "cfg2_small": (752, 480, 4, 37, 32, 1, 8, 15.0, 1, (40, 20, 10, 5), 5),
+    "cfg1_k2": (752, 480, 3, 94, 60, 2, 4, 3.0, 1, (40, 20, 10, 5), 5),
+    "cfg3_rig": (1920, 1080, 5, 48, 43, 1, 3, 40.0, 2, (40, 20, 10, 5), 5),
+    "lite": (752, 480, 4, 82, 82, 1, 8, 15.0, 1, (40, 20), 3),
+}
+
+
+@pytest.mark.parametrize("cfg", list(FRONTEND_CASES))
 def test_frontend_steps_match_oracle(cfg):
-    if cfg == "cfg2_small":
-        w, h, L, cw, ch, k, n_frames, motion = 752, 480, 4, 37, 32, 1, 8, 15.0
-    else:
-        w, h, L, cw, ch, k, n_frames, motion = 752, 480, 3, 94, 60, 2, 4, 3.0
-    seq = synth.make_sequence(4000 + n_frames, n_frames, w, h, 1, max_motion=motion,
+    w, h, L, cw, ch, k, n_frames, motion, ns, thr, gn = FRONTEND_CASES[cfg]
+    seq = synth.make_sequence(4000 + n_frames, n_frames, w, h, ns, max_motion=motion,
                               tex_size=2048)
-    p = vio.default_params(n_levels=L, cell_w=cw, cell_h=ch, k_per_cell=k)
-    op = ofe.Params(n_levels=L, cell_w=cw, cell_h=ch, k=k)
+    p = vio.default_params(n_levels=L, cell_w=cw, cell_h=ch, k_per_cell=k, thresholds=thr,
+                           gn_iters=gn)
+    op = ofe.Params(n_levels=L, cell_w=cw, cell_h=ch, k=k, thresholds=thr, gn_iters=gn)
     cap = 2 * (w // cw) * (h // ch) * k
-    fe = vio.Frontend(p, w, h, 1, cap)
-    frames = torch.from_numpy(seq.frames).cuda()                  # (F, 2, h, w)
-    st = ofe.StreamState()
-    prev_ids = [np.zeros(0, np.int32), np.zeros(0, np.int32)]
+    fe = vio.Frontend(p, w, h, ns, cap)
+    frames = torch.from_numpy(seq.frames).cuda().view(n_frames, ns, 2, h, w)
+    states = [ofe.StreamState() for _ in range(ns)]
+    prev_ids = [[np.zeros(0, np.int32), np.zeros(0, np.int32)] for _ in range(ns)]
     total_tracks = 0
+    total_new = 0
     for t in range(n_frames):
-        fe.step(frames[t: t + 1])
+        fe.step(frames[t])
         torch.cuda.synchronize()
         v = fe.view()
-        res = ofe.step(st, seq.frames[t], op, cap, n_threads=8)
-        # new detections on camera 0: bit-exact whenever the occupancy agrees
-        g_new = int(v["new_count"][0])
-        g_new_xy = v["new_xy"][0, :g_new].cpu().numpy()
-        cnt = v["track_count"][0].cpu().numpy()
-        gx = [v["track_xy"][0, c, : cnt[c]].cpu().numpy() for c in range(2)]
-        gi = [v["track_id"][0, c, : cnt[c]].cpu().numpy() for c in range(2)]
-        surv0 = cnt[0] - g_new
-        g_occ = ofe.occupancy(gx[0][:max(surv0, 0)], w, h, cw, ch)
-        if np.array_equal(g_occ, res["occupancy"]):
-            assert np.array_equal(g_new_xy, res["new_xy"]), t
-        # temporal tracks: explained differences only
-        expl = set()
-        for c in range(2):
-            if res["track"][c] is not None:
-                expl |= _explained(res["track"][c], prev_ids[c], p.fb_max_dist)
-        expl |= _explained(res["match"], st.ids[0][-len(res["new_xy"]):] if len(res["new_xy"])
-                           else [], p.fb_max_dist)
-        for c in range(2):
-            _check_track_lists(gx[c], gi[c], st.xy[c], st.ids[c], expl)
-        total_tracks += cnt.sum()
-        # hand the GPU state to the oracle for the next step
-        st.xy = [gx[0].copy(), gx[1].copy()]
-        st.ids = [gi[0].copy(), gi[1].copy()]
-        prev_ids = [gi[0].copy(), gi[1].copy()]
-    assert total_tracks > 0
+        for s in range(ns):
+            st = states[s]
+            img = seq.frames[t, 2 * s: 2 * s + 2]
+            res = ofe.step(st, img, op, cap, n_threads=8)
+            g_new = int(v["new_count"][s])
+            g_new_xy = v["new_xy"][s, :g_new].cpu().numpy()
+            cnt = v["track_count"][s].cpu().numpy()
+            gx = [v["track_xy"][s, c, : cnt[c]].cpu().numpy() for c in range(2)]
+            gi = [v["track_id"][s, c, : cnt[c]].cpu().numpy() for c in range(2)]
+            # the GPU's camera-0 survivors come first in its list: their
+            # occupancy, given to the oracle's detection, must give the GPU's
+            # detections bit for bit (whatever the threshold decisions upstream)
+            assert cnt[0] < cap            # no truncation: the survivors are cnt - new
+            surv0 = int(cnt[0]) - g_new
+            assert surv0 >= 0
+            g_occ = ofe.occupancy(gx[0][:surv0], w, h, cw, ch)
+            o_new_xy, _ = oracle.detect_grid(img[0], cw, ch, k=k, thresholds=thr,
+                                             border=p.detect_border, occupancy=g_occ)
+            assert np.array_equal(g_new_xy, o_new_xy), (t, s)
+            assert np.array_equal(gx[0][surv0:], g_new_xy)
+            total_new += g_new
+            # temporal tracks and matches: explained differences only
+            expl = set()
+            for c in range(2):
+                if res["track"][c] is not None:
+                    expl |= _explained(res["track"][c], prev_ids[s][c], p.fb_max_dist)
+            expl |= _explained(res["match"], st.ids[0][-len(res["new_xy"]):]
+                               if len(res["new_xy"]) else [], p.fb_max_dist)
+            for c in range(2):
+                _check_track_lists(gx[c], gi[c], st.xy[c], st.ids[c], expl)
+            total_tracks += int(cnt.sum())
+            # hand the GPU state to the oracle for the next step
+            st.xy = [gx[0].copy(), gx[1].copy()]
+            st.ids = [gi[0].copy(), gi[1].copy()]
+            prev_ids[s] = [gi[0].copy(), gi[1].copy()]
+    assert total_tracks > 0 and total_new > 0
     fe.close()
 
 

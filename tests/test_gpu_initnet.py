@@ -154,13 +154,55 @@ def test_forward_matches_oracle(n):
     assert np.median(err[:, :2]) < 16 * 1e-4
 
 
+def _kink_margin(p, x):
+    """Smallest |pre-activation| / (sum of the |terms| it adds up) of one
+    sample, over every ReLU input (FP64, BF16 activations)."""
+    _, a = onet.forward(p, x, keep=True, act_bf16=True)
+    ab = {k: np.abs(v) for k, v in p.items()}
+    sums = (onet.conv_s2(np.abs(x), ab["w1"], ab["b1"]), onet.conv_s2(a["h1"], ab["w2"], ab["b2"]),
+            onet.conv_s2(a["h2"], ab["w3"], ab["b3"]), ab["w4"] @ a["f"] + ab["b4"])
+    pre = (a["a1"], a["a2"], a["a3"], a["a4"])
+    return min(float((np.abs(u) / np.maximum(s_, 1e-300)).min()) for u, s_ in zip(pre, sums))
+
+
+def _abs_grad(p, xs, flows, radius):
+    """Per parameter, the mean over the batch of the sum of the |terms| that
+    make up its gradient: the backward pass with every factor replaced by its
+    magnitude (ReLU masks as they are)."""
+    ab = {k: np.abs(v) for k, v in p.items()}
+    acc = {k: np.zeros(onet.SHAPES[k]) for k in onet.ORDER}
+    for x, f in zip(xs, flows):
+        o, act = onet.forward(p, x, keep=True, act_bf16=True)
+        _, do = onet.loss_and_grad_out(o, f, radius)
+        act_abs = {k: (v if k.startswith("a") else np.abs(v)) for k, v in act.items()}
+        g = onet.backward(ab, act_abs, np.abs(do))
+        for k in onet.ORDER:
+            acc[k] += g[k]
+    return {k: v / len(xs) for k, v in acc.items()}
+
+
+# Per-element gradient bound. Both sides multiply the same BF16 weights and
+# BF16-stored activations; the GPU sums in FP32 (relative error ~1e-6) and can
+# store an activation one BF16 step (2^-8 relative) away from the oracle's
+# where the exact value sits next to a rounding tie. A gradient element is a
+# sum of products with at most four such factors on its path, so it moves by
+# at most 4 * 2^-8 times the sum of the |terms| it adds up (_abs_grad).
+# Samples are kept only where every ReLU input lies at least 2e-5 of its
+# |terms| away from zero (FP32 accumulation of up to 288 terms stays inside
+# that), so no ReLU mask can differ between the two sides.
+GRAD_REL = 4 * 2.0 ** -8
+KINK_MARGIN = 2e-5
+
+
 @pytest.mark.parametrize("radius", [1.0, 3.0])
 def test_train_gradient_matches_oracle(radius):
     n = 48
     flat = onet.flatten(he_params(2))
     _, packed = packed_of(flat)
     p = bf16_params(flat)
-    x = _inputs(n, 7)
+    pool = _inputs(4 * n, 7)
+    x = np.stack([xi for xi in pool if _kink_margin(p, xi) > KINK_MARGIN][:n])
+    assert len(x) == n
     rng = np.random.default_rng(8)
     # targets at a chosen distance from the oracle's prediction, away from the
     # label boundary so that both sides give every sample the same label
@@ -172,6 +214,7 @@ def test_train_gradient_matches_oracle(radius):
         flows.append([o[0] * 16 + r * np.cos(a), o[1] * 16 + r * np.sin(a)])
     flows = np.array(flows, np.float32).astype(np.float64)
     loss_ref, g_ref = onet.batch_loss_grad(p, x, flows, act_bf16=True, radius=radius)
+    g_abs = _abs_grad(p, x, flows, radius)
     xb = torch.from_numpy(bits_of(x.reshape(n, -1)).view(np.int16)).to(DEV)
     grad = torch.zeros(vio.INITNET_N_PARAMS, dtype=torch.float32, device=DEV)
     loss = torch.zeros(1, dtype=torch.float32, device=DEV)
@@ -181,10 +224,11 @@ def test_train_gradient_matches_oracle(radius):
     assert loss.item() / n == pytest.approx(loss_ref, rel=1e-3)
     g = onet.unflatten(grad.cpu().numpy().astype(np.float64))
     for k in onet.ORDER:
-        # BF16 weights enter the backward pass too: relative error ~2^-8 per
-        # product, averaging down over the sums
-        rel = np.linalg.norm(g[k] - g_ref[k]) / np.linalg.norm(g_ref[k])
-        assert rel < 2e-2, (k, rel)
+        bound = GRAD_REL * g_abs[k] + 1e-7 * np.abs(g_abs[k]).max()
+        err = np.abs(g[k] - g_ref[k])
+        assert np.all(err <= bound), (k, float((err / np.maximum(bound, 1e-300)).max()))
+        # and the typical element is far tighter than the bound
+        assert np.median(err / np.maximum(g_abs[k], 1e-300)) < 1e-4, k
 
 
 def test_train_index_selects_samples():

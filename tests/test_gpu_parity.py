@@ -216,7 +216,7 @@ def test_track_temporal_parity(w, h, L, n, fb):
         ref = oracle.track(oracle.pyramid(imgs[0, cam], L), oracle.pyramid(imgs[1, cam], L), kp,
                            fb=fb, fb_max_dist=p.fb_max_dist, n_threads=8)
         s = compare_tracks(out[0, : len(kp), :2].cpu().numpy(), st[0, : len(kp)].cpu().numpy(),
-                           ref, p.fb_max_dist)
+                           ref, p.fb_max_dist, g_theta=out[0, : len(kp), 2].cpu().numpy())
         assert s["n_ok"] >= 0.5 * len(kp), s
         assert (st[0, len(kp):] == 255).all()
         if fb:
@@ -246,7 +246,8 @@ def test_track_with_init_and_empty():
     torch.cuda.synchronize()
     ref = oracle.track(oracle.pyramid(imgs[0, 0], L), oracle.pyramid(imgs[1, 0], L), kp,
                        init=init, fb_max_dist=p.fb_max_dist)
-    compare_tracks(out[0, :, :2].cpu().numpy(), st[0].cpu().numpy(), ref, p.fb_max_dist)
+    compare_tracks(out[0, :, :2].cpu().numpy(), st[0].cpu().numpy(), ref, p.fb_max_dist,
+                   g_theta=out[0, :, 2].cpu().numpy())
     # zero keypoints: every slot EMPTY, nothing else touched
     cnt.zero_()
     ctx.track_patches(pyr, pyr.batch(0, 1, 1), pyr.batch(2, 1, 1), pts, cnt, cap, out, st)
