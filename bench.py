@@ -325,6 +325,124 @@ def pyramid_detect_roofline(torch, vio, frames_dev, peaks, peak_src, w=None, h=N
                     "selection; level 0 read once, upper levels and 10 B per keypoint written"}
 
 
+def selection_variants(torch, vio, frames_dev, w, h, levels, cw, ch, reps=5):
+    """The paper's per-cell selections (Sec. III-D) timed on one device-resident
+    batch through vio_pyramid_detect: k rounds of a warp maximum, a bitonic
+    k-sort and (k = 1) an atomic maximum, for k = 1 and k = 4; every mode must
+    give the same keypoints bit for bit."""
+    imgs = frames_dev.reshape(-1, h, w).contiguous()
+    n = imgs.shape[0]
+    pyr = vio.Pyramids(imgs, levels)
+    gx, gy = w // cw, h // ch
+    out = {"images": n, "image": f"{w}x{h}, {levels} levels, {gx}x{gy} cells of {cw}x{ch} px",
+           "ms": {}}
+    s = torch.cuda.current_stream()
+    for k, modes in ((1, (0, 1, 2)), (4, (0, 1))):
+        ref = None
+        for mode in modes:
+            p = vio.default_params(n_levels=levels, cell_w=cw, cell_h=ch, k_per_cell=k,
+                                   select_mode=mode)
+            ctx = vio.Context(p, w, h, n)
+            cap = gx * gy * k
+            kp = torch.zeros((n, cap, 2), dtype=torch.float32, device=imgs.device)
+            sc = torch.zeros((n, cap), dtype=torch.int16, device=imgs.device)
+            cnt = torch.zeros(n, dtype=torch.int32, device=imgs.device)
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            times = []
+            for it in range(reps + 2):
+                ev[0].record(s)
+                ctx.pyramid_detect(pyr, kp, sc, cnt, cap)
+                ev[1].record(s)
+                torch.cuda.synchronize()
+                if it >= 2:
+                    times.append(ev[0].elapsed_time(ev[1]))
+            res = (cnt.clone(), kp.clone(), sc.clone())
+            if ref is None:
+                ref = res
+            same = all(torch.equal(x, y) for x, y in zip(ref, res))
+            name = {0: "warp_max", 1: "bitonic", 2: "atomic_max"}[mode]
+            out["ms"][f"k{k}_{name}"] = statistics.median(times)
+            out.setdefault("identical", {})[f"k{k}_{name}"] = bool(same)
+            ctx.close()
+    return out
+
+
+def model_based_start(torch, vio, seeds=(8200, 8201, 8202), w=640, h=480, levels=5, cell=32,
+                      motion=40.0, n_frames=6, f=500.0):
+    """The paper's start of a track (Sec. III-E), fed with the generator's
+    ground-truth poses in place of a backend prediction: vio_predict_warp, then
+    the unchanged pyramidal tracker with the FB check, against the identity
+    start. Per frame pair of sequences with up to 40 px of motion: tracks that
+    end OK and within 0.5 px of the ground truth."""
+    import numpy as np
+    from paper_2609_30459_gb300 import synth
+    L = levels
+    tot = {"identity": 0, "model": 0, "n": 0}
+    t_pred = []
+    for seed in seeds:
+        seq = synth.make_sequence(seed, n_frames, w, h, 1, max_motion=motion, tex_size=2048)
+        frames = torch.from_numpy(np.ascontiguousarray(seq.frames[:, 0])).cuda()
+        p = vio.default_params(n_levels=L, cell_w=cell, cell_h=cell)
+        ctx = vio.Context(p, w, h, n_frames)
+        pyr = vio.Pyramids(frames, L)
+        cap = (w // cell) * (h // cell)
+        kp = torch.empty((n_frames, cap, 2), device="cuda")
+        sc = torch.empty((n_frames, cap), dtype=torch.int16, device="cuda")
+        cnt = torch.empty(n_frames, dtype=torch.int32, device="cuda")
+        ctx.pyramid_detect(pyr, kp, sc, cnt, cap)
+        poses, rhos = [], []
+        c_img = ((w - 1) / 2.0, (h - 1) / 2.0)
+        for t in range(n_frames - 1):
+            pa, pb = seq.poses[t][0], seq.poses[t + 1][0]
+            # the similarity poses of the generator as pinhole cameras looking
+            # at the plane fronto-parallel from depth f * s, rolled by th
+            def rz(a):
+                return np.array([[np.cos(a), -np.sin(a), 0], [np.sin(a), np.cos(a), 0], [0, 0, 1]])
+            Ca = np.array([pa.tx, pa.ty, -f * pa.s])
+            Cb = np.array([pb.tx, pb.ty, -f * pb.s])
+            R = rz(pb.th).T @ rz(pa.th)
+            tt = rz(pb.th).T @ (Ca - Cb)
+            poses.append(np.concatenate([R.reshape(-1), tt]))
+            rhos.append(1.0 / (f * pa.s))
+        n = n_frames - 1
+        pose = torch.from_numpy(np.array(poses, np.float32)).cuda()
+        rho = torch.from_numpy(np.repeat(np.array(rhos, np.float32)[:, None], cap, 1)).cuda()
+        pts = kp[:n].contiguous()
+        c = cnt[:n].contiguous()
+        init = torch.empty((n, cap, 3), device="cuda")
+        K = (f, f, c_img[0], c_img[1])
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        vio.predict_warp(K, K, pose, pts, rho, c, cap, n, init)
+        e1.record()
+        out = {}
+        for name, ini in (("identity", None), ("model", init)):
+            o = torch.empty((n, cap, 3), device="cuda")
+            st = torch.empty((n, cap), dtype=torch.uint8, device="cuda")
+            ctx.track_patches(pyr, pyr.batch(0, 1, n), pyr.batch(1, 1, n), pts, c, cap, o, st,
+                              init=ini)
+            out[name] = (o.cpu().numpy(), st.cpu().numpy())
+        torch.cuda.synchronize()
+        t_pred.append(e0.elapsed_time(e1))
+        kph, ch_ = pts.cpu().numpy(), c.cpu().numpy()
+        for t in range(n):
+            m = int(ch_[t])
+            gt = synth.PlanarScene.map_points(seq.poses[t][0], seq.poses[t + 1][0], kph[t, :m],
+                                              w, h, seq.c_tex)
+            tot["n"] += m
+            for name in ("identity", "model"):
+                o, st = out[name]
+                ok = (st[t, :m] == 0) & (np.abs(o[t, :m, :2] - gt).max(1) < 0.5)
+                tot[name] += int(ok.sum())
+        ctx.close()
+    return {"keypoints": tot["n"],
+            "ok_within_0.5px": {k: tot[k] / max(tot["n"], 1) for k in ("identity", "model")},
+            "predict_ms_per_launch": statistics.median(t_pred),
+            "workload": f"{len(seeds)} sequences of {n_frames} frames, {w}x{h}, motion up to "
+                        f"{motion:.0f} px, {levels} levels, {cell}-px cells; poses from the "
+                        "generator (pinhole f = 500 px over the textured plane)"}
+
+
 # Batched + learned initializer: 16 streams, 4 each of these sizes, cells for
 # 300 / 300 / 600 / 1000 keypoints per image, 5 levels, motion up to 40 px
 CFG4_CLASSES = [(640, 480, 32, 32), (752, 480, 37, 32), (1280, 720, 42, 36), (1920, 1080, 48, 43)]
@@ -959,7 +1077,18 @@ def main():
     # config 3 (4 cameras = two stereo pairs at 1920x1080, motion up to 40 px)
     # and the paper's lite parameters on 752x480 sequences like the headline's
     extra_cfgs = None
+    sel = None
+    mbs = None
     if rank == 0 and not args.no_batched:
+        # the cfg-3 frames (two stereo pairs of 1920x1080) as one detection batch
+        from paper_2609_30459_gb300 import synth
+        import numpy as np
+        seqs3 = [synth.make_sequence(3000 + i, 100, 1920, 1080, 1, max_motion=40.0,
+                                     tex_size=2048).frames for i in range(2)]
+        sel = selection_variants(torch, vio, torch.from_numpy(np.stack(seqs3, 1)).cuda(),
+                                 1920, 1080, 5, 48, 43)
+        del seqs3
+        mbs = model_based_start(torch, vio)
         extra_cfgs = [
             frontend_config_run(torch, vio, "cfg3 high-pixel: 4 cameras (2 stereo pairs) "
                                 "1920x1080, 100 frames, motion up to 40 px, 5 levels, 40x25 "
@@ -1027,6 +1156,7 @@ def main():
             "frontend_tune": fe_tune,
             "batched_16_streams": batched, "serving_32_streams": serve,
             "other_configs": extra_cfgs,
+            "selection_variants": sel, "model_based_start": mbs,
             "cpu_baseline": cpu, "accuracy": accuracy, "clocks": clk.summary(),
             "host_wall_s": wall,
         }

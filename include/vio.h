@@ -66,7 +66,7 @@ enum {
  * iterations per level (Sec. III-E), 50 px cells (Sec. IV-D). Values the
  * paper leaves open: 4 levels, round-to-nearest pyramid (Eq. 1), pattern 0,
  * forward-backward threshold 0.2 px, detection border 9 px (the level-0
- * reach of the tracking template). */
+ * reach of the tracking template), selection VIO_SELECT_WARP_MAX. */
 typedef struct {
   int32_t n_levels;                      /* pyramid levels incl. level 0, 1..8 */
   int32_t round_mode;                    /* 0 = nearest (Eq. 1), 1 = floor (Eq. 3) */
@@ -78,7 +78,18 @@ typedef struct {
   int32_t thresholds[VIO_MAX_THRESHOLDS];/* descending FAST thresholds, >= 0   */
   int32_t detect_border;                 /* candidates need b <= x <= w-1-b    */
   float fb_max_dist;                     /* forward-backward threshold, px     */
+  int32_t select_mode;                   /* per-cell top-k, VIO_SELECT_*       */
 } vio_params;
+
+/* How each cell's k strongest maxima are picked (Sec. III-D describes a
+ * bitonic k-sort per workgroup and an atomic-maximum variant for one
+ * keypoint per cell). Candidates carry unique packed keys (score << 32 |
+ * ~(y * w + x)), so every mode gives the same keypoints bit for bit:
+ *   VIO_SELECT_WARP_MAX: k rounds of a warp-wide maximum (default);
+ *   VIO_SELECT_BITONIC:  a bitonic sort of each warp's candidate keys;
+ *   VIO_SELECT_ATOMIC:   a 64-bit atomic maximum per cell, k = 1 only
+ *                        (other k: VIO_ERR_INVALID_ARG). */
+enum { VIO_SELECT_WARP_MAX = 0, VIO_SELECT_BITONIC = 1, VIO_SELECT_ATOMIC = 2 };
 
 void vio_params_default(vio_params* p);
 
@@ -249,6 +260,43 @@ vio_status vio_stereo_match(vio_ctx* ctx, const vio_pyr_layout* layout,
 vio_status vio_fb_check(const float* d_orig, const float* d_back, const int32_t* d_count,
                         int32_t capacity, int32_t n_images, float max_dist, uint8_t* d_status,
                         float* d_dist, void* stream);
+
+/* Sec. III-E, the start of a track: "the warp is initialized by projecting
+ * the pattern into the target image through the camera model, using the
+ * predicted pose and inverse depth". Pinhole cameras; the pose maps points of
+ * the source camera into the target camera, P' = R P + t (R row-major).
+ * For keypoint u with inverse depth rho: P = (1 / rho) K_src^-1 [u, 1], and
+ * u' = the projection of R P + t through K_dst. Each of the 52 pattern points
+ * u + x_i is projected the same way at the keypoint's inverse depth (a
+ * fronto-parallel patch) to y_i. The start warp is t = u' and theta = the
+ * angle of the least-squares rotation from the offsets x_i to y_i - u'
+ * (atan2 of sum x_i x (y_i - u') over sum x_i . (y_i - u')).
+ *   d_pose:      per image one vio_pose (device memory), e.g. the predicted
+ *                motion between the frames of each stream, or the stereo
+ *                extrinsics;
+ *   d_pts:       per image `capacity` float2 source positions (level-0 px);
+ *   d_inv_depth: per keypoint float, same indexing (1 / depth in the source
+ *                camera);
+ *   d_count:     per image int32 counts, or NULL for `capacity` each;
+ *   d_init:      per keypoint float3 (t_x, t_y, theta), the d_init of
+ *                vio_track_patches / vio_stereo_match;
+ *   d_valid:     per keypoint uint8, 1 where the prediction exists, or NULL.
+ * A keypoint with rho <= 0, or whose point or a pattern point is not in front
+ * of the target camera, gets the identity start (t = u, theta = 0) and
+ * valid 0; slots >= count are not written (valid 0). Invalid intrinsics
+ * (fx, fy <= 0) return VIO_ERR_INVALID_ARG. */
+typedef struct {
+  float fx, fy, cx, cy;
+} vio_pinhole;
+typedef struct {
+  float R[9];
+  float t[3];
+} vio_pose;
+
+vio_status vio_predict_warp(const vio_pinhole* k_src, const vio_pinhole* k_dst,
+                            const vio_pose* d_pose, const float* d_pts, const float* d_inv_depth,
+                            const int32_t* d_count, int32_t capacity, int32_t n_images,
+                            float* d_init, uint8_t* d_valid, void* stream);
 
 /* ------------------------------------------------------------- frontend -- */
 /* The per-frame frontend of Sec. III-B for n_streams independent stereo

@@ -11,20 +11,11 @@
 namespace {
 
 bool params_ok(const vio_params* p) {
-  if (!p) return false;
+  if (!vio::detect_params_ok(p)) return false;
   if (p->n_levels < 1 || p->n_levels > VIO_MAX_LEVELS) return false;
   if (p->round_mode != 0 && p->round_mode != 1) return false;
   if (p->gn_iters < 0 || p->gn_iters > 1000) return false;
   if (p->pattern_id != 0) return false;
-  if (p->cell_w < 1 || p->cell_h < 1 || p->cell_w > 512 || p->cell_h > 512) return false;
-  if (p->k_per_cell < 1 || p->k_per_cell > VIO_MAX_K) return false;
-  if (p->n_thresholds < 1 || p->n_thresholds > VIO_MAX_THRESHOLDS) return false;
-  for (int i = 0; i < p->n_thresholds; ++i) {
-    if (p->thresholds[i] < 0 || p->thresholds[i] > 254) return false;
-    // the sequence must not increase: the one-pass form relies on nesting
-    if (i > 0 && p->thresholds[i] > p->thresholds[i - 1]) return false;
-  }
-  if (p->detect_border < 0) return false;
   if (!(p->fb_max_dist >= 0.f)) return false;
   return true;
 }

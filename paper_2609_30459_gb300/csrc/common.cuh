@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
+
 #include "vio.h"
 
 namespace vio {
@@ -50,6 +52,44 @@ inline int sm_count() {
     n[dev] = v;
   }
   return n[dev];
+}
+
+// Host-side set-up that must run once on every device that launches a kernel
+// (function attributes are per device): f() runs under a lock the first time
+// a device is current here; its error is returned and the set-up is retried
+// at the next call.
+struct PerDeviceOnce {
+  std::mutex mu;
+  bool done[64] = {};
+};
+template <class F>
+inline cudaError_t once_per_device(PerDeviceOnce& o, F f) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return f();
+  std::lock_guard<std::mutex> lock(o.mu);
+  if (o.done[dev]) return cudaSuccess;
+  e = f();
+  if (e == cudaSuccess) o.done[dev] = true;
+  return e;
+}
+
+// The detection parameters of vio_params (cells, k, thresholds, border), as
+// every detection entry point validates them.
+inline bool detect_params_ok(const vio_params* p) {
+  if (!p) return false;
+  if (p->cell_w < 1 || p->cell_h < 1 || p->cell_w > 512 || p->cell_h > 512) return false;
+  if (p->k_per_cell < 1 || p->k_per_cell > VIO_MAX_K) return false;
+  if (p->n_thresholds < 1 || p->n_thresholds > VIO_MAX_THRESHOLDS) return false;
+  for (int i = 0; i < p->n_thresholds; ++i) {
+    if (p->thresholds[i] < 0 || p->thresholds[i] > 254) return false;
+    // the sequence must not increase: the one-pass form relies on nesting
+    if (i > 0 && p->thresholds[i] > p->thresholds[i - 1]) return false;
+  }
+  if (p->select_mode < VIO_SELECT_WARP_MAX || p->select_mode > VIO_SELECT_ATOMIC) return false;
+  if (p->select_mode == VIO_SELECT_ATOMIC && p->k_per_cell != 1) return false;
+  return p->detect_border >= 0;
 }
 
 inline Geom make_geom(const vio_pyr_layout& L) {

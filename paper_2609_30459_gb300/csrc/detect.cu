@@ -134,7 +134,8 @@ cudaError_t launch_detect(const vio_params& p, const Geom& g, const Batch& b,
   a.cand = cand;
   a.cand_count = cand_count;
   a.cg = det::CellGeom{p.cell_w, p.cell_h, g.w[0] / p.cell_w, p.k_per_cell,
-                       p.thresholds[p.n_thresholds - 1], p.detect_border, 1, 1, 1};
+                       p.thresholds[p.n_thresholds - 1], p.detect_border, 1, 1, 1,
+                       p.select_mode};
   a.gy = g.h[0] / p.cell_h;
   const int n_cells = a.cg.gx * a.gy;
   a.n_cells = n_cells;
@@ -142,14 +143,14 @@ cudaError_t launch_detect(const vio_params& p, const Geom& g, const Batch& b,
       a.cg, det::kThreads, det::warps_per_cell((long long)n_cells * b.n, sm_count()));
   if (smem < 0) return cudaErrorInvalidValue;
   if (n_cells > 0) {
-    static bool carveout = false;   // as much shared memory as the SM has: more CTAs
-    if (!carveout) {
-      const cudaError_t e = cudaFuncSetAttribute(detect_cells_kernel,
-                                                 cudaFuncAttributePreferredSharedMemoryCarveout,
-                                                 (int)cudaSharedmemCarveoutMaxShared);
-      if (e != cudaSuccess) return e;
-      carveout = true;
-    }
+    // as much shared memory as the SM has: more CTAs (once per device)
+    static PerDeviceOnce carveout;
+    const cudaError_t ec = once_per_device(carveout, [] {
+      return cudaFuncSetAttribute(detect_cells_kernel,
+                                  cudaFuncAttributePreferredSharedMemoryCarveout,
+                                  (int)cudaSharedmemCarveoutMaxShared);
+    });
+    if (ec != cudaSuccess) return ec;
     if (smem > 48 * 1024) {
       cudaError_t e = cudaFuncSetAttribute(detect_cells_kernel,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, smem);

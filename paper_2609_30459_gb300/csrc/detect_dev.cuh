@@ -98,11 +98,11 @@ __device__ __forceinline__ int ring_dy(int k) {
 
 struct BlockSmem {
   int rs, rows, stage_bytes;  // staged region: row stride (bytes), rows, bytes
-  int ms, mh;                 // map: row stride (16-bit elements, multiple of 4), rows
+  int msb, mh;                // maps: row stride (bytes, multiple of 8), rows
   int g;                      // warps per cell
   int qcap, kcap;             // queue and key entries per warp
-  int c_map, c_cols, c_red, c_merge, per_cell;   // byte offsets in a cell's piece
-  int w_queue, w_keys, per_warp;                  // byte offsets in a warp's piece
+  int c_u, c_v, c_cols, c_red, c_merge, per_cell;  // byte offsets in a cell's piece
+  int w_queue, w_keys, per_warp;                   // byte offsets in a warp's piece
   int cells_bytes, total;
 };
 
@@ -115,15 +115,17 @@ __host__ __device__ inline BlockSmem block_smem(int cw, int ch, int k, int bcx, 
   if (((S.rs >> 2) & 31) == 0) S.rs += 16;   // rows of the same column on other banks
   S.rows = bcy * ch + 2 * kHalo;
   S.stage_bytes = pyr::up16(S.rs * S.rows);
-  const int ms2 = (((cw + 2) / 2 + 2) + 1) & ~1;   // words per map row (even)
-  S.ms = 2 * ms2;
+  // a map row covers the cell and its ring from a 4-pixel boundary of the
+  // staged region, widened to whole 8-pixel words: at most cw + 5 -> 8 * ceil
+  S.msb = (cw + 5 + 7) & ~7;
   S.mh = ch + 2;
   S.g = g;
   S.qcap = 384;                                    // beyond it: pass C scans the map
   S.kcap = k + 32;
-  S.c_map = 16;                                    // a guard before and a row after
-  S.c_cols = S.c_map + pyr::up16(2 * S.ms * (S.mh + 1));
-  S.c_red = S.c_cols + pyr::up16(8 * ms2);
+  S.c_u = 16;                                      // guards around both maps
+  S.c_v = S.c_u + pyr::up16(S.msb * S.mh) + 16;
+  S.c_cols = S.c_v + pyr::up16(S.msb * S.mh) + 16;
+  S.c_red = S.c_cols + 16 * (S.msb / 4);
   S.c_merge = S.c_red + pyr::up16(4 * 2 * g);
   S.per_cell = S.c_merge + pyr::up16(8 * g * k);
   S.w_queue = 0;
@@ -144,7 +146,7 @@ __host__ __device__ inline bool pick_block(int cw, int ch, int k, int nt, int g_
                                            int& bcy, int& g) {
   const int nw = nt / 32;
   g = g_want < 1 ? 1 : (g_want > nw ? nw : g_want);
-  if (block_smem(cw, ch, k, 1, 1, 1).ms * (ch + 3) > 65535) return false;
+  if (block_smem(cw, ch, k, 1, 1, 1).msb * (ch + 2) > 65535) return false;
   for (; g >= 1; g >>= 1) {
     const int nc = nw / g;
     const int shapes[3][2] = {{nc >= 4 ? 4 : nc, nc >= 4 ? nc / 4 : 1}, {2, 1}, {1, 1}};
@@ -180,15 +182,20 @@ inline int warps_per_cell(long long n_cells, int n_sms) {
   return g;
 }
 
-// 16-bit lane j of a pair at image x = xp + j kept iff lo <= xp + j <= hi
-__device__ __forceinline__ unsigned pair_mask(int xp, int lo, int hi) {
+// 16-bit lanes of a pair at image x = xp (lane 0) and xp + 2 (lane 1): all
+// ones in a lane iff lo <= its x <= hi
+__device__ __forceinline__ unsigned pair_mask2(int xp, int lo, int hi) {
   return ((xp >= lo && xp <= hi) ? 0x0000ffffu : 0u) |
-         ((xp + 1 >= lo && xp + 1 <= hi) ? 0xffff0000u : 0u);
+         ((xp + 2 >= lo && xp + 2 <= hi) ? 0xffff0000u : 0u);
 }
 
-// per 16-bit lane: a >= b (bit 15 of the lane), for a, b in [0, 256]
-__device__ __forceinline__ unsigned ge2(unsigned a, unsigned b) {
-  return (a + 0x80008000u - b) & 0x80008000u;
+// Bit 7 of each byte of the result: that byte of a >= that byte of the
+// threshold tb (every byte the same t); tlo = tb & 0x7f7f7f7f. The low seven
+// bits compare by a borrow-free subtraction ((a | 0x80) - (t & 0x7f) keeps
+// bit 7 iff a & 0x7f >= t & 0x7f), bit 7 decides when the high bits differ.
+__device__ __forceinline__ unsigned bytes_ge(unsigned a, unsigned tb, unsigned tlo) {
+  const unsigned r = (a | 0x80808080u) - tlo;
+  return ((a & ~tb) | (~(a ^ tb) & r)) & 0x80808080u;
 }
 
 // m = score + 1 of the pixel at q (staged bytes, row stride rs), 0 if none:
@@ -246,10 +253,71 @@ __device__ __forceinline__ int warp_top_keys(const unsigned long long* keys, int
   return got;
 }
 
+// Top-k of a warp's keys by the cell's selection mode (VIO_SELECT_WARP_MAX or
+// VIO_SELECT_BITONIC; both give the same keys).
+__device__ __forceinline__ int select_top(int sel, const unsigned long long* keys, int n, int k,
+                                          unsigned long long* out);
+
 struct CellGeom {
   int cw, ch, gx, k, tmin, border;
   int bcx, bcy, g;   // cells per CTA, warps per cell
+  int sel;           // VIO_SELECT_* (per-cell top-k)
 };
+
+// Bitonic sort of 64 keys, two per lane (element lane and lane + 32), into
+// descending order across the warp (the paper's per-workgroup k-sort): for
+// each merge size m and distance j the pair (i, i ^ j) is ordered, larger
+// first where i & m == 0 (ascending blocks elsewhere, which the next merge
+// turns around).
+__device__ __forceinline__ void warp_bitonic64(unsigned long long& a, unsigned long long& b) {
+  const unsigned lane = threadIdx.x & 31u;
+#pragma unroll
+  for (unsigned m = 2; m <= 64; m <<= 1) {
+#pragma unroll
+    for (unsigned j = m >> 1; j >= 1; j >>= 1) {
+      if (j == 32) {              // pair (lane, lane + 32), both in this lane
+        const bool desc = (lane & m) == 0;
+        const unsigned long long hi = a > b ? a : b, lo = a > b ? b : a;
+        a = desc ? hi : lo;
+        b = desc ? lo : hi;
+      } else {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          unsigned long long& v = h ? b : a;
+          const unsigned i = lane + 32u * h;
+          const unsigned long long o = __shfl_xor_sync(0xffffffffu, v, j);
+          const bool lower = (i & j) == 0;          // this element is the pair's first
+          const bool desc = (i & m) == 0;
+          const bool keep_max = lower == desc;
+          v = keep_max ? (v > o ? v : o) : (v < o ? v : o);
+        }
+      }
+    }
+  }
+}
+
+// The largest min(k, n) nonzero keys of keys[0, n) (distinct, n <= 64), best
+// first, written by lane 0 to out[], by a bitonic sort; returns the count.
+__device__ __forceinline__ int warp_top_keys_sorted(const unsigned long long* keys, int n, int k,
+                                                    unsigned long long* out) {
+  const int lane = threadIdx.x & 31;
+  unsigned long long a = lane < n ? keys[lane] : 0ull;
+  unsigned long long b = lane + 32 < n ? keys[lane + 32] : 0ull;
+  warp_bitonic64(a, b);
+  const unsigned nz = __ballot_sync(0xffffffffu, a != 0ull);
+  int got = __popc(nz) + __popc(__ballot_sync(0xffffffffu, b != 0ull));
+  got = got < k ? got : k;
+  __syncwarp();
+  if (lane < got) out[lane] = a;   // k <= 8 < 32: the best k sit in the first lanes
+  __syncwarp();
+  return got;
+}
+
+__device__ __forceinline__ int select_top(int sel, const unsigned long long* keys, int n, int k,
+                                          unsigned long long* out) {
+  return sel == VIO_SELECT_BITONIC ? warp_top_keys_sorted(keys, n, k, out)
+                                   : warp_top_keys(keys, n, k, out);
+}
 
 // Synchronises the g warps of a cell (named barrier `bar` in 1..4, or the
 // warp). Constant barrier ids keep the kernel's barrier count at 5, which
@@ -268,24 +336,38 @@ __device__ __forceinline__ void group_sync(int g, int bar) {
   }
 }
 
-// Exact scores of queue entries [e0, e1) (one per lane) into the map's low
-// bytes.
+// Exact scores of queue entries [e0, e1) (one per lane) into the value map.
 __device__ __forceinline__ void eval_entries(const uint16_t* queue, int e0, int e1,
                                              const uint8_t* st, int rs, int srow0, int c0,
-                                             const Split& sm, int T, uint8_t* map8) {
+                                             const Split& sm, int T, uint8_t* vmap) {
   const int e = e0 + (threadIdx.x & 31);
   if (e < e1) {
     const int idx = queue[e];
     int r, c;
     sm(idx, r, c);
     const int m = fast_m_pair(st + (srow0 + r) * rs + c0 + c, rs);
-    map8[2 * idx] = (uint8_t)max(m - T, 0);
+    vmap[idx] = (uint8_t)max(m - T, 0);
   }
 }
 
 // Detection in one cell by warp gw of its g warps. st: the block's staged
-// region (16-bit pixels, row stride rs, column 0 at image x sxa, row 0 at
-// image y sy0). Writes up to k packed keys (best first) and the count.
+// region (bytes, row stride rs, column 0 at image x sxa, a multiple of 16,
+// row 0 at image y sy0). Writes up to k packed keys (best first) and the
+// count.
+//
+// Two byte maps cover the cell and its 1-pixel ring from a 4-pixel boundary
+// of the staged region (map column 0 at image x mx0), rows y0 - 1 .. y0 + ch:
+//   U: ub - T_min (clamped at 0), the bound; a pixel's byte is cleared once it
+//      is queued for its exact score, so each pixel is scored once;
+//   V: the value the 3x3 maximum test compares: (m - T_min)+ once scored, the
+//      bound before (a pixel that is not scored has ub < t <= m of any pixel
+//      tested against it).
+// Pass A computes the bound four pixels per thread: the 32-bit staged word
+// x .. x + 3 splits into the 16-bit pairs (x, x + 2) and (x + 1, x + 3).
+// Each round at threshold t scans U eight pixels per thread with byte-wise
+// compares, queues the pixels whose bound reaches t and scores them 32 at a
+// time; pass C then tests every scored pixel with a value in [t, tp) for a
+// strict maximum in the cell.
 template <bool MASKED>
 __device__ __forceinline__ void detect_cell(const uint8_t* __restrict__ st, int rs, int sxa,
                                             int sy0, int W, int H, const CellGeom& cg, int cx,
@@ -299,69 +381,78 @@ __device__ __forceinline__ void detect_cell(const uint8_t* __restrict__ st, int 
   const int lane = threadIdx.x & 31, tg = gw * 32 + lane;
   const int cw = cg.cw, ch = cg.ch, T = cg.tmin, b = cg.border, k = cg.k;
   const int x0 = cx * cw, y0 = cy * ch;
-  const int pa = ((x0 - 1 - sxa) >> 1) & ~1;                // staged pair of map column 0 (even)
-  const int nq = (((x0 + cw - sxa) >> 1) - pa + 2) >> 1;     // quads (two pairs) per map row
-  const int mx0 = sxa + 2 * pa;                              // image x of map column 0
-  const int MH = ch + 2, MS = S.ms, MQ = S.ms >> 2;          // map quads per row
-  const int srow0 = y0 - 1 - sy0;                            // staged row of map row 0
-  const int rw = rs >> 2;                                    // staged words per row
-  const unsigned* st32 = reinterpret_cast<const unsigned*>(st);
-  uint2* map64 = reinterpret_cast<uint2*>(csm + S.c_map);
-  uint8_t* map8 = csm + S.c_map;
-  unsigned* colm = reinterpret_cast<unsigned*>(csm + S.c_cols);   // [pair]: ring, cell masks
+  const int c0 = (x0 - 1 - sxa) & ~3;                    // staged column of map column 0
+  const int mx0 = sxa + c0;                              // image x of map column 0
+  const int MW = (x0 + cw + 1 - mx0 + 7) & ~7;           // map columns (multiple of 8)
+  const int nq = MW >> 2, n8 = MW >> 3;                  // quads, 8-pixel words per row
+  const int MH = ch + 2, MSB = S.msb;
+  const int srow0 = y0 - 1 - sy0;                        // staged row of map row 0
+  uint8_t* umap = csm + S.c_u;
+  uint8_t* vmap = csm + S.c_v;
+  uint4* colm = reinterpret_cast<uint4*>(csm + S.c_cols);   // per quad: ring, cell masks
   int* red = reinterpret_cast<int*>(csm + S.c_red);
   unsigned long long* merge = reinterpret_cast<unsigned long long*>(csm + S.c_merge);
   uint16_t* queue = reinterpret_cast<uint16_t*>(wsm + S.w_queue);
   unsigned long long* keys = reinterpret_cast<unsigned long long*>(wsm + S.w_keys);
 
-  // per pair column: lanes where the bound is defined (FAST ring inside the
-  // image, inside the cell's ring region) and lanes inside the cell
-  for (int p = tg; p < 2 * nq; p += GT) {
-    const int xp = mx0 + 2 * p;
-    colm[2 * p] = pair_mask(xp, max(x0 - 1, 3), min(x0 + cw, W - 4));
-    colm[2 * p + 1] = pair_mask(xp, max(x0, b), min(x0 + cw - 1, W - 1 - b));
+  // per quad: lanes where the bound is defined (FAST ring inside the image,
+  // inside the cell's ring region) and lanes inside the cell
+  for (int q = tg; q < nq; q += GT) {
+    const int xq = mx0 + 4 * q;
+    const int rl = max(x0 - 1, 3), rh = min(x0 + cw, W - 4);
+    const int cl = max(x0, b), chh = min(x0 + cw - 1, W - 1 - b);
+    colm[q] = make_uint4(pair_mask2(xq, rl, rh), pair_mask2(xq, cl, chh),
+                         pair_mask2(xq + 1, rl, rh), pair_mask2(xq + 1, cl, chh));
   }
+  const bool atomic_sel = cg.sel == VIO_SELECT_ATOMIC;   // k == 1: one 64-bit maximum per cell
+  if (atomic_sel && tg == 0) merge[0] = 0ull;
   group_sync(G, bar);
 
-  // this thread's quads: i = tg + j * GT -> (row r, quad q), stepped without divisions
-  const int n_items = MH * nq;
-  const int dr = GT / nq, dq = GT - dr * nq;
-  const int r_start = tg / nq, q_start = tg - r_start * nq;
-
-  // pass A: bounds of the cell and its ring, the largest of the cell's
+  // pass A: bounds of the cell and its ring, the largest of the cell's; this
+  // thread's quads i = tg + j * GT -> (row r, quad q), stepped without divisions
   const unsigned K = (0x100u + (unsigned)T) * 0x00010001u;
   unsigned acc = 0;
   {
-    int r = r_start, q = q_start;
+    const int n_items = MH * nq;
+    const int dr = GT / nq, dq = GT - dr * nq;
+    int r = tg / nq, q = tg - (tg / nq) * nq;
     for (int i = tg; i < n_items; i += GT) {
       const int y = y0 - 1 + r;
-      const unsigned* sq = st32 + (srow0 + r) * rw + (pa >> 1) + q;   // pixels x .. x+3
-      const unsigned Cw = sq[0], Uw = sq[-3 * rw], Dw = sq[3 * rw], Lw = sq[-1], Rw = sq[1];
-      const uint2 C = make_uint2(__byte_perm(Cw, 0u, 0x4140), __byte_perm(Cw, 0u, 0x4342));
-      const uint2 U = make_uint2(__byte_perm(Uw, 0u, 0x4140), __byte_perm(Uw, 0u, 0x4342));
-      const uint2 D = make_uint2(__byte_perm(Dw, 0u, 0x4140), __byte_perm(Dw, 0u, 0x4342));
-      const unsigned V12a = __byte_perm(Lw, 0u, 0x4241);                  // x - 3, x - 2
-      const unsigned V12b = __byte_perm(Lw, Cw, 0x0403) & 0x00ff00ffu;    // x - 1, x
-      const unsigned V4a = __byte_perm(Cw, Rw, 0x0403) & 0x00ff00ffu;     // x + 3, x + 4
-      const unsigned V4b = __byte_perm(Rw, 0u, 0x4241);                   // x + 5, x + 6
-      const unsigned hia = __vminu2(__vmaxu2(U.x, D.x), __vmaxu2(V4a, V12a));
-      const unsigned loa = __vmaxu2(__vminu2(U.x, D.x), __vminu2(V4a, V12a));
-      const unsigned hib = __vminu2(__vmaxu2(U.y, D.y), __vmaxu2(V4b, V12b));
-      const unsigned lob = __vmaxu2(__vminu2(U.y, D.y), __vminu2(V4b, V12b));
+      const uint8_t* sq = st + (srow0 + r) * rs + c0 + 4 * q;           // pixels x .. x + 3
+      const unsigned Cw = *reinterpret_cast<const unsigned*>(sq);
+      const unsigned Uw = *reinterpret_cast<const unsigned*>(sq - 3 * rs);
+      const unsigned Dw = *reinterpret_cast<const unsigned*>(sq + 3 * rs);
+      const unsigned Lw = *reinterpret_cast<const unsigned*>(sq - 4);
+      const unsigned Rw = *reinterpret_cast<const unsigned*>(sq + 4);
+      // pair a = pixels (x, x + 2), pair b = (x + 1, x + 3); compass points
+      // of the ring: up, down (rows -3, +3), left (x - 3), right (x + 3)
+      const unsigned Ca = __byte_perm(Cw, 0u, 0x4240), Cb = __byte_perm(Cw, 0u, 0x4341);
+      const unsigned Ua = __byte_perm(Uw, 0u, 0x4240), Ub = __byte_perm(Uw, 0u, 0x4341);
+      const unsigned Da = __byte_perm(Dw, 0u, 0x4240), Db = __byte_perm(Dw, 0u, 0x4341);
+      const unsigned La = __byte_perm(Lw, 0u, 0x4341);                     // x - 3, x - 1
+      const unsigned Lb = __byte_perm(Lw, Cw, 0x0402) & 0x00ff00ffu;      // x - 2, x
+      const unsigned Ra = __byte_perm(Cw, Rw, 0x0503) & 0x00ff00ffu;      // x + 3, x + 5
+      const unsigned Rb = __byte_perm(Rw, 0u, 0x4240);                     // x + 4, x + 6
+      const unsigned hia = __vminu2(__vmaxu2(Ua, Da), __vmaxu2(Ra, La));
+      const unsigned loa = __vmaxu2(__vminu2(Ua, Da), __vminu2(Ra, La));
+      const unsigned hib = __vminu2(__vmaxu2(Ub, Db), __vmaxu2(Rb, Lb));
+      const unsigned lob = __vmaxu2(__vminu2(Ub, Db), __vminu2(Rb, Lb));
       // 0x100 + max(hi - c, c - lo) per lane, then max(ub - T, 0)
-      const unsigned da = __vmaxu2(hia + 0x01000100u - C.x, C.x + 0x01000100u - loa);
-      const unsigned db = __vmaxu2(hib + 0x01000100u - C.y, C.y + 0x01000100u - lob);
-      const uint4 cm = reinterpret_cast<const uint4*>(colm)[q];
+      const unsigned da = __vmaxu2(hia + 0x01000100u - Ca, Ca + 0x01000100u - loa);
+      const unsigned db = __vmaxu2(hib + 0x01000100u - Cb, Cb + 0x01000100u - lob);
+      const uint4 cm = colm[q];
       const bool yf = y >= 3 && y <= H - 4;
       const unsigned ua = (__vmaxu2(da, K) - K) & (yf ? cm.x : 0u);
       const unsigned ub = (__vmaxu2(db, K) - K) & (yf ? cm.z : 0u);
-      map64[r * MQ + q] = make_uint2(ua * 0x0101u, ub * 0x0101u);
+      const unsigned word = __byte_perm(ua, ub, 0x6240);                   // x .. x + 3
+      *reinterpret_cast<unsigned*>(umap + r * MSB + 4 * q) = word;
+      *reinterpret_cast<unsigned*>(vmap + r * MSB + 4 * q) = word;
       const bool yc = (unsigned)(r - 1) < (unsigned)ch && y >= b && y <= H - 1 - b;
       unsigned ca = ua & (yc ? cm.y : 0u), cb = ub & (yc ? cm.w : 0u);
       if (MASKED && (ca | cb)) {   // only in-cell pixels are read
         const uint8_t* mr = mask + (long long)y * W + mx0 + 4 * q;
-        ca &= ((ca & 0xffffu) && mr[0] ? 0x0000ffffu : 0u) | ((ca >> 16) && mr[1] ? 0xffff0000u : 0u);
-        cb &= ((cb & 0xffffu) && mr[2] ? 0x0000ffffu : 0u) | ((cb >> 16) && mr[3] ? 0xffff0000u : 0u);
+        ca &= ((ca & 0xffffu) && mr[0] ? 0x0000ffffu : 0u) | ((ca >> 16) && mr[2] ? 0xffff0000u : 0u);
+        cb &= ((cb & 0xffffu) && mr[1] ? 0x0000ffffu : 0u) | ((cb >> 16) && mr[3] ? 0xffff0000u : 0u);
       }
       acc = __vmaxu2(acc, __vmaxu2(ca, cb));
       q += dq;
@@ -381,72 +472,74 @@ __device__ __forceinline__ void detect_cell(const uint8_t* __restrict__ st, int 
   }
   group_sync(G, bar);
 
-  const Split sm(MS);
+  const Split sm(MSB);
   const unsigned lt_mask = (1u << lane) - 1u;
-  const int c0 = 2 * pa;       // staged column of map column 0
   int nk = 0, q_end = 0, q_eval = 0, fw = 0;
-  bool overflow = false;   // the queue lost evaluated pixels
+  bool overflow = false;   // the queue lost scored pixels
   if (umax > 0) {
     int tp = 256;              // t_prev, above every shifted value
-    int t = max(umax - 24, 1);
+    int t = max(umax - 16, 1);
+    const int n_words = MH * n8;
+    const int dr8 = GT / n8, dc8 = GT - dr8 * n8;
     for (;;) {
-      const unsigned t2 = (unsigned)t * 0x00010001u, tp2 = (unsigned)tp * 0x00010001u;
-      // pass B: queue this warp's pixels whose bound is in [t, tp); exact
-      // scores 32 at a time
+      // pass B: queue this warp's pixels whose bound reaches t (their U
+      // bytes are cleared), exact scores 32 at a time
       {
-        int r = r_start, q = q_start;
-        for (int base = gw * 32; base < n_items; base += GT) {
+        const unsigned tb = (unsigned)t * 0x01010101u, tlo = tb & 0x7f7f7f7fu;
+        int r = tg / n8, c8 = tg - (tg / n8) * n8;
+        for (int base = gw * 32; base < n_words; base += GT) {
           const int i = base + lane;
-          unsigned ha = 0, hb = 0;
-          int idx = 0;
-          if (i < n_items) {
-            const uint2 w = map64[r * MQ + q];
-            const unsigned ua = (w.x >> 8) & 0x00ff00ffu, ub = (w.y >> 8) & 0x00ff00ffu;
-            ha = ge2(ua, t2) & ~ge2(ua, tp2);
-            hb = ge2(ub, t2) & ~ge2(ub, tp2);
-            idx = r * MS + 4 * q;
-          }
-          q += dq;
-          r += dr;
-          if (q >= nq) {
-            q -= nq;
+          uint2 w = make_uint2(0u, 0u);
+          const int idx0 = r * MSB + 8 * c8;
+          if (i < n_words) w = *reinterpret_cast<const uint2*>(umap + idx0);
+          c8 += dc8;
+          r += dr8;
+          if (c8 >= n8) {
+            c8 -= n8;
             ++r;
           }
-          const unsigned b0 = __ballot_sync(FULL, ha & 0x8000u);
-          const unsigned b1 = __ballot_sync(FULL, ha & 0x80000000u);
-          const unsigned b2 = __ballot_sync(FULL, hb & 0x8000u);
-          const unsigned b3 = __ballot_sync(FULL, hb & 0x80000000u);
-          const int total = __popc(b0) + __popc(b1) + __popc(b2) + __popc(b3);
-          if (total == 0) continue;
-          if (q_end + 128 > S.qcap) {   // full: score what is pending, drop the list
-            eval_entries(queue, q_eval, q_end, st, rs, srow0, c0, sm, T, map8);
+          const unsigned hx = bytes_ge(w.x, tb, tlo), hy = bytes_ge(w.y, tb, tlo);
+          const int cnt = __popc(hx) + __popc(hy);
+          if (__ballot_sync(FULL, cnt != 0) == 0) continue;
+          int incl = cnt;
+#pragma unroll
+          for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(FULL, incl, o);
+            if (lane >= o) incl += v;
+          }
+          const int total = __shfl_sync(FULL, incl, 31);
+          if (q_end + total > S.qcap) {   // full: score what is pending, drop the list
+            eval_entries(queue, q_eval, q_end, st, rs, srow0, c0, sm, T, vmap);
             __syncwarp();
             q_end = q_eval = 0;
             overflow = true;
           }
-          int off = q_end + __popc(b0 & lt_mask) + __popc(b1 & lt_mask) +
-                    __popc(b2 & lt_mask) + __popc(b3 & lt_mask);
-          if (ha & 0x8000u) queue[off++] = (uint16_t)idx;
-          if (ha & 0x80000000u) queue[off++] = (uint16_t)(idx + 1);
-          if (hb & 0x8000u) queue[off++] = (uint16_t)(idx + 2);
-          if (hb & 0x80000000u) queue[off] = (uint16_t)(idx + 3);
+          if (cnt) {
+            int off = q_end + incl - cnt;
+            for (unsigned h = hx; h; h &= h - 1) queue[off++] = (uint16_t)(idx0 + ((__ffs(h) - 1) >> 3));
+            for (unsigned h = hy; h; h &= h - 1) queue[off++] = (uint16_t)(idx0 + 4 + ((__ffs(h) - 1) >> 3));
+            w.x &= ~((hx >> 7) * 0xffu);
+            w.y &= ~((hy >> 7) * 0xffu);
+            *reinterpret_cast<uint2*>(umap + idx0) = w;
+          }
           q_end += total;
           __syncwarp();
           while (q_end - q_eval >= 32) {
-            eval_entries(queue, q_eval, q_eval + 32, st, rs, srow0, c0, sm, T, map8);
+            eval_entries(queue, q_eval, q_eval + 32, st, rs, srow0, c0, sm, T, vmap);
             q_eval += 32;
           }
         }
-        eval_entries(queue, q_eval, q_end, st, rs, srow0, c0, sm, T, map8);
+        eval_entries(queue, q_eval, q_end, st, rs, srow0, c0, sm, T, vmap);
         q_eval = q_end;
       }
       group_sync(G, bar);
-      // pass C: evaluated pixels with a value in [t, tp) that lie in the cell
-      // and exceed all 8 neighbours, from this warp's queue (or from its part
-      // of the map when the queue did not hold every evaluated pixel)
+      // pass C: scored pixels with a value in [t, tp) that lie in the cell
+      // and exceed all 8 neighbours, from this warp's queue (or from the map
+      // words this warp scans, when its queue did not hold every pixel it
+      // scored: a pixel with a value >= t has been scored)
       int found = 0;
       auto test = [&](int idx) -> unsigned long long {
-        const int v = map8[2 * idx];
+        const int v = vmap[idx];
         if (v < t || v >= tp) return 0ull;
         int r, c;
         sm(idx, r, c);
@@ -454,9 +547,9 @@ __device__ __forceinline__ void detect_cell(const uint8_t* __restrict__ st, int 
         if ((unsigned)(r - 1) >= (unsigned)ch || x < x0 || x >= x0 + cw || x < b ||
             x > W - 1 - b || y < b || y > H - 1 - b)
           return 0ull;
-        const uint8_t* m = map8 + 2 * idx;
-        if (!(v > m[-2] && v > m[2] && v > m[-2 * MS - 2] && v > m[-2 * MS] &&
-              v > m[-2 * MS + 2] && v > m[2 * MS - 2] && v > m[2 * MS] && v > m[2 * MS + 2]))
+        const uint8_t* m = vmap + idx;
+        if (!(v > m[-1] && v > m[1] && v > m[-MSB - 1] && v > m[-MSB] && v > m[-MSB + 1] &&
+              v > m[MSB - 1] && v > m[MSB] && v > m[MSB + 1]))
           return 0ull;
         if (MASKED && mask[(long long)y * W + x] == 0) return 0ull;
         return ((unsigned long long)(v + T - 1) << 32) | (unsigned)(~(unsigned)(y * W + x));
@@ -465,8 +558,13 @@ __device__ __forceinline__ void detect_cell(const uint8_t* __restrict__ st, int 
         const unsigned bc = __ballot_sync(FULL, key != 0ull);
         if (bc == 0) return;
         const int total = __popc(bc);
+        if (atomic_sel) {
+          if (key) atomicMax(merge, key);
+          found += total;
+          return;
+        }
         if (nk + total > S.kcap) {   // keep the k best so far (merge slot as scratch)
-          const int n = warp_top_keys(keys, nk, k, merge + gw * k);
+          const int n = select_top(cg.sel, keys, nk, k, merge + gw * k);
           __syncwarp();
           if (lane < n) keys[lane] = merge[gw * k + lane];
           nk = n;
@@ -483,21 +581,19 @@ __device__ __forceinline__ void detect_cell(const uint8_t* __restrict__ st, int 
           consider(e < q_end ? test(queue[e]) : 0ull);
         }
       } else {
-        int r = r_start, q = q_start;
-        for (int base = gw * 32; base < n_items; base += GT) {
-          const bool live = base + lane < n_items;
-          const int idx0 = r * MS + 4 * q;
-          q += dq;
-          r += dr;
-          if (q >= nq) {
-            q -= nq;
+        // the 8-pixel words this warp scanned in pass B (the pixels it queued)
+        int r = tg / n8, c8 = tg - (tg / n8) * n8;
+        for (int base = gw * 32; base < n_words; base += GT) {
+          const bool live = base + lane < n_words;
+          const int idx0 = r * MSB + 8 * c8;
+          c8 += dc8;
+          r += dr8;
+          if (c8 >= n8) {
+            c8 -= n8;
             ++r;
           }
 #pragma unroll 1
-          for (int j = 0; j < 4; ++j) {
-            const int idx = idx0 + j;
-            consider(live && map8[2 * idx + 1] >= t ? test(idx) : 0ull);
-          }
+          for (int j = 0; j < 8; ++j) consider(live ? test(idx0 + j) : 0ull);
         }
       }
       // candidates of the whole cell (all g warps, all rounds so far)
@@ -511,20 +607,28 @@ __device__ __forceinline__ void detect_cell(const uint8_t* __restrict__ st, int 
       }
       if (n_found >= k || t <= 1) break;
       tp = t;
-      t = max(t - 24, 1);
+      t = max(t - 16, 1);
     }
   }
-  // top k of the cell: each warp's best k, then the best k of those
-  if (G == 1) {
-    const int n = warp_top_keys(keys, nk, k, out_keys);
+  // top k of the cell: each warp's best k, then the best k of those (or,
+  // with the atomic maximum, the cell's one slot)
+  if (atomic_sel) {
+    group_sync(G, bar);
+    if (tg == 0) {
+      const unsigned long long best = merge[0];
+      if (best) out_keys[0] = best;
+      *out_count = best ? 1 : 0;
+    }
+  } else if (G == 1) {
+    const int n = select_top(cg.sel, keys, nk, k, out_keys);
     if (lane == 0) *out_count = n;
   } else {
-    const int n = warp_top_keys(keys, nk, k, merge + gw * k);
+    const int n = select_top(cg.sel, keys, nk, k, merge + gw * k);
     if (lane == 0)
       for (int j = n; j < k; ++j) merge[gw * k + j] = 0ull;
     group_sync(G, bar);
     if (gw == 0) {
-      const int n2 = warp_top_keys(merge, G * k, k, out_keys);
+      const int n2 = select_top(cg.sel, merge, G * k, k, out_keys);
       if (lane == 0) *out_count = n2;
     }
   }

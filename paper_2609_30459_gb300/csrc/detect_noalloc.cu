@@ -56,18 +56,6 @@ bool scratch_for_current_device(unsigned long long** cand, int32_t** count) {
   return true;
 }
 
-bool noalloc_params_ok(const vio_params* p) {
-  if (!p || p->n_levels < 1 || p->n_levels > VIO_MAX_LEVELS) return false;
-  if (p->cell_w < 1 || p->cell_h < 1 || p->cell_w > 512 || p->cell_h > 512) return false;
-  if (p->k_per_cell < 1 || p->k_per_cell > VIO_MAX_K) return false;
-  if (p->n_thresholds < 1 || p->n_thresholds > VIO_MAX_THRESHOLDS) return false;
-  for (int i = 0; i < p->n_thresholds; ++i) {
-    if (p->thresholds[i] < 0 || p->thresholds[i] > 254) return false;
-    if (i > 0 && p->thresholds[i] > p->thresholds[i - 1]) return false;
-  }
-  return p->detect_border >= 0;
-}
-
 }  // namespace
 
 extern "C" vio_status vio_detect_grid_noalloc(const vio_params* p, const vio_pyr_layout* layout,
@@ -76,7 +64,8 @@ extern "C" vio_status vio_detect_grid_noalloc(const vio_params* p, const vio_pyr
                                               int64_t mask_stride, float* d_kp, int16_t* d_score,
                                               int32_t* d_count, int32_t capacity,
                                               void* stream) {
-  if (!noalloc_params_ok(p) || !layout || layout->n_levels < 1 || layout->w[0] < 1 ||
+  if (!vio::detect_params_ok(p) || p->n_levels < 1 || p->n_levels > VIO_MAX_LEVELS ||
+      !layout || layout->n_levels < 1 || layout->w[0] < 1 ||
       layout->h[0] < 1 || layout->pitch[0] < layout->w[0])
     return VIO_ERR_INVALID_ARG;
   if (!batch || batch->n_images < 1 || !batch->d_level0 || !d_kp || !d_score || !d_count ||
@@ -89,9 +78,10 @@ extern "C" vio_status vio_detect_grid_noalloc(const vio_params* p, const vio_pyr
   if (!vio::det::detect_fits(p->cell_w, p->cell_h, p->k_per_cell))
     return VIO_ERR_UNSUPPORTED;
   const long long cells = (long long)(layout->w[0] / p->cell_w) * (layout->h[0] / p->cell_h);
-  // the fixed scratch bounds the work of one call
+  // the fixed scratch bounds the work of one call (k >= 1, so the count array,
+  // one entry per cell, is within its bound whenever the key slots are)
   if ((long long)batch->n_images * cells * p->k_per_cell > VIO_NOALLOC_MAX_CELL_SLOTS ||
-      (long long)batch->n_images * cells > VIO_NOALLOC_MAX_CELL_SLOTS || batch->n_images > 65535)
+      batch->n_images > 65535)
     return VIO_ERR_UNSUPPORTED;
   unsigned long long* cand = nullptr;
   int32_t* count = nullptr;

@@ -775,7 +775,7 @@ K1Args front_args(const vio_params& p, const Geom& g, const Batch& all, int det_
   a.n_cells = gx * gy;
   a.gy = gy;
   a.cg = det::CellGeom{p.cell_w, p.cell_h, gx, p.k_per_cell, p.thresholds[p.n_thresholds - 1],
-                       p.detect_border, 1, 1, 1};
+                       p.detect_border, 1, 1, 1, p.select_mode};
   det::detect_setup(a.cg, threads, det_warps);
   a.blocks_per_unit = (a.m > 0 ? det_step * a.ntx * a.nty : 0) +
                       (a.n_cells > 0 ? det::detect_blocks(gx, gy, a.cg.bcx, a.cg.bcy) : 0);
@@ -829,7 +829,7 @@ int frame_front_smem(const Geom& g, const vio_params& p, int tile_shift, int pyr
 #define VIO_FRONT_FIRST 2
 #endif
 #ifndef VIO_FRONT_SHIFT
-#define VIO_FRONT_SHIFT 0
+#define VIO_FRONT_SHIFT 1
 #endif
 #ifndef VIO_FRONT_THREADS
 #define VIO_FRONT_THREADS 128
@@ -920,15 +920,13 @@ cudaError_t launch_frames(const FrameLaunch* fl, int n_groups, const FrameTune& 
       mn.block_end[i] = acc;
     }
     if (acc > KN_MAX_LISTS) return cudaErrorInvalidValue;
-    static int sms = 0;
-    if (!sms) {
-      int dev = 0;
-      if (cudaGetDevice(&dev) != cudaSuccess ||
-          cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-          cudaFuncSetAttribute(frame_initnet_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               net::TILE_SMEM) != cudaSuccess)
-        return cudaErrorUnknown;
-    }
+    static PerDeviceOnce kn_attr;
+    e = once_per_device(kn_attr, [] {
+      return cudaFuncSetAttribute(frame_initnet_kernel,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, net::TILE_SMEM);
+    });
+    if (e != cudaSuccess) return e;
+    const int sms = sm_count();
     const long long blocks = tiles < sms ? tiles : sms;
     if (blocks > 0)
       frame_initnet_kernel<<<(unsigned)blocks, net::TILE_THREADS, net::TILE_SMEM, s>>>(mn);
@@ -1000,7 +998,7 @@ int frame_launches(const Geom* g, int n_groups, bool with_net, bool stereo_after
   int n = (with_net ? 4 : 3) + (stereo_after ? 2 : 0);   // K1, (KN), K2, K3, (K4, K5)
   for (int i = 0; i < n_groups; ++i) {
     const int rest = g[i].n_levels - 1 - first_levels(g[i], pyr_first);
-    if (rest > 0) n += (rest + pyr::kMaxPass - 1) / pyr::kMaxPass;
+    if (rest > 0) n += pyr::rest_passes(rest);
   }
   return n;
 }

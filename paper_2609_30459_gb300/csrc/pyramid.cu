@@ -1,8 +1,8 @@
 // Image pyramid entry point (Sec. III-C, Eq. 1-3). Levels are produced by
-// passes of up to four levels each (device code in pyramid_dev.cuh): the
-// first pass reads level 0 and writes levels 1-4, a second (for more than 5
-// levels) reads level 4 and writes the rest; each pass is one launch over all
-// tiles of all images.
+// passes of up to two levels each (device code in pyramid_dev.cuh): the
+// first pass reads level 0 and writes levels 1-2, the next reads level 2 and
+// writes levels 3-4, and so on; each pass is one launch over all tiles of all
+// images.
 #include "pyramid_dev.cuh"
 
 namespace vio {
@@ -23,9 +23,9 @@ __global__ void __launch_bounds__(pyr::kThreads) pyr_pass_kernel(Geom g, Batch b
 
 cudaError_t launch_pyramid_from(const Geom& g, const Batch& b, int s0, int round_mode,
                                 cudaStream_t st) {
-  for (int s = s0; s + 1 < g.n_levels; s += pyr::kMaxPass) {
-    const int m = pyr::pass_levels(g.n_levels, s);
-    const int T = pyr::top_tile(m);
+  for (int s = s0; s + 1 < g.n_levels; s += pyr::kRestPass) {
+    const int m = pyr::rest_pass_levels(g.n_levels, s);
+    const int T = pyr::top_tile(m, pyr::kRestShift);
     int ntx, nty;
     pyr::pass_tiles(g.w, g.h, s, m, T, ntx, nty);
     const int smem = pyr::pass_smem_max(g.w, g.h, s, m, T);

@@ -30,7 +30,8 @@ class Params(ctypes.Structure):
                 ("cell_w", ctypes.c_int32), ("cell_h", ctypes.c_int32),
                 ("k_per_cell", ctypes.c_int32), ("n_thresholds", ctypes.c_int32),
                 ("thresholds", ctypes.c_int32 * MAX_THRESHOLDS),
-                ("detect_border", ctypes.c_int32), ("fb_max_dist", ctypes.c_float)]
+                ("detect_border", ctypes.c_int32), ("fb_max_dist", ctypes.c_float),
+                ("select_mode", ctypes.c_int32)]
 
 
 class PyrLayout(ctypes.Structure):
@@ -62,6 +63,11 @@ class BatchTune(ctypes.Structure):
                 ("stereo_after_select", ctypes.c_int32), ("pyr_first_levels", ctypes.c_int32),
                 ("k1_threads", ctypes.c_int32),
                 ("det_warps", ctypes.c_int32)]
+
+
+class Pinhole(ctypes.Structure):
+    _fields_ = [("fx", ctypes.c_float), ("fy", ctypes.c_float), ("cx", ctypes.c_float),
+                ("cy", ctypes.c_float)]
 
 
 class InitNetCfg(ctypes.Structure):
@@ -122,6 +128,10 @@ _SIGS = {
                                           ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                           ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
                                           ctypes.c_void_p, ctypes.c_void_p]),
+    "vio_predict_warp": (ctypes.c_int32, [ctypes.POINTER(Pinhole), ctypes.POINTER(Pinhole),
+                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                          ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
+                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "vio_fb_check": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                       ctypes.c_int32, ctypes.c_int32, ctypes.c_float,
                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
@@ -433,6 +443,19 @@ def detect_grid_noalloc(params: Params, pyr: "Pyramids", batch: PyrBatch, kp, sc
                                           mask_stride, _ptr(kp), _ptr(score), _ptr(count),
                                           capacity, _stream(stream)),
            "vio_detect_grid_noalloc")
+
+
+def predict_warp(k_src, k_dst, poses, pts, inv_depth, count, capacity, n_images, init,
+                 valid=None, stream=None):
+    """vio_predict_warp: the model-based start of each keypoint's warp.
+    k_src, k_dst: (fx, fy, cx, cy); poses: float32 CUDA tensor (n_images, 12),
+    each row R (row-major, 9) then t (3), mapping source-camera points into the
+    target camera; pts (n_images, capacity, 2), inv_depth (n_images, capacity),
+    init (n_images, capacity, 3) float32, valid (n_images, capacity) uint8."""
+    ks, kd = Pinhole(*[float(v) for v in k_src]), Pinhole(*[float(v) for v in k_dst])
+    _check(load().vio_predict_warp(ctypes.byref(ks), ctypes.byref(kd), _ptr(poses), _ptr(pts),
+                                   _ptr(inv_depth), _ptr(count), capacity, n_images, _ptr(init),
+                                   _ptr(valid), _stream(stream)), "vio_predict_warp")
 
 
 def fb_check(orig, back, count, capacity, n_images, max_dist, status, dist=None, stream=None):

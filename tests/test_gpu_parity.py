@@ -153,6 +153,50 @@ def test_detect_many_large_cells_bitexact(masked):
         assert np.array_equal(sc[i, :c].cpu().numpy(), rs)
 
 
+# The paper's three per-cell selections (Sec. III-D: k rounds of a maximum,
+# a bitonic k-sort, an atomic maximum for one keypoint per cell) pick the same
+# keys (unique under the (score, y, x) order), so each must match the oracle
+# bit for bit, through the standalone detection and the fused pyramid launch.
+@pytest.mark.parametrize("k,mode", [(1, 0), (1, 1), (1, 2), (2, 0), (2, 1), (8, 0), (8, 1)])
+@pytest.mark.parametrize("fused", [False, True])
+def test_detect_selection_modes_bitexact(k, mode, fused):
+    n, w, h, cw, ch = 4, 640, 400, 40, 32
+    imgs = np.stack([textured(300 + i, h, w, sigma=1.5) for i in range(n)])
+    gx, gy = w // cw, h // ch
+    occ = np.random.default_rng(k + 10 * mode).integers(0, k + 1, (n, gx * gy)).astype(np.uint8)
+    occ[0] = 0
+    p = vio.default_params(n_levels=3, cell_w=cw, cell_h=ch, k_per_cell=k, select_mode=mode)
+    ctx = vio.Context(p, w, h, n)
+    pyr = vio.Pyramids(to_dev(imgs), 3)
+    cap = gx * gy * k
+    kp = torch.full((n, cap, 2), -1.0, device=DEV)
+    sc = torch.zeros((n, cap), dtype=torch.int16, device=DEV)
+    cnt = torch.zeros(n, dtype=torch.int32, device=DEV)
+    d_occ = torch.from_numpy(occ).to(DEV)
+    if fused:
+        ctx.pyramid_detect(pyr, kp, sc, cnt, cap, occupancy=d_occ)
+    else:
+        ctx.detect_grid(pyr, pyr.batch(), kp, sc, cnt, cap, occupancy=d_occ)
+    torch.cuda.synchronize()
+    for i in range(n):
+        rk, rs = oracle.detect_grid(imgs[i], cw, ch, k=k, border=p.detect_border,
+                                    occupancy=occ[i])
+        c = int(cnt[i])
+        assert c == len(rk), (i, c, len(rk))
+        assert np.array_equal(kp[i, :c].cpu().numpy(), rk)
+        assert np.array_equal(sc[i, :c].cpu().numpy(), rs)
+    ctx.close()
+
+
+def test_detect_atomic_selection_needs_k1():
+    p = vio.default_params(n_levels=1, cell_w=40, cell_h=40, k_per_cell=2, select_mode=2)
+    with pytest.raises(vio.VioError):
+        vio.Context(p, 160, 120, 1)
+    p = vio.default_params(n_levels=1, cell_w=40, cell_h=40, k_per_cell=1, select_mode=3)
+    with pytest.raises(vio.VioError):
+        vio.Context(p, 160, 120, 1)
+
+
 def test_detect_capacity_truncates_in_raster_order():
     w, h = 400, 300
     img = textured(5, h, w)
