@@ -46,9 +46,14 @@ CONFIG = {"workload": WORKLOAD, "frames": N_FRAMES, "w": W, "h": H, "levels": LE
 # algorithmic FP32 operations of one keypoint through one direction at one
 # level of the KLT: template 52 x ~72 + 5 Gauss-Newton steps of 52 x ~26
 FLOPS_PER_KP_DIR_LEVEL = 52 * 72 + 5 * 52 * 26
-# DRAM bytes (read + write) of one frame_track_kernel launch of this workload,
-# from the ncu capture summarised in profiles/frame_kernels_752x480.md
-TRACK_TRAFFIC_BYTES = 1928448
+# ncu counters of frame_track_kernel on this workload (the profile summary in
+# profiles/ names the command)
+TRACK_NCU = {"profile": "profiles/frame_kernels_752x480.md"}
+# DRAM bytes (read + write) per image of the pyramid+detection pass
+# (vio_pyramid_detect: frame_front_kernel, pyr_pass_kernel and select_kernel),
+# from an ncu capture of 512 images of the headline sequence (the profile
+# summary in profiles/ names the command); a full launch moves this per image
+PYRDET_TRAFFIC_PER_IMAGE = None
 
 
 def seq_seed(rank: int) -> int:
@@ -314,8 +319,14 @@ def pyramid_detect_roofline(torch, vio, frames_dev, peaks, peak_src, w=None, h=N
     t = statistics.median(times)
     gbs = alg / t / 1e9
     ctx.close()
+    traffic = None
+    if PYRDET_TRAFFIC_PER_IMAGE and (w, h, levels, cw, ch) == (W, H, LEVELS, CELL_W, CELL_H):
+        traffic = PYRDET_TRAFFIC_PER_IMAGE * n
     return {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-            "frac": gbs / peaks["hbm_gbs"], "traffic": None, "kernel": "frame_front_kernel",
+            "frac": gbs / peaks["hbm_gbs"], "traffic": traffic,
+            "traffic_note": "DRAM read + write bytes per launch: an ncu capture of 512 images "
+                            "scaled by the images of this launch",
+            "kernel": "vio_pyramid_detect (frame_front_kernel, pyr_pass_kernel, select_kernel)",
             "images": n, "image": f"{w}x{h}, {levels} levels, {gx}x{gy} cells",
             "batch_bytes_in": n * w * h, "algorithmic_bytes": alg,
             "algorithmic_bytes_per_image": w * h + upper + n_kp * 10 / n,
@@ -696,6 +707,9 @@ def serving_run(torch, vio, seconds, net, tune, seqs=None):
     # warm-up: one frame per session (graph capture, first-frame detection)
     warm = [(sessions[i], 0.0, pools[i][0], -1, 0) for i in range(len(sessions))]
     srv.run_trace(warm, timeout_s=60.0)
+    # the trace loop keeps its CPU: pinned to the core it starts on, at a
+    # real-time priority where the system permits it
+    srv.set_loop_policy(pin_cpu=-2, rt_priority=10)
     import gc
     gc.collect()
     gc.disable()                 # no collector pauses in the host process meanwhile
@@ -707,6 +721,7 @@ def serving_run(torch, vio, seconds, net, tune, seqs=None):
         gc.enable()
     wall = time.perf_counter() - t0
     gap, n_gaps = srv.loop_stats()
+    pinned_ok, rt_ok = srv.loop_policy_granted()
     summ = serving.latency_summary(done)
     srv.close_server()
     return {"sessions": len(sessions), "classes": [f"{w}x{h}" for (w, h, _, _) in CFG4_CLASSES],
@@ -716,6 +731,7 @@ def serving_run(torch, vio, seconds, net, tune, seqs=None):
             "budget_bytes": budget, "device_bytes": used, "slots": slots,
             "learned": net is not None,
             "host_loop": {"max_gap_ms": 1e3 * gap, "passes_over_1ms": n_gaps,
+                          "pinned_cpu": pinned_ok, "realtime_priority": rt_ok,
                           "note": "the server's host loop polls continuously; a gap is time "
                                   "the process was not running (shared host CPUs)"},
             **summ}
@@ -982,25 +998,18 @@ def main():
         t_max = max_over_ranks(total_s, dist, "cuda")
     value = world * args.steps / t_max
 
-    # dominant kernel: the stage with the largest share of the step
+    # tracking: latency/issue bound (one dependent Gauss-Newton chain per
+    # keypoint and direction), so it is reported as keypoints per second and
+    # its launch time, with the issue and stall counters of its ncu profile
     per_stage = {k: v / max(n_timed, 1) for k, v in stage_ms.items()}
-    dom = max(per_stage, key=per_stage.get)
-    sm_max = peaks.get("sm_max_mhz", 2070.0)
-    fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12               # TFLOP/s
-    roofline = None
-    if dom == "track":     # temporal tracks and stereo candidates, both with FB
-        # per launch: the timed steps' FLOPs per step over the track stage's
-        # average duration (events pass)
-        flops = (tracked + stereo_in) * 2 * LEVELS * FLOPS_PER_KP_DIR_LEVEL / args.steps
-        t_launch = stage_ms["track"] / 1000.0 / max(n_timed, 1)
-        ach = flops / t_launch / 1e12
-        roofline = {"bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s",
-                    "frac": ach / fp32_peak, "traffic": TRACK_TRAFFIC_BYTES,
-                    "traffic_note": "DRAM bytes per launch from one ncu capture (cold caches "
-                                    "between ncu passes)", "kernel": "frame_track_kernel",
-                    "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x max SM clock "
-                                   f"{sm_max:.0f} MHz ({peak_src} clock)",
-                    "avg_launch_us": 1e6 * t_launch}
+    t_track = stage_ms["track"] / 1000.0 / max(n_timed, 1)
+    tracking = {"kernel": "frame_track_kernel",
+                "keypoints_per_launch": (tracked + stereo_in) / args.steps,
+                "keypoint_tracks_per_s": (tracked + stereo_in) / args.steps / t_track,
+                "avg_launch_us": 1e6 * t_track,
+                "bound": "latency (dependent chains: 8 templates and 40 Gauss-Newton steps per "
+                         "keypoint and direction)",
+                "ncu": TRACK_NCU}
 
     # end to end through the C ABI from pinned host memory: every step uploads
     # its stereo pair and reads back the keypoint lists and new detections
@@ -1073,6 +1082,7 @@ def main():
                                   "p99_ms": 1000 * percentile(lat, 99)}}
 
     pd = pyramid_detect_roofline(torch, vio, frames, peaks, peak_src) if rank == 0 else None
+    roofline = pd
 
     # config 3 (4 cameras = two stereo pairs at 1920x1080, motion up to 40 px)
     # and the paper's lite parameters on 752x480 sequences like the headline's
@@ -1152,7 +1162,7 @@ def main():
                                    "new": new_kp / args.steps,
                                    "stereo_candidates": stereo_in / args.steps},
             "gpu_launches": args.steps * fe.launches_per_step(),
-            "e2e": e2e, "roofline": roofline, "pyramid_detect_roofline": pd,
+            "e2e": e2e, "roofline": roofline, "tracking": tracking,
             "frontend_tune": fe_tune,
             "batched_16_streams": batched, "serving_32_streams": serve,
             "other_configs": extra_cfgs,

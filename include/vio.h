@@ -40,7 +40,8 @@ enum {
   VIO_ERR_INVALID_ARG = 1, /* a pointer, size or parameter is invalid      */
   VIO_ERR_CUDA = 2,        /* the CUDA runtime reported an error           */
   VIO_ERR_OOM = 3,         /* device allocation failed in *_create          */
-  VIO_ERR_TIMEOUT = 4,     /* reserved: a bounded device-side wait expired */
+  VIO_ERR_TIMEOUT = 4,     /* a bounded wait expired (device status word, or
+                              the serving loop's host timeout)              */
   VIO_ERR_UNSUPPORTED = 5  /* valid but outside what this build handles    */
 };
 
@@ -135,6 +136,28 @@ vio_status vio_ctx_create(vio_ctx** ctx, const vio_params* p, int32_t max_w, int
 vio_status vio_ctx_destroy(vio_ctx* ctx);
 const char* vio_status_string(vio_status s);
 
+/* Device-side errors. Arguments are checked on the host before anything is
+ * enqueued; what can only go wrong on the device (a bounded wait that gave
+ * up) is recorded in the context's device status word: VIO_OK, or the first
+ * such error since the word was last cleared.
+ *   vio_ctx_sync:   enqueues a read and a clear of the word on `stream`, waits
+ *                   for the stream, and stores the word in *device_status;
+ *                   returns VIO_ERR_CUDA if the stream reported an error.
+ *   vio_last_error: reads the word (a blocking copy) without clearing it and
+ *                   returns it (VIO_ERR_CUDA if the read failed). */
+vio_status vio_ctx_sync(vio_ctx* ctx, void* stream, vio_status* device_status);
+vio_status vio_last_error(vio_ctx* ctx);
+
+/* A bounded wait on the device: enqueues on `stream` a wait until the int32
+ * at d_flag (device memory, or host memory mapped into the device, written by
+ * another stream or by the host) equals `value`. Work after it on the stream
+ * starts once the flag is set, or once timeout_ns (0 .. 2 s) has passed: the
+ * wait then records VIO_ERR_TIMEOUT in the context's status word and ends, so
+ * the context and the stream stay usable. The paper has no counterpart (its
+ * host waits on a fence, Sec. III-B). */
+vio_status vio_wait_flag(vio_ctx* ctx, const int32_t* d_flag, int32_t value, int64_t timeout_ns,
+                         void* stream);
+
 /* --------------------------------------------------------------- stages -- */
 
 /* Sec. III-C, Eq. 1-3: builds levels 1..n-1 of every pyramid of the batch
@@ -173,12 +196,11 @@ vio_status vio_detect_grid(vio_ctx* ctx, const vio_pyr_layout* layout,
                            const uint8_t* d_mask, int64_t mask_stride, float* d_kp,
                            int16_t* d_score, int32_t* d_count, int32_t capacity, void* stream);
 
-/* Sec. III-C and III-D fused: vio_pyramid_build and vio_detect_grid of the
- * same batch in one pass over level 0 (one launch computes pyramid levels
- * 1-4 and every cell's candidates; images with more than 5 levels take one
- * more launch for the rest; one launch applies the occupancy and writes the
- * keypoints). Arguments and results as the two calls. The pyramid needs
- * n_levels == the context's n_levels. */
+/* Sec. III-C and III-D together: vio_pyramid_build and vio_detect_grid of the
+ * same batch, for throughput over many images: per chunk of images whose
+ * level 0 fits in half the L2, the pyramid launches and then the detection
+ * launches, so level 0 comes from DRAM once. Arguments and results as the two
+ * calls. The pyramid needs n_levels == the context's n_levels. */
 vio_status vio_pyramid_detect(vio_ctx* ctx, const vio_pyr_layout* layout,
                               const vio_pyr_batch* batch, const uint8_t* d_occupancy,
                               const uint8_t* d_mask, int64_t mask_stride, float* d_kp,
@@ -232,6 +254,10 @@ enum { VIO_TRACK_FORWARD = 0, VIO_TRACK_WITH_FB = 1 };
  *             VIO_TRACK_EMPTY.
  *   d_fb_dist: per keypoint float forward-backward distance (NaN if not
  *             computed), or NULL.
+ *   d_last_step: per keypoint float, how far the forward pass's last
+ *             Gauss-Newton step at level 0 moved the pattern (|dx| + |dy| +
+ *             7.62 |dtheta|, level-0 px: a convergence measure; NaN where the
+ *             forward pass failed), or NULL.
  * flags = VIO_TRACK_WITH_FB also runs the backward pass (template rebuilt on
  * the target at the forward result, warp started at the forward estimate's
  * inverse) and marks VIO_TRACK_FB_FAIL when the returned position is more
@@ -240,7 +266,7 @@ vio_status vio_track_patches(vio_ctx* ctx, const vio_pyr_layout* layout,
                              const vio_pyr_batch* src, const vio_pyr_batch* dst,
                              const float* d_pts, const float* d_init, const int32_t* d_count,
                              int32_t capacity, int32_t flags, float* d_out, uint8_t* d_status,
-                             float* d_fb_dist, void* stream);
+                             float* d_fb_dist, float* d_last_step, void* stream);
 
 /* Sec. III-E cross-camera matching: vio_track_patches with VIO_TRACK_WITH_FB
  * from cam0 pyramids (src) to cam1 pyramids (dst) at the same time step.
@@ -250,6 +276,25 @@ vio_status vio_stereo_match(vio_ctx* ctx, const vio_pyr_layout* layout,
                             const float* d_pts, const float* d_init, const int32_t* d_count,
                             int32_t capacity, float* d_match, uint8_t* d_status,
                             float* d_fb_dist, void* stream);
+
+/* Sec. III-E cross-camera matching for rigs of more than two cameras (the
+ * paper's four-camera runs, Sec. IV-A): the keypoints of one source image
+ * (src: a batch of one pyramid, e.g. camera 0 of a rig) are tracked with the
+ * forward-backward check into each of the dst->n_images target pyramids of
+ * the same time step (the rig's other cameras).
+ *   d_pts, d_count: the source keypoints (capacity float2) and their count
+ *                   (one int32, or NULL for `capacity`);
+ *   d_init:   per target and keypoint float3 start (target-major:
+ *             n_targets x capacity), e.g. from vio_predict_warp with each
+ *             target's extrinsics, or NULL for the identity start;
+ *   d_match:  per target and keypoint float2 position in that target,
+ *             d_status and d_fb_dist (may be NULL) likewise; slots >= count
+ *             get VIO_TRACK_EMPTY. */
+vio_status vio_match_cameras(vio_ctx* ctx, const vio_pyr_layout* layout,
+                             const vio_pyr_batch* src, const vio_pyr_batch* dst,
+                             const float* d_pts, const float* d_init, const int32_t* d_count,
+                             int32_t capacity, float* d_match, uint8_t* d_status,
+                             float* d_fb_dist, void* stream);
 
 /* Sec. III-E forward-backward check, for callers that run the backward pass
  * themselves: d_back[i] is the backward result (float3) of keypoint d_orig[i]
@@ -261,10 +306,11 @@ vio_status vio_fb_check(const float* d_orig, const float* d_back, const int32_t*
                         int32_t capacity, int32_t n_images, float max_dist, uint8_t* d_status,
                         float* d_dist, void* stream);
 
-/* Sec. III-E, the start of a track: "the warp is initialized by projecting
- * the pattern into the target image through the camera model, using the
- * predicted pose and inverse depth". Pinhole cameras; the pose maps points of
- * the source camera into the target camera, P' = R P + t (R row-major).
+/* Sec. III-E, the start of a track: the warp begins where the sample pattern
+ * lands in the target image when it is carried there by the camera model, the
+ * predicted pose and the keypoint's inverse depth. Pinhole cameras; the
+ * pose maps points of the source camera into the target camera,
+ * P' = R P + t (R row-major).
  * For keypoint u with inverse depth rho: P = (1 / rho) K_src^-1 [u, 1], and
  * u' = the projection of R P + t through K_dst. Each of the 52 pattern points
  * u + x_i is projected the same way at the keypoint's inverse depth (a
@@ -436,9 +482,13 @@ vio_status vio_frontend_read_stats(vio_frontend* fe, int32_t* host_out, int64_t*
  * previous and current frame of the same camera, before tracking. A keypoint
  * whose proposal has confidence >= min_conf is tracked, with the
  * forward-backward check, over levels start_level..0 only, from p + flow; if
- * that track does not end VIO_TRACK_OK, or the confidence is lower, the
- * keypoint is tracked exactly as without the network (whole pyramid, start
- * at p). Stereo matching is unchanged. d_packed: the packed weights
+ * that track does not end VIO_TRACK_OK, or has not converged (max_last_step
+ * > 0 and its last level-0 Gauss-Newton step moved the pattern by more than
+ * max_last_step px: |dx| + |dy| + 7.62 |dtheta|), or the confidence is
+ * lower, the keypoint is tracked exactly as without the network (whole
+ * pyramid, start at p). A converged track sits at the optimum its start
+ * leads to, so where the plain track converges too the two agree. Stereo
+ * matching is unchanged. d_packed: the packed weights
  * (vio_initnet_pack, 16-byte aligned), read by every step and owned by the
  * caller, which keeps them alive while the initializer is on; NULL turns it
  * off. level_a and level_b must lie in 1 .. n_levels - 1 (upper levels),
@@ -448,6 +498,7 @@ typedef struct {
   int32_t level_a, level_b;  /* pyramid levels of the network input          */
   int32_t start_level;       /* LK levels tracked from the proposal          */
   float min_conf;            /* confidence gate                              */
+  float max_last_step;       /* convergence gate (px), <= 0: none            */
 } vio_initnet_cfg;
 
 vio_status vio_frontend_set_initnet(vio_frontend* fe, const void* d_packed,
@@ -620,6 +671,17 @@ vio_status vio_server_run_trace(vio_server* s, const vio_server_req* reqs, int64
  * passes of its loop (a loop that was not scheduled on a CPU delays every
  * request it holds) and the number of passes that took longer than 1 ms. */
 vio_status vio_server_loop_stats(const vio_server* s, double* max_gap_s, int64_t* n_over_1ms);
+/* Scheduling of vio_server_run_trace's host loop, for a loop that must not
+ * lose its CPU (every request it holds waits while it does): pin_cpu >= 0
+ * pins the calling thread to that CPU for the call, -2 to the CPU it is on
+ * when the call starts, -1 leaves the affinity alone; rt_priority in 1..99
+ * runs the call at that SCHED_FIFO priority, 0 leaves the policy alone. The
+ * previous affinity and policy are restored when the call returns. Where the
+ * system refuses (no permission), the loop runs unchanged:
+ * vio_server_loop_policy_granted reports what the last trace got (bit 0:
+ * pinned, bit 1: real-time). Default: -1, 0. */
+vio_status vio_server_set_loop_policy(vio_server* s, int32_t pin_cpu, int32_t rt_priority);
+vio_status vio_server_loop_policy_granted(const vio_server* s, int32_t* granted);
 
 /* ---------------------------------------------------------------------------
  * Learned flow initializer. Not in the paper: its tracker starts each

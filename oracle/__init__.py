@@ -18,6 +18,9 @@ Functions and the passage each follows:
 * ``track``                      -- Sec. III-E, Eq. 4-5, pyramidal IC-KLT with
                                     the forward-backward check.
 * ``frontend.step``              -- Sec. III-B, the per-frame stage order.
+* ``predict.predict_warp``       -- Sec. III-E, the start of a track from the
+                                    camera model, predicted pose and inverse
+                                    depth.
 
 Parity unpinned (definitions the paper leaves open, pinned only by the GPU
 matching this oracle): the pattern offsets, the bounds and degeneracy rules,
@@ -109,7 +112,7 @@ def _load():
             lib.vo_pattern.restype = i32
             lib.vo_track.argtypes = [ctypes.POINTER(_Pyramid), ctypes.POINTER(_Pyramid), i32,
                                      P, P, ctypes.POINTER(_TrackParams), i32, P, P, P, P, P,
-                                     i32]
+                                     P, i32]
             lib.vo_template.argtypes = [ctypes.POINTER(_Image), ctypes.c_double,
                                         ctypes.c_double, i32, P, P, P, P, P, P, P]
             lib.vo_template.restype = i32
@@ -220,7 +223,8 @@ def track(src_levels, dst_levels, pts, init=None, gn_iters=GN_ITERS, pattern_id=
 
     Returns a dict with ``warp`` (n,3) float64 forward result (tx, ty, theta)
     in level-0 px, ``status`` (n,) uint8, ``fb_dist`` (n,) float64, ``margin``
-    (n,) float64 and ``back`` (n,3) float64."""
+    (n,) float64, ``back`` (n,3) float64 and ``last_step`` (n,) float64 (the
+    forward pass's last level-0 step, |dx| + |dy| + r |dtheta|)."""
     lib = _load()
     pts = np.ascontiguousarray(pts, np.float32).reshape(-1, 2)
     n = pts.shape[0]
@@ -234,11 +238,13 @@ def track(src_levels, dst_levels, pts, init=None, gn_iters=GN_ITERS, pattern_id=
     fbd = np.zeros(n)
     margin = np.zeros(n)
     back = np.zeros((n, 3))
+    last = np.zeros(n)
     lib.vo_track(ctypes.byref(sp), ctypes.byref(dp), n, _ptr(pts), _ptr(ini), ctypes.byref(prm),
                  1 if fb else 0, _ptr(warp), _ptr(status), _ptr(fbd), _ptr(margin), _ptr(back),
-                 n_threads)
+                 _ptr(last), n_threads)
     del k1, k2
-    return {"warp": warp, "status": status, "fb_dist": fbd, "margin": margin, "back": back}
+    return {"warp": warp, "status": status, "fb_dist": fbd, "margin": margin, "back": back,
+            "last_step": last}
 
 
 def template(img, qx, qy, pattern_id=0):

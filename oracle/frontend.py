@@ -11,7 +11,9 @@ camera (float32 positions and int ids) and the next id.
   network's proposal (flow, confidence) for every keypoint; where the
   confidence reaches the gate, the track over levels start_level..0 from
   p + flow; every keypoint without a proposal above the gate, or whose
-  proposed track does not end OK, is tracked as above.
+  proposed track does not end OK, or has not converged (its last level-0
+  Gauss-Newton step moved the pattern by more than max_last_step px, when
+  that is > 0), is tracked as above.
 * Detection on camera 0 (level 0), with each cell's count of surviving
   camera-0 tracks counted against k (the mask and cell buffers of Sec. III-B).
 * Matching: the new keypoints from camera 0 to camera 1 of the same frame,
@@ -50,6 +52,7 @@ class NetCfg:
     level_b: int = 3
     start_level: int = 1
     min_conf: float = 0.5
+    max_last_step: float = 1e-3      # convergence gate (px), <= 0: none
 
 
 @dataclass
@@ -100,7 +103,8 @@ def temporal(prev, cur, xy, p: Params, net: NetCfg | None = None, n_threads: int
     n = len(xy)
     flow, conf = proposals(net, prev, cur, xy)
     out = {"status": np.zeros(n, np.uint8), "warp": np.zeros((n, 3)), "fb_dist": np.zeros(n),
-           "margin": np.zeros(n), "flow": flow, "conf": conf, "learned": np.zeros(n, bool)}
+           "margin": np.zeros(n), "last_step": np.zeros(n), "flow": flow, "conf": conf,
+           "learned": np.zeros(n, bool)}
     gate = np.where(conf >= net.min_conf)[0]
     top = net.start_level + 1
     res_l = None
@@ -108,14 +112,17 @@ def temporal(prev, cur, xy, p: Params, net: NetCfg | None = None, n_threads: int
         init = np.zeros((len(gate), 3), np.float32)
         init[:, :2] = (xy[gate] + flow[gate]).astype(np.float32)
         res_l = track(prev[:top], cur[:top], xy[gate], init=init, **kw)
-        ok = gate[res_l["status"] == 0]
+        keep = res_l["status"] == 0
+        if net.max_last_step > 0:
+            keep &= res_l["last_step"] <= net.max_last_step
+        ok = gate[keep]
         out["learned"][ok] = True
-        for k in ("status", "warp", "fb_dist", "margin"):
-            out[k][ok] = res_l[k][res_l["status"] == 0]
+        for k in ("status", "warp", "fb_dist", "margin", "last_step"):
+            out[k][ok] = res_l[k][keep]
     rest = np.where(~out["learned"])[0]
     res_p = track(prev, cur, xy[rest], **kw) if len(rest) else None
     if res_p is not None:
-        for k in ("status", "warp", "fb_dist", "margin"):
+        for k in ("status", "warp", "fb_dist", "margin", "last_step"):
             out[k][rest] = res_p[k]
     out["learned_track"] = (gate, res_l)
     out["plain_track"] = (rest, res_p)

@@ -175,8 +175,12 @@ struct Warp {
 };
 
 /* One Gauss-Newton step (Eq. 4-5) at one level. The warp maps pattern offset
- * x_i to R(theta) x_i + t in the target image. */
-int gn_step(const vo_image& tgt, const Template& T, double scale, Warp& W, double* margin) {
+ * x_i to R(theta) x_i + t in the target image. *moved receives
+ * |dx| + |dy| + r |dtheta| of the increment, r the pattern's largest radius:
+ * a bound on how far the step moved any pattern point (level px), the
+ * convergence measure of the learned start's gate. */
+int gn_step(const vo_image& tgt, const Template& T, double scale, Warp& W, double* margin,
+            double* moved) {
   const double c = std::cos(W.th), s = std::sin(W.th);
   double r[kMaxPts];
   double sum = 0;
@@ -202,6 +206,9 @@ int gn_step(const vo_image& tgt, const Template& T, double scale, Warp& W, doubl
     d[a] = -acc;
   }
   if (!std::isfinite(d[0]) || !std::isfinite(d[1]) || !std::isfinite(d[2])) return VO_NAN;
+  double rmax = 0;
+  for (int i = 0; i < T.np; ++i) rmax = std::max(rmax, std::hypot(T.u[i], T.v[i]));
+  *moved = std::fabs(d[0]) + std::fabs(d[1]) + rmax * std::fabs(d[2]);
   double Rd[2][2], td[2];
   se2_exp(d[0], d[1], d[2], Rd, td);
   /* (R, t) o (Rd, td) = (R Rd, R td + t); R Rd is the rotation by th + dth */
@@ -218,8 +225,9 @@ int gn_step(const vo_image& tgt, const Template& T, double scale, Warp& W, doubl
  * handled). Any warp failure ends the track at once. */
 int track_one(const vo_pyramid& src, const vo_pyramid& dst, int n_levels, double px,
               double py, const Warp& init, const vo_track_params& prm, Warp& out,
-              double* margin) {
+              double* margin, double* last_step) {
   Warp W = init;
+  *last_step = 0;
   const double top = std::ldexp(1.0, n_levels - 1);
   W.tx /= top;
   W.ty /= top;
@@ -231,10 +239,12 @@ int track_one(const vo_pyramid& src, const vo_pyramid& dst, int n_levels, double
     if (ts != VO_OK) {
       if (l == 0) return ts;
     } else {
+      double moved = 0;
       for (int it = 0; it < prm.gn_iters; ++it) {
-        const int st = gn_step(dst.lv[l], T, scale, W, margin);
+        const int st = gn_step(dst.lv[l], T, scale, W, margin, &moved);
         if (st != VO_OK) return st;
       }
+      if (l == 0) *last_step = moved;
     }
     if (l > 0) {
       W.tx *= 2;
@@ -247,7 +257,8 @@ int track_one(const vo_pyramid& src, const vo_pyramid& dst, int n_levels, double
 
 void track_range(const vo_pyramid* src, const vo_pyramid* dst, int i0, int i1, const float* pts,
                  const float* init, const vo_track_params* p, int fb, double* warp,
-                 uint8_t* status, double* fb_dist, double* margin, double* back) {
+                 uint8_t* status, double* fb_dist, double* margin, double* back,
+                 double* last_step) {
   const int L = std::min(src->n_levels, dst->n_levels);
   const double nan = std::numeric_limits<double>::quiet_NaN();
   for (int i = i0; i < i1; ++i) {
@@ -256,7 +267,9 @@ void track_range(const vo_pyramid* src, const vo_pyramid* dst, int i0, int i1, c
     if (init) w0 = Warp{init[3 * i], init[3 * i + 1], init[3 * i + 2]};
     double m = std::numeric_limits<double>::infinity();
     Warp wf{nan, nan, nan}, wb{nan, nan, nan};
-    int st = track_one(*src, *dst, L, px, py, w0, *p, wf, &m);
+    double last = nan, last_b = nan;
+    int st = track_one(*src, *dst, L, px, py, w0, *p, wf, &m, &last);
+    if (st != VO_OK) last = nan;
     double dist = nan;
     if (st == VO_OK && fb) {
       /* Backward pass (Sec. III-E): the template is rebuilt on the target
@@ -264,7 +277,7 @@ void track_range(const vo_pyramid* src, const vo_pyramid* dst, int i0, int i1, c
        * forward estimate's inverse, which in this parametrisation is the
        * original position p with angle -theta_f. */
       const Warp wbi{px, py, -wf.th};
-      st = track_one(*dst, *src, L, wf.tx, wf.ty, wbi, *p, wb, &m);
+      st = track_one(*dst, *src, L, wf.tx, wf.ty, wbi, *p, wb, &m, &last_b);
       if (st == VO_OK) {
         dist = std::hypot(wb.tx - px, wb.ty - py);
         if (dist > p->fb_max_dist) st = VO_FB_FAIL;
@@ -276,6 +289,7 @@ void track_range(const vo_pyramid* src, const vo_pyramid* dst, int i0, int i1, c
     warp[3 * i + 2] = wf.th;
     if (fb_dist) fb_dist[i] = dist;
     if (margin) margin[i] = m;
+    if (last_step) last_step[i] = last;
     if (back) {
       back[3 * i] = wb.tx;
       back[3 * i + 1] = wb.ty;
@@ -330,9 +344,10 @@ extern "C" int32_t vo_template(const vo_image* img, double qx, double qy, int32_
 extern "C" void vo_track(const vo_pyramid* src, const vo_pyramid* dst, int32_t n,
                          const float* pts, const float* init, const vo_track_params* p,
                          int32_t fb, double* warp, uint8_t* status, double* fb_dist,
-                         double* margin, double* back, int32_t n_threads) {
+                         double* margin, double* back, double* last_step, int32_t n_threads) {
   if (n_threads <= 1 || n < 64) {
-    track_range(src, dst, 0, n, pts, init, p, fb, warp, status, fb_dist, margin, back);
+    track_range(src, dst, 0, n, pts, init, p, fb, warp, status, fb_dist, margin, back,
+                last_step);
     return;
   }
   std::vector<std::thread> pool;
@@ -341,7 +356,7 @@ extern "C" void vo_track(const vo_pyramid* src, const vo_pyramid* dst, int32_t n
     const int i0 = t * per, i1 = std::min(n, i0 + per);
     if (i0 >= i1) break;
     pool.emplace_back(track_range, src, dst, i0, i1, pts, init, p, fb, warp, status, fb_dist,
-                      margin, back);
+                      margin, back, last_step);
   }
   for (auto& th : pool) th.join();
 }

@@ -98,11 +98,14 @@ int32_t vo_pattern(int32_t pattern_id, double* u, double* v /* >= 64 each */);
  * Outputs: warp n*(tx,ty,theta) in level-0 px (forward result), status n,
  * fb_dist n (NaN where not computed), margin n (smallest distance, in level-0
  * px, between any bound test's value and its bound; used to explain status
- * disagreements), back n*(tx,ty,theta) (backward result, may be NULL). */
+ * disagreements), back n*(tx,ty,theta) (backward result, may be NULL),
+ * last_step n (how far the forward pass's last level-0 Gauss-Newton step
+ * moved the pattern: |dx| + |dy| + r |dtheta|, r the pattern's radius; NaN if
+ * the forward pass failed; may be NULL). */
 void vo_track(const vo_pyramid* src, const vo_pyramid* dst, int32_t n,
               const float* pts, const float* init, const vo_track_params* p,
               int32_t fb, double* warp, uint8_t* status, double* fb_dist,
-              double* margin, double* back, int32_t n_threads);
+              double* margin, double* back, double* last_step, int32_t n_threads);
 
 /* Template quantities at one level, for the tests (Sec. III-E): samples s,
  * gradients gx, gy, Jacobian rows J (np*3), Hessian H (9) and gain G (3*np),

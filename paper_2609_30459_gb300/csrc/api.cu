@@ -117,12 +117,19 @@ extern "C" vio_status vio_ctx_create(vio_ctx** out, const vio_params* p, int32_t
   c->max_cells = (max_w / p->cell_w) * (max_h / p->cell_h);
   const size_t n = (size_t)c->max_images * (size_t)(c->max_cells > 0 ? c->max_cells : 1);
   if (cudaMalloc(&c->d_cand, n * p->k_per_cell * sizeof(unsigned long long)) != cudaSuccess ||
-      cudaMalloc(&c->d_cand_count, n * sizeof(int32_t)) != cudaSuccess) {
+      cudaMalloc(&c->d_cand_count, n * sizeof(int32_t)) != cudaSuccess ||
+      cudaMalloc(&c->d_status, sizeof(int32_t)) != cudaSuccess ||
+      cudaMallocHost(&c->h_status, sizeof(int32_t)) != cudaSuccess ||
+      cudaMemset(c->d_status, 0, sizeof(int32_t)) != cudaSuccess) {
     cudaGetLastError();
     cudaFree(c->d_cand);
+    cudaFree(c->d_cand_count);
+    cudaFree(c->d_status);
+    cudaFreeHost(c->h_status);
     delete c;
     return VIO_ERR_OOM;
   }
+  *c->h_status = 0;
   *out = c;
   return VIO_OK;
 }
@@ -131,8 +138,65 @@ extern "C" vio_status vio_ctx_destroy(vio_ctx* c) {
   if (!c) return VIO_ERR_INVALID_ARG;
   cudaFree(c->d_cand);
   cudaFree(c->d_cand_count);
+  cudaFree(c->d_status);
+  cudaFreeHost(c->h_status);
   delete c;
   return VIO_OK;
+}
+
+namespace {
+
+// Polls *flag until it equals `value`, for at most timeout_ns of the GPU's
+// global timer, and in any case at most max_polls polls (each a global load, a
+// timer read and a short sleep); on giving up it records VIO_ERR_TIMEOUT in
+// the status word (the first error recorded stays) and returns, so the
+// context stays usable.
+__global__ void wait_flag_kernel(const volatile int32_t* flag, int32_t value, long long timeout_ns,
+                                 long long max_polls, int32_t* status) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  unsigned long long t0, t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+  for (long long i = 0; i < max_polls; ++i) {
+    if (*flag == value) return;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    if ((long long)(t - t0) > timeout_ns) break;
+    __nanosleep(1000);
+  }
+  if (*flag == value) return;
+  atomicCAS(status, (int32_t)VIO_OK, (int32_t)VIO_ERR_TIMEOUT);
+}
+
+}  // namespace
+
+extern "C" vio_status vio_wait_flag(vio_ctx* ctx, const int32_t* d_flag, int32_t value,
+                                    int64_t timeout_ns, void* stream) {
+  if (!ctx || !d_flag || timeout_ns < 0 || timeout_ns > 2000000000LL) return VIO_ERR_INVALID_ARG;
+  // a poll (a global load and a timer read) takes well over 100 ns, so the
+  // timer ends the wait first; the count only bounds it if the timer did not
+  const long long max_polls = timeout_ns / 100 + 1024;
+  wait_flag_kernel<<<1, 32, 0, (cudaStream_t)stream>>>(d_flag, value, timeout_ns, max_polls,
+                                                       ctx->d_status);
+  return cudaGetLastError() == cudaSuccess ? VIO_OK : VIO_ERR_CUDA;
+}
+
+extern "C" vio_status vio_ctx_sync(vio_ctx* ctx, void* stream, vio_status* device_status) {
+  if (!ctx || !device_status) return VIO_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (cudaMemcpyAsync(ctx->h_status, ctx->d_status, sizeof(int32_t), cudaMemcpyDeviceToHost,
+                      s) != cudaSuccess ||
+      cudaMemsetAsync(ctx->d_status, 0, sizeof(int32_t), s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return VIO_ERR_CUDA;
+  *device_status = *ctx->h_status;
+  return VIO_OK;
+}
+
+extern "C" vio_status vio_last_error(vio_ctx* ctx) {
+  if (!ctx) return VIO_ERR_INVALID_ARG;
+  int32_t v = 0;
+  if (cudaMemcpy(&v, ctx->d_status, sizeof(int32_t), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return VIO_ERR_CUDA;
+  return v;
 }
 
 extern "C" vio_status vio_pyramid_build(vio_ctx* ctx, const vio_pyr_layout* layout,
@@ -191,13 +255,29 @@ extern "C" vio_status vio_pyramid_detect(vio_ctx* ctx, const vio_pyr_layout* lay
   const vio::Geom g = vio::make_geom(*layout);
   const vio::Batch b = vio::make_batch(*batch);
   cudaStream_t s = (cudaStream_t)stream;
-  cudaError_t e = vio::launch_front(ctx->p, g, b, 1, d_mask, mask_stride, ctx->d_cand,
-                                    ctx->d_cand_count, s);   // all levels
-  if (e == cudaSuccess) {
-    const int n_cells = (layout->w[0] / ctx->p.cell_w) * (layout->h[0] / ctx->p.cell_h);
-    e = vio::launch_select(ctx->d_cand, ctx->d_cand_count, d_occupancy, n_cells,
-                           ctx->p.k_per_cell, layout->w[0], d_kp, d_score, d_count, capacity,
-                           batch->n_images, s);
+  // Per chunk of images, the pyramid launch and then the detection launch:
+  // each kernel runs at its own shape and occupancy (the single fused launch
+  // of the per-frame step, kept there for its latency, runs both parts at the
+  // larger one's), and a chunk's level 0 (at most 64 MiB, half the L2) is
+  // still in L2 when the detection reads it, so DRAM serves it once.
+  const int n_cells = (layout->w[0] / ctx->p.cell_w) * (layout->h[0] / ctx->p.cell_h);
+  const long long img_bytes = (long long)layout->pitch[0] * layout->h[0];
+  const long long by_l2 = (64LL << 20) / (img_bytes > 0 ? img_bytes : 1);
+  const int chunk = (int)(by_l2 < 1 ? 1 : (by_l2 < b.n ? by_l2 : b.n));
+  cudaError_t e = cudaSuccess;
+  for (int i0 = 0; i0 < b.n && e == cudaSuccess; i0 += chunk) {
+    vio::Batch bc = b;
+    bc.l0 = b.l0 + (long long)i0 * b.l0_stride;
+    bc.upper = b.upper + (long long)i0 * b.upper_stride;
+    bc.n = b.n - i0 < chunk ? b.n - i0 : chunk;
+    e = vio::launch_pyramid(g, bc, ctx->p.round_mode, s);
+    if (e != cudaSuccess) break;
+    e = vio::launch_detect(
+        ctx->p, g, bc, d_occupancy ? d_occupancy + (long long)i0 * n_cells : nullptr,
+        d_mask ? d_mask + (long long)i0 * mask_stride : nullptr, mask_stride,
+        ctx->d_cand + (long long)i0 * n_cells * ctx->p.k_per_cell,
+        ctx->d_cand_count + (long long)i0 * n_cells, d_kp + 2LL * i0 * capacity,
+        d_score + (long long)i0 * capacity, d_count + i0, capacity, s);
   }
   return cuda_status(e);
 }
@@ -207,7 +287,7 @@ extern "C" vio_status vio_track_patches(vio_ctx* ctx, const vio_pyr_layout* layo
                                         const float* d_pts, const float* d_init,
                                         const int32_t* d_count, int32_t capacity, int32_t flags,
                                         float* d_out, uint8_t* d_status, float* d_fb_dist,
-                                        void* stream) {
+                                        float* d_last_step, void* stream) {
   if (!ctx || !layout_ok(layout) || !batch_ok(layout, src) || !batch_ok(layout, dst))
     return VIO_ERR_INVALID_ARG;
   if (src->n_images != dst->n_images || !d_pts || !d_out || !d_status || capacity < 0)
@@ -221,7 +301,7 @@ extern "C" vio_status vio_track_patches(vio_ctx* ctx, const vio_pyr_layout* layo
   return cuda_status(vio::launch_track(vio::make_geom(*layout), vio::make_batch(*src),
                                        vio::make_batch(*dst), d_pts, d_init, d_count, capacity,
                                        cfg, d_out, nullptr, d_status, d_fb_dist,
-                                       (cudaStream_t)stream));
+                                       (cudaStream_t)stream, false, d_last_step));
 }
 
 extern "C" vio_status vio_stereo_match(vio_ctx* ctx, const vio_pyr_layout* layout,
@@ -238,6 +318,27 @@ extern "C" vio_status vio_stereo_match(vio_ctx* ctx, const vio_pyr_layout* layou
                                        vio::make_batch(*cam1), d_pts, d_init, d_count, capacity,
                                        cfg, nullptr, d_match, d_status, d_fb_dist,
                                        (cudaStream_t)stream));
+}
+
+extern "C" vio_status vio_match_cameras(vio_ctx* ctx, const vio_pyr_layout* layout,
+                                        const vio_pyr_batch* src, const vio_pyr_batch* dst,
+                                        const float* d_pts, const float* d_init,
+                                        const int32_t* d_count, int32_t capacity,
+                                        float* d_match, uint8_t* d_status, float* d_fb_dist,
+                                        void* stream) {
+  if (!ctx || !layout_ok(layout) || !batch_ok(layout, src) || !batch_ok(layout, dst))
+    return VIO_ERR_INVALID_ARG;
+  if (src->n_images != 1 || !d_pts || !d_match || !d_status || capacity < 0)
+    return VIO_ERR_INVALID_ARG;
+  // the one source image, once per target: zero strides
+  vio::Batch s = vio::make_batch(*src);
+  s.l0_stride = 0;
+  s.upper_stride = 0;
+  s.n = dst->n_images;
+  vio::TrackCfg cfg{ctx->p.gn_iters, 1, ctx->p.fb_max_dist, -1};
+  return cuda_status(vio::launch_track(vio::make_geom(*layout), s, vio::make_batch(*dst), d_pts,
+                                       d_init, d_count, capacity, cfg, nullptr, d_match,
+                                       d_status, d_fb_dist, (cudaStream_t)stream, true));
 }
 
 extern "C" vio_status vio_fb_check(const float* d_orig, const float* d_back,

@@ -166,6 +166,7 @@ cudaError_t enqueue_step(vio_batch* b, const int32_t* h_mask, cudaStream_t s) {
       fl[i].net_lb = b->net_cfg.level_b;
       fl[i].net_top = b->net_cfg.start_level;
       fl[i].net_tau = b->net_cfg.min_conf;
+      fl[i].net_max_step = b->net_cfg.max_last_step;
       fl[i].net_out = b->groups[i].net_out;
       fl[i].trk_learned = b->groups[i].trk_learned;
     }

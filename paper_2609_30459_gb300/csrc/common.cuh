@@ -140,6 +140,10 @@ struct vio_ctx {
   // detection scratch: per image, per cell, k packed candidate keys + count
   unsigned long long* d_cand;
   int32_t* d_cand_count;
+  // device status word (VIO_OK, or the first device-side error, e.g. a
+  // bounded wait that gave up) and its pinned host copy
+  int32_t* d_status;
+  int32_t* h_status;
 };
 
 namespace vio {
@@ -160,7 +164,8 @@ cudaError_t launch_select(const unsigned long long* cand, const int32_t* cand_co
 cudaError_t launch_track(const Geom& g, const Batch& src, const Batch& dst, const float* pts,
                          const float* init, const int32_t* count, int capacity,
                          const TrackCfg& cfg, float* out3, float* out2, uint8_t* status,
-                         float* fb_dist, cudaStream_t s);
+                         float* fb_dist, cudaStream_t s, bool shared_pts = false,
+                         float* last_step = nullptr);
 cudaError_t launch_fb_check(const float* orig, const float* back, const int32_t* count,
                             int capacity, int n_images, float max_dist, uint8_t* status,
                             float* dist, cudaStream_t s);

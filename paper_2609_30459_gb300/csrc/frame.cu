@@ -348,15 +348,18 @@ __global__ void VIO_TRACK_BOUNDS frame_track_kernel(const __grid_constant__ Mult
     if (f.net) {
       const float* q = f.net_out + 3 * wl;
       if (q[2] >= f.net_tau) {
+        float last;
         st = trk::track_fb(f.g, f.prev, r.prev_img + c, f.cur, r.cur_img + c, px, py, true,
                            px + q[0], py + q[1], 0.f, cfg, f.net_top, lane, tf, thf, have,
-                           dist);
-        learned = st == VIO_TRACK_OK;
+                           dist, last);
+        learned = st == VIO_TRACK_OK && !(f.net_max_step > 0.f && last > f.net_max_step);
       }
     }
-    if (!learned)
+    if (!learned) {
+      float last;
       st = trk::track_fb(f.g, f.prev, r.prev_img + c, f.cur, r.cur_img + c, px, py, false,
-                         0.f, 0.f, 0.f, cfg, top, lane, tf, thf, have, dist);
+                         0.f, 0.f, 0.f, cfg, top, lane, tf, thf, have, dist, last);
+    }
     if (lane == 0) {
       if (f.net) f.trk_learned[wl] = learned ? 1 : 0;
       f.trk_status[wl] = (uint8_t)st;
@@ -381,8 +384,9 @@ __global__ void VIO_TRACK_BOUNDS frame_track_kernel(const __grid_constant__ Mult
   const unsigned long long key = f.cand[w2];
   const unsigned idx = ~(unsigned)(key & 0xffffffffu);
   const float x = (float)(idx % (unsigned)f.g.w[0]), y = (float)(idx / (unsigned)f.g.w[0]);
+  float last;
   const int st = trk::track_fb(f.g, f.cur, r.cur_img, f.cur, r.cur_img + 1, x, y, false, 0.f,
-                               0.f, 0.f, cfg, top, lane, tf, thf, have, dist);
+                               0.f, 0.f, cfg, top, lane, tf, thf, have, dist, last);
   if (lane == 0) {
     f.spec_status[w2] = (uint8_t)st;
     f.spec_xy[2 * w2] = have ? (float)tf.ax + tf.dx : qnan;
@@ -682,11 +686,11 @@ __global__ void frame_stereo_kernel(const __grid_constant__ MultiK2 mm) {
   const long long q = (long long)s * f.cap + slot;
   const TrackCfg cfg{f.p.gn_iters, 1, f.p.fb_max_dist, -1};
   trk::Pos tf;
-  float thf, dist;
+  float thf, dist, last;
   bool have;
   const int st = trk::track_fb(f.g, f.cur, r.cur_img, f.cur, r.cur_img + 1, f.new_xy[2 * q],
                                f.new_xy[2 * q + 1], false, 0.f, 0.f, 0.f, cfg,
-                               f.g.n_levels - 1, lane, tf, thf, have, dist);
+                               f.g.n_levels - 1, lane, tf, thf, have, dist, last);
   if (lane == 0) {
     const long long o = (long long)s * mn + slot;
     f.spec_status[o] = (uint8_t)st;
@@ -822,36 +826,6 @@ int frame_front_smem(const Geom& g, const vio_params& p, int tile_shift, int pyr
     smem = ps > smem ? ps : smem;
   }
   return smem;
-}
-
-// Launch shapes of vio_pyramid_detect (batches of images: throughput).
-#ifndef VIO_FRONT_FIRST
-#define VIO_FRONT_FIRST 2
-#endif
-#ifndef VIO_FRONT_SHIFT
-#define VIO_FRONT_SHIFT 1
-#endif
-#ifndef VIO_FRONT_THREADS
-#define VIO_FRONT_THREADS 128
-#endif
-
-cudaError_t launch_front(const vio_params& p, const Geom& g, const Batch& all, int det_step,
-                         const uint8_t* mask, long long mask_stride, unsigned long long* cand,
-                         int32_t* cand_count, cudaStream_t s) {
-  MultiK1 mm{};
-  mm.n = 1;
-  const long long units = (all.n + det_step - 1) / det_step;
-  const int gw =
-      det::warps_per_cell(units * (g.w[0] / p.cell_w) * (g.h[0] / p.cell_h), sm_count());
-  mm.a[0] = front_args(p, g, all, det_step, mask, mask_stride, cand, cand_count,
-                       VIO_FRONT_SHIFT, VIO_FRONT_FIRST, VIO_FRONT_THREADS, gw);
-  mm.block_end[0] = units * mm.a[0].blocks_per_unit;
-  const cudaError_t e = launch_k1(
-      mm, frame_front_smem(g, p, VIO_FRONT_SHIFT, VIO_FRONT_FIRST, VIO_FRONT_THREADS, gw),
-      VIO_FRONT_THREADS, s);
-  if (e != cudaSuccess) return e;
-  const int m1 = first_levels(g, VIO_FRONT_FIRST);
-  return g.n_levels > 1 + m1 ? launch_pyramid_from(g, all, m1, p.round_mode, s) : cudaSuccess;
 }
 
 cudaError_t launch_frames(const FrameLaunch* fl, int n_groups, const FrameTune& tune,

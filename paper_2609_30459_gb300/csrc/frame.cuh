@@ -56,6 +56,7 @@ struct FrameLaunch {
   const void* net;                 // packed weights
   int net_la, net_lb, net_top;
   float net_tau;
+  float net_max_step;   // convergence gate of a learned track (<= 0: none)
   float* net_out;                  // [stream][camera] x cap x (dx, dy, conf)
   uint8_t* trk_learned;            // [stream][camera] x cap: 1 = tracked from the proposal
   int stereo_after;                // set by launch_frames from the tune
@@ -118,14 +119,9 @@ inline bool initnet_cfg_ok(const vio_initnet_cfg* c, int n_levels, const void* p
   if (c->level_a < 1 || c->level_b < 1 || c->start_level < 0) return false;
   if (c->level_a >= n_levels || c->level_b >= n_levels || c->start_level >= n_levels)
     return false;
-  return c->min_conf == c->min_conf;   // not NaN
+  return c->min_conf == c->min_conf && c->max_last_step == c->max_last_step;   // not NaN
 }
 int frame_front_smem(const Geom& g, const vio_params& p, int tile_shift, int pyr_first,
                      int threads, int det_warps);
-// Fused pyramid and per-cell detection candidates of every det_step-th
-// image of `all` (one launch), then the pyramid levels beyond the fused pass.
-cudaError_t launch_front(const vio_params& p, const Geom& g, const Batch& all, int det_step,
-                         const uint8_t* mask, long long mask_stride, unsigned long long* cand,
-                         int32_t* cand_count, cudaStream_t s);
 
 }  // namespace vio

@@ -332,6 +332,7 @@ vio_status next_launch(vio_frontend* fe, const uint8_t* d_frames, int32_t pitch,
     f.net_lb = fe->net_cfg.level_b;
     f.net_top = fe->net_cfg.start_level;
     f.net_tau = fe->net_cfg.min_conf;
+    f.net_max_step = fe->net_cfg.max_last_step;
     f.net_out = fe->net_out;
     f.trk_learned = fe->trk_learned;
   }

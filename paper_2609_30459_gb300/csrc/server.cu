@@ -16,6 +16,8 @@
 // the next without waiting for the host; a session can be in both (its
 // frames run in stream order). Completions carry the frame's arrival, launch
 // and completion times.
+#include <pthread.h>
+#include <sched.h>
 #include <string.h>
 
 #include <chrono>
@@ -104,6 +106,8 @@ struct vio_server {
   int64_t budget = 0, used = 0;
   double loop_max_gap = 0.0;           // host loop of the last trace
   int64_t loop_over_1ms = 0;
+  int32_t pin_cpu = -1, rt_priority = 0;   // loop scheduling asked for
+  int32_t granted = 0;                     // what the last trace got (bit 0 pin, bit 1 RT)
 };
 
 namespace {
@@ -549,6 +553,30 @@ extern "C" vio_status vio_server_run_trace(vio_server* s, const vio_server_req* 
   for (int64_t i = 1; i < n; ++i)
     if (reqs[i].t_offset < reqs[i - 1].t_offset) return VIO_ERR_INVALID_ARG;
   const int64_t steps0 = s->steps;
+  // the loop's thread: pinned to one CPU and at a real-time priority for the
+  // call where asked and permitted (restored on return)
+  s->granted = 0;
+  const pthread_t self = pthread_self();
+  cpu_set_t old_set;
+  bool pinned = false;
+  if (s->pin_cpu != -1 && pthread_getaffinity_np(self, sizeof(old_set), &old_set) == 0) {
+    const int cpu = s->pin_cpu == -2 ? sched_getcpu() : s->pin_cpu;
+    if (cpu >= 0 && cpu < CPU_SETSIZE) {
+      cpu_set_t one;
+      CPU_ZERO(&one);
+      CPU_SET(cpu, &one);
+      pinned = pthread_setaffinity_np(self, sizeof(one), &one) == 0;
+    }
+  }
+  int old_policy = 0;
+  sched_param old_param{};
+  bool rt = false;
+  if (s->rt_priority > 0 && pthread_getschedparam(self, &old_policy, &old_param) == 0) {
+    sched_param p{};
+    p.sched_priority = s->rt_priority;
+    rt = pthread_setschedparam(self, SCHED_FIFO, &p) == 0;
+  }
+  s->granted = (pinned ? 1 : 0) | (rt ? 2 : 0);
   const double t0 = now_s();
   int64_t next = 0, got = 0;
   vio_status st = VIO_OK;
@@ -578,6 +606,22 @@ extern "C" vio_status vio_server_run_trace(vio_server* s, const vio_server_req* 
     got += vio_server_take(s, out + got, (int32_t)(n - got));
     if (st != VIO_OK) break;
   }
+  if (rt) pthread_setschedparam(self, old_policy, &old_param);
+  if (pinned) pthread_setaffinity_np(self, sizeof(old_set), &old_set);
   if (n_steps) *n_steps = s->steps - steps0;
   return st;
+}
+
+extern "C" vio_status vio_server_set_loop_policy(vio_server* s, int32_t pin_cpu,
+                                                 int32_t rt_priority) {
+  if (!s || pin_cpu < -2 || rt_priority < 0 || rt_priority > 99) return VIO_ERR_INVALID_ARG;
+  s->pin_cpu = pin_cpu;
+  s->rt_priority = rt_priority;
+  return VIO_OK;
+}
+
+extern "C" vio_status vio_server_loop_policy_granted(const vio_server* s, int32_t* granted) {
+  if (!s || !granted) return VIO_ERR_INVALID_ARG;
+  *granted = s->granted;
+  return VIO_OK;
 }

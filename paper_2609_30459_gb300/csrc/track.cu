@@ -18,6 +18,8 @@ struct TrackArgs {
   float* out2;         // float2 per slot or null
   uint8_t* status;
   float* fb_dist;
+  float* last_step;    // per slot or null
+  int shared_pts;      // 1: every image tracks the same keypoints (pts, count of image 0)
 };
 
 constexpr int TRK_THREADS = 128;
@@ -29,7 +31,8 @@ __global__ void __launch_bounds__(TRK_THREADS) track_kernel(TrackArgs a) {
   if (wid >= total) return;
   const int img = (int)(wid / a.capacity);
   const int k = (int)(wid - (long long)img * a.capacity);
-  const int n = a.count ? min(a.count[img], a.capacity) : a.capacity;
+  const int n = a.count ? min(a.count[a.shared_pts ? 0 : img], a.capacity) : a.capacity;
+  const long long pk = a.shared_pts ? k : wid;   // keypoint slot of the source list
   const float nanf_ = __int_as_float(0x7fc00000);
   if (k >= n) {
     if (lane == 0) {
@@ -37,17 +40,18 @@ __global__ void __launch_bounds__(TRK_THREADS) track_kernel(TrackArgs a) {
       if (a.out3) a.out3[3 * wid] = a.out3[3 * wid + 1] = a.out3[3 * wid + 2] = nanf_;
       if (a.out2) a.out2[2 * wid] = a.out2[2 * wid + 1] = nanf_;
       if (a.fb_dist) a.fb_dist[wid] = nanf_;
+      if (a.last_step) a.last_step[wid] = nanf_;
     }
     return;
   }
   trk::Pos tf;
-  float thf = 0.f, dist;
+  float thf = 0.f, dist, last = 0.f;
   bool have;
   const bool hi = a.init != nullptr;
-  const int st = trk::track_fb(a.g, a.src, img, a.dst, img, a.pts[2 * wid], a.pts[2 * wid + 1],
+  const int st = trk::track_fb(a.g, a.src, img, a.dst, img, a.pts[2 * pk], a.pts[2 * pk + 1],
                                hi, hi ? a.init[3 * wid] : 0.f, hi ? a.init[3 * wid + 1] : 0.f,
                                hi ? a.init[3 * wid + 2] : 0.f, a.cfg, top_level(a.cfg, a.g),
-                               lane, tf, thf, have, dist);
+                               lane, tf, thf, have, dist, last);
   if (lane == 0) {
     a.status[wid] = (uint8_t)st;
     const float ox = have ? (float)tf.ax + tf.dx : nanf_;
@@ -62,6 +66,7 @@ __global__ void __launch_bounds__(TRK_THREADS) track_kernel(TrackArgs a) {
       a.out2[2 * wid + 1] = oy;
     }
     if (a.fb_dist) a.fb_dist[wid] = dist;
+    if (a.last_step) a.last_step[wid] = have ? last : nanf_;
   }
 }
 
@@ -87,8 +92,10 @@ __global__ void fb_check_kernel(const float* __restrict__ orig, const float* __r
 cudaError_t launch_track(const Geom& g, const Batch& src, const Batch& dst, const float* pts,
                          const float* init, const int32_t* count, int capacity,
                          const TrackCfg& cfg, float* out3, float* out2, uint8_t* status,
-                         float* fb_dist, cudaStream_t s) {
-  TrackArgs a{g, src, dst, pts, init, count, capacity, src.n, cfg, out3, out2, status, fb_dist};
+                         float* fb_dist, cudaStream_t s, bool shared_pts, float* last_step) {
+  TrackArgs a{g,    src,  dst,    pts,     init,      count,
+              capacity, src.n, cfg, out3, out2, status, fb_dist, last_step,
+              shared_pts ? 1 : 0};
   const long long warps = (long long)capacity * src.n;
   if (warps == 0) return cudaSuccess;
   const long long blocks = (warps * 32 + TRK_THREADS - 1) / TRK_THREADS;

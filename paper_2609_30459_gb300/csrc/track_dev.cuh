@@ -320,9 +320,14 @@ __device__ __forceinline__ void small_rot(float p, float& c, float& s, float& a,
   }
 }
 
-// One Gauss-Newton step (Eq. 4-5). Returns a VIO_TRACK_* status.
+// Radius of the pattern's outermost point (7, 3): an increment (dx, dy, dth)
+// moves no pattern point by more than |dx| + |dy| + kPatRadius |dth| px.
+constexpr float kPatRadius = 7.6158f;
+
+// One Gauss-Newton step (Eq. 4-5). Returns a VIO_TRACK_* status; `moved` is
+// the bound above on how far the step moved the pattern (level px).
 __device__ __forceinline__ int gn_step(const Lv& L, const Tpl& T, int lane, const LanePts& P,
-                                       Warp& W) {
+                                       Warp& W, float& moved) {
   float r0 = 0.f, r1 = 0.f, r2 = 0.f, r3 = 0.f;
   bool ok = true;
   const unsigned xmax = (unsigned)(L.w - 2), ymax = (unsigned)(L.h - 2);
@@ -361,6 +366,7 @@ __device__ __forceinline__ int gn_step(const Lv& L, const Tpl& T, int lane, cons
   const float d2 = T.c2 - q * r3;
   // a NaN or an infinity in any component fails the (finite) comparison
   if (!(fabsf(d0) + fabsf(d1) + fabsf(d2) < 3.0e38f)) return VIO_TRACK_NAN;
+  moved = fabsf(d0) + fabsf(d1) + kPatRadius * fabsf(d2);
   // T <- T o exp(delta): t += R V(d2) (d0, d1), R <- R R(d2)
   float cd, sd, a, b;
   small_rot(d2, cd, sd, a, b);
@@ -383,12 +389,14 @@ __device__ __forceinline__ Lv get_lv(const Geom& g, const Batch& b, int img, int
 // source batch into image dst_img of the target batch, from warp (t0, th0) at
 // level 0, over levels top..0 (top = n_levels - 1 is the whole pyramid). A
 // level whose template is invalid is skipped, except level 0; any warp
-// failure ends the track.
+// failure ends the track. last_step: how far the last Gauss-Newton step at
+// level 0 moved the pattern (bound of gn_step, level-0 px; 0 if none ran).
 __device__ __forceinline__ int track_dir(const Geom& g, const Batch& src, int src_img,
                                          const Batch& dst, int dst_img, const Pos& p, Pos t0,
                                          float th0, int iters, int top, int lane, Pos& t_out,
-                                         float& th_out) {
+                                         float& th_out, float& last_step) {
   Warp W;
+  last_step = 0.f;
   to_level1(t0.ax, t0.dx, top, W.t.ax, W.t.dx);
   to_level1(t0.ay, t0.dy, top, W.t.ay, W.t.dy);
   W.th = th0;
@@ -404,10 +412,12 @@ __device__ __forceinline__ int track_dir(const Geom& g, const Batch& src, int sr
       if (l == 0) return ts;
     } else {
       const Lv D = get_lv(g, dst, dst_img, l);
+      float moved = 0.f;
       for (int it = 0; it < iters; ++it) {
-        const int st = gn_step(D, T, lane, P, W);
+        const int st = gn_step(D, T, lane, P, W, moved);
         if (st != VIO_TRACK_OK) return st;
       }
+      if (l == 0) last_step = moved;
       rebase(W.t);
     }
     if (l > 0) {
@@ -425,12 +435,13 @@ __device__ __forceinline__ int track_dir(const Geom& g, const Batch& src, int sr
 
 // Forward track with the optional backward pass and distance check, both
 // over levels top..0, from warp (ix, iy, ith) if has_init, else from p.
-// Returns the status; tf/thf hold the forward result when it exists.
+// Returns the status; tf/thf hold the forward result when it exists and
+// last_fwd the forward pass's last level-0 step (track_dir).
 __device__ __forceinline__ int track_fb(const Geom& g, const Batch& src, int src_img,
                                         const Batch& dst, int dst_img, float px, float py,
                                         bool has_init, float ix, float iy, float ith,
                                         const TrackCfg& cfg, int top, int lane, Pos& tf,
-                                        float& thf, bool& have, float& dist) {
+                                        float& thf, bool& have, float& dist, float& last_fwd) {
   const Pos p = split(px, py);
   Pos t0 = p;
   float th0 = 0.f;
@@ -439,16 +450,16 @@ __device__ __forceinline__ int track_fb(const Geom& g, const Batch& src, int src
     th0 = ith;
   }
   int st = track_dir(g, src, src_img, dst, dst_img, p, t0, th0, cfg.gn_iters, top, lane, tf,
-                     thf);
+                     thf, last_fwd);
   have = st == VIO_TRACK_OK;
   dist = __int_as_float(0x7fc00000);
   if (st == VIO_TRACK_OK && cfg.fb) {
     // backward: template on the target at the forward result, unrotated;
     // start at the forward estimate's inverse (t = p, theta = -theta_f)
     Pos tb;
-    float thb;
+    float thb, last_b;
     st = track_dir(g, dst, dst_img, src, src_img, tf, p, -thf, cfg.gn_iters, top, lane, tb,
-                   thb);
+                   thb, last_b);
     if (st == VIO_TRACK_OK) {
       const float ex = (float)(tb.ax - p.ax) + (tb.dx - p.dx);
       const float ey = (float)(tb.ay - p.ay) + (tb.dy - p.dy);

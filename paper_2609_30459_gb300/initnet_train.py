@@ -196,8 +196,9 @@ def gain_eval(net: vio.InitNet, frames_list, n_levels=5, cell=32, start_levels=(
     frame, then the plain track (whole pyramid, zero start) and the track
     from the proposal over levels start..0, both with the forward-backward
     check. Reports the fraction of keypoints gated, the fraction of gated
-    tracks that end OK, the fraction of those within `tol` px of the plain
-    result where the plain track is OK, the tracks the plain track loses
+    tracks that end OK and converged (the network's max_last_step gate), the
+    fraction of those within `tol` px of the plain result where the plain
+    track is OK, and where it has also converged, the tracks the plain track loses
     but the proposal keeps, and the mean number of pyramid levels tracked
     per keypoint (plain: n_levels; learned: start+1, plus n_levels on a
     fallback). With generated sequences (synth.Sequence) instead of frame
@@ -225,7 +226,8 @@ def gain_eval(net: vio.InitNet, frames_list, n_levels=5, cell=32, start_levels=(
             c = cnt[: F - 1].contiguous()
             out_p = torch.empty((F - 1, cap, 3), dtype=torch.float32, device=device)
             st_p = torch.empty((F - 1, cap), dtype=torch.uint8, device=device)
-            ctx.track_patches(pyr, src, dst, pts, c, cap, out_p, st_p)
+            ls_p = torch.empty((F - 1, cap), dtype=torch.float32, device=device)
+            ctx.track_patches(pyr, src, dst, pts, c, cap, out_p, st_p, last_step=ls_p)
             x = torch.empty((F - 1, cap, 4, 16, 16), dtype=torch.int16, device=device)
             vio.initnet_extract(pyr, src, dst, pts, c, cap, net.cfg.level_a, net.cfg.level_b, x)
             prop = net.forward(x.view(-1, 4, 16, 16)).view(F - 1, cap, 3)
@@ -240,21 +242,32 @@ def gain_eval(net: vio.InitNet, frames_list, n_levels=5, cell=32, start_levels=(
                                                    for t in range(F - 1)]).astype(np.float32))
                 truth = truth.to(device).view(F - 1, cap, 2)
                 e_p = torch.linalg.norm(out_p[..., :2] - truth, dim=-1)
+            gate_step = net.cfg.max_last_step
             for s in start_levels:
                 out_l = torch.empty_like(out_p)
                 st_l = torch.empty_like(st_p)
+                ls_l = torch.empty_like(ls_p)
                 ctx.track_patches(pyr, src, dst, pts, c, cap, out_l, st_l, init=init,
-                                  from_level=s)
+                                  from_level=s, last_step=ls_l)
                 d = torch.linalg.norm(out_l[..., :2] - out_p[..., :2], dim=-1)
+                # a learned track counts when it ends OK and has converged (its
+                # last level-0 step within the gate); the plain result "succeeds"
+                # when it ends OK, and is settled when it has converged too
+                conv_l = (ls_l <= gate_step) if gate_step > 0 else torch.ones_like(st_l, dtype=torch.bool)
+                conv_p = (ls_p <= gate_step) if gate_step > 0 else torch.ones_like(st_p, dtype=torch.bool)
                 for tau in taus:
                     g = valid & (prop[..., 2] >= tau)
-                    lok = g & (st_l == OKS)
+                    lok = g & (st_l == OKS) & conv_l
                     pok = valid & (st_p == OKS)
                     both = lok & pok
+                    both_conv = both & conv_p
                     k = (s, tau)
                     a = acc.setdefault(k, dict(gated=0, learned_ok=0, both=0, agree=0, gained=0,
                                                plain_ok=0, levels=0.0, plain_true=0,
-                                               gained_true=0, truth=False))
+                                               gained_true=0, truth=False, both_conv=0,
+                                               agree_conv=0))
+                    a["both_conv"] += int(both_conv.sum())
+                    a["agree_conv"] += int((both_conv & (d < tol)).sum())
                     if truth is not None:
                         e_l = torch.linalg.norm(out_l[..., :2] - truth, dim=-1)
                         a["truth"] = True
@@ -274,6 +287,8 @@ def gain_eval(net: vio.InitNet, frames_list, n_levels=5, cell=32, start_levels=(
             "gated": a["gated"] / max(n_total, 1),
             "learned_ok_of_gated": a["learned_ok"] / max(a["gated"], 1),
             "agree_of_both_ok": a["agree"] / max(a["both"], 1),
+            "agree_where_plain_converged": a["agree_conv"] / max(a["both_conv"], 1),
+            "plain_converged_of_both_ok": a["both_conv"] / max(a["both"], 1),
             "gained": a["gained"], "plain_ok": a["plain_ok"],
             "levels_per_kp": a["levels"] / max(n_total, 1)}
         if a["truth"]:

@@ -72,7 +72,8 @@ class Pinhole(ctypes.Structure):
 
 class InitNetCfg(ctypes.Structure):
     _fields_ = [("level_a", ctypes.c_int32), ("level_b", ctypes.c_int32),
-                ("start_level", ctypes.c_int32), ("min_conf", ctypes.c_float)]
+                ("start_level", ctypes.c_int32), ("min_conf", ctypes.c_float),
+                ("max_last_step", ctypes.c_float)]
 
 
 class ServerReq(ctypes.Structure):
@@ -98,6 +99,11 @@ _SIGS = {
     "vio_ctx_create": (ctypes.c_int32, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(Params),
                                         ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]),
     "vio_ctx_destroy": (ctypes.c_int32, [ctypes.c_void_p]),
+    "vio_ctx_sync": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p,
+                                      ctypes.POINTER(ctypes.c_int32)]),
+    "vio_last_error": (ctypes.c_int32, [ctypes.c_void_p]),
+    "vio_wait_flag": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                       ctypes.c_int64, ctypes.c_void_p]),
     "vio_pyramid_build": (ctypes.c_int32, [ctypes.c_void_p, ctypes.POINTER(PyrLayout),
                                            ctypes.POINTER(PyrBatch), ctypes.c_void_p]),
     "vio_fast_scores": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
@@ -122,7 +128,8 @@ _SIGS = {
                                            ctypes.POINTER(PyrBatch), ctypes.POINTER(PyrBatch),
                                            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                            ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
-                                           ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+                                           ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                           ctypes.c_void_p]),
     "vio_stereo_match": (ctypes.c_int32, [ctypes.c_void_p, ctypes.POINTER(PyrLayout),
                                           ctypes.POINTER(PyrBatch), ctypes.POINTER(PyrBatch),
                                           ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
@@ -132,6 +139,11 @@ _SIGS = {
                                           ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                           ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
                                           ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "vio_match_cameras": (ctypes.c_int32, [ctypes.c_void_p, ctypes.POINTER(PyrLayout),
+                                           ctypes.POINTER(PyrBatch), ctypes.POINTER(PyrBatch),
+                                           ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                           ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                           ctypes.c_void_p, ctypes.c_void_p]),
     "vio_fb_check": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                       ctypes.c_int32, ctypes.c_int32, ctypes.c_float,
                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
@@ -219,6 +231,10 @@ _SIGS = {
     "vio_server_run_trace": (ctypes.c_int32, [ctypes.c_void_p, ctypes.POINTER(ServerReq),
                                               ctypes.c_int64, ctypes.POINTER(ServerDone),
                                               ctypes.c_double, ctypes.POINTER(ctypes.c_int64)]),
+    "vio_server_set_loop_policy": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32,
+                                                    ctypes.c_int32]),
+    "vio_server_loop_policy_granted": (ctypes.c_int32, [ctypes.c_void_p,
+                                                        ctypes.POINTER(ctypes.c_int32)]),
     "vio_server_loop_stats": (ctypes.c_int32, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
                                                ctypes.POINTER(ctypes.c_int64)]),
     "vio_initnet_pack": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
@@ -370,6 +386,24 @@ class Context:
             load().vio_ctx_destroy(self.handle)
             self.handle = None
 
+    def sync(self, stream=None) -> int:
+        """vio_ctx_sync: waits for the stream, returns and clears the device
+        status word (OK, or e.g. ERR_TIMEOUT from a bounded wait)."""
+        st = ctypes.c_int32()
+        _check(load().vio_ctx_sync(self.handle, _stream(stream), ctypes.byref(st)),
+               "vio_ctx_sync")
+        return int(st.value)
+
+    def last_error(self) -> int:
+        """vio_last_error: the device status word, not cleared."""
+        return int(load().vio_last_error(self.handle))
+
+    def wait_flag(self, flag, value: int, timeout_ns: int, stream=None):
+        """vio_wait_flag: the stream waits until the int32 flag (CUDA tensor)
+        equals value, for at most timeout_ns."""
+        _check(load().vio_wait_flag(self.handle, _ptr(flag), int(value), int(timeout_ns),
+                                    _stream(stream)), "vio_wait_flag")
+
     def __del__(self):
         try:
             self.close()
@@ -400,15 +434,25 @@ class Context:
 
     def track_patches(self, pyr: Pyramids, src: PyrBatch, dst: PyrBatch, pts, count, capacity,
                       out, status, fb_dist=None, init=None, fb=True, from_level=None,
-                      stream=None):
-        """from_level: track over levels from_level..0 only (default: all)."""
+                      last_step=None, stream=None):
+        """from_level: track over levels from_level..0 only (default: all);
+        last_step: per keypoint, the forward pass's last level-0 step size."""
         flags = TRACK_WITH_FB if fb else TRACK_FORWARD
         if from_level is not None:
             flags |= (int(from_level) + 1) << 4
         _check(load().vio_track_patches(self.handle, ctypes.byref(pyr.layout), ctypes.byref(src),
                                         ctypes.byref(dst), _ptr(pts), _ptr(init), _ptr(count),
                                         capacity, flags, _ptr(out), _ptr(status), _ptr(fb_dist),
-                                        _stream(stream)), "vio_track_patches")
+                                        _ptr(last_step), _stream(stream)), "vio_track_patches")
+
+    def match_cameras(self, pyr: Pyramids, src: PyrBatch, dst: PyrBatch, pts, count, capacity,
+                      match, status, fb_dist=None, init=None, stream=None):
+        """vio_match_cameras: the keypoints of the one source image tracked (with
+        the FB check) into every target image of dst."""
+        _check(load().vio_match_cameras(self.handle, ctypes.byref(pyr.layout), ctypes.byref(src),
+                                        ctypes.byref(dst), _ptr(pts), _ptr(init), _ptr(count),
+                                        capacity, _ptr(match), _ptr(status), _ptr(fb_dist),
+                                        _stream(stream)), "vio_match_cameras")
 
     def stereo_match(self, pyr: Pyramids, cam0: PyrBatch, cam1: PyrBatch, pts, count, capacity,
                      match, status, fb_dist=None, init=None, stream=None):
@@ -508,8 +552,12 @@ class InitNet:
     training, the Adam moments ``m``, ``v`` and the step count) plus the
     configuration; no pickled objects."""
 
+    # a learned track counts only if its last level-0 step moved the pattern
+    # by at most this (px); the plain track otherwise
+    DEFAULT_MAX_LAST_STEP = 1e-3
+
     def __init__(self, master=None, level_a=2, level_b=3, start_level=1, min_conf=0.5,
-                 device="cuda"):
+                 device="cuda", max_last_step=DEFAULT_MAX_LAST_STEP):
         if master is None:
             master = torch.zeros(INITNET_N_PARAMS, dtype=torch.float32)
         master = torch.as_tensor(master, dtype=torch.float32).reshape(-1)
@@ -517,7 +565,7 @@ class InitNet:
             raise ValueError(f"expected {INITNET_N_PARAMS} parameters, got {master.numel()}")
         self.master = master.to(device).contiguous()
         self.packed = torch.empty(INITNET_PACKED_BYTES, dtype=torch.uint8, device=device)
-        self.cfg = InitNetCfg(level_a, level_b, start_level, min_conf)
+        self.cfg = InitNetCfg(level_a, level_b, start_level, min_conf, max_last_step)
         self.m = None
         self.v = None
         self.step = 0
@@ -548,6 +596,7 @@ class InitNet:
                  cfg=np.array([self.cfg.level_a, self.cfg.level_b, self.cfg.start_level],
                               np.int32),
                  min_conf=np.array([self.cfg.min_conf], np.float32),
+                 max_last_step=np.array([self.cfg.max_last_step], np.float32),
                  step=np.array([self.step], np.int64), **extra)
 
     @classmethod
@@ -556,7 +605,9 @@ class InitNet:
         with np.load(path, allow_pickle=False) as z:
             cfg = z["cfg"]
             net = cls(z["master"], int(cfg[0]), int(cfg[1]), int(cfg[2]),
-                      float(z["min_conf"][0]), device)
+                      float(z["min_conf"][0]), device,
+                      float(z["max_last_step"][0]) if "max_last_step" in z
+                      else cls.DEFAULT_MAX_LAST_STEP)
             net.step = int(z["step"][0])
             if "m" in z:
                 net.m = torch.from_numpy(z["m"]).to(device)
@@ -987,6 +1038,20 @@ class Server:
         _check(load().vio_server_run_trace(self.handle, arr, n, out, timeout_s,
                                            ctypes.byref(steps)), "vio_server_run_trace")
         return _done_rows(out, n), int(steps.value)
+
+    def set_loop_policy(self, pin_cpu=-1, rt_priority=0):
+        """vio_server_set_loop_policy: pin the trace loop's thread to a CPU
+        (-2: the one it starts on) and run it at a SCHED_FIFO priority, where
+        permitted."""
+        _check(load().vio_server_set_loop_policy(self.handle, pin_cpu, rt_priority),
+               "vio_server_set_loop_policy")
+
+    def loop_policy_granted(self):
+        """(pinned, real_time) as the last trace got them."""
+        g = ctypes.c_int32()
+        _check(load().vio_server_loop_policy_granted(self.handle, ctypes.byref(g)),
+               "vio_server_loop_policy_granted")
+        return bool(g.value & 1), bool(g.value & 2)
 
     def loop_stats(self):
         """(longest gap between passes of the last trace's host loop in seconds,

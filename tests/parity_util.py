@@ -3,7 +3,13 @@
 Flow tolerance: 1e-3 px against the FP64 oracle. A status disagreement is
 accepted only when the oracle shows the decision sat on its threshold: the
 forward-backward distance within 1e-3 px of the threshold, or a bounds test
-within 1e-3 px (level-0) of its bound.
+within 1e-3 px (level-0) of its bound. Positions are compared where both
+sides end OK, and where both fail the forward-backward check with a settled
+forward pass (its last level-0 step below SETTLED_PX: an unsettled forward
+result that the check rejects is not determined to 1e-3 px). A position
+difference is explained only by the same bounds margin (at most 5% of the
+tracks, counted in the result): a coarse level whose template is that close to
+the image edge is tracked on one side and skipped on the other.
 
 Rotation tolerance: turning the 52-point pattern by d_theta moves its
 outermost point (radius sqrt(7^2 + 3^2) = 7.62 px at level 0) by 7.62 d_theta
@@ -15,6 +21,7 @@ import numpy as np
 FLOW_TOL = 1e-3
 BAND = 1e-3
 THETA_TOL = FLOW_TOL / np.hypot(7.0, 3.0)
+SETTLED_PX = 2e-4   # a forward pass whose last level-0 step moved the pattern less
 
 
 def compare_tracks(g_xy, g_status, ref, fb_max_dist, min_agree=0.999, g_theta=None):
@@ -38,14 +45,32 @@ def compare_tracks(g_xy, g_status, ref, fb_max_dist, min_agree=0.999, g_theta=No
         f"fb {fbd[bad][:10]}")
     if n >= 1000:
         assert agree.mean() >= min_agree, agree.mean()
-    # flow: wherever both have a forward result (OK or FB_FAIL on both sides)
-    have = agree & np.isin(o_status, (0, 5))
-    err = np.abs(g_xy[have] - ref["warp"][have, :2]).max() if have.any() else 0.0
-    assert err < FLOW_TOL, f"flow differs by {err} px"
+    # flow: wherever both sides end OK, or both fail the forward-backward check
+    # with a settled forward result (the oracle's last level-0 step within
+    # SETTLED_PX; an unsettled forward pass that the FB check rejects is not
+    # determined to FLOW_TOL). A difference is explained only by a bounds
+    # decision of the track sitting on its threshold (a coarse level whose
+    # template is within BAND of the image edge is tracked on one side and
+    # skipped on the other): few, and counted.
+    settled = ref["last_step"] <= SETTLED_PX if "last_step" in ref else np.ones(n, bool)
+    have = agree & ((o_status == 0) | ((o_status == 5) & settled))
+    e = np.abs(g_xy - ref["warp"][:, :2]).max(1)
+    big = have & ~(e < FLOW_TOL)
+    on_edge = big & (ref["margin"] <= BAND)
+    assert on_edge.sum() <= max(2, 0.05 * n), (int(on_edge.sum()), n)
+    unexplained = big & ~on_edge
+    if unexplained.any():
+        i = np.where(unexplained)[0][np.argmax(e[unexplained])]
+        raise AssertionError(f"flow differs by {e[i]} px at {i}: status {o_status[i]} margin "
+                             f"{ref['margin'][i]} fb {fbd[i]} gpu {g_xy[i]} oracle "
+                             f"{ref['warp'][i]}")
+    have &= ~on_edge
+    err = float(e[have].max()) if have.any() else 0.0
     th_err = 0.0
     if g_theta is not None and have.any():
         th_err = float(np.abs(np.asarray(g_theta, np.float64)[have] - ref["warp"][have, 2]).max())
         assert th_err < THETA_TOL, f"angle differs by {th_err} rad"
     return {"n": n, "agree": float(agree.mean()) if n else 1.0,
             "n_disagree": int((~agree).sum()), "max_err": float(err),
-            "max_theta_err": th_err, "n_ok": int((o_status == 0).sum())}
+            "max_theta_err": th_err, "n_ok": int((o_status == 0).sum()),
+            "n_flow_on_edge": int(on_edge.sum())}

@@ -294,33 +294,14 @@ def _net_master(kind):
     return flat, q
 
 
-PROPOSAL_TOL = 16 * 4e-3   # px: GPU vs oracle proposal (raw-output tolerance x 16)
-
-
-def _start_spread(prev, cur, xy, flow, op, net):
-    """How far the oracle's track from a proposal moves when the proposal
-    moves by PROPOSAL_TOL (the network's own arithmetic tolerance): a track
-    that has not converged in its iterations inherits such differences."""
-    top = net.start_level + 1
-    base = np.asarray(xy, np.float64) + flow
-    inits = [base] + [base + d for d in ([PROPOSAL_TOL, 0], [-PROPOSAL_TOL, 0],
-                                         [0, PROPOSAL_TOL], [0, -PROPOSAL_TOL])]
-    init = np.zeros((5, 3), np.float32)
-    init[:, :2] = np.array(inits, np.float32)
-    r = oracle.track(prev[:top], cur[:top], np.repeat(np.asarray(xy, np.float32)[None], 5, 0),
-                     init=init, gn_iters=op.gn_iters, fb=True, fb_max_dist=op.fb_max_dist)
-    ok = r["status"] == 0
-    if not ok[0] or ok.sum() < 2:
-        return np.inf
-    return float(np.abs(r["warp"][ok, :2] - r["warp"][0, :2]).max())
-
-
 @pytest.mark.parametrize("kind", ["const", "random"])
 def test_frontend_learned_start_matches_oracle(kind):
-    """Positions within 1e-3 px of the oracle's; a track started from a
-    proposal may differ by as much as the oracle's own result moves when the
-    proposal moves within the network's tolerance (tracks that did not
-    converge in their iterations)."""
+    """Positions within 1e-3 px of the oracle's. A learned track counts only
+    when it has converged (its last level-0 step below the gate), so it sits
+    at the optimum its start leads to whatever the proposal's last bits; the
+    only positions that may differ are those whose oracle result had not
+    converged (last step above the gate: not determined to 1e-3 px), where the
+    two sides may also have taken different paths (few, counted)."""
     w, h, L, cw, ch, n_frames, motion = 640, 480, 5, 32, 32, 5, 12.0
     seq = synth.make_sequence(4100, n_frames, w, h, 1, max_motion=motion, tex_size=2048)
     p = vio.default_params(n_levels=L, cell_w=cw, cell_h=ch)
@@ -336,14 +317,14 @@ def test_frontend_learned_start_matches_oracle(kind):
     frames = torch.from_numpy(seq.frames).cuda()
     st = ofe.StreamState()
     prev_ids = [np.zeros(0, np.int32), np.zeros(0, np.int32)]
-    n_learned_o = n_learned_g = n_common = n_spread = 0
+    n_learned_o = n_learned_g = n_common = n_unconv = 0
+    gate = net.cfg.max_last_step
+    assert gate > 0 and onet_cfg.max_last_step == pytest.approx(gate)
     worst = 0.0
     for t in range(n_frames):
         fe.step(frames[t: t + 1])
         torch.cuda.synchronize()
         v = fe.view()
-        prev_pyr = st.pyr
-        prev_xy = [x.copy() for x in st.xy]
         res = ofe.step(st, seq.frames[t], op, cap, n_threads=8, net=onet_cfg)
         cnt = v["track_count"][0].cpu().numpy()
         gx = [v["track_xy"][0, c, : cnt[c]].cpu().numpy() for c in range(2)]
@@ -368,11 +349,9 @@ def test_frontend_learned_start_matches_oracle(kind):
                     if e >= FLOW_TOL:
                         r = res["track"][c]
                         j = row[i]
-                        assert r is not None and r["learned"][j], (t, c, i, e)
-                        sp = _start_spread(prev_pyr[c], st.pyr[c], prev_xy[c][j], r["flow"][j],
-                                           op, onet_cfg)
-                        assert e < FLOW_TOL + 2 * sp, (t, c, i, e, sp)
-                        n_spread += 1
+                        assert r is not None and r["last_step"][j] > gate, (
+                            t, c, i, e, r["last_step"][j], bool(r["learned"][j]))
+                        n_unconv += 1
                     else:
                         worst = max(worst, e)
         stats, _ = fe.read_stats()
@@ -382,9 +361,9 @@ def test_frontend_learned_start_matches_oracle(kind):
         prev_ids = [gi[0].copy(), gi[1].copy()]
     assert worst < FLOW_TOL, worst
     assert n_common > 500
-    assert n_spread <= 0.05 * n_common, (n_spread, n_common)
+    assert n_unconv <= 0.01 * n_common, (n_unconv, n_common)
     assert n_learned_o > 100
-    assert abs(n_learned_g - n_learned_o) <= max(3, 0.01 * n_learned_o)
+    assert abs(n_learned_g - n_learned_o) <= max(3, 0.02 * n_learned_o)
     fe.close()
 
 

@@ -1,8 +1,10 @@
 """What the trained initializer gains over the plain tracker (the shipped
 weights, held-out sequences with motion up to 40 px, 5 levels): the plain
-pyramidal KLT from a zero start is the yardstick. Where both end OK the learned
-start's final flow must equal the plain result within 1e-3 px for nearly all
-keypoints; the learned start must track over fewer levels; and the tracks it
+pyramidal KLT from a zero start is the yardstick. A learned track counts only
+when it ends OK and has converged (its last level-0 step within the network's
+gate), so where the plain result ends OK and has converged too, the two agree
+within 1e-3 px (>= 99.9%), and where the plain result ends OK at all nearly
+always; the learned start must track over fewer levels; and the tracks it
 keeps that the plain tracker loses must be right (ground truth of the
 generator)."""
 import os
@@ -37,8 +39,10 @@ def test_trained_initializer_gain():
     print(g)
     assert g["n"] > 5000
     assert r["gated"] > 0.3                         # the gate lets a good share through
-    assert r["learned_ok_of_gated"] > 0.9           # and those mostly converge
-    assert r["agree_of_both_ok"] > 0.97             # to the plain result within 1e-3 px
+    assert r["learned_ok_of_gated"] > 0.85          # and those mostly end OK and converged
+    assert r["agree_of_both_ok"] > 0.99             # at the plain result within 1e-3 px,
+    assert r["agree_where_plain_converged"] >= 0.999   # and wherever the plain result is
+    assert r["plain_converged_of_both_ok"] > 0.95      # settled (converged) too
     assert r["levels_per_kp"] < 0.85 * g["n_levels"]
     assert r["plain_ok_within_truth"] > 0.95
     assert r["gained"] >= 0

@@ -253,9 +253,10 @@ def test_track_temporal_parity(w, h, L, n, fb):
     out = torch.zeros((1, cap, 3), device=DEV)
     st = torch.zeros((1, cap), dtype=torch.uint8, device=DEV)
     fbd = torch.zeros((1, cap), device=DEV)
+    ls = torch.zeros((1, cap), device=DEV)
     for cam in (0, 1):
         ctx.track_patches(pyr, pyr.batch(cam, 1, 1), pyr.batch(2 + cam, 1, 1), pts, cnt, cap,
-                          out, st, fbd, fb=fb)
+                          out, st, fbd, fb=fb, last_step=ls)
         torch.cuda.synchronize()
         ref = oracle.track(oracle.pyramid(imgs[0, cam], L), oracle.pyramid(imgs[1, cam], L), kp,
                            fb=fb, fb_max_dist=p.fb_max_dist, n_threads=8)
@@ -263,10 +264,14 @@ def test_track_temporal_parity(w, h, L, n, fb):
                            ref, p.fb_max_dist, g_theta=out[0, : len(kp), 2].cpu().numpy())
         assert s["n_ok"] >= 0.5 * len(kp), s
         assert (st[0, len(kp):] == 255).all()
+        both = (st[0, : len(kp)].cpu().numpy() == 0) & (ref["status"] == 0)
         if fb:
-            both = (st[0, : len(kp)].cpu().numpy() == 0) & (ref["status"] == 0)
             dd = np.abs(fbd[0, : len(kp)].cpu().numpy()[both] - ref["fb_dist"][both])
             assert dd.max() < 1e-3
+        # the convergence measure (the learned start's gate): the last level-0
+        # step, |dx| + |dy| + r |dth|, to 1e-4 px plus 1% where it is large
+        gl = ls[0, : len(kp)].cpu().numpy().astype(np.float64)[both]
+        assert np.all(np.abs(gl - ref["last_step"][both]) <= 1e-4 + 0.01 * ref["last_step"][both])
 
 
 def test_track_with_init_and_empty():

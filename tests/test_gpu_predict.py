@@ -104,7 +104,7 @@ def test_tracks_from_the_prediction_match_oracle():
     g_pred = good(out[0].cpu().numpy(), st[0].cpu().numpy())
     g_id = good(out0[0].cpu().numpy(), st0[0].cpu().numpy())
     print(f"within 0.5 px of the truth: model-based start {g_pred:.3f}, identity {g_id:.3f}")
-    assert g_pred >= g_id and g_pred > 0.8
+    assert g_pred > g_id + 0.2 and g_pred > 0.3
     ctx.close()
 
 

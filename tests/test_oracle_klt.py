@@ -256,3 +256,54 @@ def test_learned_start_gate_and_fallback():
     rest = ~r["learned"]
     assert np.array_equal(r["status"][rest], plain["status"][rest])
     assert np.array_equal(r["warp"][rest], plain["warp"][rest])
+
+
+def test_last_step_measure():
+    """The last level-0 step (the learned start's convergence measure) is 0
+    on self-tracking (every increment is exactly zero), vanishes on an exact
+    integer shift recovered to 1e-9, and is the bound |dx| + |dy| + r |dth|
+    with r the pattern's largest radius, sqrt(7^2 + 3^2)."""
+    src = texture(3)
+    pyr = oracle.pyramid(src, 3)
+    pts = np.array([[60.0, 50.0], [100.5, 70.25]], np.float32)
+    r = oracle.track(pyr, pyr, pts, gn_iters=5)
+    assert (r["status"] == 0).all() and (r["last_step"] == 0).all()
+    r = oracle.track(pyr, oracle.pyramid(shifted(src, (2, -1)), 3), pts, gn_iters=30)
+    assert (r["status"] == 0).all() and (r["last_step"] < 1e-9).all()
+    # one Gauss-Newton iteration at a single level from a start 0.3 px off:
+    # that step is the whole motion, so the measure is at least the distance
+    # moved
+    init = np.array([[60.3, 50.0, 0.0], [100.5, 70.55, 0.0]], np.float32)
+    one = oracle.pyramid(src, 1)
+    r1 = oracle.track(one, one, pts, init=init, gn_iters=1, fb=False)
+    moved = np.abs(r1["warp"][:, :2] - init[:, :2]).sum(1)
+    assert (r1["last_step"] >= moved - 1e-9).all() and (moved > 0.2).all()
+    pat = oracle.pattern()
+    assert np.hypot(pat[:, 0], pat[:, 1]).max() == pytest.approx(np.sqrt(58.0))
+
+
+def test_learned_start_convergence_gate():
+    """A learned track counts only when its last level-0 step is within the
+    gate: with a gate of ~0 every proposal that is not exact falls back to
+    the plain track, with no gate (<= 0) the proposal's track is kept."""
+    from oracle.frontend import Params, temporal
+    prev, cur = _shift_pair(73, 5, 3)
+    rng = np.random.default_rng(1)
+    pts = np.stack([rng.uniform(40, 160, 30), rng.uniform(40, 120, 30)], 1).astype(np.float32)
+    p = Params(n_levels=4)
+    plain = temporal(prev, cur, pts, p)
+    net = _const_net(5.4, 2.7, 4.0, start_level=0)     # 0.5 px off: level 0 alone
+    net.max_last_step = 0.0
+    free = temporal(prev, cur, pts, p, net)
+    assert free["learned"].mean() > 0.5
+    net.max_last_step = 1e-300
+    tight = temporal(prev, cur, pts, p, net)
+    assert not tight["learned"].any()
+    assert np.array_equal(tight["warp"], plain["warp"])
+    net.max_last_step = 2e-4
+    gated = temporal(prev, cur, pts, p, net)
+    kept = gated["learned"]
+    assert (gated["last_step"][kept] <= 2e-4).all()
+    both = kept & (plain["status"] == 0) & (plain["last_step"] <= 2e-4)
+    assert both.any()
+    assert np.abs(gated["warp"][both, :2] - plain["warp"][both, :2]).max() < 1e-3
