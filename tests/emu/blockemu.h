@@ -1,0 +1,130 @@
+// Host emulation of CUDA thread blocks, for running the library's device code
+// on the CPU under AddressSanitizer (test infrastructure). One std::thread per
+// CUDA thread; __syncthreads, named barriers and the warp collectives
+// (__ballot_sync, __shfl*_sync, __reduce_max_sync, __syncwarp) are barriers
+// over the threads that must all reach them, so code that calls a full-mask
+// collective from divergent lanes stops with "EMU DEADLOCK" instead of
+// hanging. Integer intrinsics (__byte_perm, __vminu2, __vmaxu2, __popc, __ffs,
+// atomicMax) are plain host functions.
+#pragma once
+#include <cuda_runtime.h>
+#include <algorithm>
+#include <condition_variable>
+#include <cstdint>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <functional>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+struct EmuDim { unsigned x = 0, y = 0, z = 0; };
+static thread_local EmuDim threadIdx;
+static EmuDim blockDim{128, 1, 1};
+static thread_local EmuDim blockIdx;
+
+struct EmuBarrier {
+  std::mutex m; std::condition_variable cv; int n, count = 0; long gen = 0;
+  explicit EmuBarrier(int n_) : n(n_) {}
+  void wait() {
+    std::unique_lock<std::mutex> l(m);
+    long g = gen;
+    if (++count == n) { count = 0; ++gen; cv.notify_all(); return; }
+    if (!cv.wait_for(l, std::chrono::seconds(20), [&] { return gen != g; })) {
+      fprintf(stderr, "EMU DEADLOCK (barrier of %d, %d arrived)\n", n, count); std::abort();
+    }
+  }
+};
+struct EmuWarp { EmuBarrier bar{32}; uint64_t vals[32]; };
+struct EmuBlock {
+  EmuBarrier block_bar;
+  std::vector<std::unique_ptr<EmuWarp>> warps;
+  std::mutex nm; std::map<int, std::unique_ptr<EmuBarrier>> named;
+  explicit EmuBlock(int nt) : block_bar(nt) { for (int i = 0; i < nt / 32; ++i) warps.emplace_back(new EmuWarp); }
+};
+static thread_local EmuBlock* emu_blk = nullptr;
+inline EmuWarp& emu_warp() { return *emu_blk->warps[threadIdx.x >> 5]; }
+inline void __syncthreads() { emu_blk->block_bar.wait(); }
+inline void __syncwarp(unsigned = 0xffffffffu) { emu_warp().bar.wait(); }
+inline void emu_bar(int id, int n) {
+  EmuBarrier* b;
+  { std::lock_guard<std::mutex> l(emu_blk->nm);
+    auto& p = emu_blk->named[id];
+    if (!p) p.reset(new EmuBarrier(n));
+    if (p->n != n) { fprintf(stderr, "named barrier count mismatch\n"); std::abort(); }
+    b = p.get(); }
+  b->wait();
+}
+template <class F> inline uint64_t emu_collect(uint64_t v, F f) {
+  auto& w = emu_warp(); int lane = threadIdx.x & 31;
+  w.vals[lane] = v; w.bar.wait(); uint64_t r = f(w.vals, lane); w.bar.wait(); return r;
+}
+inline void emu_check_full(unsigned mask) { if (mask != 0xffffffffu) { fprintf(stderr, "partial mask\n"); std::abort(); } }
+inline unsigned __ballot_sync(unsigned mask, int p) {
+  emu_check_full(mask);
+  return (unsigned)emu_collect(p != 0, [](uint64_t* v, int) { unsigned r = 0; for (int i = 0; i < 32; ++i) if (v[i]) r |= 1u << i; return (uint64_t)r; });
+}
+inline int __any_sync(unsigned mask, int p) { return __ballot_sync(mask, p) != 0; }
+template <class T> inline T __shfl_sync(unsigned mask, T v, int src) {
+  emu_check_full(mask); uint64_t u = 0; memcpy(&u, &v, sizeof(T));
+  uint64_t r = emu_collect(u, [src](uint64_t* vv, int) { return vv[src & 31]; });
+  T o; memcpy(&o, &r, sizeof(T)); return o;
+}
+template <class T> inline T __shfl_up_sync(unsigned mask, T v, int d) {
+  emu_check_full(mask); uint64_t u = 0; memcpy(&u, &v, sizeof(T));
+  uint64_t r = emu_collect(u, [d](uint64_t* vv, int lane) { return lane >= d ? vv[lane - d] : vv[lane]; });
+  T o; memcpy(&o, &r, sizeof(T)); return o;
+}
+template <class T> inline T __shfl_xor_sync(unsigned mask, T v, int d) {
+  emu_check_full(mask); uint64_t u = 0; memcpy(&u, &v, sizeof(T));
+  uint64_t r = emu_collect(u, [d](uint64_t* vv, int lane) { return vv[lane ^ d]; });
+  T o; memcpy(&o, &r, sizeof(T)); return o;
+}
+template <class T> inline T __shfl_down_sync(unsigned mask, T v, int d) {
+  emu_check_full(mask); uint64_t u = 0; memcpy(&u, &v, sizeof(T));
+  uint64_t r = emu_collect(u, [d](uint64_t* vv, int lane) { return lane + d < 32 ? vv[lane + d] : vv[lane]; });
+  T o; memcpy(&o, &r, sizeof(T)); return o;
+}
+inline unsigned __reduce_max_sync(unsigned mask, unsigned v) {
+  emu_check_full(mask);
+  return (unsigned)emu_collect(v, [](uint64_t* vv, int) { uint64_t m = 0; for (int i = 0; i < 32; ++i) m = std::max(m, vv[i]); return m; });
+}
+inline int __popc(unsigned v) { return __builtin_popcount(v); }
+inline int __popcll(unsigned long long v) { return __builtin_popcountll(v); }
+inline int __ffs(unsigned v) { return __builtin_ffs((int)v); }
+inline int __clz(unsigned v) { return v ? __builtin_clz(v) : 32; }
+inline unsigned __byte_perm(unsigned x, unsigned y, unsigned s) {
+  uint8_t b[8];
+  for (int i = 0; i < 4; ++i) { b[i] = (x >> (8 * i)) & 0xff; b[4 + i] = (y >> (8 * i)) & 0xff; }
+  unsigned r = 0;
+  for (int i = 0; i < 4; ++i) r |= (unsigned)b[(s >> (4 * i)) & 7] << (8 * i);
+  return r;
+}
+inline unsigned __vminu2(unsigned a, unsigned b) {
+  unsigned lo = std::min(a & 0xffffu, b & 0xffffu), hi = std::min(a >> 16, b >> 16); return lo | (hi << 16); }
+inline unsigned __vmaxu2(unsigned a, unsigned b) {
+  unsigned lo = std::max(a & 0xffffu, b & 0xffffu), hi = std::max(a >> 16, b >> 16); return lo | (hi << 16); }
+template <class T> inline T __ldg(const T* p) { return *p; }
+using std::min; using std::max;
+inline int min(int a, int b) { return a < b ? a : b; }
+inline int max(int a, int b) { return a > b ? a : b; }
+inline unsigned min(unsigned a, unsigned b) { return a < b ? a : b; }
+inline unsigned max(unsigned a, unsigned b) { return a > b ? a : b; }
+inline long long min(long long a, long long b) { return a < b ? a : b; }
+inline long long max(long long a, long long b) { return a > b ? a : b; }
+
+// runs body(tid) for every thread of one block
+inline void emu_run_block(int nt, const std::function<void()>& body, EmuDim bidx) {
+  blockDim.x = nt;
+  EmuBlock blk(nt);
+  std::vector<std::thread> th;
+  for (int t = 0; t < nt; ++t)
+    th.emplace_back([&, t] { emu_blk = &blk; threadIdx.x = t; blockIdx = bidx; body(); });
+  for (auto& x : th) x.join();
+}
+static std::mutex emu_atomic_mu;
+inline unsigned long long atomicMax(unsigned long long* p, unsigned long long v) {
+  std::lock_guard<std::mutex> l(emu_atomic_mu); unsigned long long o = *p; if (v > o) *p = v; return o; }
