@@ -486,8 +486,9 @@ INITNET_FLOP = (2 * 8 * 8 * 32 * 4 * 9 + 2 * 4 * 4 * 32 * 32 * 9 + 2 * 2 * 2 * 3
 
 
 def initnet_tensor_roofline(torch, vio, net, peaks, n=1 << 16, reps=5):
-    """The flow network's tiled forward pass (BF16 mma.sync, FP32 accumulate) over
-    n random inputs, useful FLOPs against the measured dense BF16 peak."""
+    """The flow network's forward pass on the tcgen05 tensor cores (BF16
+    operands, FP32 accumulators in tensor memory) over n random inputs, useful
+    FLOPs against the measured dense BF16 peak."""
     g = torch.Generator(device="cuda").manual_seed(11)
     x = (0.5 * torch.randn((n, 4, 16, 16), device="cuda", generator=g)).to(torch.bfloat16)
     x = x.view(torch.int16)
@@ -505,11 +506,12 @@ def initnet_tensor_roofline(torch, vio, net, peaks, n=1 << 16, reps=5):
     ach = n * INITNET_FLOP / t / 1e12
     peak = peaks.get("bf16_tflops", 1900.0)
     return {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-            "frac": ach / peak, "kernel": "forward_tile_kernel", "samples": n,
+            "frac": ach / peak, "kernel": "forward_tc_kernel", "samples": n,
             "flop_per_sample": INITNET_FLOP, "ms": 1000 * t,
             "peak_source": "measured dense BF16 (burst)",
-            "note": "legacy mma.sync m16n8k16 tiles of 16 samples per 512-thread CTA; the "
-                    "forward pass of the frame step uses the same tiles"}
+            "note": "tcgen05.mma (M = 128 rows, operands in shared memory, accumulators in "
+                    "tensor memory), rounds of 32 samples per 128-thread CTA; the proposal "
+                    "launch of the frame step runs the same code"}
 
 
 def frontend_config_run(torch, vio, name, w, h, n_streams, levels, cw, ch, n_frames, motion,

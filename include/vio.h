@@ -726,9 +726,17 @@ vio_status vio_initnet_extract(const vio_pyr_layout* layout, const vio_pyr_batch
                                const int32_t* d_count, int32_t capacity, int32_t level_a,
                                int32_t level_b, uint16_t* d_x, void* stream);
 
-/* d_out[3*i..3*i+2] = (dx, dy, confidence) of input i, i < n. */
+/* d_out[3*i..3*i+2] = (dx, dy, confidence) of input i, i < n. Runs on the
+ * tcgen05 tensor cores (BF16 operands, FP32 accumulation). */
 vio_status vio_initnet_forward(const void* d_packed, const uint16_t* d_x, int32_t n,
                                float* d_out, void* stream);
+
+/* Reads and clears (synchronously) the status word of the tensor-core
+ * forward passes of this device (vio_initnet_forward and the learned
+ * proposals of the frame steps): VIO_OK, or VIO_ERR_TIMEOUT when a launch
+ * gave up waiting for an MMA completion (bounded polling), freed its tensor
+ * memory and left its outputs unwritten. */
+vio_status vio_initnet_fault(int32_t* status);
 
 /* Adds grad_scale * (sum over the n samples d_index[0..n-1] (NULL = 0..n-1)
  * of dL_i/dparams), labels at radius label_radius px (> 0), to d_grad

@@ -88,8 +88,9 @@ __device__ __forceinline__ int ring_dy(int k) {
 // (0,8) and (4,12) (the paper's early rejection), so with m = score + 1,
 //   m <= ub = max(min(max(v0,v8), max(v4,v12)) - c, c - max(min(v0,v8), min(v4,v12))).
 // Exact scores are computed only for pixels whose bound reaches a threshold
-// t, lowered in steps until at least k candidates with m >= t are known (or t
-// reaches T_min + 1). After every pixel with ub >= t is evaluated, every
+// t, which starts 24 below the largest bound of the cell and its ring and is
+// lowered in steps of 24 until at least k candidates with m >= t are known
+// (or t reaches T_min + 1). After every pixel with ub >= t is evaluated, every
 // pixel with m >= t has its 3x3 maximum test decided: a neighbour either is
 // evaluated (exact comparison) or has ub < t <= m. So the candidates with
 // m >= t are exactly known, and if there are k of them no other pixel can
@@ -125,7 +126,7 @@ __host__ __device__ inline BlockSmem block_smem(int cw, int ch, int k, int bcx, 
   S.c_u = 16;                                      // guards around both maps
   S.c_v = S.c_u + pyr::up16(S.msb * S.mh) + 16;
   S.c_cols = S.c_v + pyr::up16(S.msb * S.mh) + 16;
-  S.c_red = S.c_cols + 16 * (S.msb / 4);
+  S.c_red = S.c_cols + 8 * (S.msb / 4);
   S.c_merge = S.c_red + pyr::up16(4 * 2 * g);
   S.per_cell = S.c_merge + pyr::up16(8 * g * k);
   S.w_queue = 0;
@@ -389,26 +390,26 @@ __device__ __forceinline__ void detect_cell(const uint8_t* __restrict__ st, int 
   const int srow0 = y0 - 1 - sy0;                        // staged row of map row 0
   uint8_t* umap = csm + S.c_u;
   uint8_t* vmap = csm + S.c_v;
-  uint4* colm = reinterpret_cast<uint4*>(csm + S.c_cols);   // per quad: ring, cell masks
+  uint2* colm = reinterpret_cast<uint2*>(csm + S.c_cols);   // per quad: ring masks
   int* red = reinterpret_cast<int*>(csm + S.c_red);
   unsigned long long* merge = reinterpret_cast<unsigned long long*>(csm + S.c_merge);
   uint16_t* queue = reinterpret_cast<uint16_t*>(wsm + S.w_queue);
   unsigned long long* keys = reinterpret_cast<unsigned long long*>(wsm + S.w_keys);
 
   // per quad: lanes where the bound is defined (FAST ring inside the image,
-  // inside the cell's ring region) and lanes inside the cell
+  // inside the cell's ring region)
   for (int q = tg; q < nq; q += GT) {
     const int xq = mx0 + 4 * q;
     const int rl = max(x0 - 1, 3), rh = min(x0 + cw, W - 4);
-    const int cl = max(x0, b), chh = min(x0 + cw - 1, W - 1 - b);
-    colm[q] = make_uint4(pair_mask2(xq, rl, rh), pair_mask2(xq, cl, chh),
-                         pair_mask2(xq + 1, rl, rh), pair_mask2(xq + 1, cl, chh));
+    colm[q] = make_uint2(pair_mask2(xq, rl, rh), pair_mask2(xq + 1, rl, rh));
   }
   const bool atomic_sel = cg.sel == VIO_SELECT_ATOMIC;   // k == 1: one 64-bit maximum per cell
   if (atomic_sel && tg == 0) merge[0] = 0ull;
   group_sync(G, bar);
 
-  // pass A: bounds of the cell and its ring, the largest of the cell's; this
+  // pass A: bounds of the cell and its ring and the largest of them (it only
+  // sets the first threshold: any start at or above the largest bound of the
+  // cell's unmasked pixels gives the same result); this
   // thread's quads i = tg + j * GT -> (row r, quad q), stepped without divisions
   const unsigned K = (0x100u + (unsigned)T) * 0x00010001u;
   unsigned acc = 0;
@@ -440,21 +441,14 @@ __device__ __forceinline__ void detect_cell(const uint8_t* __restrict__ st, int 
       // 0x100 + max(hi - c, c - lo) per lane, then max(ub - T, 0)
       const unsigned da = __vmaxu2(hia + 0x01000100u - Ca, Ca + 0x01000100u - loa);
       const unsigned db = __vmaxu2(hib + 0x01000100u - Cb, Cb + 0x01000100u - lob);
-      const uint4 cm = colm[q];
+      const uint2 cm = colm[q];
       const bool yf = y >= 3 && y <= H - 4;
       const unsigned ua = (__vmaxu2(da, K) - K) & (yf ? cm.x : 0u);
-      const unsigned ub = (__vmaxu2(db, K) - K) & (yf ? cm.z : 0u);
+      const unsigned ub = (__vmaxu2(db, K) - K) & (yf ? cm.y : 0u);
       const unsigned word = __byte_perm(ua, ub, 0x6240);                   // x .. x + 3
       *reinterpret_cast<unsigned*>(umap + r * MSB + 4 * q) = word;
       *reinterpret_cast<unsigned*>(vmap + r * MSB + 4 * q) = word;
-      const bool yc = (unsigned)(r - 1) < (unsigned)ch && y >= b && y <= H - 1 - b;
-      unsigned ca = ua & (yc ? cm.y : 0u), cb = ub & (yc ? cm.w : 0u);
-      if (MASKED && (ca | cb)) {   // only in-cell pixels are read
-        const uint8_t* mr = mask + (long long)y * W + mx0 + 4 * q;
-        ca &= ((ca & 0xffffu) && mr[0] ? 0x0000ffffu : 0u) | ((ca >> 16) && mr[2] ? 0xffff0000u : 0u);
-        cb &= ((cb & 0xffffu) && mr[1] ? 0x0000ffffu : 0u) | ((cb >> 16) && mr[3] ? 0xffff0000u : 0u);
-      }
-      acc = __vmaxu2(acc, __vmaxu2(ca, cb));
+      acc = __vmaxu2(acc, __vmaxu2(ua, ub));
       q += dq;
       r += dr;
       if (q >= nq) {
@@ -478,7 +472,7 @@ __device__ __forceinline__ void detect_cell(const uint8_t* __restrict__ st, int 
   bool overflow = false;   // the queue lost scored pixels
   if (umax > 0) {
     int tp = 256;              // t_prev, above every shifted value
-    int t = max(umax - 16, 1);
+    int t = max(umax - 24, 1);
     const int n_words = MH * n8;
     const int dr8 = GT / n8, dc8 = GT - dr8 * n8;
     for (;;) {
@@ -607,7 +601,7 @@ __device__ __forceinline__ void detect_cell(const uint8_t* __restrict__ st, int 
       }
       if (n_found >= k || t <= 1) break;
       tp = t;
-      t = max(t - 16, 1);
+      t = max(t - 24, 1);
     }
   }
   // top k of the cell: each warp's best k, then the best k of those (or,

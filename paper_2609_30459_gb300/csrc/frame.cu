@@ -7,10 +7,10 @@
 //                           launch, the per-cell FAST/NMS top-k candidates of
 //                           camera 0. Levels beyond 4 follow as a further pass.
 //  KN frame_initnet_kernel  (only with the learned initializer) persistent
-//                           CTAs over tiles of 16 live tracks of both
-//                           cameras: network input from the previous and
-//                           current pyramids, forward pass on the tensor
-//                           cores -> flow proposal + confidence.
+//                           CTAs over rounds of 32 live tracks of one
+//                           camera: network input from the previous and
+//                           current pyramids, forward pass on the tcgen05
+//                           tensor cores -> flow proposal + confidence.
 //  K2 frame_track_kernel    one warp per keypoint: temporal tracking of every
 //                           live track of both cameras (previous -> current
 //                           pyramid; from the proposal over the lower levels
@@ -43,6 +43,7 @@
 #include "detect_dev.cuh"
 #include "frame.cuh"
 #include "initnet_dev.cuh"
+#include "initnet_tc.cuh"
 #include "pyramid_dev.cuh"
 #include "track_dev.cuh"
 
@@ -133,13 +134,14 @@ struct MultiK2 {
   FrameLaunch f[kMaxGroups];
 };
 
-// Flow proposals of every live track: persistent CTAs over tiles of TT
-// consecutive slots of one keypoint list (the temporal numbering of
+// Flow proposals of every live track: persistent CTAs over tiles of
+// ntc::ROUND consecutive slots of one keypoint list (the temporal numbering of
 // frame_track_kernel: list (2 stream + camera), slot); tiles past a list's
 // count are skipped whole.
 struct MultiKN {
   int n;
   long long block_end[kMaxGroups];   // in keypoint lists (2 per stream)
+  int32_t* fault;                    // VIO_ERR_TIMEOUT when a completion wait gave up
   FrameLaunch f[kMaxGroups];
 };
 
@@ -150,7 +152,7 @@ struct NetTile {
   long long in_list;
 };
 
-static_assert(KN_MAX_LISTS * 4 + net::TILE_SMEM <= 227 * 1024,
+static_assert(KN_MAX_LISTS * 4 + 64 + ntc::SMEM <= 227 * 1024,
               "shared memory of the proposal kernel");
 
 // Per-list tile counts, prefix-summed in shared memory (every CTA), so that
@@ -171,7 +173,7 @@ __device__ __forceinline__ int list_tiles(const MultiKN& mm, int li, int& gi, in
   if (!r.active || !r.have_prev) return 0;
   in_list = ((long long)r.li * f.n_streams + s) * 2 + c;
   const int count = min(f.list_count[in_list], f.cap);
-  return (count + net::TT - 1) / net::TT;
+  return (count + ntc::ROUND - 1) / ntc::ROUND;
 }
 
 __device__ __forceinline__ NetTile net_tile(const MultiKN& mm, const NetLists& L, int v) {
@@ -186,38 +188,66 @@ __device__ __forceinline__ NetTile net_tile(const MultiKN& mm, const NetLists& L
   const int j = v - (L.end[lo] - n_tiles);
   const FrameLaunch& f = mm.f[T.gi];
   const int count = min(f.list_count[T.in_list], f.cap);
-  T.s0 = j * net::TT;
-  T.nv = min(net::TT, count - T.s0);
+  T.s0 = j * ntc::ROUND;
+  T.nv = min(ntc::ROUND, count - T.s0);
   return T;
 }
 
-// This thread's rows of a tile: items e = threadIdx.x + k * TILE_THREADS
-// over (keypoint, channel, row).
-constexpr int KN_ROWS = net::TT * 64 / net::TILE_THREADS;
-
-__device__ __forceinline__ void net_prefetch(const MultiKN& mm, const NetTile& T,
-                                             net::RowWords (&R)[KN_ROWS]) {
-  const FrameLaunch& f = mm.f[T.gi];
-  const int c = T.list & 1;
-  const float* xy = f.list_xy + 2 * (T.in_list * f.cap + T.s0);
+// Network inputs of a launch's tiles for ntc::run: the thread's row of a
+// group, four channels (source / target at levels a and b) prefetched as
+// aligned words.
+struct KNSource {
+  const MultiKN* mm;
+  NetLists L;
+  int n_valid;
+  using Tile = NetTile;
+  struct Regs {
+    net::RowWords R[4];
+    bool live;
+  };
+  __device__ int n_tiles() const { return n_valid; }
+  __device__ Tile tile(int v) const { return net_tile(*mm, L, v); }
+  __device__ void load(const Tile& T, int g, Regs& R) const {
+    const FrameLaunch& f = mm->f[T.gi];
+    const int i = g * ntc::GROUP + (threadIdx.x >> 4), r = threadIdx.x & 15, c = T.list & 1;
+    R.live = i < T.nv;
+    if (!R.live) return;
+    const float* xy = f.list_xy + 2 * (T.in_list * f.cap + T.s0 + i);
 #pragma unroll
-  for (int k = 0; k < KN_ROWS; ++k) {
-    const int e = threadIdx.x + k * net::TILE_THREADS, kp = e >> 6, ch = (e >> 4) & 3;
-    if (kp < T.nv)
-      net::row_prefetch(R[k], f.g, (ch & 1) ? f.cur : f.prev,
-                        ((ch & 1) ? T.r.cur_img : T.r.prev_img) + c, ch < 2 ? f.net_la : f.net_lb,
-                        xy[2 * kp], xy[2 * kp + 1], e & 15);
+    for (int ch = 0; ch < 4; ++ch)
+      net::row_prefetch(R.R[ch], f.g, (ch & 1) ? f.cur : f.prev,
+                        ((ch & 1) ? T.r.cur_img : T.r.prev_img) + c,
+                        ch < 2 ? f.net_la : f.net_lb, xy[0], xy[1], r);
   }
-}
+  __device__ void store(uint8_t* sm, const Regs& R) const {
+    uint32_t px[4][4];
+#pragma unroll
+    for (int ch = 0; ch < 4; ++ch) {
+      if (R.live) {
+        ntc::row_bytes(R.R[ch], px[ch]);
+      } else {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) px[ch][k] = 0x80808080u;
+      }
+    }
+    ntc::store_row_bytes(sm, threadIdx.x >> 4, threadIdx.x & 15, px);
+  }
+  __device__ void write(const Tile& T, int s, float dx, float dy, float conf) const {
+    const FrameLaunch& f = mm->f[T.gi];
+    float* o = f.net_out + 3 * ((long long)T.list * f.cap + T.s0 + s);
+    o[0] = dx;
+    o[1] = dy;
+    o[2] = conf;
+  }
+};
 
 // Persistent CTAs over the tiles that hold keypoints (valid tile v goes to
-// CTA v mod gridDim.x); the input rows of the next tile are loaded into
-// registers while the current tile computes. Needs level_a, level_b >= 1.
-__global__ void __launch_bounds__(net::TILE_THREADS, 1) frame_initnet_kernel(
+// CTA v mod gridDim.x). Needs level_a, level_b >= 1 (aligned level rows).
+__global__ void __launch_bounds__(ntc::THREADS, 1) frame_initnet_kernel(
     const __grid_constant__ MultiKN mm) {
   extern __shared__ __align__(16) uint8_t sm[];
   __shared__ int ends[KN_MAX_LISTS];
-  int* warp_tot = reinterpret_cast<int*>(sm + net::T_X);   // before tile_setup uses it
+  __shared__ int warp_tot[ntc::THREADS / 32];
   const int n_lists = (int)mm.block_end[mm.n - 1];
   // per-list tile counts and their inclusive prefix (chunks of blockDim.x)
   int carry = 0;
@@ -243,68 +273,12 @@ __global__ void __launch_bounds__(net::TILE_THREADS, 1) frame_initnet_kernel(
     for (int w = 0; w < warp; ++w) before += warp_tot[w];
     if (li < n_lists) ends[li] = before + incl;
     int tot = 0;
-    for (int w = 0; w < net::TILE_WARPS; ++w) tot += warp_tot[w];
+    for (int w = 0; w < ntc::THREADS / 32; ++w) tot += warp_tot[w];
     carry += tot;
     __syncthreads();
   }
-  const NetLists L{n_lists, ends};
-  const int n_valid = carry;
-  int v = blockIdx.x;
-  if (v >= n_valid) return;
-  NetTile cur = net_tile(mm, L, v);
-  net::RowWords R[KN_ROWS];
-  net_prefetch(mm, cur, R);
-  net::tile_setup(net::packed(mm.f[0].net), sm);
-  const net::TileSmem S = net::tile_smem(sm);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  // the first tile's input; the rows of each later tile are stored while
-  // fc1 of the tile before it runs (S.x is free after conv3), and loaded
-  // into registers one tile ahead of that
-  net::tile_clear_input_border(S);
-#pragma unroll
-  for (int k = 0; k < KN_ROWS; ++k) {
-    const int e = threadIdx.x + k * net::TILE_THREADS;
-    if ((e >> 6) < cur.nv) net::row_store(R[k], S, e >> 6, (e >> 4) & 3, e & 15);
-  }
-  v += gridDim.x;
-  NetTile next{};
-  if (v < n_valid) {
-    next = net_tile(mm, L, v);
-    net_prefetch(mm, next, R);
-  }
-  __syncthreads();
-  while (true) {
-    net::tile_convs(S);
-    if (warp < 8) net::tile_fc1(S, warp, lane);
-    const bool more = v < n_valid;
-    if (more) {
-      net::tile_clear_input_border(S);
-#pragma unroll
-      for (int k = 0; k < KN_ROWS; ++k) {
-        const int e = threadIdx.x + k * net::TILE_THREADS;
-        if ((e >> 6) < next.nv) net::row_store(R[k], S, e >> 6, (e >> 4) & 3, e & 15);
-      }
-    }
-    __syncthreads();
-    // fc2 of this tile by warp 0, writing the proposals straight to the
-    // output, while the other warps go on with the next tile's conv1 (fc2
-    // reads only H4, which is rewritten after the next tile's conv3)
-    if (warp == 0) {
-      const FrameLaunch& f = mm.f[cur.gi];
-      float* o = f.net_out + 3 * ((long long)cur.list * f.cap + cur.s0);
-      const int nv = cur.nv;
-      net::tile_fc2(S, lane, [&](int row, int n, float val) {
-        if (row < nv) o[row * 3 + n] = val;
-      });
-    }
-    if (!more) break;
-    cur = next;
-    v += gridDim.x;
-    if (v < n_valid) {
-      next = net_tile(mm, L, v);
-      net_prefetch(mm, next, R);
-    }
-  }
+  const KNSource src{&mm, NetLists{n_lists, ends}, carry};
+  ntc::run(src, mm.f[0].net, sm, mm.fault);
 }
 
 // Occupancy hint of the tracking launch (blocks of up to 512 threads, this
@@ -394,7 +368,7 @@ __global__ void VIO_TRACK_BOUNDS frame_track_kernel(const __grid_constant__ Mult
   }
 }
 
-constexpr int K3_THREADS = 512;
+constexpr int K3_THREADS = 1024;
 
 // Block-wide exclusive scan (one value per thread); returns the exclusive
 // prefix and the block total. All threads must call it.
@@ -890,20 +864,21 @@ cudaError_t launch_frames(const FrameLaunch* fl, int n_groups, const FrameTune& 
     for (int i = 0; i < n_groups; ++i) {
       mn.f[i] = fl[i];
       acc += 2LL * fl[i].n_streams;
-      tiles += 2LL * fl[i].n_streams * ((fl[i].cap + net::TT - 1) / net::TT);
+      tiles += 2LL * fl[i].n_streams * ((fl[i].cap + ntc::ROUND - 1) / ntc::ROUND);
       mn.block_end[i] = acc;
     }
     if (acc > KN_MAX_LISTS) return cudaErrorInvalidValue;
     static PerDeviceOnce kn_attr;
     e = once_per_device(kn_attr, [] {
       return cudaFuncSetAttribute(frame_initnet_kernel,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, net::TILE_SMEM);
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, ntc::SMEM);
     });
     if (e != cudaSuccess) return e;
+    mn.fault = net_fault_word();
     const int sms = sm_count();
     const long long blocks = tiles < sms ? tiles : sms;
     if (blocks > 0)
-      frame_initnet_kernel<<<(unsigned)blocks, net::TILE_THREADS, net::TILE_SMEM, s>>>(mn);
+      frame_initnet_kernel<<<(unsigned)blocks, ntc::THREADS, ntc::SMEM, s>>>(mn);
   }
 
   // K2: temporal tracking + stereo matching of all candidates

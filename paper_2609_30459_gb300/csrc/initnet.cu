@@ -3,8 +3,9 @@
 //
 //  pack     FP32 master parameters -> BF16 [N][K] matrices + FP32 biases
 //  extract  network inputs of keypoints from two pyramids
-//  forward  persistent CTAs of 512 threads over tiles of 16 samples, layer
-//           by layer on the tensor cores (BF16 in, FP32 accumulate)
+//  forward  persistent CTAs of 128 threads over rounds of 32 samples, layer
+//           by layer on the tcgen05 tensor cores (initnet_tc.cuh: BF16
+//           operands in shared memory, FP32 accumulators in tensor memory)
 //  train    the forward pass of one sample per warp (same layers, BF16
 //           activations), then the backward pass in FP32 per warp, with
 //           the weight gradients summed in shared memory per CTA and added to
@@ -13,6 +14,7 @@
 #include <math.h>
 
 #include "initnet_dev.cuh"
+#include "initnet_tc.cuh"
 
 namespace vio {
 namespace {
@@ -94,35 +96,18 @@ __device__ __forceinline__ void load_input(const uint16_t* __restrict__ x, uint8
   __syncwarp();
 }
 
-// Tiled inference over n inputs ([n][4][16][16] BF16): persistent CTAs, TT
-// inputs per tile.
-__global__ void __launch_bounds__(TILE_THREADS, 1) forward_tile_kernel(
+// Status word of the tensor-core forward passes (VIO_ERR_TIMEOUT when one
+// gave up waiting for an MMA completion).
+__device__ int32_t g_net_fault;
+
+// Inference over n inputs ([n][4][16][16] BF16): persistent CTAs over rounds
+// of 32 samples.
+__global__ void __launch_bounds__(ntc::THREADS, 1) forward_tc_kernel(
     const void* __restrict__ packed_w, const uint16_t* __restrict__ x, int n,
-    float* __restrict__ out) {
+    float* __restrict__ out, int32_t* fault) {
   extern __shared__ __align__(16) uint8_t sm[];
-  tile_setup(packed(packed_w), sm);
-  const TileSmem S = tile_smem(sm);
-  const int n_tiles = (n + TT - 1) / TT;
-  for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-    const int s0 = tile * TT, nv = min(TT, n - s0);
-    tile_clear_input_border(S);
-    for (int e = threadIdx.x; e < nv * 64; e += blockDim.x) {   // (sample, channel, row)
-      const int sidx = e >> 6, ch = (e >> 4) & 3, r = e & 15;
-      const uint4* src = reinterpret_cast<const uint4*>(x + (long long)(s0 + sidx) * 1024 +
-                                                        ch * 256 + r * 16);
-      const uint4 lo = __ldg(src), hi = __ldg(src + 1);
-      const uint32_t wv[8] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
-      uint16_t* out = S.x + sidx * XR_SAMPLE + (r + 1) * X_ROW + X_PIX + ch;
-#pragma unroll
-      for (int c = 0; c < 8; ++c) {
-        out[(2 * c) * X_PIX] = (uint16_t)(wv[c] & 0xffffu);
-        out[(2 * c + 1) * X_PIX] = (uint16_t)(wv[c] >> 16);
-      }
-    }
-    __syncthreads();
-    tile_forward(S);
-    for (int i = threadIdx.x; i < nv * 3; i += blockDim.x) out[(long long)s0 * 3 + i] = S.out[i];
-  }
+  const ntc::XSource src{x, n, out};
+  ntc::run(src, packed_w, sm, fault);
 }
 
 constexpr int TRAIN_WARPS = 4;
@@ -305,6 +290,20 @@ __global__ void adam_kernel(float* __restrict__ w, const float* __restrict__ g,
 
 }  // namespace
 
+int32_t* net_fault_word() {
+  static int32_t* addr[64] = {};
+  static PerDeviceOnce once;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  once_per_device(once, [&] {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_net_fault);
+    addr[dev] = static_cast<int32_t*>(p);
+    return e;
+  });
+  return addr[dev];
+}
+
 int initnet_train_smem() {
   return ((N_MASTER * 4 + 127) & ~127) + TRAIN_WARPS * WARP_SMEM + TRAIN_WARPS * BW_FLOATS * 4;
 }
@@ -346,16 +345,29 @@ extern "C" vio_status vio_initnet_forward(const void* d_packed, const uint16_t* 
       ((uintptr_t)d_x & 15))
     return VIO_ERR_INVALID_ARG;
   if (n == 0) return VIO_OK;
-  if (cudaFuncSetAttribute(vio::forward_tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           TILE_SMEM) != cudaSuccess)
+  static vio::PerDeviceOnce attr;
+  if (vio::once_per_device(attr, [] {
+        return cudaFuncSetAttribute(vio::forward_tc_kernel,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, vio::ntc::SMEM);
+      }) != cudaSuccess)
     return VIO_ERR_CUDA;
-  int dev = 0, sms = 148;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int tiles = (n + TT - 1) / TT;
-  vio::forward_tile_kernel<<<tiles < sms ? tiles : sms, TILE_THREADS, TILE_SMEM,
-                             (cudaStream_t)stream>>>(d_packed, d_x, n, d_out);
+  const int rounds = (n + vio::ntc::ROUND - 1) / vio::ntc::ROUND, sms = vio::sm_count();
+  vio::forward_tc_kernel<<<rounds < sms ? rounds : sms, vio::ntc::THREADS, vio::ntc::SMEM,
+                           (cudaStream_t)stream>>>(d_packed, d_x, n, d_out,
+                                                   vio::net_fault_word());
   return cudaGetLastError() == cudaSuccess ? VIO_OK : VIO_ERR_CUDA;
+}
+
+extern "C" vio_status vio_initnet_fault(int32_t* status) {
+  if (!status) return VIO_ERR_INVALID_ARG;
+  int32_t* w = vio::net_fault_word();
+  if (!w) return VIO_ERR_CUDA;
+  int32_t v = 0;
+  if (cudaMemcpy(&v, w, sizeof(v), cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemset(w, 0, sizeof(v)) != cudaSuccess)
+    return VIO_ERR_CUDA;
+  *status = v;
+  return VIO_OK;
 }
 
 extern "C" vio_status vio_initnet_train_step(const void* d_packed, const uint16_t* d_x,

@@ -1,0 +1,459 @@
+// Forward pass of the flow initializer on the fifth-generation tensor cores
+// (tcgen05): every layer is a sum of M = 128-row MMAs with BF16 operands in
+// shared memory and the FP32 accumulator in tensor memory; the epilogues
+// (bias, ReLU, BF16) read the accumulator back and write the next layer's
+// operand. Same network and arithmetic as initnet_dev.cuh (BF16 weights and
+// activations, FP32 sums), in another summation order.
+//
+// A CTA of 128 threads (one per accumulator row) runs rounds of 32 samples:
+//
+//   conv1  per group of 8 samples: 4 tiles of 2 samples x 64 positions; a
+//          row's K = 3 tap rows x 16 (the 3 taps of a kernel row and a zero-
+//          weighted fourth, x 4 channels)                  -> 4 x 3 MMAs, N 32
+//   conv2  per group: 16 positions x 8 samples, K = 9 taps x 32 channels
+//                                                          -> 18 MMAs, N 32
+//   conv3  per round: 4 positions x 32 samples, K = 9 x 32 -> 18 MMAs, N 32
+//   fc1    per round: rows = the 32 samples (96 rows unused), K 128 -> 8, N 64
+//   fc2    per round: K 64, N 16 (3 used)                  -> 4 MMAs
+//
+// Stride-2 3x3 convolutions need no im2col: a layer's input is stored in
+// "phase maps", so that for every tap the 128 rows of the A operand sit at
+// one fixed stride (16 bytes) from a tap-dependent start. For a bordered input
+// map (border 1 = the zero padding) the output (i, j) reads pixel
+// (2i + u, 2j + v) for tap (u, v); pixels split by row parity pu = Y % 2 and
+// by column into three maps: even columns at X / 2 (tap v = 0), odd columns
+// at X / 2 (v = 1) and even columns at X / 2 - 1 (v = 2). In each map the
+// entry of output (i, j) for tap row u sits at map row i + u / 2 and column j,
+// so (row, column, sample) order makes the A rows of a tap contiguous.
+// conv1's input (4 channels, 8 bytes per pixel) pairs the pixels instead:
+// one 16-byte entry holds pixels X and X + 1, in an even-start map (taps 0,
+// 1) and a map shifted by two pixels (tap 2 and the unused X + 3).
+#pragma once
+#include "initnet_dev.cuh"
+#include "tc05.cuh"
+
+namespace vio {
+
+// Device address of the forward passes' status word (per device; null if the
+// lookup fails).
+int32_t* net_fault_word();
+
+namespace ntc {
+
+constexpr int THREADS = 128;
+constexpr int ROUND = 32;     // samples per round
+constexpr int GROUP = 8;      // samples per conv1/conv2 group
+
+// Shared memory (byte offsets). B operands: [K chunk][N group][8 rows][16 B].
+constexpr int W1_OFF = 0;                      // 3 tap rows x (N 32, K 16)
+constexpr int W2_OFF = W1_OFF + 3 * 1024;      // 9 taps x 2 K halves x (N 32, K 16)
+constexpr int W3_OFF = W2_OFF + 18 * 1024;
+constexpr int W4_OFF = W3_OFF + 18 * 1024;     // N 64, K 128 (K in position-major order)
+constexpr int W5_OFF = W4_OFF + 16 * 1024;     // N 16, K 64
+// conv1 input, per tile (2 samples): [pu 2][shift 2][row 9][col 8][sample 2][16 B]
+constexpr int P_OFF = W5_OFF + 2 * 1024;
+constexpr int P_MAP = 2304, P_TILE = 4 * P_MAP;
+// conv1 output = conv2 input: [map 6][K chunk 4][row 5][col 4][sample 8][16 B]
+constexpr int H1_OFF = P_OFF + 4 * P_TILE;
+constexpr int H1_CHUNK = 5 * 4 * 8 * 16, H1_MAP = 4 * H1_CHUNK;
+// conv2 output = conv3 input: [map 6][K chunk 4][row 3][col 2][sample 32][16 B]
+constexpr int H2_OFF = H1_OFF + 6 * H1_MAP;
+constexpr int H2_CHUNK = 3 * 2 * 32 * 16, H2_MAP = 4 * H2_CHUNK;
+// conv3 output and fc1 output (the A operands of fc1 and fc2) share conv1's
+// input region (free once a round's conv layers are done): [K chunk][row
+// group 4][8 rows][16 B], the 96 unused rows of the M = 128 MMA read the next
+// chunks (and 1.5 KB after the last one)
+constexpr int H3_OFF = P_OFF;
+constexpr int H4_OFF = P_OFF + 16 * 512 + 1536;
+constexpr int BIAS_OFF = H2_OFF + 6 * H2_MAP;
+constexpr int BAR_OFF = BIAS_OFF + net::N_BIAS * 4;
+constexpr int SLOT_OFF = BAR_OFF + 8;
+constexpr int SMEM = SLOT_OFF + 8;
+static_assert(H4_OFF + 8 * 512 + 1536 <= P_OFF + 4 * P_TILE, "fc operands inside conv1's input");
+static_assert(BAR_OFF % 8 == 0, "mbarrier alignment");
+
+// Tensor-memory columns of the accumulators.
+constexpr int C1 = 0, C2 = 128, C3 = 160, C4 = 192, C5 = 256, TMEM_COLS = 512;
+
+constexpr uint32_t ID_N16 = tc::idesc_bf16(128, 16);
+constexpr uint32_t ID_N32 = tc::idesc_bf16(128, 32);
+constexpr uint32_t ID_N64 = tc::idesc_bf16(128, 64);
+constexpr int kMaxPolls = 1 << 20;
+
+__device__ __forceinline__ int boff(int n, int k, int lbo) {   // B element (n, k)
+  return (k >> 3) * lbo + (n >> 3) * 128 + (n & 7) * 16 + (k & 7) * 2;
+}
+
+// Weights into their operand layouts, biases, zeros in both phase-map regions
+// (their border entries are never written again). Ends with a barrier.
+__device__ __forceinline__ void stage(const void* packed_w, uint8_t* sm) {
+  const net::Packed P = net::packed(packed_w);
+  const int tid = threadIdx.x, nt = blockDim.x;
+  uint4* z = reinterpret_cast<uint4*>(sm + H1_OFF);
+  for (int i = tid; i < (BIAS_OFF - H1_OFF) / 16; i += nt) z[i] = make_uint4(0u, 0u, 0u, 0u);
+  for (int e = tid; e < 3 * 32 * 16; e += nt) {
+    const int u = e >> 9, n = (e >> 4) & 31, k = e & 15;
+    const int v = 2 * (k >> 3) + ((k & 7) >> 2), c = k & 3;
+    const uint16_t w = v <= 2 ? P.w[net::OFF_W1 + n * net::K1 + c * 9 + u * 3 + v] : 0;
+    *reinterpret_cast<uint16_t*>(sm + W1_OFF + u * 1024 + boff(n, k, 512)) = w;
+  }
+  for (int e = tid; e < 2 * 18 * 32 * 16; e += nt) {
+    const int layer = e / (18 * 512), rem = e - layer * 18 * 512;
+    const int th = rem >> 9, n = (rem >> 4) & 31, k = rem & 15;
+    const int tap = th >> 1, h = th & 1;
+    const int src = (layer ? net::OFF_W3 : net::OFF_W2) + n * net::K2 + (16 * h + k) * 9 + tap;
+    *reinterpret_cast<uint16_t*>(sm + (layer ? W3_OFF : W2_OFF) + th * 1024 + boff(n, k, 512)) =
+        P.w[src];
+  }
+  for (int e = tid; e < 64 * 128; e += nt) {
+    const int n = e >> 7, kp = e & 127;          // kp = position * 32 + channel
+    const int k = (kp & 31) * 4 + (kp >> 5);     // flatten index (channel, row, col)
+    *reinterpret_cast<uint16_t*>(sm + W4_OFF + boff(n, kp, 1024)) =
+        P.w[net::OFF_W4 + n * net::K4 + k];
+  }
+  for (int e = tid; e < 16 * 64; e += nt) {
+    const int n = e >> 6, k = e & 63;
+    *reinterpret_cast<uint16_t*>(sm + W5_OFF + boff(n, k, 256)) =
+        n < net::N5 ? P.w[net::OFF_W5 + n * net::K5 + k] : (uint16_t)0;
+  }
+  float* b = reinterpret_cast<float*>(sm + BIAS_OFF);
+  for (int i = tid; i < net::N_BIAS; i += nt) b[i] = P.b[i];
+  __syncthreads();
+}
+
+// BF16 bits (high half of the result) of (byte k of w - 128) / 64, exact:
+// 2^23 + byte as a float, scaled and shifted by one rounding-free FMA.
+__device__ __forceinline__ uint32_t byte_bf(uint32_t w, uint32_t k) {
+  const float f = __uint_as_float(__byte_perm(w, 0x4B00u, 0x5440u | k));
+  return __float_as_uint(__fmaf_rn(f, 1.f / 64.f, -131074.f));
+}
+
+// conv1 operand entries of input row r (0..15) of group sample s: lo[x] and
+// hi[x] = the BF16 pairs (channels 0, 1) and (channels 2, 3) of pixel x.
+__device__ __forceinline__ void store_row(uint8_t* sm, int s, int r,
+                                          const uint32_t (&lo)[16], const uint32_t (&hi)[16]) {
+  const int Y = r + 1, pu = Y & 1, a = Y >> 1;
+  uint8_t* base = sm + P_OFF + (s >> 1) * P_TILE + (s & 1) * 16 + pu * 2 * P_MAP + a * 256;
+#pragma unroll
+  for (int q = 0; q <= 8; ++q) {        // pixels X = 2q, 2q + 1 (bordered) = x 2q - 1, 2q
+    const uint4 e = make_uint4(q > 0 ? lo[2 * q - 1] : 0u, q > 0 ? hi[2 * q - 1] : 0u,
+                               q < 8 ? lo[2 * q] : 0u, q < 8 ? hi[2 * q] : 0u);
+    if (q <= 7) *reinterpret_cast<uint4*>(base + q * 32) = e;
+    if (q >= 1) *reinterpret_cast<uint4*>(base + P_MAP + (q - 1) * 32) = e;
+  }
+}
+
+// The zero top rows (bordered row 0) of the four conv1 tiles: 128 entries,
+// one per thread (the region also holds the fc operands between rounds).
+__device__ __forceinline__ void store_top_rows(uint8_t* sm) {
+  const int e = threadIdx.x;   // tile, shift, col, sample
+  const int t = e >> 5, sh = (e >> 4) & 1, j = (e >> 1) & 7, s = e & 1;
+  *reinterpret_cast<uint4*>(sm + P_OFF + t * P_TILE + sh * P_MAP + j * 32 + s * 16) =
+      make_uint4(0u, 0u, 0u, 0u);
+}
+
+// Row r of group sample s from four rows of 16 bytes (channels 0..3, pixels
+// as bytes, 0x80 where outside the level).
+__device__ __forceinline__ void store_row_bytes(uint8_t* sm, int s, int r,
+                                                const uint32_t (&px)[4][4]) {
+  uint32_t lo[16], hi[16];
+#pragma unroll
+  for (int x = 0; x < 16; ++x) {
+    const uint32_t k = (uint32_t)(x & 3);
+    lo[x] = __byte_perm(byte_bf(px[0][x >> 2], k), byte_bf(px[1][x >> 2], k), 0x7632);
+    hi[x] = __byte_perm(byte_bf(px[2][x >> 2], k), byte_bf(px[3][x >> 2], k), 0x7632);
+  }
+  store_row(sm, s, r, lo, hi);
+}
+
+// Row r of group sample s from BF16 rows: v[ch][k] = pixels 2k, 2k + 1.
+__device__ __forceinline__ void store_row_bf16(uint8_t* sm, int s, int r,
+                                               const uint32_t (&v)[4][8]) {
+  uint32_t lo[16], hi[16];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    lo[2 * k] = __byte_perm(v[0][k], v[1][k], 0x5410);
+    lo[2 * k + 1] = __byte_perm(v[0][k], v[1][k], 0x7632);
+    hi[2 * k] = __byte_perm(v[2][k], v[3][k], 0x5410);
+    hi[2 * k + 1] = __byte_perm(v[2][k], v[3][k], 0x7632);
+  }
+  store_row(sm, s, r, lo, hi);
+}
+
+__device__ __forceinline__ uint32_t relu_bf2(float a, float b) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(fmaxf(a, 0.f), fmaxf(b, 0.f));
+  return *reinterpret_cast<const uint32_t*>(&h);
+}
+
+// 32 accumulator columns + bias, ReLU, BF16: four 16-byte chunks of 8 channels.
+__device__ __forceinline__ void act32(const float (&v)[32], const float* bias, uint4 (&q)[4]) {
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const int n = 8 * c;
+    q[c] = make_uint4(relu_bf2(v[n] + bias[n], v[n + 1] + bias[n + 1]),
+                      relu_bf2(v[n + 2] + bias[n + 2], v[n + 3] + bias[n + 3]),
+                      relu_bf2(v[n + 4] + bias[n + 4], v[n + 5] + bias[n + 5]),
+                      relu_bf2(v[n + 6] + bias[n + 6], v[n + 7] + bias[n + 7]));
+  }
+}
+
+// Writes pixel (Y, X) (bordered, interior) of a layer's output, four chunks
+// of 8 channels, into the next layer's phase maps (COLS columns and NS
+// samples per map row): odd X into the odd-column map, even X into the
+// even-column map (when inside it) and the map shifted by one column.
+template <int MAP, int CHUNK, int COLS, int NS>
+__device__ __forceinline__ void store_phase(uint8_t* region, int Y, int X, int s,
+                                            const uint4 (&q)[4]) {
+  const int half = X >> 1;
+  uint8_t* row = region + (Y & 1) * 3 * MAP + (Y >> 1) * COLS * NS * 16 + s * 16;
+  auto put = [&](int var, int col) {
+    uint8_t* p = row + var * MAP + col * NS * 16;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) *reinterpret_cast<uint4*>(p + c * CHUNK) = q[c];
+  };
+  if (X & 1) {
+    put(1, half);
+  } else {
+    if (half < COLS) put(0, half);
+    put(2, half - 1);
+  }
+}
+
+// Runs every round of a source on this CTA (rounds blockIdx.x, + gridDim.x,
+// ...). Src provides: Tile, Regs; n_tiles(); tile(v) (its sample count nv);
+// load(tile, g, regs): this thread's input row of group g into registers (row
+// threadIdx.x % 16 of group sample threadIdx.x / 16); store(sm, regs): that
+// row into conv1's operand; write(tile, s, dx, dy, conf). 128 threads. A
+// completion that does not come within the poll limit ends the kernel with
+// VIO_ERR_TIMEOUT in *fault (when not null), after a further bounded wait
+// for the MMAs in flight and with tensor memory freed.
+template <class Src>
+__device__ __forceinline__ void run(const Src& src, const void* packed_w, uint8_t* sm,
+                                    int32_t* fault) {
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int n_tiles = src.n_tiles();
+  int v = blockIdx.x;
+  if (v >= n_tiles) return;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sm + BAR_OFF);
+  uint32_t* slot = reinterpret_cast<uint32_t*>(sm + SLOT_OFF);
+  typename Src::Tile cur = src.tile(v), nxt = cur;
+  typename Src::Regs R;
+  src.load(cur, 0, R);
+  stage(packed_w, sm);
+  if (tid == 0) {
+    tc::mbar_init(bar, 1);
+    tc::fence_mbar_init();
+  }
+  if (warp == 0) tc::tmem_alloc(slot, TMEM_COLS);
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t tm = *slot;
+  const uint32_t sb = tc::smem_u32(sm);
+  const float* bias = reinterpret_cast<const float*>(sm + BIAS_OFF);
+  const int lane_q = 32 * warp;   // this warp's accumulator rows
+  uint32_t phase = 0;
+  bool failed = false;
+  // one layer: operands made visible to the tensor core, thread 0 issues the
+  // MMAs and commits, every thread waits for the completion
+  auto layer = [&](auto issue) -> bool {
+    tc::fence_smem_to_async();
+    tc::fence_before();
+    __syncthreads();
+    if (tid == 0) {
+      tc::fence_after();
+      issue();
+      tc::commit(bar);
+    }
+    const bool ok = tc::mbar_wait(bar, phase, kMaxPolls);
+    phase ^= 1u;
+    failed = __syncthreads_or(!ok) != 0;
+    tc::fence_after();
+    return !failed;
+  };
+  for (;;) {
+    const int ng = (cur.nv + GROUP - 1) / GROUP;
+    const int v_next = v + (int)gridDim.x;
+    for (int g = 0; g < ng; ++g) {
+      src.store(sm, R);
+      store_top_rows(sm);
+      if (g + 1 < ng) {
+        src.load(cur, g + 1, R);
+      } else if (v_next < n_tiles) {
+        nxt = src.tile(v_next);
+        src.load(nxt, 0, R);
+      }
+      if (!layer([&] {
+            for (int t = 0; t < 4; ++t)
+              for (int u = 0; u < 3; ++u)
+                tc::mma_bf16(tm + C1 + 32 * t,
+                             tc::sdesc(sb + P_OFF + t * P_TILE + (u & 1) * 2 * P_MAP +
+                                           (u >> 1) * 256, P_MAP, 128),
+                             tc::sdesc(sb + W1_OFF + u * 1024, 512, 128), ID_N32, u > 0);
+          }))
+        break;
+      {   // conv1 epilogue: row 32 warp + lane of tile t = (position p, sample)
+        const int r = 32 * warp + lane, p = r >> 1;
+#pragma unroll 1
+        for (int t = 0; t < 4; ++t) {
+          float a[32];
+          uint4 q[4];
+          tc::ld32(tc::taddr(tm, lane_q, C1 + 32 * t), a);
+          act32(a, bias + net::OFF_B1, q);
+          store_phase<H1_MAP, H1_CHUNK, 4, GROUP>(sm + H1_OFF, (p >> 3) + 1, (p & 7) + 1,
+                                                  2 * t + (r & 1), q);
+        }
+      }
+      if (!layer([&] {
+            for (int tap = 0; tap < 9; ++tap) {
+              const int u = tap / 3, m = (u & 1) * 3 + tap % 3;
+              for (int h = 0; h < 2; ++h)
+                tc::mma_bf16(tm + C2,
+                             tc::sdesc(sb + H1_OFF + m * H1_MAP + 2 * h * H1_CHUNK +
+                                           (u >> 1) * 512, H1_CHUNK, 128),
+                             tc::sdesc(sb + W2_OFF + (2 * tap + h) * 1024, 512, 128), ID_N32,
+                             (tap | h) != 0);
+            }
+          }))
+        break;
+      {   // conv2 epilogue: row = (position p, sample)
+        const int r = 32 * warp + lane, p = r >> 3;
+        float a[32];
+        uint4 q[4];
+        tc::ld32(tc::taddr(tm, lane_q, C2), a);
+        act32(a, bias + net::OFF_B2, q);
+        store_phase<H2_MAP, H2_CHUNK, 2, ROUND>(sm + H2_OFF, (p >> 2) + 1, (p & 3) + 1,
+                                                GROUP * g + (r & 7), q);
+      }
+    }
+    if (failed) break;
+    if (!layer([&] {
+          for (int tap = 0; tap < 9; ++tap) {
+            const int u = tap / 3, m = (u & 1) * 3 + tap % 3;
+            for (int h = 0; h < 2; ++h)
+              tc::mma_bf16(tm + C3,
+                           tc::sdesc(sb + H2_OFF + m * H2_MAP + 2 * h * H2_CHUNK +
+                                         (u >> 1) * 1024, H2_CHUNK, 128),
+                           tc::sdesc(sb + W3_OFF + (2 * tap + h) * 1024, 512, 128), ID_N32,
+                           (tap | h) != 0);
+          }
+        }))
+      break;
+    {   // conv3 epilogue: row = (position warp, sample lane) -> fc1 input at
+        // K = position * 32 + channel
+      float a[32];
+      uint4 q[4];
+      tc::ld32(tc::taddr(tm, lane_q, C3), a);
+      act32(a, bias + net::OFF_B3, q);
+      uint8_t* o = sm + H3_OFF + (lane >> 3) * 128 + (lane & 7) * 16;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) *reinterpret_cast<uint4*>(o + (4 * warp + c) * 512) = q[c];
+    }
+    if (!layer([&] {
+          for (int h = 0; h < 8; ++h)
+            tc::mma_bf16(tm + C4, tc::sdesc(sb + H3_OFF + 2 * h * 512, 512, 128),
+                         tc::sdesc(sb + W4_OFF + 2 * h * 1024, 1024, 128), ID_N64, h > 0);
+        }))
+      break;
+    if (warp == 0) {   // fc1 epilogue: rows 0..31 = the samples
+      uint8_t* o = sm + H4_OFF + (lane >> 3) * 128 + (lane & 7) * 16;
+#pragma unroll
+      for (int half = 0; half < 2; ++half) {
+        float a[32];
+        uint4 q[4];
+        tc::ld32(tc::taddr(tm, 0, C4 + 32 * half), a);
+        act32(a, bias + net::OFF_B4 + 32 * half, q);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) *reinterpret_cast<uint4*>(o + (4 * half + c) * 512) = q[c];
+      }
+    }
+    if (!layer([&] {
+          for (int h = 0; h < 4; ++h)
+            tc::mma_bf16(tm + C5, tc::sdesc(sb + H4_OFF + 2 * h * 512, 512, 128),
+                         tc::sdesc(sb + W5_OFF + 2 * h * 256, 256, 128), ID_N16, h > 0);
+        }))
+      break;
+    if (warp == 0) {
+      float a[16];
+      tc::ld16(tc::taddr(tm, 0, C5), a);
+      if (lane < cur.nv) {
+        const float o0 = a[0] + bias[net::OFF_B5], o1 = a[1] + bias[net::OFF_B5 + 1];
+        const float o2 = a[2] + bias[net::OFF_B5 + 2];
+        src.write(cur, lane, o0 * net::kScale, o1 * net::kScale, 1.f / (1.f + expf(-o2)));
+      }
+    }
+    if (v_next >= n_tiles) break;
+    cur = nxt;
+    v = v_next;
+  }
+  if (failed) {
+    if (tid == 0 && fault) atomicExch(fault, (int32_t)VIO_ERR_TIMEOUT);
+    tc::mbar_wait(bar, phase ^ 1u, kMaxPolls);
+  }
+  tc::fence_before();
+  __syncthreads();
+  if (warp == 0) tc::tmem_free(tm, TMEM_COLS);
+}
+
+// Source of rounds: inputs [n][4][16][16] BF16 in global memory, outputs
+// [n][3] (dx, dy, conf).
+struct XSource {
+  const uint16_t* x;
+  int n;
+  float* out;
+  struct Tile {
+    int s0, nv;
+  };
+  struct Regs {
+    uint32_t v[4][8];
+  };
+  __device__ int n_tiles() const { return (n + ROUND - 1) / ROUND; }
+  __device__ Tile tile(int t) const { return Tile{t * ROUND, min(ROUND, n - t * ROUND)}; }
+  __device__ void load(const Tile& T, int g, Regs& R) const {
+    const int i = g * GROUP + (threadIdx.x >> 4), r = threadIdx.x & 15;
+#pragma unroll
+    for (int ch = 0; ch < 4; ++ch) {
+      uint4 lo = make_uint4(0u, 0u, 0u, 0u), hi = lo;
+      if (i < T.nv) {
+        const uint4* p =
+            reinterpret_cast<const uint4*>(x + (long long)(T.s0 + i) * 1024 + ch * 256 + r * 16);
+        lo = __ldg(p);
+        hi = __ldg(p + 1);
+      }
+      R.v[ch][0] = lo.x;
+      R.v[ch][1] = lo.y;
+      R.v[ch][2] = lo.z;
+      R.v[ch][3] = lo.w;
+      R.v[ch][4] = hi.x;
+      R.v[ch][5] = hi.y;
+      R.v[ch][6] = hi.z;
+      R.v[ch][7] = hi.w;
+    }
+  }
+  __device__ void store(uint8_t* sm, const Regs& R) const {
+    store_row_bf16(sm, threadIdx.x >> 4, threadIdx.x & 15, R.v);
+  }
+  __device__ void write(const Tile& T, int s, float dx, float dy, float conf) const {
+    float* o = out + 3LL * (T.s0 + s);
+    o[0] = dx;
+    o[1] = dy;
+    o[2] = conf;
+  }
+};
+
+// The 16 bytes of a prefetched input row (net::RowWords), aligned to its
+// first pixel, 0x80 (input 0) where the pixel lies outside the level.
+__device__ __forceinline__ void row_bytes(const net::RowWords& R, uint32_t (&b)[4]) {
+  const unsigned sh = 8u * (unsigned)(R.cx - R.x4);
+  const int valid = R.wl - R.cx;   // pixels inside the level from the first
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const uint32_t a = __funnelshift_r(R.w[k], R.w[k + 1], sh);
+    const int vk = valid - 4 * k;
+    const uint32_t keep = vk >= 4 ? 0xffffffffu : (vk <= 0 ? 0u : (1u << (8 * vk)) - 1u);
+    b[k] = (a & keep) | (0x80808080u & ~keep);
+  }
+}
+
+}  // namespace ntc
+}  // namespace vio

@@ -244,6 +244,7 @@ _SIGS = {
                                              ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]),
     "vio_initnet_forward": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
                                              ctypes.c_void_p, ctypes.c_void_p]),
+    "vio_initnet_fault": (ctypes.c_int32, [ctypes.POINTER(ctypes.c_int32)]),
     "vio_initnet_train_step": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p,
                                                 ctypes.c_void_p, ctypes.c_void_p,
                                                 ctypes.c_int32, ctypes.c_float, ctypes.c_float,
@@ -530,6 +531,14 @@ def initnet_extract(pyr: Pyramids, src: PyrBatch, dst: PyrBatch, pts, count, cap
 def initnet_forward(packed, x, n, out, stream=None):
     _check(load().vio_initnet_forward(_ptr(packed), _ptr(x), n, _ptr(out), _stream(stream)),
            "vio_initnet_forward")
+
+
+def initnet_fault() -> int:
+    """vio_initnet_fault: the tensor-core forward passes' status word (VIO_OK
+    or VIO_ERR_TIMEOUT), read and cleared."""
+    v = ctypes.c_int32(0)
+    _check(load().vio_initnet_fault(ctypes.byref(v)), "vio_initnet_fault")
+    return int(v.value)
 
 
 def initnet_train_step(packed, x, flow, index, n, grad_scale, grad, loss, label_radius=1.0,

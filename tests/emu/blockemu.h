@@ -4,11 +4,13 @@
 // (__ballot_sync, __shfl*_sync, __reduce_max_sync, __syncwarp) are barriers
 // over the threads that must all reach them, so code that calls a full-mask
 // collective from divergent lanes stops with "EMU DEADLOCK" instead of
-// hanging. Integer intrinsics (__byte_perm, __vminu2, __vmaxu2, __popc, __ffs,
-// atomicMax) are plain host functions.
+// hanging; __syncthreads_or too. Integer and bit intrinsics (__byte_perm,
+// __vminu2, __vmaxu2, __popc, __ffs, __funnelshift_r, __fmaf_rn, atomicMax,
+// atomicExch) are plain host functions.
 #pragma once
 #include <cuda_runtime.h>
 #include <algorithm>
+#include <cmath>
 #include <condition_variable>
 #include <cstdint>
 #include <cstdio>
@@ -25,6 +27,7 @@ struct EmuDim { unsigned x = 0, y = 0, z = 0; };
 static thread_local EmuDim threadIdx;
 static EmuDim blockDim{128, 1, 1};
 static thread_local EmuDim blockIdx;
+static EmuDim gridDim{1, 1, 1};
 
 struct EmuBarrier {
   std::mutex m; std::condition_variable cv; int n, count = 0; long gen = 0;
@@ -43,12 +46,25 @@ struct EmuBlock {
   EmuBarrier block_bar;
   std::vector<std::unique_ptr<EmuWarp>> warps;
   std::mutex nm; std::map<int, std::unique_ptr<EmuBarrier>> named;
+  int or_acc[3] = {0, 0, 0};   // __syncthreads_or, rounds in turn
   explicit EmuBlock(int nt) : block_bar(nt) { for (int i = 0; i < nt / 32; ++i) warps.emplace_back(new EmuWarp); }
 };
 static thread_local EmuBlock* emu_blk = nullptr;
 inline EmuWarp& emu_warp() { return *emu_blk->warps[threadIdx.x >> 5]; }
 inline void __syncthreads() { emu_blk->block_bar.wait(); }
 inline void __syncwarp(unsigned = 0xffffffffu) { emu_warp().bar.wait(); }
+static thread_local int emu_or_round = 0;
+// Round k ORs into slot k % 3; after its barrier thread 0 clears the slot of
+// round k + 2, which no thread can reach before the barrier of round k + 1.
+inline int __syncthreads_or(int p) {
+  const int k = emu_or_round++ % 3;
+  { std::lock_guard<std::mutex> l(emu_blk->nm); emu_blk->or_acc[k] |= (p != 0); }
+  __syncthreads();
+  int r;
+  { std::lock_guard<std::mutex> l(emu_blk->nm); r = emu_blk->or_acc[k];
+    if (threadIdx.x == 0) emu_blk->or_acc[(k + 2) % 3] = 0; }
+  return r;
+}
 inline void emu_bar(int id, int n) {
   EmuBarrier* b;
   { std::lock_guard<std::mutex> l(emu_blk->nm);
@@ -108,6 +124,13 @@ inline unsigned __vminu2(unsigned a, unsigned b) {
 inline unsigned __vmaxu2(unsigned a, unsigned b) {
   unsigned lo = std::max(a & 0xffffu, b & 0xffffu), hi = std::max(a >> 16, b >> 16); return lo | (hi << 16); }
 template <class T> inline T __ldg(const T* p) { return *p; }
+inline float __uint_as_float(unsigned u) { float f; memcpy(&f, &u, 4); return f; }
+inline float __int_as_float(int u) { float f; memcpy(&f, &u, 4); return f; }
+inline unsigned __float_as_uint(float f) { unsigned u; memcpy(&u, &f, 4); return u; }
+inline float __fmaf_rn(float a, float b, float c) { return std::fma(a, b, c); }
+inline unsigned __funnelshift_r(unsigned lo, unsigned hi, unsigned sh) {
+  sh &= 31; return sh ? (lo >> sh) | (hi << (32 - sh)) : lo; }
+inline size_t __cvta_generic_to_shared(const void*) { fprintf(stderr, "cvta on the host\n"); std::abort(); }
 using std::min; using std::max;
 inline int min(int a, int b) { return a < b ? a : b; }
 inline int max(int a, int b) { return a > b ? a : b; }
@@ -126,5 +149,6 @@ inline void emu_run_block(int nt, const std::function<void()>& body, EmuDim bidx
   for (auto& x : th) x.join();
 }
 static std::mutex emu_atomic_mu;
+inline int atomicExch(int* p, int v) { std::lock_guard<std::mutex> l(emu_atomic_mu); int o = *p; *p = v; return o; }
 inline unsigned long long atomicMax(unsigned long long* p, unsigned long long v) {
   std::lock_guard<std::mutex> l(emu_atomic_mu); unsigned long long o = *p; if (v > o) *p = v; return o; }

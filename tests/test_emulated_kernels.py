@@ -1,33 +1,43 @@
-"""The pyramid and detection device code run on the host (no GPU) under
-AddressSanitizer, against the oracle: the check that stands in for a bounds
-checking build and for compute-sanitizer, which is closed on the GPU pool.
+"""The pyramid, detection and tensor-core network device code run on the
+host (no GPU) under AddressSanitizer, against the oracle: the check that
+stands in for a bounds checking build and for compute-sanitizer, which is
+closed on the GPU pool.
 
 tests/emu/blockemu.h emulates thread blocks with one host thread per CUDA
 thread and real barriers for __syncthreads, named barriers and the warp
 collectives; the harnesses give every CTA's shared memory a heap buffer of
 exactly its computed size (and the pyramid's launch size must cover every
 tile's plan), so any out-of-bounds shared or global access, any wrong
-keypoint or pyramid value, and any collective called from divergent lanes
-(a deadlock the emulator reports) fails the test. The device headers are
-compiled unchanged except for two host spellings: the named barrier's inline
-PTX becomes an emulated barrier, and a function-scope __shared__ variable a
-block-shared static (blocks run one at a time)."""
+keypoint, pyramid value or network output, and any collective called from
+divergent lanes (a deadlock the emulator reports) fails the test. The device
+headers are compiled unchanged except for two host spellings: the named
+barrier's inline PTX becomes an emulated barrier, and a function-scope
+__shared__ variable a block-shared static (blocks run one at a time). The
+network's tcgen05 primitives (tc05.cuh) are replaced by tests/emu/tc05_emu.h,
+which carries out each MMA through its decoded shared-memory descriptors (so
+the operand layouts of the kernel are what is checked) into an emulated
+tensor memory."""
 import os
 import re
 import shutil
 import subprocess
 
+import numpy as np
 import pytest
 
 import oracle
+from oracle import initnet as onet
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 CSRC = os.path.join(ROOT, "paper_2609_30459_gb300", "csrc")
 EMU = os.path.join(ROOT, "tests", "emu")
+PYR_DETECT = os.path.join(ROOT, "oracle", "src", "pyramid_detect.cpp")
 
 
 def _host_copy(dst):
-    for name in ("common.cuh", "pyramid_dev.cuh", "detect_dev.cuh"):
+    shutil.copy(os.path.join(EMU, "tc05_emu.h"), os.path.join(dst, "tc05.cuh"))
+    for name in ("common.cuh", "pyramid_dev.cuh", "detect_dev.cuh", "initnet_dev.cuh",
+                 "initnet_tc.cuh"):
         s = open(os.path.join(CSRC, name)).read()
         s = re.sub(r'asm volatile\("bar\.sync (\d), %0;" ::"r"\(n\) : "memory"\);',
                    r"emu_bar(\1, n);", s)
@@ -35,7 +45,7 @@ def _host_copy(dst):
         open(os.path.join(dst, name), "w").write(s)
 
 
-def _build(tmp_path, main):
+def _build(tmp_path, main, extra=()):
     gxx = shutil.which("g++")
     if gxx is None:
         pytest.skip("no g++")
@@ -47,7 +57,7 @@ def _build(tmp_path, main):
     cmd = [gxx, "-std=c++17", "-O1", "-g", "-fsanitize=address", "-pthread",
            "-I", str(tmp_path), "-I", EMU, "-I", cuda_inc, "-I", os.path.join(ROOT, "include"),
            "-I", os.path.join(ROOT, "oracle", "src"), "-o", exe, os.path.join(EMU, main + ".cpp"),
-           os.path.join(ROOT, "oracle", "src", "pyramid_detect.cpp")]
+           *extra]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0 and "sanitize" in r.stderr:
         pytest.skip("AddressSanitizer not available")
@@ -55,21 +65,70 @@ def _build(tmp_path, main):
     return exe
 
 
-def _run(exe, *args, timeout=600):
+def _run(exe, *args, timeout=600, expect="FAILS 0"):
     r = subprocess.run([exe, *map(str, args)], capture_output=True, text=True, timeout=timeout,
                        env={**os.environ, "ASAN_OPTIONS": "detect_leaks=0"})
     out = r.stdout + r.stderr
     assert r.returncode == 0, out[-4000:]
-    assert "FAILS 0" in out, out[-4000:]
+    if expect:
+        assert expect in out, out[-4000:]
     return out
 
 
 def test_pyramid_pass_on_host(tmp_path):
     oracle.build()
-    out = _run(_build(tmp_path, "pyr_check"))
+    out = _run(_build(tmp_path, "pyr_check", [PYR_DETECT]))
     assert re.search(r"cases (\d+)", out) and int(re.search(r"cases (\d+)", out).group(1)) > 30
 
 
 def test_detection_on_host(tmp_path):
     oracle.build()
-    _run(_build(tmp_path, "det_check"))
+    _run(_build(tmp_path, "det_check", [PYR_DETECT]))
+
+
+def _bf16_bits(a):
+    return (np.ascontiguousarray(onet.bf16_round(a), np.float32).view(np.uint32) >> 16
+            ).astype(np.uint16)
+
+
+def _packed(p):
+    """The packed weights of vio_initnet_pack: BF16 [N][K] rows (conv K =
+    c*9 + u*3 + v, conv1 padded to 48, fc2 to 8 rows), then 168 FP32 biases."""
+    w1 = np.zeros((32, 48))
+    w1[:, :36] = p["w1"].reshape(32, 36)
+    w5 = np.zeros((8, 64))
+    w5[:3] = p["w5"]
+    w = np.concatenate([_bf16_bits(m).reshape(-1) for m in
+                        (w1, p["w2"].reshape(32, 288), p["w3"].reshape(32, 288), p["w4"], w5)])
+    b = np.zeros(168, np.float32)
+    b[0:32], b[32:64], b[64:96], b[96:160], b[160:163] = p["b1"], p["b2"], p["b3"], p["b4"], p["b5"]
+    return w.tobytes() + b.tobytes()
+
+
+@pytest.mark.parametrize("n,blocks", [(70, 2), (32, 1)])
+def test_initnet_tc_forward_on_host(tmp_path, n, blocks):
+    """Rounds of 32 over a persistent grid (a ragged last round, a zero input)
+    against the FP64 oracle with BF16 activations, at the GPU test's bound."""
+    rng = np.random.default_rng(n)
+    fan = {"w1": 36, "w2": 288, "w3": 288, "w4": 128, "w5": 64}
+    p = {k: (rng.normal(0, np.sqrt(2.0 / fan[k]), onet.SHAPES[k]) if k.startswith("w")
+             else rng.normal(0, 0.05, onet.SHAPES[k])) for k in onet.ORDER}
+    p = onet.unflatten(onet.flatten(p).astype(np.float32).astype(np.float64))
+    x = (rng.integers(0, 256, (n, 4, 16, 16)).astype(np.float64) - 128) / 64
+    x[min(3, n - 1)] = 0
+    xb = (x.astype(np.float32).view(np.uint32) >> 16).astype(np.uint16)
+    inp, outp = tmp_path / "in.bin", tmp_path / "out.bin"
+    with open(inp, "wb") as f:
+        f.write(np.array([n, blocks], np.int32).tobytes())
+        f.write(_packed(p))
+        f.write(xb.tobytes())
+    _run(_build(tmp_path, "net_check"), inp, outp, expect=None)
+    got = np.fromfile(outp, np.float32).reshape(n, 3).astype(np.float64)
+    pb = {k: (onet.bf16_round(v) if k.startswith("w") else v) for k, v in p.items()}
+    o = np.array([onet.forward(pb, xi, act_bf16=True) for xi in x])
+    exp = np.stack([o[:, 0] * 16, o[:, 1] * 16, onet.sigmoid(o[:, 2])], 1)
+    err = np.abs(got - exp)
+    tol = 4e-3   # the GPU forward test's bound on the raw outputs (BF16 rounding flips)
+    assert np.all(err[:, :2] <= 16 * tol), err.max(0)
+    assert np.all(err[:, 2] <= tol / 4), err.max(0)
+    assert np.median(err[:, :2]) < 16 * 1e-4

@@ -152,6 +152,7 @@ def test_forward_matches_oracle(n):
     assert np.all(err[:, :2] <= 16 * O_TOL), err.max()
     assert np.all(err[:, 2] <= O_TOL / 4)
     assert np.median(err[:, :2]) < 16 * 1e-4
+    assert vio.initnet_fault() == 0           # no completion wait gave up
 
 
 def _kink_margin(p, x):
