@@ -209,7 +209,7 @@ struct KNSource {
   __device__ Tile tile(int v) const { return net_tile(*mm, L, v); }
   __device__ void load(const Tile& T, int g, Regs& R) const {
     const FrameLaunch& f = mm->f[T.gi];
-    const int i = g * ntc::GROUP + (threadIdx.x >> 4), r = threadIdx.x & 15, c = T.list & 1;
+    const int i = g * ntc::GROUP + (threadIdx.x & 7), r = threadIdx.x >> 3, c = T.list & 1;
     R.live = i < T.nv;
     if (!R.live) return;
     const float* xy = f.list_xy + 2 * (T.in_list * f.cap + T.s0 + i);
@@ -230,7 +230,7 @@ struct KNSource {
         for (int k = 0; k < 4; ++k) px[ch][k] = 0x80808080u;
       }
     }
-    ntc::store_row_bytes(sm, threadIdx.x >> 4, threadIdx.x & 15, px);
+    ntc::store_row_bytes(sm, threadIdx.x & 7, threadIdx.x >> 3, px);
   }
   __device__ void write(const Tile& T, int s, float dx, float dy, float conf) const {
     const FrameLaunch& f = mm->f[T.gi];

@@ -7,9 +7,9 @@
 //
 // A CTA of 128 threads (one per accumulator row) runs rounds of 32 samples:
 //
-//   conv1  per group of 8 samples: 4 tiles of 2 samples x 64 positions; a
-//          row's K = 3 tap rows x 16 (the 3 taps of a kernel row and a zero-
-//          weighted fourth, x 4 channels)                  -> 4 x 3 MMAs, N 32
+//   conv1  per group of 8 samples: 4 tiles of 16 positions (two output rows)
+//          x 8 samples; a row's K = 3 tap rows x 16 (the 3 taps of a kernel
+//          row and a zero-weighted fourth, x 4 channels)   -> 4 x 3 MMAs, N 32
 //   conv2  per group: 16 positions x 8 samples, K = 9 taps x 32 channels
 //                                                          -> 18 MMAs, N 32
 //   conv3  per round: 4 positions x 32 samples, K = 9 x 32 -> 18 MMAs, N 32
@@ -24,7 +24,9 @@
 // by column into three maps: even columns at X / 2 (tap v = 0), odd columns
 // at X / 2 (v = 1) and even columns at X / 2 - 1 (v = 2). In each map the
 // entry of output (i, j) for tap row u sits at map row i + u / 2 and column j,
-// so (row, column, sample) order makes the A rows of a tap contiguous.
+// so (row, column, sample) order makes the A rows of a tap contiguous. With
+// the sample as the fastest index, the 8 lanes of a 16-byte store phase (8
+// samples) write 8 different bank groups in every epilogue and input store.
 // conv1's input (4 channels, 8 bytes per pixel) pairs the pixels instead:
 // one 16-byte entry holds pixels X and X + 1, in an even-start map (taps 0,
 // 1) and a map shifted by two pixels (tap 2 and the unused X + 3).
@@ -50,11 +52,11 @@ constexpr int W2_OFF = W1_OFF + 3 * 1024;      // 9 taps x 2 K halves x (N 32, K
 constexpr int W3_OFF = W2_OFF + 18 * 1024;
 constexpr int W4_OFF = W3_OFF + 18 * 1024;     // N 64, K 128 (K in position-major order)
 constexpr int W5_OFF = W4_OFF + 16 * 1024;     // N 16, K 64
-// conv1 input, per tile (2 samples): [pu 2][shift 2][row 9][col 8][sample 2][16 B]
+// conv1 input: [pu 2][shift 2][row 9][col 8][sample 8][16 B]
 constexpr int P_OFF = W5_OFF + 2 * 1024;
-constexpr int P_MAP = 2304, P_TILE = 4 * P_MAP;
+constexpr int P_MAP = 9 * 8 * 8 * 16, P_ROW = 8 * 8 * 16;
 // conv1 output = conv2 input: [map 6][K chunk 4][row 5][col 4][sample 8][16 B]
-constexpr int H1_OFF = P_OFF + 4 * P_TILE;
+constexpr int H1_OFF = P_OFF + 4 * P_MAP;
 constexpr int H1_CHUNK = 5 * 4 * 8 * 16, H1_MAP = 4 * H1_CHUNK;
 // conv2 output = conv3 input: [map 6][K chunk 4][row 3][col 2][sample 32][16 B]
 constexpr int H2_OFF = H1_OFF + 6 * H1_MAP;
@@ -69,7 +71,7 @@ constexpr int BIAS_OFF = H2_OFF + 6 * H2_MAP;
 constexpr int BAR_OFF = BIAS_OFF + net::N_BIAS * 4;
 constexpr int SLOT_OFF = BAR_OFF + 8;
 constexpr int SMEM = SLOT_OFF + 8;
-static_assert(H4_OFF + 8 * 512 + 1536 <= P_OFF + 4 * P_TILE, "fc operands inside conv1's input");
+static_assert(H4_OFF + 8 * 512 + 1536 <= P_OFF + 4 * P_MAP, "fc operands inside conv1's input");
 static_assert(BAR_OFF % 8 == 0, "mbarrier alignment");
 
 // Tensor-memory columns of the accumulators.
@@ -133,22 +135,21 @@ __device__ __forceinline__ uint32_t byte_bf(uint32_t w, uint32_t k) {
 __device__ __forceinline__ void store_row(uint8_t* sm, int s, int r,
                                           const uint32_t (&lo)[16], const uint32_t (&hi)[16]) {
   const int Y = r + 1, pu = Y & 1, a = Y >> 1;
-  uint8_t* base = sm + P_OFF + (s >> 1) * P_TILE + (s & 1) * 16 + pu * 2 * P_MAP + a * 256;
+  uint8_t* base = sm + P_OFF + pu * 2 * P_MAP + a * P_ROW + s * 16;
 #pragma unroll
   for (int q = 0; q <= 8; ++q) {        // pixels X = 2q, 2q + 1 (bordered) = x 2q - 1, 2q
     const uint4 e = make_uint4(q > 0 ? lo[2 * q - 1] : 0u, q > 0 ? hi[2 * q - 1] : 0u,
                                q < 8 ? lo[2 * q] : 0u, q < 8 ? hi[2 * q] : 0u);
-    if (q <= 7) *reinterpret_cast<uint4*>(base + q * 32) = e;
-    if (q >= 1) *reinterpret_cast<uint4*>(base + P_MAP + (q - 1) * 32) = e;
+    if (q <= 7) *reinterpret_cast<uint4*>(base + q * 128) = e;
+    if (q >= 1) *reinterpret_cast<uint4*>(base + P_MAP + (q - 1) * 128) = e;
   }
 }
 
-// The zero top rows (bordered row 0) of the four conv1 tiles: 128 entries,
-// one per thread (the region also holds the fc operands between rounds).
+// The zero top row (bordered row 0) of conv1's input: 128 entries, one per
+// thread (the region also holds the fc operands between rounds).
 __device__ __forceinline__ void store_top_rows(uint8_t* sm) {
-  const int e = threadIdx.x;   // tile, shift, col, sample
-  const int t = e >> 5, sh = (e >> 4) & 1, j = (e >> 1) & 7, s = e & 1;
-  *reinterpret_cast<uint4*>(sm + P_OFF + t * P_TILE + sh * P_MAP + j * 32 + s * 16) =
+  const int e = threadIdx.x;   // shift, col, sample
+  *reinterpret_cast<uint4*>(sm + P_OFF + (e >> 6) * P_MAP + (e & 63) * 16) =
       make_uint4(0u, 0u, 0u, 0u);
 }
 
@@ -222,7 +223,7 @@ __device__ __forceinline__ void store_phase(uint8_t* region, int Y, int X, int s
 // Runs every round of a source on this CTA (rounds blockIdx.x, + gridDim.x,
 // ...). Src provides: Tile, Regs; n_tiles(); tile(v) (its sample count nv);
 // load(tile, g, regs): this thread's input row of group g into registers (row
-// threadIdx.x % 16 of group sample threadIdx.x / 16); store(sm, regs): that
+// threadIdx.x / 8 of group sample threadIdx.x % 8); store(sm, regs): that
 // row into conv1's operand; write(tile, s, dx, dy, conf). 128 threads. A
 // completion that does not come within the poll limit ends the kernel with
 // VIO_ERR_TIMEOUT in *fault (when not null), after a further bounded wait
@@ -287,21 +288,22 @@ __device__ __forceinline__ void run(const Src& src, const void* packed_w, uint8_
             for (int t = 0; t < 4; ++t)
               for (int u = 0; u < 3; ++u)
                 tc::mma_bf16(tm + C1 + 32 * t,
-                             tc::sdesc(sb + P_OFF + t * P_TILE + (u & 1) * 2 * P_MAP +
-                                           (u >> 1) * 256, P_MAP, 128),
+                             tc::sdesc(sb + P_OFF + (u & 1) * 2 * P_MAP +
+                                           (2 * t + (u >> 1)) * P_ROW, P_MAP, 128),
                              tc::sdesc(sb + W1_OFF + u * 1024, 512, 128), ID_N32, u > 0);
           }))
         break;
-      {   // conv1 epilogue: row 32 warp + lane of tile t = (position p, sample)
-        const int r = 32 * warp + lane, p = r >> 1;
+      {   // conv1 epilogue: row 32 warp + lane of tile t = (position p of output
+          // rows 2t, 2t + 1, sample)
+        const int r = 32 * warp + lane, p = r >> 3;
 #pragma unroll 1
         for (int t = 0; t < 4; ++t) {
           float a[32];
           uint4 q[4];
           tc::ld32(tc::taddr(tm, lane_q, C1 + 32 * t), a);
           act32(a, bias + net::OFF_B1, q);
-          store_phase<H1_MAP, H1_CHUNK, 4, GROUP>(sm + H1_OFF, (p >> 3) + 1, (p & 7) + 1,
-                                                  2 * t + (r & 1), q);
+          store_phase<H1_MAP, H1_CHUNK, 4, GROUP>(sm + H1_OFF, 2 * t + (p >> 3) + 1,
+                                                  (p & 7) + 1, r & 7, q);
         }
       }
       if (!layer([&] {
@@ -410,7 +412,7 @@ struct XSource {
   __device__ int n_tiles() const { return (n + ROUND - 1) / ROUND; }
   __device__ Tile tile(int t) const { return Tile{t * ROUND, min(ROUND, n - t * ROUND)}; }
   __device__ void load(const Tile& T, int g, Regs& R) const {
-    const int i = g * GROUP + (threadIdx.x >> 4), r = threadIdx.x & 15;
+    const int i = g * GROUP + (threadIdx.x & 7), r = threadIdx.x >> 3;
 #pragma unroll
     for (int ch = 0; ch < 4; ++ch) {
       uint4 lo = make_uint4(0u, 0u, 0u, 0u), hi = lo;
@@ -431,7 +433,7 @@ struct XSource {
     }
   }
   __device__ void store(uint8_t* sm, const Regs& R) const {
-    store_row_bf16(sm, threadIdx.x >> 4, threadIdx.x & 15, R.v);
+    store_row_bf16(sm, threadIdx.x & 7, threadIdx.x >> 3, R.v);
   }
   __device__ void write(const Tile& T, int s, float dx, float dy, float conf) const {
     float* o = out + 3LL * (T.s0 + s);
