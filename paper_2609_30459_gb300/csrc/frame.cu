@@ -209,7 +209,7 @@ struct KNSource {
   __device__ Tile tile(int v) const { return net_tile(*mm, L, v); }
   __device__ void load(const Tile& T, int g, Regs& R) const {
     const FrameLaunch& f = mm->f[T.gi];
-    const int i = g * ntc::GROUP + (threadIdx.x & 7), r = threadIdx.x >> 3, c = T.list & 1;
+    const int i = g * ntc::GROUP + ntc::item_sample(), r = ntc::item_row(), c = T.list & 1;
     R.live = i < T.nv;
     if (!R.live) return;
     const float* xy = f.list_xy + 2 * (T.in_list * f.cap + T.s0 + i);
@@ -230,7 +230,10 @@ struct KNSource {
         for (int k = 0; k < 4; ++k) px[ch][k] = 0x80808080u;
       }
     }
-    ntc::store_row_bytes(sm, threadIdx.x & 7, threadIdx.x >> 3, px);
+    if (threadIdx.x >> 7)
+      ntc::store_row_bytes<1>(sm, ntc::item_sample(), ntc::item_row(), px);
+    else
+      ntc::store_row_bytes<0>(sm, ntc::item_sample(), ntc::item_row(), px);
   }
   __device__ void write(const Tile& T, int s, float dx, float dy, float conf) const {
     const FrameLaunch& f = mm->f[T.gi];

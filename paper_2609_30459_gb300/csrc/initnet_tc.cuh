@@ -5,7 +5,7 @@
 // operand. Same network and arithmetic as initnet_dev.cuh (BF16 weights and
 // activations, FP32 sums), in another summation order.
 //
-// A CTA of 128 threads (one per accumulator row) runs rounds of 32 samples:
+// A CTA of 256 threads (two per accumulator row) runs rounds of 32 samples:
 //
 //   conv1  per group of 8 samples: 4 tiles of 16 positions (two output rows)
 //          x 8 samples; a row's K = 3 tap rows x 16 (the 3 taps of a kernel
@@ -42,7 +42,7 @@ int32_t* net_fault_word();
 
 namespace ntc {
 
-constexpr int THREADS = 128;
+constexpr int THREADS = 256;
 constexpr int ROUND = 32;     // samples per round
 constexpr int GROUP = 8;      // samples per conv1/conv2 group
 
@@ -69,7 +69,7 @@ constexpr int H3_OFF = P_OFF;
 constexpr int H4_OFF = P_OFF + 16 * 512 + 1536;
 constexpr int BIAS_OFF = H2_OFF + 6 * H2_MAP;
 constexpr int BAR_OFF = BIAS_OFF + net::N_BIAS * 4;
-constexpr int SLOT_OFF = BAR_OFF + 8;
+constexpr int SLOT_OFF = BAR_OFF + 16;   // two mbarriers
 constexpr int SMEM = SLOT_OFF + 8;
 static_assert(H4_OFF + 8 * 512 + 1536 <= P_OFF + 4 * P_MAP, "fc operands inside conv1's input");
 static_assert(BAR_OFF % 8 == 0, "mbarrier alignment");
@@ -130,14 +130,17 @@ __device__ __forceinline__ uint32_t byte_bf(uint32_t w, uint32_t k) {
   return __float_as_uint(__fmaf_rn(f, 1.f / 64.f, -131074.f));
 }
 
-// conv1 operand entries of input row r (0..15) of group sample s: lo[x] and
-// hi[x] = the BF16 pairs (channels 0, 1) and (channels 2, 3) of pixel x.
-__device__ __forceinline__ void store_row(uint8_t* sm, int s, int r,
-                                          const uint32_t (&lo)[16], const uint32_t (&hi)[16]) {
+// Half H of the conv1 operand entries of input row r (0..15) of group sample
+// s (entries q = 0..4, or 5..8, of pixel pairs X = 2q, 2q + 1 of the bordered
+// row): lo[x] and hi[x] = the BF16 pairs (channels 0, 1) and (channels 2, 3)
+// of pixel x, read for x = 2q - 1 and 2q inside 0..15 only.
+template <int H>
+__device__ __forceinline__ void store_row(uint8_t* sm, int s, int r, const uint32_t (&lo)[16],
+                                          const uint32_t (&hi)[16]) {
   const int Y = r + 1, pu = Y & 1, a = Y >> 1;
   uint8_t* base = sm + P_OFF + pu * 2 * P_MAP + a * P_ROW + s * 16;
 #pragma unroll
-  for (int q = 0; q <= 8; ++q) {        // pixels X = 2q, 2q + 1 (bordered) = x 2q - 1, 2q
+  for (int q = H ? 5 : 0; q < (H ? 9 : 5); ++q) {
     const uint4 e = make_uint4(q > 0 ? lo[2 * q - 1] : 0u, q > 0 ? hi[2 * q - 1] : 0u,
                                q < 8 ? lo[2 * q] : 0u, q < 8 ? hi[2 * q] : 0u);
     if (q <= 7) *reinterpret_cast<uint4*>(base + q * 128) = e;
@@ -146,28 +149,37 @@ __device__ __forceinline__ void store_row(uint8_t* sm, int s, int r,
 }
 
 // The zero top row (bordered row 0) of conv1's input: 128 entries, one per
-// thread (the region also holds the fc operands between rounds).
+// thread of the first 128 (the region also holds the fc operands between
+// rounds).
 __device__ __forceinline__ void store_top_rows(uint8_t* sm) {
   const int e = threadIdx.x;   // shift, col, sample
-  *reinterpret_cast<uint4*>(sm + P_OFF + (e >> 6) * P_MAP + (e & 63) * 16) =
-      make_uint4(0u, 0u, 0u, 0u);
+  if (e < 128)
+    *reinterpret_cast<uint4*>(sm + P_OFF + (e >> 6) * P_MAP + (e & 63) * 16) =
+        make_uint4(0u, 0u, 0u, 0u);
 }
 
-// Row r of group sample s from four rows of 16 bytes (channels 0..3, pixels
-// as bytes, 0x80 where outside the level).
+// This thread's input item: group sample s = tid % 8 (the 8 lanes of a store
+// phase are 8 samples), row r = (tid / 8) % 16, half of the row tid / 128.
+__device__ __forceinline__ int item_sample() { return threadIdx.x & 7; }
+__device__ __forceinline__ int item_row() { return (threadIdx.x >> 3) & 15; }
+
+// Half H of row r of group sample s from four rows of 16 bytes (channels
+// 0..3, pixels as bytes, 0x80 where outside the level).
+template <int H>
 __device__ __forceinline__ void store_row_bytes(uint8_t* sm, int s, int r,
                                                 const uint32_t (&px)[4][4]) {
   uint32_t lo[16], hi[16];
 #pragma unroll
-  for (int x = 0; x < 16; ++x) {
+  for (int x = H ? 9 : 0; x < (H ? 16 : 9); ++x) {
     const uint32_t k = (uint32_t)(x & 3);
     lo[x] = __byte_perm(byte_bf(px[0][x >> 2], k), byte_bf(px[1][x >> 2], k), 0x7632);
     hi[x] = __byte_perm(byte_bf(px[2][x >> 2], k), byte_bf(px[3][x >> 2], k), 0x7632);
   }
-  store_row(sm, s, r, lo, hi);
+  store_row<H>(sm, s, r, lo, hi);
 }
 
-// Row r of group sample s from BF16 rows: v[ch][k] = pixels 2k, 2k + 1.
+// Half H of row r of group sample s from BF16 rows: v[ch][k] = pixels 2k, 2k + 1.
+template <int H>
 __device__ __forceinline__ void store_row_bf16(uint8_t* sm, int s, int r,
                                                const uint32_t (&v)[4][8]) {
   uint32_t lo[16], hi[16];
@@ -178,7 +190,7 @@ __device__ __forceinline__ void store_row_bf16(uint8_t* sm, int s, int r,
     hi[2 * k] = __byte_perm(v[2][k], v[3][k], 0x5410);
     hi[2 * k + 1] = __byte_perm(v[2][k], v[3][k], 0x7632);
   }
-  store_row(sm, s, r, lo, hi);
+  store_row<H>(sm, s, r, lo, hi);
 }
 
 __device__ __forceinline__ uint32_t relu_bf2(float a, float b) {
@@ -186,10 +198,11 @@ __device__ __forceinline__ uint32_t relu_bf2(float a, float b) {
   return *reinterpret_cast<const uint32_t*>(&h);
 }
 
-// 32 accumulator columns + bias, ReLU, BF16: four 16-byte chunks of 8 channels.
-__device__ __forceinline__ void act32(const float (&v)[32], const float* bias, uint4 (&q)[4]) {
+// NC chunks of 8 accumulator columns + bias, ReLU, BF16.
+template <int NC>
+__device__ __forceinline__ void act(const float* v, const float* bias, uint4 (&q)[NC]) {
 #pragma unroll
-  for (int c = 0; c < 4; ++c) {
+  for (int c = 0; c < NC; ++c) {
     const int n = 8 * c;
     q[c] = make_uint4(relu_bf2(v[n] + bias[n], v[n + 1] + bias[n + 1]),
                       relu_bf2(v[n + 2] + bias[n + 2], v[n + 3] + bias[n + 3]),
@@ -198,19 +211,20 @@ __device__ __forceinline__ void act32(const float (&v)[32], const float* bias, u
   }
 }
 
-// Writes pixel (Y, X) (bordered, interior) of a layer's output, four chunks
-// of 8 channels, into the next layer's phase maps (COLS columns and NS
-// samples per map row): odd X into the odd-column map, even X into the
-// even-column map (when inside it) and the map shifted by one column.
-template <int MAP, int CHUNK, int COLS, int NS>
-__device__ __forceinline__ void store_phase(uint8_t* region, int Y, int X, int s,
-                                            const uint4 (&q)[4]) {
+// Writes chunks c0 .. c0 + NC - 1 (8 channels each) of pixel (Y, X)
+// (bordered, interior) of a layer's output into the next layer's phase maps
+// (COLS columns and NS samples per map row): odd X into the odd-column map,
+// even X into the even-column map (when inside it) and the map shifted by
+// one column.
+template <int MAP, int CHUNK, int COLS, int NS, int NC>
+__device__ __forceinline__ void store_phase(uint8_t* region, int Y, int X, int s, int c0,
+                                            const uint4 (&q)[NC]) {
   const int half = X >> 1;
-  uint8_t* row = region + (Y & 1) * 3 * MAP + (Y >> 1) * COLS * NS * 16 + s * 16;
+  uint8_t* row = region + (Y & 1) * 3 * MAP + (Y >> 1) * COLS * NS * 16 + s * 16 + c0 * CHUNK;
   auto put = [&](int var, int col) {
     uint8_t* p = row + var * MAP + col * NS * 16;
 #pragma unroll
-    for (int c = 0; c < 4; ++c) *reinterpret_cast<uint4*>(p + c * CHUNK) = q[c];
+    for (int c = 0; c < NC; ++c) *reinterpret_cast<uint4*>(p + c * CHUNK) = q[c];
   };
   if (X & 1) {
     put(1, half);
@@ -222,27 +236,37 @@ __device__ __forceinline__ void store_phase(uint8_t* region, int Y, int X, int s
 
 // Runs every round of a source on this CTA (rounds blockIdx.x, + gridDim.x,
 // ...). Src provides: Tile, Regs; n_tiles(); tile(v) (its sample count nv);
-// load(tile, g, regs): this thread's input row of group g into registers (row
-// threadIdx.x / 8 of group sample threadIdx.x % 8); store(sm, regs): that
-// row into conv1's operand; write(tile, s, dx, dy, conf). 128 threads. A
-// completion that does not come within the poll limit ends the kernel with
-// VIO_ERR_TIMEOUT in *fault (when not null), after a further bounded wait
-// for the MMAs in flight and with tensor memory freed.
+// load(tile, g, regs): this thread's input item of group g into registers
+// (item_sample(), item_row()); store(sm, regs): that item into conv1's
+// operand; write(tile, s, dx, dy, conf). THREADS threads: warp w reads the
+// accumulator lanes of quarter w % 4, its half w / 4 of the columns (or of
+// conv1's tiles).
+//
+// Per group g the MMAs overlap CUDA-core work: conv1(g) runs while the
+// epilogue of conv2(g - 1) drains, and conv2(g) while group g + 1's input is
+// stored; conv1 and the per-round layers complete on one mbarrier, conv2 on
+// the other, each with at most one commit outstanding. A completion that does
+// not come within the poll limit ends the kernel with VIO_ERR_TIMEOUT in
+// *fault (when not null), after a further bounded wait for the MMAs in flight
+// and with tensor memory freed.
 template <class Src>
 __device__ __forceinline__ void run(const Src& src, const void* packed_w, uint8_t* sm,
                                     int32_t* fault) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int quarter = 32 * (warp & 3), hw = warp >> 2;
   const int n_tiles = src.n_tiles();
   int v = blockIdx.x;
   if (v >= n_tiles) return;
-  uint64_t* bar = reinterpret_cast<uint64_t*>(sm + BAR_OFF);
+  uint64_t* bar1 = reinterpret_cast<uint64_t*>(sm + BAR_OFF);
+  uint64_t* bar2 = bar1 + 1;
   uint32_t* slot = reinterpret_cast<uint32_t*>(sm + SLOT_OFF);
   typename Src::Tile cur = src.tile(v), nxt = cur;
   typename Src::Regs R;
   src.load(cur, 0, R);
   stage(packed_w, sm);
   if (tid == 0) {
-    tc::mbar_init(bar, 1);
+    tc::mbar_init(bar1, 1);
+    tc::mbar_init(bar2, 1);
     tc::fence_mbar_init();
   }
   if (warp == 0) tc::tmem_alloc(slot, TMEM_COLS);
@@ -252,129 +276,156 @@ __device__ __forceinline__ void run(const Src& src, const void* packed_w, uint8_
   const uint32_t tm = *slot;
   const uint32_t sb = tc::smem_u32(sm);
   const float* bias = reinterpret_cast<const float*>(sm + BIAS_OFF);
-  const int lane_q = 32 * warp;   // this warp's accumulator rows
-  uint32_t phase = 0;
-  bool failed = false;
-  // one layer: operands made visible to the tensor core, thread 0 issues the
-  // MMAs and commits, every thread waits for the completion
-  auto layer = [&](auto issue) -> bool {
+  uint32_t ph1 = 0, ph2 = 0;
+  bool pend1 = false, pend2 = false, failed = false;
+  // operands made visible to the tensor core, thread 0 issues and commits
+  auto issue = [&](uint64_t* b, auto body) {
     tc::fence_smem_to_async();
     tc::fence_before();
     __syncthreads();
     if (tid == 0) {
       tc::fence_after();
-      issue();
-      tc::commit(bar);
+      body();
+      tc::commit(b);
     }
-    const bool ok = tc::mbar_wait(bar, phase, kMaxPolls);
-    phase ^= 1u;
+  };
+  auto wait = [&](uint64_t* b, uint32_t& ph, bool& pend) -> bool {
+    const bool ok = tc::mbar_wait(b, ph, kMaxPolls);
+    if (ok) {
+      ph ^= 1u;
+      pend = false;
+    }
     failed = __syncthreads_or(!ok) != 0;
     tc::fence_after();
     return !failed;
   };
+  auto conv1 = [&] {
+    for (int t = 0; t < 4; ++t)
+      for (int u = 0; u < 3; ++u)
+        tc::mma_bf16(tm + C1 + 32 * t,
+                     tc::sdesc(sb + P_OFF + (u & 1) * 2 * P_MAP + (2 * t + (u >> 1)) * P_ROW,
+                               P_MAP, 128),
+                     tc::sdesc(sb + W1_OFF + u * 1024, 512, 128), ID_N32, u > 0);
+  };
+  auto conv2 = [&] {
+    for (int tap = 0; tap < 9; ++tap) {
+      const int u = tap / 3, m = (u & 1) * 3 + tap % 3;
+      for (int h = 0; h < 2; ++h)
+        tc::mma_bf16(tm + C2,
+                     tc::sdesc(sb + H1_OFF + m * H1_MAP + 2 * h * H1_CHUNK + (u >> 1) * 512,
+                               H1_CHUNK, 128),
+                     tc::sdesc(sb + W2_OFF + (2 * tap + h) * 1024, 512, 128), ID_N32,
+                     (tap | h) != 0);
+    }
+  };
+  // conv2's epilogue of group g: row (position p, sample), this warp's 16
+  // channels -> conv3's phase maps
+  auto epi2 = [&](int g) {
+    const int r = quarter + lane, p = r >> 3;
+    float a[16];
+    uint4 q[2];
+    tc::ld16(tc::taddr(tm, quarter, C2 + 16 * hw), a);
+    act<2>(a, bias + net::OFF_B2 + 16 * hw, q);
+    store_phase<H2_MAP, H2_CHUNK, 2, ROUND, 2>(sm + H2_OFF, (p >> 2) + 1, (p & 3) + 1,
+                                               GROUP * g + (r & 7), 2 * hw, q);
+  };
   for (;;) {
     const int ng = (cur.nv + GROUP - 1) / GROUP;
     const int v_next = v + (int)gridDim.x;
-    for (int g = 0; g < ng; ++g) {
-      src.store(sm, R);
-      store_top_rows(sm);
+    // the next input after group g's: this tile's group g + 1, else the next
+    // tile's first
+    auto prefetch_after = [&](int g) {
       if (g + 1 < ng) {
         src.load(cur, g + 1, R);
       } else if (v_next < n_tiles) {
         nxt = src.tile(v_next);
         src.load(nxt, 0, R);
       }
-      if (!layer([&] {
-            for (int t = 0; t < 4; ++t)
-              for (int u = 0; u < 3; ++u)
-                tc::mma_bf16(tm + C1 + 32 * t,
-                             tc::sdesc(sb + P_OFF + (u & 1) * 2 * P_MAP +
-                                           (2 * t + (u >> 1)) * P_ROW, P_MAP, 128),
-                             tc::sdesc(sb + W1_OFF + u * 1024, 512, 128), ID_N32, u > 0);
-          }))
-        break;
-      {   // conv1 epilogue: row 32 warp + lane of tile t = (position p of output
+    };
+    src.store(sm, R);
+    store_top_rows(sm);
+    prefetch_after(0);
+    for (int g = 0; g < ng; ++g) {
+      issue(bar1, conv1);
+      pend1 = true;
+      if (g > 0) epi2(g - 1);
+      if (!wait(bar1, ph1, pend1)) break;
+      {   // conv1 epilogue: this warp's two tiles; row = (position p of output
           // rows 2t, 2t + 1, sample)
-        const int r = 32 * warp + lane, p = r >> 3;
-#pragma unroll 1
-        for (int t = 0; t < 4; ++t) {
-          float a[32];
+        uint32_t a0[32], a1[32];
+        tc::ld32_raw(tc::taddr(tm, quarter, C1 + 64 * hw), a0);
+        tc::ld32_raw(tc::taddr(tm, quarter, C1 + 64 * hw + 32), a1);
+        tc::wait_ld(a0);
+        tc::wait_ld(a1);
+        const int r = quarter + lane, p = r >> 3;
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+          float f[32];
+#pragma unroll
+          for (int i = 0; i < 32; ++i) f[i] = __uint_as_float(k ? a1[i] : a0[i]);
           uint4 q[4];
-          tc::ld32(tc::taddr(tm, lane_q, C1 + 32 * t), a);
-          act32(a, bias + net::OFF_B1, q);
-          store_phase<H1_MAP, H1_CHUNK, 4, GROUP>(sm + H1_OFF, 2 * t + (p >> 3) + 1,
-                                                  (p & 7) + 1, r & 7, q);
+          act<4>(f, bias + net::OFF_B1, q);
+          store_phase<H1_MAP, H1_CHUNK, 4, GROUP, 4>(sm + H1_OFF, 2 * (2 * hw + k) + (p >> 3) + 1,
+                                                     (p & 7) + 1, r & 7, 0, q);
         }
       }
-      if (!layer([&] {
-            for (int tap = 0; tap < 9; ++tap) {
-              const int u = tap / 3, m = (u & 1) * 3 + tap % 3;
-              for (int h = 0; h < 2; ++h)
-                tc::mma_bf16(tm + C2,
-                             tc::sdesc(sb + H1_OFF + m * H1_MAP + 2 * h * H1_CHUNK +
-                                           (u >> 1) * 512, H1_CHUNK, 128),
-                             tc::sdesc(sb + W2_OFF + (2 * tap + h) * 1024, 512, 128), ID_N32,
-                             (tap | h) != 0);
-            }
-          }))
-        break;
-      {   // conv2 epilogue: row = (position p, sample)
-        const int r = 32 * warp + lane, p = r >> 3;
-        float a[32];
-        uint4 q[4];
-        tc::ld32(tc::taddr(tm, lane_q, C2), a);
-        act32(a, bias + net::OFF_B2, q);
-        store_phase<H2_MAP, H2_CHUNK, 2, ROUND>(sm + H2_OFF, (p >> 2) + 1, (p & 3) + 1,
-                                                GROUP * g + (r & 7), q);
+      issue(bar2, conv2);
+      pend2 = true;
+      if (g + 1 < ng) {
+        src.store(sm, R);
+        prefetch_after(g + 1);
       }
+      if (!wait(bar2, ph2, pend2)) break;
     }
     if (failed) break;
-    if (!layer([&] {
-          for (int tap = 0; tap < 9; ++tap) {
-            const int u = tap / 3, m = (u & 1) * 3 + tap % 3;
-            for (int h = 0; h < 2; ++h)
-              tc::mma_bf16(tm + C3,
-                           tc::sdesc(sb + H2_OFF + m * H2_MAP + 2 * h * H2_CHUNK +
-                                         (u >> 1) * 1024, H2_CHUNK, 128),
-                           tc::sdesc(sb + W3_OFF + (2 * tap + h) * 1024, 512, 128), ID_N32,
-                           (tap | h) != 0);
-          }
-        }))
-      break;
-    {   // conv3 epilogue: row = (position warp, sample lane) -> fc1 input at
-        // K = position * 32 + channel
-      float a[32];
-      uint4 q[4];
-      tc::ld32(tc::taddr(tm, lane_q, C3), a);
-      act32(a, bias + net::OFF_B3, q);
+    epi2(ng - 1);
+    issue(bar1, [&] {
+      for (int tap = 0; tap < 9; ++tap) {
+        const int u = tap / 3, m = (u & 1) * 3 + tap % 3;
+        for (int h = 0; h < 2; ++h)
+          tc::mma_bf16(tm + C3,
+                       tc::sdesc(sb + H2_OFF + m * H2_MAP + 2 * h * H2_CHUNK + (u >> 1) * 1024,
+                                 H2_CHUNK, 128),
+                       tc::sdesc(sb + W3_OFF + (2 * tap + h) * 1024, 512, 128), ID_N32,
+                       (tap | h) != 0);
+      }
+    });
+    pend1 = true;
+    if (!wait(bar1, ph1, pend1)) break;
+    {   // conv3 epilogue: row = (position warp % 4, sample lane), this warp's
+        // 16 channels -> fc1 input at K = position * 32 + channel
+      float a[16];
+      uint4 q[2];
+      tc::ld16(tc::taddr(tm, quarter, C3 + 16 * hw), a);
+      act<2>(a, bias + net::OFF_B3 + 16 * hw, q);
       uint8_t* o = sm + H3_OFF + (lane >> 3) * 128 + (lane & 7) * 16;
 #pragma unroll
-      for (int c = 0; c < 4; ++c) *reinterpret_cast<uint4*>(o + (4 * warp + c) * 512) = q[c];
+      for (int c = 0; c < 2; ++c)
+        *reinterpret_cast<uint4*>(o + (4 * (warp & 3) + 2 * hw + c) * 512) = q[c];
     }
-    if (!layer([&] {
-          for (int h = 0; h < 8; ++h)
-            tc::mma_bf16(tm + C4, tc::sdesc(sb + H3_OFF + 2 * h * 512, 512, 128),
-                         tc::sdesc(sb + W4_OFF + 2 * h * 1024, 1024, 128), ID_N64, h > 0);
-        }))
-      break;
-    if (warp == 0) {   // fc1 epilogue: rows 0..31 = the samples
+    issue(bar1, [&] {
+      for (int h = 0; h < 8; ++h)
+        tc::mma_bf16(tm + C4, tc::sdesc(sb + H3_OFF + 2 * h * 512, 512, 128),
+                     tc::sdesc(sb + W4_OFF + 2 * h * 1024, 1024, 128), ID_N64, h > 0);
+    });
+    pend1 = true;
+    if (!wait(bar1, ph1, pend1)) break;
+    if (quarter == 0) {   // fc1 epilogue: rows 0..31 = the samples, 32 columns per warp
+      float a[32];
+      uint4 q[4];
+      tc::ld32(tc::taddr(tm, 0, C4 + 32 * hw), a);
+      act<4>(a, bias + net::OFF_B4 + 32 * hw, q);
       uint8_t* o = sm + H4_OFF + (lane >> 3) * 128 + (lane & 7) * 16;
 #pragma unroll
-      for (int half = 0; half < 2; ++half) {
-        float a[32];
-        uint4 q[4];
-        tc::ld32(tc::taddr(tm, 0, C4 + 32 * half), a);
-        act32(a, bias + net::OFF_B4 + 32 * half, q);
-#pragma unroll
-        for (int c = 0; c < 4; ++c) *reinterpret_cast<uint4*>(o + (4 * half + c) * 512) = q[c];
-      }
+      for (int c = 0; c < 4; ++c) *reinterpret_cast<uint4*>(o + (4 * hw + c) * 512) = q[c];
     }
-    if (!layer([&] {
-          for (int h = 0; h < 4; ++h)
-            tc::mma_bf16(tm + C5, tc::sdesc(sb + H4_OFF + 2 * h * 512, 512, 128),
-                         tc::sdesc(sb + W5_OFF + 2 * h * 256, 256, 128), ID_N16, h > 0);
-        }))
-      break;
+    issue(bar1, [&] {
+      for (int h = 0; h < 4; ++h)
+        tc::mma_bf16(tm + C5, tc::sdesc(sb + H4_OFF + 2 * h * 512, 512, 128),
+                     tc::sdesc(sb + W5_OFF + 2 * h * 256, 256, 128), ID_N16, h > 0);
+    });
+    pend1 = true;
+    if (!wait(bar1, ph1, pend1)) break;
     if (warp == 0) {
       float a[16];
       tc::ld16(tc::taddr(tm, 0, C5), a);
@@ -390,7 +441,8 @@ __device__ __forceinline__ void run(const Src& src, const void* packed_w, uint8_
   }
   if (failed) {
     if (tid == 0 && fault) atomicExch(fault, (int32_t)VIO_ERR_TIMEOUT);
-    tc::mbar_wait(bar, phase ^ 1u, kMaxPolls);
+    if (pend1) tc::mbar_wait(bar1, ph1, kMaxPolls);
+    if (pend2) tc::mbar_wait(bar2, ph2, kMaxPolls);
   }
   tc::fence_before();
   __syncthreads();
@@ -412,7 +464,7 @@ struct XSource {
   __device__ int n_tiles() const { return (n + ROUND - 1) / ROUND; }
   __device__ Tile tile(int t) const { return Tile{t * ROUND, min(ROUND, n - t * ROUND)}; }
   __device__ void load(const Tile& T, int g, Regs& R) const {
-    const int i = g * GROUP + (threadIdx.x & 7), r = threadIdx.x >> 3;
+    const int i = g * GROUP + item_sample(), r = item_row();
 #pragma unroll
     for (int ch = 0; ch < 4; ++ch) {
       uint4 lo = make_uint4(0u, 0u, 0u, 0u), hi = lo;
@@ -433,7 +485,10 @@ struct XSource {
     }
   }
   __device__ void store(uint8_t* sm, const Regs& R) const {
-    store_row_bf16(sm, threadIdx.x & 7, threadIdx.x >> 3, R.v);
+    if (threadIdx.x >> 7)
+      store_row_bf16<1>(sm, item_sample(), item_row(), R.v);
+    else
+      store_row_bf16<0>(sm, item_sample(), item_row(), R.v);
   }
   __device__ void write(const Tile& T, int s, float dx, float dy, float conf) const {
     float* o = out + 3LL * (T.s0 + s);

@@ -135,6 +135,12 @@ inline void emu_ld(uint32_t ta, float (&v)[NC]) {
   __syncwarp();
 }
 inline void ld32(uint32_t ta, float (&v)[32]) { emu_ld<32>(ta, v); }
+inline void ld32_raw(uint32_t ta, uint32_t (&r)[32]) {
+  float v[32];
+  emu_ld<32>(ta, v);
+  memcpy(r, v, sizeof(v));
+}
+inline void wait_ld(uint32_t (&)[32]) {}
 inline void ld16(uint32_t ta, float (&v)[16]) { emu_ld<16>(ta, v); }
 
 }  // namespace tc
