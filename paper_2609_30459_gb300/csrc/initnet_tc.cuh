@@ -69,13 +69,14 @@ constexpr int H3_OFF = P_OFF;
 constexpr int H4_OFF = P_OFF + 16 * 512 + 1536;
 constexpr int BIAS_OFF = H2_OFF + 6 * H2_MAP;
 constexpr int BAR_OFF = BIAS_OFF + net::N_BIAS * 4;
-constexpr int SLOT_OFF = BAR_OFF + 16;   // two mbarriers
+constexpr int SLOT_OFF = BAR_OFF + 40;   // five mbarriers
 constexpr int SMEM = SLOT_OFF + 8;
 static_assert(H4_OFF + 8 * 512 + 1536 <= P_OFF + 4 * P_MAP, "fc operands inside conv1's input");
 static_assert(BAR_OFF % 8 == 0, "mbarrier alignment");
 
-// Tensor-memory columns of the accumulators.
-constexpr int C1 = 0, C2 = 128, C3 = 160, C4 = 192, C5 = 256, TMEM_COLS = 512;
+// Tensor-memory columns of the accumulators (conv1 and conv2 double-buffered
+// by group parity).
+constexpr int C1 = 0, C2 = 256, C3 = 320, C4 = 352, C5 = 416, TMEM_COLS = 512;
 
 constexpr uint32_t ID_N16 = tc::idesc_bf16(128, 16);
 constexpr uint32_t ID_N32 = tc::idesc_bf16(128, 32);
@@ -242,13 +243,16 @@ __device__ __forceinline__ void store_phase(uint8_t* region, int Y, int X, int s
 // accumulator lanes of quarter w % 4, its half w / 4 of the columns (or of
 // conv1's tiles).
 //
-// Per group g the MMAs overlap CUDA-core work: conv1(g) runs while the
-// epilogue of conv2(g - 1) drains, and conv2(g) while group g + 1's input is
-// stored; conv1 and the per-round layers complete on one mbarrier, conv2 on
-// the other, each with at most one commit outstanding. A completion that does
-// not come within the poll limit ends the kernel with VIO_ERR_TIMEOUT in
-// *fault (when not null), after a further bounded wait for the MMAs in flight
-// and with tensor memory freed.
+// Groups are software-pipelined over double-buffered accumulators: in step g
+// the CTA waits for conv1(g), stores group g + 1's input and issues
+// conv1(g + 1), waits for conv2(g - 1), drains conv1(g) into conv2's operand,
+// issues conv2(g) and drains conv2(g - 1) - so the tensor core runs
+// conv1(g + 1) and conv2(g) while the CUDA cores run those two epilogues.
+// Every commit has its own mbarrier (conv1 and conv2 by group parity, one for
+// the per-round layers) and is waited for once. A completion that does not
+// come within the poll limit ends the kernel with VIO_ERR_TIMEOUT in *fault
+// (when not null), after a further bounded wait for the MMAs in flight and
+// with tensor memory freed.
 template <class Src>
 __device__ __forceinline__ void run(const Src& src, const void* packed_w, uint8_t* sm,
                                     int32_t* fault) {
@@ -257,16 +261,15 @@ __device__ __forceinline__ void run(const Src& src, const void* packed_w, uint8_
   const int n_tiles = src.n_tiles();
   int v = blockIdx.x;
   if (v >= n_tiles) return;
-  uint64_t* bar1 = reinterpret_cast<uint64_t*>(sm + BAR_OFF);
-  uint64_t* bar2 = bar1 + 1;
+  // mbarriers: 0, 1 conv1 by group parity; 2, 3 conv2; 4 the per-round layers
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sm + BAR_OFF);
   uint32_t* slot = reinterpret_cast<uint32_t*>(sm + SLOT_OFF);
   typename Src::Tile cur = src.tile(v), nxt = cur;
   typename Src::Regs R;
   src.load(cur, 0, R);
   stage(packed_w, sm);
   if (tid == 0) {
-    tc::mbar_init(bar1, 1);
-    tc::mbar_init(bar2, 1);
+    for (int b = 0; b < 5; ++b) tc::mbar_init(bar + b, 1);
     tc::fence_mbar_init();
   }
   if (warp == 0) tc::tmem_alloc(slot, TMEM_COLS);
@@ -276,46 +279,69 @@ __device__ __forceinline__ void run(const Src& src, const void* packed_w, uint8_
   const uint32_t tm = *slot;
   const uint32_t sb = tc::smem_u32(sm);
   const float* bias = reinterpret_cast<const float*>(sm + BIAS_OFF);
-  uint32_t ph1 = 0, ph2 = 0;
-  bool pend1 = false, pend2 = false, failed = false;
+  uint32_t ph[5] = {0, 0, 0, 0, 0};
+  bool pend[5] = {false, false, false, false, false};
+  bool failed = false;
   // operands made visible to the tensor core, thread 0 issues and commits
-  auto issue = [&](uint64_t* b, auto body) {
+  auto issue = [&](int b, auto body) {
     tc::fence_smem_to_async();
     tc::fence_before();
     __syncthreads();
     if (tid == 0) {
       tc::fence_after();
       body();
-      tc::commit(b);
+      tc::commit(bar + b);
     }
+    pend[b] = true;
   };
-  auto wait = [&](uint64_t* b, uint32_t& ph, bool& pend) -> bool {
-    const bool ok = tc::mbar_wait(b, ph, kMaxPolls);
+  auto wait = [&](int b) -> bool {
+    const bool ok = tc::mbar_wait(bar + b, ph[b], kMaxPolls);
     if (ok) {
-      ph ^= 1u;
-      pend = false;
+      ph[b] ^= 1u;
+      pend[b] = false;
     }
     failed = __syncthreads_or(!ok) != 0;
     tc::fence_after();
     return !failed;
   };
-  auto conv1 = [&] {
+  auto conv1 = [&](int buf) {
     for (int t = 0; t < 4; ++t)
       for (int u = 0; u < 3; ++u)
-        tc::mma_bf16(tm + C1 + 32 * t,
+        tc::mma_bf16(tm + C1 + 128 * buf + 32 * t,
                      tc::sdesc(sb + P_OFF + (u & 1) * 2 * P_MAP + (2 * t + (u >> 1)) * P_ROW,
                                P_MAP, 128),
                      tc::sdesc(sb + W1_OFF + u * 1024, 512, 128), ID_N32, u > 0);
   };
-  auto conv2 = [&] {
+  auto conv2 = [&](int buf) {
     for (int tap = 0; tap < 9; ++tap) {
       const int u = tap / 3, m = (u & 1) * 3 + tap % 3;
       for (int h = 0; h < 2; ++h)
-        tc::mma_bf16(tm + C2,
+        tc::mma_bf16(tm + C2 + 32 * buf,
                      tc::sdesc(sb + H1_OFF + m * H1_MAP + 2 * h * H1_CHUNK + (u >> 1) * 512,
                                H1_CHUNK, 128),
                      tc::sdesc(sb + W2_OFF + (2 * tap + h) * 1024, 512, 128), ID_N32,
                      (tap | h) != 0);
+    }
+  };
+  // conv1's epilogue of group g: this warp's two tiles; row = (position p of
+  // output rows 2t, 2t + 1, sample) -> conv2's phase maps
+  auto epi1 = [&](int g) {
+    uint32_t a0[32], a1[32];
+    const int col = C1 + 128 * (g & 1) + 64 * hw;
+    tc::ld32_raw(tc::taddr(tm, quarter, col), a0);
+    tc::ld32_raw(tc::taddr(tm, quarter, col + 32), a1);
+    tc::wait_ld(a0);
+    tc::wait_ld(a1);
+    const int r = quarter + lane, p = r >> 3;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      float f[32];
+#pragma unroll
+      for (int i = 0; i < 32; ++i) f[i] = __uint_as_float(k ? a1[i] : a0[i]);
+      uint4 q[4];
+      act<4>(f, bias + net::OFF_B1, q);
+      store_phase<H1_MAP, H1_CHUNK, 4, GROUP, 4>(sm + H1_OFF, 2 * (2 * hw + k) + (p >> 3) + 1,
+                                                 (p & 7) + 1, r & 7, 0, q);
     }
   };
   // conv2's epilogue of group g: row (position p, sample), this warp's 16
@@ -324,7 +350,7 @@ __device__ __forceinline__ void run(const Src& src, const void* packed_w, uint8_
     const int r = quarter + lane, p = r >> 3;
     float a[16];
     uint4 q[2];
-    tc::ld16(tc::taddr(tm, quarter, C2 + 16 * hw), a);
+    tc::ld16(tc::taddr(tm, quarter, C2 + 32 * (g & 1) + 16 * hw), a);
     act<2>(a, bias + net::OFF_B2 + 16 * hw, q);
     store_phase<H2_MAP, H2_CHUNK, 2, ROUND, 2>(sm + H2_OFF, (p >> 2) + 1, (p & 3) + 1,
                                                GROUP * g + (r & 7), 2 * hw, q);
@@ -345,41 +371,23 @@ __device__ __forceinline__ void run(const Src& src, const void* packed_w, uint8_
     src.store(sm, R);
     store_top_rows(sm);
     prefetch_after(0);
+    issue(0, [&] { conv1(0); });
     for (int g = 0; g < ng; ++g) {
-      issue(bar1, conv1);
-      pend1 = true;
-      if (g > 0) epi2(g - 1);
-      if (!wait(bar1, ph1, pend1)) break;
-      {   // conv1 epilogue: this warp's two tiles; row = (position p of output
-          // rows 2t, 2t + 1, sample)
-        uint32_t a0[32], a1[32];
-        tc::ld32_raw(tc::taddr(tm, quarter, C1 + 64 * hw), a0);
-        tc::ld32_raw(tc::taddr(tm, quarter, C1 + 64 * hw + 32), a1);
-        tc::wait_ld(a0);
-        tc::wait_ld(a1);
-        const int r = quarter + lane, p = r >> 3;
-#pragma unroll
-        for (int k = 0; k < 2; ++k) {
-          float f[32];
-#pragma unroll
-          for (int i = 0; i < 32; ++i) f[i] = __uint_as_float(k ? a1[i] : a0[i]);
-          uint4 q[4];
-          act<4>(f, bias + net::OFF_B1, q);
-          store_phase<H1_MAP, H1_CHUNK, 4, GROUP, 4>(sm + H1_OFF, 2 * (2 * hw + k) + (p >> 3) + 1,
-                                                     (p & 7) + 1, r & 7, 0, q);
-        }
-      }
-      issue(bar2, conv2);
-      pend2 = true;
+      if (!wait(g & 1)) break;                       // conv1(g): its input is free
       if (g + 1 < ng) {
         src.store(sm, R);
         prefetch_after(g + 1);
+        issue((g + 1) & 1, [&] { conv1((g + 1) & 1); });
       }
-      if (!wait(bar2, ph2, pend2)) break;
+      if (g > 0 && !wait(2 + ((g - 1) & 1))) break;   // conv2(g - 1): conv2's input is free
+      epi1(g);
+      issue(2 + (g & 1), [&] { conv2(g & 1); });
+      if (g > 0) epi2(g - 1);
     }
     if (failed) break;
+    if (!wait(2 + ((ng - 1) & 1))) break;
     epi2(ng - 1);
-    issue(bar1, [&] {
+    issue(4, [&] {
       for (int tap = 0; tap < 9; ++tap) {
         const int u = tap / 3, m = (u & 1) * 3 + tap % 3;
         for (int h = 0; h < 2; ++h)
@@ -390,8 +398,7 @@ __device__ __forceinline__ void run(const Src& src, const void* packed_w, uint8_
                        (tap | h) != 0);
       }
     });
-    pend1 = true;
-    if (!wait(bar1, ph1, pend1)) break;
+    if (!wait(4)) break;
     {   // conv3 epilogue: row = (position warp % 4, sample lane), this warp's
         // 16 channels -> fc1 input at K = position * 32 + channel
       float a[16];
@@ -403,13 +410,12 @@ __device__ __forceinline__ void run(const Src& src, const void* packed_w, uint8_
       for (int c = 0; c < 2; ++c)
         *reinterpret_cast<uint4*>(o + (4 * (warp & 3) + 2 * hw + c) * 512) = q[c];
     }
-    issue(bar1, [&] {
+    issue(4, [&] {
       for (int h = 0; h < 8; ++h)
         tc::mma_bf16(tm + C4, tc::sdesc(sb + H3_OFF + 2 * h * 512, 512, 128),
                      tc::sdesc(sb + W4_OFF + 2 * h * 1024, 1024, 128), ID_N64, h > 0);
     });
-    pend1 = true;
-    if (!wait(bar1, ph1, pend1)) break;
+    if (!wait(4)) break;
     if (quarter == 0) {   // fc1 epilogue: rows 0..31 = the samples, 32 columns per warp
       float a[32];
       uint4 q[4];
@@ -419,13 +425,12 @@ __device__ __forceinline__ void run(const Src& src, const void* packed_w, uint8_
 #pragma unroll
       for (int c = 0; c < 4; ++c) *reinterpret_cast<uint4*>(o + (4 * hw + c) * 512) = q[c];
     }
-    issue(bar1, [&] {
+    issue(4, [&] {
       for (int h = 0; h < 4; ++h)
         tc::mma_bf16(tm + C5, tc::sdesc(sb + H4_OFF + 2 * h * 512, 512, 128),
                      tc::sdesc(sb + W5_OFF + 2 * h * 256, 256, 128), ID_N16, h > 0);
     });
-    pend1 = true;
-    if (!wait(bar1, ph1, pend1)) break;
+    if (!wait(4)) break;
     if (warp == 0) {
       float a[16];
       tc::ld16(tc::taddr(tm, 0, C5), a);
@@ -441,8 +446,8 @@ __device__ __forceinline__ void run(const Src& src, const void* packed_w, uint8_
   }
   if (failed) {
     if (tid == 0 && fault) atomicExch(fault, (int32_t)VIO_ERR_TIMEOUT);
-    if (pend1) tc::mbar_wait(bar1, ph1, kMaxPolls);
-    if (pend2) tc::mbar_wait(bar2, ph2, kMaxPolls);
+    for (int b = 0; b < 5; ++b)
+      if (pend[b]) tc::mbar_wait(bar + b, ph[b], kMaxPolls);
   }
   tc::fence_before();
   __syncthreads();
