@@ -5,7 +5,8 @@
 // operand. Same network and arithmetic as initnet_dev.cuh (BF16 weights and
 // activations, FP32 sums), in another summation order.
 //
-// A CTA of 256 threads (two per accumulator row) runs rounds of 32 samples:
+// A CTA of 9 warps runs rounds of 32 samples (8 warps stage inputs and drain
+// the accumulators, two per accumulator row; the ninth issues the MMAs):
 //
 //   conv1  per group of 8 samples: 4 tiles of 16 positions (two output rows)
 //          x 8 samples; a row's K = 3 tap rows x 16 (the 3 taps of a kernel
@@ -42,7 +43,8 @@ int32_t* net_fault_word();
 
 namespace ntc {
 
-constexpr int THREADS = 256;
+constexpr int EPI_WARPS = 8;                       // epilogue / input warps
+constexpr int THREADS = 32 * (EPI_WARPS + 1);      // + one MMA-issuing warp
 constexpr int ROUND = 32;     // samples per round
 constexpr int GROUP = 8;      // samples per conv1/conv2 group
 
@@ -69,7 +71,8 @@ constexpr int H3_OFF = P_OFF;
 constexpr int H4_OFF = P_OFF + 16 * 512 + 1536;
 constexpr int BIAS_OFF = H2_OFF + 6 * H2_MAP;
 constexpr int BAR_OFF = BIAS_OFF + net::N_BIAS * 4;
-constexpr int SLOT_OFF = BAR_OFF + 40;   // five mbarriers
+constexpr int N_BARS = 10;
+constexpr int SLOT_OFF = BAR_OFF + 8 * N_BARS;    // tensor-memory address, abort flag
 constexpr int SMEM = SLOT_OFF + 8;
 static_assert(H4_OFF + 8 * 512 + 1536 <= P_OFF + 4 * P_MAP, "fc operands inside conv1's input");
 static_assert(BAR_OFF % 8 == 0, "mbarrier alignment");
@@ -235,42 +238,51 @@ __device__ __forceinline__ void store_phase(uint8_t* region, int Y, int X, int s
   }
 }
 
+// mbarriers: completions of the MMAs (conv1 and conv2 by group parity, the
+// per-round layers) and operands ready (one arrival per epilogue warp).
+enum Bar { B_C1 = 0, B_C2 = 2, B_R = 4, B_P = 5, B_H1 = 6, B_H2 = 7, B_H3 = 8, B_H4 = 9 };
+
 // Runs every round of a source on this CTA (rounds blockIdx.x, + gridDim.x,
 // ...). Src provides: Tile, Regs; n_tiles(); tile(v) (its sample count nv);
 // load(tile, g, regs): this thread's input item of group g into registers
 // (item_sample(), item_row()); store(sm, regs): that item into conv1's
-// operand; write(tile, s, dx, dy, conf). THREADS threads: warp w reads the
-// accumulator lanes of quarter w % 4, its half w / 4 of the columns (or of
-// conv1's tiles).
+// operand; write(tile, s, dx, dy, conf). THREADS threads.
 //
-// Groups are software-pipelined over double-buffered accumulators: in step g
-// the CTA waits for conv1(g), stores group g + 1's input and issues
-// conv1(g + 1), waits for conv2(g - 1), drains conv1(g) into conv2's operand,
-// issues conv2(g) and drains conv2(g - 1) - so the tensor core runs
-// conv1(g + 1) and conv2(g) while the CUDA cores run those two epilogues.
-// Every commit has its own mbarrier (conv1 and conv2 by group parity, one for
-// the per-round layers) and is waited for once. A completion that does not
-// come within the poll limit ends the kernel with VIO_ERR_TIMEOUT in *fault
-// (when not null), after a further bounded wait for the MMAs in flight and
-// with tensor memory freed.
+// Warp-specialised: warp EPI_WARPS only issues MMAs, each layer as soon as
+// its operand is complete (an mbarrier that every epilogue warp arrives on);
+// the epilogue warps stage inputs and drain the accumulators, waiting only on
+// MMA completions. Warp w < EPI_WARPS reads the accumulator lanes of quarter
+// w % 4 and its half w / 4 of the columns (or of conv1's tiles). conv1 and
+// conv2 accumulate into buffers chosen by group parity, so that in step g the
+// tensor core runs conv1(g + 1) and conv2(g) while the epilogue warps drain
+// conv1(g) and conv2(g - 1):
+//   epilogue: wait conv1(g) | store input g + 1 -> ready | wait conv2(g - 1) |
+//             drain conv1(g) -> ready | drain conv2(g - 1)
+//   issuer:   wait ready -> conv1(g + 1) | wait ready -> conv2(g)
+// Every wait is bounded; one that gives up sets a shared abort flag, which
+// every other wait also stops on, then the kernel records VIO_ERR_TIMEOUT in
+// *fault (when not null), lets the MMAs in flight finish (bounded) and frees
+// its tensor memory.
 template <class Src>
 __device__ __forceinline__ void run(const Src& src, const void* packed_w, uint8_t* sm,
                                     int32_t* fault) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int quarter = 32 * (warp & 3), hw = warp >> 2;
+  const int quarter = 32 * (warp & 3), hw = (warp >> 2) & 1;
   const int n_tiles = src.n_tiles();
-  int v = blockIdx.x;
-  if (v >= n_tiles) return;
-  // mbarriers: 0, 1 conv1 by group parity; 2, 3 conv2; 4 the per-round layers
+  if ((int)blockIdx.x >= n_tiles) return;
   uint64_t* bar = reinterpret_cast<uint64_t*>(sm + BAR_OFF);
   uint32_t* slot = reinterpret_cast<uint32_t*>(sm + SLOT_OFF);
-  typename Src::Tile cur = src.tile(v), nxt = cur;
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(sm + SLOT_OFF + 4);
+  const bool issuer = warp == EPI_WARPS;
   typename Src::Regs R;
-  src.load(cur, 0, R);
+  int v = blockIdx.x;
+  typename Src::Tile cur = src.tile(v), nxt = cur;
+  if (!issuer) src.load(cur, 0, R);
   stage(packed_w, sm);
   if (tid == 0) {
-    for (int b = 0; b < 5; ++b) tc::mbar_init(bar + b, 1);
+    for (int b = 0; b < N_BARS; ++b) tc::mbar_init(bar + b, b < B_P ? 1 : EPI_WARPS);
     tc::fence_mbar_init();
+    *abort_flag = 0;
   }
   if (warp == 0) tc::tmem_alloc(slot, TMEM_COLS);
   tc::fence_before();
@@ -279,175 +291,219 @@ __device__ __forceinline__ void run(const Src& src, const void* packed_w, uint8_
   const uint32_t tm = *slot;
   const uint32_t sb = tc::smem_u32(sm);
   const float* bias = reinterpret_cast<const float*>(sm + BIAS_OFF);
-  uint32_t ph[5] = {0, 0, 0, 0, 0};
-  bool pend[5] = {false, false, false, false, false};
-  bool failed = false;
-  // operands made visible to the tensor core, thread 0 issues and commits
-  auto issue = [&](int b, auto body) {
+  uint32_t ph = 0;    // phase bits of the barriers this thread waits on (bit b)
+  // bounded wait for the next phase of barrier b; false on a time-out or abort
+  auto wait = [&](int b) -> bool {
+    const uint32_t parity = (ph >> b) & 1u;
+    for (int i = 0; i < kMaxPolls; ++i) {
+      if (tc::mbar_try(bar + b, parity)) {
+        ph ^= 1u << b;
+        tc::fence_after();
+        return true;
+      }
+      if ((i & 63) == 63 && *abort_flag) return false;
+    }
+    *abort_flag = 1;
+    return false;
+  };
+  // an epilogue warp's operand writes made visible to the tensor core, then
+  // its arrival on ready barrier b
+  auto ready = [&](int b) {
     tc::fence_smem_to_async();
     tc::fence_before();
-    __syncthreads();
-    if (tid == 0) {
-      tc::fence_after();
-      body();
-      tc::commit(bar + b);
-    }
-    pend[b] = true;
+    __syncwarp();
+    if (lane == 0) tc::mbar_arrive(bar + b);
   };
-  auto wait = [&](int b) -> bool {
-    const bool ok = tc::mbar_wait(bar + b, ph[b], kMaxPolls);
-    if (ok) {
-      ph[b] ^= 1u;
-      pend[b] = false;
-    }
-    failed = __syncthreads_or(!ok) != 0;
-    tc::fence_after();
-    return !failed;
-  };
-  auto conv1 = [&](int buf) {
-    for (int t = 0; t < 4; ++t)
-      for (int u = 0; u < 3; ++u)
-        tc::mma_bf16(tm + C1 + 128 * buf + 32 * t,
-                     tc::sdesc(sb + P_OFF + (u & 1) * 2 * P_MAP + (2 * t + (u >> 1)) * P_ROW,
-                               P_MAP, 128),
-                     tc::sdesc(sb + W1_OFF + u * 1024, 512, 128), ID_N32, u > 0);
-  };
-  auto conv2 = [&](int buf) {
-    for (int tap = 0; tap < 9; ++tap) {
-      const int u = tap / 3, m = (u & 1) * 3 + tap % 3;
-      for (int h = 0; h < 2; ++h)
-        tc::mma_bf16(tm + C2 + 32 * buf,
-                     tc::sdesc(sb + H1_OFF + m * H1_MAP + 2 * h * H1_CHUNK + (u >> 1) * 512,
-                               H1_CHUNK, 128),
-                     tc::sdesc(sb + W2_OFF + (2 * tap + h) * 1024, 512, 128), ID_N32,
-                     (tap | h) != 0);
-    }
-  };
-  // conv1's epilogue of group g: this warp's two tiles; row = (position p of
-  // output rows 2t, 2t + 1, sample) -> conv2's phase maps
-  auto epi1 = [&](int g) {
-    uint32_t a0[32], a1[32];
-    const int col = C1 + 128 * (g & 1) + 64 * hw;
-    tc::ld32_raw(tc::taddr(tm, quarter, col), a0);
-    tc::ld32_raw(tc::taddr(tm, quarter, col + 32), a1);
-    tc::wait_ld(a0);
-    tc::wait_ld(a1);
-    const int r = quarter + lane, p = r >> 3;
+
+  if (issuer) {
+    // Descriptors: a layer's base descriptor plus the operand's byte offset /
+    // 16 (the start address field is the low bits; every address stays below
+    // 256 KB), the offsets compile-time constants of the unrolled loops.
+    const uint64_t dP = tc::sdesc(sb + P_OFF, P_MAP, 128);
+    const uint64_t dH1 = tc::sdesc(sb + H1_OFF, H1_CHUNK, 128);
+    const uint64_t dH2 = tc::sdesc(sb + H2_OFF, H2_CHUNK, 128);
+    const uint64_t dH3 = tc::sdesc(sb + H3_OFF, 512, 128);
+    const uint64_t dH4 = tc::sdesc(sb + H4_OFF, 512, 128);
+    const uint64_t dW1 = tc::sdesc(sb + W1_OFF, 512, 128);
+    const uint64_t dW2 = tc::sdesc(sb + W2_OFF, 512, 128);
+    const uint64_t dW3 = tc::sdesc(sb + W3_OFF, 512, 128);
+    const uint64_t dW4 = tc::sdesc(sb + W4_OFF, 1024, 128);
+    const uint64_t dW5 = tc::sdesc(sb + W5_OFF, 256, 128);
+    // conv2 and conv3: 9 taps x 2 K halves over the phase maps of their input
+    auto conv3x3 = [&](uint32_t d, uint64_t dA, int map, int chunk, int row, uint64_t dB) {
 #pragma unroll
-    for (int k = 0; k < 2; ++k) {
-      float f[32];
+      for (int tap = 0; tap < 9; ++tap)
 #pragma unroll
-      for (int i = 0; i < 32; ++i) f[i] = __uint_as_float(k ? a1[i] : a0[i]);
-      uint4 q[4];
-      act<4>(f, bias + net::OFF_B1, q);
-      store_phase<H1_MAP, H1_CHUNK, 4, GROUP, 4>(sm + H1_OFF, 2 * (2 * hw + k) + (p >> 3) + 1,
-                                                 (p & 7) + 1, r & 7, 0, q);
+        for (int h = 0; h < 2; ++h) {
+          const int u = tap / 3, m = (u & 1) * 3 + tap % 3;
+          tc::mma_bf16(d, dA + ((m * map + 2 * h * chunk + (u >> 1) * row) >> 4),
+                       dB + (((2 * tap + h) * 1024) >> 4), ID_N32, (tap | h) != 0);
+        }
+    };
+    for (; v < n_tiles && !*abort_flag; v += gridDim.x) {
+      const int ng = (src.tile(v).nv + GROUP - 1) / GROUP;
+      bool ok = true;
+      for (int g = 0; g < ng && ok; ++g) {
+        if (!(ok = wait(B_P))) break;
+        if (lane == 0) {
+          const uint32_t d = tm + C1 + 128 * (g & 1);
+#pragma unroll
+          for (int u = 0; u < 3; ++u)
+#pragma unroll
+            for (int t = 0; t < 4; ++t)
+              tc::mma_bf16(d + 32 * t,
+                           dP + (((u & 1) * 2 * P_MAP + (2 * t + (u >> 1)) * P_ROW) >> 4),
+                           dW1 + ((u * 1024) >> 4), ID_N32, u > 0);
+          tc::commit(bar + B_C1 + (g & 1));
+        }
+        __syncwarp();
+        if (!(ok = wait(B_H1))) break;
+        if (lane == 0) {
+          conv3x3(tm + C2 + 32 * (g & 1), dH1, H1_MAP, H1_CHUNK, 512, dW2);
+          tc::commit(bar + B_C2 + (g & 1));
+        }
+        __syncwarp();
+      }
+      if (!ok || !wait(B_H2)) break;
+      if (lane == 0) {
+        conv3x3(tm + C3, dH2, H2_MAP, H2_CHUNK, 1024, dW3);
+        tc::commit(bar + B_R);
+      }
+      __syncwarp();
+      if (!wait(B_H3)) break;
+      if (lane == 0) {
+#pragma unroll
+        for (int h = 0; h < 8; ++h)
+          tc::mma_bf16(tm + C4, dH3 + ((2 * h * 512) >> 4), dW4 + ((2 * h * 1024) >> 4), ID_N64,
+                       h > 0);
+        tc::commit(bar + B_R);
+      }
+      __syncwarp();
+      if (!wait(B_H4)) break;
+      if (lane == 0) {
+#pragma unroll
+        for (int h = 0; h < 4; ++h)
+          tc::mma_bf16(tm + C5, dH4 + ((2 * h * 512) >> 4), dW5 + ((2 * h * 256) >> 4), ID_N16,
+                       h > 0);
+        tc::commit(bar + B_R);
+      }
+      __syncwarp();
     }
-  };
-  // conv2's epilogue of group g: row (position p, sample), this warp's 16
-  // channels -> conv3's phase maps
-  auto epi2 = [&](int g) {
-    const int r = quarter + lane, p = r >> 3;
-    float a[16];
-    uint4 q[2];
-    tc::ld16(tc::taddr(tm, quarter, C2 + 32 * (g & 1) + 16 * hw), a);
-    act<2>(a, bias + net::OFF_B2 + 16 * hw, q);
-    store_phase<H2_MAP, H2_CHUNK, 2, ROUND, 2>(sm + H2_OFF, (p >> 2) + 1, (p & 3) + 1,
-                                               GROUP * g + (r & 7), 2 * hw, q);
-  };
-  for (;;) {
-    const int ng = (cur.nv + GROUP - 1) / GROUP;
-    const int v_next = v + (int)gridDim.x;
-    // the next input after group g's: this tile's group g + 1, else the next
-    // tile's first
-    auto prefetch_after = [&](int g) {
-      if (g + 1 < ng) {
-        src.load(cur, g + 1, R);
-      } else if (v_next < n_tiles) {
-        nxt = src.tile(v_next);
-        src.load(nxt, 0, R);
+  } else {
+    // conv1's epilogue of group g: this warp's two tiles; row = (position p
+    // of output rows 2t, 2t + 1, sample) -> conv2's phase maps
+    auto epi1 = [&](int g) {
+      uint32_t a0[32], a1[32];
+      const int col = C1 + 128 * (g & 1) + 64 * hw;
+      tc::ld32_raw(tc::taddr(tm, quarter, col), a0);
+      tc::ld32_raw(tc::taddr(tm, quarter, col + 32), a1);
+      tc::wait_ld(a0);
+      tc::wait_ld(a1);
+      const int r = quarter + lane, p = r >> 3;
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        float f[32];
+#pragma unroll
+        for (int i = 0; i < 32; ++i) f[i] = __uint_as_float(k ? a1[i] : a0[i]);
+        uint4 q[4];
+        act<4>(f, bias + net::OFF_B1, q);
+        store_phase<H1_MAP, H1_CHUNK, 4, GROUP, 4>(
+            sm + H1_OFF, 2 * (2 * hw + k) + (p >> 3) + 1, (p & 7) + 1, r & 7, 0, q);
       }
     };
-    src.store(sm, R);
-    store_top_rows(sm);
-    prefetch_after(0);
-    issue(0, [&] { conv1(0); });
-    for (int g = 0; g < ng; ++g) {
-      if (!wait(g & 1)) break;                       // conv1(g): its input is free
-      if (g + 1 < ng) {
-        src.store(sm, R);
-        prefetch_after(g + 1);
-        issue((g + 1) & 1, [&] { conv1((g + 1) & 1); });
-      }
-      if (g > 0 && !wait(2 + ((g - 1) & 1))) break;   // conv2(g - 1): conv2's input is free
-      epi1(g);
-      issue(2 + (g & 1), [&] { conv2(g & 1); });
-      if (g > 0) epi2(g - 1);
-    }
-    if (failed) break;
-    if (!wait(2 + ((ng - 1) & 1))) break;
-    epi2(ng - 1);
-    issue(4, [&] {
-      for (int tap = 0; tap < 9; ++tap) {
-        const int u = tap / 3, m = (u & 1) * 3 + tap % 3;
-        for (int h = 0; h < 2; ++h)
-          tc::mma_bf16(tm + C3,
-                       tc::sdesc(sb + H2_OFF + m * H2_MAP + 2 * h * H2_CHUNK + (u >> 1) * 1024,
-                                 H2_CHUNK, 128),
-                       tc::sdesc(sb + W3_OFF + (2 * tap + h) * 1024, 512, 128), ID_N32,
-                       (tap | h) != 0);
-      }
-    });
-    if (!wait(4)) break;
-    {   // conv3 epilogue: row = (position warp % 4, sample lane), this warp's
-        // 16 channels -> fc1 input at K = position * 32 + channel
+    // conv2's epilogue of group g: row (position p, sample), this warp's 16
+    // channels -> conv3's phase maps
+    auto epi2 = [&](int g) {
+      const int r = quarter + lane, p = r >> 3;
       float a[16];
       uint4 q[2];
-      tc::ld16(tc::taddr(tm, quarter, C3 + 16 * hw), a);
-      act<2>(a, bias + net::OFF_B3 + 16 * hw, q);
-      uint8_t* o = sm + H3_OFF + (lane >> 3) * 128 + (lane & 7) * 16;
-#pragma unroll
-      for (int c = 0; c < 2; ++c)
-        *reinterpret_cast<uint4*>(o + (4 * (warp & 3) + 2 * hw + c) * 512) = q[c];
-    }
-    issue(4, [&] {
-      for (int h = 0; h < 8; ++h)
-        tc::mma_bf16(tm + C4, tc::sdesc(sb + H3_OFF + 2 * h * 512, 512, 128),
-                     tc::sdesc(sb + W4_OFF + 2 * h * 1024, 1024, 128), ID_N64, h > 0);
-    });
-    if (!wait(4)) break;
-    if (quarter == 0) {   // fc1 epilogue: rows 0..31 = the samples, 32 columns per warp
-      float a[32];
-      uint4 q[4];
-      tc::ld32(tc::taddr(tm, 0, C4 + 32 * hw), a);
-      act<4>(a, bias + net::OFF_B4 + 32 * hw, q);
-      uint8_t* o = sm + H4_OFF + (lane >> 3) * 128 + (lane & 7) * 16;
-#pragma unroll
-      for (int c = 0; c < 4; ++c) *reinterpret_cast<uint4*>(o + (4 * hw + c) * 512) = q[c];
-    }
-    issue(4, [&] {
-      for (int h = 0; h < 4; ++h)
-        tc::mma_bf16(tm + C5, tc::sdesc(sb + H4_OFF + 2 * h * 512, 512, 128),
-                     tc::sdesc(sb + W5_OFF + 2 * h * 256, 256, 128), ID_N16, h > 0);
-    });
-    if (!wait(4)) break;
-    if (warp == 0) {
-      float a[16];
-      tc::ld16(tc::taddr(tm, 0, C5), a);
-      if (lane < cur.nv) {
-        const float o0 = a[0] + bias[net::OFF_B5], o1 = a[1] + bias[net::OFF_B5 + 1];
-        const float o2 = a[2] + bias[net::OFF_B5 + 2];
-        src.write(cur, lane, o0 * net::kScale, o1 * net::kScale, 1.f / (1.f + expf(-o2)));
+      tc::ld16(tc::taddr(tm, quarter, C2 + 32 * (g & 1) + 16 * hw), a);
+      act<2>(a, bias + net::OFF_B2 + 16 * hw, q);
+      store_phase<H2_MAP, H2_CHUNK, 2, ROUND, 2>(sm + H2_OFF, (p >> 2) + 1, (p & 3) + 1,
+                                                 GROUP * g + (r & 7), 2 * hw, q);
+    };
+    for (;;) {
+      const int ng = (cur.nv + GROUP - 1) / GROUP;
+      const int v_next = v + (int)gridDim.x;
+      // the next input after group g's: this tile's group g + 1, else the
+      // next tile's first
+      auto prefetch_after = [&](int g) {
+        if (g + 1 < ng) {
+          src.load(cur, g + 1, R);
+        } else if (v_next < n_tiles) {
+          nxt = src.tile(v_next);
+          src.load(nxt, 0, R);
+        }
+      };
+      src.store(sm, R);
+      store_top_rows(sm);
+      ready(B_P);
+      prefetch_after(0);
+      bool ok = true;
+      for (int g = 0; g < ng && ok; ++g) {
+        if (!(ok = wait(B_C1 + (g & 1)))) break;              // conv1(g): its input is free
+        if (g + 1 < ng) {
+          src.store(sm, R);
+          ready(B_P);
+          prefetch_after(g + 1);
+        }
+        if (g > 0 && !(ok = wait(B_C2 + ((g - 1) & 1)))) break;   // conv2(g - 1) done
+        epi1(g);
+        ready(B_H1);
+        if (g > 0) epi2(g - 1);
       }
+      if (!ok || !wait(B_C2 + ((ng - 1) & 1))) break;
+      epi2(ng - 1);
+      ready(B_H2);
+      if (!wait(B_R)) break;
+      {   // conv3 epilogue: row = (position warp % 4, sample lane), this warp's
+          // 16 channels -> fc1 input at K = position * 32 + channel
+        float a[16];
+        uint4 q[2];
+        tc::ld16(tc::taddr(tm, quarter, C3 + 16 * hw), a);
+        act<2>(a, bias + net::OFF_B3 + 16 * hw, q);
+        uint8_t* o = sm + H3_OFF + (lane >> 3) * 128 + (lane & 7) * 16;
+#pragma unroll
+        for (int c = 0; c < 2; ++c)
+          *reinterpret_cast<uint4*>(o + (4 * (warp & 3) + 2 * hw + c) * 512) = q[c];
+      }
+      ready(B_H3);
+      if (!wait(B_R)) break;
+      if (quarter == 0) {   // fc1 epilogue: rows 0..31 = the samples, 32 columns per warp
+        float a[32];
+        uint4 q[4];
+        tc::ld32(tc::taddr(tm, 0, C4 + 32 * hw), a);
+        act<4>(a, bias + net::OFF_B4 + 32 * hw, q);
+        uint8_t* o = sm + H4_OFF + (lane >> 3) * 128 + (lane & 7) * 16;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) *reinterpret_cast<uint4*>(o + (4 * hw + c) * 512) = q[c];
+      }
+      ready(B_H4);
+      if (!wait(B_R)) break;
+      if (warp == 0) {
+        float a[16];
+        tc::ld16(tc::taddr(tm, 0, C5), a);
+        if (lane < cur.nv) {
+          const float o0 = a[0] + bias[net::OFF_B5], o1 = a[1] + bias[net::OFF_B5 + 1];
+          const float o2 = a[2] + bias[net::OFF_B5 + 2];
+          src.write(cur, lane, o0 * net::kScale, o1 * net::kScale, 1.f / (1.f + expf(-o2)));
+        }
+      }
+      if (v_next >= n_tiles) break;
+      cur = nxt;
+      v = v_next;
     }
-    if (v_next >= n_tiles) break;
-    cur = nxt;
-    v = v_next;
   }
-  if (failed) {
-    if (tid == 0 && fault) atomicExch(fault, (int32_t)VIO_ERR_TIMEOUT);
-    for (int b = 0; b < 5; ++b)
-      if (pend[b]) tc::mbar_wait(bar + b, ph[b], kMaxPolls);
+  __syncthreads();
+  if (*abort_flag) {
+    // every MMA issued before a further commit has completed when it arrives
+    if (tid == 32 * EPI_WARPS) {
+      if (fault) atomicExch(fault, (int32_t)VIO_ERR_TIMEOUT);
+      tc::mbar_init(bar + B_P, 1);
+      tc::commit(bar + B_P);
+      tc::mbar_wait(bar + B_P, 0, kMaxPolls);
+    }
+    __syncthreads();
   }
   tc::fence_before();
   __syncthreads();

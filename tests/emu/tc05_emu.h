@@ -13,6 +13,8 @@
 #include <cstdlib>
 #include <cstring>
 #include <cuda_bf16.h>
+#include <map>
+#include <mutex>
 #include <thread>
 
 namespace vio {
@@ -99,19 +101,48 @@ inline void mma_bf16(uint32_t d, uint64_t a, uint64_t b, uint32_t id, bool accum
   ++T.mmas;
 }
 
+// The barrier word: completed phases (low 32 bits) and arrivals in the
+// current phase (high 32 bits); the expected count is kept beside it.
 inline std::atomic<uint64_t>* emu_bar(uint64_t* bar) {
   static_assert(sizeof(std::atomic<uint64_t>) == 8, "barrier word");
   return reinterpret_cast<std::atomic<uint64_t>*>(bar);
 }
-inline void mbar_init(uint64_t* bar, uint32_t) { emu_bar(bar)->store(0); }
+inline std::mutex& emu_bar_mu() {
+  static std::mutex m;
+  return m;
+}
+inline std::map<const void*, uint32_t>& emu_bar_count() {
+  static std::map<const void*, uint32_t> m;
+  return m;
+}
+inline void mbar_init(uint64_t* bar, uint32_t count) {
+  std::lock_guard<std::mutex> l(emu_bar_mu());
+  emu_bar_count()[bar] = count;
+  emu_bar(bar)->store(0);
+}
 inline void fence_mbar_init() {}
-inline void commit(uint64_t* bar) { emu_bar(bar)->fetch_add(1); }   // completed phases
+inline void mbar_arrive(uint64_t* bar) {
+  std::lock_guard<std::mutex> l(emu_bar_mu());
+  const uint64_t v = emu_bar(bar)->load();
+  const uint32_t arrived = (uint32_t)(v >> 32) + 1, done = (uint32_t)v;
+  if (arrived == emu_bar_count()[bar])
+    emu_bar(bar)->store((uint64_t)(done + 1));
+  else
+    emu_bar(bar)->store(((uint64_t)arrived << 32) | done);
+}
+inline void commit(uint64_t* bar) { mbar_arrive(bar); }   // barriers of count 1
 inline void fence_before() {}
 inline void fence_after() {}
 inline void fence_smem_to_async() {}
 
 // Phase `parity` has completed when the count of completed phases has the
 // other parity (waits are for the latest phase). Blocks up to 20 s.
+// (not ready: a short sleep, so that a poll limit covers emulated MMA time)
+inline bool mbar_try(uint64_t* bar, uint32_t parity) {
+  if ((emu_bar(bar)->load() & 1) != parity) return true;
+  std::this_thread::sleep_for(std::chrono::microseconds(20));
+  return (emu_bar(bar)->load() & 1) != parity;
+}
 inline bool mbar_wait(uint64_t* bar, uint32_t parity, int) {
   const auto t0 = std::chrono::steady_clock::now();
   while ((emu_bar(bar)->load() & 1) == parity) {
