@@ -259,6 +259,9 @@ enum Bar { B_C1 = 0, B_C2 = 2, B_R = 4, B_P = 5, B_H1 = 6, B_H2 = 7, B_H3 = 8, B
 //   epilogue: wait conv1(g) | store input g + 1 -> ready | wait conv2(g - 1) |
 //             drain conv1(g) -> ready | drain conv2(g - 1)
 //   issuer:   wait ready -> conv1(g + 1) | wait ready -> conv2(g)
+// (an MMA of 128 rows x 16 K costs about 50-65 cycles to issue, the tensor
+// core's reading of its 4-5 KB of operands, and completes shortly after the
+// last one is issued).
 // Every wait is bounded; one that gives up sets a shared abort flag, which
 // every other wait also stops on, then the kernel records VIO_ERR_TIMEOUT in
 // *fault (when not null), lets the MMAs in flight finish (bounded) and frees
@@ -340,23 +343,31 @@ __device__ __forceinline__ void run(const Src& src, const void* packed_w, uint8_
                        dB + (((2 * tap + h) * 1024) >> 4), ID_N32, (tap | h) != 0);
         }
     };
+    auto conv1 = [&](int g) {
+      if (lane == 0) {
+        const uint32_t d = tm + C1 + 128 * (g & 1);
+#pragma unroll
+        for (int u = 0; u < 3; ++u)
+#pragma unroll
+          for (int t = 0; t < 4; ++t)
+            tc::mma_bf16(d + 32 * t,
+                         dP + (((u & 1) * 2 * P_MAP + (2 * t + (u >> 1)) * P_ROW) >> 4),
+                         dW1 + ((u * 1024) >> 4), ID_N32, u > 0);
+        tc::commit(bar + B_C1 + (g & 1));
+      }
+      __syncwarp();
+    };
     for (; v < n_tiles && !*abort_flag; v += gridDim.x) {
       const int ng = (src.tile(v).nv + GROUP - 1) / GROUP;
-      bool ok = true;
+      // the epilogue warps' order: input g + 1 is ready before conv1(g)'s
+      // output has been drained, so conv1(g + 1) goes ahead of conv2(g)
+      bool ok = wait(B_P);
+      if (ok) conv1(0);
       for (int g = 0; g < ng && ok; ++g) {
-        if (!(ok = wait(B_P))) break;
-        if (lane == 0) {
-          const uint32_t d = tm + C1 + 128 * (g & 1);
-#pragma unroll
-          for (int u = 0; u < 3; ++u)
-#pragma unroll
-            for (int t = 0; t < 4; ++t)
-              tc::mma_bf16(d + 32 * t,
-                           dP + (((u & 1) * 2 * P_MAP + (2 * t + (u >> 1)) * P_ROW) >> 4),
-                           dW1 + ((u * 1024) >> 4), ID_N32, u > 0);
-          tc::commit(bar + B_C1 + (g & 1));
+        if (g + 1 < ng) {
+          if (!(ok = wait(B_P))) break;
+          conv1(g + 1);
         }
-        __syncwarp();
         if (!(ok = wait(B_H1))) break;
         if (lane == 0) {
           conv3x3(tm + C2 + 32 * (g & 1), dH1, H1_MAP, H1_CHUNK, 512, dW2);
