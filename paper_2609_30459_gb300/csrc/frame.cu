@@ -230,9 +230,9 @@ struct KNSource {
         for (int k = 0; k < 4; ++k) px[ch][k] = 0x80808080u;
       }
     }
-    if (threadIdx.x >> 7)
+    if (ntc::NH == 1 || (threadIdx.x >> 7))
       ntc::store_row_bytes<1>(sm, ntc::item_sample(), ntc::item_row(), px);
-    else
+    if (ntc::NH == 1 || !(threadIdx.x >> 7))
       ntc::store_row_bytes<0>(sm, ntc::item_sample(), ntc::item_row(), px);
   }
   __device__ void write(const Tile& T, int s, float dx, float dy, float conf) const {

@@ -5,8 +5,8 @@
 // operand. Same network and arithmetic as initnet_dev.cuh (BF16 weights and
 // activations, FP32 sums), in another summation order.
 //
-// A CTA of 9 warps runs rounds of 32 samples (8 warps stage inputs and drain
-// the accumulators, two per accumulator row; the ninth issues the MMAs):
+// A CTA of EPI_WARPS + 1 warps runs rounds of 32 samples (EPI_WARPS warps stage
+// inputs and drain the accumulators; the last one issues the MMAs):
 //
 //   conv1  per group of 8 samples: 4 tiles of 16 positions (two output rows)
 //          x 8 samples; a row's K = 3 tap rows x 16 (the 3 taps of a kernel
@@ -43,7 +43,8 @@ int32_t* net_fault_word();
 
 namespace ntc {
 
-constexpr int EPI_WARPS = 8;                       // epilogue / input warps
+constexpr int EPI_WARPS = 4;                       // epilogue / input warps (4 or 8)
+constexpr int NH = EPI_WARPS / 4;                  // epilogue warps per accumulator lane quarter
 constexpr int THREADS = 32 * (EPI_WARPS + 1);      // + one MMA-issuing warp
 constexpr int ROUND = 32;     // samples per round
 constexpr int GROUP = 8;      // samples per conv1/conv2 group
@@ -84,7 +85,7 @@ constexpr int C1 = 0, C2 = 256, C3 = 320, C4 = 352, C5 = 416, TMEM_COLS = 512;
 constexpr uint32_t ID_N16 = tc::idesc_bf16(128, 16);
 constexpr uint32_t ID_N32 = tc::idesc_bf16(128, 32);
 constexpr uint32_t ID_N64 = tc::idesc_bf16(128, 64);
-constexpr int kMaxPolls = 1 << 20;
+constexpr int kMaxPolls = 1 << 22;   // non-suspending tests: tens of ms
 
 __device__ __forceinline__ int boff(int n, int k, int lbo) {   // B element (n, k)
   return (k >> 3) * lbo + (n >> 3) * 128 + (n & 7) * 16 + (k & 7) * 2;
@@ -163,7 +164,8 @@ __device__ __forceinline__ void store_top_rows(uint8_t* sm) {
 }
 
 // This thread's input item: group sample s = tid % 8 (the 8 lanes of a store
-// phase are 8 samples), row r = (tid / 8) % 16, half of the row tid / 128.
+// phase are 8 samples), row r = (tid / 8) % 16, and (with 8 epilogue warps)
+// half of the row tid / 128, else the whole row.
 __device__ __forceinline__ int item_sample() { return threadIdx.x & 7; }
 __device__ __forceinline__ int item_row() { return (threadIdx.x >> 3) & 15; }
 
@@ -196,6 +198,10 @@ __device__ __forceinline__ void store_row_bf16(uint8_t* sm, int s, int r,
   }
   store_row<H>(sm, s, r, lo, hi);
 }
+
+// CW (16 or 32) accumulator columns of this warp's lanes (tc::ld16 / ld32).
+__device__ __forceinline__ void ld_cols(uint32_t ta, float (&v)[32]) { tc::ld32(ta, v); }
+__device__ __forceinline__ void ld_cols(uint32_t ta, float (&v)[16]) { tc::ld16(ta, v); }
 
 __device__ __forceinline__ uint32_t relu_bf2(float a, float b) {
   const __nv_bfloat162 h = __floats2bfloat162_rn(fmaxf(a, 0.f), fmaxf(b, 0.f));
@@ -252,7 +258,8 @@ enum Bar { B_C1 = 0, B_C2 = 2, B_R = 4, B_P = 5, B_H1 = 6, B_H2 = 7, B_H3 = 8, B
 // its operand is complete (an mbarrier that every epilogue warp arrives on);
 // the epilogue warps stage inputs and drain the accumulators, waiting only on
 // MMA completions. Warp w < EPI_WARPS reads the accumulator lanes of quarter
-// w % 4 and its half w / 4 of the columns (or of conv1's tiles). conv1 and
+// w % 4 and (with 8 epilogue warps) its half w / 4 of the columns (or of
+// conv1's tiles). conv1 and
 // conv2 accumulate into buffers chosen by group parity, so that in step g the
 // tensor core runs conv1(g + 1) and conv2(g) while the epilogue warps drain
 // conv1(g) and conv2(g - 1):
@@ -270,7 +277,7 @@ template <class Src>
 __device__ __forceinline__ void run(const Src& src, const void* packed_w, uint8_t* sm,
                                     int32_t* fault) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int quarter = 32 * (warp & 3), hw = (warp >> 2) & 1;
+  const int quarter = 32 * (warp & 3), hw = NH > 1 ? (warp >> 2) & 1 : 0;
   const int n_tiles = src.n_tiles();
   if ((int)blockIdx.x >= n_tiles) return;
   uint64_t* bar = reinterpret_cast<uint64_t*>(sm + BAR_OFF);
@@ -404,34 +411,30 @@ __device__ __forceinline__ void run(const Src& src, const void* packed_w, uint8_
     // conv1's epilogue of group g: this warp's two tiles; row = (position p
     // of output rows 2t, 2t + 1, sample) -> conv2's phase maps
     auto epi1 = [&](int g) {
-      uint32_t a0[32], a1[32];
-      const int col = C1 + 128 * (g & 1) + 64 * hw;
-      tc::ld32_raw(tc::taddr(tm, quarter, col), a0);
-      tc::ld32_raw(tc::taddr(tm, quarter, col + 32), a1);
-      tc::wait_ld(a0);
-      tc::wait_ld(a1);
+      constexpr int TW = 4 / NH;   // tiles per warp
+      const int col = C1 + 128 * (g & 1) + 32 * TW * hw;
       const int r = quarter + lane, p = r >> 3;
-#pragma unroll
-      for (int k = 0; k < 2; ++k) {
+#pragma unroll 1
+      for (int k = 0; k < TW; ++k) {
         float f[32];
-#pragma unroll
-        for (int i = 0; i < 32; ++i) f[i] = __uint_as_float(k ? a1[i] : a0[i]);
+        tc::ld32(tc::taddr(tm, quarter, col + 32 * k), f);
         uint4 q[4];
         act<4>(f, bias + net::OFF_B1, q);
         store_phase<H1_MAP, H1_CHUNK, 4, GROUP, 4>(
-            sm + H1_OFF, 2 * (2 * hw + k) + (p >> 3) + 1, (p & 7) + 1, r & 7, 0, q);
+            sm + H1_OFF, 2 * (TW * hw + k) + (p >> 3) + 1, (p & 7) + 1, r & 7, 0, q);
       }
     };
     // conv2's epilogue of group g: row (position p, sample), this warp's 16
     // channels -> conv3's phase maps
     auto epi2 = [&](int g) {
+      constexpr int CW = 32 / NH, NC = CW / 8;   // columns, chunks per warp
       const int r = quarter + lane, p = r >> 3;
-      float a[16];
-      uint4 q[2];
-      tc::ld16(tc::taddr(tm, quarter, C2 + 32 * (g & 1) + 16 * hw), a);
-      act<2>(a, bias + net::OFF_B2 + 16 * hw, q);
-      store_phase<H2_MAP, H2_CHUNK, 2, ROUND, 2>(sm + H2_OFF, (p >> 2) + 1, (p & 3) + 1,
-                                                 GROUP * g + (r & 7), 2 * hw, q);
+      float a[CW];
+      uint4 q[NC];
+      ld_cols(tc::taddr(tm, quarter, C2 + 32 * (g & 1) + CW * hw), a);
+      act<NC>(a, bias + net::OFF_B2 + CW * hw, q);
+      store_phase<H2_MAP, H2_CHUNK, 2, ROUND, NC>(sm + H2_OFF, (p >> 2) + 1, (p & 3) + 1,
+                                                  GROUP * g + (r & 7), NC * hw, q);
     };
     for (;;) {
       const int ng = (cur.nv + GROUP - 1) / GROUP;
@@ -468,26 +471,30 @@ __device__ __forceinline__ void run(const Src& src, const void* packed_w, uint8_
       ready(B_H2);
       if (!wait(B_R)) break;
       {   // conv3 epilogue: row = (position warp % 4, sample lane), this warp's
-          // 16 channels -> fc1 input at K = position * 32 + channel
-        float a[16];
-        uint4 q[2];
-        tc::ld16(tc::taddr(tm, quarter, C3 + 16 * hw), a);
-        act<2>(a, bias + net::OFF_B3 + 16 * hw, q);
+          // channels -> fc1 input at K = position * 32 + channel
+        constexpr int CW = 32 / NH, NC = CW / 8;
+        float a[CW];
+        uint4 q[NC];
+        ld_cols(tc::taddr(tm, quarter, C3 + CW * hw), a);
+        act<NC>(a, bias + net::OFF_B3 + CW * hw, q);
         uint8_t* o = sm + H3_OFF + (lane >> 3) * 128 + (lane & 7) * 16;
 #pragma unroll
-        for (int c = 0; c < 2; ++c)
-          *reinterpret_cast<uint4*>(o + (4 * (warp & 3) + 2 * hw + c) * 512) = q[c];
+        for (int c = 0; c < NC; ++c)
+          *reinterpret_cast<uint4*>(o + (4 * (warp & 3) + NC * hw + c) * 512) = q[c];
       }
       ready(B_H3);
       if (!wait(B_R)) break;
-      if (quarter == 0) {   // fc1 epilogue: rows 0..31 = the samples, 32 columns per warp
-        float a[32];
-        uint4 q[4];
-        tc::ld32(tc::taddr(tm, 0, C4 + 32 * hw), a);
-        act<4>(a, bias + net::OFF_B4 + 32 * hw, q);
+      if (quarter == 0) {   // fc1 epilogue: rows 0..31 = the samples, 64 / NH columns per warp
         uint8_t* o = sm + H4_OFF + (lane >> 3) * 128 + (lane & 7) * 16;
+#pragma unroll 1
+        for (int half = hw; half < 2; half += NH) {
+          float a[32];
+          uint4 q[4];
+          tc::ld32(tc::taddr(tm, 0, C4 + 32 * half), a);
+          act<4>(a, bias + net::OFF_B4 + 32 * half, q);
 #pragma unroll
-        for (int c = 0; c < 4; ++c) *reinterpret_cast<uint4*>(o + (4 * hw + c) * 512) = q[c];
+          for (int c = 0; c < 4; ++c) *reinterpret_cast<uint4*>(o + (4 * half + c) * 512) = q[c];
+        }
       }
       ready(B_H4);
       if (!wait(B_R)) break;
@@ -557,10 +564,8 @@ struct XSource {
     }
   }
   __device__ void store(uint8_t* sm, const Regs& R) const {
-    if (threadIdx.x >> 7)
-      store_row_bf16<1>(sm, item_sample(), item_row(), R.v);
-    else
-      store_row_bf16<0>(sm, item_sample(), item_row(), R.v);
+    if (NH == 1 || (threadIdx.x >> 7)) store_row_bf16<1>(sm, item_sample(), item_row(), R.v);
+    if (NH == 1 || !(threadIdx.x >> 7)) store_row_bf16<0>(sm, item_sample(), item_row(), R.v);
   }
   __device__ void write(const Tile& T, int s, float dx, float dy, float conf) const {
     float* o = out + 3LL * (T.s0 + s);

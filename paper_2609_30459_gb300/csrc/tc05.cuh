@@ -100,11 +100,13 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
       : "memory");
 }
 
-// True when the mbarrier's phase `parity` has completed (one test).
+// True when the mbarrier's phase `parity` has completed: one test that does
+// not suspend the thread (try_wait may park it for up to a hardware time
+// limit, which shows as ~1000 cycles of latency per hand-off).
 __device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
   uint32_t done;
   asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
       " selp.u32 %0, 1, 0, p;\n}\n"
       : "=r"(done)
       : "r"(smem_u32(bar)), "r"(parity)
@@ -115,17 +117,8 @@ __device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
 // Waits until the mbarrier's phase `parity` has completed, at most
 // `max_polls` polls; false when it gave up.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int max_polls) {
-  const uint32_t a = smem_u32(bar);
-  for (int i = 0; i < max_polls; ++i) {
-    uint32_t done;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-        " selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(done)
-        : "r"(a), "r"(parity)
-        : "memory");
-    if (done) return true;
-  }
+  for (int i = 0; i < max_polls; ++i)
+    if (mbar_try(bar, parity)) return true;
   return false;
 }
 
