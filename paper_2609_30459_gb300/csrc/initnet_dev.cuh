@@ -266,388 +266,8 @@ __device__ __forceinline__ void extract_warp(const Geom& g, const Batch& src, in
 namespace vio {
 namespace net {
 
-// ---------------------------------------------------------------------------
-// Tiled inference: one CTA evaluates TT samples at a time, layer by layer,
-// with the weights staged once per CTA in shared memory and every MMA tile
-// filled with 16 rows (conv1: 64 positions x TT samples, conv2: 16 x TT,
-// conv3: 4 x TT, dense layers: TT samples).
-//
-// Activations are channel-last (HWC) BF16 maps with a zero border, and the
-// convolution weights are staged with their K axis in (tap, channel) order,
-// so the two K values of an A-fragment register are two adjacent channels of
-// one tap: one 32-bit shared load at an offset that is a compile-time
-// constant of the K step plus the row's base. Pixel, row and sample strides
-// are padded so that the 8 rows x 4 channel pairs of a fragment load hit 32
-// distinct banks; weight rows are padded by 8 elements for the same reason.
-// ---------------------------------------------------------------------------
-constexpr int TT = 16;
-constexpr int TILE_THREADS = 512;
-constexpr int TILE_WARPS = TILE_THREADS / 32;
-constexpr int PK1 = K1 + 8, PK2 = K2 + 8, PK3 = K3 + 8, PK4 = K4 + 8, PK5 = K5 + 8;
-constexpr int SW1 = 0;
-constexpr int SW2 = SW1 + N1 * PK1;
-constexpr int SW3 = SW2 + N2 * PK2;
-constexpr int SW4 = SW3 + N3 * PK3;
-constexpr int SW5 = SW4 + N4 * PK4;
-constexpr int SW_END = SW5 + N5 * PK5;          // elements
-// map geometry (elements): pixel stride, row stride, sample stride
-constexpr int X_PIX = 4, X_ROW = XP * X_PIX;                 // input 18 x 18 x 4
-constexpr int H1_PIX = 36, H1_ROW = H1P * H1_PIX + 8;        // 10 x 10 x 32 (+pad)
-constexpr int H1_SAMPLE = H1P * H1_ROW;
-constexpr int H2_PIX = 36, H2_ROW = H2P * H2_PIX + 16;       // 6 x 6 x 32 (+pad)
-constexpr int XR_SAMPLE = 1440;                              // input / H2 region per sample
-constexpr int H3_SAMPLE = 136, H4_SAMPLE = 72;
-static_assert(XP * X_ROW <= XR_SAMPLE && H2P * H2_ROW <= XR_SAMPLE, "region");
-constexpr int T_W = 0;                                       // byte offsets
-constexpr int T_B = T_W + SW_END * 2;
-constexpr int T_X = ((T_B + N_BIAS * 4) + 15) & ~15;
-constexpr int T_H1 = T_X + TT * XR_SAMPLE * 2;
-constexpr int T_H3 = T_H1 + TT * H1_SAMPLE * 2;
-constexpr int T_H4 = T_H3 + TT * H3_SAMPLE * 2;
-constexpr int T_OUT = T_H4 + TT * H4_SAMPLE * 2;             // TT x 3 floats
-constexpr int T_ZERO = T_OUT + TT * 3 * 4;
-constexpr int TILE_SMEM = T_ZERO + 16;
-static_assert(TILE_SMEM <= 227 * 1024, "tile shared memory");
-// ldmatrix rows: 16-byte aligned weight rows and layer bases
-static_assert((PK1 * 2) % 16 == 0 && (PK2 * 2) % 16 == 0 && (PK4 * 2) % 16 == 0 &&
-                  (PK5 * 2) % 16 == 0 && (SW2 * 2) % 16 == 0 && (SW3 * 2) % 16 == 0 &&
-                  (SW4 * 2) % 16 == 0 && (SW5 * 2) % 16 == 0 && T_W % 16 == 0,
-              "ldmatrix alignment");
-
-struct TileSmem {
-  uint16_t* w;
-  float* b;
-  uint16_t* x;      // input, then conv2's output
-  uint16_t* h1;
-  uint16_t* h3;
-  uint16_t* h4;
-  float* out;
-  const uint16_t* zero;
-};
-
-__device__ __forceinline__ TileSmem tile_smem(uint8_t* sm) {
-  return TileSmem{reinterpret_cast<uint16_t*>(sm + T_W), reinterpret_cast<float*>(sm + T_B),
-                  reinterpret_cast<uint16_t*>(sm + T_X), reinterpret_cast<uint16_t*>(sm + T_H1),
-                  reinterpret_cast<uint16_t*>(sm + T_H3), reinterpret_cast<uint16_t*>(sm + T_H4),
-                  reinterpret_cast<float*>(sm + T_OUT),
-                  reinterpret_cast<const uint16_t*>(sm + T_ZERO)};
-}
-
-// Weights into padded rows (convolutions re-ordered to K = tap * CIN + c),
-// biases, and zeros everywhere else (H1's border is never written again).
-// Ends with a barrier.
-__device__ __forceinline__ void tile_setup(const Packed& P, uint8_t* sm) {
-  uint32_t* z = reinterpret_cast<uint32_t*>(sm + T_X);
-  for (int i = threadIdx.x; i < (TILE_SMEM - T_X) / 4; i += blockDim.x) z[i] = 0u;
-  uint32_t* zw = reinterpret_cast<uint32_t*>(sm + T_W + SW1 * 2);
-  for (int i = threadIdx.x; i < N1 * PK1 / 2; i += blockDim.x) zw[i] = 0u;
-  __syncthreads();
-  const TileSmem S = tile_smem(sm);
-  // convolutions: packed (n, c*9 + tap) -> staged (n, tap*CIN + c); reads
-  // are coalesced words of the packed rows, the permutation is in the stores
-  // (the padding columns 36..47 of conv1 stay zero from the clear above)
-  for (int i = threadIdx.x; i < N1 * K1 / 2; i += blockDim.x) {
-    const uint32_t v = __ldg(reinterpret_cast<const uint32_t*>(P.w + OFF_W1) + i);
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int e = 2 * i + h, n = e / K1, kc = e - n * K1;
-      const int c = kc / 9, tap = kc - 9 * c;
-      if (kc < 36) S.w[SW1 + n * PK1 + tap * 4 + c] = (uint16_t)(v >> (16 * h));
-    }
-  }
-  for (int i = threadIdx.x; i < N2 * K2; i += blockDim.x) {   // conv2 and conv3 words
-    const int l = i >= N2 * K2 / 2, j = i - l * (N2 * K2 / 2);
-    const uint32_t v = __ldg(reinterpret_cast<const uint32_t*>(P.w + (l ? OFF_W3 : OFF_W2)) + j);
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int e = 2 * j + h, n = e / K2, kc = e - n * K2;
-      const int c = kc / 9, tap = kc - 9 * c;
-      S.w[(l ? SW3 : SW2) + n * PK2 + tap * 32 + c] = (uint16_t)(v >> (16 * h));
-    }
-  }
-  // dense layers: rows as packed
-  for (int i = threadIdx.x; i < N4 * K4 / 2; i += blockDim.x) {
-    const int n = i / (K4 / 2), c = i - n * (K4 / 2);
-    reinterpret_cast<uint32_t*>(S.w + SW4 + n * PK4)[c] =
-        __ldg(reinterpret_cast<const uint32_t*>(P.w + OFF_W4) + i);
-  }
-  for (int i = threadIdx.x; i < N5 * K5 / 2; i += blockDim.x) {
-    const int n = i / (K5 / 2), c = i - n * (K5 / 2);
-    reinterpret_cast<uint32_t*>(S.w + SW5 + n * PK5)[c] =
-        __ldg(reinterpret_cast<const uint32_t*>(P.w + OFF_W5) + i);
-  }
-  for (int i = threadIdx.x; i < N_BIAS; i += blockDim.x) S.b[i] = __ldg(P.b + i);
-  __syncthreads();
-}
-
-__device__ __forceinline__ uint32_t lds32(const uint16_t* p) {
-  return *reinterpret_cast<const uint32_t*>(p);
-}
-
-// B fragments of two n-tiles (rows n0 .. n0+15 of a weight matrix W[n][k]
-// with row stride PK, columns k0 .. k0+15) by one ldmatrix: b[0], b[1] for
-// n-tile n0, b[2], b[3] for n0 + 8. Rows are 16-byte aligned (PK * 2 and k0
-// * 2 multiples of 16).
-__device__ __forceinline__ void ldsm_b2(uint32_t (&b)[4], const uint16_t* W, int PK, int n0,
-                                        int k0, int lane) {
-  const int m = lane >> 3, row = lane & 7;
-  const uint16_t* p = W + (n0 + (m >> 1) * 8 + row) * PK + k0 + (m & 1) * 8;
-  const unsigned a = (unsigned)__cvta_generic_to_shared(p);
-  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-               : "=r"(b[0]), "=r"(b[1]), "=r"(b[2]), "=r"(b[3])
-               : "r"(a));
-}
-
-// B fragment of one n-tile (rows n0 .. n0+7, columns k0 .. k0+15).
-__device__ __forceinline__ void ldsm_b1(uint32_t (&b)[2], const uint16_t* W, int PK, int n0,
-                                        int k0, int lane) {
-  const int m = (lane >> 3) & 1, row = lane & 7;
-  const uint16_t* p = W + (n0 + row) * PK + k0 + m * 8;
-  const unsigned a = (unsigned)__cvta_generic_to_shared(p);
-  asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];\n"
-               : "=r"(b[0]), "=r"(b[1])
-               : "r"(a));
-}
-
-// Epilogue of one accumulator tile: bias, ReLU, BF16 pairs (n, n+1) stored as
-// one word at out_row[h] + n (the caller's per-row base).
-__device__ __forceinline__ void store_pairs(const float (&acc)[4], const float* bias, int n0,
-                                            uint16_t* row0, uint16_t* row1) {
-  const float b0 = bias[n0], b1 = bias[n0 + 1];
-  const uint32_t lo = (uint32_t)f2bf(fmaxf(acc[0] + b0, 0.f)) |
-                      ((uint32_t)f2bf(fmaxf(acc[1] + b1, 0.f)) << 16);
-  const uint32_t hi = (uint32_t)f2bf(fmaxf(acc[2] + b0, 0.f)) |
-                      ((uint32_t)f2bf(fmaxf(acc[3] + b1, 0.f)) << 16);
-  *reinterpret_cast<uint32_t*>(row0 + n0) = lo;
-  *reinterpret_cast<uint32_t*>(row1 + n0) = hi;
-}
-
-// conv1 on one M tile: rows mt*16.. of TT*64 (sample, 8x8 position), all 32
-// output channels into H1 (HWC).
-__device__ __forceinline__ void tile_conv1(const TileSmem& S, int mt, int lane) {
-  const int g = lane >> 2, t = lane & 3;
-  int base[2];
-  uint16_t* orow[2];
-#pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    const int r = mt * 16 + g + 8 * h, s = r >> 6, p = r & 63, i = p >> 3, j = p & 7;
-    base[h] = s * XR_SAMPLE + (2 * i) * X_ROW + (2 * j) * X_PIX;
-    orow[h] = S.h1 + s * H1_SAMPLE + (i + 1) * H1_ROW + (j + 1) * H1_PIX;
-  }
-  float acc[4][4] = {};
-#pragma unroll
-  for (int ks = 0; ks < K1 / 16; ++ks) {
-    // lane's K pairs: taps 4 ks + t/2 and that + 2, channels 2 (t & 1) + {0, 1}
-    uint32_t a[4];
-#pragma unroll
-    for (int half = 0; half < 2; ++half) {
-      const int tap = 4 * ks + (t >> 1) + 2 * half;
-      const int off = (tap / 3) * X_ROW + (tap % 3) * X_PIX + 2 * (t & 1);
-#pragma unroll
-      for (int h = 0; h < 2; ++h)
-        a[h + 2 * half] = tap < 9 ? lds32(S.x + base[h] + off) : 0u;
-    }
-#pragma unroll
-    for (int q = 0; q < 4; q += 2) {
-      uint32_t b[4];
-      ldsm_b2(b, S.w + SW1, PK1, q * 8, ks * 16, lane);
-      mma16816(acc[q], a, b[0], b[1]);
-      mma16816(acc[q + 1], a, b[2], b[3]);
-    }
-  }
-#pragma unroll
-  for (int q = 0; q < 4; ++q) store_pairs(acc[q], S.b + OFF_B1, q * 8 + 2 * t, orow[0], orow[1]);
-}
-
-// conv2 on one sample's 16 positions (one M tile), all 32 channels into the
-// X region as H2 (HWC, 6x6 bordered).
-__device__ __forceinline__ void tile_conv2(const TileSmem& S, int s, int lane) {
-  const int g = lane >> 2, t = lane & 3;
-  int base[2];
-  uint16_t* orow[2];
-#pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    const int p = g + 8 * h, i = p >> 2, j = p & 3;
-    base[h] = s * H1_SAMPLE + (2 * i) * H1_ROW + (2 * j) * H1_PIX + 2 * t;
-    orow[h] = S.x + s * XR_SAMPLE + (i + 1) * H2_ROW + (j + 1) * H2_PIX;
-  }
-  float acc[4][4] = {};
-#pragma unroll
-  for (int ks = 0; ks < K2 / 16; ++ks) {
-    const int tap = ks >> 1, c0 = (ks & 1) * 16;
-    const int off = (tap / 3) * H1_ROW + (tap % 3) * H1_PIX + c0;
-    uint32_t a[4];
-    a[0] = lds32(S.h1 + base[0] + off);
-    a[1] = lds32(S.h1 + base[1] + off);
-    a[2] = lds32(S.h1 + base[0] + off + 8);
-    a[3] = lds32(S.h1 + base[1] + off + 8);
-#pragma unroll
-    for (int q = 0; q < 4; q += 2) {
-      uint32_t b[4];
-      ldsm_b2(b, S.w + SW2, PK2, q * 8, ks * 16, lane);
-      mma16816(acc[q], a, b[0], b[1]);
-      mma16816(acc[q + 1], a, b[2], b[3]);
-    }
-  }
-#pragma unroll
-  for (int q = 0; q < 4; ++q) store_pairs(acc[q], S.b + OFF_B2, q * 8 + 2 * t, orow[0], orow[1]);
-}
-
-// conv3 on one M tile (4 samples x 2x2 positions), one n-tile, into H3 as
-// (channel, row, column) vectors.
-__device__ __forceinline__ void tile_conv3(const TileSmem& S, int mt, int nt, int lane) {
-  const int g = lane >> 2, t = lane & 3;
-  int base[2], orow[2];
-#pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    const int r = mt * 16 + g + 8 * h, s = r >> 2, p = r & 3, i = p >> 1, j = p & 1;
-    base[h] = s * XR_SAMPLE + (2 * i) * H2_ROW + (2 * j) * H2_PIX + 2 * t;
-    orow[h] = s * H3_SAMPLE + p;
-  }
-  // two accumulators (the two channel halves of each tap): two independent
-  // MMA chains of nine instead of one of eighteen
-  float acc[2][4] = {};
-#pragma unroll
-  for (int ks = 0; ks < K3 / 16; ++ks) {
-    const int tap = ks >> 1, c0 = (ks & 1) * 16;
-    const int off = (tap / 3) * H2_ROW + (tap % 3) * H2_PIX + c0;
-    uint32_t a[4];
-    a[0] = lds32(S.x + base[0] + off);
-    a[1] = lds32(S.x + base[1] + off);
-    a[2] = lds32(S.x + base[0] + off + 8);
-    a[3] = lds32(S.x + base[1] + off + 8);
-    uint32_t b[2];
-    ldsm_b1(b, S.w + SW3, PK3, nt * 8, ks * 16, lane);
-    mma16816(acc[ks & 1], a, b[0], b[1]);
-  }
-#pragma unroll
-  for (int e = 0; e < 4; ++e) {
-    const int n = nt * 8 + 2 * t + (e & 1);
-    S.h3[orow[e >> 1] + n * 4] = f2bf(fmaxf(acc[0][e] + acc[1][e] + S.b[OFF_B3 + n], 0.f));
-  }
-}
-
-// Dense layer over the TT samples (rows), n-tile nt.
-template <int K, int PK, int STRIDE>
-__device__ __forceinline__ void fc_ntile(const uint16_t* in, const uint16_t* W, int nt, int lane,
-                                         float (&acc)[4]) {
-  const int g = lane >> 2, t = lane & 3;
-  float part[2][4] = {};        // even and odd K steps: two independent chains
-#pragma unroll
-  for (int ks = 0; ks < K / 16; ++ks) {
-    uint32_t a[4];
-    a[0] = lds32(in + g * STRIDE + ks * 16 + 2 * t);
-    a[1] = lds32(in + (g + 8) * STRIDE + ks * 16 + 2 * t);
-    a[2] = lds32(in + g * STRIDE + ks * 16 + 2 * t + 8);
-    a[3] = lds32(in + (g + 8) * STRIDE + ks * 16 + 2 * t + 8);
-    uint32_t b[2];
-    ldsm_b1(b, W, PK, nt * 8, ks * 16, lane);
-    mma16816(part[ks & 1], a, b[0], b[1]);
-  }
-#pragma unroll
-  for (int e = 0; e < 4; ++e) acc[e] = part[0][e] + part[1][e];
-}
-
-// Zero border pixels of the input maps (the region held conv2's output).
-__device__ __forceinline__ void tile_clear_input_border(const TileSmem& S) {
-  for (int i = threadIdx.x; i < TT * 68; i += blockDim.x) {
-    const int s = i / 68, k = i - s * 68;
-    const int y = k < 18 ? 0 : (k < 36 ? 17 : 1 + (k - 36) / 2);
-    const int x = k < 36 ? k % 18 : ((k - 36) & 1) * 17;
-    *reinterpret_cast<uint2*>(S.x + s * XR_SAMPLE + y * X_ROW + x * X_PIX) = make_uint2(0u, 0u);
-  }
-}
-
-// conv1, conv2 and conv3 of the TT inputs in S.x (interior written by the
-// caller and the border cleared by tile_clear_input_border, then a barrier):
-// H3 in S.h3. Ends with a barrier, after which S.x is free.
-__device__ __forceinline__ void tile_convs(const TileSmem& S) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int mt = warp; mt < TT * 4; mt += TILE_WARPS) tile_conv1(S, mt, lane);
-  __syncthreads();
-  // conv2 writes into the input region: clear its border pixels first
-  // (20 per sample, 32 channels = 8 words each)
-  for (int i = threadIdx.x; i < TT * 20 * 8; i += blockDim.x) {
-    const int s = i / 160, r = i - s * 160, k = r >> 3, w4 = r & 7;
-    const int y = k < 6 ? 0 : (k < 12 ? 5 : 1 + (k - 12) / 2);
-    const int x = k < 12 ? k % 6 : ((k - 12) & 1) * 5;
-    *reinterpret_cast<uint2*>(S.x + s * XR_SAMPLE + y * H2_ROW + x * H2_PIX + 4 * w4) =
-        make_uint2(0u, 0u);
-  }
-  for (int s = warp; s < TT; s += TILE_WARPS) tile_conv2(S, s, lane);
-  __syncthreads();
-  for (int it = warp; it < (TT / 4) * 4; it += TILE_WARPS) tile_conv3(S, it >> 2, it & 3, lane);
-  __syncthreads();
-}
-
-// fc1, one n-tile of 8 outputs per warp (warps 0..7): H3 -> H4. The caller
-// places the barrier before fc2.
-__device__ __forceinline__ void tile_fc1(const TileSmem& S, int warp, int lane) {
-  const int g = lane >> 2, t = lane & 3;
-  float acc[4];
-  fc_ntile<K4, PK4, H3_SAMPLE>(S.h3, S.w + SW4, warp, lane, acc);
-  store_pairs(acc, S.b + OFF_B4, warp * 8 + 2 * t, S.h4 + g * H4_SAMPLE,
-              S.h4 + (g + 8) * H4_SAMPLE);
-}
-
-// fc2 by one warp: out(sample, n, value) for the TT samples and n < 3, value
-// (dx, dy, conf) = (16 o0, 16 o1, sigmoid(o2)).
-template <class Out>
-__device__ __forceinline__ void tile_fc2(const TileSmem& S, int lane, Out out) {
-  const int g = lane >> 2, t = lane & 3;
-  float acc[4];
-  fc_ntile<K5, PK5, H4_SAMPLE>(S.h4, S.w + SW5, 0, lane, acc);
-#pragma unroll
-  for (int e = 0; e < 4; ++e) {
-    const int row = g + 8 * (e >> 1), n = 2 * t + (e & 1);
-    if (n < 3) {
-      const float o = acc[e] + S.b[OFF_B5 + n];
-      out(row, n, n < 2 ? o * kScale : 1.f / (1.f + expf(-o)));
-    }
-  }
-}
-
-// The network on the TT inputs in S.x (as for tile_convs); results
-// (dx, dy, conf) in S.out[3 s ..]. Ends with a barrier.
-__device__ __forceinline__ void tile_forward(const TileSmem& S) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  tile_convs(S);
-  if (warp < 8) tile_fc1(S, warp, lane);
-  __syncthreads();
-  if (warp == 0) tile_fc2(S, lane, [&](int row, int n, float v) { S.out[row * 3 + n] = v; });
-  __syncthreads();
-}
-
-// Writes row r (0..15) of channel ch of sample s's input map from the level
-// images: 16 values (v - 128) / 64 of the integer grid of keypoint (px, py),
-// 0 outside the level (the sampling of extract_warp).
-__device__ __forceinline__ void tile_input_row(const TileSmem& S, int s, int ch, int r,
-                                               const Geom& g, const Batch& src, int src_img,
-                                               const Batch& dst, int dst_img, float px,
-                                               float py, int la, int lb) {
-  const int lv = ch < 2 ? la : lb;
-  const float sc = __int_as_float((127 - lv) << 23);
-  const int cx = (int)floorf(px * sc + 0.5f) - 8;
-  const int cy = (int)floorf(py * sc + 0.5f) - 8 + r;
-  const bool in_row = cy >= 0 && cy < g.h[lv];
-  const uint8_t* row = nullptr;
-  if (in_row)
-    row = level_ptr(g, (ch & 1) ? dst : src, (ch & 1) ? dst_img : src_img, lv) +
-          (long long)cy * g.pitch[lv];
-  uint8_t v[16];
-#pragma unroll
-  for (int c = 0; c < 16; ++c) {
-    const int x = cx + c;
-    v[c] = (in_row && x >= 0 && x < g.w[lv]) ? __ldg(row + x) : (uint8_t)128;
-  }
-  uint16_t* out = S.x + s * XR_SAMPLE + (r + 1) * X_ROW + X_PIX + ch;
-#pragma unroll
-  for (int c = 0; c < 16; ++c) out[c * X_PIX] = f2bf(((float)v[c] - 128.f) * (1.f / 64.f));
-}
-
-
 // Prefetch of one input row into registers, so that the loads of the next
-// tile are in flight while the current tile computes: the five aligned
+// group are in flight while the current one computes: the five aligned
 // 32-bit words that cover the row's 16 pixels. Only for upper pyramid levels
 // (rows start 128-byte aligned and the pitch is a multiple of 128 bytes, so
 // a word that starts inside the level lies inside the row's pitch).
@@ -671,22 +291,6 @@ __device__ __forceinline__ void row_prefetch(RowWords& R, const Geom& g, const B
     const int x = R.x4 + 4 * k;
     R.w[k] = (R.row_ok && x >= 0 && x < R.wl)
                  ? __ldg(reinterpret_cast<const uint32_t*>(row + x)) : 0x80808080u;
-  }
-}
-
-__device__ __forceinline__ void row_store(const RowWords& R, const TileSmem& S, int s, int ch,
-                                          int r) {
-  uint16_t* out = S.x + s * XR_SAMPLE + (r + 1) * X_ROW + X_PIX + ch;
-  const unsigned sh = 8u * (unsigned)(R.cx - R.x4);
-  uint32_t a[4];      // the 16 pixels, aligned to the row's first pixel
-#pragma unroll
-  for (int k = 0; k < 4; ++k) a[k] = __funnelshift_r(R.w[k], R.w[k + 1], sh);
-#pragma unroll
-  for (int c = 0; c < 16; ++c) {
-    const int x = R.cx + c;
-    uint32_t v = (a[c >> 2] >> (8 * (c & 3))) & 0xffu;
-    if (!R.row_ok || x < 0 || x >= R.wl) v = 128u;
-    out[c * X_PIX] = f2bf(((float)v - 128.f) * (1.f / 64.f));
   }
 }
 
