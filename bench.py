@@ -50,10 +50,11 @@ FLOPS_PER_KP_DIR_LEVEL = 52 * 72 + 5 * 52 * 26
 # profiles/ names the command)
 TRACK_NCU = {"profile": "profiles/frame_kernels_752x480.md"}
 # DRAM bytes (read + write) per image of the pyramid+detection pass
-# (vio_pyramid_detect: frame_front_kernel, pyr_pass_kernel and select_kernel),
-# from an ncu capture of 512 images of the headline sequence (the profile
-# summary in profiles/ names the command); a full launch moves this per image
-PYRDET_TRAFFIC_PER_IMAGE = None
+# (vio_pyramid_detect: pyr_pass_kernel, detect_cells_kernel, select_kernel),
+# from an ncu capture of 512 images of the headline sequence with the L2 kept
+# between launches (profiles/pyramid_detect_752x480x512.md names the command);
+# a full launch moves this per image
+PYRDET_TRAFFIC_PER_IMAGE = 808243
 
 
 def seq_seed(rank: int) -> int:
@@ -324,16 +325,18 @@ def pyramid_detect_roofline(torch, vio, frames_dev, peaks, peak_src, w=None, h=N
         traffic = PYRDET_TRAFFIC_PER_IMAGE * n
     return {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
             "frac": gbs / peaks["hbm_gbs"], "traffic": traffic,
-            "traffic_note": "DRAM read + write bytes per launch: an ncu capture of 512 images "
+            "traffic_note": "DRAM read + write bytes per launch: an ncu capture of 512 images (L2 kept "
+                            "between launches) "
                             "scaled by the images of this launch",
-            "kernel": "vio_pyramid_detect (frame_front_kernel, pyr_pass_kernel, select_kernel)",
+            "kernel": "vio_pyramid_detect (pyr_pass_kernel, detect_cells_kernel, select_kernel)",
             "images": n, "image": f"{w}x{h}, {levels} levels, {gx}x{gy} cells",
             "batch_bytes_in": n * w * h, "algorithmic_bytes": alg,
             "algorithmic_bytes_per_image": w * h + upper + n_kp * 10 / n,
             "ms": 1000 * t, "peak_source": peak_src,
-            "note": "vio_pyramid_detect: pyramid levels 1-2 and per-cell FAST/NMS/top-k in one "
-                    "launch, the deeper levels in one more pyramid launch, then the per-image "
-                    "selection; level 0 read once, upper levels and 10 B per keypoint written"}
+            "note": "vio_pyramid_detect: per chunk of images (level 0 at most 64 MiB) the "
+                    "pyramid launch (levels 1-2, then 3) and the per-cell FAST/NMS/top-k "
+                    "launch, then the per-image selection; algorithmic bytes: level 0 read "
+                    "once, upper levels and 10 B per keypoint written"}
 
 
 def selection_variants(torch, vio, frames_dev, w, h, levels, cw, ch, reps=5):
@@ -856,6 +859,24 @@ def profile_batch(mode, steps=18):
     return 0
 
 
+def profile_initnet(n=1 << 16, reps=3):
+    """The flow network's forward pass (vio_initnet_forward, tcgen05) on n
+    random inputs with the shipped weights, `reps` times (kernel profiles)."""
+    import torch
+    from paper_2609_30459_gb300 import initnet_train, vio
+    vio.load(build=True)
+    net = vio.InitNet.load(initnet_train.DEFAULT_WEIGHTS)
+    g = torch.Generator(device="cuda").manual_seed(11)
+    x = (0.5 * torch.randn((n, 4, 16, 16), device="cuda", generator=g)).to(torch.bfloat16)
+    x = x.view(torch.int16)
+    out = torch.empty((n, 3), dtype=torch.float32, device="cuda")
+    for _ in range(reps):
+        net.forward(x, out)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_initnet": n, "status": vio.initnet_fault()}))
+    return 0
+
+
 def profile_detect(n=64, reps=3):
     """Standalone detection (vio_detect_grid) of a device-resident batch of n
     images of the headline sequence, pyramids built first, for kernel
@@ -901,11 +922,17 @@ def main():
                     help="only run vio_pyramid_detect 3 times on IMAGES images (default 512)")
     ap.add_argument("--profile-batch", choices=["plain", "learned"],
                     help="only step the 16-stream batch 18 times without graphs (launch lists)")
+    ap.add_argument("--profile-initnet", type=int, nargs="?", const=1 << 16, default=None,
+                    metavar="SAMPLES",
+                    help="only run the network's forward pass 3 times on SAMPLES random inputs "
+                         "(default 65536; for kernel profiles)")
     ap.add_argument("--profile-detect", type=int, nargs="?", const=64, default=None,
                     metavar="IMAGES",
                     help="only run 3 detections of a batch of IMAGES images (default 64; "
                          "for kernel profiles)")
     args = ap.parse_args()
+    if args.profile_initnet:
+        return profile_initnet(args.profile_initnet)
     if args.profile_detect:
         return profile_detect(args.profile_detect)
     if args.profile_batch:
