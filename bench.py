@@ -488,7 +488,7 @@ INITNET_FLOP = (2 * 8 * 8 * 32 * 4 * 9 + 2 * 4 * 4 * 32 * 32 * 9 + 2 * 2 * 2 * 3
                 + 2 * 128 * 64 + 2 * 64 * 3)
 
 
-def initnet_tensor_roofline(torch, vio, net, peaks, n=1 << 16, reps=5):
+def initnet_tensor_roofline(torch, vio, net, peaks, n=1 << 16, reps=5, peak_src="measured"):
     """The flow network's forward pass on the tcgen05 tensor cores (BF16
     operands, FP32 accumulators in tensor memory) over n random inputs, useful
     FLOPs against the measured dense BF16 peak."""
@@ -511,7 +511,7 @@ def initnet_tensor_roofline(torch, vio, net, peaks, n=1 << 16, reps=5):
     return {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
             "frac": ach / peak, "kernel": "forward_tc_kernel", "samples": n,
             "flop_per_sample": INITNET_FLOP, "ms": 1000 * t,
-            "peak_source": "measured dense BF16 (burst)",
+            "peak_source": f"{peak_src} dense BF16 (burst)",
             "note": "tcgen05.mma (M = 128 rows, operands in shared memory, accumulators in "
                     "tensor memory), rounds of 32 samples per 128-thread CTA; the proposal "
                     "launch of the frame step runs the same code"}
@@ -1151,7 +1151,8 @@ def main():
             net = vio.InitNet.load(initnet_train.DEFAULT_WEIGHTS)
         batched = batched_compare(torch, vio, args.batched_steps, args.warmup, net, seqs=seqs4)
         if net is not None:
-            batched["initnet_tensor_roofline"] = initnet_tensor_roofline(torch, vio, net, peaks)
+            batched["initnet_tensor_roofline"] = initnet_tensor_roofline(torch, vio, net, peaks,
+                                                                         peak_src=peak_src)
     serve = None
     if rank == 0 and not args.no_serve:
         from paper_2609_30459_gb300 import initnet_train
