@@ -409,11 +409,220 @@ __device__ __forceinline__ int cell_of(float x, int cw) {
 
 constexpr int kRunMax = 16;   // slots (or cells) one thread owns in one pass
 
+// Two block-wide exclusive scans sharing their two barriers (as block_scan).
+__device__ __forceinline__ void block_scan2(unsigned a, unsigned long long b, unsigned* wa,
+                                           unsigned long long* wb, unsigned& ea,
+                                           unsigned long long& eb, unsigned& ta,
+                                           unsigned long long& tb) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned ia = a;
+  unsigned long long ib = b;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned x = __shfl_up_sync(0xffffffffu, ia, o);
+    const unsigned long long y = __shfl_up_sync(0xffffffffu, ib, o);
+    if (lane >= o) {
+      ia += x;
+      ib += y;
+    }
+  }
+  if (lane == 31) {
+    wa[warp] = ia;
+    wb[warp] = ib;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    unsigned x = lane < K3_THREADS / 32 ? wa[lane] : 0u;
+    unsigned long long y = lane < K3_THREADS / 32 ? wb[lane] : 0ull;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned u = __shfl_up_sync(0xffffffffu, x, o);
+      const unsigned long long w = __shfl_up_sync(0xffffffffu, y, o);
+      if (lane >= o) {
+        x += u;
+        y += w;
+      }
+    }
+    if (lane < K3_THREADS / 32) {
+      wa[lane] = x;
+      wb[lane] = y;
+    }
+  }
+  __syncthreads();
+  ta = wa[K3_THREADS / 32 - 1];
+  tb = wb[K3_THREADS / 32 - 1];
+  ea = (warp ? wa[warp - 1] : 0u) + ia - a;
+  eb = (warp ? wb[warp - 1] : 0ull) + ib - b;
+}
+
 struct MultiK3 {
   int n;
   long long block_end[kMaxGroups];   // in blocks (= streams)
   FrameLaunch f[kMaxGroups];
 };
+
+// The finalisation in one pass, when the capacity and the cell count are at
+// most K3_THREADS (thread t owns list slot t and cell t). Every global load
+// the pass needs is issued at entry, so that their latencies overlap: the
+// counts, the statuses, positions and ids of the owned slots, the owned
+// cell's candidate count and its first candidate with its stereo match (the
+// further candidates of a cell, k > 1, are read where used). Then the
+// occupancy of the surviving camera-0 tracks is counted, the survivors' scan
+// and the cells' selection scan run together (one pair of barriers), and
+// every output is written from registers. Same lists, order and statistics
+// as the phased version below.
+__device__ __forceinline__ void finalize_one_pass(const FrameLaunch& f, int s, const StreamRef& sr,
+                                                  int32_t* st, int* occ_s, unsigned* wsa,
+                                                  unsigned long long* wsb) {
+  __shared__ int learned_s;
+  const int t = threadIdx.x;
+  const int k = f.p.k_per_cell;
+  const int gx = f.g.w[0] / f.p.cell_w, gy = f.g.h[0] / f.p.cell_h;
+  const int n_cells = gx * gy;
+  const int W = f.g.w[0];
+  const long long cap = f.cap;
+  const long long cbase = (long long)s * n_cells;
+  const long long in0 = (((long long)sr.li * f.n_streams + s) * 2) * cap;
+  const long long out0 = (((long long)sr.lo * f.n_streams + s) * 2) * cap;
+  const long long trk0 = (2LL * s) * cap;
+  const long long cnt_in = ((long long)sr.li * f.n_streams + s) * 2;
+  const long long cnt_out = ((long long)sr.lo * f.n_streams + s) * 2;
+  const bool slot_ok = t < f.cap, cell_ok = t < n_cells;
+  // every load of the pass
+  const int n0r = f.list_count[cnt_in], n1r = f.list_count[cnt_in + 1];
+  const int id0 = f.next_id[s];
+  int st0 = VIO_TRACK_EMPTY, st1 = VIO_TRACK_EMPTY, lid0 = 0, lid1 = 0, lr0 = 0, lr1 = 0;
+  float x0 = 0.f, y0 = 0.f, x1 = 0.f, y1 = 0.f;
+  if (slot_ok) {
+    st0 = f.trk_status[trk0 + t];
+    st1 = f.trk_status[trk0 + cap + t];
+    x0 = f.trk_xy[2 * (trk0 + t)];
+    y0 = f.trk_xy[2 * (trk0 + t) + 1];
+    x1 = f.trk_xy[2 * (trk0 + cap + t)];
+    y1 = f.trk_xy[2 * (trk0 + cap + t) + 1];
+    lid0 = f.list_id[in0 + t];
+    lid1 = f.list_id[in0 + cap + t];
+    if (f.net) {
+      lr0 = f.trk_learned[trk0 + t];
+      lr1 = f.trk_learned[trk0 + cap + t];
+    }
+  }
+  const long long q0 = (cbase + t) * k;   // the owned cell's first candidate
+  int nc = 0, ss0 = VIO_TRACK_EMPTY;
+  unsigned long long key0 = 0;
+  float sx0 = 0.f, sy0 = 0.f;
+  if (cell_ok) {
+    nc = f.cand_count[cbase + t];
+    key0 = f.cand[q0];
+    if (!f.stereo_after) {
+      ss0 = f.spec_status[q0];
+      sx0 = f.spec_xy[2 * q0];
+      sy0 = f.spec_xy[2 * q0 + 1];
+    }
+    occ_s[t] = 0;
+  }
+  if (t == 0) learned_s = 0;
+  __syncthreads();
+
+  // survivors of both cameras; occupancy of camera 0's
+  const int n0 = sr.have_prev ? min(n0r, f.cap) : 0;
+  const int n1 = sr.have_prev ? min(n1r, f.cap) : 0;
+  const bool keep0 = t < n0 && st0 == VIO_TRACK_OK, keep1 = t < n1 && st1 == VIO_TRACK_OK;
+  if (keep0 && x0 >= 0.f && y0 >= 0.f) {
+    const int cx = cell_of(x0, f.p.cell_w), cy = cell_of(y0, f.p.cell_h);
+    if (cx < gx && cy < gy) atomicAdd(&occ_s[cy * gx + cx], 1);
+  }
+  if (f.net) {
+    const int nl = (keep0 ? lr0 : 0) + (keep1 ? lr1 : 0);
+    if (nl) atomicAdd(&learned_s, nl);
+  }
+  __syncthreads();   // occupancy complete
+
+  // the owned cell: selection (k_eff = k - occupancy), matched subset
+  int nsel = 0, nm = 0;
+  if (cell_ok) {
+    const int occ = min(occ_s[t], 255);
+    f.occupancy[cbase + t] = (uint8_t)occ;
+    nsel = max(0, min(k - occ, nc));
+    if (!f.stereo_after)
+      for (int r = 0; r < nsel; ++r)
+        nm += (r == 0 ? ss0 : (int)f.spec_status[q0 + r]) == VIO_TRACK_OK;
+  }
+  const unsigned long long packed = (unsigned long long)nsel | ((unsigned long long)nm << 21) |
+                                    ((unsigned long long)nc << 42);
+  unsigned sex, stot;
+  unsigned long long cex, ctot;
+  block_scan2((keep0 ? 1u : 0u) | (keep1 ? 0x10000u : 0u), packed, wsa, wsb, sex, cex, stot,
+              ctot);
+  const int surv0 = (int)(stot & 0xffffu), surv1 = (int)(stot >> 16);
+  const int new_tot = (int)(ctot & 0x1fffff), m_tot = (int)((ctot >> 21) & 0x1fffff);
+  const int c_tot = (int)((ctot >> 42) & 0x1fffff);
+
+  // survivors, in order
+  if (keep0) {
+    const long long d = out0 + (sex & 0xffffu);
+    f.list_xy[2 * d] = x0;
+    f.list_xy[2 * d + 1] = y0;
+    f.list_id[d] = lid0;
+  }
+  if (keep1) {
+    const long long d = out0 + cap + (sex >> 16);
+    f.list_xy[2 * d] = x1;
+    f.list_xy[2 * d + 1] = y1;
+    f.list_id[d] = lid1;
+  }
+  // the selected candidates: new keypoints, camera 0's list, camera 1's
+  // successful matches
+  const long long bn = (long long)s * cap;
+  int o = (int)(cex & 0x1fffff), om = (int)((cex >> 21) & 0x1fffff);
+  for (int r = 0; r < nsel; ++r, ++o) {
+    const long long q = q0 + r;
+    const unsigned idx = ~(unsigned)((r == 0 ? key0 : f.cand[q]) & 0xffffffffu);
+    const float x = (float)(idx % (unsigned)W), y = (float)(idx / (unsigned)W);
+    if (o < f.cap) {
+      f.new_xy[2 * (bn + o)] = x;
+      f.new_xy[2 * (bn + o) + 1] = y;
+    }
+    const int a0 = surv0 + o;
+    if (a0 < f.cap) {
+      f.list_xy[2 * (out0 + a0)] = x;
+      f.list_xy[2 * (out0 + a0) + 1] = y;
+      f.list_id[out0 + a0] = id0 + o;
+    }
+    if (!f.stereo_after && (r == 0 ? ss0 : (int)f.spec_status[q]) == VIO_TRACK_OK) {
+      const int a1 = surv1 + om++;
+      if (a1 < f.cap) {
+        f.list_xy[2 * (out0 + cap + a1)] = r == 0 ? sx0 : f.spec_xy[2 * q];
+        f.list_xy[2 * (out0 + cap + a1) + 1] = r == 0 ? sy0 : f.spec_xy[2 * q + 1];
+        f.list_id[out0 + cap + a1] = id0 + o;
+      }
+    }
+  }
+  const int c0 = min(surv0 + new_tot, f.cap);
+  const int c1 = min(surv1 + m_tot, f.cap);
+  if (slot_ok) {
+    f.list_status[out0 + t] = t < c0 ? VIO_TRACK_OK : VIO_TRACK_EMPTY;
+    f.list_status[out0 + cap + t] = t < c1 ? VIO_TRACK_OK : VIO_TRACK_EMPTY;
+  }
+  if (t == 0) {
+    f.list_count[cnt_out] = c0;
+    f.list_count[cnt_out + 1] = c1;
+    f.new_count[s] = min(new_tot, f.cap);
+    f.next_id[s] = id0 + new_tot;
+    st[VIO_STAT_TRK0] = n0;
+    st[VIO_STAT_TRK1] = n1;
+    st[VIO_STAT_OK0] = surv0;
+    st[VIO_STAT_OK1] = surv1;
+    st[VIO_STAT_NEW] = new_tot;
+    st[VIO_STAT_MATCHED] = m_tot;
+    st[VIO_STAT_CAND] = c_tot;
+    st[VIO_STAT_LEARNED] = learned_s;
+    if (f.slotted && !f.stereo_after) {   // else the append kernel ends the step
+      f.parity[s] = sr.lo;
+      f.have_prev[s] = 1;
+    }
+  }
+}
 
 // One CTA per stream. Each thread owns a contiguous run of list slots (then
 // of cells), so each phase is one block-wide scan of packed counts.
@@ -438,6 +647,10 @@ __global__ void __launch_bounds__(K3_THREADS)
   int32_t* st = f.stats + ((long long)((ctr - 1) % VIO_STATS_RING) * f.n_streams + s) * VIO_N_STATS;
   if (!sr.active) {
     if (t < VIO_N_STATS) st[t] = 0;
+    return;
+  }
+  if (f.cap <= K3_THREADS && n_cells <= K3_THREADS) {
+    finalize_one_pass(f, s, sr, st, occ_s, reinterpret_cast<unsigned*>(ws32), ws64);
     return;
   }
   // the inputs of part 2 for this thread's first cell and its first
