@@ -293,6 +293,9 @@ __global__ void __launch_bounds__(ntc::THREADS, 1) frame_initnet_kernel(
 #endif
 
 __global__ void VIO_TRACK_BOUNDS frame_track_kernel(const __grid_constant__ MultiK2 mm) {
+  // the finalisation (launched as this launch's programmatic dependent) may
+  // take its SM now and wait there for this launch's completion
+  asm volatile("griddepcontrol.launch_dependents;");
   const long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (w >= mm.block_end[mm.n - 1]) return;
@@ -628,6 +631,9 @@ __device__ __forceinline__ void finalize_one_pass(const FrameLaunch& f, int s, c
 // of cells), so each phase is one block-wide scan of packed counts.
 __global__ void __launch_bounds__(K3_THREADS)
     frame_finalize_kernel(const __grid_constant__ MultiK3 mm) {
+  // launched as the tracking launch's programmatic dependent: wait for its
+  // completion and memory (a no-op after an ordinary launch)
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   extern __shared__ int occ_s[];
   __shared__ int ws32[K3_THREADS / 32];
   __shared__ unsigned long long ws64[K3_THREADS / 32];
@@ -1137,7 +1143,22 @@ cudaError_t launch_frames(const FrameLaunch* fl, int n_groups, const FrameTune& 
                              cudaFuncAttributeMaxDynamicSharedMemorySize, smem3);
     if (e != cudaSuccess) return e;
   }
-  frame_finalize_kernel<<<(unsigned)acc, K3_THREADS, smem3, s>>>(m3);
+  {
+    // a programmatic dependent of the tracking launch: its CTA is resident
+    // and waiting when the tracking ends, instead of being launched then
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)acc);
+    cfg.blockDim = dim3(K3_THREADS);
+    cfg.dynamicSmemBytes = (size_t)smem3;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelEx(&cfg, frame_finalize_kernel, m3);
+    if (e != cudaSuccess) return e;
+  }
   if (tune.stereo_after) {
     // K4: stereo matching of the selected keypoints; K5: append to camera 1
     MultiK2 m4{};
