@@ -110,26 +110,23 @@ __device__ __forceinline__ void warp_sum(float (&v)[N]) {
     for (int i = 0; i < N; ++i) v[i] += __shfl_xor_sync(0xffffffffu, v[i], o);
 }
 
-// Sums four values over the warp and gives every lane all four totals, with
-// a transposed butterfly: after the xor-16 and xor-8 exchanges each lane
-// carries one of the four partial sums (value 2*bit4 + bit3 of its lane id),
-// three more xor rounds finish it, and four broadcasts hand it out.
+// Sums four values over the warp and gives every lane all four totals: an
+// xor butterfly, five rounds of four independent exchanges. The two lanes of
+// every exchange add the same two operands, so after each round a lane and
+// its partner hold bitwise equal partial sums, and at the end every lane
+// holds the same totals.
 __device__ __forceinline__ void warp_sum4(float& a0, float& a1, float& a2, float& a3) {
-  const unsigned lane = threadIdx.x & 31u;
-  const bool h16 = lane & 16u, h8 = lane & 8u;
-  float k0 = h16 ? a2 : a0, k1 = h16 ? a3 : a1;
-  const float s0 = h16 ? a0 : a2, s1 = h16 ? a1 : a3;
-  k0 += __shfl_xor_sync(0xffffffffu, s0, 16);
-  k1 += __shfl_xor_sync(0xffffffffu, s1, 16);
-  float k = h8 ? k1 : k0;
-  k += __shfl_xor_sync(0xffffffffu, h8 ? k0 : k1, 8);
-  k += __shfl_xor_sync(0xffffffffu, k, 4);
-  k += __shfl_xor_sync(0xffffffffu, k, 2);
-  k += __shfl_xor_sync(0xffffffffu, k, 1);
-  a0 = __shfl_sync(0xffffffffu, k, 0);
-  a1 = __shfl_sync(0xffffffffu, k, 8);
-  a2 = __shfl_sync(0xffffffffu, k, 16);
-  a3 = __shfl_sync(0xffffffffu, k, 24);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float b0 = __shfl_xor_sync(0xffffffffu, a0, o);
+    const float b1 = __shfl_xor_sync(0xffffffffu, a1, o);
+    const float b2 = __shfl_xor_sync(0xffffffffu, a2, o);
+    const float b3 = __shfl_xor_sync(0xffffffffu, a3, o);
+    a0 += b0;
+    a1 += b1;
+    a2 += b2;
+    a3 += b3;
+  }
 }
 
 // position = anchor (int) + offset (float)
@@ -357,8 +354,12 @@ __device__ __forceinline__ int gn_step(const Lv& L, const Tpl& T, int lane, cons
       }
     }
   }
-  if (!__all_sync(0xffffffffu, ok)) return VIO_TRACK_OOB_WARP;
+  // a sample outside the level adds 1e30 to the sum of intensities (at most
+  // 52 x 255 otherwise), so the one reduction also tells every lane whether
+  // any lane left the level
+  if (!ok) r0 += 1e30f;
   warp_sum4(r0, r1, r2, r3);
+  if (r0 >= 1e29f) return VIO_TRACK_OOB_WARP;
   if (!(r0 > 0.f)) return VIO_TRACK_ZERO_MEAN;
   const float q = __fdividef(T.S, r0);
   const float d0 = T.c0 - q * r1;
