@@ -292,6 +292,9 @@ __global__ void __launch_bounds__(ntc::THREADS, 1) frame_initnet_kernel(
 #define VIO_TRACK_BOUNDS
 #endif
 
+// BUTTERFLY: the reduction form for a launch that leaves most of the GPU
+// idle (trk::warp_sum4).
+template <bool BUTTERFLY>
 __global__ void VIO_TRACK_BOUNDS frame_track_kernel(const __grid_constant__ MultiK2 mm) {
   // the finalisation (launched as this launch's programmatic dependent) may
   // take its SM now and wait there for this launch's completion
@@ -329,16 +332,17 @@ __global__ void VIO_TRACK_BOUNDS frame_track_kernel(const __grid_constant__ Mult
       const float* q = f.net_out + 3 * wl;
       if (q[2] >= f.net_tau) {
         float last;
-        st = trk::track_fb(f.g, f.prev, r.prev_img + c, f.cur, r.cur_img + c, px, py, true,
-                           px + q[0], py + q[1], 0.f, cfg, f.net_top, lane, tf, thf, have,
-                           dist, last);
+        st = trk::track_fb<BUTTERFLY>(f.g, f.prev, r.prev_img + c, f.cur, r.cur_img + c, px, py,
+                                      true, px + q[0], py + q[1], 0.f, cfg, f.net_top, lane, tf,
+                                      thf, have, dist, last);
         learned = st == VIO_TRACK_OK && !(f.net_max_step > 0.f && last > f.net_max_step);
       }
     }
     if (!learned) {
       float last;
-      st = trk::track_fb(f.g, f.prev, r.prev_img + c, f.cur, r.cur_img + c, px, py, false,
-                         0.f, 0.f, 0.f, cfg, top, lane, tf, thf, have, dist, last);
+      st = trk::track_fb<BUTTERFLY>(f.g, f.prev, r.prev_img + c, f.cur, r.cur_img + c, px, py,
+                                    false, 0.f, 0.f, 0.f, cfg, top, lane, tf, thf, have, dist,
+                                    last);
     }
     if (lane == 0) {
       if (f.net) f.trk_learned[wl] = learned ? 1 : 0;
@@ -365,8 +369,9 @@ __global__ void VIO_TRACK_BOUNDS frame_track_kernel(const __grid_constant__ Mult
   const unsigned idx = ~(unsigned)(key & 0xffffffffu);
   const float x = (float)(idx % (unsigned)f.g.w[0]), y = (float)(idx / (unsigned)f.g.w[0]);
   float last;
-  const int st = trk::track_fb(f.g, f.cur, r.cur_img, f.cur, r.cur_img + 1, x, y, false, 0.f,
-                               0.f, 0.f, cfg, top, lane, tf, thf, have, dist, last);
+  const int st = trk::track_fb<BUTTERFLY>(f.g, f.cur, r.cur_img, f.cur, r.cur_img + 1, x, y,
+                                          false, 0.f, 0.f, 0.f, cfg, top, lane, tf, thf, have,
+                                          dist, last);
   if (lane == 0) {
     f.spec_status[w2] = (uint8_t)st;
     f.spec_xy[2 * w2] = have ? (float)tf.ax + tf.dx : qnan;
@@ -375,6 +380,31 @@ __global__ void VIO_TRACK_BOUNDS frame_track_kernel(const __grid_constant__ Mult
 }
 
 constexpr int K3_THREADS = 1024;
+
+// Launches `kernel` on stream s, as a programmatic dependent of the previous
+// launch when `dependent`: its CTAs may then be scheduled once every CTA of
+// the previous launch has passed griddepcontrol.launch_dependents (or
+// exited), and the kernel itself waits on griddepcontrol.wait before touching
+// memory. Only after a launch that leaves most of the GPU idle (at most
+// kDependentMaxWarpsPerSm warps per SM): after one that fills the GPU, the
+// dependent's early-resident CTAs (a 1024-thread CTA holds all of an SM's
+// registers) would slow it more than the launch latency they hide.
+constexpr int kDependentMaxWarpsPerSm = 16;
+template <class K, class A>
+cudaError_t launch_dependent(K kernel, unsigned grid, unsigned block, size_t smem,
+                             cudaStream_t s, const A& args, bool dependent = true) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = dependent ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kernel, args);
+}
 
 // Block-wide exclusive scan (one value per thread); returns the exclusive
 // prefix and the block total. All threads must call it.
@@ -632,8 +662,10 @@ __device__ __forceinline__ void finalize_one_pass(const FrameLaunch& f, int s, c
 __global__ void __launch_bounds__(K3_THREADS)
     frame_finalize_kernel(const __grid_constant__ MultiK3 mm) {
   // launched as the tracking launch's programmatic dependent: wait for its
-  // completion and memory (a no-op after an ordinary launch)
+  // completion and memory (a no-op after an ordinary launch); the stereo
+  // launch that may follow can be scheduled now
   asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;");
   extern __shared__ int occ_s[];
   __shared__ int ws32[K3_THREADS / 32];
   __shared__ unsigned long long ws64[K3_THREADS / 32];
@@ -868,6 +900,10 @@ __host__ __device__ inline int max_new(const FrameLaunch& f) {
 }
 
 __global__ void frame_stereo_kernel(const __grid_constant__ MultiK2 mm) {
+  // a programmatic dependent of the finalisation; the append may be
+  // scheduled now
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;");
   const long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (w >= mm.block_end[mm.n - 1]) return;
@@ -899,6 +935,7 @@ __global__ void frame_stereo_kernel(const __grid_constant__ MultiK2 mm) {
 // order, to camera 1 after its surviving tracks, and ends the stream's step.
 __global__ void __launch_bounds__(K3_THREADS)
     frame_append_kernel(const __grid_constant__ MultiK3 mm) {
+  asm volatile("griddepcontrol.wait;" ::: "memory");   // after the stereo matching
   __shared__ int ws32[K3_THREADS / 32];
   long long start;
   const int gi = group_of(mm, blockIdx.x, start);
@@ -1118,9 +1155,13 @@ cudaError_t launch_frames(const FrameLaunch* fl, int n_groups, const FrameTune& 
     m2.block_end[i] = acc;
   }
   const int k2t = tune.k2_threads;
+  const bool k2_small = acc <= (long long)kDependentMaxWarpsPerSm * sm_count();
   if (acc > 0) {
     const long long blocks2 = (acc * 32 + k2t - 1) / k2t;
-    frame_track_kernel<<<(unsigned)blocks2, k2t, 0, s>>>(m2);
+    if (k2_small)
+      frame_track_kernel<true><<<(unsigned)blocks2, k2t, 0, s>>>(m2);
+    else
+      frame_track_kernel<false><<<(unsigned)blocks2, k2t, 0, s>>>(m2);
   }
 
   // K3: finalize
@@ -1143,22 +1184,11 @@ cudaError_t launch_frames(const FrameLaunch* fl, int n_groups, const FrameTune& 
                              cudaFuncAttributeMaxDynamicSharedMemorySize, smem3);
     if (e != cudaSuccess) return e;
   }
-  {
-    // a programmatic dependent of the tracking launch: its CTA is resident
-    // and waiting when the tracking ends, instead of being launched then
-    cudaLaunchConfig_t cfg{};
-    cfg.gridDim = dim3((unsigned)acc);
-    cfg.blockDim = dim3(K3_THREADS);
-    cfg.dynamicSmemBytes = (size_t)smem3;
-    cfg.stream = s;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    at[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
-    e = cudaLaunchKernelEx(&cfg, frame_finalize_kernel, m3);
-    if (e != cudaSuccess) return e;
-  }
+  // a programmatic dependent of a small tracking launch (a single frame): its
+  // CTA is resident and waiting when the tracking ends
+  e = launch_dependent(frame_finalize_kernel, (unsigned)acc, K3_THREADS, (size_t)smem3, s, m3,
+                       k2_small);
+  if (e != cudaSuccess) return e;
   if (tune.stereo_after) {
     // K4: stereo matching of the selected keypoints; K5: append to camera 1
     MultiK2 m4{};
@@ -1171,9 +1201,12 @@ cudaError_t launch_frames(const FrameLaunch* fl, int n_groups, const FrameTune& 
     }
     if (w4 > 0) {
       const long long blocks4 = (w4 * 32 + k2t - 1) / k2t;
-      frame_stereo_kernel<<<(unsigned)blocks4, k2t, 0, s>>>(m4);
+      e = launch_dependent(frame_stereo_kernel, (unsigned)blocks4, (unsigned)k2t, 0, s, m4);
+      if (e != cudaSuccess) return e;
     }
-    frame_append_kernel<<<(unsigned)acc, K3_THREADS, 0, s>>>(m3);
+    e = launch_dependent(frame_append_kernel, (unsigned)acc, K3_THREADS, 0, s, m3,
+                         w4 <= (long long)kDependentMaxWarpsPerSm * sm_count());
+    if (e != cudaSuccess) return e;
   }
   mark(5);
   return cudaGetLastError();

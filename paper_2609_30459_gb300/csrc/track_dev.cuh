@@ -110,23 +110,46 @@ __device__ __forceinline__ void warp_sum(float (&v)[N]) {
     for (int i = 0; i < N; ++i) v[i] += __shfl_xor_sync(0xffffffffu, v[i], o);
 }
 
-// Sums four values over the warp and gives every lane all four totals: an
-// xor butterfly, five rounds of four independent exchanges. The two lanes of
-// every exchange add the same two operands, so after each round a lane and
-// its partner hold bitwise equal partial sums, and at the end every lane
-// holds the same totals.
+// Sums four values over the warp and gives every lane all four totals.
+// BUTTERFLY: an xor butterfly, five rounds of four independent exchanges
+// (the two lanes of every exchange add the same two operands, so partners
+// hold bitwise equal partial sums after each round and every lane ends with
+// the same totals): the shortest dependent chain, for launches that leave the
+// GPU mostly idle. Else a transposed butterfly with half the exchanges (after
+// the xor-16 and xor-8 rounds each lane carries one of the four partial sums,
+// value 2*bit4 + bit3 of its lane id, three more xor rounds finish it, four
+// broadcasts hand it out): fewer instructions, for launches that fill it.
+template <bool BUTTERFLY>
 __device__ __forceinline__ void warp_sum4(float& a0, float& a1, float& a2, float& a3) {
+  if (BUTTERFLY) {
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const float b0 = __shfl_xor_sync(0xffffffffu, a0, o);
-    const float b1 = __shfl_xor_sync(0xffffffffu, a1, o);
-    const float b2 = __shfl_xor_sync(0xffffffffu, a2, o);
-    const float b3 = __shfl_xor_sync(0xffffffffu, a3, o);
-    a0 += b0;
-    a1 += b1;
-    a2 += b2;
-    a3 += b3;
+    for (int o = 16; o > 0; o >>= 1) {
+      const float b0 = __shfl_xor_sync(0xffffffffu, a0, o);
+      const float b1 = __shfl_xor_sync(0xffffffffu, a1, o);
+      const float b2 = __shfl_xor_sync(0xffffffffu, a2, o);
+      const float b3 = __shfl_xor_sync(0xffffffffu, a3, o);
+      a0 += b0;
+      a1 += b1;
+      a2 += b2;
+      a3 += b3;
+    }
+    return;
   }
+  const unsigned lane = threadIdx.x & 31u;
+  const bool h16 = lane & 16u, h8 = lane & 8u;
+  float k0 = h16 ? a2 : a0, k1 = h16 ? a3 : a1;
+  const float s0 = h16 ? a0 : a2, s1 = h16 ? a1 : a3;
+  k0 += __shfl_xor_sync(0xffffffffu, s0, 16);
+  k1 += __shfl_xor_sync(0xffffffffu, s1, 16);
+  float k = h8 ? k1 : k0;
+  k += __shfl_xor_sync(0xffffffffu, h8 ? k0 : k1, 8);
+  k += __shfl_xor_sync(0xffffffffu, k, 4);
+  k += __shfl_xor_sync(0xffffffffu, k, 2);
+  k += __shfl_xor_sync(0xffffffffu, k, 1);
+  a0 = __shfl_sync(0xffffffffu, k, 0);
+  a1 = __shfl_sync(0xffffffffu, k, 8);
+  a2 = __shfl_sync(0xffffffffu, k, 16);
+  a3 = __shfl_sync(0xffffffffu, k, 24);
 }
 
 // position = anchor (int) + offset (float)
@@ -323,6 +346,7 @@ constexpr float kPatRadius = 7.6158f;
 
 // One Gauss-Newton step (Eq. 4-5). Returns a VIO_TRACK_* status; `moved` is
 // the bound above on how far the step moved the pattern (level px).
+template <bool BUTTERFLY = false>
 __device__ __forceinline__ int gn_step(const Lv& L, const Tpl& T, int lane, const LanePts& P,
                                        Warp& W, float& moved) {
   float r0 = 0.f, r1 = 0.f, r2 = 0.f, r3 = 0.f;
@@ -358,7 +382,7 @@ __device__ __forceinline__ int gn_step(const Lv& L, const Tpl& T, int lane, cons
   // 52 x 255 otherwise), so the one reduction also tells every lane whether
   // any lane left the level
   if (!ok) r0 += 1e30f;
-  warp_sum4(r0, r1, r2, r3);
+  warp_sum4<BUTTERFLY>(r0, r1, r2, r3);
   if (r0 >= 1e29f) return VIO_TRACK_OOB_WARP;
   if (!(r0 > 0.f)) return VIO_TRACK_ZERO_MEAN;
   const float q = __fdividef(T.S, r0);
@@ -392,6 +416,7 @@ __device__ __forceinline__ Lv get_lv(const Geom& g, const Batch& b, int img, int
 // level whose template is invalid is skipped, except level 0; any warp
 // failure ends the track. last_step: how far the last Gauss-Newton step at
 // level 0 moved the pattern (bound of gn_step, level-0 px; 0 if none ran).
+template <bool BUTTERFLY = false>
 __device__ __forceinline__ int track_dir(const Geom& g, const Batch& src, int src_img,
                                          const Batch& dst, int dst_img, const Pos& p, Pos t0,
                                          float th0, int iters, int top, int lane, Pos& t_out,
@@ -415,7 +440,7 @@ __device__ __forceinline__ int track_dir(const Geom& g, const Batch& src, int sr
       const Lv D = get_lv(g, dst, dst_img, l);
       float moved = 0.f;
       for (int it = 0; it < iters; ++it) {
-        const int st = gn_step(D, T, lane, P, W, moved);
+        const int st = gn_step<BUTTERFLY>(D, T, lane, P, W, moved);
         if (st != VIO_TRACK_OK) return st;
       }
       if (l == 0) last_step = moved;
@@ -438,6 +463,7 @@ __device__ __forceinline__ int track_dir(const Geom& g, const Batch& src, int sr
 // over levels top..0, from warp (ix, iy, ith) if has_init, else from p.
 // Returns the status; tf/thf hold the forward result when it exists and
 // last_fwd the forward pass's last level-0 step (track_dir).
+template <bool BUTTERFLY = false>
 __device__ __forceinline__ int track_fb(const Geom& g, const Batch& src, int src_img,
                                         const Batch& dst, int dst_img, float px, float py,
                                         bool has_init, float ix, float iy, float ith,
@@ -450,8 +476,8 @@ __device__ __forceinline__ int track_fb(const Geom& g, const Batch& src, int src
     t0 = split(ix, iy);
     th0 = ith;
   }
-  int st = track_dir(g, src, src_img, dst, dst_img, p, t0, th0, cfg.gn_iters, top, lane, tf,
-                     thf, last_fwd);
+  int st = track_dir<BUTTERFLY>(g, src, src_img, dst, dst_img, p, t0, th0, cfg.gn_iters, top,
+                                lane, tf, thf, last_fwd);
   have = st == VIO_TRACK_OK;
   dist = __int_as_float(0x7fc00000);
   if (st == VIO_TRACK_OK && cfg.fb) {
@@ -459,8 +485,8 @@ __device__ __forceinline__ int track_fb(const Geom& g, const Batch& src, int src
     // start at the forward estimate's inverse (t = p, theta = -theta_f)
     Pos tb;
     float thb, last_b;
-    st = track_dir(g, dst, dst_img, src, src_img, tf, p, -thf, cfg.gn_iters, top, lane, tb,
-                   thb, last_b);
+    st = track_dir<BUTTERFLY>(g, dst, dst_img, src, src_img, tf, p, -thf, cfg.gn_iters, top,
+                              lane, tb, thb, last_b);
     if (st == VIO_TRACK_OK) {
       const float ex = (float)(tb.ax - p.ax) + (tb.dx - p.dx);
       const float ey = (float)(tb.ay - p.ay) + (tb.dy - p.dy);
