@@ -18,6 +18,12 @@
 // rotation, whose cosine, sine and the SE(2) left-Jacobian terms come from
 // their Taylor series for small angles (|phi| < 0.25, error < 1e-9), so a
 // Gauss-Newton step evaluates no trigonometric function.
+//
+// Every product that meets a sum is written as an explicit FMA (__fmaf_rn)
+// or an unfused product (__fmul_rn), so the rounding of each expression is
+// fixed in the source rather than by the compiler's contraction in each
+// kernel that inlines this code: all tracking kernels and launch shapes give
+// bit-identical results.
 #pragma once
 #include <math.h>
 
@@ -196,12 +202,12 @@ struct Chol {
   float i00, l10, l20, i11, l21, i22;   // i.. = 1 / l..
   __device__ __forceinline__ void solve(float b0, float b1, float b2, float& x0, float& x1,
                                         float& x2) const {
-    const float y0 = b0 * i00;
-    const float y1 = (b1 - l10 * y0) * i11;
-    const float y2 = (b2 - l20 * y0 - l21 * y1) * i22;
-    x2 = y2 * i22;
-    x1 = (y1 - l21 * x2) * i11;
-    x0 = (y0 - l10 * x1 - l20 * x2) * i00;
+    const float y0 = __fmul_rn(b0, i00);
+    const float y1 = __fmul_rn(__fmaf_rn(-l10, y0, b1), i11);
+    const float y2 = __fmul_rn(__fmaf_rn(-l21, y1, __fmaf_rn(-l20, y0, b2)), i22);
+    x2 = __fmul_rn(y2, i22);
+    x1 = __fmul_rn(__fmaf_rn(-l21, x2, y1), i11);
+    x0 = __fmul_rn(__fmaf_rn(-l20, x2, __fmaf_rn(-l10, x1, y0)), i00);
   }
 };
 
@@ -249,8 +255,8 @@ __device__ __forceinline__ int build_template(const Lv& L, const Pos& q, int l, 
   const bool ok = Qx - 7 >= 1 && Qx + 7 <= L.w - 3 && Qy - 7 >= 1 && Qy + 7 <= L.h - 3;
   if (!ok) return VIO_TRACK_OOB_TEMPLATE;   // same value in every lane
 
-  const float w00 = (1.f - fx) * (1.f - fy), w10 = fx * (1.f - fy);
-  const float w01 = (1.f - fx) * fy, w11 = fx * fy;
+  const float w00 = __fmul_rn(1.f - fx, 1.f - fy), w10 = __fmul_rn(fx, 1.f - fy);
+  const float w01 = __fmul_rn(1.f - fx, fy), w11 = __fmul_rn(fx, fy);
   float Jp[2][3];
   float acc[10];
 #pragma unroll
@@ -272,43 +278,44 @@ __device__ __forceinline__ int build_template(const Lv& L, const Pos& q, int l, 
                          ? 0.f
                          : (float)__ldg(base + (long long)r * L.pitch + cc);
       auto bl = [&](float a, float b, float c, float d) {
-        return w00 * a + w10 * b + w01 * c + w11 * d;
+        return __fmaf_rn(w11, d, __fmaf_rn(w01, c, __fmaf_rn(w10, b, __fmul_rn(w00, a))));
       };
       const float s = bl(t[1][1], t[1][2], t[2][1], t[2][2]);
-      const float gx = 0.5f * (bl(t[1][2], t[1][3], t[2][2], t[2][3]) -
-                               bl(t[1][0], t[1][1], t[2][0], t[2][1]));
-      const float gy = 0.5f * (bl(t[2][1], t[2][2], t[3][1], t[3][2]) -
-                               bl(t[0][1], t[0][2], t[1][1], t[1][2]));
+      const float gx = __fmul_rn(0.5f, bl(t[1][2], t[1][3], t[2][2], t[2][3]) -
+                                            bl(t[1][0], t[1][1], t[2][0], t[2][1]));
+      const float gy = __fmul_rn(0.5f, bl(t[2][1], t[2][2], t[3][1], t[3][2]) -
+                                            bl(t[0][1], t[0][2], t[1][1], t[1][2]));
       Jp[j][0] = gx;
       Jp[j][1] = gy;
-      Jp[j][2] = gy * u - gx * v;
+      const float jt = __fmaf_rn(-gx, v, __fmul_rn(gy, u));
+      Jp[j][2] = jt;
       acc[0] += s;
-      acc[1] += gx * gx;
-      acc[2] += gx * gy;
-      acc[3] += gx * Jp[j][2];
-      acc[4] += gy * gy;
-      acc[5] += gy * Jp[j][2];
-      acc[6] += Jp[j][2] * Jp[j][2];
-      acc[7] += gx * s;
-      acc[8] += gy * s;
-      acc[9] += Jp[j][2] * s;
+      acc[1] = __fmaf_rn(gx, gx, acc[1]);
+      acc[2] = __fmaf_rn(gx, gy, acc[2]);
+      acc[3] = __fmaf_rn(gx, jt, acc[3]);
+      acc[4] = __fmaf_rn(gy, gy, acc[4]);
+      acc[5] = __fmaf_rn(gy, jt, acc[5]);
+      acc[6] = __fmaf_rn(jt, jt, acc[6]);
+      acc[7] = __fmaf_rn(gx, s, acc[7]);
+      acc[8] = __fmaf_rn(gy, s, acc[8]);
+      acc[9] = __fmaf_rn(jt, s, acc[9]);
     }
   }
   warp_sum_t(acc);
   T.S = acc[0];
   if (!(acc[0] > 0.f)) return VIO_TRACK_ZERO_MEAN;
   // Cholesky of H'; a pivot <= 1e-9 trace marks a degenerate patch
-  const float eps = 1e-9f * (acc[1] + acc[4] + acc[6]);
+  const float eps = __fmul_rn(1e-9f, acc[1] + acc[4] + acc[6]);
   Chol C;
   if (!(acc[1] > eps)) return VIO_TRACK_DEGENERATE_H;
   C.i00 = rsqrtf(acc[1]);
-  C.l10 = acc[2] * C.i00;
-  C.l20 = acc[3] * C.i00;
-  const float d1 = acc[4] - C.l10 * C.l10;
+  C.l10 = __fmul_rn(acc[2], C.i00);
+  C.l20 = __fmul_rn(acc[3], C.i00);
+  const float d1 = __fmaf_rn(-C.l10, C.l10, acc[4]);
   if (!(d1 > eps)) return VIO_TRACK_DEGENERATE_H;
   C.i11 = rsqrtf(d1);
-  C.l21 = (acc[5] - C.l20 * C.l10) * C.i11;
-  const float d2 = acc[6] - C.l20 * C.l20 - C.l21 * C.l21;
+  C.l21 = __fmul_rn(__fmaf_rn(-C.l20, C.l10, acc[5]), C.i11);
+  const float d2 = __fmaf_rn(-C.l21, C.l21, __fmaf_rn(-C.l20, C.l20, acc[6]));
   if (!(d2 > eps)) return VIO_TRACK_DEGENERATE_H;
   C.i22 = rsqrtf(d2);
   C.solve(acc[7], acc[8], acc[9], T.c0, T.c1, T.c2);
@@ -327,11 +334,15 @@ struct Warp {
 // cos, sin, sin(phi)/phi and (1 - cos(phi))/phi of a small angle
 __device__ __forceinline__ void small_rot(float p, float& c, float& s, float& a, float& b) {
   if (fabsf(p) < 0.25f) {
-    const float p2 = p * p;
-    c = 1.f - p2 * (0.5f - p2 * (1.f / 24.f - p2 * (1.f / 720.f)));
-    a = 1.f - p2 * (1.f / 6.f - p2 * (1.f / 120.f - p2 * (1.f / 5040.f)));
-    s = p * a;
-    b = p * (0.5f - p2 * (1.f / 24.f - p2 * (1.f / 720.f - p2 * (1.f / 40320.f))));
+    const float p2 = __fmul_rn(p, p);
+    c = __fmaf_rn(-p2, __fmaf_rn(-p2, __fmaf_rn(-p2, 1.f / 720.f, 1.f / 24.f), 0.5f), 1.f);
+    a = __fmaf_rn(-p2, __fmaf_rn(-p2, __fmaf_rn(-p2, 1.f / 5040.f, 1.f / 120.f), 1.f / 6.f),
+                  1.f);
+    s = __fmul_rn(p, a);
+    b = __fmul_rn(p, __fmaf_rn(-p2,
+                               __fmaf_rn(-p2, __fmaf_rn(-p2, 1.f / 40320.f, 1.f / 720.f),
+                                         1.f / 24.f),
+                               0.5f));
   } else {
     sincosf(p, &s, &c);
     a = s / p;
@@ -357,8 +368,8 @@ __device__ __forceinline__ int gn_step(const Lv& L, const Tpl& T, int lane, cons
     const int i = lane + 32 * j;
     if (j == 0 || i < kNP) {
       const float u = P.u[j], v = P.v[j];
-      const float vx = W.cs * u - W.sn * v + W.t.dx;
-      const float vy = W.sn * u + W.cs * v + W.t.dy;
+      const float vx = __fmaf_rn(W.cs, u, __fmaf_rn(-W.sn, v, W.t.dx));
+      const float vy = __fmaf_rn(W.sn, u, __fmaf_rn(W.cs, v, W.t.dy));
       const float flx = floorf(vx), fly = floorf(vy);
       const int ix = W.t.ax + (int)flx, iy = W.t.ay + (int)fly;
       const float fx = vx - flx, fy = vy - fly;
@@ -367,12 +378,12 @@ __device__ __forceinline__ int gn_step(const Lv& L, const Tpl& T, int lane, cons
         const uint8_t* p = L.p + (long long)iy * L.pitch + ix;
         const float a = __ldg(p), b = __ldg(p + 1);
         const float c = __ldg(p + L.pitch), d = __ldg(p + L.pitch + 1);
-        const float top = a + fx * (b - a), bot = c + fx * (d - c);
-        const float r = top + fy * (bot - top);
+        const float top = __fmaf_rn(fx, b - a, a), bot = __fmaf_rn(fx, d - c, c);
+        const float r = __fmaf_rn(fy, bot - top, top);
         r0 += r;
-        r1 += T.K[j][0] * r;
-        r2 += T.K[j][1] * r;
-        r3 += T.K[j][2] * r;
+        r1 = __fmaf_rn(T.K[j][0], r, r1);
+        r2 = __fmaf_rn(T.K[j][1], r, r2);
+        r3 = __fmaf_rn(T.K[j][2], r, r3);
       } else {
         ok = false;
       }
@@ -386,20 +397,21 @@ __device__ __forceinline__ int gn_step(const Lv& L, const Tpl& T, int lane, cons
   if (r0 >= 1e29f) return VIO_TRACK_OOB_WARP;
   if (!(r0 > 0.f)) return VIO_TRACK_ZERO_MEAN;
   const float q = __fdividef(T.S, r0);
-  const float d0 = T.c0 - q * r1;
-  const float d1 = T.c1 - q * r2;
-  const float d2 = T.c2 - q * r3;
+  const float d0 = __fmaf_rn(-q, r1, T.c0);
+  const float d1 = __fmaf_rn(-q, r2, T.c1);
+  const float d2 = __fmaf_rn(-q, r3, T.c2);
   // a NaN or an infinity in any component fails the (finite) comparison
   if (!(fabsf(d0) + fabsf(d1) + fabsf(d2) < 3.0e38f)) return VIO_TRACK_NAN;
-  moved = fabsf(d0) + fabsf(d1) + kPatRadius * fabsf(d2);
+  moved = __fmaf_rn(kPatRadius, fabsf(d2), fabsf(d0) + fabsf(d1));
   // T <- T o exp(delta): t += R V(d2) (d0, d1), R <- R R(d2)
   float cd, sd, a, b;
   small_rot(d2, cd, sd, a, b);
-  const float vx = a * d0 - b * d1, vy = b * d0 + a * d1;
-  W.t.dx += W.cs * vx - W.sn * vy;
-  W.t.dy += W.sn * vx + W.cs * vy;
-  const float cs = W.cs * cd - W.sn * sd;
-  const float sn = W.sn * cd + W.cs * sd;
+  const float vx = __fmaf_rn(-b, d1, __fmul_rn(a, d0));
+  const float vy = __fmaf_rn(a, d1, __fmul_rn(b, d0));
+  W.t.dx = __fmaf_rn(W.cs, vx, __fmaf_rn(-W.sn, vy, W.t.dx));
+  W.t.dy = __fmaf_rn(W.sn, vx, __fmaf_rn(W.cs, vy, W.t.dy));
+  const float cs = __fmaf_rn(-W.sn, sd, __fmul_rn(W.cs, cd));
+  const float sn = __fmaf_rn(W.cs, sd, __fmul_rn(W.sn, cd));
   W.cs = cs;
   W.sn = sn;
   W.th += d2;
@@ -490,7 +502,7 @@ __device__ __forceinline__ int track_fb(const Geom& g, const Batch& src, int src
     if (st == VIO_TRACK_OK) {
       const float ex = (float)(tb.ax - p.ax) + (tb.dx - p.dx);
       const float ey = (float)(tb.ay - p.ay) + (tb.dy - p.dy);
-      dist = sqrtf(ex * ex + ey * ey);
+      dist = sqrtf(__fmaf_rn(ey, ey, __fmul_rn(ex, ex)));
       if (dist > cfg.fb_max_dist) st = VIO_TRACK_FB_FAIL;
     }
   }

@@ -220,3 +220,32 @@ def test_batch_with_initnet_equals_streams_alone():
         _run_batch(b, seqs, schedule, stream=s)
     s.synchronize()
     _check_equal(b, groups, seqs, schedule, net)
+
+
+@pytest.mark.parametrize("learned", [False, True])
+def test_batch_filling_the_gpu_equals_streams_alone(learned):
+    """A batch with more keypoints than 16 per SM tracks them with the
+    reduction form for launches that fill the GPU; a stream alone is a small
+    launch, tracked with the other form (trk::warp_sum4): the lists agree bit
+    for bit, the learned start's kept and rejected first passes included."""
+    w, h, cell, L = 376, 240, 37, 4
+    cells = (w // cell) * (h // cell)
+    cap = 2 * cells
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    n = 16 * sms // (2 * cap + cells) + 1
+    p = vio.default_params(n_levels=L, cell_w=cell, cell_h=cell)
+    groups = [(p, w, h, n, cap)]
+    seqs = [[synth.make_sequence(6100 + s, N_FRAMES, w, h, 1, max_motion=6.0,
+                                 tex_size=1024).frames for s in range(n)]]
+    net = None
+    if learned:
+        rng = np.random.default_rng(7)
+        flat = (rng.normal(0, 0.05, vio.INITNET_N_PARAMS)).astype(np.float32)
+        flat[-1] = 3.0                               # confident proposals
+        net = vio.InitNet(flat, 1, 2, 1, 0.5)
+    b = vio.Batch(groups)
+    if net is not None:
+        b.set_initnet(net)
+    schedule = [[1] * n for _ in range(N_FRAMES)]
+    _run_batch(b, seqs, schedule)
+    _check_equal(b, groups, seqs, schedule, net)
