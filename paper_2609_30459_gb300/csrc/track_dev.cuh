@@ -351,6 +351,11 @@ __device__ __forceinline__ void small_rot(float p, float& c, float& s, float& a,
   }
 }
 
+// 1.5 * 2^23 and its bit pattern: v + kFloorBias rounded toward -inf is
+// kFloorBias + floor(v) on the integer grid of [2^23, 2^24).
+constexpr float kFloorBias = 12582912.f;
+constexpr int kFloorBiasBits = 0x4B400000;
+
 // Radius of the pattern's outermost point (7, 3): an increment (dx, dy, dth)
 // moves no pattern point by more than |dx| + |dy| + kPatRadius |dth| px.
 constexpr float kPatRadius = 7.6158f;
@@ -370,9 +375,13 @@ __device__ __forceinline__ int gn_step(const Lv& L, const Tpl& T, int lane, cons
       const float u = P.u[j], v = P.v[j];
       const float vx = __fmaf_rn(W.cs, u, __fmaf_rn(-W.sn, v, W.t.dx));
       const float vy = __fmaf_rn(W.sn, u, __fmaf_rn(W.cs, v, W.t.dy));
-      const float flx = floorf(vx), fly = floorf(vy);
-      const int ix = W.t.ax + (int)flx, iy = W.t.ay + (int)fly;
-      const float fx = vx - flx, fy = vy - fly;
+      // floor without a conversion instruction: adding 1.5 * 2^23 rounded
+      // down leaves floor(v) in the low mantissa bits (exact for |v| < 2^22;
+      // beyond that the sample is outside the level either way)
+      const float tx = __fadd_rd(vx, kFloorBias), ty = __fadd_rd(vy, kFloorBias);
+      const int ix = W.t.ax + (__float_as_int(tx) - kFloorBiasBits);
+      const int iy = W.t.ay + (__float_as_int(ty) - kFloorBiasBits);
+      const float fx = vx - (tx - kFloorBias), fy = vy - (ty - kFloorBias);
       // 0 <= y < w - 1 on the integer part: 0 <= ix <= w - 2 (one unsigned test)
       if ((unsigned)ix <= xmax && (unsigned)iy <= ymax) {
         const uint8_t* p = L.p + (long long)iy * L.pitch + ix;
