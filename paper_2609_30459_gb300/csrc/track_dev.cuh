@@ -384,7 +384,8 @@ __device__ __forceinline__ int gn_step(const Lv& L, const Tpl& T, int lane, cons
       const float fx = vx - (tx - kFloorBias), fy = vy - (ty - kFloorBias);
       // 0 <= y < w - 1 on the integer part: 0 <= ix <= w - 2 (one unsigned test)
       if ((unsigned)ix <= xmax && (unsigned)iy <= ymax) {
-        const uint8_t* p = L.p + (long long)iy * L.pitch + ix;
+        // (iy, ix) inside the level: a 32-bit offset
+        const uint8_t* p = L.p + (unsigned)(iy * L.pitch + ix);
         const float a = __ldg(p), b = __ldg(p + 1);
         const float c = __ldg(p + L.pitch), d = __ldg(p + L.pitch + 1);
         const float top = __fmaf_rn(fx, b - a, a), bot = __fmaf_rn(fx, d - c, c);
@@ -403,15 +404,18 @@ __device__ __forceinline__ int gn_step(const Lv& L, const Tpl& T, int lane, cons
   // any lane left the level
   if (!ok) r0 += 1e30f;
   warp_sum4<BUTTERFLY>(r0, r1, r2, r3);
-  if (r0 >= 1e29f) return VIO_TRACK_OOB_WARP;
-  if (!(r0 > 0.f)) return VIO_TRACK_ZERO_MEAN;
+  // the increment before its checks, so that one branch takes all three
+  // failures (in this order): a sample outside the level, a non-positive
+  // mean, a non-finite increment (a NaN or an infinity in any component
+  // fails the finite comparison)
   const float q = __fdividef(T.S, r0);
   const float d0 = __fmaf_rn(-q, r1, T.c0);
   const float d1 = __fmaf_rn(-q, r2, T.c1);
   const float d2 = __fmaf_rn(-q, r3, T.c2);
-  // a NaN or an infinity in any component fails the (finite) comparison
-  if (!(fabsf(d0) + fabsf(d1) + fabsf(d2) < 3.0e38f)) return VIO_TRACK_NAN;
-  moved = __fmaf_rn(kPatRadius, fabsf(d2), fabsf(d0) + fabsf(d1));
+  const float s01 = fabsf(d0) + fabsf(d1);
+  if (!(r0 < 1e29f && r0 > 0.f && s01 + fabsf(d2) < 3.0e38f))
+    return r0 >= 1e29f ? VIO_TRACK_OOB_WARP : !(r0 > 0.f) ? VIO_TRACK_ZERO_MEAN : VIO_TRACK_NAN;
+  moved = __fmaf_rn(kPatRadius, fabsf(d2), s01);
   // T <- T o exp(delta): t += R V(d2) (d0, d1), R <- R R(d2)
   float cd, sd, a, b;
   small_rot(d2, cd, sd, a, b);
