@@ -83,10 +83,12 @@ constexpr bool pattern_rows_match() {
 }
 static_assert(pattern_rows_match(), "row form of the pattern");
 
-// The lane's two pattern points (the second exists for lanes 0..19).
+// The lane's two pattern points (the second exists for lanes 0..19; lanes
+// 20..31 evaluate the pattern's centre there, with weight w1 = 0).
 struct LanePts {
   int iu[2], iv[2];
   float u[2], v[2];
+  float w1;
 };
 __device__ __forceinline__ LanePts lane_points(int lane) {
   LanePts P;
@@ -100,6 +102,7 @@ __device__ __forceinline__ LanePts lane_points(int lane) {
     P.u[j] = (float)u;
     P.v[j] = (float)v;
   }
+  P.w1 = lane + 32 < kNP ? 1.f : 0.f;
   return P;
 }
 
@@ -368,10 +371,13 @@ __device__ __forceinline__ int gn_step(const Lv& L, const Tpl& T, int lane, cons
   float r0 = 0.f, r1 = 0.f, r2 = 0.f, r3 = 0.f;
   bool ok = true;
   const unsigned xmax = (unsigned)(L.w - 2), ymax = (unsigned)(L.h - 2);
+  // no branch in the loop: a lane without a second point evaluates the
+  // pattern's centre with weight 0 (its K is 0 too); it lies inside the
+  // level whenever the pattern's points do. A sample outside the level is
+  // read at the clamped position and only clears `ok`.
 #pragma unroll
   for (int j = 0; j < 2; ++j) {
-    const int i = lane + 32 * j;
-    if (j == 0 || i < kNP) {
+    {
       const float u = P.u[j], v = P.v[j];
       const float vx = __fmaf_rn(W.cs, u, __fmaf_rn(-W.sn, v, W.t.dx));
       const float vy = __fmaf_rn(W.sn, u, __fmaf_rn(W.cs, v, W.t.dy));
@@ -383,19 +389,18 @@ __device__ __forceinline__ int gn_step(const Lv& L, const Tpl& T, int lane, cons
       const int iy = W.t.ay + (__float_as_int(ty) - kFloorBiasBits);
       const float fx = vx - (tx - kFloorBias), fy = vy - (ty - kFloorBias);
       // 0 <= y < w - 1 on the integer part: 0 <= ix <= w - 2 (one unsigned test)
-      if ((unsigned)ix <= xmax && (unsigned)iy <= ymax) {
-        // (iy, ix) inside the level: a 32-bit offset
-        const uint8_t* p = L.p + (unsigned)(iy * L.pitch + ix);
+      {
+        ok = ok && (unsigned)ix <= xmax && (unsigned)iy <= ymax;
+        const unsigned cx = min((unsigned)ix, xmax), cy = min((unsigned)iy, ymax);
+        const uint8_t* p = L.p + (cy * (unsigned)L.pitch + cx);
         const float a = __ldg(p), b = __ldg(p + 1);
         const float c = __ldg(p + L.pitch), d = __ldg(p + L.pitch + 1);
         const float top = __fmaf_rn(fx, b - a, a), bot = __fmaf_rn(fx, d - c, c);
         const float r = __fmaf_rn(fy, bot - top, top);
-        r0 += r;
+        r0 = j == 0 ? r0 + r : __fmaf_rn(P.w1, r, r0);
         r1 = __fmaf_rn(T.K[j][0], r, r1);
         r2 = __fmaf_rn(T.K[j][1], r, r2);
         r3 = __fmaf_rn(T.K[j][2], r, r3);
-      } else {
-        ok = false;
       }
     }
   }
