@@ -6,7 +6,8 @@
 // collective from divergent lanes stops with "EMU DEADLOCK" instead of
 // hanging; __syncthreads_or too. Integer and bit intrinsics (__byte_perm,
 // __vminu2, __vmaxu2, __popc, __ffs, __funnelshift_r, __fmaf_rn, atomicMax,
-// atomicExch) are plain host functions.
+// atomicExch) are plain host functions, as are the float intrinsics of the
+// tracker (__fmul_rn, __fadd_rd, rsqrtf, __fdividef).
 #pragma once
 #include <cuda_runtime.h>
 #include <algorithm>
@@ -128,6 +129,17 @@ inline float __uint_as_float(unsigned u) { float f; memcpy(&f, &u, 4); return f;
 inline float __int_as_float(int u) { float f; memcpy(&f, &u, 4); return f; }
 inline unsigned __float_as_uint(float f) { unsigned u; memcpy(&u, &f, 4); return u; }
 inline float __fmaf_rn(float a, float b, float c) { return std::fma(a, b, c); }
+inline float __fmul_rn(float a, float b) { return a * b; }
+inline int __float_as_int(float f) { int u; memcpy(&u, &f, 4); return u; }
+// a + b rounded toward -inf: the nearest sum, stepped down when the exact
+// rounding error (TwoSum) shows it above the exact sum
+inline float __fadd_rd(float a, float b) {
+  const float s = a + b, bb = s - a;
+  const float err = (a - (s - bb)) + (b - bb);
+  return err < 0.f ? std::nextafter(s, -INFINITY) : s;
+}
+inline float rsqrtf(float x) { return 1.0f / std::sqrt(x); }
+inline float __fdividef(float a, float b) { return a / b; }
 inline unsigned __funnelshift_r(unsigned lo, unsigned hi, unsigned sh) {
   sh &= 31; return sh ? (lo >> sh) | (hi << (32 - sh)) : lo; }
 inline size_t __cvta_generic_to_shared(const void*) { fprintf(stderr, "cvta on the host\n"); std::abort(); }

@@ -1,7 +1,7 @@
-"""The pyramid, detection and tensor-core network device code run on the
-host (no GPU) under AddressSanitizer, against the oracle: the check that
-stands in for a bounds checking build and for compute-sanitizer, which is
-closed on the GPU pool.
+"""The pyramid, detection, tracker and tensor-core network device code run
+on the host (no GPU) under AddressSanitizer, against the oracle: the check
+that stands in for a bounds checking build and for compute-sanitizer, which
+is closed on the GPU pool.
 
 tests/emu/blockemu.h emulates thread blocks with one host thread per CUDA
 thread and real barriers for __syncthreads, named barriers and the warp
@@ -37,7 +37,7 @@ PYR_DETECT = os.path.join(ROOT, "oracle", "src", "pyramid_detect.cpp")
 def _host_copy(dst):
     shutil.copy(os.path.join(EMU, "tc05_emu.h"), os.path.join(dst, "tc05.cuh"))
     for name in ("common.cuh", "pyramid_dev.cuh", "detect_dev.cuh", "initnet_dev.cuh",
-                 "initnet_tc.cuh"):
+                 "initnet_tc.cuh", "track_dev.cuh"):
         s = open(os.path.join(CSRC, name)).read()
         s = re.sub(r'asm volatile\("bar\.sync (\d), %0;" ::"r"\(n\) : "memory"\);',
                    r"emu_bar(\1, n);", s)
@@ -132,3 +132,63 @@ def test_initnet_tc_forward_on_host(tmp_path, n, blocks):
     assert np.all(err[:, :2] <= 16 * tol), err.max(0)
     assert np.all(err[:, 2] <= tol / 4), err.max(0)
     assert np.median(err[:, :2]) < 16 * 1e-4
+
+
+def test_tracker_on_host(tmp_path):
+    """The tracker's device code (templates, branch-free Gauss-Newton steps
+    with clamped reads, the forward-backward check) on the host, every
+    pyramid level between poisoned gaps so that AddressSanitizer reports any
+    read outside a level, against the FP64 oracle at the GPU parity tests'
+    bounds: detected keypoints, keypoints at and beyond the borders, starts
+    near the answer and far from it."""
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
+    import parity_util
+    from paper_2609_30459_gb300 import synth
+    oracle.build()
+    w, h, L, iters, fbm = 200, 152, 3, 5, 0.5
+    seq = synth.make_sequence(7100, 2, w, h, 1, max_motion=6.0, tex_size=1024)
+    src = oracle.pyramid(seq.frames[0, 0], L)
+    dst = oracle.pyramid(seq.frames[1, 0], L)
+    det, _ = oracle.detect_grid(seq.frames[0, 0], 25, 19, k=1)
+    border = np.array([[1, 1], [3, 70], [195, 70], [100, 149], [100.5, 2.25], [198.9, 150.9],
+                       [12.25, 12.75], [187.5, 139.5], [7.5, 70], [8.0, 40], [70, 7.5],
+                       [189.5, 100], [100, 141.5]], np.float32)
+    pts = np.concatenate([det, border]).astype(np.float32)
+    plain = oracle.track(src, dst, pts, gn_iters=iters, fb_max_dist=fbm)
+    # starts: the plain answer (a start at the optimum) for the first eight
+    # detections and a start 11 px off for the next eight
+    m = len(det)
+    init = np.zeros((len(pts), 3), np.float32)
+    has = np.zeros(len(pts), bool)
+    init[:8, :2] = plain["warp"][:8, :2]
+    has[:8] = plain["status"][:8] == 0
+    init[8:16, :2] = pts[8:16] + np.array([9.0, -7.0], np.float32)
+    has[8:16] = True
+    cases = [(pts, None, np.zeros(len(pts), bool)),
+             (pts[:16][has[:16]], init[:16][has[:16]], np.ones(int(has[:16].sum()), bool))]
+    inp, outp = tmp_path / "in.bin", tmp_path / "out.bin"
+    exe = _build(tmp_path, "trk_check")
+    compared = 0
+    for P, ini, flag in cases:
+        with open(inp, "wb") as f:
+            f.write(np.array([L, len(P), iters], np.int32).tobytes())
+            f.write(np.array([fbm], np.float32).tobytes())
+            for l in range(L):
+                f.write(np.array(src[l].shape[::-1], np.int32).tobytes())
+                f.write(np.ascontiguousarray(src[l], np.uint8).tobytes())
+                f.write(np.ascontiguousarray(dst[l], np.uint8).tobytes())
+            rec = np.zeros((len(P), 5), np.float32)
+            rec[:, :2] = P
+            if ini is not None:
+                rec[:, 2:4] = ini[:, :2]
+            rec[:, 4] = flag
+            f.write(rec.tobytes())
+        _run(exe, inp, outp, timeout=900, expect="points")
+        got = np.fromfile(outp, np.float32).reshape(-1, 5)
+        ref = oracle.track(src, dst, P, init=ini, gn_iters=iters, fb_max_dist=fbm)
+        st = parity_util.compare_tracks(got[:, 1:3], got[:, 0].astype(np.uint8), ref, fbm,
+                                        g_theta=got[:, 3])
+        compared += len(P)
+        assert (got[:, 0] == 0).sum() >= len(P) // 3, got[:, 0]
+    assert compared >= m + 8
