@@ -625,11 +625,11 @@ def frontend_config_run(torch, vio, name, w, h, n_streams, levels, cw, ch, n_fra
     stats, _ = fe.read_stats()
     idx = [(steps0 + k) % vio.STATS_RING for k in range(steps)]
     st = stats[idx].astype(np.int64)
-    fe.set_timing(True)
+    fe.set_timing(2)              # each step's first and last event only
     fe.reset()
     for t in range(min(steps, 200)):
         fe.step(frames[order[t % len(order)]])
-    stage_ms, n_t, step_ms = fe.read_timing(max_steps=200)
+    _, n_t, step_ms = fe.read_timing(max_steps=200)
     fe.close()
     pd = None
     if roofline is not None:       # all frames of all cameras as one detection batch
@@ -1084,19 +1084,27 @@ def main():
             dist.barrier()
     total_s = ev0.elapsed_time(ev1) / 1000.0
     stats, steps_after = fe.read_stats()
-    # per-step latency and per-stage times: a separate pass with CUDA events
-    # at every stage boundary (the events themselves cost a little per step,
-    # so the throughput above is taken without them)
+    # per-stage times: a separate pass with CUDA events at every stage
+    # boundary; per-step latency: another with only each step's first and
+    # last event (events between launches cancel the tracking -> finalisation
+    # overlap); steps in order, each after the previous one ended (the
+    # throughput above is taken without events)
     n_lat = min(args.steps, 1000)
-    fe.reset()
-    fe.set_timing(True)
-    left = n_lat
-    while left > 0:
-        n = min(N_FRAMES, left)
-        fe.run(frames5[:n])
-        left -= n
-    stage_ms, n_timed, step_ms = fe.read_timing(max_steps=n_lat)
-    fe.set_timing(False)
+
+    def timed_pass(mode):
+        fe.reset()
+        fe.set_timing(mode)
+        left = n_lat
+        while left > 0:
+            n = min(N_FRAMES, left)
+            fe.run(frames5[:n])
+            left -= n
+        out = fe.read_timing(max_steps=n_lat)
+        fe.set_timing(False)
+        return out
+
+    stage_ms, n_timed, stage_step_ms = timed_pass(1)
+    _, _, step_ms = timed_pass(2)
     idx = [(steps_before + k) % vio.STATS_RING for k in range(args.steps)]
     st = stats[idx, 0, :].astype(np.int64)                       # (K, 7)
     tracked = int(st[:, 0].sum() + st[:, 1].sum())

@@ -443,11 +443,15 @@ struct vio_batch_tune_s;
 vio_status vio_frontend_set_tune(vio_frontend* fe, const struct vio_batch_tune_s* t);
 
 /* Stage timing (the paper's per-stage GPU timestamps, Sec. IV-B, Fig. 5).
- * While enabled, every step records CUDA events on its stream at the stage
- * boundaries: 0 pyramid levels 1-4 and the per-cell detection candidates
- * (one launch), 1 deeper pyramid levels, 2 learned flow proposals (when the
- * initializer is on), 3 temporal tracking and stereo matching (one launch),
- * 4 finalisation (survivors, per-cell selection, appends).
+ * enable: 0 off; 1: every step records CUDA events on its stream at the
+ * stage boundaries; 2: only its first and last event (a step's latency with
+ * its launches as in an untimed step: events between launches break the
+ * overlap of a programmatic dependent with its predecessor; stage_ms then
+ * stays 0 for those steps); other values VIO_ERR_INVALID_ARG. Stages: 0
+ * pyramid levels 1-4 and the per-cell detection candidates (one launch), 1
+ * deeper pyramid levels, 2 learned flow proposals (when the initializer is
+ * on), 3 temporal tracking and stereo matching (one launch), 4 finalisation
+ * (survivors, per-cell selection, appends).
  * vio_frontend_read_timing waits for the recorded events, adds each stage's
  * elapsed milliseconds into stage_ms[0..VIO_N_STAGES-1] (overwritten), stores
  * the number of timed steps in *n_steps and clears the record. Enabling,

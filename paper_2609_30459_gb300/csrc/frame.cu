@@ -1065,7 +1065,7 @@ cudaError_t launch_frames(const FrameLaunch* fl, int n_groups, const FrameTune& 
                           cudaStream_t s, cudaEvent_t* marks, int part) {
   if (n_groups < 1 || n_groups > kMaxGroups) return cudaErrorInvalidValue;
   auto mark = [&](int i) {
-    if (marks) cudaEventRecord(marks[i], s);
+    if (marks && marks[i]) cudaEventRecord(marks[i], s);
   };
 
   cudaError_t e = cudaSuccess;

@@ -63,7 +63,7 @@ struct vio_frontend {
   int32_t prev_pitch;
   int64_t prev_stride;
   int64_t steps;
-  bool timing;
+  int timing;   // 0 off, 1 every stage boundary, 2 first and last event of a step
   std::vector<cudaEvent_t> ev_free;
   std::vector<std::array<cudaEvent_t, VIO_N_STAGES + 1>> ev_rec;
 };
@@ -198,7 +198,7 @@ extern "C" vio_status vio_frontend_create(vio_frontend** out, const vio_params* 
   fe->prev_pitch = 0;
   fe->prev_stride = 0;
   fe->steps = 0;
-  fe->timing = false;
+  fe->timing = 0;
   *out = fe;
   return VIO_OK;
 }
@@ -437,8 +437,9 @@ extern "C" vio_status vio_frontend_step(vio_frontend* fe, const uint8_t* d_frame
   if (!caller_enter(fe, s)) return VIO_ERR_CUDA;
   std::array<cudaEvent_t, VIO_N_STAGES + 1> ev{};
   if (fe->timing)
-    for (auto& e : ev)
-      if (!(e = take_event(fe))) return VIO_ERR_CUDA;
+    for (int i = 0; i <= VIO_N_STAGES; ++i)
+      if ((fe->timing == 1 || i == 0 || i == VIO_N_STAGES) && !(ev[i] = take_event(fe)))
+        return VIO_ERR_CUDA;
   if (launch_frames(&f, 1, fe->tune, s, fe->timing ? ev.data() : nullptr) != cudaSuccess)
     return VIO_ERR_CUDA;
   if (fe->timing) fe->ev_rec.push_back(ev);
@@ -566,7 +567,8 @@ extern "C" vio_status vio_frontend_run(vio_frontend* fe, const uint8_t* d_frames
 
 extern "C" vio_status vio_frontend_set_timing(vio_frontend* fe, int32_t enable) {
   if (!fe) return VIO_ERR_INVALID_ARG;
-  fe->timing = enable != 0;
+  if (enable < 0 || enable > 2) return VIO_ERR_INVALID_ARG;
+  fe->timing = enable;
   return VIO_OK;
 }
 
@@ -581,7 +583,8 @@ extern "C" vio_status vio_frontend_read_timing(vio_frontend* fe, double* stage_m
     if (cudaEventSynchronize(row[VIO_N_STAGES]) != cudaSuccess) st = VIO_ERR_CUDA;
     for (int i = 0; i < VIO_N_STAGES; ++i) {
       float ms = 0.f;
-      if (cudaEventElapsedTime(&ms, row[i], row[i + 1]) == cudaSuccess) stage_ms[i] += ms;
+      if (row[i] && row[i + 1] && cudaEventElapsedTime(&ms, row[i], row[i + 1]) == cudaSuccess)
+        stage_ms[i] += ms;
     }
     if (step_ms && k < step_ms_cap) {
       float ms = 0.f;
@@ -589,7 +592,8 @@ extern "C" vio_status vio_frontend_read_timing(vio_frontend* fe, double* stage_m
       step_ms[k] = ms;
     }
     ++k;
-    for (cudaEvent_t e : row) fe->ev_free.push_back(e);
+    for (cudaEvent_t e : row)
+      if (e) fe->ev_free.push_back(e);
   }
   *n_steps = (int64_t)fe->ev_rec.size();
   fe->ev_rec.clear();

@@ -710,8 +710,10 @@ class Frontend:
                                                ctypes.byref(net.cfg) if net else None),
                "vio_frontend_set_initnet")
 
-    def set_timing(self, enable: bool):
-        _check(load().vio_frontend_set_timing(self.handle, 1 if enable else 0), "set_timing")
+    def set_timing(self, enable):
+        """False/0 off, True/1 events at every stage boundary, 2 only the first
+        and last event of each step (vio_frontend_set_timing)."""
+        _check(load().vio_frontend_set_timing(self.handle, int(enable)), "set_timing")
 
     def read_timing(self, max_steps: int = 0):
         """(summed per-stage ms, number of timed steps, per-step ms list) of the

@@ -248,6 +248,18 @@ def test_frontend_run_equals_steps():
         assert torch.equal(va["track_id"][0, c, :nc], vb["track_id"][0, c, :nc])
     stats, steps = b.read_stats()
     assert steps == 6 and stats[5, 0, 4] == int(vb["new_count"][0])
+    # step-only timing: the same lists, per-step times, no stage times
+    c = vio.Frontend(p, w, h, 1, cap)
+    c.set_timing(2)
+    c.run(frames)
+    torch.cuda.synchronize()
+    stage_ms, n, per_step = c.read_timing(max_steps=6)
+    assert n == 6 and all(x > 0 for x in per_step) and all(v == 0 for v in stage_ms.values())
+    vc = c.view()
+    assert torch.equal(va["track_count"], vc["track_count"])
+    for cam, nc in ((0, n0), (1, n1)):
+        assert torch.equal(va["track_xy"][0, cam, :nc], vc["track_xy"][0, cam, :nc])
+    c.close()
 
 
 # ------------------------------------------------ learned start of tracking ---
