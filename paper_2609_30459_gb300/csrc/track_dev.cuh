@@ -377,32 +377,28 @@ __device__ __forceinline__ int gn_step(const Lv& L, const Tpl& T, int lane, cons
   // read at the clamped position and only clears `ok`.
 #pragma unroll
   for (int j = 0; j < 2; ++j) {
-    {
-      const float u = P.u[j], v = P.v[j];
-      const float vx = __fmaf_rn(W.cs, u, __fmaf_rn(-W.sn, v, W.t.dx));
-      const float vy = __fmaf_rn(W.sn, u, __fmaf_rn(W.cs, v, W.t.dy));
-      // floor without a conversion instruction: adding 1.5 * 2^23 rounded
-      // down leaves floor(v) in the low mantissa bits (exact for |v| < 2^22;
-      // beyond that the sample is outside the level either way)
-      const float tx = __fadd_rd(vx, kFloorBias), ty = __fadd_rd(vy, kFloorBias);
-      const int ix = W.t.ax + (__float_as_int(tx) - kFloorBiasBits);
-      const int iy = W.t.ay + (__float_as_int(ty) - kFloorBiasBits);
-      const float fx = vx - (tx - kFloorBias), fy = vy - (ty - kFloorBias);
-      // 0 <= y < w - 1 on the integer part: 0 <= ix <= w - 2 (one unsigned test)
-      {
-        ok = ok && (unsigned)ix <= xmax && (unsigned)iy <= ymax;
-        const unsigned cx = min((unsigned)ix, xmax), cy = min((unsigned)iy, ymax);
-        const uint8_t* p = L.p + (cy * (unsigned)L.pitch + cx);
-        const float a = __ldg(p), b = __ldg(p + 1);
-        const float c = __ldg(p + L.pitch), d = __ldg(p + L.pitch + 1);
-        const float top = __fmaf_rn(fx, b - a, a), bot = __fmaf_rn(fx, d - c, c);
-        const float r = __fmaf_rn(fy, bot - top, top);
-        r0 = j == 0 ? r0 + r : __fmaf_rn(P.w1, r, r0);
-        r1 = __fmaf_rn(T.K[j][0], r, r1);
-        r2 = __fmaf_rn(T.K[j][1], r, r2);
-        r3 = __fmaf_rn(T.K[j][2], r, r3);
-      }
-    }
+    const float u = P.u[j], v = P.v[j];
+    const float vx = __fmaf_rn(W.cs, u, __fmaf_rn(-W.sn, v, W.t.dx));
+    const float vy = __fmaf_rn(W.sn, u, __fmaf_rn(W.cs, v, W.t.dy));
+    // floor without a conversion instruction: adding 1.5 * 2^23 rounded
+    // down leaves floor(v) in the low mantissa bits (exact for |v| < 2^22;
+    // beyond that the sample is outside the level either way)
+    const float tx = __fadd_rd(vx, kFloorBias), ty = __fadd_rd(vy, kFloorBias);
+    const int ix = W.t.ax + (__float_as_int(tx) - kFloorBiasBits);
+    const int iy = W.t.ay + (__float_as_int(ty) - kFloorBiasBits);
+    const float fx = vx - (tx - kFloorBias), fy = vy - (ty - kFloorBias);
+    // 0 <= y < w - 1 on the integer part: 0 <= ix <= w - 2 (one unsigned test)
+    ok = ok && (unsigned)ix <= xmax && (unsigned)iy <= ymax;
+    const unsigned cx = min((unsigned)ix, xmax), cy = min((unsigned)iy, ymax);
+    const uint8_t* p = L.p + (cy * (unsigned)L.pitch + cx);
+    const float a = __ldg(p), b = __ldg(p + 1);
+    const float c = __ldg(p + L.pitch), d = __ldg(p + L.pitch + 1);
+    const float top = __fmaf_rn(fx, b - a, a), bot = __fmaf_rn(fx, d - c, c);
+    const float r = __fmaf_rn(fy, bot - top, top);
+    r0 = j == 0 ? r0 + r : __fmaf_rn(P.w1, r, r0);
+    r1 = __fmaf_rn(T.K[j][0], r, r1);
+    r2 = __fmaf_rn(T.K[j][1], r, r2);
+    r3 = __fmaf_rn(T.K[j][2], r, r3);
   }
   // a sample outside the level adds 1e30 to the sum of intensities (at most
   // 52 x 255 otherwise), so the one reduction also tells every lane whether
