@@ -6,8 +6,8 @@
 // collective from divergent lanes stops with "EMU DEADLOCK" instead of
 // hanging; __syncthreads_or too. Integer and bit intrinsics (__byte_perm,
 // __vminu2, __vmaxu2, __popc, __ffs, __funnelshift_r, __fmaf_rn, atomicMax,
-// atomicExch) are plain host functions, as are the float intrinsics of the
-// tracker (__fmul_rn, __fadd_rd, rsqrtf, __fdividef).
+// atomicExch, atomicAdd) are plain host functions, as are the tracker's float
+// intrinsics (__fmul_rn, __fadd_rd, rsqrtf, __fdividef).
 #pragma once
 #include <cuda_runtime.h>
 #include <algorithm>
@@ -161,6 +161,7 @@ inline void emu_run_block(int nt, const std::function<void()>& body, EmuDim bidx
   for (auto& x : th) x.join();
 }
 static std::mutex emu_atomic_mu;
+inline int atomicAdd(int* p, int v) { std::lock_guard<std::mutex> l(emu_atomic_mu); int o = *p; *p += v; return o; }
 inline int atomicExch(int* p, int v) { std::lock_guard<std::mutex> l(emu_atomic_mu); int o = *p; *p = v; return o; }
 inline unsigned long long atomicMax(unsigned long long* p, unsigned long long v) {
   std::lock_guard<std::mutex> l(emu_atomic_mu); unsigned long long o = *p; if (v > o) *p = v; return o; }

@@ -37,11 +37,12 @@ PYR_DETECT = os.path.join(ROOT, "oracle", "src", "pyramid_detect.cpp")
 def _host_copy(dst):
     shutil.copy(os.path.join(EMU, "tc05_emu.h"), os.path.join(dst, "tc05.cuh"))
     for name in ("common.cuh", "pyramid_dev.cuh", "detect_dev.cuh", "initnet_dev.cuh",
-                 "initnet_tc.cuh", "track_dev.cuh"):
+                 "initnet_tc.cuh", "track_dev.cuh", "frame.cuh", "finalize_dev.cuh"):
         s = open(os.path.join(CSRC, name)).read()
         s = re.sub(r'asm volatile\("bar\.sync (\d), %0;" ::"r"\(n\) : "memory"\);',
                    r"emu_bar(\1, n);", s)
         s = s.replace("__shared__ PassPlan plan;", "static PassPlan plan;")
+        s = s.replace("__shared__ int learned_s;", "static int learned_s;")
         open(os.path.join(dst, name), "w").write(s)
 
 
@@ -192,3 +193,127 @@ def test_tracker_on_host(tmp_path):
         compared += len(P)
         assert (got[:, 0] == 0).sum() >= len(P) // 3, got[:, 0]
     assert compared >= m + 8
+
+
+def _finalize_expected(W, H, cw, ch, k, cap, n0, n1, next_id, have_prev, trk_status, trk_xy,
+                       list_id, cand_count, cand, spec_status, spec_xy):
+    """One stream's finalisation written from its rules (Sec. III-B/III-D:
+    surviving tracks in order, cell occupancy of camera 0's survivors, per
+    cell in raster order the first k - occupancy candidates, new ids in
+    selection order, camera 1 gets the successful stereo matches of the new
+    keypoints, lists truncated to the capacity)."""
+    from oracle import frontend as ofe
+    gx, gy = W // cw, H // ch
+    n0, n1 = (min(n0, cap), min(n1, cap)) if have_prev else (0, 0)
+    ok0 = [i for i in range(n0) if trk_status[i] == 0]
+    ok1 = [i for i in range(n1) if trk_status[cap + i] == 0]
+    xy0 = [trk_xy[i] for i in ok0]
+    xy1 = [trk_xy[cap + i] for i in ok1]
+    id0 = [list_id[i] for i in ok0]
+    id1 = [list_id[cap + i] for i in ok1]
+    occ = ofe.occupancy(np.array(xy0, np.float32).reshape(-1, 2), W, H, cw, ch).reshape(-1)
+    new_xy, new_m = [], []
+    for cell in range(gx * gy):
+        nsel = max(0, min(k - min(int(occ[cell]), 255), int(cand_count[cell])))
+        for r in range(nsel):
+            q = cell * k + r
+            idx = (~int(cand[q])) & 0xffffffff
+            new_xy.append([float(idx % W), float(idx // W)])
+            if spec_status[q] == 0:
+                new_m.append((len(new_xy) - 1, spec_xy[q]))
+    ids = [next_id + o for o in range(len(new_xy))]
+    cam0_xy = (xy0 + new_xy)[:cap]
+    cam0_id = (id0 + ids)[:cap]
+    cam1_xy = (xy1 + [m[1] for m in new_m])[:cap]
+    cam1_id = (id1 + [ids[m[0]] for m in new_m])[:cap]
+    return {"count": [len(cam0_xy), len(cam1_xy)], "xy": [cam0_xy, cam1_xy],
+            "id": [cam0_id, cam1_id], "new_xy": new_xy[:cap], "new_count": min(len(new_xy), cap),
+            "next_id": next_id + len(new_xy), "occ": np.minimum(occ, 255),
+            "stats": [n0, n1, len(ok0), len(ok1), len(new_xy), len(new_m),
+                      int(np.sum(cand_count)), 0]}
+
+
+@pytest.mark.parametrize("case", ["one_pass", "first_frame", "truncated", "multi_pass"])
+def test_finalize_on_host(tmp_path, case):
+    """The finalisation's device code on the host (one emulated CTA of 1024
+    threads, every array its own exactly sized heap buffer under
+    AddressSanitizer) against its rules written out in the test: the one-pass
+    form (capacity and cells at most 1024), a first frame, lists truncated at
+    the capacity, and the multi-pass form (2000 slots, 1980 cells)."""
+    W, H, cw, ch, k = {"one_pass": (376, 240, 40, 40, 2), "first_frame": (376, 240, 40, 40, 2),
+                       "truncated": (376, 240, 40, 40, 3),
+                       "multi_pass": (1920, 1080, 32, 32, 1)}[case]
+    cells = (W // cw) * (H // ch)
+    cap = {"one_pass": 216, "first_frame": 216, "truncated": 120, "multi_pass": 2000}[case]
+    rng = np.random.default_rng({"one_pass": 1, "first_frame": 2, "truncated": 3,
+                                 "multi_pass": 4}[case])
+    n0, n1 = int(cap * 0.7), int(cap * 0.55)
+    if case == "truncated":
+        n0, n1 = cap - 3, cap - 10
+    have_prev = 0 if case == "first_frame" else 1
+    trk_status = np.where(rng.random(2 * cap) < 0.75, 0, rng.integers(1, 7, 2 * cap)).astype(
+        np.uint8)
+    trk_xy = np.stack([rng.uniform(-2, W + 2, 2 * cap), rng.uniform(-2, H + 2, 2 * cap)],
+                      1).astype(np.float32)
+    trk_xy[:8] = [[0, 0], [cw, ch], [cw - 1e-4, 0], [W - 1, H - 1], [-0.5, 3], [W - 0.001, 5],
+                  [(W // cw) * cw, 7], [3, (H // ch) * ch]]
+    # every cell edge and the float just below it, in x and in y (the cell of
+    # a position must be exact where x / cw rounds onto an integer)
+    edges = np.arange(1, W // cw + 1, dtype=np.float32) * np.float32(cw)
+    ex = np.concatenate([edges, np.nextafter(edges, np.float32(0))])
+    edges = np.arange(1, H // ch + 1, dtype=np.float32) * np.float32(ch)
+    ey = np.concatenate([edges, np.nextafter(edges, np.float32(0))])
+    m = min(len(ex), (n0 - 8) // 2)
+    trk_xy[8:8 + m, 0] = ex[:m]
+    m2 = min(len(ey), n0 - 8 - m)
+    trk_xy[8 + m:8 + m + m2, 1] = ey[:m2]
+    trk_status[:8 + m + m2] = 0
+    if case == "truncated":
+        trk_xy[:cap, 0] = -1.0     # camera-0 survivors outside the grid: no occupancy
+    list_id = rng.integers(0, 1 << 20, 2 * cap).astype(np.int32)
+    cand_count = rng.integers(0, k + 1, cells).astype(np.int32)
+    if case == "truncated":
+        cand_count[:] = k          # more new keypoints than the capacity
+    idx = rng.integers(0, W * H, cells * k).astype(np.uint64)
+    score = rng.integers(1, 255, cells * k).astype(np.uint64)
+    cand = ((score << np.uint64(32)) | (~idx & np.uint64(0xffffffff))).astype(np.uint64)
+    spec_status = np.where(rng.random(cells * k) < 0.8, 0, 5).astype(np.uint8)
+    spec_xy = rng.uniform(0, W, (cells * k, 2)).astype(np.float32)
+    next_id = 1000
+    inp, outp = tmp_path / "in.bin", tmp_path / "out.bin"
+    with open(inp, "wb") as f:
+        f.write(np.array([W, H, cw, ch, k, cap, n0, n1, next_id, have_prev], np.int32).tobytes())
+        for a in (trk_status, trk_xy, list_id, cand_count, cand, spec_status, spec_xy):
+            f.write(np.ascontiguousarray(a).tobytes())
+    _run(_build(tmp_path, "fin_check"), inp, outp, timeout=900, expect="finalised")
+    b = open(outp, "rb").read()
+    o = 0
+
+    def take(dt, n):
+        nonlocal o
+        a = np.frombuffer(b, dt, n, o)
+        o += a.nbytes
+        return a
+    cnt = take(np.int32, 2)
+    lxy = take(np.float32, 4 * cap).reshape(2, cap, 2)
+    lid = take(np.int32, 2 * cap).reshape(2, cap)
+    lst = take(np.uint8, 2 * cap).reshape(2, cap)
+    new_count = int(take(np.int32, 1)[0])
+    new_xy = take(np.float32, 2 * cap).reshape(cap, 2)
+    nid = int(take(np.int32, 1)[0])
+    occ = take(np.uint8, cells)
+    stats = take(np.int32, 8)
+    e = _finalize_expected(W, H, cw, ch, k, cap, n0, n1, next_id, have_prev, trk_status,
+                           trk_xy, list_id, cand_count, cand, spec_status, spec_xy)
+    assert cnt.tolist() == e["count"]
+    for c in range(2):
+        n = e["count"][c]
+        assert np.array_equal(lxy[c, :n], np.array(e["xy"][c], np.float32).reshape(-1, 2)), c
+        assert np.array_equal(lid[c, :n], np.array(e["id"][c], np.int32)), c
+        assert np.all(lst[c, :n] == 0) and np.all(lst[c, n:] == 255), c
+    assert new_count == e["new_count"] and nid == e["next_id"]
+    assert np.array_equal(new_xy[:new_count], np.array(e["new_xy"], np.float32).reshape(-1, 2))
+    assert np.array_equal(occ, e["occ"].astype(np.uint8))
+    assert stats.tolist() == e["stats"]
+    if case == "truncated":
+        assert e["count"][0] == cap and e["stats"][4] > cap
