@@ -72,12 +72,43 @@ def max_over_ranks(value: float, dist=None, device: str = "cpu") -> float:
     return float(t.item())
 
 
-def load_peaks():
+FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
+
+
+def _find_number(d, key):
+    """The first numeric value stored under `key` in a (possibly nested) dict."""
+    if isinstance(d, dict):
+        v = d.get(key)
+        if isinstance(v, (int, float)) and not isinstance(v, bool) and v > 0:
+            return float(v)
+        for x in d.values():
+            r = _find_number(x, key)
+            if r is not None:
+                return r
+    return None
+
+
+def load_peaks(path=None):
+    """The measured HBM copy bandwidth and BF16 GEMM rate of this machine's GPUs
+    (MEASURED_PEAKS.json, flat or nested), else the fallback figures; each
+    missing figure falls back on its own, and the source says which."""
+    path = path or os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
-        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-            return json.load(f), "measured"
-    except OSError:
-        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+        with open(path) as f:
+            d = json.load(f)
+    except (OSError, ValueError):
+        return dict(FALLBACK_PEAKS), "fallback"
+    out, missing = {}, []
+    for k in ("hbm_gbs", "bf16_tflops", "bf16_tflops_sustained"):
+        v = _find_number(d, k)
+        if v is not None:
+            out[k] = v
+        elif k in FALLBACK_PEAKS:
+            out[k] = FALLBACK_PEAKS[k]
+            missing.append(k)
+    if "hbm_gbs" in missing and "bf16_tflops" in missing:
+        return dict(FALLBACK_PEAKS), "fallback"
+    return out, "measured" if not missing else "measured (fallback: " + ", ".join(missing) + ")"
 
 
 class ClockSampler:
@@ -595,7 +626,8 @@ def frontend_config_run(torch, vio, name, w, h, n_streams, levels, cw, ch, n_fra
     """One frontend configuration over its own synthetic sequences (each
     stream its own seed), autotuned launch shapes, device-resident frames
     played forward and back: stereo frames/s (n_streams frames per step) and
-    per-step latency from a separate per-stage-events pass."""
+    per-step latency from a separate pass that records each step's first and
+    last event only."""
     import numpy as np
     from paper_2609_30459_gb300 import synth
     seqs = [synth.make_sequence(seed0 + i, n_frames, w, h, 1, max_motion=motion,

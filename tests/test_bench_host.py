@@ -1,6 +1,7 @@
 """Host logic of the benchmark, without a GPU: the clock record taken during
-the timed region (median SM clock, the throttle reasons that were active)
-and the percentile used for per-step latencies."""
+the timed region (median SM clock, the throttle reasons that were active),
+the percentile used for per-step latencies, and the reading of the measured
+peaks."""
 import os
 import sys
 
@@ -55,3 +56,21 @@ def test_percentile_nearest_rank():
     assert bench.percentile([3.0], 99) == 3.0
     assert bench.percentile([], 50) is None
     assert bench.percentile([5, 1, 3], 50) == 3   # unsorted input
+
+
+def test_load_peaks_flat_nested_missing_and_partial(tmp_path):
+    p = tmp_path / "peaks.json"
+    p.write_text('{"hbm_gbs": 6789.5, "bf16_tflops": 1907.0, "bf16_tflops_sustained": 1700}')
+    pk, src = bench.load_peaks(str(p))
+    assert src == "measured" and pk["hbm_gbs"] == 6789.5 and pk["bf16_tflops_sustained"] == 1700
+    p.write_text('{"gpu": {"name": "GB300", "peaks": {"hbm_gbs": 7000, "bf16_tflops": 2000}}}')
+    pk, src = bench.load_peaks(str(p))
+    assert src == "measured" and pk["hbm_gbs"] == 7000.0 and pk["bf16_tflops"] == 2000.0
+    p.write_text('{"hbm_gbs": 7000}')
+    pk, src = bench.load_peaks(str(p))
+    assert pk == {"hbm_gbs": 7000.0, "bf16_tflops": 1900.0} and "fallback: bf16_tflops" in src
+    p.write_text("not json")
+    assert bench.load_peaks(str(p)) == (bench.FALLBACK_PEAKS, "fallback")
+    assert bench.load_peaks(str(tmp_path / "absent.json"))[1] == "fallback"
+    p.write_text('{"hbm_gbs": "n/a", "bf16_tflops": true}')
+    assert bench.load_peaks(str(p))[1] == "fallback"
