@@ -88,6 +88,18 @@ def _find_number(d, key):
     return None
 
 
+def section(name, fn):
+    """fn() for one optional part of the report; an exception there is
+    reported as {"error": ...} in its place (traceback on stderr), so the
+    headline line is still printed."""
+    import traceback
+    try:
+        return fn()
+    except Exception as e:                       # noqa: BLE001 - reported, not hidden
+        traceback.print_exc()
+        return {"error": f"{name}: {type(e).__name__}: {e}"[:500]}
+
+
 def load_peaks(path=None):
     """The measured HBM copy bandwidth and BF16 GEMM rate of this machine's GPUs
     (MEASURED_PEAKS.json, flat or nested), else the fallback figures; each
@@ -1247,20 +1259,21 @@ def main():
         import numpy as np
         seqs3 = [synth.make_sequence(3000 + i, 100, 1920, 1080, 1, max_motion=40.0,
                                      tex_size=2048).frames for i in range(2)]
-        sel = selection_variants(torch, vio, torch.from_numpy(np.stack(seqs3, 1)).cuda(),
-                                 1920, 1080, 5, 48, 43)
+        sel = section("selection_variants", lambda: selection_variants(
+            torch, vio, torch.from_numpy(np.stack(seqs3, 1)).cuda(), 1920, 1080, 5, 48, 43))
         del seqs3
-        mbs = model_based_start(torch, vio)
-        lite = lite_vs_standard(torch, vio)
+        mbs = section("model_based_start", lambda: model_based_start(torch, vio))
+        lite = section("lite_vs_standard", lambda: lite_vs_standard(torch, vio))
         extra_cfgs = [
-            frontend_config_run(torch, vio, "cfg3 high-pixel: 4 cameras (2 stereo pairs) "
-                                "1920x1080, 100 frames, motion up to 40 px, 5 levels, 40x25 "
-                                "cells (1000 keypoints/image)", 1920, 1080, 2, 5, 48, 43, 100,
-                                40.0, 3000, args.batched_steps, roofline=(peaks, peak_src)),
-            frontend_config_run(torch, vio, "lite parameters (Sec. IV-D): minimum FAST threshold "
-                                "20, 82-px cells, 3 Gauss-Newton iterations; 752x480, 4 levels",
-                                752, 480, 1, 4, 82, 82, 100, 15.0, 2000, args.batched_steps,
-                                params_kw={"gn_iters": 3, "thresholds": (40, 20)})]
+            section("cfg3", lambda: frontend_config_run(
+                torch, vio, "cfg3 high-pixel: 4 cameras (2 stereo pairs) 1920x1080, 100 frames, "
+                "motion up to 40 px, 5 levels, 40x25 cells (1000 keypoints/image)", 1920, 1080,
+                2, 5, 48, 43, 100, 40.0, 3000, args.batched_steps, roofline=(peaks, peak_src))),
+            section("lite", lambda: frontend_config_run(
+                torch, vio, "lite parameters (Sec. IV-D): minimum FAST threshold 20, 82-px "
+                "cells, 3 Gauss-Newton iterations; 752x480, 4 levels", 752, 480, 1, 4, 82, 82,
+                100, 15.0, 2000, args.batched_steps,
+                params_kw={"gn_iters": 3, "thresholds": (40, 20)}))]
 
     # the 16 mixed-size sequences of cfg 4 (also the sessions' frames of cfg 5),
     # rendered once by a pool of host processes
@@ -1273,10 +1286,12 @@ def main():
         net = None
         if os.path.exists(initnet_train.DEFAULT_WEIGHTS):
             net = vio.InitNet.load(initnet_train.DEFAULT_WEIGHTS)
-        batched = batched_compare(torch, vio, args.batched_steps, args.warmup, net, seqs=seqs4)
-        if net is not None:
-            batched["initnet_tensor_roofline"] = initnet_tensor_roofline(torch, vio, net, peaks,
-                                                                         peak_src=peak_src)
+        batched = section("batched_16_streams", lambda: batched_compare(
+            torch, vio, args.batched_steps, args.warmup, net, seqs=seqs4))
+        if net is not None and "error" not in batched:
+            batched["initnet_tensor_roofline"] = section(
+                "initnet_tensor_roofline",
+                lambda: initnet_tensor_roofline(torch, vio, net, peaks, peak_src=peak_src))
     serve = None
     if rank == 0 and not args.no_serve:
         from paper_2609_30459_gb300 import initnet_train
@@ -1285,7 +1300,8 @@ def main():
             net = vio.InitNet.load(initnet_train.DEFAULT_WEIGHTS)
         # the batch's default tune: steps here hold one or two frames, for which
         # the fewest launches per step are best (the batched tune is for full steps)
-        serve = serving_run(torch, vio, args.serve_seconds, net, None, seqs=seqs4)
+        serve = section("serving_32_streams", lambda: serving_run(
+            torch, vio, args.serve_seconds, net, None, seqs=seqs4))
 
     cpu = None
     accuracy = None
@@ -1300,7 +1316,7 @@ def main():
                                "sample": "8 frames after 2 warm-up frames, one thread"}}
         # oracle-side accuracy of the same configs (the oracle runs on the host
         # here, beside its timing)
-        accuracy = accuracy_report(torch, vio, frames_np)
+        accuracy = section("accuracy", lambda: accuracy_report(torch, vio, frames_np))
 
     if rank == 0:
         line = {

@@ -74,3 +74,9 @@ def test_load_peaks_flat_nested_missing_and_partial(tmp_path):
     assert bench.load_peaks(str(tmp_path / "absent.json"))[1] == "fallback"
     p.write_text('{"hbm_gbs": "n/a", "bf16_tflops": true}')
     assert bench.load_peaks(str(p))[1] == "fallback"
+
+
+def test_section_reports_errors_in_place():
+    assert bench.section("ok", lambda: {"a": 1}) == {"a": 1}
+    r = bench.section("serving_32_streams", lambda: 1 / 0)
+    assert r == {"error": "serving_32_streams: ZeroDivisionError: division by zero"}
