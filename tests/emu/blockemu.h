@@ -162,6 +162,54 @@ inline void emu_run_block(int nt, const std::function<void()>& body, EmuDim bidx
 }
 static std::mutex emu_atomic_mu;
 inline int atomicAdd(int* p, int v) { std::lock_guard<std::mutex> l(emu_atomic_mu); int o = *p; *p += v; return o; }
+inline float atomicAdd(float* p, float v) { std::lock_guard<std::mutex> l(emu_atomic_mu); float o = *p; *p += v; return o; }
+
+// mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 of one warp, with the
+// fragment layout of the PTX ISA (groupID g = lane / 4, t = lane % 4):
+// A (16 x 16, row-major) a[0]: (g, 2t..2t+1), a[1]: (g+8, 2t..), a[2]:
+// (g, 2t+8..), a[3]: (g+8, 2t+8..); B (16 x 8) b0: rows 2t..2t+1 of column g,
+// b1: rows 2t+8..2t+9; C and D c0, c1: (g, 2t..2t+1), c2, c3: (g+8, 2t..);
+// the lower half of a 32-bit register holds the lower column (row of B).
+// Every lane posts its fragments, then computes its own four outputs.
+struct EmuMma { uint32_t a[32][4]; uint32_t b[32][2]; };
+inline EmuMma& emu_mma_buf() {
+  static std::mutex m;
+  static std::map<const void*, std::unique_ptr<EmuMma>> bufs;
+  std::lock_guard<std::mutex> l(m);
+  auto& p = bufs[&emu_warp()];
+  if (!p) p.reset(new EmuMma);
+  return *p;
+}
+inline float emu_bf16_bits(uint32_t w, int hi) {
+  const uint32_t u = (hi ? (w >> 16) : (w & 0xffffu)) << 16;
+  float f;
+  memcpy(&f, &u, 4);
+  return f;
+}
+inline void emu_mma16816(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+  EmuMma& M = emu_mma_buf();
+  const int lane = threadIdx.x & 31;
+  for (int i = 0; i < 4; ++i) M.a[lane][i] = a[i];
+  M.b[lane][0] = b0;
+  M.b[lane][1] = b1;
+  emu_warp().bar.wait();
+  auto A = [&](int r, int k) {
+    return emu_bf16_bits(M.a[(r & 7) * 4 + ((k & 7) >> 1)][(r >> 3) + 2 * (k >> 3)], k & 1);
+  };
+  auto B = [&](int k, int n) {
+    return emu_bf16_bits(M.b[n * 4 + ((k & 7) >> 1)][k >> 3], k & 1);
+  };
+  const int g = lane >> 2, t = lane & 3;
+  float out[4];
+  for (int e = 0; e < 4; ++e) {
+    const int r = g + 8 * (e >> 1), n = 2 * t + (e & 1);
+    float s = 0.f;
+    for (int k = 0; k < 16; ++k) s += A(r, k) * B(k, n);
+    out[e] = d[e] + s;
+  }
+  emu_warp().bar.wait();       // every lane has read the fragments
+  for (int e = 0; e < 4; ++e) d[e] = out[e];
+}
 inline int atomicExch(int* p, int v) { std::lock_guard<std::mutex> l(emu_atomic_mu); int o = *p; *p = v; return o; }
 inline unsigned long long atomicMax(unsigned long long* p, unsigned long long v) {
   std::lock_guard<std::mutex> l(emu_atomic_mu); unsigned long long o = *p; if (v > o) *p = v; return o; }

@@ -37,12 +37,15 @@ PYR_DETECT = os.path.join(ROOT, "oracle", "src", "pyramid_detect.cpp")
 def _host_copy(dst):
     shutil.copy(os.path.join(EMU, "tc05_emu.h"), os.path.join(dst, "tc05.cuh"))
     for name in ("common.cuh", "pyramid_dev.cuh", "detect_dev.cuh", "initnet_dev.cuh",
-                 "initnet_tc.cuh", "track_dev.cuh", "frame.cuh", "finalize_dev.cuh"):
+                 "initnet_tc.cuh", "track_dev.cuh", "frame.cuh", "finalize_dev.cuh",
+                 "initnet_train_dev.cuh"):
         s = open(os.path.join(CSRC, name)).read()
         s = re.sub(r'asm volatile\("bar\.sync (\d), %0;" ::"r"\(n\) : "memory"\);',
                    r"emu_bar(\1, n);", s)
         s = s.replace("__shared__ PassPlan plan;", "static PassPlan plan;")
         s = s.replace("__shared__ int learned_s;", "static int learned_s;")
+        s = re.sub(r'asm volatile\(\s*"mma\.sync\.aligned\.m16n8k16.*?\);',
+                   "emu_mma16816(d, a, b0, b1);", s, flags=re.S)
         open(os.path.join(dst, name), "w").write(s)
 
 
@@ -317,3 +320,56 @@ def test_finalize_on_host(tmp_path, case):
     assert stats.tolist() == e["stats"]
     if case == "truncated":
         assert e["count"][0] == cap and e["stats"][4] > cap
+
+
+@pytest.mark.parametrize("radius", [1.0, 3.0])
+def test_initnet_training_pass_on_host(tmp_path, radius):
+    """The flow network's training pass (per-warp forward on mma.sync tiles,
+    the loss, the FP32 backward, the gradient sums) on the host, its shared
+    memory exactly train_smem_bytes() under AddressSanitizer, against the
+    FP64 oracle's batch gradient at the GPU test's per-element bound; 14
+    samples over 4 warps, so warps take several samples and share the
+    accumulator."""
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
+    from initnet_util import GRAD_REL, KINK_MARGIN, _abs_grad, _kink_margin
+    rng = np.random.default_rng(11 + int(radius))
+    fan = {"w1": 36, "w2": 288, "w3": 288, "w4": 128, "w5": 64}
+    p = {k: (rng.normal(0, np.sqrt(2.0 / fan[k]), onet.SHAPES[k]) if k.startswith("w")
+             else rng.normal(0, 0.05, onet.SHAPES[k])) for k in onet.ORDER}
+    p = onet.unflatten(onet.flatten(p).astype(np.float32).astype(np.float64))
+    pb = {k: (onet.bf16_round(v) if k.startswith("w") else v) for k, v in p.items()}
+    n = 14
+    xs = []
+    while len(xs) < n:
+        xi = (rng.integers(0, 256, (4, 16, 16)).astype(np.float64) - 128) / 64
+        if _kink_margin(pb, xi) > KINK_MARGIN:
+            xs.append(xi)
+    x = np.stack(xs)
+    flows = []
+    for xi in x:
+        o = onet.forward(pb, xi, act_bf16=True)
+        r = rng.choice([rng.uniform(0.0, 0.8 * radius), rng.uniform(1.2 * radius, 6.0 * radius)])
+        a = rng.uniform(0, 2 * np.pi)
+        flows.append([o[0] * 16 + r * np.cos(a), o[1] * 16 + r * np.sin(a)])
+    flows = np.array(flows, np.float32).astype(np.float64)
+    loss_ref, g_ref = onet.batch_loss_grad(pb, x, flows, act_bf16=True, radius=radius)
+    g_abs = _abs_grad(pb, x, flows, radius)
+    xb = (x.reshape(n, -1).astype(np.float32).view(np.uint32) >> 16).astype(np.uint16)
+    inp, outp = tmp_path / "in.bin", tmp_path / "out.bin"
+    with open(inp, "wb") as f:
+        f.write(np.array([n], np.int32).tobytes())
+        f.write(np.array([1.0 / n, radius], np.float32).tobytes())
+        f.write(_packed(p))
+        f.write(xb.tobytes())
+        f.write(flows.astype(np.float32).tobytes())
+    _run(_build(tmp_path, "train_check"), inp, outp, timeout=1200, expect="trained")
+    out = np.fromfile(outp, np.float32)
+    grad, loss = out[:-1].astype(np.float64), float(out[-1])
+    assert loss / n == pytest.approx(loss_ref, rel=1e-3)
+    g = onet.unflatten(grad)
+    for k in onet.ORDER:
+        bound = GRAD_REL * g_abs[k] + 1e-7 * np.abs(g_abs[k]).max()
+        err = np.abs(g[k] - g_ref[k])
+        assert np.all(err <= bound), (k, float((err / np.maximum(bound, 1e-300)).max()))
+        assert np.median(err / np.maximum(g_abs[k], 1e-300)) < 1e-4, k
