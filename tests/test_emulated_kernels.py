@@ -373,3 +373,40 @@ def test_initnet_training_pass_on_host(tmp_path, radius):
         err = np.abs(g[k] - g_ref[k])
         assert np.all(err <= bound), (k, float((err / np.maximum(bound, 1e-300)).max()))
         assert np.median(err / np.maximum(g_abs[k], 1e-300)) < 1e-4, k
+
+
+@pytest.mark.parametrize("la,lb", [(2, 3), (1, 2)])
+def test_network_input_extraction_on_host(tmp_path, la, lb):
+    """The flow network's input, both device forms (the warp's extraction and
+    the frame launch's aligned-word prefetch with its per-byte BF16
+    conversion), read from levels between poisoned gaps with padded pitches
+    full of other bytes, bit for bit against the oracle's extraction:
+    interior keypoints, keypoints at and past the borders, positions on the
+    rounding half."""
+    from paper_2609_30459_gb300 import synth
+    oracle.build()
+    w, h, L = 218, 151, 4
+    seq = synth.make_sequence(7200, 2, w, h, 1, max_motion=6.0, tex_size=1024)
+    src = oracle.pyramid(seq.frames[0, 0], L)
+    dst = oracle.pyramid(seq.frames[1, 0], L)
+    rng = np.random.default_rng(la * 10 + lb)
+    pts = np.concatenate([
+        np.stack([rng.uniform(0, w, 20), rng.uniform(0, h, 20)], 1),
+        np.array([[0, 0], [w - 1, h - 1], [2, 75], [w - 3, 75], [100, 1], [100, h - 2],
+                  [-6, 40], [w + 5, 40], [40, -9], [40, h + 7], [12.0, 20.0], [14.0, 22.0],
+                  [63.999, 17.5], [64.0, 18.0]])]).astype(np.float32)
+    inp, outp = tmp_path / "in.bin", tmp_path / "out.bin"
+    with open(inp, "wb") as f:
+        f.write(np.array([L, len(pts), la, lb], np.int32).tobytes())
+        for l in range(L):
+            f.write(np.array(src[l].shape[::-1], np.int32).tobytes())
+            f.write(np.ascontiguousarray(src[l], np.uint8).tobytes())
+            f.write(np.ascontiguousarray(dst[l], np.uint8).tobytes())
+        f.write(pts.tobytes())
+    _run(_build(tmp_path, "netin_check"), inp, outp, timeout=600, expect="inputs")
+    got = np.fromfile(outp, np.uint16).reshape(len(pts), 2, 4, 16, 16)
+    for i, (x, y) in enumerate(pts):
+        ref = onet.extract(src, dst, float(x), float(y), la, lb)
+        bits = _bf16_bits(ref)
+        assert np.array_equal(got[i, 0], bits), ("warp", i, x, y)
+        assert np.array_equal(got[i, 1], bits), ("prefetch", i, x, y)
